@@ -1,0 +1,786 @@
+/*
+ * Plain CPU oracle for the RBF-FD explicit Poisson solver of
+ * Vehovar, Rot and Kosec, "Performance Trade-offs of High Order Meshless
+ * Approximation on Distributed Memory Systems" (arXiv 2502.12878).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may link, load or
+ * call this file: only the tests, the package's smoke check and the
+ * benchmark's CPU-baseline leg use it.  It shares no code, header, table or
+ * helper with the CUDA library; every routine below is written from the
+ * paper's definitions, in the paper's order, as plainly as possible.
+ *
+ * Floating point: FP64 throughout (the FP32 defect-correction emulation
+ * excepted).  Built with -ffp-contract=off, so every fused multiply-add in
+ * this file is an explicit fma()/fmaf() call and every other operation is a
+ * separately rounded IEEE operation.
+ *
+ * Routines and what they follow:
+ *   sm64_at            SplitMix64 (Steele, Lea & Flood 2014), counter form
+ *   oracle_nodes       jittered-grid stand-in for the Poisson-disc sampler
+ *                      of Sec. II-C (test problem); unit d-cube or disk
+ *   oracle_knn_brute   support = n nearest nodes incl. the centre (Sec. II,
+ *                      text after Eq. 1), ties by lower index
+ *   oracle_knn_kdtree  the same set, via a kd-tree (pinned to brute force)
+ *   oracle_weights     RBF-FD augmented system of Eq. 2-3, phi(r)=r^3,
+ *                      monomials up to order m, Gaussian elimination with
+ *                      partial pivoting in FP64
+ *   oracle_apply       Eq. 1 (stencil operator as a weighted sum)
+ *   oracle_solve_explicit  Jacobi-style explicit step, Eq. 6 (jacobi_step)
+ *   oracle_solve_dc    Eq. 6 with an FP32 inner iteration on the correction
+ *                      inside an FP64 defect-correction loop (paper silent)
+ *   oracle_adjoint     transpose of Eq. 6 for a sensor misfit (paper silent)
+ *   oracle_power_rho   spectral-radius estimate for the stability bound that
+ *                      Eq. 7 (cfl) only gives as a guideline
+ *   oracle_gepp_dense  dense Gaussian elimination used by the pin tests
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------------- */
+/* SplitMix64: the c-th output (c = 0, 1, ...) of the generator seeded with  */
+/* `seed`.  State after c+1 increments is seed + (c+1)*golden; the output is */
+/* the published two-round xor-shift-multiply finaliser of that state.       */
+/* ------------------------------------------------------------------------- */
+uint64_t sm64_at(uint64_t seed, uint64_t c)
+{
+    uint64_t z = seed + (c + 1u) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static double u01(uint64_t seed, uint64_t c)
+{
+    /* top 53 bits -> [0, 1) */
+    return (double)(sm64_at(seed, c) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Node generation.                                                          */
+/*                                                                           */
+/* The paper samples Omega with a Poisson-disc variant seeded from the       */
+/* boundary (Sec. II-C, last paragraph).  The stand-in used here is a        */
+/* jittered grid of spacing h = 1/Kg:                                        */
+/*  shape 0 (unit d-cube): generator indices (i0..i_{d-1}) in [0,Kg]^d, the  */
+/*    last axis fastest.  A node is a boundary node iff some index is 0 or   */
+/*    Kg, and then sits at (i*h) exactly; otherwise each coordinate is       */
+/*    i*h + (2U-1)*(jf*h) with U the (lin*d + axis)-th SplitMix64 draw.       */
+/*  shape 1 (disk, d = 2, centre (1/2,1/2), R = 1/2): every grid point is    */
+/*    jittered as above and kept iff |p - c|^2 < (R - h/2)^2; after them come */
+/*    Nb = round(2*pi*R/h) boundary nodes at angles 2*pi*k/Nb.                */
+/* ------------------------------------------------------------------------- */
+
+/* sin and cos on [0, pi/2] by their Taylor series (terms up to x^21 / x^20),  */
+/* Horner form, separately rounded operations.  Truncation < 2e-17.          */
+static void taylor_sincos(double x, double* s, double* c)
+{
+    double x2 = x * x;
+    double ps = 1.0, pc = 1.0;
+    /* sin x = x (1 - x^2/(2*3) (1 - x^2/(4*5) (1 - ...))) */
+    for (int k = 10; k >= 1; --k) {
+        double den_s = (double)((2 * k) * (2 * k + 1));
+        double den_c = (double)((2 * k - 1) * (2 * k));
+        ps = 1.0 - (x2 / den_s) * ps;
+        pc = 1.0 - (x2 / den_c) * pc;
+    }
+    *s = x * ps;
+    *c = pc;
+}
+
+/* angle 2*pi*k/Nb reduced to a quadrant and an offset in [0, pi/2) */
+static void disk_point(int64_t k, int64_t Nb, double R, double* px, double* py)
+{
+    const double two_pi = 6.283185307179586;
+    const double half_pi = 1.5707963267948966;
+    double a = (two_pi * (double)k) / (double)Nb;
+    int q = (int)(a / half_pi);
+    if (q > 3) q = 3;
+    double r = a - (double)q * half_pi;
+    if (r < 0.0) r = 0.0;
+    double s, c;
+    taylor_sincos(r, &s, &c);
+    double cx, cy;
+    switch (q) {
+        case 0: cx = c;  cy = s;  break;
+        case 1: cx = -s; cy = c;  break;
+        case 2: cx = -c; cy = -s; break;
+        default: cx = s; cy = -c; break;
+    }
+    *px = 0.5 + R * cx;
+    *py = 0.5 + R * cy;
+}
+
+static int64_t disk_nb(int Kg)
+{
+    const double two_pi = 6.283185307179586;
+    double h = 1.0 / (double)Kg;
+    return (int64_t)floor((two_pi * 0.5) / h + 0.5);
+}
+
+/* returns the node count; writes at most cap nodes (SoA, xyz[axis*cap + i]) */
+int64_t oracle_nodes(int d, int shape, int Kg, double jf, uint64_t seed,
+                     double* xyz, uint8_t* is_bnd, int64_t cap)
+{
+    if (d < 1 || d > 3 || Kg < 2) return -1;
+    if (shape == 1 && d != 2) return -1;
+    double h = 1.0 / (double)Kg;
+    double amp = jf * h;
+    int64_t side = (int64_t)Kg + 1;
+    int64_t total = 1;
+    for (int a = 0; a < d; ++a) total *= side;
+
+    int64_t out = 0;
+    for (int64_t lin = 0; lin < total; ++lin) {
+        int64_t gi[3] = {0, 0, 0};
+        int64_t rem = lin;
+        for (int a = d - 1; a >= 0; --a) { gi[a] = rem % side; rem /= side; }
+        int bnd = 0;
+        for (int a = 0; a < d; ++a)
+            if (gi[a] == 0 || gi[a] == Kg) bnd = 1;
+        double p[3];
+        if (shape == 0 && bnd) {
+            for (int a = 0; a < d; ++a) p[a] = (double)gi[a] * h;
+        } else {
+            for (int a = 0; a < d; ++a) {
+                double U = u01(seed, (uint64_t)lin * (uint64_t)d + (uint64_t)a);
+                p[a] = (double)gi[a] * h + (2.0 * U - 1.0) * amp;
+            }
+        }
+        if (shape == 1) {
+            double dx = p[0] - 0.5, dy = p[1] - 0.5;
+            double lim = 0.5 - 0.5 * h;
+            if (!(dx * dx + dy * dy < lim * lim)) continue;
+            bnd = 0;
+        }
+        if (out < cap) {
+            for (int a = 0; a < d; ++a) xyz[(int64_t)a * cap + out] = p[a];
+            is_bnd[out] = (uint8_t)bnd;
+        }
+        ++out;
+    }
+    if (shape == 1) {
+        int64_t Nb = disk_nb(Kg);
+        for (int64_t k = 0; k < Nb; ++k) {
+            if (out < cap) {
+                double px, py;
+                disk_point(k, Nb, 0.5, &px, &py);
+                xyz[out] = px;
+                xyz[cap + out] = py;
+                is_bnd[out] = 1;
+            }
+            ++out;
+        }
+    }
+    return out;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Squared distance, as both kNN routines and the weight build evaluate it:  */
+/* dx = x_j - x_c per axis, then fl(fl(dx0^2) + fl(dx1^2)) [+ fl(dx2^2)].    */
+/* ------------------------------------------------------------------------- */
+static double dist2(const double* xyz, int64_t N, int d, int64_t j, const double* q)
+{
+    double s = 0.0;
+    for (int a = 0; a < d; ++a) {
+        double dx = xyz[(int64_t)a * N + j] - q[a];
+        double sq = dx * dx;
+        s = (a == 0) ? sq : s + sq;
+    }
+    return s;
+}
+
+/* key order (d2, j): lexicographic */
+static int key_less(double da, int64_t ja, double db, int64_t jb)
+{
+    return da < db || (da == db && ja < jb);
+}
+
+/* insert (dd, j) into the sorted list (best first) of length *len <= n */
+static void topn_insert(double* bd, int32_t* bj, int* len, int n, double dd, int64_t j)
+{
+    int L = *len;
+    if (L == n && !key_less(dd, j, bd[n - 1], bj[n - 1])) return;
+    int pos = (L < n) ? L : n - 1;
+    while (pos > 0 && key_less(dd, j, bd[pos - 1], bj[pos - 1])) {
+        bd[pos] = bd[pos - 1];
+        bj[pos] = bj[pos - 1];
+        --pos;
+    }
+    bd[pos] = dd;
+    bj[pos] = (int32_t)j;
+    if (L < n) *len = L + 1;
+}
+
+/* Support of each centre: the n nodes with the smallest (d2, index) key,    */
+/* listed in increasing key order, so the centre itself comes first.          */
+int oracle_knn_brute(const double* xyz, int64_t N, int d, const int32_t* centres,
+                     int64_t nc, int n, int32_t* idx)
+{
+    if (n < 1 || n > N) return -1;
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(| : bad)
+    for (int64_t r = 0; r < nc; ++r) {
+        double q[3];
+        int64_t c = centres[r];
+        for (int a = 0; a < d; ++a) q[a] = xyz[(int64_t)a * N + c];
+        double* bd = (double*)malloc(sizeof(double) * (size_t)n);
+        int len = 0;
+        if (!bd) { bad = 1; continue; }
+        for (int64_t j = 0; j < N; ++j)
+            topn_insert(bd, idx + r * n, &len, n, dist2(xyz, N, d, j, q), j);
+        free(bd);
+    }
+    return bad ? -2 : 0;
+}
+
+/* ---------------------------- kd-tree ------------------------------------ */
+typedef struct {
+    int axis;        /* -1 for a leaf */
+    double split;
+    int64_t lo, hi;  /* range in perm[] for a leaf */
+    int64_t left, right;
+} kd_node;
+
+typedef struct {
+    const double* xyz;
+    int64_t N;
+    int d;
+    int64_t* perm;
+    kd_node* nodes;
+    int64_t count;
+} kd_tree;
+
+static const double* g_sort_coord; /* used only inside the single-threaded build */
+static int cmp_coord(const void* a, const void* b)
+{
+    int64_t ia = *(const int64_t*)a, ib = *(const int64_t*)b;
+    double va = g_sort_coord[ia], vb = g_sort_coord[ib];
+    if (va < vb) return -1;
+    if (va > vb) return 1;
+    return (ia < ib) ? -1 : (ia > ib);
+}
+
+static int64_t kd_build(kd_tree* t, int64_t lo, int64_t hi, int depth)
+{
+    int64_t me = t->count++;
+    kd_node* nd = &t->nodes[me];
+    if (hi - lo <= 8) {
+        nd->axis = -1;
+        nd->lo = lo;
+        nd->hi = hi;
+        return me;
+    }
+    int axis = depth % t->d;
+    g_sort_coord = t->xyz + (int64_t)axis * t->N;
+    qsort(t->perm + lo, (size_t)(hi - lo), sizeof(int64_t), cmp_coord);
+    int64_t mid = lo + (hi - lo) / 2;
+    double split = g_sort_coord[t->perm[mid]];
+    int64_t l = kd_build(t, lo, mid, depth + 1);
+    int64_t r = kd_build(t, mid, hi, depth + 1);
+    nd = &t->nodes[me];
+    nd->axis = axis;
+    nd->split = split;
+    nd->left = l;
+    nd->right = r;
+    return me;
+}
+
+/* Points left of the split have coordinate <= split, right ones >= split.
+ * A subtree is skipped only when the squared distance to its half-space,
+ * computed with the same rounded subtraction and square as dist2, exceeds
+ * the current n-th key strictly: rounding is monotone, so no point of the
+ * subtree can have a smaller computed d2, and ties are still visited. */
+static void kd_query(const kd_tree* t, int64_t ni, const double* q, double* bd,
+                     int32_t* bj, int* len, int n)
+{
+    const kd_node* nd = &t->nodes[ni];
+    if (nd->axis < 0) {
+        for (int64_t p = nd->lo; p < nd->hi; ++p) {
+            int64_t j = t->perm[p];
+            topn_insert(bd, bj, len, n, dist2(t->xyz, t->N, t->d, j, q), j);
+        }
+        return;
+    }
+    double diff = q[nd->axis] - nd->split;
+    int64_t near = diff <= 0.0 ? nd->left : nd->right;
+    int64_t far = diff <= 0.0 ? nd->right : nd->left;
+    kd_query(t, near, q, bd, bj, len, n);
+    double lb = diff * diff;
+    if (*len < n || !(lb > bd[n - 1])) kd_query(t, far, q, bd, bj, len, n);
+}
+
+int oracle_knn_kdtree(const double* xyz, int64_t N, int d, const int32_t* centres,
+                      int64_t nc, int n, int32_t* idx)
+{
+    if (n < 1 || n > N) return -1;
+    kd_tree t;
+    t.xyz = xyz;
+    t.N = N;
+    t.d = d;
+    t.perm = (int64_t*)malloc(sizeof(int64_t) * (size_t)N);
+    t.nodes = (kd_node*)malloc(sizeof(kd_node) * (size_t)(2 * N / 4 + 64));
+    t.count = 0;
+    if (!t.perm || !t.nodes) { free(t.perm); free(t.nodes); return -2; }
+    for (int64_t i = 0; i < N; ++i) t.perm[i] = i;
+    kd_build(&t, 0, N, 0);
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 256) reduction(| : bad)
+    for (int64_t r = 0; r < nc; ++r) {
+        double q[3];
+        int64_t c = centres[r];
+        for (int a = 0; a < d; ++a) q[a] = xyz[(int64_t)a * N + c];
+        double* bd = (double*)malloc(sizeof(double) * (size_t)n);
+        if (!bd) { bad = 1; continue; }
+        int len = 0;
+        kd_query(&t, 0, q, bd, idx + r * n, &len, n);
+        free(bd);
+    }
+    free(t.perm);
+    free(t.nodes);
+    return bad ? -2 : 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* RBF-FD weights (Eq. 2-3).                                                 */
+/*                                                                           */
+/* For centre x_c with support x_1..x_n (x_1 = x_c):                         */
+/*  sigma = max_j ||x_j - x_c||, xi_j = (x_j - x_c)/sigma per axis.          */
+/*  A_jk = phi(||xi_j - xi_k||), phi(r) = r^3 = (r*r)*r.                     */
+/*  P_ja = xi_j^alpha over the M = C(m+d, d) monomials of degree <= m in     */
+/*    graded order: degree ascending, then x exponent descending, then y     */
+/*    exponent descending; powers by repeated multiplication, the factors    */
+/*    multiplied in axis order.                                              */
+/*  RHS: (L Phi)_j = Laplacian of r^3 about x_j, at x_c:                     */
+/*    3(d+1) ||xi_j||;  (L p)_a = 2 for x^2, y^2, z^2 and 0 otherwise.       */
+/*  Solve [[A P];[P^T 0]] [w; lambda] = [L Phi; L p] (s = n + M unknowns)     */
+/*    by Gaussian elimination with partial pivoting (gepp_solve below).      */
+/*  w_j = x_j / sigma^2 (the Laplacian scales as 1/sigma^2).                  */
+/* ------------------------------------------------------------------------- */
+int oracle_num_monomials(int d, int m)
+{
+    /* C(m+d, d) */
+    int64_t num = 1, den = 1;
+    for (int k = 1; k <= d; ++k) { num *= (m + k); den *= k; }
+    return (int)(num / den);
+}
+
+/* exponents [M][3] in graded order */
+int oracle_monomials(int d, int m, int* ex)
+{
+    int M = 0;
+    for (int deg = 0; deg <= m; ++deg) {
+        if (d == 1) {
+            ex[3 * M + 0] = deg; ex[3 * M + 1] = 0; ex[3 * M + 2] = 0; ++M;
+        } else if (d == 2) {
+            for (int a = deg; a >= 0; --a) {
+                ex[3 * M + 0] = a; ex[3 * M + 1] = deg - a; ex[3 * M + 2] = 0; ++M;
+            }
+        } else {
+            for (int a = deg; a >= 0; --a)
+                for (int b = deg - a; b >= 0; --b) {
+                    ex[3 * M + 0] = a; ex[3 * M + 1] = b; ex[3 * M + 2] = deg - a - b; ++M;
+                }
+        }
+    }
+    return M;
+}
+
+static double ipow(double x, int e)
+{
+    double p = 1.0;
+    for (int k = 0; k < e; ++k) p = p * x;
+    return p;
+}
+
+/* Gaussian elimination with partial pivoting on the s x (s+1) row-major
+ * augmented matrix G (last column = right-hand side); solution in x.
+ * Elimination: for k = 0..s-1, pivot row p = first row i >= k with the
+ * largest |G[i][k]|; swap rows k and p; for every row i > k,
+ * l = G[i][k] / G[k][k] and G[i][j] = fma(-l, G[k][j], G[i][j]) for j > k.
+ * Back substitution by columns: for j = s-1..0, x_j = G[j][s] / G[j][j],
+ * then G[i][s] = fma(-G[i][j], x_j, G[i][s]) for every i < j.
+ * Returns 0, or 1 when a pivot is non-finite or |pivot| <= 1e-300. */
+int oracle_gepp_solve(int s, double* G, double* x)
+{
+    const int W = s + 1;
+    for (int k = 0; k < s; ++k) {
+        int p = k;
+        double best = fabs(G[(int64_t)k * W + k]);
+        for (int i = k + 1; i < s; ++i) {
+            double v = fabs(G[(int64_t)i * W + k]);
+            if (v > best) { best = v; p = i; }
+        }
+        if (!(best > 1e-300) || !isfinite(best)) return 1;
+        if (p != k)
+            for (int j = 0; j < W; ++j) {
+                double t = G[(int64_t)k * W + j];
+                G[(int64_t)k * W + j] = G[(int64_t)p * W + j];
+                G[(int64_t)p * W + j] = t;
+            }
+        double piv = G[(int64_t)k * W + k];
+        for (int i = k + 1; i < s; ++i) {
+            double l = G[(int64_t)i * W + k] / piv;
+            for (int j = k + 1; j < W; ++j)
+                G[(int64_t)i * W + j] = fma(-l, G[(int64_t)k * W + j], G[(int64_t)i * W + j]);
+        }
+    }
+    for (int j = s - 1; j >= 0; --j) {
+        double xj = G[(int64_t)j * W + s] / G[(int64_t)j * W + j];
+        if (!isfinite(xj)) return 1;
+        x[j] = xj;
+        for (int i = 0; i < j; ++i)
+            G[(int64_t)i * W + s] = fma(-G[(int64_t)i * W + j], xj, G[(int64_t)i * W + s]);
+    }
+    return 0;
+}
+
+/* one stencil; xyz is SoA with stride N; sup holds n node indices */
+int oracle_weights_one(const double* xyz, int64_t N, int d, const int32_t* sup, int n,
+                       int m, double* w_out)
+{
+    int ex[3 * 400];
+    if (oracle_num_monomials(d, m) > 400) return 2;
+    int M = oracle_monomials(d, m, ex);
+    int s = n + M;
+    int64_t c = sup[0];
+    double* xi = (double*)malloc(sizeof(double) * (size_t)(3 * n));
+    double* G = (double*)malloc(sizeof(double) * (size_t)s * (size_t)(s + 1));
+    double* x = (double*)malloc(sizeof(double) * (size_t)s);
+    if (!xi || !G || !x) { free(xi); free(G); free(x); return 2; }
+
+    /* scale: sigma = max_j sqrt(d2_j) */
+    double sigma = 0.0;
+    for (int j = 0; j < n; ++j) {
+        double s2 = 0.0;
+        for (int a = 0; a < d; ++a) {
+            double dx = xyz[(int64_t)a * N + sup[j]] - xyz[(int64_t)a * N + c];
+            double sq = dx * dx;
+            s2 = (a == 0) ? sq : s2 + sq;
+        }
+        double r = sqrt(s2);
+        if (r > sigma) sigma = r;
+    }
+    if (!(sigma > 0.0)) { free(xi); free(G); free(x); return 1; }
+    for (int j = 0; j < n; ++j)
+        for (int a = 0; a < d; ++a) {
+            double dx = xyz[(int64_t)a * N + sup[j]] - xyz[(int64_t)a * N + c];
+            xi[3 * j + a] = dx / sigma;
+        }
+
+    const int W = s + 1;
+    memset(G, 0, sizeof(double) * (size_t)s * (size_t)W);
+    for (int j = 0; j < n; ++j) {
+        for (int k = 0; k < n; ++k) {
+            double r2 = 0.0;
+            for (int a = 0; a < d; ++a) {
+                double t = xi[3 * j + a] - xi[3 * k + a];
+                double sq = t * t;
+                r2 = (a == 0) ? sq : r2 + sq;
+            }
+            double r = sqrt(r2);
+            G[(int64_t)j * W + k] = (r * r) * r;
+        }
+        for (int al = 0; al < M; ++al) {
+            double p = ipow(xi[3 * j + 0], ex[3 * al + 0]);
+            if (d >= 2) p = p * ipow(xi[3 * j + 1], ex[3 * al + 1]);
+            if (d >= 3) p = p * ipow(xi[3 * j + 2], ex[3 * al + 2]);
+            G[(int64_t)j * W + n + al] = p;
+            G[(int64_t)(n + al) * W + j] = p;
+        }
+        double rc2 = 0.0;
+        for (int a = 0; a < d; ++a) {
+            double sq = xi[3 * j + a] * xi[3 * j + a];
+            rc2 = (a == 0) ? sq : rc2 + sq;
+        }
+        G[(int64_t)j * W + s] = (double)(3 * (d + 1)) * sqrt(rc2);
+    }
+    for (int al = 0; al < M; ++al) {
+        int deg = ex[3 * al] + ex[3 * al + 1] + ex[3 * al + 2];
+        int pure2 = (deg == 2) && (ex[3 * al] == 2 || ex[3 * al + 1] == 2 || ex[3 * al + 2] == 2);
+        G[(int64_t)(n + al) * W + s] = pure2 ? 2.0 : 0.0;
+    }
+
+    int st = oracle_gepp_solve(s, G, x);
+    if (st == 0) {
+        double sig2 = sigma * sigma;
+        for (int j = 0; j < n; ++j) w_out[j] = x[j] / sig2;
+    }
+    free(xi);
+    free(G);
+    free(x);
+    return st;
+}
+
+/* all stencils; idx[r*n..] is the support of centre r; status[r] = 0 ok,
+ * 1 singular, 2 bad arguments.  Returns the number of non-zero statuses. */
+int64_t oracle_weights(const double* xyz, int64_t N, int d, const int32_t* idx, int64_t nc,
+                       int n, int m, double* w, int8_t* status)
+{
+    int64_t bad = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : bad)
+    for (int64_t r = 0; r < nc; ++r) {
+        int st = oracle_weights_one(xyz, N, d, idx + r * n, n, m, w + r * n);
+        status[r] = (int8_t)st;
+        if (st) {
+            bad += 1;
+            for (int j = 0; j < n; ++j) w[r * n + j] = 0.0;
+        }
+    }
+    return bad;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Eq. 1: (L u)(x_c) = sum_j w_j u(x_j), one row per centre, accumulated as  */
+/* an fma chain in support order starting from 0.                           */
+/* ------------------------------------------------------------------------- */
+void oracle_apply(const double* w, const int32_t* idx, int64_t nc, int n, const double* u,
+                  double* Lu)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < nc; ++r) {
+        double acc = 0.0;
+        for (int j = 0; j < n; ++j) acc = fma(w[r * n + j], u[idx[r * n + j]], acc);
+        Lu[r] = acc;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Eq. 6 (jacobi_step): u_i <- u_i + dt (Lu_i - f_i) at interior nodes,      */
+/* boundary values held.  Jacobi: every row reads the previous iterate.      */
+/* Per step k: r_i = (sum_j w_ij u^k_j) - f_i, u^{k+1}_i = fma(dt, r_i, u^k_i). */
+/* The stop test after step k uses R_k = max_i |r_i| (the residual of u^k):  */
+/* if R_k < tol the result is u^{k+1} and steps = k+1.  A non-finite R_k     */
+/* stops with status 2.  u: [N] in/out (interior entries are the start       */
+/* iterate, boundary entries the Dirichlet data); rows listed by interior.   */
+/* Returns 0 converged, 1 step cap reached, 2 non-finite.                    */
+/* ------------------------------------------------------------------------- */
+int oracle_solve_explicit(const double* w, const int32_t* idx, const int32_t* interior,
+                          int64_t N, int64_t NI, int n, const double* f, double* u,
+                          double dt, int64_t max_steps, double tol, int64_t* steps_out,
+                          double* res_out)
+{
+    double* v = (double*)malloc(sizeof(double) * (size_t)N);
+    if (!v) return -2;
+    memcpy(v, u, sizeof(double) * (size_t)N);
+    double* cur = u;
+    double* nxt = v;
+    int status = 1;
+    int64_t k = 0;
+    double R = 0.0;
+    for (k = 0; k < max_steps; ++k) {
+        R = 0.0;
+        int nonfinite = 0;
+#pragma omp parallel for schedule(static) reduction(max : R) reduction(| : nonfinite)
+        for (int64_t r = 0; r < NI; ++r) {
+            double acc = 0.0;
+            for (int j = 0; j < n; ++j) acc = fma(w[r * n + j], cur[idx[r * n + j]], acc);
+            double ri = acc - f[r];
+            int64_t i = interior[r];
+            nxt[i] = fma(dt, ri, cur[i]);
+            double a = fabs(ri);
+            if (!isfinite(a)) nonfinite = 1;
+            else if (a > R) R = a;
+        }
+        double* t = cur; cur = nxt; nxt = t;
+        if (nonfinite) { status = 2; R = INFINITY; ++k; break; }
+        if (R < tol) { status = 0; ++k; break; }
+    }
+    if (cur != u) memcpy(u, cur, sizeof(double) * (size_t)N);
+    free(v);
+    *steps_out = k;
+    *res_out = R;
+    return status;
+}
+
+/* ------------------------------------------------------------------------- */
+/* FP32 inner iteration inside FP64 defect correction (paper silent; the    */
+/* precision split is the build's).  Outer t: d = W u - f in FP64 (apply   */
+/* chain, then - f); D = max|d|; stop when D < tol.  Inner, on the          */
+/* correction e (float, e = 0 at start and on the boundary):                */
+/*   q_i = fmaf-chain of w32_ij e_j, rho_i = q_i + d32_i,                   */
+/*   e_i <- fmaf(dt32, rho_i, e_i),                                         */
+/* stopping after step k when max|rho| (of e^k) < rho_in * D, or at K_in.   */
+/* Then u_i += (double) e_i at interior nodes.                              */
+/* w32 = (float) w, d32 = (float) d, dt32 = (float) dt.                      */
+/* Returns 0 converged, 1 outer cap, 2 non-finite.                          */
+/* ------------------------------------------------------------------------- */
+int oracle_solve_dc(const double* w, const int32_t* idx, const int32_t* interior, int64_t N,
+                    int64_t NI, int n, const double* f, double* u, double dt, double tol,
+                    int64_t max_outer, int64_t K_in, double rho_in, int64_t* outer_out,
+                    int64_t* inner_total_out, double* res_out)
+{
+    float* w32 = (float*)malloc(sizeof(float) * (size_t)(NI * n));
+    float* e0 = (float*)calloc((size_t)N, sizeof(float));
+    float* e1 = (float*)calloc((size_t)N, sizeof(float));
+    float* d32 = (float*)malloc(sizeof(float) * (size_t)NI);
+    if (!w32 || !e0 || !e1 || !d32) { free(w32); free(e0); free(e1); free(d32); return -2; }
+    for (int64_t q = 0; q < NI * n; ++q) w32[q] = (float)w[q];
+    float dt32 = (float)dt;
+    int status = 1;
+    int64_t t = 0, inner_total = 0;
+    double D = 0.0;
+    for (t = 0; t <= max_outer; ++t) {
+        D = 0.0;
+        int nonfinite = 0;
+#pragma omp parallel for schedule(static) reduction(max : D) reduction(| : nonfinite)
+        for (int64_t r = 0; r < NI; ++r) {
+            double acc = 0.0;
+            for (int j = 0; j < n; ++j) acc = fma(w[r * n + j], u[idx[r * n + j]], acc);
+            double dr = acc - f[r];
+            d32[r] = (float)dr;
+            double a = fabs(dr);
+            if (!isfinite(a)) nonfinite = 1;
+            else if (a > D) D = a;
+        }
+        if (nonfinite) { status = 2; D = INFINITY; break; }
+        if (D < tol) { status = 0; break; }
+        if (t == max_outer) break;
+        memset(e0, 0, sizeof(float) * (size_t)N);
+        memset(e1, 0, sizeof(float) * (size_t)N);
+        float* ec = e0;
+        float* en = e1;
+        double lim = rho_in * D;
+        int inner_bad = 0;
+        for (int64_t k = 0; k < K_in; ++k) {
+            double Rin = 0.0;
+            int nf = 0;
+#pragma omp parallel for schedule(static) reduction(max : Rin) reduction(| : nf)
+            for (int64_t r = 0; r < NI; ++r) {
+                float acc = 0.0f;
+                for (int j = 0; j < n; ++j) acc = fmaf(w32[r * n + j], ec[idx[r * n + j]], acc);
+                float rho = acc + d32[r];
+                int64_t i = interior[r];
+                en[i] = fmaf(dt32, rho, ec[i]);
+                double a = fabs((double)rho);
+                if (!isfinite(a)) nf = 1;
+                else if (a > Rin) Rin = a;
+            }
+            float* tmp = ec; ec = en; en = tmp;
+            ++inner_total;
+            if (nf) { inner_bad = 1; break; }
+            if (Rin < lim) break;
+        }
+        if (inner_bad) { status = 2; D = INFINITY; break; }
+        for (int64_t r = 0; r < NI; ++r) {
+            int64_t i = interior[r];
+            u[i] = u[i] + (double)ec[i];
+        }
+    }
+    *outer_out = t;
+    *inner_total_out = inner_total;
+    *res_out = D;
+    free(w32); free(e0); free(e1); free(d32);
+    return status;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Adjoint of K explicit steps (paper silent; derived from Eq. 6).           */
+/* Forward: u^{k+1}_I = u^k_I + dt (W_II u^k_I + W_IB g - f), u^0 given.     */
+/* Loss L = sum_s (u^K_s - u_obs_s)^2 over sensor rows s (interior rows).    */
+/* lambda^K = dL/du^K (2 (u^K - u_obs) at sensors, 0 elsewhere);             */
+/* lambda^k = lambda^{k+1} + dt W_II^T lambda^{k+1}, k = K-1..0.             */
+/* dL/df = -dt sum_{k=1..K} lambda^k ;  dL/dg = dt W_IB^T sum_{k=1..K} lambda^k */
+/* dL/du^0_I = lambda^0.                                                     */
+/* (W^T lambda)_j is accumulated over rows i in ascending order as an fma    */
+/* chain from 0; the update is fma(dt, acc_j, lambda_j).                     */
+/* Inputs: lamK [NI] (rows), col_of_node [N] -> interior row or -1.          */
+/* Outputs: grad_f [NI], grad_g [N] (only boundary entries non-zero),        */
+/* lam0 [NI].  Sum of lambda is accumulated with plain additions in k order. */
+/* ------------------------------------------------------------------------- */
+int oracle_adjoint(const double* w, const int32_t* idx, const int32_t* interior, int64_t N,
+                   int64_t NI, int n, const double* lamK, int64_t K, double dt,
+                   double* grad_f, double* grad_g, double* lam0)
+{
+    double* lam = (double*)malloc(sizeof(double) * (size_t)NI);
+    double* acc = (double*)malloc(sizeof(double) * (size_t)N);
+    double* S = (double*)calloc((size_t)NI, sizeof(double));
+    int32_t* row_of = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);
+    if (!lam || !acc || !S || !row_of) { free(lam); free(acc); free(S); free(row_of); return -2; }
+    for (int64_t i = 0; i < N; ++i) row_of[i] = -1;
+    for (int64_t r = 0; r < NI; ++r) row_of[interior[r]] = (int32_t)r;
+    memcpy(lam, lamK, sizeof(double) * (size_t)NI);
+    for (int64_t k = K; k >= 1; --k) {
+        /* S += lambda^k */
+        for (int64_t r = 0; r < NI; ++r) S[r] = S[r] + lam[r];
+        /* lambda^{k-1} = lambda^k + dt W_II^T lambda^k */
+        for (int64_t i = 0; i < N; ++i) acc[i] = 0.0;
+        for (int64_t r = 0; r < NI; ++r)
+            for (int j = 0; j < n; ++j) {
+                int64_t col = idx[r * n + j];
+                acc[col] = fma(w[r * n + j], lam[r], acc[col]);
+            }
+        for (int64_t r = 0; r < NI; ++r) lam[r] = fma(dt, acc[interior[r]], lam[r]);
+    }
+    memcpy(lam0, lam, sizeof(double) * (size_t)NI);
+    for (int64_t r = 0; r < NI; ++r) grad_f[r] = -dt * S[r];
+    for (int64_t i = 0; i < N; ++i) acc[i] = 0.0;
+    for (int64_t r = 0; r < NI; ++r)
+        for (int j = 0; j < n; ++j) {
+            int64_t col = idx[r * n + j];
+            acc[col] = fma(w[r * n + j], S[r], acc[col]);
+        }
+    for (int64_t i = 0; i < N; ++i) grad_g[i] = (row_of[i] < 0) ? dt * acc[i] : 0.0;
+    free(lam); free(acc); free(S); free(row_of);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Spectral radius of W_II by power iteration from v (length NI, overwritten) */
+/* for `iters` steps: y = W_II v, rho = ||y||_2 / ||v||_2, v = y / ||y||_2.   */
+/* Boundary columns see 0.  Returns the last rho.                             */
+/* ------------------------------------------------------------------------- */
+double oracle_power_rho(const double* w, const int32_t* idx, const int32_t* interior,
+                        int64_t N, int64_t NI, int n, double* v, int iters)
+{
+    double* full = (double*)calloc((size_t)N, sizeof(double));
+    double* y = (double*)malloc(sizeof(double) * (size_t)NI);
+    if (!full || !y) { free(full); free(y); return -1.0; }
+    double nv = 0.0;
+    for (int64_t r = 0; r < NI; ++r) nv += v[r] * v[r];
+    nv = sqrt(nv);
+    for (int64_t r = 0; r < NI; ++r) v[r] = v[r] / nv;
+    double rho = 0.0;
+    for (int it = 0; it < iters; ++it) {
+        for (int64_t r = 0; r < NI; ++r) full[interior[r]] = v[r];
+        oracle_apply(w, idx, NI, n, full, y);
+        double ny = 0.0;
+        for (int64_t r = 0; r < NI; ++r) ny += y[r] * y[r];
+        ny = sqrt(ny);
+        rho = ny;
+        if (!(ny > 0.0)) break;
+        for (int64_t r = 0; r < NI; ++r) v[r] = y[r] / ny;
+    }
+    free(full);
+    free(y);
+    return rho;
+}
+
+/* dense s x s solve A x = b by the same elimination as the weight build
+ * (A row-major, overwritten); used by the pin tests on tiny problems */
+int oracle_gepp_dense(int s, const double* A, const double* b, double* x)
+{
+    double* G = (double*)malloc(sizeof(double) * (size_t)s * (size_t)(s + 1));
+    if (!G) return -2;
+    for (int i = 0; i < s; ++i) {
+        for (int j = 0; j < s; ++j) G[(int64_t)i * (s + 1) + j] = A[(int64_t)i * s + j];
+        G[(int64_t)i * (s + 1) + s] = b[i];
+    }
+    int st = oracle_gepp_solve(s, G, x);
+    free(G);
+    return st;
+}
+
+/* threads OpenMP would use for the parallel loops above */
+int oracle_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,175 @@
+"""Pins for the oracle's explicit iteration (Eq. 6), its stop rule, the
+stability estimate, FP32 defect correction, the adjoint and the error metric.
+
+Fixed by the mathematics rather than by the oracle's code:
+* the iteration's limit is the discrete solution W_II u = f - W_IB g (numpy LAPACK),
+* the start error -u*, close to the slowest mode sin(pi x) sin(pi y), decays
+  by (1 - dt d pi^2) per step,
+* the discrete solution converges to the closed form at order >= m - 1,
+* the power-iteration radius equals numpy's largest |eigenvalue|,
+* the loss is quadratic in (f, g), so central differences are exact up to
+  rounding and a dense reverse sweep in numpy gives the same gradient.
+"""
+import numpy as np
+import pytest
+
+import rbffd_inputs as gen
+from oracle_problem import build, dt_guideline, dt_stable
+
+
+def _fixed_point(p):
+    WII, WIB, bnd = p.dense()
+    return np.linalg.solve(WII, p.f - WIB @ p.u0[bnd])
+
+
+@pytest.mark.parametrize("m", [2, 4])
+def test_iteration_reaches_discrete_solution(orc, m):
+    p = build(orc, 2, 14, m, seed=3)
+    ustar = _fixed_point(p)
+    dt = dt_stable(orc, p)
+    u, steps, res, st = orc.solve_explicit(p.w, p.idx, p.interior, p.f, p.u0, dt, 200000, 1e-10)
+    assert st == 0 and res < 1e-10
+    assert np.max(np.abs(u[p.interior] - ustar)) < 1e-9
+    assert np.array_equal(u[p.is_bnd == 1], p.u0[p.is_bnd == 1])   # Dirichlet held
+
+
+def test_slowest_mode_decay_rate(orc):
+    p = build(orc, 2, 30, 4, seed=4)
+    ustar = _fixed_point(p)
+    dt = dt_stable(orc, p)
+    errs = []
+    u = p.u0
+    for k in range(3):
+        u, steps, res, st = orc.solve_explicit(p.w, p.idx, p.interior, p.f, u, dt, 2000, 0.0)
+        errs.append(np.max(np.abs(u[p.interior] - ustar)))
+    rate = (errs[2] / errs[1]) ** (1.0 / 2000)
+    expect = 1.0 - dt * 2 * np.pi ** 2
+    assert abs(np.log(rate) / np.log(expect) - 1.0) < 0.02
+
+
+def test_stop_rule_and_step_count(orc):
+    p = build(orc, 2, 10, 2, seed=5)
+    dt = dt_stable(orc, p)
+    u1, s1, r1, st1 = orc.solve_explicit(p.w, p.idx, p.interior, p.f, p.u0, dt, 7, 0.0)
+    assert (s1, st1) == (7, 1)
+    # residual of u^0 is max|W u^0 - f|; a tolerance just above it stops after one step
+    R0 = np.max(np.abs(orc.apply(p.w, p.idx, p.u0) - p.f))
+    u2, s2, r2, st2 = orc.solve_explicit(p.w, p.idx, p.interior, p.f, p.u0, dt, 100, R0 * 1.0001)
+    assert (s2, st2) == (1, 0) and r2 == R0
+    # that one step is u + dt (W u - f)
+    ref = p.u0.copy()
+    ref[p.interior] = p.u0[p.interior] + dt * (orc.apply(p.w, p.idx, p.u0) - p.f)
+    np.testing.assert_allclose(u2, ref, rtol=0, atol=1e-15)
+
+
+def test_nonfinite_source_stops(orc):
+    p = build(orc, 2, 10, 2, seed=5)
+    f = p.f.copy()
+    f[3] = np.nan
+    u, s, r, st = orc.solve_explicit(p.w, p.idx, p.interior, f, p.u0, dt_stable(orc, p), 50, 0.0)
+    assert st == 2 and s == 1
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("m,min_slope", [(2, 0.7), (4, 2.7), (6, 4.7)])
+def test_convergence_order(orc, m, min_slope):
+    errs, hs = [], []
+    for Kg in (24, 48, 96):
+        p = build(orc, 2, Kg, m, seed=6)
+        import scipy.sparse as sp
+        import scipy.sparse.linalg as spl
+        NI = p.NI
+        rows = np.repeat(np.arange(NI), p.n)
+        W = sp.csr_matrix((p.w.ravel(), (rows, p.idx.ravel())), shape=(NI, p.N))
+        WII = W[:, p.interior]
+        bnd = np.nonzero(p.is_bnd)[0]
+        rhs = p.f - W[:, bnd] @ p.u0[bnd]
+        u = spl.spsolve(WII.tocsc(), rhs)
+        errs.append(np.max(np.abs(u - p.ua[p.interior])))
+        hs.append(p.h)
+    slope = np.polyfit(np.log(hs), np.log(errs), 1)[0]
+    assert slope >= min_slope, (slope, errs)
+    # higher order is more accurate at the finest spacing (Sec. III-D)
+    assert errs[-1] < {2: 1e-3, 4: 1e-6, 6: 1e-8}[m]
+
+
+def test_power_rho_matches_eigenvalues(orc):
+    p = build(orc, 2, 12, 4, seed=8)
+    WII, _, _ = p.dense()
+    lam = np.linalg.eigvals(WII)
+    rho_ref = np.max(np.abs(lam))
+    rho = orc.power_rho(p.w, p.idx, p.interior, p.N, gen.random_vector(p.NI, 1), 3000)
+    assert abs(rho / rho_ref - 1) < 1e-3
+    # the eigenvalues sit in the left half plane (explicit step can be stable)
+    assert np.max(lam.real) < 0
+
+
+def test_stable_dt_is_stable_and_bounds_are_sharp(orc):
+    p = build(orc, 2, 16, 4, seed=9)
+    dt = orc.stable_dt(p.w, p.idx, p.interior, p.N, gen.random_vector(p.NI, 2), 400)
+    WII, _, _ = p.dense()
+    amp = np.max(np.abs(1 + dt * np.linalg.eigvals(WII)))
+    assert amp <= 1.0
+    # on jittered nodes rho(W_II) h^2 ~ 32, four times the 5-point stencil's 8, so the
+    # paper's alpha = 0.3 of the Eq. 7 guideline would already be unstable here
+    assert dt < 0.3 * p.h ** 2 / (2 * p.d)
+    amp_paper = np.max(np.abs(1 + dt_guideline(p, 0.3) * np.linalg.eigvals(WII)))
+    assert amp_paper > 1.0
+
+
+def test_defect_correction_reaches_fp64_solution(orc):
+    p = build(orc, 2, 14, 4, seed=10)
+    ustar = _fixed_point(p)
+    dt = dt_stable(orc, p)
+    u, outer, inner, res, st = orc.solve_dc(p.w, p.idx, p.interior, p.f, p.u0, dt, 1e-9,
+                                            60, 20000, 1e-3)
+    assert st == 0 and res < 1e-9
+    assert np.max(np.abs(u[p.interior] - ustar)) < 1e-10
+    assert outer >= 2          # the FP32 inner loop alone cannot get there
+
+
+def test_adjoint_matches_dense_reverse_sweep_and_fd(orc):
+    p = build(orc, 2, 9, 2, seed=11)
+    WII, WIB, bnd = p.dense()
+    dt, K = dt_stable(orc, p), 40
+    g = p.u0[bnd]
+    sens = gen.sensors(p.NI, 10, 3)
+    uobs = p.ua[p.interior][sens]
+
+    def forward(f, gb):
+        uI = np.zeros(p.NI)
+        for _ in range(K):
+            uI = uI + dt * (WII @ uI + WIB @ gb - f)
+        return uI
+
+    def loss(f, gb):
+        return np.sum((forward(f, gb)[sens] - uobs) ** 2)
+
+    uK = forward(p.f, g)
+    lamK = np.zeros(p.NI)
+    lamK[sens] = 2 * (uK[sens] - uobs)
+    gf, gg, l0 = orc.adjoint(p.w, p.idx, p.interior, p.N, lamK, K, dt)
+    # dense reverse sweep
+    lam, S = lamK.copy(), np.zeros(p.NI)
+    for _ in range(K):
+        S += lam
+        lam = lam + dt * (WII.T @ lam)
+    np.testing.assert_allclose(gf, -dt * S, rtol=1e-12, atol=1e-14 * np.abs(S).max() * dt)
+    np.testing.assert_allclose(gg[bnd], dt * (WIB.T @ S), rtol=1e-10,
+                               atol=1e-13 * np.abs(gg).max())
+    assert np.all(gg[p.interior] == 0)
+    np.testing.assert_allclose(l0, lam, rtol=1e-12, atol=1e-15)
+    # central differences along seeded directions (exact for a quadratic)
+    rng = np.random.default_rng(0)
+    for _ in range(5):
+        vf = rng.standard_normal(p.NI)
+        vg = rng.standard_normal(len(bnd))
+        eps = 1e-3
+        fd = (loss(p.f + eps * vf, g + eps * vg) - loss(p.f - eps * vf, g - eps * vg)) / (2 * eps)
+        an = gf @ vf + gg[bnd] @ vg
+        assert abs(fd - an) <= 1e-7 * max(abs(an), 1e-12)
+
+
+def test_mean_abs_error_definition(orc):
+    # Eq. 8 on a hand-made vector
+    assert orc.mean_abs_error([1.0, 2.0, 3.0], [1.0, 1.5, 4.0]) == pytest.approx(0.5)

@@ -1,0 +1,221 @@
+/*
+ * rbffd.h - C ABI of librbffd, a GB300 (sm_103a) implementation of the
+ * data-parallel hot path of the RBF-FD explicit Poisson solver of
+ * Vehovar, Rot and Kosec, "Performance Trade-offs of High Order Meshless
+ * Approximation on Distributed Memory Systems" (arXiv 2502.12878).
+ *
+ * Conventions, for every entry point:
+ *  - Pointers are DEVICE pointers unless the name starts with h_ (host).
+ *    All arrays are caller-owned; the library never frees them.  The only
+ *    memory the library owns is inside an rbffd_plan (freed by
+ *    rbffd_plan_destroy) and short-lived scratch taken from the stream-ordered
+ *    allocator (cudaMallocAsync on the given stream) and returned before the
+ *    call returns.
+ *  - Coordinates are structure-of-arrays FP64: xyz[a * N + i] is coordinate a
+ *    (a < d) of node i.  Node indices are int32.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *    enqueued on it; device outputs are valid once the stream has reached the
+ *    end of the call.  Host outputs (h_*, *_out) are written before return;
+ *    calls with host outputs synchronise the stream.
+ *  - Return value: RBFFD_OK (0), RBFFD_NOT_CONVERGED (1, a warning), or a
+ *    negative error code.  rbffd_last_error() gives a message for the last
+ *    failing call on this host thread.  Invalid arguments are rejected before
+ *    any device work is enqueued.
+ *  - Floating point follows IEEE round-to-nearest: products and sums that the
+ *    method defines as separate operations are separately rounded, and every
+ *    fused multiply-add is an explicit one (the library is compiled without
+ *    contraction).
+ */
+#ifndef RBFFD_H
+#define RBFFD_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RBFFD_API __attribute__((visibility("default")))
+#else
+#define RBFFD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RBFFD_OK 0
+#define RBFFD_NOT_CONVERGED 1      /* step / outer-iteration cap reached */
+#define RBFFD_ERR_ARG (-1)         /* invalid argument (nothing enqueued) */
+#define RBFFD_ERR_CUDA (-2)        /* CUDA runtime error */
+#define RBFFD_ERR_SINGULAR (-3)    /* a local weight system had no usable pivot */
+#define RBFFD_ERR_NONFINITE (-4)   /* residual became NaN or Inf */
+#define RBFFD_ERR_DIVERGED (-5)    /* residual grew 1e6-fold over its first value */
+#define RBFFD_ERR_TIMEOUT (-6)     /* an in-kernel wait gave up (no progress) */
+#define RBFFD_ERR_CAPACITY (-7)    /* output capacity or a compiled-in limit exceeded */
+
+/* plan flags */
+#define RBFFD_ORDER_MORTON 0       /* interior nodes first, each group in Morton order */
+#define RBFFD_ORDER_INPUT 1        /* interior nodes first, each group in input order */
+#define RBFFD_ORDER_RANDOM 2       /* interior nodes first, seeded random order */
+#define RBFFD_LAUNCH_GRAPH 0       /* one kernel per step, replayed from a CUDA graph */
+#define RBFFD_LAUNCH_PERSISTENT 16 /* one cooperative kernel runs many steps */
+
+typedef struct rbffd_plan rbffd_plan;
+
+/* Message for the last failing call on this host thread ("" if none). */
+RBFFD_API const char* rbffd_last_error(void);
+/* Library version, major*10000 + minor*100 + patch. */
+RBFFD_API int rbffd_version(void);
+
+/*
+ * rbffd_nodes - seeded jittered-grid node set.
+ * Stands in for the Poisson-disc node generator of Sec. II-C (test problem),
+ * which the paper uses to discretise the unit d-cube of Eq. 4-5.
+ *   d        2 or 3 (shape 0), 2 (shape 1)
+ *   shape    0: unit d-cube; grid of spacing h = 1/Kg, generator indices in
+ *               [0,Kg]^d with the last axis fastest; nodes with an index 0 or
+ *               Kg are boundary nodes on the exact grid position, the others
+ *               get an independent offset (2U-1)*jitter_frac*h per axis, U the
+ *               (lin*d+axis)-th output of SplitMix64(seed) mapped to [0,1).
+ *            1: disk of radius 1/2 about (1/2,1/2); every grid point is
+ *               jittered and kept iff it lies closer than 1/2 - h/2 to the
+ *               centre; then round(pi/h) boundary nodes at equal angles.
+ *   xyz      [d][cap] FP64 out, is_bnd [cap] out (1 = boundary node)
+ *   cap      capacity; with cap = 0 only the count is returned
+ *   h_n_out  host: number of nodes.  RBFFD_ERR_CAPACITY if it exceeds cap > 0.
+ */
+RBFFD_API int rbffd_nodes(int d, int shape, int Kg, double jitter_frac, uint64_t seed, double* xyz,
+                uint8_t* is_bnd, int64_t cap, int64_t* h_n_out, void* stream);
+
+/*
+ * rbffd_interior - ascending list of the interior (non-boundary) node indices.
+ *   interior [N] out (first *h_ni_out entries used), h_ni_out host count.
+ * The interior rows are where Eq. 6 (jacobi_step) updates u; boundary nodes
+ * carry Dirichlet data (Eq. 4).
+ */
+RBFFD_API int rbffd_interior(const uint8_t* is_bnd, int64_t N, int32_t* interior, int64_t* h_ni_out,
+                   void* stream);
+
+/*
+ * rbffd_knn - support selection (Sec. II, text after Eq. 1): for each centre,
+ * the n nearest of all N nodes, the centre itself included.
+ *   xyz      [d][N] coordinates; d in {1, 2, 3}; 1 <= n <= min(N, 128)
+ *   centres  [nc] node indices; idx [nc][n] out, row-major.
+ * Row r lists its n nodes by increasing key (d2, j), where
+ * d2 = fl(fl(dx0*dx0) + fl(dx1*dx1) [+ fl(dx2*dx2)]), dx = fl(x_j - x_c), so
+ * equal distances are ordered by node index and the centre comes first.
+ * Uses a uniform cell grid (counting sort) and ring search; scratch comes
+ * from cudaMallocAsync on `stream`.
+ */
+RBFFD_API int rbffd_knn(const double* xyz, int64_t N, int d, const int32_t* centres, int64_t nc, int n,
+              int32_t* idx, void* stream);
+
+/*
+ * rbffd_weights - RBF-FD weights of the Laplacian (Eq. 2-3), phi(r) = r^3
+ * with all monomials of degree <= m (M = C(m+d, d) of them; Sec. II).
+ *   idx [nc][n] supports (first entry = centre, as rbffd_knn returns them)
+ *   w   [nc][n] FP64 out; status [nc] int8 out: 0 ok, 1 singular.
+ *   s = n + M <= 128.
+ * Per row, in scaled coordinates xi = (x_j - x_c)/sigma, sigma the largest
+ * support distance: A_jk = r_jk^3, P_ja = xi_j^alpha (graded order: degree,
+ * then x exponent descending, then y descending), right-hand side
+ * 3(d+1)|xi_j| and 2 for the pure squares; the (n+M)^2 system is solved in
+ * FP64 by Gaussian elimination with partial pivoting (first row of largest
+ * |pivot|; multiplier by division, updates by fused multiply-add; back
+ * substitution by columns), and w_j = x_j / sigma^2.
+ * Returns RBFFD_ERR_SINGULAR if any row failed; h_n_bad / h_first_bad (host,
+ * may be NULL) receive the count and the first failing row.
+ */
+RBFFD_API int rbffd_weights(const double* xyz, int64_t N, int d, const int32_t* idx, int64_t nc, int n,
+                  int m, double* w, int8_t* status, int64_t* h_n_bad, int64_t* h_first_bad,
+                  void* stream);
+
+/*
+ * rbffd_apply - Eq. 1: Lu[r] = sum_j w[r][j] * u[idx[r][j]], accumulated as
+ * a fused multiply-add chain in support order starting from 0.
+ *   w, idx [nc][n] (row-major, as rbffd_weights / rbffd_knn give them),
+ *   u [N], Lu [nc] out.
+ */
+RBFFD_API int rbffd_apply(const double* w, const int32_t* idx, int64_t nc, int n, const double* u,
+                double* Lu, void* stream);
+
+/*
+ * rbffd_plan_create - device-resident solver plan for Eq. 6.
+ * Reorders the nodes (interior first, then by `flags` order), packs the
+ * stencils into 32-row slices (weights and neighbour indices interleaved so a
+ * warp reads them as contiguous 256-byte lines), keeps an FP32 copy of the
+ * weights for defect correction and the transposed interior operator for the
+ * adjoint.  All inputs are copied; they may be freed afterwards.
+ *   interior [NI] must list exactly the nodes with is_bnd == 0 (any order);
+ *   idx / w [NI][n] are the supports/weights of those rows.
+ *   flags: RBFFD_ORDER_* | RBFFD_LAUNCH_*; seed is used by RBFFD_ORDER_RANDOM.
+ *   *plan out.
+ */
+RBFFD_API int rbffd_plan_create(const double* xyz, const uint8_t* is_bnd, int64_t N, int d,
+                      const int32_t* interior, const int32_t* idx, const double* w, int64_t NI,
+                      int n, int flags, uint64_t seed, rbffd_plan** plan, void* stream);
+RBFFD_API int rbffd_plan_destroy(rbffd_plan* plan);
+/* node permutation of the plan: perm [N] out, perm[p] = original index of slot p */
+RBFFD_API int rbffd_plan_perm(const rbffd_plan* plan, int32_t* perm, void* stream);
+
+/*
+ * rbffd_solve_explicit - Eq. 6 (jacobi_step): u_i <- u_i + dt (Lu_i - f_i)
+ * at interior nodes, boundary values held; Jacobi order (every row reads the
+ * previous iterate).  Step k computes r_i = (sum_j w_ij u^k_j) - f_i and
+ * u^{k+1}_i = fma(dt, r_i, u^k_i); R_k = max_i |r_i|.  The run stops after
+ * step k when R_k < tol (result u^{k+1}, steps = k+1) or at max_steps.
+ *   f [NI] in the order of the plan's `interior` list; u [N] in/out: in, the
+ *   start iterate with the Dirichlet data on boundary nodes; out, the result.
+ *   dt: time step.  Eq. 7 (cfl) gives h^2/(2d) only as a guideline; use
+ *   rbffd_stable_dt for the bound of the actual operator.
+ *   precision 0: FP64.  precision 1: FP32 inner iteration inside FP64 defect
+ *   correction, see rbffd_solve_dc (its K_in/rho_in from
+ *   rbffd_plan_set_dc, its outer cap max(1, max_steps / K_in)).
+ *   h_steps_out, h_res_out (host, may be NULL): steps taken (precision 1:
+ *   inner steps in total) and the last residual max-norm.
+ * Returns RBFFD_OK, RBFFD_NOT_CONVERGED, RBFFD_ERR_NONFINITE,
+ * RBFFD_ERR_DIVERGED or RBFFD_ERR_TIMEOUT.
+ */
+RBFFD_API int rbffd_solve_explicit(rbffd_plan* plan, const double* f, double* u, double dt,
+                         int64_t max_steps, double tol, int precision, int64_t* h_steps_out,
+                         double* h_res_out, void* stream);
+
+/*
+ * rbffd_solve_dc - defect correction (the precision split is not in the
+ * paper).  Outer, FP64: d = W u - f, D = max|d|; stop when D < tol or after
+ * max_outer corrections.  Inner, FP32, on the correction e (0 at the start
+ * and on the boundary), w32 = (float) w, d32 = (float) d, dt32 = (float) dt:
+ *   rho_i = fmaf-chain(w32_ij e_j) + d32_i,  e_i <- fmaf(dt32, rho_i, e_i),
+ * stopping after step k when max|rho| (of e^k) < rho_in * D, or after K_in
+ * steps.  Then u_i += (double) e_i.
+ */
+RBFFD_API int rbffd_solve_dc(rbffd_plan* plan, const double* f, double* u, double dt, double tol,
+                   int64_t max_outer, int64_t K_in, double rho_in, int64_t* h_outer_out,
+                   int64_t* h_inner_out, double* h_res_out, void* stream);
+RBFFD_API int rbffd_plan_set_dc(rbffd_plan* plan, int64_t K_in, double rho_in);
+
+/*
+ * rbffd_stable_dt - stability bound of the explicit step for this operator.
+ * Eq. 7 (cfl) bounds dt by h^2/(2d) for regular nodes only; here the bound is
+ * 2 / (safety * rho), rho the spectral radius of the interior block W_II
+ * estimated by `iters` power iterations from v0 [NI] (plan's interior order):
+ * y = W_II v, rho = ||y||_2, v = y / rho.
+ */
+RBFFD_API int rbffd_stable_dt(rbffd_plan* plan, const double* v0, int iters, double safety,
+                    double* h_dt_out, double* h_rho_out, void* stream);
+
+/*
+ * rbffd_adjoint - gradients of a loss of the K-th iterate of Eq. 6 (the
+ * adjoint is not in the paper).  With u^{k+1}_I = u^k_I + dt (W_II u^k_I +
+ * W_IB g - f) and lamK = dL/du^K_I [NI]:
+ *   lambda^k = lambda^{k+1} + dt W_II^T lambda^{k+1}, k = K-1..0,
+ *   grad_f [NI] = -dt sum_{k=1..K} lambda^k,
+ *   grad_g [N]  = dt W_IB^T sum_{k=1..K} lambda^k (boundary entries; 0 inside),
+ *   lam0 [NI]   = lambda^0 = dL/du^0_I (may be NULL).
+ * (W^T v)_c is accumulated over rows in ascending interior-list order.
+ */
+RBFFD_API int rbffd_adjoint(rbffd_plan* plan, const double* lamK, int64_t K, double dt, double* grad_f,
+                  double* grad_g, double* lam0, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RBFFD_H */

@@ -1,0 +1,303 @@
+"""GB300 (sm_103a) RBF-FD explicit Poisson path: thin Python binding of librbffd.
+
+Vehovar, Rot and Kosec, "Performance Trade-offs of High Order Meshless
+Approximation on Distributed Memory Systems" (arXiv 2502.12878): the stencil
+operator of Eq. 1, the RBF-FD weights of Eq. 2-3 (phi(r) = r^3 plus monomials
+up to order m), and the explicit iteration of Eq. 6 for the Poisson problem of
+Eq. 4-5, all computed by the hand-written CUDA kernels in ``csrc/`` behind the
+C ABI of ``include/rbffd.h``.
+
+This module only marshals arguments: torch tensors provide device memory and
+the current CUDA stream; every step of the computation runs in librbffd.
+There is no CPU fallback.  If the library has not been built, every call raises
+``RbffdError`` (build it with ``paper_2502_12878_gb300.build.build()``).
+
+The functions keep the C names (``rbffd_nodes``, ``rbffd_knn``, ``rbffd_weights``,
+``rbffd_apply``, ``rbffd_solve_explicit`` ...).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "librbffd.so")
+
+RBFFD_OK = 0
+RBFFD_NOT_CONVERGED = 1
+RBFFD_ERR_ARG = -1
+RBFFD_ERR_CUDA = -2
+RBFFD_ERR_SINGULAR = -3
+RBFFD_ERR_NONFINITE = -4
+RBFFD_ERR_DIVERGED = -5
+RBFFD_ERR_TIMEOUT = -6
+RBFFD_ERR_CAPACITY = -7
+
+RBFFD_ORDER_MORTON = 0
+RBFFD_ORDER_INPUT = 1
+RBFFD_ORDER_RANDOM = 2
+RBFFD_LAUNCH_GRAPH = 0
+RBFFD_LAUNCH_PERSISTENT = 16
+
+EXPORTED = [
+    "rbffd_last_error", "rbffd_version", "rbffd_nodes", "rbffd_interior", "rbffd_knn",
+    "rbffd_weights", "rbffd_apply", "rbffd_plan_create", "rbffd_plan_destroy", "rbffd_plan_perm",
+    "rbffd_solve_explicit", "rbffd_solve_dc", "rbffd_plan_set_dc", "rbffd_stable_dt",
+    "rbffd_adjoint",
+]
+
+
+class RbffdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"librbffd error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """The loaded librbffd (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RbffdError(RBFFD_ERR_CUDA, f"{LIB_PATH} is missing: build it with "
+                         "paper_2502_12878_gb300.build.build() (needs nvcc)")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I, I64, D, U64 = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double,
+                         ctypes.c_uint64)
+    PI64 = ctypes.POINTER(ctypes.c_int64)
+    PD = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "rbffd_last_error": (ctypes.c_char_p, []),
+        "rbffd_version": (I, []),
+        "rbffd_nodes": (I, [I, I, I, D, U64, P, P, I64, PI64, P]),
+        "rbffd_interior": (I, [P, I64, P, PI64, P]),
+        "rbffd_knn": (I, [P, I64, I, P, I64, I, P, P]),
+        "rbffd_weights": (I, [P, I64, I, P, I64, I, I, P, P, PI64, PI64, P]),
+        "rbffd_apply": (I, [P, P, I64, I, P, P, P]),
+        "rbffd_plan_create": (I, [P, P, I64, I, P, P, P, I64, I, I, U64,
+                                  ctypes.POINTER(ctypes.c_void_p), P]),
+        "rbffd_plan_destroy": (I, [P]),
+        "rbffd_plan_perm": (I, [P, P, P]),
+        "rbffd_solve_explicit": (I, [P, P, P, D, I64, D, I, PI64, PD, P]),
+        "rbffd_solve_dc": (I, [P, P, P, D, D, I64, I64, D, PI64, PI64, PD, P]),
+        "rbffd_plan_set_dc": (I, [P, I64, D]),
+        "rbffd_stable_dt": (I, [P, P, I, D, PD, PD, P]),
+        "rbffd_adjoint": (I, [P, P, I64, D, P, P, P, P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _stream(device=None):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check(code: int, allow=(RBFFD_OK,)):
+    if code in allow:
+        return code
+    msg = lib().rbffd_last_error().decode(errors="replace")
+    raise RbffdError(code, msg)
+
+
+def _dev(t: torch.Tensor, dtype, name):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    return t.contiguous()
+
+
+# ------------------------------------------------------------------ entry points
+def rbffd_nodes(d: int, shape: int, Kg: int, jitter_frac: float, seed: int, device="cuda"):
+    """Jittered-grid node set.  Returns (xyz [d, N] float64, is_bnd [N] uint8)."""
+    L = lib()
+    n = ctypes.c_int64(0)
+    s = _stream(device)
+    _check(L.rbffd_nodes(d, shape, Kg, jitter_frac, seed, None, None, 0, ctypes.byref(n), s))
+    N = n.value
+    xyz = torch.empty((d, N), dtype=torch.float64, device=device)
+    bnd = torch.empty(N, dtype=torch.uint8, device=device)
+    _check(L.rbffd_nodes(d, shape, Kg, jitter_frac, seed, _ptr(xyz), _ptr(bnd), N,
+                         ctypes.byref(n), s))
+    return xyz, bnd
+
+
+def rbffd_interior(is_bnd: torch.Tensor) -> torch.Tensor:
+    """Ascending int32 list of interior node indices."""
+    is_bnd = _dev(is_bnd, torch.uint8, "is_bnd")
+    out = torch.empty(is_bnd.numel(), dtype=torch.int32, device=is_bnd.device)
+    ni = ctypes.c_int64(0)
+    _check(lib().rbffd_interior(_ptr(is_bnd), is_bnd.numel(), _ptr(out), ctypes.byref(ni),
+                                _stream(is_bnd.device)))
+    return out[: ni.value]
+
+
+def rbffd_knn(xyz: torch.Tensor, centres: torch.Tensor, n: int) -> torch.Tensor:
+    """Support of each centre: the n nearest nodes by (d^2, index), centre first."""
+    xyz = _dev(xyz, torch.float64, "xyz")
+    centres = _dev(centres, torch.int32, "centres")
+    d, N = xyz.shape
+    idx = torch.empty((centres.numel(), n), dtype=torch.int32, device=xyz.device)
+    _check(lib().rbffd_knn(_ptr(xyz), N, d, _ptr(centres), centres.numel(), n, _ptr(idx),
+                           _stream(xyz.device)))
+    return idx
+
+
+def rbffd_weights(xyz: torch.Tensor, idx: torch.Tensor, m: int, check: bool = True):
+    """RBF-FD Laplacian weights.  Returns (w [rows, n] float64, status [rows] int8)."""
+    xyz = _dev(xyz, torch.float64, "xyz")
+    idx = _dev(idx, torch.int32, "idx")
+    d, N = xyz.shape
+    rows, n = idx.shape
+    w = torch.empty((rows, n), dtype=torch.float64, device=xyz.device)
+    st = torch.empty(rows, dtype=torch.int8, device=xyz.device)
+    nbad = ctypes.c_int64(0)
+    first = ctypes.c_int64(0)
+    code = lib().rbffd_weights(_ptr(xyz), N, d, _ptr(idx), rows, n, m, _ptr(w), _ptr(st),
+                               ctypes.byref(nbad), ctypes.byref(first), _stream(xyz.device))
+    _check(code, (RBFFD_OK,) if check else (RBFFD_OK, RBFFD_ERR_SINGULAR))
+    return w, st
+
+
+def rbffd_apply(w: torch.Tensor, idx: torch.Tensor, u: torch.Tensor) -> torch.Tensor:
+    """Eq. 1 for every row: Lu[r] = sum_j w[r, j] u[idx[r, j]]."""
+    w = _dev(w, torch.float64, "w")
+    idx = _dev(idx, torch.int32, "idx")
+    u = _dev(u, torch.float64, "u")
+    rows, n = idx.shape
+    Lu = torch.empty(rows, dtype=torch.float64, device=u.device)
+    _check(lib().rbffd_apply(_ptr(w), _ptr(idx), rows, n, _ptr(u), _ptr(Lu), _stream(u.device)))
+    return Lu
+
+
+class Plan:
+    """Device-resident solver plan (rbffd_plan_create / rbffd_plan_destroy)."""
+
+    def __init__(self, xyz, is_bnd, interior, idx, w, flags=0, seed=0):
+        xyz = _dev(xyz, torch.float64, "xyz")
+        is_bnd = _dev(is_bnd, torch.uint8, "is_bnd")
+        interior = _dev(interior, torch.int32, "interior")
+        idx = _dev(idx, torch.int32, "idx")
+        w = _dev(w, torch.float64, "w")
+        self.d, self.N = xyz.shape
+        self.NI, self.n = idx.shape
+        self.device = xyz.device
+        self.flags = flags
+        self._h = ctypes.c_void_p(None)
+        _check(lib().rbffd_plan_create(_ptr(xyz), _ptr(is_bnd), self.N, self.d, _ptr(interior),
+                                       _ptr(idx), _ptr(w), self.NI, self.n, flags, seed,
+                                       ctypes.byref(self._h), _stream(self.device)))
+
+    @property
+    def handle(self):
+        if not self._h.value:
+            raise RbffdError(RBFFD_ERR_ARG, "plan already destroyed")
+        return self._h
+
+    def destroy(self):
+        if self._h is not None and self._h.value:
+            lib().rbffd_plan_destroy(self._h)
+            self._h = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def perm(self) -> torch.Tensor:
+        out = torch.empty(self.N, dtype=torch.int32, device=self.device)
+        _check(lib().rbffd_plan_perm(self.handle, _ptr(out), _stream(self.device)))
+        return out
+
+    def solve_explicit(self, f, u, dt, max_steps, tol=0.0, precision=0):
+        """Eq. 6 in place on ``u`` [N].  Returns (status, steps, last residual max-norm)."""
+        f = _dev(f, torch.float64, "f")
+        if not (u.is_cuda and u.dtype == torch.float64 and u.is_contiguous()):
+            raise ValueError("u must be a contiguous float64 CUDA tensor (updated in place)")
+        steps = ctypes.c_int64(0)
+        res = ctypes.c_double(0.0)
+        code = lib().rbffd_solve_explicit(self.handle, _ptr(f), _ptr(u), float(dt), int(max_steps),
+                                          float(tol), int(precision), ctypes.byref(steps),
+                                          ctypes.byref(res), _stream(self.device))
+        _check(code, (RBFFD_OK, RBFFD_NOT_CONVERGED))
+        return code, steps.value, res.value
+
+    def solve_dc(self, f, u, dt, tol, max_outer, K_in, rho_in):
+        """FP64 defect correction around an FP32 inner sweep, in place on ``u``.
+
+        Returns (status, outer corrections, inner steps in total, final defect max-norm)."""
+        f = _dev(f, torch.float64, "f")
+        if not (u.is_cuda and u.dtype == torch.float64 and u.is_contiguous()):
+            raise ValueError("u must be a contiguous float64 CUDA tensor (updated in place)")
+        outer = ctypes.c_int64(0)
+        inner = ctypes.c_int64(0)
+        res = ctypes.c_double(0.0)
+        code = lib().rbffd_solve_dc(self.handle, _ptr(f), _ptr(u), float(dt), float(tol),
+                                    int(max_outer), int(K_in), float(rho_in), ctypes.byref(outer),
+                                    ctypes.byref(inner), ctypes.byref(res), _stream(self.device))
+        _check(code, (RBFFD_OK, RBFFD_NOT_CONVERGED))
+        return code, outer.value, inner.value, res.value
+
+    def set_dc(self, K_in, rho_in):
+        _check(lib().rbffd_plan_set_dc(self.handle, int(K_in), float(rho_in)))
+
+    def stable_dt(self, v0, iters=200, safety=1.05):
+        """(2 / (safety * rho), rho) with rho the power-iteration radius of W_II."""
+        v0 = _dev(v0, torch.float64, "v0")
+        dt = ctypes.c_double(0.0)
+        rho = ctypes.c_double(0.0)
+        _check(lib().rbffd_stable_dt(self.handle, _ptr(v0), int(iters), float(safety),
+                                     ctypes.byref(dt), ctypes.byref(rho), _stream(self.device)))
+        return dt.value, rho.value
+
+    def adjoint(self, lamK, K, dt, want_lam0=True):
+        """Reverse sweep of K steps.  Returns (grad_f [NI], grad_g [N], lam0 [NI] or None)."""
+        lamK = _dev(lamK, torch.float64, "lamK")
+        gf = torch.empty(self.NI, dtype=torch.float64, device=self.device)
+        gg = torch.empty(self.N, dtype=torch.float64, device=self.device)
+        l0 = torch.empty(self.NI, dtype=torch.float64, device=self.device) if want_lam0 else None
+        _check(lib().rbffd_adjoint(self.handle, _ptr(lamK), int(K), float(dt), _ptr(gf), _ptr(gg),
+                                   _ptr(l0), _stream(self.device)))
+        return gf, gg, l0
+
+
+def rbffd_plan_create(xyz, is_bnd, interior, idx, w, flags=0, seed=0) -> Plan:
+    return Plan(xyz, is_bnd, interior, idx, w, flags, seed)
+
+
+def rbffd_solve_explicit(plan: Plan, f, u, dt, max_steps, tol=0.0, precision=0):
+    return plan.solve_explicit(f, u, dt, max_steps, tol, precision)
+
+
+def rbffd_solve_dc(plan: Plan, f, u, dt, tol, max_outer, K_in, rho_in):
+    return plan.solve_dc(f, u, dt, tol, max_outer, K_in, rho_in)
+
+
+def rbffd_stable_dt(plan: Plan, v0, iters=200, safety=1.05):
+    return plan.stable_dt(v0, iters, safety)
+
+
+def rbffd_adjoint(plan: Plan, lamK, K, dt):
+    return plan.adjoint(lamK, K, dt)
+
+
+def monomial_count(d: int, m: int) -> int:
+    """M = C(m + d, d) (Sec. II, text after Eq. 3)."""
+    return math.comb(m + d, d)

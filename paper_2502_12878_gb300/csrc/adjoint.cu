@@ -1,0 +1,291 @@
+// rbffd_adjoint: reverse sweep of K explicit steps of Eq. 6 (the adjoint is
+// an addition of this library; the paper only runs the forward iteration).
+//
+// The forward step is u^{k+1}_I = u^k_I + dt (W_II u^k_I + W_IB g - f).  Its
+// transpose needs W^T: built once per plan as a column-major copy of the
+// packed stencils (count per column, scan, scatter, then each column's
+// entries sorted by the caller's interior row so every column sums in the
+// same order as a row-ascending scatter would).  The columns are stored as
+// 32-column slices [slice][j][lane] padded to the slice's longest column with
+// zero weights, so the reverse step is the same coalesced thread-per-column
+// gather as the forward sweep - no atomics, deterministic.
+#include <math.h>
+
+#include <algorithm>
+
+#include "plan.cuh"
+
+namespace rbffd {
+
+struct Transpose {
+    int64_t nslices = 0;      // over all N columns
+    int64_t* off = nullptr;   // [nslices + 1] element offset of each slice
+    int32_t* len = nullptr;   // [nslices] padded length of each slice
+    int32_t* row = nullptr;   // row slot of each entry
+    double* w = nullptr;      // weight of each entry (0 for padding)
+    double* lam[2] = {nullptr, nullptr};   // [NI]
+    double* S = nullptr;      // [NI] sum of lambda^k
+};
+
+void free_transpose(rbffd_plan* p) {
+    if (!p || !p->tr) return;
+    Transpose* t = p->tr;
+    void* b[] = {t->off, t->len, t->row, t->w, t->lam[0], t->lam[1], t->S};
+    for (void* x : b)
+        if (x) cudaFree(x);
+    delete t;
+    p->tr = nullptr;
+}
+
+__global__ void tr_count(const int32_t* col, int64_t NI, int n, int32_t* cnt) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < NI;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        int64_t base = (p / SLICE) * (int64_t)n * SLICE + (p % SLICE);
+        for (int j = 0; j < n; ++j) atomicAdd(&cnt[col[base + j * SLICE]], 1);
+    }
+}
+
+__global__ void tr_scatter(const int32_t* col, const double* w64, const int32_t* row_of_slot,
+                           int64_t NI, int n, int32_t* cursor, int32_t* erow, int32_t* ekey,
+                           double* ew) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < NI;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        int64_t base = (p / SLICE) * (int64_t)n * SLICE + (p % SLICE);
+        for (int j = 0; j < n; ++j) {
+            int c = col[base + j * SLICE];
+            int pos = atomicAdd(&cursor[c], 1);
+            erow[pos] = (int32_t)p;
+            ekey[pos] = row_of_slot[p];
+            ew[pos] = w64[base + j * SLICE];
+        }
+    }
+}
+
+// each column's entries into ascending caller row order
+__global__ void tr_sort(const int32_t* start, int64_t N, int32_t* erow, int32_t* ekey, double* ew) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < N;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int b = start[c], e = start[c + 1];
+        for (int i = b + 1; i < e; ++i) {
+            int32_t k = ekey[i], r = erow[i];
+            double wv = ew[i];
+            int j = i - 1;
+            while (j >= b && ekey[j] > k) {
+                ekey[j + 1] = ekey[j];
+                erow[j + 1] = erow[j];
+                ew[j + 1] = ew[j];
+                --j;
+            }
+            ekey[j + 1] = k;
+            erow[j + 1] = r;
+            ew[j + 1] = wv;
+        }
+    }
+}
+
+__global__ void tr_slice_len(const int32_t* start, int64_t N, int64_t nsl, int32_t* len,
+                             int64_t* size) {
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < nsl;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        int L = 0;
+        for (int l = 0; l < SLICE; ++l) {
+            int64_t c = s * SLICE + l;
+            if (c < N) L = max(L, start[c + 1] - start[c]);
+        }
+        len[s] = L;
+        size[s] = (int64_t)L * SLICE;
+    }
+}
+
+__global__ void tr_fill(const int32_t* start, const int32_t* erow, const double* ew, int64_t N,
+                        int64_t nsl, const int64_t* off, const int32_t* len, int32_t* trow,
+                        double* tw) {
+    const int64_t total = nsl * SLICE;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < total;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int64_t s = c / SLICE, l = c % SLICE;
+        int L = len[s];
+        int b = c < N ? start[c] : 0, e = c < N ? start[c + 1] : 0;
+        for (int j = 0; j < L; ++j) {
+            int64_t o = off[s] + (int64_t)j * SLICE + l;
+            if (b + j < e) {
+                trow[o] = erow[b + j];
+                tw[o] = ew[b + j];
+            } else {
+                trow[o] = 0;
+                tw[o] = 0.0;
+            }
+        }
+    }
+}
+
+// exclusive scan of int64 slice sizes (single block; slice counts are modest)
+__global__ void scan64_single(const int64_t* in, int64_t n, int64_t* out) {
+    __shared__ int64_t carry;
+    __shared__ int64_t buf[256];
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t b = 0; b < n; b += 256) {
+        int64_t i = b + threadIdx.x;
+        buf[threadIdx.x] = i < n ? in[i] : 0;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int64_t run = carry;
+            for (int k = 0; k < 256 && b + k < n; ++k) {
+                int64_t v = buf[k];
+                out[b + k] = run;
+                run += v;
+            }
+            carry = run;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[n] = carry;
+}
+
+// one reverse step over interior columns c < NI:
+//   S_c += lam_c;  lam'_c = fma(dt, sum_rows w_rc lam_r, lam_c)
+__global__ void adjoint_step(const Transpose T, const int64_t NI, const double dt,
+                             const double* __restrict__ lam, double* __restrict__ lam_out,
+                             double* __restrict__ S) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nsl_int = (NI + SLICE - 1) / SLICE;
+    for (int64_t s = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); s < nsl_int;
+         s += (int64_t)gridDim.x * (blockDim.x / 32)) {
+        const int64_t c = s * SLICE + lane;
+        if (c >= NI) continue;
+        const int L = T.len[s];
+        const int64_t o = T.off[s] + lane;
+        double acc = 0.0;
+        for (int j = 0; j < L; ++j)
+            acc = __fma_rn(__ldcs(T.w + o + (int64_t)j * SLICE),
+                           __ldg(lam + __ldcs(T.row + o + (int64_t)j * SLICE)), acc);
+        const double lc = lam[c];
+        S[c] = __dadd_rn(S[c], lc);
+        lam_out[c] = __fma_rn(dt, acc, lc);
+    }
+}
+
+// boundary columns: grad_g[node] = dt * sum_rows w_rc S_r
+__global__ void adjoint_grad_g(const Transpose T, const int64_t NI, const int64_t N,
+                               const double dt, const double* __restrict__ S,
+                               const int32_t* perm, double* grad_g) {
+    for (int64_t c = NI + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < N;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = c / SLICE, lane = c % SLICE;
+        const int L = T.len[s];
+        const int64_t o = T.off[s] + lane;
+        double acc = 0.0;
+        for (int j = 0; j < L; ++j)
+            acc = __fma_rn(T.w[o + (int64_t)j * SLICE], S[T.row[o + (int64_t)j * SLICE]], acc);
+        grad_g[perm[c]] = __dmul_rn(dt, acc);
+    }
+}
+
+__global__ void adj_gather(const double* src, const int32_t* row_of_slot, int64_t NI,
+                           double* dst) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < NI;
+         p += (int64_t)gridDim.x * blockDim.x)
+        dst[p] = src[row_of_slot[p]];
+}
+
+__global__ void adj_outputs(const double* S, const double* lam, const int32_t* row_of_slot,
+                            const int32_t* perm, int64_t NI, double dt, double* grad_f,
+                            double* grad_g, double* lam0) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < NI;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        int32_t r = row_of_slot[p];
+        grad_f[r] = __dmul_rn(-dt, S[p]);
+        grad_g[perm[p]] = 0.0;
+        if (lam0) lam0[r] = lam[p];
+    }
+}
+
+static int build_transpose(rbffd_plan* p, cudaStream_t s) {
+    if (p->tr) return RBFFD_OK;
+    const int64_t N = p->N, NI = p->NI;
+    const int n = p->n;
+    const int64_t nnz = NI * n;
+    const int sms = device_sm_count();
+    Transpose* t = new Transpose();
+    t->nslices = (N + SLICE - 1) / SLICE;
+    Scratch start, cursor, erow, ekey, ew, tmp, size;
+    cudaError_t e = cudaSuccess;
+    int64_t total = 0;
+    do {
+        if ((e = start.alloc(sizeof(int32_t) * (N + 1), s))) break;
+        if ((e = cursor.alloc(sizeof(int32_t) * (N + 1), s))) break;
+        if ((e = erow.alloc(sizeof(int32_t) * nnz, s))) break;
+        if ((e = ekey.alloc(sizeof(int32_t) * nnz, s))) break;
+        if ((e = ew.alloc(sizeof(double) * nnz, s))) break;
+        if ((e = tmp.alloc(sizeof(int64_t) * scan_tmp_elems(N), s))) break;
+        if ((e = size.alloc(sizeof(int64_t) * t->nslices, s))) break;
+        if ((e = cudaMalloc((void**)&t->off, sizeof(int64_t) * (t->nslices + 1)))) break;
+        if ((e = cudaMalloc((void**)&t->len, sizeof(int32_t) * t->nslices))) break;
+        if ((e = cudaMemsetAsync(cursor.p, 0, sizeof(int32_t) * (N + 1), s))) break;
+        tr_count<<<sms * 8, 256, 0, s>>>(p->col, NI, n, cursor.as<int32_t>());
+        if ((e = exclusive_scan_i32(cursor.as<int32_t>(), start.as<int32_t>(), N,
+                                    tmp.as<int64_t>(), s)))
+            break;
+        if ((e = cudaMemcpyAsync(cursor.p, start.p, sizeof(int32_t) * N,
+                                 cudaMemcpyDeviceToDevice, s)))
+            break;
+        tr_scatter<<<sms * 8, 256, 0, s>>>(p->col, p->w64, p->row_of_slot, NI, n,
+                                           cursor.as<int32_t>(), erow.as<int32_t>(),
+                                           ekey.as<int32_t>(), ew.as<double>());
+        tr_sort<<<sms * 8, 256, 0, s>>>(start.as<int32_t>(), N, erow.as<int32_t>(),
+                                        ekey.as<int32_t>(), ew.as<double>());
+        tr_slice_len<<<sms * 4, 256, 0, s>>>(start.as<int32_t>(), N, t->nslices, t->len,
+                                             size.as<int64_t>());
+        scan64_single<<<1, 256, 0, s>>>(size.as<int64_t>(), t->nslices, t->off);
+        if ((e = cudaGetLastError())) break;
+        if ((e = cudaMemcpyAsync(&total, t->off + t->nslices, sizeof(int64_t),
+                                 cudaMemcpyDeviceToHost, s)))
+            break;
+        if ((e = cudaStreamSynchronize(s))) break;
+        if ((e = cudaMalloc((void**)&t->row, sizeof(int32_t) * std::max<int64_t>(total, 1)))) break;
+        if ((e = cudaMalloc((void**)&t->w, sizeof(double) * std::max<int64_t>(total, 1)))) break;
+        if ((e = cudaMalloc((void**)&t->lam[0], sizeof(double) * NI))) break;
+        if ((e = cudaMalloc((void**)&t->lam[1], sizeof(double) * NI))) break;
+        if ((e = cudaMalloc((void**)&t->S, sizeof(double) * NI))) break;
+        tr_fill<<<sms * 8, 256, 0, s>>>(start.as<int32_t>(), erow.as<int32_t>(), ew.as<double>(),
+                                        N, t->nslices, t->off, t->len, t->row, t->w);
+        e = cudaGetLastError();
+    } while (0);
+    p->tr = t;
+    if (e != cudaSuccess) {
+        set_error("rbffd_adjoint: building the transpose: %s", cudaGetErrorString(e));
+        free_transpose(p);
+        return RBFFD_ERR_CUDA;
+    }
+    return RBFFD_OK;
+}
+
+}  // namespace rbffd
+
+using namespace rbffd;
+
+extern "C" int rbffd_adjoint(rbffd_plan* p, const double* lamK, int64_t K, double dt,
+                             double* grad_f, double* grad_g, double* lam0, void* stream) {
+    clear_error();
+    RBFFD_ARG(p && lamK && grad_f && grad_g, "rbffd_adjoint: NULL argument");
+    RBFFD_ARG(K >= 0 && isfinite(dt), "rbffd_adjoint: bad K / dt");
+    cudaStream_t s = as_stream(stream);
+    int st = build_transpose(p, s);
+    if (st) return st;
+    Transpose& T = *p->tr;
+    const int sms = device_sm_count();
+    const unsigned G = (unsigned)sms * 8;
+    adj_gather<<<G, 256, 0, s>>>(lamK, p->row_of_slot, p->NI, T.lam[0]);
+    RBFFD_CHECK_CUDA(cudaMemsetAsync(T.S, 0, sizeof(double) * p->NI, s));
+    const int64_t nsl_int = (p->NI + SLICE - 1) / SLICE;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, (nsl_int + 7) / 8);
+    for (int64_t k = 0; k < K; ++k)
+        adjoint_step<<<grid, 256, 0, s>>>(T, p->NI, dt, T.lam[k & 1], T.lam[(k + 1) & 1], T.S);
+    RBFFD_CHECK_CUDA(cudaGetLastError());
+    adjoint_grad_g<<<G, 256, 0, s>>>(T, p->NI, p->N, dt, T.S, p->perm, grad_g);
+    adj_outputs<<<G, 256, 0, s>>>(T.S, T.lam[K & 1], p->row_of_slot, p->perm, p->NI, dt, grad_f,
+                                  grad_g, lam0);
+    RBFFD_CHECK_CUDA(cudaGetLastError());
+    return RBFFD_OK;
+}

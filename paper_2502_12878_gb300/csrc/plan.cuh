@@ -1,0 +1,68 @@
+// Internal layout of an rbffd_plan: the node permutation and the packed
+// (sliced-ELL) stencils that the explicit sweep streams, plus the device
+// control block shared by the step kernels.
+#pragma once
+
+#include "common.cuh"
+
+namespace rbffd {
+
+static constexpr int SLICE = 32;   // rows per slice = one warp
+
+// Device control block of a step loop.  Step kernels read their parameters
+// here (so a captured graph can be replayed with new ones) and the last block
+// of a step publishes the decision.
+struct StepCtrl {
+    unsigned long long res[3];   // per-step max |r| as IEEE bits (r >= 0 orders as uint64)
+    unsigned int arrive[3];      // blocks finished with step k (ring by k % 3)
+    unsigned int bar_count;      // grid barrier (persistent mode)
+    unsigned int bar_gen;
+    long long k;                 // steps taken so far
+    long long max_steps;
+    int done;                    // 0 running, 1 converged, 2 cap, 3 non-finite, 4 diverged, 5 timeout
+    int pad;
+    double dt;
+    double tol;
+    double res_first;            // R_0 of this run (divergence test)
+    double res_last;             // R of the last step taken
+};
+
+enum : int { DONE_RUNNING = 0, DONE_CONVERGED = 1, DONE_CAP = 2, DONE_NONFINITE = 3,
+             DONE_DIVERGED = 4, DONE_TIMEOUT = 5 };
+
+struct Transpose;
+void free_transpose(rbffd_plan* p);   // adjoint.cu
+
+// stable split of ids 0..N-1 by key != 0 (key 0 first, each group ascending)
+int split_by_flag(const int32_t* key, int64_t N, int32_t* out, int32_t* pos, int64_t* tmp,
+                  cudaStream_t s);
+
+}  // namespace rbffd
+
+struct rbffd_plan {
+    int d = 2;
+    int64_t N = 0, NI = 0;
+    int n = 0;
+    int flags = 0;
+    int64_t nslices = 0;
+    int32_t* perm = nullptr;        // [N] slot -> original node
+    int32_t* inv = nullptr;         // [N] original node -> slot
+    int32_t* row_of_slot = nullptr; // [NI] slot -> row of the caller's interior list
+    double* w64 = nullptr;          // [nslices][n][32]
+    float* w32 = nullptr;           // [nslices][n][32]
+    int32_t* col = nullptr;         // [nslices][n][32] neighbour slots
+    double* u[2] = {nullptr, nullptr};   // iterates in slot order [N]
+    double* fs = nullptr;           // f in slot order [NI]
+    float* e[2] = {nullptr, nullptr};    // DC correction [N]
+    float* d32 = nullptr;           // DC defect [NI]
+    double* scratch = nullptr;      // [2 * NI + 1024] reductions, power iteration
+    rbffd::StepCtrl* ctrl = nullptr;
+    int64_t dc_K_in = 20000;
+    double dc_rho_in = 1e-3;
+    // CUDA graphs of a chunk of step launches (built on first use)
+    void* graph64 = nullptr;
+    void* graph32 = nullptr;
+    int graph_chunk = 0;
+    int grid_steps = 0;             // blocks of a step launch
+    rbffd::Transpose* tr = nullptr;
+};

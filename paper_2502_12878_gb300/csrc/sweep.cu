@@ -1,0 +1,1132 @@
+// The explicit solver of Eq. 6 (jacobi_step) on one GPU:
+//   rbffd_apply           Eq. 1 on the caller's row-major layout
+//   rbffd_plan_create     node reordering + packed stencil layout
+//   rbffd_solve_explicit  FP64 sweep (or FP32 defect correction)
+//   rbffd_solve_dc        FP64 defect correction around an FP32 inner sweep
+//   rbffd_stable_dt       power-iteration bound for dt (Eq. 7 is a guideline)
+//
+// Layout.  Nodes are renumbered into "slots": interior nodes first, then
+// boundary nodes, each group in Morton order of a uniform cell grid (the
+// paper's subdomain idea of Sec. II-A reused as on-chip locality blocking).
+// Interior rows are grouped into slices of 32 rows; a slice stores its
+// weights and neighbour slots as [slice][j][lane], so one warp reads each
+// j-plane as a contiguous 256-byte (FP64) or 128-byte (FP32/int32) line.
+// Thread = row, so each row's sum is the same fused multiply-add chain in
+// support order as the definition.  Weights and indices are streamed with
+// evict-first loads; the iterate (8 bytes per node) stays in L2.
+//
+// Step loop.  One step = one pass over all rows.  Two launch modes:
+//  graph       one launch per step, a chunk of launches captured once into a
+//              CUDA graph and replayed; the last block of a step (atomic
+//              ticket) reads the step's residual max and publishes the stop
+//              decision to a device control block that later launches read.
+//  persistent  one cooperative launch runs the steps, separated by a grid
+//              barrier whose waits are bounded in time (RBFFD_ERR_TIMEOUT).
+// The residual max-norm is reduced warp -> block -> atomicMax on its IEEE
+// bits (non-negative doubles order like unsigned integers).
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "plan.cuh"
+
+namespace rbffd {
+
+static constexpr int STEP_THREADS = 256;
+static constexpr long long SPIN_LIMIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
+
+// ------------------------------------------------------------- utilities
+__device__ __forceinline__ unsigned long long dbits(double x) {
+    return (unsigned long long)__double_as_longlong(x);
+}
+__device__ __forceinline__ double bitsd(unsigned long long b) {
+    return __longlong_as_double((long long)b);
+}
+
+// block max of a non-negative value (NaN mapped to +Inf by the caller);
+// valid in thread 0
+__device__ __forceinline__ double block_max(double v) {
+    __shared__ double wm[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) wm[wid] = v;
+    __syncthreads();
+    double m = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, wm[w]);
+    __syncthreads();
+    return m;
+}
+
+// ---------------------------------------------------------- row kernels
+// Streaming loads of the stencil planes (read once per step: evict-first).
+// Plain (non-volatile) asm so the compiler may batch them ahead of use.
+__device__ __forceinline__ double ld_stream(const double* p) {
+    double v;
+    asm("ld.global.cs.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float ld_stream(const float* p) {
+    float v;
+    asm("ld.global.cs.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ int32_t ld_stream(const int32_t* p) {
+    int32_t v;
+    asm("ld.global.cs.s32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+// Gather of the iterate.  Within one launch per step the iterate is
+// read-only, so the non-coherent path (L1) is used; a persistent launch
+// rewrites it between steps from other SMs, so it reads through L2 (.cg).
+template <bool COHERENT, class T>
+__device__ __forceinline__ T ld_iter(const T* p) {
+    if (COHERENT) return __ldcg(p);
+    return __ldg(p);
+}
+
+// sum_j w_j u[col_j] as an fma chain from 0, j ascending.  Loads are issued
+// in phases of CH (indices, weights, then the gathers) so each thread keeps
+// 2*CH streaming loads and CH gathers in flight.
+template <int NN, bool COH, class T>
+__device__ __forceinline__ T row_dot(const T* __restrict__ w, const int32_t* __restrict__ col,
+                                     const T* __restrict__ u, int n) {
+    constexpr int CH = 16;
+    T acc = T(0);
+    const int nn = NN > 0 ? NN : n;
+#pragma unroll
+    for (int j0 = 0; j0 < (NN > 0 ? NN : 1 << 30); j0 += CH) {
+        if (NN == 0 && j0 >= nn) break;
+        int32_t c[CH];
+        T wv[CH], uv[CH];
+#pragma unroll
+        for (int t = 0; t < CH; ++t)
+            if (j0 + t < nn) c[t] = ld_stream(col + (j0 + t) * SLICE);
+#pragma unroll
+        for (int t = 0; t < CH; ++t)
+            if (j0 + t < nn) wv[t] = ld_stream(w + (j0 + t) * SLICE);
+#pragma unroll
+        for (int t = 0; t < CH; ++t)
+            if (j0 + t < nn) uv[t] = ld_iter<COH>(u + c[t]);
+#pragma unroll
+        for (int t = 0; t < CH; ++t)
+            if (j0 + t < nn) {
+                if constexpr (sizeof(T) == 8) acc = __fma_rn(wv[t], uv[t], acc);
+                else acc = __fmaf_rn(wv[t], uv[t], acc);
+            }
+    }
+    return acc;
+}
+
+template <int NN, bool COH = false>
+__device__ __forceinline__ double row_dot64(const double* __restrict__ w,
+                                            const int32_t* __restrict__ col,
+                                            const double* __restrict__ u, int n) {
+    return row_dot<NN, COH, double>(w, col, u, n);
+}
+
+template <int NN, bool COH = false>
+__device__ __forceinline__ float row_dot32(const float* __restrict__ w,
+                                           const int32_t* __restrict__ col,
+                                           const float* __restrict__ e, int n) {
+    return row_dot<NN, COH, float>(w, col, e, n);
+}
+
+enum : int { MODE_SWEEP64 = 0, MODE_INNER32 = 1 };
+
+struct StepArgs {
+    const double* w64;
+    const float* w32;
+    const int32_t* col;
+    const double* f;      // FP64 sweep: f in slot order
+    float* d32;           // FP32 inner: defect in slot order
+    double* u0;
+    double* u1;
+    float* e0;
+    float* e1;
+    int64_t NI;
+    int64_t nslices;
+    int n;
+};
+
+// one step over the slices owned by this warp (slice0, slice0 + stride, ...);
+// returns this thread's max |r| with NaN -> +Inf
+template <int NN, int MODE, bool COH>
+__device__ __forceinline__ double step_rows(const StepArgs& A, int par, double dt, float dt32,
+                                            int64_t slice0, int64_t stride) {
+    const int lane = threadIdx.x & 31;
+    double m = 0.0;
+    for (int64_t sl = slice0; sl < A.nslices; sl += stride) {
+        const int64_t row = sl * SLICE + lane;
+        const int64_t base = sl * (int64_t)A.n * SLICE + lane;
+        if (row < A.NI) {
+            if (MODE == MODE_SWEEP64) {
+                const double* uin = par ? A.u1 : A.u0;
+                double* uout = par ? A.u0 : A.u1;
+                double acc = row_dot64<NN, COH>(A.w64 + base, A.col + base, uin, A.n);
+                double r = __dsub_rn(acc, A.f[row]);
+                uout[row] = __fma_rn(dt, r, uin[row]);
+                double a = fabs(r);
+                m = (a != a) ? INFINITY : fmax(m, a);
+            } else {
+                const float* ein = par ? A.e1 : A.e0;
+                float* eout = par ? A.e0 : A.e1;
+                float acc = row_dot32<NN, COH>(A.w32 + base, A.col + base, ein, A.n);
+                float rho = __fadd_rn(acc, A.d32[row]);
+                eout[row] = __fmaf_rn(dt32, rho, ein[row]);
+                double a = fabs((double)rho);
+                m = (a != a) ? INFINITY : fmax(m, a);
+            }
+        }
+    }
+    return m;
+}
+
+// decision after step k with residual R (same rule in both launch modes);
+// returns the new `done` code
+__device__ __forceinline__ int decide(StepCtrl* c, long long k, double R) {
+    if (k == 0) c->res_first = R;
+    c->res_last = R;
+    c->k = k + 1;
+    if (!isfinite(R)) return DONE_NONFINITE;
+    if (R < c->tol) return DONE_CONVERGED;
+    double R0 = (k == 0) ? R : c->res_first;
+    if (R > 1e6 * R0 && R0 > 0.0) return DONE_DIVERGED;
+    if (k + 1 >= c->max_steps) return DONE_CAP;
+    return DONE_RUNNING;
+}
+
+// graph mode: one step per launch, one slice per warp
+template <int NN, int MODE>
+__global__ void __launch_bounds__(STEP_THREADS) step_kernel(StepArgs A, StepCtrl* c) {
+    __shared__ long long s_k;
+    __shared__ int s_skip;
+    __shared__ double s_dt;
+    if (threadIdx.x == 0) {
+        volatile StepCtrl* vc = c;
+        long long k = vc->k;
+        s_k = k;
+        s_skip = (vc->done != DONE_RUNNING) || (k >= vc->max_steps);
+        s_dt = vc->dt;
+    }
+    __syncthreads();
+    if (s_skip) return;
+    const long long k = s_k;
+    const int par = (int)(k & 1);
+    const int64_t warp = (int64_t)blockIdx.x * (STEP_THREADS / 32) + (threadIdx.x >> 5);
+    double m = step_rows<NN, MODE, false>(A, par, s_dt, (float)s_dt, warp,
+                                          (int64_t)gridDim.x * (STEP_THREADS / 32));
+    m = block_max(m);
+    if (threadIdx.x == 0) {
+        const int slot = (int)(k % 3);
+        atomicMax(&c->res[slot], dbits(m));
+        __threadfence();
+        unsigned t = atomicAdd(&c->arrive[slot], 1u);
+        if (t == gridDim.x - 1) {
+            __threadfence();
+            double R = bitsd(atomicAdd(&c->res[slot], 0ull));
+            int dn = decide(c, k, R);
+            c->res[slot] = 0ull;
+            c->arrive[slot] = 0u;
+            __threadfence();
+            c->done = dn;
+        }
+    }
+}
+
+// grid barrier for the cooperative launch; waits give up after
+// SPIN_LIMIT_CYCLES and report false
+__device__ bool grid_sync(StepCtrl* c) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* genp = &c->bar_gen;
+        unsigned g = *genp;
+        int ok = 1;
+        __threadfence();
+        unsigned t = atomicAdd(&c->bar_count, 1u);
+        if (t == gridDim.x - 1) {
+            atomicExch(&c->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&c->bar_gen, 1u);
+        } else {
+            long long t0 = clock64();
+            while (*genp == g) {
+                if (clock64() - t0 > SPIN_LIMIT_CYCLES) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// persistent mode: all steps in one cooperative launch
+template <int NN, int MODE>
+__global__ void __launch_bounds__(STEP_THREADS) persistent_kernel(StepArgs A, StepCtrl* c) {
+    __shared__ long long s_k, s_max;
+    __shared__ double s_dt;
+    __shared__ int s_stop;
+    if (threadIdx.x == 0) {
+        volatile StepCtrl* vc = c;
+        s_k = vc->k;
+        s_max = vc->max_steps;
+        s_dt = vc->dt;
+    }
+    __syncthreads();
+    const double dt = s_dt;
+    const long long kmax = s_max;
+    const int64_t warp = (int64_t)blockIdx.x * (STEP_THREADS / 32) + (threadIdx.x >> 5);
+    const int64_t nw = (int64_t)gridDim.x * (STEP_THREADS / 32);
+    for (long long k = s_k; k < kmax; ++k) {
+        double m = step_rows<NN, MODE, true>(A, (int)(k & 1), dt, (float)dt, warp, nw);
+        m = block_max(m);
+        if (threadIdx.x == 0) {
+            atomicMax(&c->res[k % 3], dbits(m));
+            if (blockIdx.x == 0) atomicExch(&c->res[(k + 1) % 3], 0ull);
+        }
+        if (!grid_sync(c)) {
+            if (threadIdx.x == 0) atomicExch(&c->done, DONE_TIMEOUT);
+            return;
+        }
+        if (threadIdx.x == 0) {
+            volatile unsigned long long* rp = &c->res[k % 3];
+            double R = bitsd(*rp);
+            // every block evaluates the same rule on the same value
+            int dn;
+            if (!isfinite(R)) dn = DONE_NONFINITE;
+            else if (R < c->tol) dn = DONE_CONVERGED;
+            else if (k > 0 && R > 1e6 * ((volatile StepCtrl*)c)->res_first &&
+                     ((volatile StepCtrl*)c)->res_first > 0.0) dn = DONE_DIVERGED;
+            else if (k + 1 >= kmax) dn = DONE_CAP;
+            else dn = DONE_RUNNING;
+            s_stop = dn;
+            if (blockIdx.x == 0) {
+                if (k == 0) c->res_first = R;
+                c->res_last = R;
+                c->k = k + 1;
+                if (dn != DONE_RUNNING) c->done = dn;
+            }
+        }
+        __syncthreads();
+        if (s_stop != DONE_RUNNING) return;
+        // res_first must be visible before the next step's divergence test
+        if (k == 0 && !grid_sync(c)) {
+            if (threadIdx.x == 0) atomicExch(&c->done, DONE_TIMEOUT);
+            return;
+        }
+    }
+}
+
+// ------------------------------------------------------ dispatch by n
+typedef void (*StepFn)(StepArgs, StepCtrl*);
+
+template <int MODE>
+static StepFn pick_step(int n, bool persistent) {
+#define RBFFD_CASE(NN) \
+    case NN: return persistent ? persistent_kernel<NN, MODE> : step_kernel<NN, MODE>;
+    switch (n) {
+        RBFFD_CASE(6)
+        RBFFD_CASE(12)
+        RBFFD_CASE(13)
+        RBFFD_CASE(20)
+        RBFFD_CASE(30)
+        RBFFD_CASE(31)
+        RBFFD_CASE(56)
+        RBFFD_CASE(57)
+        RBFFD_CASE(70)
+        RBFFD_CASE(71)
+        default: return persistent ? persistent_kernel<0, MODE> : step_kernel<0, MODE>;
+    }
+#undef RBFFD_CASE
+}
+
+// ------------------------------------------------------- plan building
+__device__ __forceinline__ uint32_t spread2(uint32_t x) {
+    x &= 0x0000ffffu;
+    x = (x | (x << 8)) & 0x00ff00ffu;
+    x = (x | (x << 4)) & 0x0f0f0f0fu;
+    x = (x | (x << 2)) & 0x33333333u;
+    x = (x | (x << 1)) & 0x55555555u;
+    return x;
+}
+__device__ __forceinline__ uint32_t spread3(uint32_t x) {
+    x &= 0x000003ffu;
+    x = (x | (x << 16)) & 0x030000ffu;
+    x = (x | (x << 8)) & 0x0300f00fu;
+    x = (x | (x << 4)) & 0x030c30c3u;
+    x = (x | (x << 2)) & 0x09249249u;
+    return x;
+}
+
+// key = (boundary ? cells : 0) + Morton index of the node's cell
+__global__ void morton_keys(const double* xyz, const uint8_t* is_bnd, int64_t N, GridGeom g,
+                            int64_t cells, int32_t* key) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t c[3] = {0, 0, 0};
+        for (int a = 0; a < g.d; ++a)
+            c[a] = (uint32_t)cell_coord(xyz[(int64_t)a * N + i], g.org[a], g.cs, g.G[a]);
+        uint32_t mk;
+        if (g.d == 1) mk = c[0];
+        else if (g.d == 2) mk = spread2(c[0]) | (spread2(c[1]) << 1);
+        else mk = spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[2]) << 2);
+        key[i] = (int32_t)((is_bnd[i] ? cells : 0) + (int64_t)mk);
+    }
+}
+
+__global__ void bnd_keys(const uint8_t* is_bnd, int64_t N, int32_t* key) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x)
+        key[i] = is_bnd[i] ? 1 : 0;
+}
+
+__global__ void invert_perm(const int32_t* perm, int64_t N, int32_t* inv) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N;
+         p += (int64_t)gridDim.x * blockDim.x)
+        inv[perm[p]] = (int32_t)p;
+}
+
+// random bijection of [0, NI) by a 4-round Feistel network on 2^(2b) with
+// cycle walking; keys from SplitMix64
+__device__ uint32_t feistel(uint32_t x, int hb, uint64_t seed) {
+    uint32_t mask = (1u << hb) - 1u;
+    uint32_t L = x >> hb, R = x & mask;
+    for (int r = 0; r < 4; ++r) {
+        uint64_t z = seed + (uint64_t)(r + 1) * 0x9E3779B97F4A7C15ull + R;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        uint32_t t = L ^ ((uint32_t)z & mask);
+        L = R;
+        R = t;
+    }
+    return (L << hb) | R;
+}
+
+__global__ void random_interior_perm(const int32_t* ordered, int64_t NI, int hb, uint64_t seed,
+                                     int32_t* perm) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < NI;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t x = (uint32_t)p;
+        do {
+            x = feistel(x, hb, seed);
+        } while ((int64_t)x >= NI);
+        perm[p] = ordered[x];
+    }
+}
+
+__global__ void check_interior(const uint8_t* is_bnd, const int32_t* interior, const int32_t* inv,
+                               int64_t N, int64_t NI, int32_t* row_of_slot, int* err) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < NI;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        int32_t node = interior[r];
+        if (node < 0 || node >= N || is_bnd[node]) {
+            atomicExch(err, 1);
+            continue;
+        }
+        int32_t p = inv[node];
+        if (p >= NI) {
+            atomicExch(err, 1);
+            continue;
+        }
+        if (atomicExch(&row_of_slot[p], (int32_t)r) != -1) atomicExch(err, 2);
+    }
+}
+
+__global__ void count_interior(const uint8_t* is_bnd, int64_t N, unsigned long long* cnt) {
+    unsigned long long c = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x)
+        c += is_bnd[i] ? 0 : 1;
+    atomicAdd(cnt, c);
+}
+
+__global__ void pack_stencils(const int32_t* row_of_slot, const int32_t* inv, const int32_t* idx,
+                              const double* w, int64_t NI, int64_t nslices, int n, int64_t N,
+                              double* w64, float* w32, int32_t* col, int* err) {
+    const int64_t total = nslices * SLICE;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        int64_t sl = p / SLICE, lane = p % SLICE;
+        int64_t base = sl * (int64_t)n * SLICE + lane;
+        int32_t r = p < NI ? row_of_slot[p] : -1;
+        if (p < NI && (r < 0 || r >= NI)) {
+            atomicExch(err, 2);   // slot not covered by the interior list
+            r = -1;
+        }
+        if (r >= 0) {
+            for (int j = 0; j < n; ++j) {
+                int32_t nb = idx[(int64_t)r * n + j];
+                if (nb < 0 || nb >= N) {
+                    atomicExch(err, 3);
+                    nb = 0;
+                }
+                double wv = w[(int64_t)r * n + j];
+                w64[base + j * SLICE] = wv;
+                w32[base + j * SLICE] = (float)wv;
+                col[base + j * SLICE] = inv[nb];
+            }
+        } else {
+            for (int j = 0; j < n; ++j) {
+                w64[base + j * SLICE] = 0.0;
+                w32[base + j * SLICE] = 0.0f;
+                col[base + j * SLICE] = 0;
+            }
+        }
+    }
+}
+
+__global__ void gather_f(const double* f, const int32_t* row_of_slot, int64_t NI, double* fs) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < NI;
+         p += (int64_t)gridDim.x * blockDim.x)
+        fs[p] = f[row_of_slot[p]];
+}
+
+__global__ void gather_u(const double* u, const int32_t* perm, int64_t N, double* a, double* b) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        double v = u[perm[p]];
+        a[p] = v;
+        b[p] = v;
+    }
+}
+
+__global__ void scatter_u(const double* us, const int32_t* perm, int64_t NI, double* u) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < NI;
+         p += (int64_t)gridDim.x * blockDim.x)
+        u[perm[p]] = us[p];
+}
+
+// --------------------------------------------------------- DC kernels
+// d = W u - f (FP64 chain), d32 = (float) d; max |d| into *dmax (bits)
+template <int NN>
+__global__ void __launch_bounds__(STEP_THREADS) defect_kernel(StepArgs A, const double* u,
+                                                              unsigned long long* dmax) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (int64_t)blockIdx.x * (STEP_THREADS / 32) + (threadIdx.x >> 5);
+    const int64_t nw = (int64_t)gridDim.x * (STEP_THREADS / 32);
+    double m = 0.0;
+    for (int64_t sl = warp; sl < A.nslices; sl += nw) {
+        const int64_t row = sl * SLICE + lane;
+        const int64_t base = sl * (int64_t)A.n * SLICE + lane;
+        if (row < A.NI) {
+            double acc = row_dot64<NN>(A.w64 + base, A.col + base, u, A.n);
+            double dr = __dsub_rn(acc, A.f[row]);
+            A.d32[row] = (float)dr;
+            double a = fabs(dr);
+            m = (a != a || isinf(a)) ? INFINITY : fmax(m, a);
+        }
+    }
+    m = block_max(m);
+    if (threadIdx.x == 0) atomicMax(dmax, dbits(m));
+}
+
+__global__ void dc_update(double* u, const float* e, int64_t NI) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < NI;
+         p += (int64_t)gridDim.x * blockDim.x)
+        u[p] = __dadd_rn(u[p], (double)e[p]);
+}
+
+// ----------------------------------------------- power iteration kernels
+// y = W_II v (v in slot order, boundary slots 0); partial sums of y^2 per block
+template <int NN>
+__global__ void __launch_bounds__(STEP_THREADS) power_apply(StepArgs A, const double* v, double* y,
+                                                            double* part) {
+    __shared__ double ws[STEP_THREADS / 32];
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (int64_t)blockIdx.x * (STEP_THREADS / 32) + (threadIdx.x >> 5);
+    const int64_t nw = (int64_t)gridDim.x * (STEP_THREADS / 32);
+    double s = 0.0;
+    for (int64_t sl = warp; sl < A.nslices; sl += nw) {
+        const int64_t row = sl * SLICE + lane;
+        const int64_t base = sl * (int64_t)A.n * SLICE + lane;
+        if (row < A.NI) {
+            double acc = row_dot64<NN>(A.w64 + base, A.col + base, v, A.n);
+            y[row] = acc;
+            s = __fma_rn(acc, acc, s);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < STEP_THREADS / 32; ++w) t += ws[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+// single block: norm = sqrt(sum part) in a fixed order; v = y / norm
+__global__ void power_normalize(const double* part, int nparts, const double* y, double* v,
+                                int64_t NI, double* norm_out) {
+    __shared__ double sh[256];
+    double t = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) t += part[i];
+    sh[threadIdx.x] = t;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    double nrm = sqrt(sh[0]);
+    if (threadIdx.x == 0) *norm_out = nrm;
+    for (int64_t p = threadIdx.x; p < NI; p += blockDim.x) v[p] = y[p] / nrm;
+}
+
+__global__ void power_scale(const double* norm, const double* y, double* v, int64_t NI) {
+    double nrm = *norm;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < NI;
+         p += (int64_t)gridDim.x * blockDim.x)
+        v[p] = y[p] / nrm;
+}
+
+__global__ void norm_partials(const double* v, int64_t NI, double* part) {
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < NI;
+         p += (int64_t)gridDim.x * blockDim.x)
+        s = __fma_rn(v[p], v[p], s);
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void sum_to_norm(const double* part, int nparts, double* norm_out) {
+    __shared__ double sh[256];
+    double t = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) t += part[i];
+    sh[threadIdx.x] = t;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *norm_out = sqrt(sh[0]);
+}
+
+// ------------------------------------------------------------ apply (Eq. 1)
+__global__ void apply_rowmajor(const double* w, const int32_t* idx, int64_t nc, int n,
+                               const double* u, double* Lu) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nc;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int j = 0; j < n; ++j)
+            acc = __fma_rn(w[r * n + j], __ldg(u + idx[r * n + j]), acc);
+        Lu[r] = acc;
+    }
+}
+
+// ------------------------------------------------------------ host side
+static StepArgs make_args(const rbffd_plan* p) {
+    StepArgs A;
+    A.w64 = p->w64;
+    A.w32 = p->w32;
+    A.col = p->col;
+    A.f = p->fs;
+    A.d32 = p->d32;
+    A.u0 = p->u[0];
+    A.u1 = p->u[1];
+    A.e0 = p->e[0];
+    A.e1 = p->e[1];
+    A.NI = p->NI;
+    A.nslices = p->nslices;
+    A.n = p->n;
+    return A;
+}
+
+static void free_plan(rbffd_plan* p) {
+    if (!p) return;
+    void* bufs[] = {p->perm, p->inv, p->row_of_slot, p->w64, p->w32, p->col, p->u[0], p->u[1],
+                    p->fs, p->e[0], p->e[1], p->d32, p->scratch, p->ctrl};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    if (p->graph64) cudaGraphExecDestroy((cudaGraphExec_t)p->graph64);
+    if (p->graph32) cudaGraphExecDestroy((cudaGraphExec_t)p->graph32);
+    free_transpose(p);
+    delete p;
+}
+
+static int step_grid(const rbffd_plan* p) {
+    int64_t warps = p->nslices;
+    int64_t blocks = (warps + STEP_THREADS / 32 - 1) / (STEP_THREADS / 32);
+    return (int)std::max<int64_t>(1, blocks);
+}
+
+static int persistent_grid(StepFn fn) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)fn, STEP_THREADS, 0) !=
+            cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    return per_sm * device_sm_count();
+}
+
+// reset the control block for a run of at most max_steps steps
+static int ctrl_reset(rbffd_plan* p, double dt, double tol, long long max_steps, cudaStream_t s) {
+    StepCtrl h;
+    memset(&h, 0, sizeof(h));
+    h.max_steps = max_steps;
+    h.dt = dt;
+    h.tol = tol;
+    h.done = max_steps <= 0 ? DONE_CAP : DONE_RUNNING;
+    RBFFD_CHECK_CUDA(cudaMemcpyAsync(p->ctrl, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+    return RBFFD_OK;
+}
+
+// build (once) a graph of `chunk` step launches of the given mode
+static int ensure_graph(rbffd_plan* p, int mode) {
+    void** slot = mode == MODE_SWEEP64 ? &p->graph64 : &p->graph32;
+    if (*slot) return RBFFD_OK;
+    StepFn fn = mode == MODE_SWEEP64 ? pick_step<MODE_SWEEP64>(p->n, false)
+                                     : pick_step<MODE_INNER32>(p->n, false);
+    cudaStream_t cs;
+    RBFFD_CHECK_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    StepArgs A = make_args(p);
+    int grid = step_grid(p);
+    cudaGraph_t g;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        for (int i = 0; i < p->graph_chunk; ++i) fn<<<grid, STEP_THREADS, 0, cs>>>(A, p->ctrl);
+        e = cudaStreamEndCapture(cs, &g);
+    }
+    if (e == cudaSuccess) {
+        cudaGraphExec_t ex;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e == cudaSuccess) *slot = (void*)ex;
+    }
+    cudaStreamDestroy(cs);
+    RBFFD_CHECK_CUDA(e);
+    return RBFFD_OK;
+}
+
+// run the step loop of `mode` until the control block says done.
+// Reads back done / k / res_last.
+static int run_steps(rbffd_plan* p, int mode, double dt, double tol, long long max_steps,
+                     cudaStream_t s, long long* steps, double* res, int* done) {
+    int st = ctrl_reset(p, dt, tol, max_steps, s);
+    if (st) return st;
+    StepCtrl h;
+    if (max_steps > 0) {
+        bool persistent = (p->flags & RBFFD_LAUNCH_PERSISTENT) != 0;
+        if (persistent) {
+            StepFn fn = mode == MODE_SWEEP64 ? pick_step<MODE_SWEEP64>(p->n, true)
+                                             : pick_step<MODE_INNER32>(p->n, true);
+            int grid = std::min<int64_t>(persistent_grid(fn), std::max<int64_t>(1, p->nslices));
+            StepArgs A = make_args(p);
+            StepCtrl* c = p->ctrl;
+            void* args[] = {(void*)&A, (void*)&c};
+            RBFFD_CHECK_CUDA(cudaLaunchCooperativeKernel((const void*)fn, dim3(grid),
+                                                         dim3(STEP_THREADS), args, 0, s));
+        } else {
+            st = ensure_graph(p, mode);
+            if (st) return st;
+            cudaGraphExec_t ex = (cudaGraphExec_t)(mode == MODE_SWEEP64 ? p->graph64 : p->graph32);
+            long long launched = 0;
+            // replay chunks; check the device decision every `per_check` chunks
+            long long per_check = std::max<long long>(1, std::min<long long>(
+                                       64, (max_steps + p->graph_chunk - 1) / p->graph_chunk));
+            for (;;) {
+                for (long long i = 0; i < per_check && launched < max_steps; ++i) {
+                    RBFFD_CHECK_CUDA(cudaGraphLaunch(ex, s));
+                    launched += p->graph_chunk;
+                }
+                RBFFD_CHECK_CUDA(cudaMemcpyAsync(&h, p->ctrl, sizeof(h), cudaMemcpyDeviceToHost, s));
+                RBFFD_CHECK_CUDA(cudaStreamSynchronize(s));
+                if (h.done != DONE_RUNNING || launched >= max_steps) break;
+            }
+        }
+    }
+    RBFFD_CHECK_CUDA(cudaMemcpyAsync(&h, p->ctrl, sizeof(h), cudaMemcpyDeviceToHost, s));
+    RBFFD_CHECK_CUDA(cudaStreamSynchronize(s));
+    *steps = h.k;
+    *res = h.res_last;
+    *done = h.done;
+    return RBFFD_OK;
+}
+
+static int done_status(int done) {
+    switch (done) {
+        case DONE_CONVERGED: return RBFFD_OK;
+        case DONE_CAP: return RBFFD_NOT_CONVERGED;
+        case DONE_NONFINITE: set_error("residual became non-finite"); return RBFFD_ERR_NONFINITE;
+        case DONE_DIVERGED: set_error("residual grew 1e6-fold: dt above the stability bound?");
+            return RBFFD_ERR_DIVERGED;
+        case DONE_TIMEOUT: set_error("grid barrier wait timed out"); return RBFFD_ERR_TIMEOUT;
+        default: set_error("step loop ended in an unknown state"); return RBFFD_ERR_CUDA;
+    }
+}
+
+// stable split by a 0/1 flag: ids with flag 0 first, each group ascending
+__global__ void flag_invert(const int32_t* key, int64_t N, int32_t* f) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x)
+        f[i] = key[i] ? 0 : 1;
+}
+__global__ void split_write(const int32_t* pos0, int64_t N, int32_t* out) {
+    int64_t n0 = pos0[N];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        bool zero = pos0[i + 1] != pos0[i];
+        int64_t o = zero ? pos0[i] : n0 + (i - pos0[i]);
+        out[o] = (int32_t)i;
+    }
+}
+int split_by_flag(const int32_t* key, int64_t N, int32_t* out, int32_t* pos, int64_t* tmp,
+                  cudaStream_t s) {
+    int sms = device_sm_count();
+    flag_invert<<<sms * 8, 256, 0, s>>>(key, N, pos);
+    RBFFD_CHECK_CUDA(cudaGetLastError());
+    RBFFD_CHECK_CUDA(exclusive_scan_i32(pos, pos, N, tmp, s));
+    split_write<<<sms * 8, 256, 0, s>>>(pos, N, out);
+    RBFFD_CHECK_CUDA(cudaGetLastError());
+    return RBFFD_OK;
+}
+}  // namespace rbffd
+
+using namespace rbffd;
+
+extern "C" int rbffd_apply(const double* w, const int32_t* idx, int64_t nc, int n, const double* u,
+                           double* Lu, void* stream) {
+    clear_error();
+    RBFFD_ARG(w && idx && u && Lu, "rbffd_apply: NULL argument");
+    RBFFD_ARG(nc >= 0 && n >= 1, "rbffd_apply: bad sizes");
+    if (nc == 0) return RBFFD_OK;
+    int sms = device_sm_count();
+    int64_t blocks = std::min<int64_t>((nc + 255) / 256, (int64_t)sms * 16);
+    apply_rowmajor<<<(unsigned)blocks, 256, 0, as_stream(stream)>>>(w, idx, nc, n, u, Lu);
+    RBFFD_CHECK_CUDA(cudaGetLastError());
+    return RBFFD_OK;
+}
+
+extern "C" int rbffd_plan_create(const double* xyz, const uint8_t* is_bnd, int64_t N, int d,
+                                 const int32_t* interior, const int32_t* idx, const double* w,
+                                 int64_t NI, int n, int flags, uint64_t seed, rbffd_plan** out,
+                                 void* stream) {
+    clear_error();
+    RBFFD_ARG(xyz && is_bnd && interior && idx && w && out, "rbffd_plan_create: NULL argument");
+    RBFFD_ARG(d >= 1 && d <= 3, "rbffd_plan_create: d must be 1, 2 or 3");
+    RBFFD_ARG(N >= 1 && N < (int64_t(1) << 31) && NI >= 1 && NI <= N,
+              "rbffd_plan_create: bad N / NI");
+    RBFFD_ARG(n >= 1 && n <= 128, "rbffd_plan_create: n must be in [1, 128]");
+    int order = flags & 15;
+    RBFFD_ARG(order <= RBFFD_ORDER_RANDOM, "rbffd_plan_create: unknown order flag");
+    *out = nullptr;
+    cudaStream_t s = as_stream(stream);
+    rbffd_plan* p = new rbffd_plan();
+    p->d = d;
+    p->N = N;
+    p->NI = NI;
+    p->n = n;
+    p->flags = flags;
+    p->nslices = (NI + SLICE - 1) / SLICE;
+    p->graph_chunk = 32;
+    const size_t ell = (size_t)p->nslices * n * SLICE;
+    cudaError_t e = cudaSuccess;
+#define RBFFD_ALLOC(ptr, bytes) \
+    if (e == cudaSuccess) e = cudaMalloc((void**)&(ptr), (bytes));
+    RBFFD_ALLOC(p->perm, sizeof(int32_t) * N);
+    RBFFD_ALLOC(p->inv, sizeof(int32_t) * N);
+    RBFFD_ALLOC(p->row_of_slot, sizeof(int32_t) * NI);
+    RBFFD_ALLOC(p->w64, sizeof(double) * ell);
+    RBFFD_ALLOC(p->w32, sizeof(float) * ell);
+    RBFFD_ALLOC(p->col, sizeof(int32_t) * ell);
+    RBFFD_ALLOC(p->u[0], sizeof(double) * N);
+    RBFFD_ALLOC(p->u[1], sizeof(double) * N);
+    RBFFD_ALLOC(p->fs, sizeof(double) * NI);
+    RBFFD_ALLOC(p->e[0], sizeof(float) * N);
+    RBFFD_ALLOC(p->e[1], sizeof(float) * N);
+    RBFFD_ALLOC(p->d32, sizeof(float) * NI);
+    RBFFD_ALLOC(p->scratch, sizeof(double) * (2 * NI + 4096));
+    RBFFD_ALLOC(p->ctrl, sizeof(StepCtrl));
+#undef RBFFD_ALLOC
+    if (e != cudaSuccess) {
+        set_error("rbffd_plan_create: cudaMalloc: %s", cudaGetErrorString(e));
+        free_plan(p);
+        return RBFFD_ERR_CUDA;
+    }
+    int st = RBFFD_OK;
+    int sms = device_sm_count();
+    const unsigned G = (unsigned)sms * 8;
+    do {
+        Scratch key, start, err;
+        if ((e = key.alloc(sizeof(int32_t) * N, s)) != cudaSuccess) break;
+        if ((e = err.alloc(4 * sizeof(unsigned long long), s)) != cudaSuccess) break;
+        if ((e = cudaMemsetAsync(err.p, 0, 4 * sizeof(unsigned long long), s)) != cudaSuccess)
+            break;
+        count_interior<<<G, 256, 0, s>>>(is_bnd, N, err.as<unsigned long long>() + 1);
+        if (order == RBFFD_ORDER_MORTON) {
+            double lo[3], hi[3];
+            st = bounding_box(xyz, N, d, lo, hi, s);
+            if (st) break;
+            GridGeom g = make_grid(d, lo, hi, N, 1.0);
+            int bits = d == 1 ? 26 : (d == 2 ? 12 : 8);
+            for (int a = 0; a < d; ++a) {
+                while (g.G[a] > (1 << bits)) {   // coarsen until the Morton key fits
+                    g.cs *= 1.25;
+                    for (int b = 0; b < d; ++b) g.G[b] = (int)floor((hi[b] - lo[b]) / g.cs) + 1;
+                }
+            }
+            int maxG = 1;
+            for (int a = 0; a < d; ++a) maxG = std::max(maxG, g.G[a]);
+            int64_t P2 = 1;
+            while (P2 < maxG) P2 <<= 1;
+            int64_t cells = 1;
+            for (int a = 0; a < d; ++a) cells *= P2;
+            if ((e = start.alloc(sizeof(int32_t) * (2 * cells + 1), s)) != cudaSuccess) break;
+            morton_keys<<<G, 256, 0, s>>>(xyz, is_bnd, N, g, cells, key.as<int32_t>());
+            st = counting_sort_by_key(key.as<int32_t>(), N, 2 * cells, start.as<int32_t>(),
+                                      p->perm, s);
+            if (st) break;
+        } else {
+            if ((e = start.alloc(sizeof(int32_t) * 3, s)) != cudaSuccess) break;
+            bnd_keys<<<G, 256, 0, s>>>(is_bnd, N, key.as<int32_t>());
+            // two keys: a stable split by an ordered compaction (scan per key)
+            Scratch flag, tmp;
+            if ((e = flag.alloc(sizeof(int32_t) * (N + 1), s)) != cudaSuccess) break;
+            if ((e = tmp.alloc(sizeof(int64_t) * scan_tmp_elems(N), s)) != cudaSuccess) break;
+            st = split_by_flag(key.as<int32_t>(), N, p->perm, flag.as<int32_t>(),
+                               tmp.as<int64_t>(), s);
+            if (st) break;
+            if (order == RBFFD_ORDER_RANDOM) {
+                int hb = 1;
+                while ((int64_t(1) << (2 * hb)) < NI) ++hb;
+                if ((e = cudaMemcpyAsync(key.p, p->perm, sizeof(int32_t) * NI,
+                                         cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+                    break;
+                random_interior_perm<<<G, 256, 0, s>>>(key.as<int32_t>(), NI, hb, seed, p->perm);
+            }
+        }
+        invert_perm<<<G, 256, 0, s>>>(p->perm, N, p->inv);
+        if ((e = cudaMemsetAsync(p->row_of_slot, 0xff, sizeof(int32_t) * NI, s)) != cudaSuccess)
+            break;
+        check_interior<<<G, 256, 0, s>>>(is_bnd, interior, p->inv, N, NI, p->row_of_slot,
+                                         err.as<int>());
+        pack_stencils<<<G, 256, 0, s>>>(p->row_of_slot, p->inv, idx, w, NI, p->nslices, n, N,
+                                        p->w64, p->w32, p->col, err.as<int>());
+        if ((e = cudaGetLastError()) != cudaSuccess) break;
+        unsigned long long hv[2] = {0, 0};
+        if ((e = cudaMemcpyAsync(hv, err.p, sizeof(hv), cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess)
+            break;
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
+        int herr = (int)(hv[0] & 0xffffffffull);
+        if (!herr && (int64_t)hv[1] != NI) herr = 1;
+        if (herr) {
+            set_error(herr == 3 ? "rbffd_plan_create: support index out of range"
+                                : "rbffd_plan_create: `interior` must list each non-boundary node "
+                                  "exactly once (NI = number of interior nodes)");
+            st = RBFFD_ERR_ARG;
+        }
+    } while (0);
+    if (e != cudaSuccess && st == RBFFD_OK) {
+        set_error("rbffd_plan_create: %s", cudaGetErrorString(e));
+        st = RBFFD_ERR_CUDA;
+    }
+    if (st) {
+        free_plan(p);
+        return st;
+    }
+    *out = p;
+    return RBFFD_OK;
+}
+
+
+extern "C" int rbffd_plan_destroy(rbffd_plan* plan) {
+    clear_error();
+    if (!plan) return RBFFD_OK;
+    cudaDeviceSynchronize();
+    free_plan(plan);
+    return RBFFD_OK;
+}
+
+extern "C" int rbffd_plan_perm(const rbffd_plan* p, int32_t* perm, void* stream) {
+    clear_error();
+    RBFFD_ARG(p && perm, "rbffd_plan_perm: NULL argument");
+    RBFFD_CHECK_CUDA(cudaMemcpyAsync(perm, p->perm, sizeof(int32_t) * p->N,
+                                     cudaMemcpyDeviceToDevice, as_stream(stream)));
+    return RBFFD_OK;
+}
+
+extern "C" int rbffd_plan_set_dc(rbffd_plan* p, int64_t K_in, double rho_in) {
+    clear_error();
+    RBFFD_ARG(p && K_in >= 1 && rho_in >= 0.0, "rbffd_plan_set_dc: bad argument");
+    p->dc_K_in = K_in;
+    p->dc_rho_in = rho_in;
+    return RBFFD_OK;
+}
+
+static int load_problem(rbffd_plan* p, const double* f, const double* u, cudaStream_t s) {
+    int sms = device_sm_count();
+    gather_f<<<sms * 8, 256, 0, s>>>(f, p->row_of_slot, p->NI, p->fs);
+    gather_u<<<sms * 8, 256, 0, s>>>(u, p->perm, p->N, p->u[0], p->u[1]);
+    RBFFD_CHECK_CUDA(cudaGetLastError());
+    return RBFFD_OK;
+}
+
+extern "C" int rbffd_solve_dc(rbffd_plan* p, const double* f, double* u, double dt, double tol,
+                              int64_t max_outer, int64_t K_in, double rho_in, int64_t* h_outer_out,
+                              int64_t* h_inner_out, double* h_res_out, void* stream) {
+    clear_error();
+    RBFFD_ARG(p && f && u, "rbffd_solve_dc: NULL argument");
+    RBFFD_ARG(dt > 0.0 && isfinite(dt) && tol >= 0.0, "rbffd_solve_dc: bad dt / tol");
+    RBFFD_ARG(max_outer >= 0 && K_in >= 1 && rho_in >= 0.0, "rbffd_solve_dc: bad loop limits");
+    cudaStream_t s = as_stream(stream);
+    int st = load_problem(p, f, u, s);
+    if (st) return st;
+    StepArgs A = make_args(p);
+    const int sms = device_sm_count();
+    const int grid = step_grid(p);
+    unsigned long long* dmax = reinterpret_cast<unsigned long long*>(p->scratch);
+    typedef void (*DefFn)(StepArgs, const double*, unsigned long long*);
+    DefFn def;
+    switch (p->n) {
+        case 12: def = defect_kernel<12>; break;
+        case 30: def = defect_kernel<30>; break;
+        case 56: def = defect_kernel<56>; break;
+        case 70: def = defect_kernel<70>; break;
+        default: def = defect_kernel<0>; break;
+    }
+    int64_t outer = 0, inner_total = 0;
+    double D = 0.0;
+    int status = RBFFD_NOT_CONVERGED;
+    // the FP64 iterate lives in u[0]; the inner loop ping-pongs e[0]/e[1]
+    for (outer = 0; outer <= max_outer; ++outer) {
+        RBFFD_CHECK_CUDA(cudaMemsetAsync(dmax, 0, sizeof(unsigned long long), s));
+        def<<<grid, STEP_THREADS, 0, s>>>(A, p->u[0], dmax);
+        RBFFD_CHECK_CUDA(cudaGetLastError());
+        unsigned long long hb = 0;
+        RBFFD_CHECK_CUDA(cudaMemcpyAsync(&hb, dmax, sizeof(hb), cudaMemcpyDeviceToHost, s));
+        RBFFD_CHECK_CUDA(cudaStreamSynchronize(s));
+        memcpy(&D, &hb, sizeof(D));
+        if (!isfinite(D)) {
+            status = RBFFD_ERR_NONFINITE;
+            set_error("defect became non-finite");
+            break;
+        }
+        if (D < tol) {
+            status = RBFFD_OK;
+            break;
+        }
+        if (outer == max_outer) break;
+        RBFFD_CHECK_CUDA(cudaMemsetAsync(p->e[0], 0, sizeof(float) * p->N, s));
+        RBFFD_CHECK_CUDA(cudaMemsetAsync(p->e[1], 0, sizeof(float) * p->N, s));
+        long long steps = 0;
+        double R = 0.0;
+        int done = 0;
+        st = run_steps(p, MODE_INNER32, dt, rho_in * D, K_in, s, &steps, &R, &done);
+        if (st) return st;
+        inner_total += steps;
+        if (done == DONE_NONFINITE) {
+            status = RBFFD_ERR_NONFINITE;
+            set_error("inner residual became non-finite");
+            D = INFINITY;
+            break;
+        }
+        if (done == DONE_TIMEOUT) return done_status(done);
+        const float* ef = p->e[steps & 1];
+        dc_update<<<sms * 8, 256, 0, s>>>(p->u[0], ef, p->NI);
+        RBFFD_CHECK_CUDA(cudaGetLastError());
+    }
+    scatter_u<<<sms * 8, 256, 0, s>>>(p->u[0], p->perm, p->NI, u);
+    RBFFD_CHECK_CUDA(cudaGetLastError());
+    RBFFD_CHECK_CUDA(cudaStreamSynchronize(s));
+    if (h_outer_out) *h_outer_out = outer;
+    if (h_inner_out) *h_inner_out = inner_total;
+    if (h_res_out) *h_res_out = D;
+    return status;
+}
+
+extern "C" int rbffd_solve_explicit(rbffd_plan* p, const double* f, double* u, double dt,
+                                    int64_t max_steps, double tol, int precision,
+                                    int64_t* h_steps_out, double* h_res_out, void* stream) {
+    clear_error();
+    RBFFD_ARG(p && f && u, "rbffd_solve_explicit: NULL argument");
+    RBFFD_ARG(dt > 0.0 && isfinite(dt), "rbffd_solve_explicit: dt must be positive and finite");
+    RBFFD_ARG(max_steps >= 0 && tol >= 0.0, "rbffd_solve_explicit: bad max_steps / tol");
+    RBFFD_ARG(precision == 0 || precision == 1, "rbffd_solve_explicit: precision must be 0 or 1");
+    if (precision == 1) {
+        int64_t outer_cap = std::max<int64_t>(1, max_steps / p->dc_K_in);
+        int64_t outer = 0, inner = 0;
+        int st = rbffd_solve_dc(p, f, u, dt, tol, outer_cap, p->dc_K_in, p->dc_rho_in, &outer,
+                                &inner, h_res_out, stream);
+        if (h_steps_out) *h_steps_out = inner;
+        return st;
+    }
+    cudaStream_t s = as_stream(stream);
+    int st = load_problem(p, f, u, s);
+    if (st) return st;
+    long long steps = 0;
+    double R = 0.0;
+    int done = 0;
+    st = run_steps(p, MODE_SWEEP64, dt, tol, max_steps, s, &steps, &R, &done);
+    if (st) return st;
+    int sms = device_sm_count();
+    scatter_u<<<sms * 8, 256, 0, s>>>(p->u[steps & 1], p->perm, p->NI, u);
+    RBFFD_CHECK_CUDA(cudaGetLastError());
+    RBFFD_CHECK_CUDA(cudaStreamSynchronize(s));
+    if (h_steps_out) *h_steps_out = steps;
+    if (h_res_out) *h_res_out = R;
+    if (max_steps == 0) return RBFFD_NOT_CONVERGED;
+    return done_status(done);
+}
+
+extern "C" int rbffd_stable_dt(rbffd_plan* p, const double* v0, int iters, double safety,
+                               double* h_dt_out, double* h_rho_out, void* stream) {
+    clear_error();
+    RBFFD_ARG(p && v0 && iters >= 1 && safety > 0.0, "rbffd_stable_dt: bad argument");
+    cudaStream_t s = as_stream(stream);
+    const int sms = device_sm_count();
+    // v lives in u[0] (slot order; boundary slots 0), y in scratch[1024 ..]
+    double* v = p->u[0];
+    double* y = p->scratch + 4096;
+    double* part = p->scratch + 8;
+    double* nrm = p->scratch;
+    const int nparts = 1024;
+    RBFFD_CHECK_CUDA(cudaMemsetAsync(v, 0, sizeof(double) * p->N, s));
+    gather_f<<<sms * 8, 256, 0, s>>>(v0, p->row_of_slot, p->NI, y);
+    norm_partials<<<nparts, 256, 0, s>>>(y, p->NI, part);
+    sum_to_norm<<<1, 256, 0, s>>>(part, nparts, nrm);
+    power_scale<<<sms * 8, 256, 0, s>>>(nrm, y, v, p->NI);
+    RBFFD_CHECK_CUDA(cudaGetLastError());
+    StepArgs A = make_args(p);
+    typedef void (*PowFn)(StepArgs, const double*, double*, double*);
+    PowFn pf;
+    switch (p->n) {
+        case 12: pf = power_apply<12>; break;
+        case 30: pf = power_apply<30>; break;
+        case 56: pf = power_apply<56>; break;
+        case 70: pf = power_apply<70>; break;
+        default: pf = power_apply<0>; break;
+    }
+    const int grid = std::min(step_grid(p), nparts);
+    for (int it = 0; it < iters; ++it) {
+        pf<<<grid, STEP_THREADS, 0, s>>>(A, v, y, part);
+        sum_to_norm<<<1, 256, 0, s>>>(part, grid, nrm);
+        power_scale<<<sms * 8, 256, 0, s>>>(nrm, y, v, p->NI);
+    }
+    RBFFD_CHECK_CUDA(cudaGetLastError());
+    double rho = 0.0;
+    RBFFD_CHECK_CUDA(cudaMemcpyAsync(&rho, nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
+    RBFFD_CHECK_CUDA(cudaStreamSynchronize(s));
+    if (!(rho > 0.0) || !isfinite(rho)) {
+        set_error("rbffd_stable_dt: spectral radius estimate is %g", rho);
+        return RBFFD_ERR_NONFINITE;
+    }
+    if (h_rho_out) *h_rho_out = rho;
+    if (h_dt_out) *h_dt_out = 2.0 / (safety * rho);
+    return RBFFD_OK;
+}

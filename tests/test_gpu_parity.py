@@ -1,0 +1,349 @@
+"""GPU path vs the CPU oracle, element by element, through the C ABI.
+
+Tolerances (fixed here, stated per check):
+* node coordinates, interior lists, support indices: bit-exact;
+* weights: per stencil max_j |dw_j| <= 1e-12 max_j |w_j|;
+* stencil application: |d(Lu)_i| <= 1e-12 max(|Lu_i|, sum_j |w_ij u_j|);
+* K-step FP64 sweep (K <= 1000): max |du| <= 1e-12 max |u|, same step count;
+* FP32 defect correction: same outer/inner counts, max |du| <= 1e-12 max|u|;
+* stability estimate: relative 1e-9 on rho;
+* adjoint: max |dg| <= 1e-12 max |g| per gradient.
+The kernels follow the oracle's operation order, so most of these are met
+with equality; the tolerances leave room only for reduction order.
+"""
+import numpy as np
+import pytest
+
+import rbffd_inputs as gen
+from oracle_problem import build
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_12878_gb300 import build as nvbuild
+    nvbuild.build()
+    import paper_2502_12878_gb300 as m
+    m.lib()
+    return m
+
+
+DEV = "cuda"
+
+
+def T(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.to(DEV)
+
+
+def H(t):
+    return t.cpu().numpy()
+
+
+# ------------------------------------------------------------------ nodes
+@pytest.mark.parametrize("d,shape,Kg,seed", [(2, 0, 37, 1), (3, 0, 11, 2), (2, 1, 45, 3),
+                                             (1, 0, 50, 4), (2, 0, 2, 5)])
+def test_nodes_bit_exact(rb, orc, d, shape, Kg, seed):
+    xyz, bnd = rb.rbffd_nodes(d, shape, Kg, 0.3, seed)
+    oxyz, obnd = orc.nodes(d, shape, Kg, 0.3, seed)
+    assert np.array_equal(H(xyz), oxyz)
+    assert np.array_equal(H(bnd), obnd)
+    inter = rb.rbffd_interior(bnd)
+    assert np.array_equal(H(inter), gen.interior_ids(obnd))
+
+
+def test_nodes_capacity_error(rb):
+    import ctypes
+    L = rb.lib()
+    n = ctypes.c_int64(0)
+    buf = torch.empty(10, dtype=torch.float64, device=DEV)
+    b = torch.empty(10, dtype=torch.uint8, device=DEV)
+    code = L.rbffd_nodes(2, 0, 20, 0.3, 1, rb._ptr(buf), rb._ptr(b), 5, ctypes.byref(n), None)
+    assert code == rb.RBFFD_ERR_CAPACITY and n.value == 21 * 21
+
+
+# ------------------------------------------------------------------ kNN
+def _knn_case(orc, case):
+    if case == "jit2_n12":
+        xyz, bnd = orc.nodes(2, 0, 60, 0.3, 11)
+        return xyz, gen.interior_ids(bnd), 12
+    if case == "jit2_n30":
+        xyz, bnd = orc.nodes(2, 0, 45, 0.3, 12)
+        return xyz, gen.interior_ids(bnd), 30
+    if case == "jit2_n56_all":
+        xyz, bnd = orc.nodes(2, 0, 30, 0.3, 13)
+        return xyz, np.arange(xyz.shape[1], dtype=np.int32), 56
+    if case == "jit3_n70":
+        xyz, bnd = orc.nodes(3, 0, 12, 0.3, 14)
+        return xyz, gen.interior_ids(bnd), 70
+    if case == "grid2_ties":
+        xyz = gen.grid_points(23, 2)
+        return xyz, np.arange(xyz.shape[1], dtype=np.int32), 30
+    if case == "grid3_ties":
+        xyz = gen.grid_points(9, 3)
+        return xyz, np.arange(xyz.shape[1], dtype=np.int32), 35
+    if case == "random2_clustered":
+        rng = np.random.default_rng(5)
+        a = rng.uniform(0, 1, (2, 2000))
+        b = rng.normal(0.3, 0.002, (2, 600))      # dense cluster: many nodes per cell
+        xyz = np.concatenate([a, b], axis=1)
+        return xyz, rng.choice(xyz.shape[1], 500, replace=False).astype(np.int32), 40
+    if case == "disk_n56":
+        xyz, bnd = orc.nodes(2, 1, 50, 0.3, 15)
+        return xyz, gen.interior_ids(bnd), 56
+    if case == "tiny_n_eq_N":
+        xyz = gen.random_points(9, 2, 3)
+        return xyz, np.arange(9, dtype=np.int32), 9
+    if case == "max_n128":
+        xyz = gen.random_points(3000, 2, 4)
+        return xyz, np.arange(0, 3000, 7, dtype=np.int32), 128
+    if case == "line1d":
+        xyz, bnd = orc.nodes(1, 0, 400, 0.3, 16)
+        return xyz, gen.interior_ids(bnd), 7
+    raise KeyError(case)
+
+
+KNN_CASES = ["jit2_n12", "jit2_n30", "jit2_n56_all", "jit3_n70", "grid2_ties", "grid3_ties",
+             "random2_clustered", "disk_n56", "tiny_n_eq_N", "max_n128", "line1d"]
+
+
+@pytest.mark.parametrize("case", KNN_CASES)
+def test_knn_bit_exact(rb, orc, case):
+    xyz, centres, n = _knn_case(orc, case)
+    ref = orc.knn_kdtree(xyz, centres, n)
+    got = H(rb.rbffd_knn(T(xyz), T(centres), n))
+    assert np.array_equal(got, ref)
+
+
+def test_knn_empty_centres(rb):
+    xyz = T(gen.random_points(50, 2, 1))
+    idx = rb.rbffd_knn(xyz, torch.empty(0, dtype=torch.int32, device=DEV), 5)
+    assert idx.shape == (0, 5)
+
+
+# ------------------------------------------------------------------ weights
+@pytest.mark.parametrize("d,m,Kg,nplus", [(2, 2, 40, 0), (2, 4, 35, 0), (2, 6, 30, 0),
+                                          (3, 4, 10, 0), (2, 2, 30, 1), (3, 2, 10, 3),
+                                          (2, 4, 30, 9), (1, 4, 200, 0)])
+def test_weights_parity(rb, orc, d, m, Kg, nplus):
+    xyz, bnd = orc.nodes(d, 0, Kg, 0.3, 21 + m)
+    inter = gen.interior_ids(bnd)
+    n = gen.stencil_size(d, m) + nplus
+    idx = orc.knn_kdtree(xyz, inter, n)
+    ow, ost = orc.weights(xyz, idx, m)
+    w, st = rb.rbffd_weights(T(xyz), T(idx), m)
+    w, st = H(w), H(st)
+    assert np.array_equal(st, ost)
+    scale = np.abs(ow).max(axis=1, keepdims=True)
+    assert np.all(np.abs(w - ow) <= 1e-12 * scale)
+    # the operation order is the oracle's, so nearly every row is bit-identical
+    assert np.mean(np.all(w == ow, axis=1)) > 0.99
+
+
+def test_weights_max_system(rb, orc):
+    # s = n + M = 128 (largest supported): d=2, m=7 (M=36), n=92
+    xyz, bnd = orc.nodes(2, 0, 30, 0.3, 8)
+    inter = gen.interior_ids(bnd)[::37]
+    idx = orc.knn_kdtree(xyz, inter, 92)
+    ow, ost = orc.weights(xyz, idx, 7)
+    w, st = rb.rbffd_weights(T(xyz), T(idx), 7)
+    assert np.array_equal(H(st), ost)
+    ok = ost == 0
+    scale = np.abs(ow[ok]).max(axis=1, keepdims=True)
+    assert np.all(np.abs(H(w)[ok] - ow[ok]) <= 1e-12 * scale)
+
+
+def test_weights_singular_status(rb, orc):
+    pts = np.array([[0.0, 0.1, 0.1, 0.0, 0.2, -0.1, 0.05, 0.3],
+                    [0.0, 0.0, 0.0, 0.1, 0.1, 0.2, -0.1, 0.3]])
+    idx = np.array([[0, 1, 2, 3, 4, 5, 6], [7, 0, 3, 4, 5, 6, 1]], np.int32)
+    ow, ost = orc.weights(pts, idx, 2)
+    w, st = rb.rbffd_weights(T(pts), T(idx), 2, check=False)
+    assert list(H(st)) == list(ost) == [1, 0]
+    assert np.all(H(w)[0] == 0)
+    with pytest.raises(rb.RbffdError) as ei:
+        rb.rbffd_weights(T(pts), T(idx), 2)
+    assert ei.value.code == rb.RBFFD_ERR_SINGULAR
+
+
+# ------------------------------------------------------------------ apply
+def test_apply_parity(rb, orc):
+    p = build(orc, 2, 50, 4, seed=31)
+    u = gen.random_vector(p.N, 3)
+    ref = orc.apply(p.w, p.idx, u)
+    got = H(rb.rbffd_apply(T(p.w), T(p.idx), T(u)))
+    bound = 1e-12 * np.maximum(np.abs(ref), np.abs(p.w * u[p.idx]).sum(axis=1))
+    assert np.all(np.abs(got - ref) <= bound)
+
+
+# ------------------------------------------------------------------ sweep
+def _plan(rb, p, flags=0, seed=0):
+    return rb.Plan(T(p.xyz), T(p.is_bnd), T(p.interior), T(p.idx), T(p.w), flags, seed)
+
+
+def _dt(orc, p):
+    return 0.9 * orc.stable_dt(p.w, p.idx, p.interior, p.N, gen.random_vector(p.NI, 77), 200)
+
+
+SWEEP_CASES = [
+    (2, 40, 2, 0, "morton_graph"),
+    (2, 33, 4, 16, "morton_persistent"),
+    (2, 30, 6, 1, "input_graph"),
+    (2, 29, 4, 2 | 16, "random_persistent"),
+    (3, 9, 4, 0, "cube_m4"),
+]
+
+
+@pytest.mark.parametrize("d,Kg,m,flags,name", SWEEP_CASES)
+def test_sweep_parity_fixed_steps(rb, orc, d, Kg, m, flags, name):
+    p = build(orc, d, Kg, m, seed=41)
+    dt = _dt(orc, p)
+    K = 300
+    ou, os_, ores, ost = orc.solve_explicit(p.w, p.idx, p.interior, p.f, p.u0, dt, K, 0.0)
+    plan = _plan(rb, p, flags, seed=9)
+    u = T(p.u0)
+    code, steps, res = plan.solve_explicit(T(p.f), u, dt, K, 0.0)
+    assert code == rb.RBFFD_NOT_CONVERGED and steps == os_ == K
+    assert np.max(np.abs(H(u) - ou)) <= 1e-12 * np.max(np.abs(ou))
+    assert res == pytest.approx(ores, rel=1e-12)
+    plan.destroy()
+
+
+def test_sweep_stop_rule_matches(rb, orc):
+    p = build(orc, 2, 24, 2, seed=42)
+    dt = _dt(orc, p)
+    # a tolerance the oracle reaches after a few hundred steps
+    ou, os_, ores, ost = orc.solve_explicit(p.w, p.idx, p.interior, p.f, p.u0, dt, 5000, 1.0)
+    assert ost == 0 and 1 < os_ < 5000
+    for flags in (0, 16):
+        plan = _plan(rb, p, flags)
+        u = T(p.u0)
+        code, steps, res = plan.solve_explicit(T(p.f), u, dt, 5000, 1.0)
+        assert code == rb.RBFFD_OK and steps == os_ and res == ores
+        assert np.max(np.abs(H(u) - ou)) <= 1e-12 * np.max(np.abs(ou))
+        plan.destroy()
+
+
+def test_sweep_ragged_small_and_generic_n(rb, orc):
+    # NI = 9 (one partial slice), n = 7 (generic-n kernel path)
+    p = build(orc, 2, 4, 1, seed=43, n=7)
+    dt = _dt(orc, p)
+    for flags in (0, 16):
+        ou, os_, _, _ = orc.solve_explicit(p.w, p.idx, p.interior, p.f, p.u0, dt, 50, 0.0)
+        plan = _plan(rb, p, flags)
+        u = T(p.u0)
+        plan.solve_explicit(T(p.f), u, dt, 50, 0.0)
+        assert np.max(np.abs(H(u) - ou)) <= 1e-12 * max(np.max(np.abs(ou)), 1e-300)
+        plan.destroy()
+
+
+def test_sweep_zero_steps_and_errors(rb, orc):
+    p = build(orc, 2, 12, 2, seed=44)
+    plan = _plan(rb, p)
+    u = T(p.u0)
+    code, steps, _ = plan.solve_explicit(T(p.f), u, 1e-5, 0, 0.0)
+    assert steps == 0 and np.array_equal(H(u), p.u0)
+    # non-finite source -> RBFFD_ERR_NONFINITE after one step (host-made failure)
+    f = p.f.copy()
+    f[5] = np.inf
+    with pytest.raises(rb.RbffdError) as ei:
+        plan.solve_explicit(T(f), T(p.u0), 1e-5, 100, 0.0)
+    assert ei.value.code == rb.RBFFD_ERR_NONFINITE
+    # dt far above the stability bound -> RBFFD_ERR_DIVERGED, both launch modes
+    for flags in (0, 16):
+        pl = _plan(rb, p, flags)
+        with pytest.raises(rb.RbffdError) as ei:
+            pl.solve_explicit(T(p.f), T(p.u0), 50 * _dt(orc, p), 5000, 0.0)
+        assert ei.value.code == rb.RBFFD_ERR_DIVERGED
+        pl.destroy()
+    with pytest.raises(rb.RbffdError):
+        plan.solve_explicit(T(p.f), T(p.u0), -1.0, 10, 0.0)
+    plan.destroy()
+
+
+def test_plan_rejects_bad_interior(rb, orc):
+    p = build(orc, 2, 10, 2, seed=45)
+    bad = p.interior.copy()
+    bad[3] = np.nonzero(p.is_bnd)[0][0]       # a boundary node in the interior list
+    with pytest.raises(rb.RbffdError):
+        rb.Plan(T(p.xyz), T(p.is_bnd), T(bad), T(p.idx), T(p.w))
+
+
+def test_orderings_are_permutations(rb, orc):
+    p = build(orc, 2, 20, 2, seed=46)
+    for flags in (0, 1, 2):
+        plan = _plan(rb, p, flags, seed=3)
+        perm = H(plan.perm())
+        assert np.array_equal(np.sort(perm), np.arange(p.N))
+        assert np.all(p.is_bnd[perm[: p.NI]] == 0)
+        plan.destroy()
+
+
+# ------------------------------------------------------------------ stable dt
+def test_stable_dt_parity(rb, orc):
+    p = build(orc, 2, 30, 4, seed=51)
+    v0 = gen.random_vector(p.NI, 5)
+    rho = orc.power_rho(p.w, p.idx, p.interior, p.N, v0, 200)
+    plan = _plan(rb, p)
+    dt, rho_g = plan.stable_dt(T(v0), 200, 1.05)
+    assert rho_g == pytest.approx(rho, rel=1e-9)
+    assert dt == pytest.approx(2.0 / (1.05 * rho), rel=1e-9)
+    plan.destroy()
+
+
+# ------------------------------------------------------------------ defect correction
+def test_dc_parity(rb, orc):
+    p = build(orc, 2, 20, 4, seed=61)
+    dt = _dt(orc, p)
+    args = (dt, 1e-8, 30, 3000, 1e-3)
+    ou, oo, oi, ores, ost = orc.solve_dc(p.w, p.idx, p.interior, p.f, p.u0, *args)
+    plan = _plan(rb, p)
+    u = T(p.u0)
+    code, outer, inner, res = plan.solve_dc(T(p.f), u, *args)
+    assert (outer, inner) == (oo, oi)
+    assert code == (rb.RBFFD_OK if ost == 0 else rb.RBFFD_NOT_CONVERGED)
+    assert np.max(np.abs(H(u) - ou)) <= 1e-12 * np.max(np.abs(ou))
+    plan.destroy()
+
+
+# ------------------------------------------------------------------ adjoint
+def test_adjoint_parity(rb, orc):
+    p = build(orc, 2, 25, 4, seed=71)
+    dt = _dt(orc, p)
+    K = 200
+    lamK = np.zeros(p.NI)
+    sens = gen.sensors(p.NI, 40, 2)
+    lamK[sens] = gen.random_vector(40, 3)
+    gf, gg, l0 = orc.adjoint(p.w, p.idx, p.interior, p.N, lamK, K, dt)
+    plan = _plan(rb, p)
+    g_f, g_g, g_l0 = plan.adjoint(T(lamK), K, dt)
+    for a, b in ((H(g_f), gf), (H(g_g), gg), (H(g_l0), l0)):
+        assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(b))
+    plan.destroy()
+
+
+# ------------------------------------------------------------------ whole pipeline on GPU
+def test_pipeline_gpu_vs_oracle(rb, orc):
+    d, Kg, m, seed = 2, 64, 4, 81
+    n = gen.stencil_size(d, m)
+    xyz, bnd = rb.rbffd_nodes(d, 0, Kg, 0.3, seed)
+    inter = rb.rbffd_interior(bnd)
+    idx = rb.rbffd_knn(xyz, inter, n)
+    w, st = rb.rbffd_weights(xyz, idx, m)
+    p = build(orc, d, Kg, m, seed=seed)
+    assert np.array_equal(H(idx), p.idx)
+    scale = np.abs(p.w).max(axis=1, keepdims=True)
+    assert np.all(np.abs(H(w) - p.w) <= 1e-12 * scale)
+    dt = _dt(orc, p)
+    plan = rb.Plan(xyz, bnd, inter, idx, w)
+    u = T(p.u0)
+    plan.solve_explicit(T(p.f), u, dt, 400, 0.0)
+    ou, *_ = orc.solve_explicit(p.w, p.idx, p.interior, p.f, p.u0, dt, 400, 0.0)
+    assert np.max(np.abs(H(u) - ou)) <= 1e-12 * np.max(np.abs(ou))
+    plan.destroy()

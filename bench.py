@@ -1,0 +1,373 @@
+#!/usr/bin/env python3
+"""Benchmark of the RBF-FD explicit Poisson path (Eq. 6 of arXiv 2502.12878).
+
+Workload (node-updates/s at 1 GPU): the 2D unit square with 1,002,001
+jittered nodes (998,001 interior), PHS r^3 + monomials of order m = 4
+(n = 30 neighbours), Dirichlet data and source of the manufactured solution
+u = sin(pi x) sin(pi y), FP64.  The plan (nodes, supports, weights, packed
+layout) is built once, untimed.  One bench step = one call of
+rbffd_solve_explicit running S = 200 explicit sweeps on the device-resident
+problem (the stop tolerance is 0, so every step does the same work).
+value = interior nodes x sweeps x steps / time (all ranks).
+
+Also reported: the dominant kernel's roofline (the FP64 sweep, algorithmic
+bytes 12n + 24 per node-update: n FP64 weights + n int32 indices + read u_i,
+f_i and write u_i; the gathers of u are served by L1/L2), an end-to-end number
+through the same C-ABI call with host buffers (H2D of f and u, D2H of u per
+step), the FP32 + defect-correction inner sweep, the other orders (m = 2, 6),
+the setup kernels, and the CPU oracle on this host's cores as a baseline.
+
+With --impl reference the CPU oracle itself is timed on the same workload
+(each step a bounded sample of sweeps).  Multi-GPU (torchrun): every rank runs
+an independent replica of the workload (the path has no exchange step on one
+GPU per problem), value = sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import rbffd_inputs as gen  # noqa: E402
+
+METRIC = "node-updates/s & HBM GB/s vs peak; time-to-max-error 1e-6, FP64 vs FP32+DC"
+UNIT = "node-updates/s"
+D, KG, M, SEED = 2, 1000, 4, 2
+SWEEPS = 200
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv",
+                                          "-i", str(self.idx), "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9 or not parts[1].split()[0].isdigit():
+                    continue
+                rows.append(parts)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [int(r[1].split()[0]) for r in rows]
+        mx = int(rows[0][2].split()[0])
+        loaded = [v for v in sm if v > 0.5 * mx] or sm
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def build_gpu_problem(rb, torch, d, Kg, m, seed, dev):
+    n = gen.stencil_size(d, m)
+    t = {}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    xyz, bnd = rb.rbffd_nodes(d, 0, Kg, 0.3, seed, device=dev)
+    torch.cuda.synchronize()
+    t["nodes_ms"] = (time.perf_counter() - t0) * 1e3
+    t0 = time.perf_counter()
+    inter = rb.rbffd_interior(bnd)
+    idx = rb.rbffd_knn(xyz, inter, n)
+    torch.cuda.synchronize()
+    t["knn_ms"] = (time.perf_counter() - t0) * 1e3
+    t0 = time.perf_counter()
+    w, st = rb.rbffd_weights(xyz, idx, m)
+    torch.cuda.synchronize()
+    t["weights_ms"] = (time.perf_counter() - t0) * 1e3
+    t0 = time.perf_counter()
+    plan = rb.Plan(xyz, bnd, inter, idx, w, rb.RBFFD_ORDER_MORTON)
+    torch.cuda.synchronize()
+    t["plan_ms"] = (time.perf_counter() - t0) * 1e3
+    # inputs of the test problem (Eq. 4-5) from the node coordinates
+    xyz_h, bnd_h, inter_h = xyz.cpu().numpy(), bnd.cpu().numpy(), inter.cpu().numpy()
+    f = torch.from_numpy(gen.source(xyz_h, inter_h)).to(dev)
+    u0 = torch.from_numpy(gen.start_iterate(xyz_h, bnd_h)).to(dev)
+    v0 = torch.from_numpy(gen.random_vector(len(inter_h), 7)).to(dev)
+    t0 = time.perf_counter()
+    dt_stab, rho = plan.stable_dt(v0, 200, 1.05)
+    torch.cuda.synchronize()
+    t["stable_dt_ms"] = (time.perf_counter() - t0) * 1e3
+    return dict(xyz=xyz, bnd=bnd, inter=inter, idx=idx, w=w, plan=plan, f=f, u0=u0, n=n,
+                NI=len(inter_h), N=xyz.shape[1], dt=0.9 * dt_stab, rho=rho, setup=t,
+                weight_flops=len(inter_h) * (2.0 / 3.0) * (n + gen.num_monomials(d, m)) ** 3)
+
+
+def cpu_baseline(seconds_budget=12.0):
+    """The oracle as it stands: same workload, bounded number of sweeps."""
+    import oracle
+    oracle.build()
+    xyz, bnd = oracle.nodes(D, 0, KG, 0.3, SEED)
+    inter = gen.interior_ids(bnd)
+    n = gen.stencil_size(D, M)
+    t0 = time.perf_counter()
+    idx = oracle.knn_kdtree(xyz, inter, n)
+    w, st = oracle.weights(xyz, idx, M)
+    setup = time.perf_counter() - t0
+    f = gen.source(xyz, inter)
+    u = gen.start_iterate(xyz, bnd)
+    dt = 3.7e-8
+    t0 = time.perf_counter()
+    u, steps, res, stt = oracle.solve_explicit(w, idx, inter, f, u, dt, 5, 0.0)
+    per = (time.perf_counter() - t0) / 5
+    sweeps = max(5, int(seconds_budget / max(per, 1e-6)))
+    t0 = time.perf_counter()
+    u, steps, res, stt = oracle.solve_explicit(w, idx, inter, f, u, dt, sweeps, 0.0)
+    el = time.perf_counter() - t0
+    return {"value": len(inter) * sweeps / el, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{sweeps} FP64 sweeps of the full 998,001-row m=4 problem "
+                      f"({el:.1f} s; oracle kd-tree kNN + weights setup {setup:.1f} s untimed)"}
+
+
+def run_reference(args):
+    rank, world, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        if rank != 0:
+            dist.destroy_process_group()
+            return
+    import oracle
+    oracle.build()
+    xyz, bnd = oracle.nodes(D, 0, KG, 0.3, SEED)
+    inter = gen.interior_ids(bnd)
+    n = gen.stencil_size(D, M)
+    idx = oracle.knn_kdtree(xyz, inter, n)
+    w, st = oracle.weights(xyz, idx, M)
+    f = gen.source(xyz, inter)
+    u = gen.start_iterate(xyz, bnd)
+    dt = 3.7e-8
+    t0 = time.perf_counter()
+    oracle.solve_explicit(w, idx, inter, f, u, dt, 2, 0.0)
+    per = (time.perf_counter() - t0) / 2
+    # each step a bounded sample of sweeps (about 1 s)
+    S = max(2, int(1.0 / max(per, 1e-6)))
+    for _ in range(args.warmup):
+        u, *_ = oracle.solve_explicit(w, idx, inter, f, u, dt, S, 0.0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        u, *_ = oracle.solve_explicit(w, idx, inter, f, u, dt, S, 0.0)
+    el = time.perf_counter() - t0
+    v = len(inter) * S * args.steps / el
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": "2D unit square, 1,002,001 jittered nodes, m=4 (n=30), FP64 "
+                                  "explicit sweeps", "sweeps_per_step": S,
+                      "l2": "inputs larger than L2"},
+           "cpu_baseline": {"kind": "oracle", "cores": oracle.num_threads(), "value": v,
+                            "unit": UNIT,
+                            "sample": f"{S} sweeps of the full 998,001-row problem per step"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    args.warmup = max(args.warmup, 3)
+
+    import torch
+    import paper_2502_12878_gb300 as rb
+    from paper_2502_12878_gb300 import build as nvbuild
+
+    rank, world, local = _dist()
+    nvbuild.build()
+    rb.lib()
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    P = build_gpu_problem(rb, torch, D, KG, M, SEED + rank * 0, dev)
+    plan, f, u0, NI, n = P["plan"], P["f"], P["u0"], P["NI"], P["n"]
+    u = u0.clone()
+    for _ in range(args.warmup):
+        plan.solve_explicit(f, u, P["dt"], SWEEPS, 0.0)
+    # device-resident timed region
+    gpu_index = torch.cuda.current_device()
+    loop_ms, loop_steps, launches = 0.0, 0, 0
+    with Clocks(gpu_index) as clk:
+        barrier()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(args.steps):
+            code, steps, res = plan.solve_explicit(f, u, P["dt"], SWEEPS, 0.0)
+            ms, st_steps, nl, shape = plan.stats()
+            loop_ms += ms
+            loop_steps += st_steps
+            launches += nl
+        ev1.record()
+        barrier()
+    el = ev0.elapsed_time(ev1) * 1e-3
+    if dist is not None:
+        t = torch.tensor([el], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+    updates = NI * SWEEPS * args.steps * world
+    value = updates / el
+    clocks = clk.summary()
+
+    # roofline of the dominant kernel (FP64 sweep): algorithmic bytes per launch / event time
+    hbm, peak_kind = _peaks()
+    per_launch_s = loop_ms * 1e-3 / max(loop_steps, 1)
+    alg_bytes = NI * (12 * n + 24)
+    achieved = alg_bytes / per_launch_s / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(achieved / hbm, 4), "traffic": None,
+            "kernel": f"step_kernel<{n},0> (FP64 sweep)", "peak_kind": peak_kind,
+            "alg_bytes_per_launch": alg_bytes, "launch_us": round(per_launch_s * 1e6, 2),
+            "fp64_pipe_frac": round(NI * (n + 2) / per_launch_s / 6.28e11, 4)}
+
+    # end to end through the same C-ABI call with host buffers
+    f_h = f.cpu().pin_memory()
+    u_h = u0.cpu().pin_memory()
+    out_h = torch.empty_like(u_h).pin_memory()
+    f_d = torch.empty_like(f)
+    u_d = torch.empty_like(u0)
+    e2e_steps = max(3, args.steps // 2)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        f_d.copy_(f_h, non_blocking=True)
+        u_d.copy_(u_h, non_blocking=True)
+        plan.solve_explicit(f_d, u_d, P["dt"], SWEEPS, 0.0)
+        out_h.copy_(u_d, non_blocking=True)
+        torch.cuda.synchronize()
+    barrier()
+    e2e_el = time.perf_counter() - t0
+    e2e = {"value": NI * SWEEPS * e2e_steps * world / e2e_el, "unit": UNIT,
+           "h2d_bytes_per_step": int(f_h.numel() * 8 + u_h.numel() * 8),
+           "d2h_bytes_per_step": int(out_h.numel() * 8)}
+
+    extras = {}
+    if not args.no_extras:
+        # FP32 inner sweep of defect correction (8n + 12 algorithmic bytes per update)
+        u2 = u0.clone()
+        plan.solve_dc(f, u2, P["dt"], 0.0, 1, 50, 0.0)
+        plan.solve_dc(f, u2, P["dt"], 0.0, 2, SWEEPS, 0.0)
+        ms, st_steps, nl, shape = plan.stats()
+        per = ms * 1e-3 / max(st_steps, 1)
+        extras["fp32_dc_inner"] = {"node_updates_per_s": NI / per,
+                                   "alg_GBps": NI * (8 * n + 12) / per / 1e9,
+                                   "frac_hbm": NI * (8 * n + 12) / per / 1e9 / hbm}
+        extras["launch_shape"] = {"fp64": shape[:2], "fp32": shape[2:]}
+        extras["setup_ms"] = {k: round(v, 2) for k, v in P["setup"].items()}
+        extras["weights_fp64_tflops"] = P["weight_flops"] / P["setup"]["weights_ms"] / 1e9
+        extras["rho_h2"] = P["rho"] / KG ** 2
+        plan_other = {}
+        for mo in (2, 6):
+            Q = build_gpu_problem(rb, torch, D, KG, mo, SEED, dev)
+            uq = Q["u0"].clone()
+            Q["plan"].solve_explicit(Q["f"], uq, Q["dt"], 40, 0.0)
+            Q["plan"].solve_explicit(Q["f"], uq, Q["dt"], SWEEPS, 0.0)
+            ms, st_steps, nl, shape = Q["plan"].stats()
+            per = ms * 1e-3 / max(st_steps, 1)
+            plan_other[f"m{mo}_n{Q['n']}"] = {
+                "node_updates_per_s": Q["NI"] / per,
+                "alg_GBps": Q["NI"] * (12 * Q["n"] + 24) / per / 1e9,
+                "setup_ms": {k: round(v, 2) for k, v in Q["setup"].items()}}
+            Q["plan"].destroy()
+        extras["fp64_other_orders"] = plan_other
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "2D unit square, 1,002,001 jittered nodes (998,001 interior), "
+                                  "m=4 (n=30), FP64 explicit sweeps, Morton-packed plan",
+                      "sweeps_per_step": SWEEPS, "dt": P["dt"],
+                      "l2": "inputs larger than L2 (stencils 360 MB per sweep)",
+                      "parallelism": f"replicas x{world}"},
+           "roofline": roof, "e2e": e2e, "clocks": clocks,
+           "gpu_launches": int(launches), "extras": extras}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    plan.destroy()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -179,6 +179,17 @@ RBFFD_API int rbffd_solve_explicit(rbffd_plan* plan, const double* f, double* u,
                          double* h_res_out, void* stream);
 
 /*
+ * rbffd_plan_stats - what the last solve on this plan did (host outputs, may
+ * be NULL): h_loop_ms, the GPU time of its step loops measured with CUDA
+ * events recorded on the caller's stream around the step launches;
+ * h_loop_steps, the steps those loops took; h_launches, the kernels the solve
+ * launched; h_shape[4], the autotuned launch shape (register budget, blocks
+ * per SM) of the FP64 sweep and of the FP32 inner sweep.
+ */
+RBFFD_API int rbffd_plan_stats(const rbffd_plan* plan, double* h_loop_ms, int64_t* h_loop_steps,
+                               int64_t* h_launches, int* h_shape);
+
+/*
  * rbffd_solve_dc - defect correction (the precision split is not in the
  * paper).  Outer, FP64: d = W u - f, D = max|d|; stop when D < tol or after
  * max_outer corrections.  Inner, FP32, on the correction e (0 at the start

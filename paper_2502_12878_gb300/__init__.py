@@ -46,7 +46,7 @@ EXPORTED = [
     "rbffd_last_error", "rbffd_version", "rbffd_nodes", "rbffd_interior", "rbffd_knn",
     "rbffd_weights", "rbffd_apply", "rbffd_plan_create", "rbffd_plan_destroy", "rbffd_plan_perm",
     "rbffd_solve_explicit", "rbffd_solve_dc", "rbffd_plan_set_dc", "rbffd_stable_dt",
-    "rbffd_adjoint",
+    "rbffd_adjoint", "rbffd_plan_stats",
 ]
 
 
@@ -89,6 +89,7 @@ def lib():
         "rbffd_plan_set_dc": (I, [P, I64, D]),
         "rbffd_stable_dt": (I, [P, P, I, D, PD, PD, P]),
         "rbffd_adjoint": (I, [P, P, I64, D, P, P, P, P]),
+        "rbffd_plan_stats": (I, [P, PD, PI64, PI64, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -254,6 +255,16 @@ class Plan:
                                     ctypes.byref(inner), ctypes.byref(res), _stream(self.device))
         _check(code, (RBFFD_OK, RBFFD_NOT_CONVERGED))
         return code, outer.value, inner.value, res.value
+
+    def stats(self):
+        """(GPU ms of the last solve's step loops, their steps, kernels launched, launch shape)."""
+        ms = ctypes.c_double(0.0)
+        steps = ctypes.c_int64(0)
+        launches = ctypes.c_int64(0)
+        shape = (ctypes.c_int * 4)()
+        _check(lib().rbffd_plan_stats(self.handle, ctypes.byref(ms), ctypes.byref(steps),
+                                      ctypes.byref(launches), shape))
+        return ms.value, steps.value, launches.value, list(shape)
 
     def set_dc(self, K_in, rho_in):
         _check(lib().rbffd_plan_set_dc(self.handle, int(K_in), float(rho_in)))

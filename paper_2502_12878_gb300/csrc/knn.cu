@@ -231,13 +231,13 @@ using namespace rbffd;
 extern "C" int rbffd_knn(const double* xyz, int64_t N, int d, const int32_t* centres, int64_t nc,
                          int n, int32_t* idx, void* stream) {
     clear_error();
+    RBFFD_ARG(nc >= 0, "rbffd_knn: negative centre count");
+    if (nc == 0) return RBFFD_OK;
     RBFFD_ARG(xyz && centres && idx, "rbffd_knn: NULL argument");
     RBFFD_ARG(d >= 1 && d <= 3, "rbffd_knn: d must be 1, 2 or 3");
     RBFFD_ARG(N >= 1 && N < (int64_t(1) << 31), "rbffd_knn: bad N");
     RBFFD_ARG(n >= 1 && n <= KNN_NMAX && n <= N, "rbffd_knn: need 1 <= n <= min(N, %d)",
               KNN_NMAX);
-    RBFFD_ARG(nc >= 0, "rbffd_knn: negative centre count");
-    if (nc == 0) return RBFFD_OK;
     cudaStream_t s = as_stream(stream);
     double lo[3], hi[3];
     int st = bounding_box(xyz, N, d, lo, hi, s);

@@ -63,6 +63,17 @@ struct rbffd_plan {
     void* graph64 = nullptr;
     void* graph32 = nullptr;
     int graph_chunk = 0;
-    int grid_steps = 0;             // blocks of a step launch
+    int grid_steps = 0;             // blocks per SM of auxiliary sweeps (defect, power)
+    // tuned launch shape per mode (0 FP64 sweep, 1 FP32 inner sweep)
+    bool tuned[2] = {false, false};
+    int minb[2] = {2, 2};
+    int per_sm[2] = {2, 2};
+    float tune_ms[2] = {0.f, 0.f};
+    // timing of the last step loop (CUDA events on the caller's stream around
+    // the step launches) and the number of kernels the last solve launched
+    void* ev[2] = {nullptr, nullptr};
+    double last_loop_ms = 0.0;
+    long long last_loop_steps = 0;
+    long long last_launches = 0;
     rbffd::Transpose* tr = nullptr;
 };

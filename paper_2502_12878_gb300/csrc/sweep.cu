@@ -62,29 +62,39 @@ __device__ __forceinline__ double block_max(double v) {
 
 // ---------------------------------------------------------- row kernels
 // Streaming loads of the stencil planes (read once per step: evict-first).
-// Plain (non-volatile) asm so the compiler may batch them ahead of use.
+// Ordered asm: the compiler keeps them in program order, so the phases of
+// row_dot below really put 2*CH loads in flight before the first use.
 __device__ __forceinline__ double ld_stream(const double* p) {
     double v;
-    asm("ld.global.cs.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    asm volatile("ld.global.cs.f64 %0, [%1];" : "=d"(v) : "l"(p));
     return v;
 }
 __device__ __forceinline__ float ld_stream(const float* p) {
     float v;
-    asm("ld.global.cs.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    asm volatile("ld.global.cs.f32 %0, [%1];" : "=f"(v) : "l"(p));
     return v;
 }
 __device__ __forceinline__ int32_t ld_stream(const int32_t* p) {
     int32_t v;
-    asm("ld.global.cs.s32 %0, [%1];" : "=r"(v) : "l"(p));
+    asm volatile("ld.global.cs.s32 %0, [%1];" : "=r"(v) : "l"(p));
     return v;
 }
 // Gather of the iterate.  Within one launch per step the iterate is
 // read-only, so the non-coherent path (L1) is used; a persistent launch
 // rewrites it between steps from other SMs, so it reads through L2 (.cg).
-template <bool COHERENT, class T>
-__device__ __forceinline__ T ld_iter(const T* p) {
-    if (COHERENT) return __ldcg(p);
-    return __ldg(p);
+template <bool COHERENT>
+__device__ __forceinline__ double ld_iter(const double* p) {
+    double v;
+    if (COHERENT) asm volatile("ld.global.cg.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    else asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+template <bool COHERENT>
+__device__ __forceinline__ float ld_iter(const float* p) {
+    float v;
+    if (COHERENT) asm volatile("ld.global.cg.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    else asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
 }
 
 // sum_j w_j u[col_j] as an fma chain from 0, j ascending.  Loads are issued
@@ -118,6 +128,16 @@ __device__ __forceinline__ T row_dot(const T* __restrict__ w, const int32_t* __r
             }
     }
     return acc;
+}
+
+// |x| as IEEE bits, NaN mapped to +Inf: integer ops only (keeps the FP64
+// pipe for the multiply-adds)
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+    return b > 0x7ff0000000000000ull ? 0x7ff0000000000000ull : b;
+}
+__device__ __forceinline__ unsigned long long abs_bits(float x) {
+    return abs_bits((double)x);
 }
 
 template <int NN, bool COH = false>
@@ -154,10 +174,11 @@ struct StepArgs {
 // one step over the slices owned by this warp (slice0, slice0 + stride, ...);
 // returns this thread's max |r| with NaN -> +Inf
 template <int NN, int MODE, bool COH>
-__device__ __forceinline__ double step_rows(const StepArgs& A, int par, double dt, float dt32,
-                                            int64_t slice0, int64_t stride) {
+__device__ __forceinline__ unsigned long long step_rows(const StepArgs& A, int par, double dt,
+                                                        float dt32, int64_t slice0,
+                                                        int64_t stride) {
     const int lane = threadIdx.x & 31;
-    double m = 0.0;
+    unsigned long long m = 0;
     for (int64_t sl = slice0; sl < A.nslices; sl += stride) {
         const int64_t row = sl * SLICE + lane;
         const int64_t base = sl * (int64_t)A.n * SLICE + lane;
@@ -168,19 +189,31 @@ __device__ __forceinline__ double step_rows(const StepArgs& A, int par, double d
                 double acc = row_dot64<NN, COH>(A.w64 + base, A.col + base, uin, A.n);
                 double r = __dsub_rn(acc, A.f[row]);
                 uout[row] = __fma_rn(dt, r, uin[row]);
-                double a = fabs(r);
-                m = (a != a) ? INFINITY : fmax(m, a);
+                m = max(m, abs_bits(r));
             } else {
                 const float* ein = par ? A.e1 : A.e0;
                 float* eout = par ? A.e0 : A.e1;
                 float acc = row_dot32<NN, COH>(A.w32 + base, A.col + base, ein, A.n);
                 float rho = __fadd_rn(acc, A.d32[row]);
                 eout[row] = __fmaf_rn(dt32, rho, ein[row]);
-                double a = fabs((double)rho);
-                m = (a != a) ? INFINITY : fmax(m, a);
+                m = max(m, abs_bits(rho));
             }
         }
     }
+    return m;
+}
+
+// block max of IEEE bits; valid in thread 0
+__device__ __forceinline__ unsigned long long block_max_bits(unsigned long long v) {
+    __shared__ unsigned long long wm[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) wm[wid] = v;
+    __syncthreads();
+    unsigned long long m = 0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, wm[w]);
     return m;
 }
 
@@ -199,8 +232,8 @@ __device__ __forceinline__ int decide(StepCtrl* c, long long k, double R) {
 }
 
 // graph mode: one step per launch, one slice per warp
-template <int NN, int MODE>
-__global__ void __launch_bounds__(STEP_THREADS) step_kernel(StepArgs A, StepCtrl* c) {
+template <int NN, int MODE, int MINB>
+__global__ void __launch_bounds__(STEP_THREADS, MINB) step_kernel(StepArgs A, StepCtrl* c) {
     __shared__ long long s_k;
     __shared__ int s_skip;
     __shared__ double s_dt;
@@ -216,12 +249,12 @@ __global__ void __launch_bounds__(STEP_THREADS) step_kernel(StepArgs A, StepCtrl
     const long long k = s_k;
     const int par = (int)(k & 1);
     const int64_t warp = (int64_t)blockIdx.x * (STEP_THREADS / 32) + (threadIdx.x >> 5);
-    double m = step_rows<NN, MODE, false>(A, par, s_dt, (float)s_dt, warp,
-                                          (int64_t)gridDim.x * (STEP_THREADS / 32));
-    m = block_max(m);
+    unsigned long long m = step_rows<NN, MODE, false>(A, par, s_dt, (float)s_dt, warp,
+                                                      (int64_t)gridDim.x * (STEP_THREADS / 32));
+    m = block_max_bits(m);
     if (threadIdx.x == 0) {
         const int slot = (int)(k % 3);
-        atomicMax(&c->res[slot], dbits(m));
+        atomicMax(&c->res[slot], m);
         __threadfence();
         unsigned t = atomicAdd(&c->arrive[slot], 1u);
         if (t == gridDim.x - 1) {
@@ -269,8 +302,8 @@ __device__ bool grid_sync(StepCtrl* c) {
 }
 
 // persistent mode: all steps in one cooperative launch
-template <int NN, int MODE>
-__global__ void __launch_bounds__(STEP_THREADS) persistent_kernel(StepArgs A, StepCtrl* c) {
+template <int NN, int MODE, int MINB>
+__global__ void __launch_bounds__(STEP_THREADS, MINB) persistent_kernel(StepArgs A, StepCtrl* c) {
     __shared__ long long s_k, s_max;
     __shared__ double s_dt;
     __shared__ int s_stop;
@@ -286,10 +319,10 @@ __global__ void __launch_bounds__(STEP_THREADS) persistent_kernel(StepArgs A, St
     const int64_t warp = (int64_t)blockIdx.x * (STEP_THREADS / 32) + (threadIdx.x >> 5);
     const int64_t nw = (int64_t)gridDim.x * (STEP_THREADS / 32);
     for (long long k = s_k; k < kmax; ++k) {
-        double m = step_rows<NN, MODE, true>(A, (int)(k & 1), dt, (float)dt, warp, nw);
-        m = block_max(m);
+        unsigned long long m = step_rows<NN, MODE, true>(A, (int)(k & 1), dt, (float)dt, warp, nw);
+        m = block_max_bits(m);
         if (threadIdx.x == 0) {
-            atomicMax(&c->res[k % 3], dbits(m));
+            atomicMax(&c->res[k % 3], m);
             if (blockIdx.x == 0) atomicExch(&c->res[(k + 1) % 3], 0ull);
         }
         if (!grid_sync(c)) {
@@ -328,10 +361,15 @@ __global__ void __launch_bounds__(STEP_THREADS) persistent_kernel(StepArgs A, St
 // ------------------------------------------------------ dispatch by n
 typedef void (*StepFn)(StepArgs, StepCtrl*);
 
-template <int MODE>
-static StepFn pick_step(int n, bool persistent) {
+// launch shape of a step kernel: the register budget (min resident blocks per
+// SM the compiler must allow: more blocks = fewer registers = fewer loads in
+// flight per thread) and the grid (blocks per SM of the grid-stride sweep)
+static constexpr int N_MINB = 3;
+
+template <int MODE, int MINB>
+static StepFn pick_step_m(int n, bool persistent) {
 #define RBFFD_CASE(NN) \
-    case NN: return persistent ? persistent_kernel<NN, MODE> : step_kernel<NN, MODE>;
+    case NN: return persistent ? persistent_kernel<NN, MODE, MINB> : step_kernel<NN, MODE, MINB>;
     switch (n) {
         RBFFD_CASE(6)
         RBFFD_CASE(12)
@@ -343,9 +381,23 @@ static StepFn pick_step(int n, bool persistent) {
         RBFFD_CASE(57)
         RBFFD_CASE(70)
         RBFFD_CASE(71)
-        default: return persistent ? persistent_kernel<0, MODE> : step_kernel<0, MODE>;
+        default: return persistent ? persistent_kernel<0, MODE, MINB> : step_kernel<0, MODE, MINB>;
     }
 #undef RBFFD_CASE
+}
+
+template <int MODE>
+static StepFn pick_step(int n, bool persistent, int minb) {
+    switch (minb) {
+        case 1: return pick_step_m<MODE, 1>(n, persistent);
+        case 3: return pick_step_m<MODE, 3>(n, persistent);
+        default: return pick_step_m<MODE, 2>(n, persistent);
+    }
+}
+
+static StepFn pick(int mode, int n, bool persistent, int minb) {
+    return mode == MODE_SWEEP64 ? pick_step<MODE_SWEEP64>(n, persistent, minb)
+                                : pick_step<MODE_INNER32>(n, persistent, minb);
 }
 
 // ------------------------------------------------------- plan building
@@ -654,16 +706,22 @@ static void free_plan(rbffd_plan* p) {
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (p->graph64) cudaGraphExecDestroy((cudaGraphExec_t)p->graph64);
+    for (void* e : p->ev)
+        if (e) cudaEventDestroy((cudaEvent_t)e);
     if (p->graph32) cudaGraphExecDestroy((cudaGraphExec_t)p->graph32);
     free_transpose(p);
     delete p;
 }
 
-static int step_grid(const rbffd_plan* p) {
+// blocks of a grid-stride launch with `per_sm` blocks per SM (fewer,
+// longer-lived blocks avoid the tail of many short ones)
+static int grid_for(const rbffd_plan* p, int per_sm) {
     int64_t warps = p->nslices;
     int64_t blocks = (warps + STEP_THREADS / 32 - 1) / (STEP_THREADS / 32);
-    return (int)std::max<int64_t>(1, blocks);
+    int64_t cap = (int64_t)device_sm_count() * std::max(1, per_sm);
+    return (int)std::max<int64_t>(1, std::min(blocks, cap));
 }
+static int step_grid(const rbffd_plan* p) { return grid_for(p, p->grid_steps); }
 
 static int persistent_grid(StepFn fn) {
     int per_sm = 0;
@@ -686,16 +744,89 @@ static int ctrl_reset(rbffd_plan* p, double dt, double tol, long long max_steps,
     return RBFFD_OK;
 }
 
+// Autotuner: time every launch shape of `mode` for a few steps on this plan's
+// own stencils (u / e buffers zeroed; dt = 0 so nothing moves) and keep the
+// fastest.  Candidates: register budget minb in {1, 2, 3} x blocks per SM in
+// {1, 2, 3, 4} (graph mode), or minb alone (persistent mode, whose grid is
+// the resident maximum).  Runs once per plan and mode, on `s`.
+static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
+    const int mi = mode == MODE_SWEEP64 ? 0 : 1;
+    if (p->tuned[mi]) return RBFFD_OK;
+    const bool persistent = (p->flags & RBFFD_LAUNCH_PERSISTENT) != 0;
+    RBFFD_CHECK_CUDA(cudaMemsetAsync(p->u[0], 0, sizeof(double) * p->N, s));
+    RBFFD_CHECK_CUDA(cudaMemsetAsync(p->u[1], 0, sizeof(double) * p->N, s));
+    RBFFD_CHECK_CUDA(cudaMemsetAsync(p->e[0], 0, sizeof(float) * p->N, s));
+    RBFFD_CHECK_CUDA(cudaMemsetAsync(p->e[1], 0, sizeof(float) * p->N, s));
+    RBFFD_CHECK_CUDA(cudaMemsetAsync(p->d32, 0, sizeof(float) * p->NI, s));
+    cudaEvent_t e0, e1;
+    RBFFD_CHECK_CUDA(cudaEventCreate(&e0));
+    RBFFD_CHECK_CUDA(cudaEventCreate(&e1));
+    StepArgs A = make_args(p);
+    // enough steps to time reliably on small plans, few on large ones
+    const long long reps = std::max<long long>(3, std::min<long long>(40, 20000000 / (p->NI * p->n + 1)));
+    float best = 1e30f;
+    int bm = 2, bg = 2;
+    int st = RBFFD_OK;
+    for (int minb = 1; minb <= N_MINB && st == RBFFD_OK; ++minb) {
+        StepFn fn = pick(mode, p->n, persistent, minb);
+        for (int per_sm = 1; per_sm <= (persistent ? 1 : 4); ++per_sm) {
+            int grid = persistent
+                           ? (int)std::min<int64_t>(persistent_grid(fn), std::max<int64_t>(1, p->nslices))
+                           : grid_for(p, per_sm);
+            float ms = 0.f;
+            for (int pass = 0; pass < 2; ++pass) {   // pass 0 warms up
+                if ((st = ctrl_reset(p, 0.0, 0.0, pass ? reps : 2, s))) break;
+                cudaEventRecord(e0, s);
+                if (persistent) {
+                    StepCtrl* c = p->ctrl;
+                    void* args[] = {(void*)&A, (void*)&c};
+                    cudaLaunchCooperativeKernel((const void*)fn, dim3(grid), dim3(STEP_THREADS), args,
+                                                0, s);
+                } else {
+                    for (long long i = 0; i < (pass ? reps : 2); ++i)
+                        fn<<<grid, STEP_THREADS, 0, s>>>(A, p->ctrl);
+                }
+                cudaEventRecord(e1, s);
+            }
+            if (st) break;
+            cudaError_t e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaGetLastError();
+            if (e != cudaSuccess) {
+                set_error("autotune: %s", cudaGetErrorString(e));
+                st = RBFFD_ERR_CUDA;
+                break;
+            }
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                bm = minb;
+                bg = per_sm;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    p->minb[mi] = bm;
+    p->per_sm[mi] = bg;
+    p->tune_ms[mi] = best / (float)reps;
+    p->tuned[mi] = true;
+    return RBFFD_OK;
+}
+
 // build (once) a graph of `chunk` step launches of the given mode
-static int ensure_graph(rbffd_plan* p, int mode) {
+static int ensure_graph(rbffd_plan* p, int mode, cudaStream_t s) {
     void** slot = mode == MODE_SWEEP64 ? &p->graph64 : &p->graph32;
     if (*slot) return RBFFD_OK;
-    StepFn fn = mode == MODE_SWEEP64 ? pick_step<MODE_SWEEP64>(p->n, false)
-                                     : pick_step<MODE_INNER32>(p->n, false);
+    const int mi = mode == MODE_SWEEP64 ? 0 : 1;
+    int st = tune_shape(p, mode, s);
+    if (st) return st;
+    RBFFD_CHECK_CUDA(cudaStreamSynchronize(s));
+    StepFn fn = pick(mode, p->n, false, p->minb[mi]);
     cudaStream_t cs;
     RBFFD_CHECK_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     StepArgs A = make_args(p);
-    int grid = step_grid(p);
+    int grid = grid_for(p, p->per_sm[mi]);
     cudaGraph_t g;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
@@ -723,31 +854,80 @@ static int run_steps(rbffd_plan* p, int mode, double dt, double tol, long long m
     if (max_steps > 0) {
         bool persistent = (p->flags & RBFFD_LAUNCH_PERSISTENT) != 0;
         if (persistent) {
-            StepFn fn = mode == MODE_SWEEP64 ? pick_step<MODE_SWEEP64>(p->n, true)
-                                             : pick_step<MODE_INNER32>(p->n, true);
+            const int mi = mode == MODE_SWEEP64 ? 0 : 1;
+            if (!p->tuned[mi]) {
+                // the tuner clobbers the iterate buffers: save and restore them
+                Scratch save;
+                RBFFD_CHECK_CUDA(save.alloc(sizeof(double) * 2 * p->N + sizeof(float) * 2 * p->N, s));
+                double* sv = save.as<double>();
+                float* se = reinterpret_cast<float*>(sv + 2 * p->N);
+                RBFFD_CHECK_CUDA(cudaMemcpyAsync(sv, p->u[0], sizeof(double) * p->N, cudaMemcpyDeviceToDevice, s));
+                RBFFD_CHECK_CUDA(cudaMemcpyAsync(sv + p->N, p->u[1], sizeof(double) * p->N, cudaMemcpyDeviceToDevice, s));
+                RBFFD_CHECK_CUDA(cudaMemcpyAsync(se, p->e[0], sizeof(float) * p->N, cudaMemcpyDeviceToDevice, s));
+                RBFFD_CHECK_CUDA(cudaMemcpyAsync(se + p->N, p->e[1], sizeof(float) * p->N, cudaMemcpyDeviceToDevice, s));
+                Scratch saved32;
+                RBFFD_CHECK_CUDA(saved32.alloc(sizeof(float) * p->NI, s));
+                RBFFD_CHECK_CUDA(cudaMemcpyAsync(saved32.p, p->d32, sizeof(float) * p->NI, cudaMemcpyDeviceToDevice, s));
+                st = tune_shape(p, mode, s);
+                if (st) return st;
+                RBFFD_CHECK_CUDA(cudaMemcpyAsync(p->u[0], sv, sizeof(double) * p->N, cudaMemcpyDeviceToDevice, s));
+                RBFFD_CHECK_CUDA(cudaMemcpyAsync(p->u[1], sv + p->N, sizeof(double) * p->N, cudaMemcpyDeviceToDevice, s));
+                RBFFD_CHECK_CUDA(cudaMemcpyAsync(p->e[0], se, sizeof(float) * p->N, cudaMemcpyDeviceToDevice, s));
+                RBFFD_CHECK_CUDA(cudaMemcpyAsync(p->e[1], se + p->N, sizeof(float) * p->N, cudaMemcpyDeviceToDevice, s));
+                RBFFD_CHECK_CUDA(cudaMemcpyAsync(p->d32, saved32.p, sizeof(float) * p->NI, cudaMemcpyDeviceToDevice, s));
+                st = ctrl_reset(p, dt, tol, max_steps, s);
+                if (st) return st;
+            }
+            StepFn fn = pick(mode, p->n, true, p->minb[mi]);
             int grid = std::min<int64_t>(persistent_grid(fn), std::max<int64_t>(1, p->nslices));
             StepArgs A = make_args(p);
             StepCtrl* c = p->ctrl;
             void* args[] = {(void*)&A, (void*)&c};
+            RBFFD_CHECK_CUDA(cudaEventRecord((cudaEvent_t)p->ev[0], s));
             RBFFD_CHECK_CUDA(cudaLaunchCooperativeKernel((const void*)fn, dim3(grid),
                                                          dim3(STEP_THREADS), args, 0, s));
+            RBFFD_CHECK_CUDA(cudaEventRecord((cudaEvent_t)p->ev[1], s));
+            p->last_launches += 1;
         } else {
-            st = ensure_graph(p, mode);
-            if (st) return st;
+            if (!p->graph64 && mode == MODE_SWEEP64 || !p->graph32 && mode == MODE_INNER32) {
+                Scratch save;
+                RBFFD_CHECK_CUDA(save.alloc(sizeof(double) * 2 * p->N + sizeof(float) * 2 * p->N, s));
+                double* sv = save.as<double>();
+                float* se = reinterpret_cast<float*>(sv + 2 * p->N);
+                RBFFD_CHECK_CUDA(cudaMemcpyAsync(sv, p->u[0], sizeof(double) * p->N, cudaMemcpyDeviceToDevice, s));
+                RBFFD_CHECK_CUDA(cudaMemcpyAsync(sv + p->N, p->u[1], sizeof(double) * p->N, cudaMemcpyDeviceToDevice, s));
+                RBFFD_CHECK_CUDA(cudaMemcpyAsync(se, p->e[0], sizeof(float) * p->N, cudaMemcpyDeviceToDevice, s));
+                RBFFD_CHECK_CUDA(cudaMemcpyAsync(se + p->N, p->e[1], sizeof(float) * p->N, cudaMemcpyDeviceToDevice, s));
+                Scratch saved32;
+                RBFFD_CHECK_CUDA(saved32.alloc(sizeof(float) * p->NI, s));
+                RBFFD_CHECK_CUDA(cudaMemcpyAsync(saved32.p, p->d32, sizeof(float) * p->NI, cudaMemcpyDeviceToDevice, s));
+                st = ensure_graph(p, mode, s);
+                if (st) return st;
+                RBFFD_CHECK_CUDA(cudaMemcpyAsync(p->u[0], sv, sizeof(double) * p->N, cudaMemcpyDeviceToDevice, s));
+                RBFFD_CHECK_CUDA(cudaMemcpyAsync(p->u[1], sv + p->N, sizeof(double) * p->N, cudaMemcpyDeviceToDevice, s));
+                RBFFD_CHECK_CUDA(cudaMemcpyAsync(p->e[0], se, sizeof(float) * p->N, cudaMemcpyDeviceToDevice, s));
+                RBFFD_CHECK_CUDA(cudaMemcpyAsync(p->e[1], se + p->N, sizeof(float) * p->N, cudaMemcpyDeviceToDevice, s));
+                RBFFD_CHECK_CUDA(cudaMemcpyAsync(p->d32, saved32.p, sizeof(float) * p->NI, cudaMemcpyDeviceToDevice, s));
+                st = ctrl_reset(p, dt, tol, max_steps, s);
+                if (st) return st;
+            }
             cudaGraphExec_t ex = (cudaGraphExec_t)(mode == MODE_SWEEP64 ? p->graph64 : p->graph32);
             long long launched = 0;
             // replay chunks; check the device decision every `per_check` chunks
             long long per_check = std::max<long long>(1, std::min<long long>(
                                        64, (max_steps + p->graph_chunk - 1) / p->graph_chunk));
+            RBFFD_CHECK_CUDA(cudaEventRecord((cudaEvent_t)p->ev[0], s));
             for (;;) {
                 for (long long i = 0; i < per_check && launched < max_steps; ++i) {
                     RBFFD_CHECK_CUDA(cudaGraphLaunch(ex, s));
                     launched += p->graph_chunk;
                 }
+                RBFFD_CHECK_CUDA(cudaEventRecord((cudaEvent_t)p->ev[1], s));
                 RBFFD_CHECK_CUDA(cudaMemcpyAsync(&h, p->ctrl, sizeof(h), cudaMemcpyDeviceToHost, s));
                 RBFFD_CHECK_CUDA(cudaStreamSynchronize(s));
                 if (h.done != DONE_RUNNING || launched >= max_steps) break;
             }
+            p->last_launches += launched;
         }
     }
     RBFFD_CHECK_CUDA(cudaMemcpyAsync(&h, p->ctrl, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -755,6 +935,12 @@ static int run_steps(rbffd_plan* p, int mode, double dt, double tol, long long m
     *steps = h.k;
     *res = h.res_last;
     *done = h.done;
+    if (max_steps > 0) {
+        float ms = 0.f;
+        RBFFD_CHECK_CUDA(cudaEventElapsedTime(&ms, (cudaEvent_t)p->ev[0], (cudaEvent_t)p->ev[1]));
+        p->last_loop_ms += ms;
+        p->last_loop_steps += h.k;
+    }
     return RBFFD_OK;
 }
 
@@ -802,9 +988,9 @@ using namespace rbffd;
 extern "C" int rbffd_apply(const double* w, const int32_t* idx, int64_t nc, int n, const double* u,
                            double* Lu, void* stream) {
     clear_error();
-    RBFFD_ARG(w && idx && u && Lu, "rbffd_apply: NULL argument");
     RBFFD_ARG(nc >= 0 && n >= 1, "rbffd_apply: bad sizes");
     if (nc == 0) return RBFFD_OK;
+    RBFFD_ARG(w && idx && u && Lu, "rbffd_apply: NULL argument");
     int sms = device_sm_count();
     int64_t blocks = std::min<int64_t>((nc + 255) / 256, (int64_t)sms * 16);
     apply_rowmajor<<<(unsigned)blocks, 256, 0, as_stream(stream)>>>(w, idx, nc, n, u, Lu);
@@ -834,6 +1020,7 @@ extern "C" int rbffd_plan_create(const double* xyz, const uint8_t* is_bnd, int64
     p->flags = flags;
     p->nslices = (NI + SLICE - 1) / SLICE;
     p->graph_chunk = 32;
+    p->grid_steps = 2;
     const size_t ell = (size_t)p->nslices * n * SLICE;
     cudaError_t e = cudaSuccess;
 #define RBFFD_ALLOC(ptr, bytes) \
@@ -853,6 +1040,11 @@ extern "C" int rbffd_plan_create(const double* xyz, const uint8_t* is_bnd, int64
     RBFFD_ALLOC(p->scratch, sizeof(double) * (2 * NI + 4096));
     RBFFD_ALLOC(p->ctrl, sizeof(StepCtrl));
 #undef RBFFD_ALLOC
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        cudaEvent_t ev;
+        e = cudaEventCreate(&ev);
+        if (e == cudaSuccess) p->ev[i] = (void*)ev;
+    }
     if (e != cudaSuccess) {
         set_error("rbffd_plan_create: cudaMalloc: %s", cudaGetErrorString(e));
         free_plan(p);
@@ -971,6 +1163,9 @@ extern "C" int rbffd_plan_set_dc(rbffd_plan* p, int64_t K_in, double rho_in) {
 
 static int load_problem(rbffd_plan* p, const double* f, const double* u, cudaStream_t s) {
     int sms = device_sm_count();
+    p->last_loop_ms = 0.0;
+    p->last_loop_steps = 0;
+    p->last_launches = 2;   // gather_f, gather_u (+ the step kernels, + scatter_u)
     gather_f<<<sms * 8, 256, 0, s>>>(f, p->row_of_slot, p->NI, p->fs);
     gather_u<<<sms * 8, 256, 0, s>>>(u, p->perm, p->N, p->u[0], p->u[1]);
     RBFFD_CHECK_CUDA(cudaGetLastError());
@@ -1008,6 +1203,7 @@ extern "C" int rbffd_solve_dc(rbffd_plan* p, const double* f, double* u, double 
         RBFFD_CHECK_CUDA(cudaMemsetAsync(dmax, 0, sizeof(unsigned long long), s));
         def<<<grid, STEP_THREADS, 0, s>>>(A, p->u[0], dmax);
         RBFFD_CHECK_CUDA(cudaGetLastError());
+        p->last_launches += 1;
         unsigned long long hb = 0;
         RBFFD_CHECK_CUDA(cudaMemcpyAsync(&hb, dmax, sizeof(hb), cudaMemcpyDeviceToHost, s));
         RBFFD_CHECK_CUDA(cudaStreamSynchronize(s));
@@ -1040,9 +1236,11 @@ extern "C" int rbffd_solve_dc(rbffd_plan* p, const double* f, double* u, double 
         const float* ef = p->e[steps & 1];
         dc_update<<<sms * 8, 256, 0, s>>>(p->u[0], ef, p->NI);
         RBFFD_CHECK_CUDA(cudaGetLastError());
+        p->last_launches += 1;
     }
     scatter_u<<<sms * 8, 256, 0, s>>>(p->u[0], p->perm, p->NI, u);
     RBFFD_CHECK_CUDA(cudaGetLastError());
+    p->last_launches += 1;
     RBFFD_CHECK_CUDA(cudaStreamSynchronize(s));
     if (h_outer_out) *h_outer_out = outer;
     if (h_inner_out) *h_inner_out = inner_total;
@@ -1076,6 +1274,7 @@ extern "C" int rbffd_solve_explicit(rbffd_plan* p, const double* f, double* u, d
     if (st) return st;
     int sms = device_sm_count();
     scatter_u<<<sms * 8, 256, 0, s>>>(p->u[steps & 1], p->perm, p->NI, u);
+    p->last_launches += 1;
     RBFFD_CHECK_CUDA(cudaGetLastError());
     RBFFD_CHECK_CUDA(cudaStreamSynchronize(s));
     if (h_steps_out) *h_steps_out = steps;
@@ -1128,5 +1327,21 @@ extern "C" int rbffd_stable_dt(rbffd_plan* p, const double* v0, int iters, doubl
     }
     if (h_rho_out) *h_rho_out = rho;
     if (h_dt_out) *h_dt_out = 2.0 / (safety * rho);
+    return RBFFD_OK;
+}
+
+extern "C" int rbffd_plan_stats(const rbffd_plan* p, double* h_loop_ms, int64_t* h_loop_steps,
+                                int64_t* h_launches, int* h_shape) {
+    clear_error();
+    RBFFD_ARG(p, "rbffd_plan_stats: NULL plan");
+    if (h_loop_ms) *h_loop_ms = p->last_loop_ms;
+    if (h_loop_steps) *h_loop_steps = p->last_loop_steps;
+    if (h_launches) *h_launches = p->last_launches;
+    if (h_shape) {
+        h_shape[0] = p->minb[0];
+        h_shape[1] = p->per_sm[0];
+        h_shape[2] = p->minb[1];
+        h_shape[3] = p->per_sm[1];
+    }
     return RBFFD_OK;
 }

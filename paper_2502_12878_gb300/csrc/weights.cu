@@ -233,6 +233,11 @@ extern "C" int rbffd_weights(const double* xyz, int64_t N, int d, const int32_t*
                              int n, int m, double* w, int8_t* status, int64_t* h_n_bad,
                              int64_t* h_first_bad, void* stream) {
     clear_error();
+    if (nc == 0 && n >= 1) {
+        if (h_n_bad) *h_n_bad = 0;
+        if (h_first_bad) *h_first_bad = -1;
+        return RBFFD_OK;
+    }
     RBFFD_ARG(xyz && idx && w && status, "rbffd_weights: NULL argument");
     RBFFD_ARG(d >= 1 && d <= 3, "rbffd_weights: d must be 1, 2 or 3");
     RBFFD_ARG(m >= 0 && m <= 12, "rbffd_weights: m must be in [0, 12]");

@@ -119,8 +119,9 @@ RBFFD_API int rbffd_knn(const double* xyz, int64_t N, int d, const int32_t* cent
  * then x exponent descending, then y descending), right-hand side
  * 3(d+1)|xi_j| and 2 for the pure squares; the (n+M)^2 system is solved in
  * FP64 by Gaussian elimination with partial pivoting (first row of largest
- * |pivot|; multiplier by division, updates by fused multiply-add; back
- * substitution by columns), and w_j = x_j / sigma^2.
+ * |pivot|; multiplier = entry x (1/pivot); updates by fused multiply-add; back
+ * substitution by columns), and w_j = x_j / sigma^2.  A row is singular when a
+ * pivot is not finite or |pivot| <= 1e-13 x max|entry| of its system.
  * Returns RBFFD_ERR_SINGULAR if any row failed; h_n_bad / h_first_bad (host,
  * may be NULL) receive the count and the first failing row.
  */

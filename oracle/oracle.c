@@ -400,14 +400,25 @@ static double ipow(double x, int e)
 /* Gaussian elimination with partial pivoting on the s x (s+1) row-major
  * augmented matrix G (last column = right-hand side); solution in x.
  * Elimination: for k = 0..s-1, pivot row p = first row i >= k with the
- * largest |G[i][k]|; swap rows k and p; for every row i > k,
- * l = G[i][k] / G[k][k] and G[i][j] = fma(-l, G[k][j], G[i][j]) for j > k.
+ * largest |G[i][k]|; swap rows k and p; rp = 1 / G[k][k]; for every row
+ * i > k, l = G[i][k] * rp (the column scaled by the reciprocal pivot, as
+ * LAPACK's unblocked LU does) and G[i][j] = fma(-l, G[k][j], G[i][j]) for j > k.
+ * A pivot is unusable (status 1: numerically singular system) when it is not
+ * finite or |pivot| <= 1e-13 * gmax, gmax = max |G[i][j]| over the matrix as
+ * assembled (right-hand side excluded); an all-zero matrix is singular too.
  * Back substitution by columns: for j = s-1..0, x_j = G[j][s] / G[j][j],
  * then G[i][s] = fma(-G[i][j], x_j, G[i][s]) for every i < j.
  * Returns 0, or 1 when a pivot is non-finite or |pivot| <= 1e-300. */
 int oracle_gepp_solve(int s, double* G, double* x)
 {
     const int W = s + 1;
+    double gmax = 0.0;
+    for (int i = 0; i < s; ++i)
+        for (int j = 0; j < s; ++j) {
+            double v = fabs(G[(int64_t)i * W + j]);
+            if (v > gmax) gmax = v;
+        }
+    const double tiny = 1e-13 * gmax;
     for (int k = 0; k < s; ++k) {
         int p = k;
         double best = fabs(G[(int64_t)k * W + k]);
@@ -415,16 +426,16 @@ int oracle_gepp_solve(int s, double* G, double* x)
             double v = fabs(G[(int64_t)i * W + k]);
             if (v > best) { best = v; p = i; }
         }
-        if (!(best > 1e-300) || !isfinite(best)) return 1;
+        if (!(best > tiny) || !(best > 1e-300) || !isfinite(best)) return 1;
         if (p != k)
             for (int j = 0; j < W; ++j) {
                 double t = G[(int64_t)k * W + j];
                 G[(int64_t)k * W + j] = G[(int64_t)p * W + j];
                 G[(int64_t)p * W + j] = t;
             }
-        double piv = G[(int64_t)k * W + k];
+        double rp = 1.0 / G[(int64_t)k * W + k];
         for (int i = k + 1; i < s; ++i) {
-            double l = G[(int64_t)i * W + k] / piv;
+            double l = G[(int64_t)i * W + k] * rp;
             for (int j = k + 1; j < W; ++j)
                 G[(int64_t)i * W + j] = fma(-l, G[(int64_t)k * W + j], G[(int64_t)i * W + j]);
         }

@@ -1,16 +1,19 @@
 // rbffd_weights: batched RBF-FD Laplacian weights (Eq. 2-3), phi(r) = r^3
 // augmented with every monomial of degree <= m, solved in FP64.
 //
-// One warp owns one local system at a time.  The (n+M) x (n+M+1) augmented
-// matrix lives in shared memory (odd row pitch, so column walks are
-// bank-conflict free); the warp assembles it, eliminates with partial
-// pivoting (lanes across columns for the trailing update, the pivot row kept
-// in registers), and back-substitutes by columns.  Every element sees the
-// same sequence of IEEE operations as the textbook algorithm (multiplier by
-// division, update by fused multiply-add, first row of largest |pivot|), so
-// the result does not depend on how lanes split the work.
+// A team of TW warps owns one local system at a time (TW = 1 for s <= 48,
+// several systems per block; TW = 4 above, one system per block, so large
+// systems still give every SM sub-partition warps).  The (n+M) x (n+M+1)
+// augmented matrix lives in shared memory (odd row pitch: column walks hit
+// distinct banks).  The team assembles it (the symmetric r^3 block from its
+// upper triangle), eliminates with partial pivoting, and back-substitutes by
+// columns.  The trailing update is flattened over (row, column) pairs so every
+// issued FP64 instruction is a useful multiply-add.  Every element sees the
+// same sequence of IEEE operations as the textbook algorithm (first row of
+// largest |pivot|, multiplier = entry x reciprocal pivot, update by fused
+// multiply-add), so the result does not depend on how lanes split the work.
 //
-// The work is FP64-ALU bound: (2/3) s^3 multiply-adds per stencil.
+// FP64-ALU bound: about s^3/3 multiply-adds per stencil.
 #include <math.h>
 
 #include <algorithm>
@@ -40,21 +43,74 @@ __device__ __forceinline__ double powi(double x, int e) {
     return p;
 }
 
-__global__ void weights_kernel(WeightArgs A, int warps_per_block) {
-    extern __shared__ double wsm[];
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const int n = A.n, M = A.M, s = A.s, P = A.pitch, d = A.d;
-    double* G = wsm + (size_t)wib * ((size_t)s * P + 3 * n);
-    double* xi = G + (size_t)s * P;
-    const int64_t warps = (int64_t)gridDim.x * warps_per_block;
+template <int TW>
+__device__ __forceinline__ void team_sync() {
+    if (TW == 1) __syncwarp();
+    else __syncthreads();
+}
 
-    for (int64_t r = (int64_t)blockIdx.x * warps_per_block + wib; r < A.nc; r += warps) {
+// team-wide max of a double / argmax (value, lowest index on ties)
+template <int TW>
+__device__ __forceinline__ double team_max(double v, double* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (TW == 1) return v;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double m = red[0];
+    for (int q = 1; q < TW; ++q) m = fmax(m, red[q]);
+    __syncthreads();
+    return m;
+}
+
+template <int TW>
+__device__ __forceinline__ void team_argmax(double& bv, int& bi, double* redv, int* redi) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > bv || (ov == bv && oi < bi)) {
+            bv = ov;
+            bi = oi;
+        }
+    }
+    if (TW == 1) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        redv[wid] = bv;
+        redi[wid] = bi;
+    }
+    __syncthreads();
+    bv = redv[0];
+    bi = redi[0];
+    for (int q = 1; q < TW; ++q)
+        if (redv[q] > bv || (redv[q] == bv && redi[q] < bi)) {
+            bv = redv[q];
+            bi = redi[q];
+        }
+    __syncthreads();
+}
+
+template <int TW>
+__global__ void __launch_bounds__(256) weights_kernel(WeightArgs A, int teams_per_block) {
+    extern __shared__ double wsm[];
+    __shared__ double redv[8];
+    __shared__ int redi[8];
+    constexpr int T = 32 * TW;
+    const int tid = threadIdx.x % T;
+    const int team = threadIdx.x / T;
+    const int n = A.n, M = A.M, s = A.s, P = A.pitch, d = A.d;
+    double* G = wsm + (size_t)team * ((size_t)s * P + 3 * n);
+    double* xi = G + (size_t)s * P;
+    const int64_t teams = (int64_t)gridDim.x * teams_per_block;
+
+    for (int64_t r = (int64_t)blockIdx.x * teams_per_block + team; r < A.nc; r += teams) {
         const int32_t* sup = A.idx + r * n;
         const int32_t c = sup[0];
         // scale sigma = max_j |x_j - x_c|
         double sig = 0.0;
-        for (int j = lane; j < n; j += 32) {
+        for (int j = tid; j < n; j += T) {
             int32_t id = sup[j];
             double s2 = 0.0;
             for (int a = 0; a < d; ++a) {
@@ -64,34 +120,54 @@ __global__ void weights_kernel(WeightArgs A, int warps_per_block) {
             }
             sig = fmax(sig, __dsqrt_rn(s2));
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sig = fmax(sig, __shfl_xor_sync(0xffffffffu, sig, o));
+        sig = team_max<TW>(sig, redv);
         if (!(sig > 0.0)) {
-            for (int j = lane; j < n; j += 32) A.w[r * n + j] = 0.0;
-            if (lane == 0) A.status[r] = 1;
+            for (int j = tid; j < n; j += T) A.w[r * n + j] = 0.0;
+            if (tid == 0) A.status[r] = 1;
+            team_sync<TW>();
             continue;
         }
-        for (int j = lane; j < n; j += 32) {
+        for (int j = tid; j < n; j += T) {
             int32_t id = sup[j];
             for (int a = 0; a < d; ++a) {
                 double t = __dsub_rn(A.xyz[(int64_t)a * A.N + id], A.xyz[(int64_t)a * A.N + c]);
                 xi[3 * j + a] = __ddiv_rn(t, sig);
             }
         }
-        __syncwarp();
-        // assemble [[A P] [P^T 0]] | rhs
-        for (int e = lane; e < n * n; e += 32) {
-            int j = e / n, k = e - j * n;
-            double r2 = 0.0;
-            for (int a = 0; a < d; ++a) {
-                double t = __dsub_rn(xi[3 * j + a], xi[3 * k + a]);
-                double sq = __dmul_rn(t, t);
-                r2 = a == 0 ? sq : __dadd_rn(r2, sq);
+        team_sync<TW>();
+        // assemble [[A P] [P^T 0]] | rhs; A from its strict upper triangle
+        // (pairs j < k enumerated row by row), diagonal 0
+        {
+            const int npairs = n * (n - 1) / 2;
+            // pair number e -> (j, k): row j holds the n - 1 - j pairs (j, j+1..n-1)
+            int e = tid, j = 0, rowlen = n - 1, off = tid;
+            while (rowlen > 0 && off >= rowlen) {
+                off -= rowlen;
+                ++j;
+                --rowlen;
             }
-            double rr = __dsqrt_rn(r2);
-            G[j * P + k] = __dmul_rn(__dmul_rn(rr, rr), rr);
+            int k = j + 1 + off;
+            for (; e < npairs; e += T) {
+                double r2 = 0.0;
+                for (int a = 0; a < d; ++a) {
+                    double t = __dsub_rn(xi[3 * j + a], xi[3 * k + a]);
+                    double sq = __dmul_rn(t, t);
+                    r2 = a == 0 ? sq : __dadd_rn(r2, sq);
+                }
+                double rr = __dsqrt_rn(r2);
+                double v = __dmul_rn(__dmul_rn(rr, rr), rr);
+                G[j * P + k] = v;
+                G[k * P + j] = v;
+                // advance by T pairs (spilling into the following rows)
+                k += T;
+                while (j < n - 1 && k >= n) {
+                    k = k - (n - 1 - j) + 1;
+                    ++j;
+                }
+            }
         }
-        for (int e = lane; e < n * M; e += 32) {
+        for (int j = tid; j < n; j += T) G[j * P + j] = 0.0;
+        for (int e = tid; e < n * M; e += T) {
             int j = e / M, al = e - j * M;
             double p = powi(xi[3 * j + 0], A.ex[al][0]);
             if (d >= 2) p = __dmul_rn(p, powi(xi[3 * j + 1], A.ex[al][1]));
@@ -99,11 +175,11 @@ __global__ void weights_kernel(WeightArgs A, int warps_per_block) {
             G[j * P + n + al] = p;
             G[(n + al) * P + j] = p;
         }
-        for (int e = lane; e < M * M; e += 32) {
+        for (int e = tid; e < M * M; e += T) {
             int a1 = e / M, a2 = e - a1 * M;
             G[(n + a1) * P + n + a2] = 0.0;
         }
-        for (int j = lane; j < n; j += 32) {
+        for (int j = tid; j < n; j += T) {
             double rc2 = 0.0;
             for (int a = 0; a < d; ++a) {
                 double sq = __dmul_rn(xi[3 * j + a], xi[3 * j + a]);
@@ -111,22 +187,30 @@ __global__ void weights_kernel(WeightArgs A, int warps_per_block) {
             }
             G[j * P + s] = __dmul_rn(A.lap_phi, __dsqrt_rn(rc2));
         }
-        for (int al = lane; al < M; al += 32) {
+        for (int al = tid; al < M; al += T) {
             int e0 = A.ex[al][0], e1 = A.ex[al][1], e2 = A.ex[al][2];
             bool pure2 = (e0 + e1 + e2 == 2) && (e0 == 2 || e1 == 2 || e2 == 2);
             G[(n + al) * P + s] = pure2 ? 2.0 : 0.0;
         }
-        __syncwarp();
+        team_sync<TW>();
+        // scale of the assembled matrix for the relative pivot test
+        double gmax = 0.0;
+        for (int e = tid; e < s * s; e += T) {
+            int i = e / s, j = e - i * s;
+            gmax = fmax(gmax, fabs(G[i * P + j]));
+        }
+        gmax = team_max<TW>(gmax, redv);
+        const double tiny = __dmul_rn(1e-13, gmax);
 
         // elimination with partial pivoting
         int bad = 0;
         for (int k = 0; k < s; ++k) {
-            // pivot: the first row of largest |a_ik| (NaN entries below the
-            // diagonal never win; a NaN on the diagonal makes the row singular)
+            // pivot: the first row of largest |a_ik| (NaN entries never win;
+            // a NaN on the diagonal leaves no usable pivot)
             const bool diag_nan = isnan(G[k * P + k]);
             double bv = -1.0;
             int bi = s;
-            for (int i = k + lane; i < s; i += 32) {
+            for (int i = k + tid; i < s; i += T) {
                 double v = fabs(G[i * P + k]);
                 if (v != v) v = -1.0;
                 if (v > bv) {
@@ -134,45 +218,38 @@ __global__ void weights_kernel(WeightArgs A, int warps_per_block) {
                     bi = i;
                 }
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-                int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (ov > bv || (ov == bv && oi < bi)) {
-                    bv = ov;
-                    bi = oi;
-                }
-            }
-            if (diag_nan || !(bv > 1e-300) || isinf(bv)) {
+            team_argmax<TW>(bv, bi, redv, redi);
+            if (diag_nan || !(bv > tiny) || !(bv > 1e-300) || isinf(bv)) {
                 bad = 1;
                 break;
             }
             if (bi != k)
-                for (int j = k + lane; j <= s; j += 32) {
+                for (int j = k + tid; j <= s; j += T) {
                     double t = G[k * P + j];
                     G[k * P + j] = G[bi * P + j];
                     G[bi * P + j] = t;
                 }
-            __syncwarp();
-            const double piv = G[k * P + k];
-            for (int i = k + 1 + lane; i < s; i += 32) G[i * P + k] = __ddiv_rn(G[i * P + k], piv);
-            __syncwarp();
-            // trailing update, pivot row in registers
-            double pr[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                int j = k + 1 + lane + 32 * q;
-                pr[q] = j <= s ? G[k * P + j] : 0.0;
-            }
-            for (int i = k + 1; i < s; ++i) {
-                const double l = G[i * P + k];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    int j = k + 1 + lane + 32 * q;
-                    if (j <= s) G[i * P + j] = __fma_rn(-l, pr[q], G[i * P + j]);
+            team_sync<TW>();
+            const double rp = __drcp_rn(G[k * P + k]);
+            for (int i = k + 1 + tid; i < s; i += T) G[i * P + k] = __dmul_rn(G[i * P + k], rp);
+            team_sync<TW>();
+            // trailing update over (row, column) pairs: rows k+1..s-1,
+            // columns k+1..s (the right-hand side included)
+            const int cols = s - k;
+            const int total = (s - k - 1) * cols;
+            const int di = T / cols, dj = T - di * cols;
+            int ii = tid / cols, jj = tid - ii * cols;
+            for (int e = tid; e < total; e += T) {
+                const int i = k + 1 + ii, j = k + 1 + jj;
+                G[i * P + j] = __fma_rn(-G[i * P + k], G[k * P + j], G[i * P + j]);
+                ii += di;
+                jj += dj;
+                if (jj >= cols) {
+                    jj -= cols;
+                    ++ii;
                 }
             }
-            __syncwarp();
+            team_sync<TW>();
         }
         if (!bad) {
             // back substitution by columns; x_j overwrites the rhs entry of row j
@@ -182,17 +259,17 @@ __global__ void weights_kernel(WeightArgs A, int warps_per_block) {
                     bad = 1;
                     break;
                 }
-                __syncwarp();
-                for (int i = lane; i < j; i += 32)
+                team_sync<TW>();
+                for (int i = tid; i < j; i += T)
                     G[i * P + s] = __fma_rn(-G[i * P + j], xj, G[i * P + s]);
-                if (lane == 0) G[j * P + s] = xj;
-                __syncwarp();
+                if (tid == 0) G[j * P + s] = xj;
+                team_sync<TW>();
             }
         }
         const double sig2 = __dmul_rn(sig, sig);
-        for (int j = lane; j < n; j += 32) A.w[r * n + j] = bad ? 0.0 : __ddiv_rn(G[j * P + s], sig2);
-        if (lane == 0) A.status[r] = (int8_t)bad;
-        __syncwarp();
+        for (int j = tid; j < n; j += T) A.w[r * n + j] = bad ? 0.0 : __ddiv_rn(G[j * P + s], sig2);
+        if (tid == 0) A.status[r] = (int8_t)bad;
+        team_sync<TW>();
     }
 }
 
@@ -261,19 +338,23 @@ extern "C" int rbffd_weights(const double* xyz, int64_t N, int d, const int32_t*
     A.w = w;
     A.status = status;
     A.lap_phi = (double)(3 * (d + 1));
-    size_t per_warp = sizeof(double) * ((size_t)A.s * A.pitch + 3 * (size_t)n);
-    const size_t smem_cap = 200 * 1024;
-    int wpb = (int)std::min<size_t>(8, smem_cap / per_warp);
-    if (wpb < 1) wpb = 1;
-    size_t smem = per_warp * wpb;
-    RBFFD_CHECK_CUDA(cudaFuncSetAttribute(weights_kernel,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t per_team = sizeof(double) * ((size_t)A.s * A.pitch + 3 * (size_t)n);
+    const int sms = device_sm_count();
+    const bool big = A.s > 48;
+    // small systems: one warp per system, several per block; large: four warps
+    int tpb = big ? 1 : (int)std::min<size_t>(8, (200 * 1024) / per_team);
+    if (tpb < 1) tpb = 1;
+    const size_t smem = per_team * tpb;
+    const int threads = big ? 128 : 32 * tpb;
+    auto kern = big ? weights_kernel<4> : weights_kernel<1>;
+    RBFFD_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)std::max<size_t>(smem, 48 * 1024)));
-    int sms = device_sm_count();
-    int per_sm = std::max(1, (int)(220 * 1024 / smem));
-    int64_t want = (nc + wpb - 1) / wpb;
-    int64_t grid = std::min<int64_t>(want, (int64_t)sms * per_sm * 4);
-    weights_kernel<<<(unsigned)grid, 32 * wpb, smem, s>>>(A, wpb);
+    int per_sm = 0;
+    RBFFD_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+    per_sm = std::max(per_sm, 1);
+    int64_t want = (nc + tpb - 1) / tpb;
+    int64_t grid = std::min<int64_t>(want, (int64_t)sms * per_sm);
+    kern<<<(unsigned)grid, threads, smem, s>>>(A, tpb);
     RBFFD_CHECK_CUDA(cudaGetLastError());
     Scratch cnt;
     RBFFD_CHECK_CUDA(cnt.alloc(2 * sizeof(unsigned long long), s));

@@ -226,6 +226,32 @@ def run_reference(args):
         dist.destroy_process_group()
 
 
+def run_stage(args):
+    """One stage of the path on the workload, for profiler captures."""
+    import torch
+    import paper_2502_12878_gb300 as rb
+    from paper_2502_12878_gb300 import build as nvbuild
+    nvbuild.build()
+    dev = torch.device("cuda:0")
+    n = gen.stencil_size(D, args.m)
+    xyz, bnd = rb.rbffd_nodes(D, 0, args.Kg, 0.3, SEED, device=dev)
+    inter = rb.rbffd_interior(bnd)
+    idx = rb.rbffd_knn(xyz, inter, n)
+    if args.mode == "knn":
+        torch.cuda.synchronize()
+        return
+    w, st = rb.rbffd_weights(xyz, idx, args.m)
+    if args.mode == "weights":
+        torch.cuda.synchronize()
+        return
+    plan = rb.Plan(xyz, bnd, inter, idx, w, rb.RBFFD_ORDER_MORTON)
+    f = torch.zeros(inter.numel(), dtype=torch.float64, device=dev)
+    u = torch.zeros(xyz.shape[1], dtype=torch.float64, device=dev)
+    plan.solve_explicit(f, u, 1e-8, args.sweeps, 0.0)
+    torch.cuda.synchronize()
+    plan.destroy()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -234,9 +260,17 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--mode", default="bench", choices=["bench", "sweep", "weights", "knn"],
+                    help="sweep/weights/knn: build the workload and run only that stage "
+                         "(driver for profiler captures; prints nothing else)")
+    ap.add_argument("--m", type=int, default=M, help="monomial order of the workload")
+    ap.add_argument("--Kg", type=int, default=KG, help="grid cells per side of the workload")
+    ap.add_argument("--sweeps", type=int, default=5, help="sweeps in --mode sweep")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode != "bench":
+        return run_stage(args)
     args.warmup = max(args.warmup, 3)
 
     import torch

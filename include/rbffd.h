@@ -109,6 +109,31 @@ RBFFD_API int rbffd_knn(const double* xyz, int64_t N, int d, const int32_t* cent
               int32_t* idx, void* stream);
 
 /*
+ * rbffd_knn_noalloc - rbffd_knn for callers that cannot allocate device
+ * memory while they run (the paper has no counterpart): for example an
+ * application that reserves all of a GPU's memory up front in its own pool
+ * and forbids allocation afterwards, or a latency-bound loop where an
+ * allocation's cost or possible failure is not acceptable.  Same arguments
+ * and the same result, bit for bit, as rbffd_knn.
+ *   Working memory: one fixed array of about 6 MB in the library's device
+ *   image, held on every GPU that loads the library until the process exits.
+ *   It never calls cudaMalloc, cudaMallocAsync, cudaFree or any allocating
+ *   library routine; memsets, copies and kernels go on `stream`, and the call
+ *   synchronises `stream` (host copies of the bounding box and of an error
+ *   flag).
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress, once per device, with that device current); make
+ *   that first call before any stream capture.
+ *   N <= RBFFD_KNN_NOALLOC_MAX_NODES, else RBFFD_ERR_CAPACITY (nothing
+ *   enqueued).  All calls share the one array: calls that overlap on the GPU
+ *   (other streams, other host threads) race and must be serialised by the
+ *   caller.  Each call clears the parts that must start at zero.
+ */
+#define RBFFD_KNN_NOALLOC_MAX_NODES 262144
+RBFFD_API int rbffd_knn_noalloc(const double* xyz, int64_t N, int d, const int32_t* centres,
+                                int64_t nc, int n, int32_t* idx, void* stream);
+
+/*
  * rbffd_weights - RBF-FD weights of the Laplacian (Eq. 2-3), phi(r) = r^3
  * with all monomials of degree <= m (M = C(m+d, d) of them; Sec. II).
  *   idx [nc][n] supports (first entry = centre, as rbffd_knn returns them)

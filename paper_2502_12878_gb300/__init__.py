@@ -46,8 +46,9 @@ EXPORTED = [
     "rbffd_last_error", "rbffd_version", "rbffd_nodes", "rbffd_interior", "rbffd_knn",
     "rbffd_weights", "rbffd_apply", "rbffd_plan_create", "rbffd_plan_destroy", "rbffd_plan_perm",
     "rbffd_solve_explicit", "rbffd_solve_dc", "rbffd_plan_set_dc", "rbffd_stable_dt",
-    "rbffd_adjoint", "rbffd_plan_stats",
+    "rbffd_adjoint", "rbffd_plan_stats", "rbffd_knn_noalloc",
 ]
+RBFFD_KNN_NOALLOC_MAX_NODES = 262144
 
 
 class RbffdError(RuntimeError):
@@ -90,6 +91,7 @@ def lib():
         "rbffd_stable_dt": (I, [P, P, I, D, PD, PD, P]),
         "rbffd_adjoint": (I, [P, P, I64, D, P, P, P, P]),
         "rbffd_plan_stats": (I, [P, PD, PI64, PI64, P]),
+        "rbffd_knn_noalloc": (I, [P, I64, I, P, I64, I, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -157,6 +159,22 @@ def rbffd_knn(xyz: torch.Tensor, centres: torch.Tensor, n: int) -> torch.Tensor:
     idx = torch.empty((centres.numel(), n), dtype=torch.int32, device=xyz.device)
     _check(lib().rbffd_knn(_ptr(xyz), N, d, _ptr(centres), centres.numel(), n, _ptr(idx),
                            _stream(xyz.device)))
+    return idx
+
+
+def rbffd_knn_noalloc(xyz: torch.Tensor, centres: torch.Tensor, idx: torch.Tensor) -> torch.Tensor:
+    """rbffd_knn into a caller-provided ``idx`` [nc, n], with no device allocation.
+
+    For callers that cannot allocate GPU memory while running: the library works in
+    a fixed array of its own (N <= RBFFD_KNN_NOALLOC_MAX_NODES).  Calls that overlap
+    on the GPU share that array and race; serialise them."""
+    xyz = _dev(xyz, torch.float64, "xyz")
+    centres = _dev(centres, torch.int32, "centres")
+    if not (idx.is_cuda and idx.dtype == torch.int32 and idx.is_contiguous()):
+        raise ValueError("idx must be a contiguous int32 CUDA tensor [nc, n]")
+    d, N = xyz.shape
+    _check(lib().rbffd_knn_noalloc(_ptr(xyz), N, d, _ptr(centres), centres.numel(), idx.shape[1],
+                                   _ptr(idx), _stream(xyz.device)))
     return idx
 
 

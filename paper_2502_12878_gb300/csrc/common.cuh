@@ -98,4 +98,11 @@ int build_cell_lists(const double* xyz, int64_t N, const GridGeom& g, int32_t* c
 int counting_sort_by_key(const int32_t* key, int64_t N, int64_t nkeys, int32_t* start,
                          int32_t* sorted, cudaStream_t s);
 
+// kernels of common.cu that other translation units launch directly
+__global__ void bbox_partial(const double* xyz, int64_t N, int d, double* part);
+__global__ void cells_key(const double* xyz, int64_t N, GridGeom g, int32_t* key);
+__global__ void keys_count(const int32_t* key, int64_t N, int32_t* count);
+__global__ void cells_scatter(int64_t N, const int32_t* cellof, int32_t* cursor, int32_t* sorted);
+__global__ void cells_sort(int64_t ncell, const int32_t* start, int32_t* sorted);
+
 }  // namespace rbffd

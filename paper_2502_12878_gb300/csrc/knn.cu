@@ -13,6 +13,8 @@
 // and the result is bit-identical to any exact implementation.
 #include <math.h>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace rbffd {
@@ -282,3 +284,152 @@ extern "C" int rbffd_knn(const double* xyz, int64_t N, int d, const int32_t* cen
     }
     return RBFFD_OK;
 }
+
+// ---------------------------------------------------------------------------
+// rbffd_knn_noalloc: the same support selection for callers that cannot
+// allocate device memory while they run.  Its working memory is one
+// file-scope __device__ array of fixed size (every GPU that loads the library
+// holds it until the process exits), reached from host code through the
+// address that cudaGetSymbolAddress returns for the current device.
+// ---------------------------------------------------------------------------
+namespace rbffd {
+
+static constexpr int64_t NA_MAX_NODES = RBFFD_KNN_NOALLOC_MAX_NODES;
+static constexpr int64_t NA_MAX_CELLS = 2 * NA_MAX_NODES;
+static constexpr size_t na_round(size_t b) { return (b + 255) / 256 * 256; }
+static constexpr int NA_BBOX_BLOCKS = 256;
+// byte offsets of the regions inside the scratch array (each 256-aligned)
+static constexpr size_t NA_OFF_PART = 0;                                       // bbox partials
+static constexpr size_t NA_OFF_ERR = NA_OFF_PART + na_round(sizeof(double) * 6 * NA_BBOX_BLOCKS);
+static constexpr size_t NA_OFF_START = NA_OFF_ERR + 256;                         // cell starts
+static constexpr size_t NA_OFF_COUNT = NA_OFF_START + na_round(4 * (NA_MAX_CELLS + 1));
+static constexpr size_t NA_OFF_TMP = NA_OFF_COUNT + na_round(4 * (NA_MAX_CELLS + 1));
+static constexpr int64_t NA_TMP_ELEMS = (NA_MAX_CELLS + 2047) / 2048 + 1;      // scan tiles
+static constexpr size_t NA_OFF_KEY = NA_OFF_TMP + na_round(8 * NA_TMP_ELEMS);
+static constexpr size_t NA_OFF_SORTED = NA_OFF_KEY + na_round(4 * NA_MAX_NODES);
+static constexpr size_t NA_BYTES = NA_OFF_SORTED + na_round(4 * NA_MAX_NODES);
+
+static __device__ __align__(256) unsigned char g_knn_noalloc_scratch[NA_BYTES];
+
+// device address of the scratch array for the current device, looked up once
+// per device (host code may not use the array's name as a device pointer)
+static int noalloc_scratch(unsigned char** out) {
+    static std::mutex mu;
+    static void* addr[128] = {};
+    int dev = 0;
+    RBFFD_CHECK_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 128) {
+        set_error("rbffd_knn_noalloc: device ordinal %d out of range", dev);
+        return RBFFD_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_knn_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            set_error("rbffd_knn_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+            return RBFFD_ERR_CUDA;
+        }
+        addr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(addr[dev]);
+    return RBFFD_OK;
+}
+
+}  // namespace rbffd
+
+extern "C" int rbffd_knn_noalloc(const double* xyz, int64_t N, int d, const int32_t* centres,
+                                 int64_t nc, int n, int32_t* idx, void* stream) {
+    clear_error();
+    RBFFD_ARG(nc >= 0, "rbffd_knn_noalloc: negative centre count");
+    RBFFD_ARG(d >= 1 && d <= 3, "rbffd_knn_noalloc: d must be 1, 2 or 3");
+    RBFFD_ARG(N >= 1, "rbffd_knn_noalloc: bad N");
+    if (N > NA_MAX_NODES) {
+        set_error("rbffd_knn_noalloc: %lld nodes exceed the fixed scratch limit of %lld "
+                  "(use rbffd_knn)", (long long)N, (long long)NA_MAX_NODES);
+        return RBFFD_ERR_CAPACITY;
+    }
+    RBFFD_ARG(n >= 1 && n <= KNN_NMAX && n <= N, "rbffd_knn_noalloc: need 1 <= n <= min(N, %d)",
+              KNN_NMAX);
+    if (nc == 0) return RBFFD_OK;
+    RBFFD_ARG(xyz && centres && idx, "rbffd_knn_noalloc: NULL argument");
+    cudaStream_t s = as_stream(stream);
+    unsigned char* base = nullptr;
+    int st = noalloc_scratch(&base);
+    if (st) return st;
+    double* part = reinterpret_cast<double*>(base + NA_OFF_PART);
+    int* err = reinterpret_cast<int*>(base + NA_OFF_ERR);
+    int32_t* start = reinterpret_cast<int32_t*>(base + NA_OFF_START);
+    int32_t* count = reinterpret_cast<int32_t*>(base + NA_OFF_COUNT);
+    int64_t* tmp = reinterpret_cast<int64_t*>(base + NA_OFF_TMP);
+    int32_t* key = reinterpret_cast<int32_t*>(base + NA_OFF_KEY);
+    int32_t* sorted = reinterpret_cast<int32_t*>(base + NA_OFF_SORTED);
+
+    // bounding box (partials in the scratch array, final reduction on the host)
+    double hpart[NA_BBOX_BLOCKS * 6];
+    bbox_partial<<<NA_BBOX_BLOCKS, 256, 0, s>>>(xyz, N, d, part);
+    RBFFD_CHECK_CUDA(cudaGetLastError());
+    RBFFD_CHECK_CUDA(cudaMemcpyAsync(hpart, part, sizeof(hpart), cudaMemcpyDeviceToHost, s));
+    RBFFD_CHECK_CUDA(cudaStreamSynchronize(s));
+    double lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = INFINITY;
+        hi[a] = -INFINITY;
+        for (int b = 0; b < NA_BBOX_BLOCKS; ++b) {
+            lo[a] = fmin(lo[a], hpart[b * 6 + a]);
+            hi[a] = fmax(hi[a], hpart[b * 6 + 3 + a]);
+        }
+        if (a >= d) lo[a] = hi[a] = 0.0;
+    }
+    for (int a = 0; a < d; ++a)
+        RBFFD_ARG(isfinite(lo[a]) && isfinite(hi[a]), "rbffd_knn_noalloc: coordinates not finite");
+    // cell grid of about one node per cell, coarsened to fit the fixed cell arrays
+    GridGeom g = make_grid(d, lo, hi, N, 1.0);
+    while (g.ncell() > NA_MAX_CELLS) {
+        g.cs *= 1.25;
+        for (int a = 0; a < d; ++a) g.G[a] = (int)floor((hi[a] - lo[a]) / g.cs) + 1;
+    }
+    const int64_t ncell = g.ncell();
+    const int sms = device_sm_count();
+    // the scratch keeps the previous call's contents: clear what must start at 0
+    RBFFD_CHECK_CUDA(cudaMemsetAsync(count, 0, sizeof(int32_t) * (ncell + 1), s));
+    RBFFD_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    cells_key<<<sms * 8, 256, 0, s>>>(xyz, N, g, key);
+    keys_count<<<sms * 8, 256, 0, s>>>(key, N, count);
+    RBFFD_CHECK_CUDA(cudaGetLastError());
+    RBFFD_CHECK_CUDA(exclusive_scan_i32(count, start, ncell, tmp, s));
+    RBFFD_CHECK_CUDA(cudaMemcpyAsync(count, start, sizeof(int32_t) * ncell,
+                                     cudaMemcpyDeviceToDevice, s));
+    cells_scatter<<<sms * 8, 256, 0, s>>>(N, key, count, sorted);
+    cells_sort<<<sms * 8, 256, 0, s>>>(ncell, start, sorted);
+    RBFFD_CHECK_CUDA(cudaGetLastError());
+    double per_cell = (double)N / (double)ncell;
+    const double ball[4] = {0, 2.0, M_PI, 4.0 * M_PI / 3.0};
+    double rad = pow((double)n / (ball[d] * per_cell), 1.0 / d);
+    KnnArgs A;
+    A.xyz = xyz;
+    A.N = N;
+    A.d = d;
+    A.centres = centres;
+    A.nc = nc;
+    A.n = n;
+    A.idx = idx;
+    A.g = g;
+    A.cell_start = start;
+    A.sorted = sorted;
+    A.r0 = (int)ceil(rad) > 1 ? (int)ceil(rad) : 1;
+    A.err = err;
+    int64_t blocks = (nc + KNN_WARPS - 1) / KNN_WARPS;
+    int64_t cap = (int64_t)sms * 64;
+    knn_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 32 * KNN_WARPS, 0, s>>>(A);
+    RBFFD_CHECK_CUDA(cudaGetLastError());
+    int herr = 0;
+    RBFFD_CHECK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    RBFFD_CHECK_CUDA(cudaStreamSynchronize(s));
+    if (herr) {
+        set_error("rbffd_knn_noalloc: ring search did not terminate");
+        return RBFFD_ERR_CAPACITY;
+    }
+    return RBFFD_OK;
+}
+

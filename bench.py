@@ -55,6 +55,24 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def _traffic():
+    """ncu DRAM bytes per launch of the FP64 sweep, if captured for the current kernel source."""
+    import hashlib
+    try:
+        rec = {}
+        for line in open(os.path.join(ROOT, "profiles", "sweep64_traffic.txt")):
+            if "=" in line and not line.startswith("#"):
+                k, v = line.split("=", 1)
+                rec[k.strip()] = v.strip()
+        src = os.path.join(ROOT, "paper_2502_12878_gb300", "csrc", "sweep.cu")
+        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+        if rec.get("kernel_source_sha1") == sha:
+            return int(rec["traffic_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
 def _dist():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -255,7 +273,7 @@ def run_stage(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -328,7 +346,7 @@ def main():
     alg_bytes = NI * (12 * n + 24)
     achieved = alg_bytes / per_launch_s / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-            "frac": round(achieved / hbm, 4), "traffic": None,
+            "frac": round(achieved / hbm, 4), "traffic": _traffic(),
             "kernel": f"step_kernel<{n},0> (FP64 sweep)", "peak_kind": peak_kind,
             "alg_bytes_per_launch": alg_bytes, "launch_us": round(per_launch_s * 1e6, 2),
             "fp64_pipe_frac": round(NI * (n + 2) / per_launch_s / 6.28e11, 4)}

@@ -230,6 +230,44 @@ RBFFD_API int rbffd_solve_dc(rbffd_plan* plan, const double* f, double* u, doubl
 RBFFD_API int rbffd_plan_set_dc(rbffd_plan* plan, int64_t K_in, double rho_in);
 
 /*
+ * Batched solves: many independent domains (uneven node counts and stencil
+ * sizes, e.g. squares and disks of 5e3..2e5 nodes with m in {2,4,6}) run
+ * Eq. 6 in ONE persistent launch, replayed from a CUDA graph (batching is
+ * not in the paper).  Each domain keeps its own plan; every block of the
+ * persistent grid belongs to one domain's team, team sizes proportional to
+ * the domains' bytes per step; each domain stops on its own (tolerance, step
+ * cap, non-finite, divergence).  Domains run concurrently, so the launch
+ * overhead of small domains is paid once.
+ *
+ * rbffd_batch_create - batch over `ndom` plans (they must outlive the batch
+ *   and must not be solved separately while a batched solve runs).
+ *   blocks_per_sm: blocks of the persistent grid per SM (0: 2); the grid is
+ *   max(SMs x blocks_per_sm, ndom) and must fit on the device at once
+ *   (else RBFFD_ERR_CAPACITY).
+ * rbffd_solve_batch - one batched solve.  f[i] (device, [NI_i], the order of
+ *   plan i's interior list) and u[i] (device, [N_i], in/out, Dirichlet data
+ *   on boundary nodes) are host arrays of device pointers; dt, max_steps and
+ *   tol are host arrays [ndom].  Per domain (host outputs, may be NULL):
+ *   steps taken, last residual max-norm, status (RBFFD_OK, RBFFD_NOT_CONVERGED
+ *   or an error).  Returns the most severe per-domain status.
+ * rbffd_batch_set_shape - register budget (min resident blocks per SM, 1..3)
+ *   and blocks per SM of the persistent grid (re-captures the graph); the
+ *   binding's autotuner times candidates through it.
+ * rbffd_batch_stats - GPU ms of the last batched solve (events around the
+ *   graph launch) and the shape {minb, blocks_per_sm, grid, cooperative}.
+ */
+typedef struct rbffd_batch rbffd_batch;
+RBFFD_API int rbffd_batch_create(rbffd_plan* const* plans, int ndom, int blocks_per_sm,
+                                 rbffd_batch** batch, void* stream);
+RBFFD_API int rbffd_batch_destroy(rbffd_batch* batch);
+RBFFD_API int rbffd_solve_batch(rbffd_batch* batch, const double* const* f, double* const* u,
+                                const double* dt, const int64_t* max_steps, const double* tol,
+                                int64_t* h_steps, double* h_res, int* h_status, void* stream);
+RBFFD_API int rbffd_batch_set_shape(rbffd_batch* batch, int minb, int blocks_per_sm,
+                                    void* stream);
+RBFFD_API int rbffd_batch_stats(const rbffd_batch* batch, double* h_ms, int* h_shape);
+
+/*
  * rbffd_stable_dt - stability bound of the explicit step for this operator.
  * Eq. 7 (cfl) bounds dt by h^2/(2d) for regular nodes only; here the bound is
  * 2 / (safety * rho), rho the spectral radius of the interior block W_II

@@ -46,7 +46,8 @@ EXPORTED = [
     "rbffd_last_error", "rbffd_version", "rbffd_nodes", "rbffd_interior", "rbffd_knn",
     "rbffd_weights", "rbffd_apply", "rbffd_plan_create", "rbffd_plan_destroy", "rbffd_plan_perm",
     "rbffd_solve_explicit", "rbffd_solve_dc", "rbffd_plan_set_dc", "rbffd_stable_dt",
-    "rbffd_adjoint", "rbffd_plan_stats", "rbffd_knn_noalloc",
+    "rbffd_adjoint", "rbffd_plan_stats", "rbffd_knn_noalloc", "rbffd_batch_create",
+    "rbffd_batch_destroy", "rbffd_solve_batch", "rbffd_batch_set_shape", "rbffd_batch_stats",
 ]
 RBFFD_KNN_NOALLOC_MAX_NODES = 262144
 
@@ -92,6 +93,11 @@ def lib():
         "rbffd_adjoint": (I, [P, P, I64, D, P, P, P, P]),
         "rbffd_plan_stats": (I, [P, PD, PI64, PI64, P]),
         "rbffd_knn_noalloc": (I, [P, I64, I, P, I64, I, P, P]),
+        "rbffd_batch_create": (I, [P, I, I, ctypes.POINTER(ctypes.c_void_p), P]),
+        "rbffd_batch_destroy": (I, [P]),
+        "rbffd_solve_batch": (I, [P, P, P, P, P, P, P, P, P, P]),
+        "rbffd_batch_set_shape": (I, [P, I, I, P]),
+        "rbffd_batch_stats": (I, [P, PD, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -305,6 +311,101 @@ class Plan:
         _check(lib().rbffd_adjoint(self.handle, _ptr(lamK), int(K), float(dt), _ptr(gf), _ptr(gg),
                                    _ptr(l0), _stream(self.device)))
         return gf, gg, l0
+
+
+class Batch:
+    """Independent domains solved together in one persistent launch (rbffd_batch_*).
+
+    ``plans`` must stay alive (and unused elsewhere) while the batch exists."""
+
+    def __init__(self, plans, blocks_per_sm=0):
+        self.plans = list(plans)
+        self.ndom = len(self.plans)
+        self.device = self.plans[0].device
+        arr = (ctypes.c_void_p * self.ndom)(*[p.handle.value for p in self.plans])
+        self._h = ctypes.c_void_p(None)
+        _check(lib().rbffd_batch_create(arr, self.ndom, int(blocks_per_sm), ctypes.byref(self._h),
+                                        _stream(self.device)))
+
+    def destroy(self):
+        if self._h is not None and self._h.value:
+            lib().rbffd_batch_destroy(self._h)
+            self._h = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def solve(self, fs, us, dts, max_steps, tols):
+        """Batched Eq. 6 in place on every ``us[i]``.  Returns (code, steps, res, status) lists."""
+        nd = self.ndom
+        for t in list(fs) + list(us):
+            if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+                raise ValueError("f and u must be contiguous float64 CUDA tensors")
+        fa = (ctypes.c_void_p * nd)(*[t.data_ptr() for t in fs])
+        ua = (ctypes.c_void_p * nd)(*[t.data_ptr() for t in us])
+        dta = (ctypes.c_double * nd)(*[float(x) for x in dts])
+        ma = (ctypes.c_int64 * nd)(*[int(x) for x in max_steps])
+        ta = (ctypes.c_double * nd)(*[float(x) for x in tols])
+        steps = (ctypes.c_int64 * nd)()
+        res = (ctypes.c_double * nd)()
+        st = (ctypes.c_int * nd)()
+        code = lib().rbffd_solve_batch(self._h, fa, ua, dta, ma, ta, steps, res, st,
+                                       _stream(self.device))
+        _check(code, (RBFFD_OK, RBFFD_NOT_CONVERGED))
+        return code, list(steps), list(res), list(st)
+
+    def set_shape(self, minb, blocks_per_sm):
+        _check(lib().rbffd_batch_set_shape(self._h, int(minb), int(blocks_per_sm),
+                                           _stream(self.device)))
+
+    def stats(self):
+        ms = ctypes.c_double(0.0)
+        shape = (ctypes.c_int * 4)()
+        _check(lib().rbffd_batch_stats(self._h, ctypes.byref(ms), shape))
+        return ms.value, list(shape)
+
+    def tune(self, fs, us, dts, probe_steps=200, candidates=None, cache=None):
+        """Autotune the launch shape: time a short solve per (minb, blocks/SM) candidate.
+
+        ``us`` are clobbered.  ``cache`` (a JSON path) remembers the choice per device,
+        domain count and total bytes per step."""
+        import json
+        key = None
+        if cache:
+            dev = torch.cuda.get_device_properties(self.device)
+            work = sum(p.NI * (12 * p.n + 24) for p in self.plans)
+            key = f"{dev.name}|{dev.multi_processor_count}|{self.ndom}|{int(math.log2(work + 1))}"
+            try:
+                with open(cache) as fh:
+                    known = json.load(fh)
+                if key in known:
+                    self.set_shape(*known[key])
+                    return tuple(known[key])
+            except (OSError, ValueError):
+                known = {}
+        cands = candidates or [(m, b) for m in (1, 2, 3) for b in (1, 2, 3, 4) if b >= m - 1]
+        best, best_ms = None, float("inf")
+        for (m, b) in cands:
+            try:
+                self.set_shape(m, b)
+            except RbffdError:
+                continue
+            self.solve(fs, us, dts, [probe_steps] * self.ndom, [0.0] * self.ndom)
+            self.solve(fs, us, dts, [probe_steps] * self.ndom, [0.0] * self.ndom)
+            ms, _ = self.stats()
+            if ms < best_ms:
+                best, best_ms = (m, b), ms
+        if best is None:
+            raise RbffdError(RBFFD_ERR_CAPACITY, "no launch shape fits")
+        self.set_shape(*best)
+        if cache and key:
+            known[key] = list(best)
+            with open(cache, "w") as fh:
+                json.dump(known, fh)
+        return best
 
 
 def rbffd_plan_create(xyz, is_bnd, interior, idx, w, flags=0, seed=0) -> Plan:

@@ -1,0 +1,563 @@
+// rbffd_batch_*: many independent domains (uneven node counts and stencil
+// sizes) solved by Eq. 6 in ONE persistent launch, replayed from a CUDA graph.
+//
+// Each domain keeps its own plan (packed stencils, iterates, f).  A device
+// table describes the domains; every block of the persistent grid belongs to
+// one domain's team (team size proportional to the domain's bytes per step,
+// at least one block).  A team sweeps its domain's slices, reduces the step's
+// residual, and decides on its own when the domain stops (tolerance, step cap,
+// non-finite, divergence) - domains finish independently.  One-block teams
+// synchronise with __syncthreads only; larger teams use a per-domain barrier
+// whose waits give up after ~2 s (RBFFD_ERR_TIMEOUT).  Gathers of the iterate
+// go through L2 (.cg) because other blocks of the same launch rewrite it.
+//
+// The per-call inputs (the caller's f / u pointers, dt, tol, step caps) are
+// copied into a device table at a fixed address, so one captured graph -
+// gather of all domains, the persistent kernel, scatter of all domains - is
+// replayed for every call.
+#include <math.h>
+
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "plan.cuh"
+
+namespace rbffd {
+
+static constexpr int BATCH_THREADS = 256;
+static constexpr long long BATCH_SPIN_CYCLES = 4000000000LL;
+
+struct DomDesc {           // static part (from the plan)
+    const double* w64;
+    const int32_t* col;
+    double* fs;            // plan's f in slot order
+    double* u0;            // plan's iterates in slot order
+    double* u1;
+    const int32_t* perm;
+    const int32_t* row_of_slot;
+    int64_t N, NI, nslices;
+    int n, pad;
+};
+
+struct DomCall {           // per-call part
+    const double* f;       // caller's f [NI] (interior-list order)
+    double* u;             // caller's u [N] in/out
+    double dt, tol;
+    long long max_steps;
+};
+
+struct DomState {          // per-domain control, written by the kernel
+    unsigned long long res[3];
+    unsigned int bar_count, bar_gen;
+    long long k;
+    int done, pad;
+    double res_first, res_last;
+};
+
+struct TeamDesc {
+    int dom, rank, size, pad;
+};
+
+}  // namespace rbffd
+
+struct rbffd_batch {
+    int ndom = 0;
+    int grid = 0;
+    int minb = 2;
+    int per_sm = 2;
+    rbffd::DomDesc* d_desc = nullptr;
+    rbffd::DomCall* d_call = nullptr;
+    rbffd::DomState* d_state = nullptr;
+    rbffd::TeamDesc* d_team = nullptr;
+    rbffd::DomCall* h_call = nullptr;     // pinned staging
+    rbffd::DomState* h_state = nullptr;   // pinned read-back
+    std::vector<rbffd::DomDesc> desc;
+    std::vector<double> work;
+    void* graph = nullptr;
+    int coop = 0;                         // graph holds a cooperative kernel node
+    void* ev[2] = {nullptr, nullptr};
+    double last_ms = 0.0;
+};
+
+namespace rbffd {
+
+__device__ __forceinline__ double bld_cg(const double* p) {
+    double v;
+    asm volatile("ld.global.cg.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ double bld_cs(const double* p) {
+    double v;
+    asm volatile("ld.global.cs.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ int32_t bld_cs(const int32_t* p) {
+    int32_t v;
+    asm volatile("ld.global.cs.s32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+template <int NN>
+__device__ __forceinline__ double brow(const double* __restrict__ w, const int32_t* __restrict__ col,
+                                       const double* __restrict__ u, int n) {
+    constexpr int CH = 16;
+    double acc = 0.0;
+    const int nn = NN > 0 ? NN : n;
+#pragma unroll
+    for (int j0 = 0; j0 < (NN > 0 ? NN : 1 << 30); j0 += CH) {
+        if (NN == 0 && j0 >= nn) break;
+        int32_t c[CH];
+        double wv[CH], uv[CH];
+#pragma unroll
+        for (int t = 0; t < CH; ++t)
+            if (j0 + t < nn) c[t] = bld_cs(col + (j0 + t) * SLICE);
+#pragma unroll
+        for (int t = 0; t < CH; ++t)
+            if (j0 + t < nn) wv[t] = bld_cs(w + (j0 + t) * SLICE);
+#pragma unroll
+        for (int t = 0; t < CH; ++t)
+            if (j0 + t < nn) uv[t] = bld_cg(u + c[t]);
+#pragma unroll
+        for (int t = 0; t < CH; ++t)
+            if (j0 + t < nn) acc = __fma_rn(wv[t], uv[t], acc);
+    }
+    return acc;
+}
+
+__device__ __forceinline__ unsigned long long babs_bits(double x) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+    return b > 0x7ff0000000000000ull ? 0x7ff0000000000000ull : b;
+}
+
+// one step of domain D over the slices of this team member; returns max |r| bits
+template <int NN>
+__device__ unsigned long long bstep(const DomDesc& D, int par, double dt, int64_t s0,
+                                    int64_t stride) {
+    const int lane = threadIdx.x & 31;
+    const double* uin = par ? D.u1 : D.u0;
+    double* uout = par ? D.u0 : D.u1;
+    unsigned long long m = 0;
+    for (int64_t sl = s0; sl < D.nslices; sl += stride) {
+        const int64_t row = sl * SLICE + lane;
+        const int64_t base = sl * (int64_t)D.n * SLICE + lane;
+        if (row < D.NI) {
+            double acc = brow<NN>(D.w64 + base, D.col + base, uin, D.n);
+            double r = __dsub_rn(acc, D.fs[row]);
+            uout[row] = __fma_rn(dt, r, uin[row]);
+            m = max(m, babs_bits(r));
+        }
+    }
+    return m;
+}
+
+__device__ unsigned long long bstep_any(const DomDesc& D, int par, double dt, int64_t s0,
+                                        int64_t stride) {
+    switch (D.n) {
+        case 12: return bstep<12>(D, par, dt, s0, stride);
+        case 30: return bstep<30>(D, par, dt, s0, stride);
+        case 56: return bstep<56>(D, par, dt, s0, stride);
+        default: return bstep<0>(D, par, dt, s0, stride);
+    }
+}
+
+// per-domain barrier over the team's blocks; false when a wait gave up
+__device__ bool team_sync_global(DomState* st, int size) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* genp = &st->bar_gen;
+        unsigned g = *genp;
+        int ok = 1;
+        __threadfence();
+        unsigned t = atomicAdd(&st->bar_count, 1u);
+        if (t == (unsigned)size - 1) {
+            atomicExch(&st->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&st->bar_gen, 1u);
+        } else {
+            long long t0 = clock64();
+            while (*genp == g) {
+                if (clock64() - t0 > BATCH_SPIN_CYCLES) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <int MINB>
+__global__ void __launch_bounds__(BATCH_THREADS, MINB)
+    batch_kernel(const DomDesc* __restrict__ desc, const DomCall* __restrict__ call,
+                 DomState* state, const TeamDesc* __restrict__ teams) {
+    __shared__ unsigned long long wmax[BATCH_THREADS / 32];
+    __shared__ int s_stop;
+    const TeamDesc T = teams[blockIdx.x];
+    const DomDesc D = desc[T.dom];
+    const DomCall C = call[T.dom];
+    DomState* st = state + T.dom;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t s0 = (int64_t)T.rank * (BATCH_THREADS / 32) + wid;
+    const int64_t stride = (int64_t)T.size * (BATCH_THREADS / 32);
+    double R0 = 0.0;
+    for (long long k = 0; k < C.max_steps; ++k) {
+        unsigned long long m = bstep_any(D, (int)(k & 1), C.dt, s0, stride);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) wmax[wid] = m;
+        __syncthreads();
+        unsigned long long bm = 0;
+        if (threadIdx.x == 0)
+            for (int w = 0; w < BATCH_THREADS / 32; ++w) bm = max(bm, wmax[w]);
+        double R;
+        if (T.size == 1) {
+            R = __longlong_as_double((long long)bm);
+        } else {
+            if (threadIdx.x == 0) {
+                atomicMax(&st->res[k % 3], bm);
+                if (T.rank == 0) atomicExch(&st->res[(k + 1) % 3], 0ull);
+            }
+            if (!team_sync_global(st, T.size)) {
+                if (threadIdx.x == 0) atomicExch(&st->done, DONE_TIMEOUT);
+                return;
+            }
+            volatile unsigned long long* rp = &st->res[k % 3];
+            R = __longlong_as_double((long long)*rp);
+        }
+        if (threadIdx.x == 0) {
+            if (k == 0) R0 = R;
+            int dn;
+            if (!isfinite(R)) dn = DONE_NONFINITE;
+            else if (R < C.tol) dn = DONE_CONVERGED;
+            else if (k > 0 && R0 > 0.0 && R > 1e6 * R0) dn = DONE_DIVERGED;
+            else if (k + 1 >= C.max_steps) dn = DONE_CAP;
+            else dn = DONE_RUNNING;
+            s_stop = dn;
+            if (T.rank == 0 && dn != DONE_RUNNING) {
+                st->k = k + 1;
+                st->res_first = R0;
+                st->res_last = R;
+                st->done = dn;
+            }
+        }
+        __syncthreads();
+        if (s_stop != DONE_RUNNING) return;
+    }
+}
+
+// gather f and u of every domain into its plan (one launch for all domains)
+__global__ void batch_gather(const DomDesc* desc, const DomCall* call, DomState* state,
+                             int ndom) {
+    for (int dI = blockIdx.y; dI < ndom; dI += gridDim.y) {
+        const DomDesc D = desc[dI];
+        const DomCall C = call[dI];
+        for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < D.N;
+             p += (int64_t)gridDim.x * blockDim.x) {
+            double v = C.u[D.perm[p]];
+            D.u0[p] = v;
+            D.u1[p] = v;
+            if (p < D.NI) D.fs[p] = C.f[D.row_of_slot[p]];
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            DomState& s = state[dI];
+            s.res[0] = s.res[1] = s.res[2] = 0ull;
+            s.bar_count = s.bar_gen = 0u;
+            s.k = 0;
+            s.done = C.max_steps <= 0 ? DONE_CAP : DONE_RUNNING;
+            s.res_first = s.res_last = 0.0;
+        }
+    }
+}
+
+__global__ void batch_scatter(const DomDesc* desc, const DomCall* call, const DomState* state,
+                              int ndom) {
+    for (int dI = blockIdx.y; dI < ndom; dI += gridDim.y) {
+        const DomDesc D = desc[dI];
+        const DomCall C = call[dI];
+        const double* us = (state[dI].k & 1) ? D.u1 : D.u0;
+        for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < D.NI;
+             p += (int64_t)gridDim.x * blockDim.x)
+            C.u[D.perm[p]] = us[p];
+    }
+}
+
+typedef void (*BatchFn)(const DomDesc*, const DomCall*, DomState*, const TeamDesc*);
+
+static BatchFn batch_fn(int minb) {
+    switch (minb) {
+        case 1: return batch_kernel<1>;
+        case 3: return batch_kernel<3>;
+        default: return batch_kernel<2>;
+    }
+}
+
+// teams: blocks per domain proportional to its bytes per step, >= 1 each,
+// summing to exactly `grid` (largest remainders get the leftovers)
+static std::vector<TeamDesc> make_teams(const std::vector<double>& work, int grid) {
+    const int nd = (int)work.size();
+    std::vector<int> b(nd, 1);
+    double tot = std::accumulate(work.begin(), work.end(), 0.0);
+    int left = grid - nd;
+    if (left > 0 && tot > 0) {
+        std::vector<std::pair<double, int>> frac;
+        int used = 0;
+        for (int i = 0; i < nd; ++i) {
+            double share = work[i] / tot * left;
+            int extra = (int)floor(share);
+            b[i] += extra;
+            used += extra;
+            frac.push_back({share - extra, i});
+        }
+        std::sort(frac.begin(), frac.end(), [](auto a, auto c) { return a.first > c.first; });
+        for (int q = 0; q < left - used && q < nd; ++q) b[frac[q].second] += 1;
+    }
+    std::vector<TeamDesc> t;
+    for (int i = 0; i < nd; ++i)
+        for (int r = 0; r < b[i]; ++r) t.push_back({i, r, b[i], 0});
+    return t;
+}
+
+static int batch_capture(rbffd_batch* B, cudaStream_t user) {
+    if (B->graph) {
+        cudaGraphExecDestroy((cudaGraphExec_t)B->graph);
+        B->graph = nullptr;
+    }
+    BatchFn fn = batch_fn(B->minb);
+    std::vector<TeamDesc> teams = make_teams(B->work, B->grid);
+    RBFFD_CHECK_CUDA(cudaMemcpyAsync(B->d_team, teams.data(), sizeof(TeamDesc) * teams.size(),
+                                     cudaMemcpyHostToDevice, user));
+    RBFFD_CHECK_CUDA(cudaStreamSynchronize(user));
+    cudaStream_t cs;
+    RBFFD_CHECK_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t e = cudaErrorUnknown;
+    // first try a cooperative kernel node; if capture refuses it, a plain node
+    // (the grid was checked to fit on the device at once; waits are bounded)
+    for (int coop = 1; coop >= 0 && e != cudaSuccess; --coop) {
+    cudaGraph_t g;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        dim3 gg(64, (unsigned)std::min(B->ndom, 65535));
+        batch_gather<<<gg, 256, 0, cs>>>(B->d_desc, B->d_call, B->d_state, B->ndom);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(B->grid);
+        cfg.blockDim = dim3(BATCH_THREADS);
+        cfg.stream = cs;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = coop;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, fn, (const DomDesc*)B->d_desc, (const DomCall*)B->d_call,
+                               B->d_state, (const TeamDesc*)B->d_team);
+        if (e == cudaSuccess) {
+            batch_scatter<<<gg, 256, 0, cs>>>(B->d_desc, B->d_call, B->d_state, B->ndom);
+            e = cudaStreamEndCapture(cs, &g);
+        } else {
+            cudaGraph_t dummy;
+            cudaStreamEndCapture(cs, &dummy);
+        }
+    }
+    if (e == cudaSuccess) {
+        cudaGraphExec_t ex;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e == cudaSuccess) {
+            B->graph = (void*)ex;
+            B->coop = coop;
+        }
+    }
+    if (e != cudaSuccess) cudaGetLastError();
+    }
+    cudaStreamDestroy(cs);
+    RBFFD_CHECK_CUDA(e);
+    return RBFFD_OK;
+}
+
+static void batch_free(rbffd_batch* B) {
+    if (!B) return;
+    void* dv[] = {B->d_desc, B->d_call, B->d_state, B->d_team};
+    for (void* p : dv)
+        if (p) cudaFree(p);
+    if (B->h_call) cudaFreeHost(B->h_call);
+    if (B->h_state) cudaFreeHost(B->h_state);
+    if (B->graph) cudaGraphExecDestroy((cudaGraphExec_t)B->graph);
+    for (void* e : B->ev)
+        if (e) cudaEventDestroy((cudaEvent_t)e);
+    delete B;
+}
+
+}  // namespace rbffd
+
+using namespace rbffd;
+
+extern "C" int rbffd_batch_create(rbffd_plan* const* plans, int ndom, int blocks_per_sm,
+                                  rbffd_batch** out, void* stream) {
+    clear_error();
+    RBFFD_ARG(plans && out && ndom >= 1, "rbffd_batch_create: bad argument");
+    RBFFD_ARG(blocks_per_sm >= 0 && blocks_per_sm <= 8, "rbffd_batch_create: blocks_per_sm in [0, 8]");
+    for (int i = 0; i < ndom; ++i) RBFFD_ARG(plans[i] != nullptr, "rbffd_batch_create: NULL plan %d", i);
+    *out = nullptr;
+    cudaStream_t s = as_stream(stream);
+    rbffd_batch* B = new rbffd_batch();
+    B->ndom = ndom;
+    for (int i = 0; i < ndom; ++i) {
+        const rbffd_plan* p = plans[i];
+        DomDesc d;
+        d.w64 = p->w64;
+        d.col = p->col;
+        d.fs = p->fs;
+        d.u0 = p->u[0];
+        d.u1 = p->u[1];
+        d.perm = p->perm;
+        d.row_of_slot = p->row_of_slot;
+        d.N = p->N;
+        d.NI = p->NI;
+        d.nslices = p->nslices;
+        d.n = p->n;
+        d.pad = 0;
+        B->desc.push_back(d);
+        B->work.push_back((double)p->NI * (12.0 * p->n + 24.0));
+    }
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc((void**)&B->d_desc, sizeof(DomDesc) * ndom);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&B->d_call, sizeof(DomCall) * ndom);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&B->d_state, sizeof(DomState) * ndom);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&B->h_call, sizeof(DomCall) * ndom);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&B->h_state, sizeof(DomState) * ndom);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        cudaEvent_t ev;
+        e = cudaEventCreate(&ev);
+        if (e == cudaSuccess) B->ev[i] = (void*)ev;
+    }
+    int sms = device_sm_count();
+    if (e == cudaSuccess) e = cudaMalloc((void**)&B->d_team, sizeof(TeamDesc) * (size_t)sms * 8 + sizeof(TeamDesc) * ndom);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(B->d_desc, B->desc.data(), sizeof(DomDesc) * ndom, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(B->d_state, 0, sizeof(DomState) * ndom, s);
+    if (e != cudaSuccess) {
+        set_error("rbffd_batch_create: %s", cudaGetErrorString(e));
+        batch_free(B);
+        return RBFFD_ERR_CUDA;
+    }
+    // launch shape: register budget minb and blocks per SM; blocks_per_sm = 0 -> tune
+    // (the tuner times one short solve per candidate in rbffd_batch_tune)
+    int per_sm_max = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_max, (const void*)batch_fn(2),
+                                                  BATCH_THREADS, 0);
+    B->minb = 2;
+    B->per_sm = blocks_per_sm > 0 ? std::min(blocks_per_sm, std::max(per_sm_max, 1))
+                                  : std::min(2, std::max(per_sm_max, 1));
+    B->grid = std::max(sms * B->per_sm, ndom);
+    int maxres = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxres, (const void*)batch_fn(B->minb),
+                                                  BATCH_THREADS, 0);
+    if (B->grid > maxres * sms) {
+        set_error("rbffd_batch_create: %d domains need %d co-resident blocks, the device holds %d",
+                  ndom, B->grid, maxres * sms);
+        batch_free(B);
+        return RBFFD_ERR_CAPACITY;
+    }
+    int st = batch_capture(B, s);
+    if (st) {
+        batch_free(B);
+        return st;
+    }
+    *out = B;
+    return RBFFD_OK;
+}
+
+extern "C" int rbffd_batch_destroy(rbffd_batch* B) {
+    clear_error();
+    if (!B) return RBFFD_OK;
+    cudaDeviceSynchronize();
+    batch_free(B);
+    return RBFFD_OK;
+}
+
+extern "C" int rbffd_solve_batch(rbffd_batch* B, const double* const* f, double* const* u,
+                                 const double* dt, const int64_t* max_steps, const double* tol,
+                                 int64_t* h_steps, double* h_res, int* h_status, void* stream) {
+    clear_error();
+    RBFFD_ARG(B && f && u && dt && max_steps && tol, "rbffd_solve_batch: NULL argument");
+    cudaStream_t s = as_stream(stream);
+    for (int i = 0; i < B->ndom; ++i) {
+        RBFFD_ARG(f[i] && u[i], "rbffd_solve_batch: NULL f/u of domain %d", i);
+        RBFFD_ARG(dt[i] > 0.0 && isfinite(dt[i]) && tol[i] >= 0.0 && max_steps[i] >= 0,
+                  "rbffd_solve_batch: bad dt / tol / max_steps of domain %d", i);
+        B->h_call[i].f = f[i];
+        B->h_call[i].u = u[i];
+        B->h_call[i].dt = dt[i];
+        B->h_call[i].tol = tol[i];
+        B->h_call[i].max_steps = max_steps[i];
+    }
+    RBFFD_CHECK_CUDA(cudaMemcpyAsync(B->d_call, B->h_call, sizeof(DomCall) * B->ndom,
+                                     cudaMemcpyHostToDevice, s));
+    RBFFD_CHECK_CUDA(cudaEventRecord((cudaEvent_t)B->ev[0], s));
+    RBFFD_CHECK_CUDA(cudaGraphLaunch((cudaGraphExec_t)B->graph, s));
+    RBFFD_CHECK_CUDA(cudaEventRecord((cudaEvent_t)B->ev[1], s));
+    RBFFD_CHECK_CUDA(cudaMemcpyAsync(B->h_state, B->d_state, sizeof(DomState) * B->ndom,
+                                     cudaMemcpyDeviceToHost, s));
+    RBFFD_CHECK_CUDA(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, (cudaEvent_t)B->ev[0], (cudaEvent_t)B->ev[1]);
+    B->last_ms = ms;
+    int worst = RBFFD_OK;
+    for (int i = 0; i < B->ndom; ++i) {
+        const DomState& st = B->h_state[i];
+        int code;
+        switch (st.done) {
+            case DONE_CONVERGED: code = RBFFD_OK; break;
+            case DONE_CAP: code = RBFFD_NOT_CONVERGED; break;
+            case DONE_NONFINITE: code = RBFFD_ERR_NONFINITE; break;
+            case DONE_DIVERGED: code = RBFFD_ERR_DIVERGED; break;
+            case DONE_TIMEOUT: code = RBFFD_ERR_TIMEOUT; break;
+            default: code = RBFFD_ERR_CUDA; break;
+        }
+        if (h_steps) h_steps[i] = st.k;
+        if (h_res) h_res[i] = st.res_last;
+        if (h_status) h_status[i] = code;
+        if (code < 0 && (worst >= 0 || code < worst)) worst = code;
+        if (worst >= 0 && code == RBFFD_NOT_CONVERGED) worst = RBFFD_NOT_CONVERGED;
+    }
+    if (worst < 0) set_error("rbffd_solve_batch: a domain ended with status %d", worst);
+    return worst;
+}
+
+extern "C" int rbffd_batch_set_shape(rbffd_batch* B, int minb, int blocks_per_sm, void* stream) {
+    clear_error();
+    RBFFD_ARG(B && minb >= 1 && minb <= 3 && blocks_per_sm >= 1 && blocks_per_sm <= 8,
+              "rbffd_batch_set_shape: bad argument");
+    int sms = device_sm_count();
+    int maxres = 0;
+    RBFFD_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxres, (const void*)batch_fn(minb),
+                                                                   BATCH_THREADS, 0));
+    int grid = std::max(sms * blocks_per_sm, B->ndom);
+    if (grid > maxres * sms) {
+        set_error("rbffd_batch_set_shape: %d blocks cannot be co-resident (max %d)", grid,
+                  maxres * sms);
+        return RBFFD_ERR_CAPACITY;
+    }
+    B->minb = minb;
+    B->per_sm = blocks_per_sm;
+    B->grid = grid;
+    return batch_capture(B, as_stream(stream));
+}
+
+extern "C" int rbffd_batch_stats(const rbffd_batch* B, double* h_ms, int* h_shape) {
+    clear_error();
+    RBFFD_ARG(B, "rbffd_batch_stats: NULL batch");
+    if (h_ms) *h_ms = B->last_ms;
+    if (h_shape) {
+        h_shape[0] = B->minb;
+        h_shape[1] = B->per_sm;
+        h_shape[2] = B->grid;
+        h_shape[3] = B->coop;
+    }
+    return RBFFD_OK;
+}

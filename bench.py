@@ -244,6 +244,246 @@ def run_reference(args):
         dist.destroy_process_group()
 
 
+def _gpu_problem_from_nodes(rb, torch, xyz, bnd, m, dev, power_iters=200):
+    d = xyz.shape[0]
+    n = gen.stencil_size(d, m)
+    inter = rb.rbffd_interior(bnd)
+    idx = rb.rbffd_knn(xyz, inter, n)
+    w, st = rb.rbffd_weights(xyz, idx, m)
+    plan = rb.Plan(xyz, bnd, inter, idx, w, rb.RBFFD_ORDER_MORTON)
+    xyz_h, bnd_h, inter_h = xyz.cpu().numpy(), bnd.cpu().numpy(), inter.cpu().numpy()
+    f = torch.from_numpy(gen.source(xyz_h, inter_h)).to(dev)
+    u0 = torch.from_numpy(gen.start_iterate(xyz_h, bnd_h)).to(dev)
+    ua = torch.from_numpy(gen.exact_solution(xyz_h)).to(dev)
+    dt, rho = plan.stable_dt(torch.from_numpy(gen.random_vector(len(inter_h), 7)).to(dev),
+                             power_iters, 1.05)
+    return dict(plan=plan, f=f, u0=u0, ua=ua, dt=0.9 * dt, rho=rho, n=n, NI=len(inter_h),
+                N=xyz.shape[1], xyz=xyz, bnd=bnd, inter=inter, idx=idx, w=w)
+
+
+def _line(workload, value, unit, ms_per_step, steps, warmup, extra, higher=True, dtype="f64"):
+    out = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": 1, "steps": steps,
+           "warmup": warmup, "ms_per_step": ms_per_step, "higher_is_better": higher,
+           "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+           "config": {"workload": workload}}
+    out.update(extra)
+    print(json.dumps(out), flush=True)
+
+
+def run_workload(args):
+    """The other workloads of the study, one JSON line each (not the headline)."""
+    import torch
+    import paper_2502_12878_gb300 as rb
+    from paper_2502_12878_gb300 import build as nvbuild
+    nvbuild.build()
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    hbm, peak_kind = _peaks()
+
+    if args.workload == "batched256":
+        t0 = time.perf_counter()
+        P = []
+        for (shape, Kg, m, seed) in gen.batched_domains(256, seed=4):
+            xyz, bnd = rb.rbffd_nodes(2, shape, Kg, 0.3, seed, device=dev)
+            P.append(_gpu_problem_from_nodes(rb, torch, xyz, bnd, m, dev, power_iters=200))
+        setup = time.perf_counter() - t0
+        plans = [q["plan"] for q in P]
+        fs = [q["f"] for q in P]
+        dts = [q["dt"] for q in P]
+        cap, tol = args.batch_cap, 1e-10
+        batch = rb.Batch(plans)
+        us = [q["u0"].clone() for q in P]
+        shape = batch.tune(fs, us, dts, probe_steps=200)
+        nodes = sum(q["N"] for q in P)
+        # batched: one persistent launch per solve
+        us = [q["u0"].clone() for q in P]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        code, steps_b, res_b, st_b = batch.solve(fs, us, dts, [cap] * 256, [tol] * 256)
+        torch.cuda.synchronize()
+        tb = time.perf_counter() - t0
+        upd = sum(q["NI"] * k for q, k in zip(P, steps_b))
+        errs_b = [rb.rbffd_error(u, q["ua"])[0] for u, q in zip(us, P)]
+        t_start, t_end, blk, team = batch.domain_times()
+        dur = [e - b for b, e in zip(t_start, t_end)]
+        # per-block finish times: where the grid waits
+        fin = {}
+        for i, b in enumerate(blk):
+            fin[b] = max(fin.get(b, 0.0), t_end[i])
+        fins = sorted(fin.values())
+        timing = {"domain_ms_min": min(dur), "domain_ms_median": float(np.median(dur)),
+                  "domain_ms_max": max(dur), "block_finish_ms_p10": fins[len(fins) // 10],
+                  "block_finish_ms_median": fins[len(fins) // 2], "block_finish_ms_max": fins[-1],
+                  "slowest_domains": sorted(
+                      [{"N": P[i]["N"], "n": P[i]["n"], "ms": dur[i], "team": team[i]}
+                       for i in range(len(P))], key=lambda r: -r["ms"])[:5]}
+        # one domain at a time (graph-replayed launches per domain)
+        us2 = [q["u0"].clone() for q in P]
+        for q, u in zip(P, us2):          # warm the per-plan graphs and autotuner
+            q["plan"].solve_explicit(q["f"], u.clone(), q["dt"], 64, 0.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        steps_s = []
+        for q, u in zip(P, us2):
+            c, k, r = q["plan"].solve_explicit(q["f"], u, q["dt"], cap, tol)
+            steps_s.append(k)
+        torch.cuda.synchronize()
+        ts = time.perf_counter() - t0
+        same = all(torch.equal(a, b) for a, b in zip(us, us2)) and steps_s == steps_b
+        _line("batched: 256 independent 2D domains (squares and disks), N log-uniform "
+              "[5e3, 2e5], m in {2,4,6}, cap 20,000 steps or max|r| < 1e-10",
+              upd / tb, UNIT, tb * 1e3, 1, 0,
+              {"batched_s": tb, "one_at_a_time_s": ts, "speedup_vs_one_at_a_time": ts / tb,
+               "node_updates": upd, "nodes_total": nodes,
+               "domains_converged": sum(1 for x in st_b if x == 0),
+               "max_error_vs_closed_form": max(errs_b), "identical_to_one_at_a_time": same,
+               "launch_shape": list(shape), "setup_s": setup, "timing": timing})
+        batch.destroy()
+        return
+
+    if args.workload == "cube8M_m4":
+        t = {}
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xyz, bnd = rb.rbffd_nodes(3, 0, 200, 0.3, 3, device=dev)
+        inter = rb.rbffd_interior(bnd)
+        n = gen.stencil_size(3, 4)
+        torch.cuda.synchronize()
+        t["nodes_ms"] = (time.perf_counter() - t0) * 1e3
+        t0 = time.perf_counter()
+        idx = rb.rbffd_knn(xyz, inter, n)
+        torch.cuda.synchronize()
+        t["knn_ms"] = (time.perf_counter() - t0) * 1e3
+        t0 = time.perf_counter()
+        w, st = rb.rbffd_weights(xyz, idx, 4)
+        torch.cuda.synchronize()
+        t["weights_ms"] = (time.perf_counter() - t0) * 1e3
+        NI = inter.numel()
+        s_ = n + gen.num_monomials(3, 4)
+        wflops = NI * s_ ** 3 / 3.0 * 2
+        xyz_h, bnd_h, inter_h = xyz.cpu().numpy(), bnd.cpu().numpy(), inter.cpu().numpy()
+        f = torch.from_numpy(gen.source(xyz_h, inter_h)).to(dev)
+        u0 = torch.from_numpy(gen.start_iterate(xyz_h, bnd_h)).to(dev)
+        res = {}
+        S = 50
+        for order in (rb.RBFFD_ORDER_MORTON, rb.RBFFD_ORDER_RANDOM):
+            plan = rb.Plan(xyz, bnd, inter, idx, w, order, seed=9)
+            if order == rb.RBFFD_ORDER_MORTON:
+                dt, rho = plan.stable_dt(torch.from_numpy(gen.random_vector(NI, 7)).to(dev), 100)
+                dt *= 0.9
+            u = u0.clone()
+            plan.solve_explicit(f, u, dt, 10, 0.0)
+            plan.solve_explicit(f, u, dt, S, 0.0)
+            ms, k, nl, shape = plan.stats()
+            per = ms * 1e-3 / k
+            u2 = u0.clone()
+            plan.solve_dc(f, u2, dt, 0.0, 1, 10, 0.0)
+            plan.solve_dc(f, u2, dt, 0.0, 1, S, 0.0)
+            ms32, k32, _, shape = plan.stats()
+            per32 = ms32 * 1e-3 / k32
+            name = "morton" if order == 0 else "random"
+            res[name] = {"fp64_node_updates_per_s": NI / per,
+                         "fp64_alg_GBps": NI * (12 * n + 24) / per / 1e9,
+                         "fp32_inner_node_updates_per_s": NI / per32,
+                         "fp32_alg_GBps": NI * (8 * n + 12) / per32 / 1e9,
+                         "launch_shape": shape}
+            plan.destroy()
+        v = res["morton"]["fp64_node_updates_per_s"]
+        _line("3D unit cube, 8,120,601 jittered nodes (7,880,599 interior), m=4 (n=70)",
+              v, UNIT, NI / v * 1e3, S, 10,
+              {"orders": res, "setup_ms": t, "weights_fp64_tflops": wflops / t["weights_ms"] / 1e9,
+               "roofline": {"bound": "hbm", "achieved": res["morton"]["fp64_alg_GBps"],
+                            "peak": hbm, "unit": "GB/s",
+                            "frac": res["morton"]["fp64_alg_GBps"] / hbm, "traffic": None}})
+        return
+
+    if args.workload == "adjoint1M_m4":
+        xyz, bnd = rb.rbffd_nodes(2, 0, 1000, 0.3, 5, device=dev)
+        Q = _gpu_problem_from_nodes(rb, torch, xyz, bnd, 4, dev)
+        plan, NI, N, dt = Q["plan"], Q["NI"], Q["N"], Q["dt"]
+        K = 5000
+        sens = torch.from_numpy(gen.sensors(NI, 10000, 5).astype(np.int64)).to(dev)
+        inter = Q["inter"].long()
+        bidx = torch.nonzero(Q["bnd"]).flatten()
+        uobs = Q["ua"][inter[sens]]
+        g = Q["u0"][bidx].clone()
+
+        def loss(f, gb):
+            u = torch.zeros(N, dtype=torch.float64, device=dev)
+            u[bidx] = gb
+            plan.solve_explicit(f, u, dt, K, 0.0)
+            return u, float(((u[inter[sens]] - uobs) ** 2).sum())
+
+        loss(Q["f"], g)                   # warm: autotuner, graph capture
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        uK, L0 = loss(Q["f"], g)
+        torch.cuda.synchronize()
+        tf = time.perf_counter() - t0
+        lamK = torch.zeros(NI, dtype=torch.float64, device=dev)
+        lamK[sens] = 2 * (uK[inter[sens]] - uobs)
+        plan.adjoint(lamK, 10, dt)        # builds the transpose
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gf, gg, _ = plan.adjoint(lamK, K, dt)
+        torch.cuda.synchronize()
+        tb = time.perf_counter() - t0
+        gen_r = np.random.default_rng(5)
+        rel = []
+        for _ in range(20):
+            vf = torch.from_numpy(gen_r.standard_normal(NI)).to(dev)
+            vg = torch.from_numpy(gen_r.standard_normal(len(bidx))).to(dev)
+            eps = 1e-3
+            _, Lp = loss(Q["f"] + eps * vf, g + eps * vg)
+            _, Lm = loss(Q["f"] - eps * vf, g - eps * vg)
+            fd = (Lp - Lm) / (2 * eps)
+            an = float((gf * vf).sum() + (gg[bidx] * vg).sum())
+            rel.append(abs(fd - an) / max(abs(an), 1e-300))
+        _line("adjoint: 2D square 1,002,001 nodes, m=4 (n=30), K=5,000 steps, 10,000 sensors",
+              NI * K / tb, "node-updates/s (reverse sweep)", tb * 1e3, 1, 1,
+              {"forward_s": tf, "backward_s": tb, "loss": L0,
+               "fd_directions": 20, "fd_max_rel_err": max(rel), "fd_median_rel_err": float(np.median(rel))})
+        return
+
+    if args.workload == "tta":
+        out = {}
+        for Kg in (100, 200, 300):
+            xyz, bnd = rb.rbffd_nodes(2, 0, Kg, 0.3, 1, device=dev)
+            Q = _gpu_problem_from_nodes(rb, torch, xyz, bnd, 4, dev)
+            plan = Q["plan"]
+            chunk, target, cap = 1000, 1e-6, 4_000_000
+            row = {}
+            for prec in ("fp64", "fp32_dc"):
+                u = Q["u0"].clone()
+                plan.solve_explicit(Q["f"], u.clone(), Q["dt"], 64, 0.0)   # warm graph/tuner
+                plan.solve_dc(Q["f"], u.clone(), Q["dt"], 0.0, 1, 64, 0.0)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                steps, err = 0, 1.0
+                while steps < cap:
+                    if prec == "fp64":
+                        plan.solve_explicit(Q["f"], u, Q["dt"], chunk, 0.0)
+                    else:
+                        plan.solve_dc(Q["f"], u, Q["dt"], 0.0, 1, chunk, 0.0)
+                    steps += chunk
+                    err, mean = rb.rbffd_error(u, Q["ua"])
+                    if err <= target:
+                        break
+                torch.cuda.synchronize()
+                el = time.perf_counter() - t0
+                row[prec] = {"seconds": el, "steps": steps, "max_err": err, "mean_abs_err": mean,
+                             "reached": err <= target}
+            row["speedup_fp32_dc"] = row["fp64"]["seconds"] / row["fp32_dc"]["seconds"]
+            out[f"Kg{Kg}_N{Q['N']}"] = row
+            plan.destroy()
+        first = out[next(iter(out))]
+        _line("time to max error 1e-6 vs u = sin(pi x) sin(pi y), 2D squares K_g 100/200/300, "
+              "m=4, error checked every 1,000 steps (included)", first["fp64"]["seconds"],
+              "s (K_g=100, FP64)", first["fp64"]["seconds"] * 1e3, 1, 0, {"tta": out},
+              higher=False)
+        return
+
+
 def run_stage(args):
     """One stage of the path on the workload, for profiler captures."""
     import torch
@@ -284,7 +524,13 @@ def main():
     ap.add_argument("--m", type=int, default=M, help="monomial order of the workload")
     ap.add_argument("--Kg", type=int, default=KG, help="grid cells per side of the workload")
     ap.add_argument("--sweeps", type=int, default=5, help="sweeps in --mode sweep")
+    ap.add_argument("--batch-cap", type=int, default=20000, help="step cap per domain (batched256)")
+    ap.add_argument("--workload", default="square1M_m4",
+                    choices=["square1M_m4", "batched256", "cube8M_m4", "adjoint1M_m4", "tta"],
+                    help="square1M_m4 is the headline; the others measure the other workloads")
     args = ap.parse_args()
+    if args.workload != "square1M_m4":
+        return run_workload(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.mode != "bench":

@@ -164,6 +164,15 @@ RBFFD_API int rbffd_apply(const double* w, const int32_t* idx, int64_t nc, int n
                 double* Lu, void* stream);
 
 /*
+ * rbffd_error - quality of a solution against a reference field u^a (both
+ * [N], device): h_max = max_i |u_i - u^a_i| and h_mean = (1/N) sum_i
+ * |u_i - u^a_i|, the error measure of Eq. 8 (N = all nodes of the domain).
+ * Deterministic (fixed two-pass reduction).  Host outputs, may be NULL.
+ */
+RBFFD_API int rbffd_error(const double* u, const double* ua, int64_t N, double* h_max,
+                          double* h_mean, void* stream);
+
+/*
  * rbffd_plan_create - device-resident solver plan for Eq. 6.
  * Reorders the nodes (interior first, then by `flags` order), packs the
  * stencils into 32-row slices (weights and neighbour indices interleaved so a
@@ -266,6 +275,15 @@ RBFFD_API int rbffd_solve_batch(rbffd_batch* batch, const double* const* f, doub
 RBFFD_API int rbffd_batch_set_shape(rbffd_batch* batch, int minb, int blocks_per_sm,
                                     void* stream);
 RBFFD_API int rbffd_batch_stats(const rbffd_batch* batch, double* h_ms, int* h_shape);
+/* relative cost of one step of each domain (host [ndom], > 0), used to size the
+ * domains' teams; the default is the number of memory rounds of its slices
+ * (slices x (ceil(n/16) + 1)).  The binding's autotuner sets measured costs. */
+RBFFD_API int rbffd_batch_set_costs(rbffd_batch* batch, const double* h_cost_per_step);
+/* per domain of the last batched solve (host arrays [ndom], may be NULL): start
+ * and end of its step loop in ms after the earliest start (GPU global timer), the
+ * block that ran its team's rank 0, and its team size in blocks */
+RBFFD_API int rbffd_batch_domain_times(const rbffd_batch* batch, double* h_start_ms,
+                                       double* h_end_ms, int* h_block, int* h_team);
 
 /*
  * rbffd_stable_dt - stability bound of the explicit step for this operator.

@@ -48,6 +48,7 @@ EXPORTED = [
     "rbffd_solve_explicit", "rbffd_solve_dc", "rbffd_plan_set_dc", "rbffd_stable_dt",
     "rbffd_adjoint", "rbffd_plan_stats", "rbffd_knn_noalloc", "rbffd_batch_create",
     "rbffd_batch_destroy", "rbffd_solve_batch", "rbffd_batch_set_shape", "rbffd_batch_stats",
+    "rbffd_error", "rbffd_batch_domain_times", "rbffd_batch_set_costs",
 ]
 RBFFD_KNN_NOALLOC_MAX_NODES = 262144
 
@@ -98,6 +99,9 @@ def lib():
         "rbffd_solve_batch": (I, [P, P, P, P, P, P, P, P, P, P]),
         "rbffd_batch_set_shape": (I, [P, I, I, P]),
         "rbffd_batch_stats": (I, [P, PD, P]),
+        "rbffd_error": (I, [P, P, I64, PD, PD, P]),
+        "rbffd_batch_domain_times": (I, [P, P, P, P, P]),
+        "rbffd_batch_set_costs": (I, [P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -209,6 +213,17 @@ def rbffd_apply(w: torch.Tensor, idx: torch.Tensor, u: torch.Tensor) -> torch.Te
     Lu = torch.empty(rows, dtype=torch.float64, device=u.device)
     _check(lib().rbffd_apply(_ptr(w), _ptr(idx), rows, n, _ptr(u), _ptr(Lu), _stream(u.device)))
     return Lu
+
+
+def rbffd_error(u: torch.Tensor, ua: torch.Tensor):
+    """(max |u - u^a|, mean |u - u^a|) over all nodes (Eq. 8 is the mean)."""
+    u = _dev(u, torch.float64, "u")
+    ua = _dev(ua, torch.float64, "ua")
+    mx = ctypes.c_double(0.0)
+    mean = ctypes.c_double(0.0)
+    _check(lib().rbffd_error(_ptr(u), _ptr(ua), u.numel(), ctypes.byref(mx), ctypes.byref(mean),
+                             _stream(u.device)))
+    return mx.value, mean.value
 
 
 class Plan:
@@ -367,13 +382,36 @@ class Batch:
         _check(lib().rbffd_batch_stats(self._h, ctypes.byref(ms), shape))
         return ms.value, list(shape)
 
-    def tune(self, fs, us, dts, probe_steps=200, candidates=None, cache=None):
-        """Autotune the launch shape: time a short solve per (minb, blocks/SM) candidate.
+    def domain_times(self):
+        """Per domain of the last solve: (start ms, end ms, rank-0 block, team size)."""
+        a = (ctypes.c_double * self.ndom)()
+        b = (ctypes.c_double * self.ndom)()
+        c = (ctypes.c_int * self.ndom)()
+        d = (ctypes.c_int * self.ndom)()
+        _check(lib().rbffd_batch_domain_times(self._h, a, b, c, d))
+        return list(a), list(b), list(c), list(d)
 
-        ``us`` are clobbered.  ``cache`` (a JSON path) remembers the choice per device,
-        domain count and total bytes per step."""
+    def set_costs(self, costs):
+        arr = (ctypes.c_double * self.ndom)(*[float(c) for c in costs])
+        _check(lib().rbffd_batch_set_costs(self._h, arr))
+
+    def calibrate(self, fs, us, dts, probe_steps=200):
+        """Measure each domain's cost of one step (block-ms: its duration in a probe
+        solve x its team size / steps) and give the costs to the library's load
+        balancer for the next solves.  ``us`` are clobbered."""
+        self.solve(fs, us, dts, [probe_steps] * self.ndom, [0.0] * self.ndom)
+        t0, t1, _, team = self.domain_times()
+        costs = [max(e - b, 1e-6) * max(s, 1) / probe_steps for b, e, s in zip(t0, t1, team)]
+        self.set_costs(costs)
+        return costs
+
+    def tune(self, fs, us, dts, probe_steps=200, candidates=None, cache=None):
+        """Autotune the launch shape: time a short solve per (minb, blocks/SM) candidate,
+        then calibrate the per-domain costs at the chosen shape.  ``us`` are clobbered.
+        ``cache`` (a JSON path) remembers the shape per device, domain count and size."""
         import json
         key = None
+        known = {}
         if cache:
             dev = torch.cuda.get_device_properties(self.device)
             work = sum(p.NI * (12 * p.n + 24) for p in self.plans)
@@ -381,30 +419,33 @@ class Batch:
             try:
                 with open(cache) as fh:
                     known = json.load(fh)
-                if key in known:
-                    self.set_shape(*known[key])
-                    return tuple(known[key])
             except (OSError, ValueError):
                 known = {}
-        cands = candidates or [(m, b) for m in (1, 2, 3) for b in (1, 2, 3, 4) if b >= m - 1]
-        best, best_ms = None, float("inf")
-        for (m, b) in cands:
-            try:
-                self.set_shape(m, b)
-            except RbffdError:
-                continue
-            self.solve(fs, us, dts, [probe_steps] * self.ndom, [0.0] * self.ndom)
-            self.solve(fs, us, dts, [probe_steps] * self.ndom, [0.0] * self.ndom)
-            ms, _ = self.stats()
-            if ms < best_ms:
-                best, best_ms = (m, b), ms
-        if best is None:
-            raise RbffdError(RBFFD_ERR_CAPACITY, "no launch shape fits")
-        self.set_shape(*best)
-        if cache and key:
-            known[key] = list(best)
-            with open(cache, "w") as fh:
-                json.dump(known, fh)
+        if key and key in known:
+            best = tuple(known[key])
+            self.set_shape(*best)
+        else:
+            cands = candidates or [(m, b) for m in (1, 2, 3) for b in (1, 2, 3, 4) if b >= m - 1]
+            best, best_ms = None, float("inf")
+            for (m, b) in cands:
+                try:
+                    self.set_shape(m, b)
+                except RbffdError:
+                    continue
+                # costs measured at this shape, then a timed probe with them
+                self.calibrate(fs, us, dts, probe_steps)
+                self.solve(fs, us, dts, [probe_steps] * self.ndom, [0.0] * self.ndom)
+                ms, _ = self.stats()
+                if ms < best_ms:
+                    best, best_ms = (m, b), ms
+            if best is None:
+                raise RbffdError(RBFFD_ERR_CAPACITY, "no launch shape fits")
+            self.set_shape(*best)
+            if cache and key:
+                known[key] = list(best)
+                with open(cache, "w") as fh:
+                    json.dump(known, fh)
+        self.calibrate(fs, us, dts, probe_steps)
         return best
 
 

@@ -2,14 +2,18 @@
 // sizes) solved by Eq. 6 in ONE persistent launch, replayed from a CUDA graph.
 //
 // Each domain keeps its own plan (packed stencils, iterates, f).  A device
-// table describes the domains; every block of the persistent grid belongs to
-// one domain's team (team size proportional to the domain's bytes per step,
-// at least one block).  A team sweeps its domain's slices, reduces the step's
+// table describes the domains.  Load balance (per call, on the host): a
+// domain's work is its bytes per step x its step cap; with target = total
+// work / blocks, a domain of at least the target gets a team of
+// floor(work/target) blocks, and the smaller domains are packed first-fit-
+// decreasing into the remaining blocks, each of which then runs its domains
+// one after another.  A team sweeps its domain's slices, reduces the step's
 // residual, and decides on its own when the domain stops (tolerance, step cap,
-// non-finite, divergence) - domains finish independently.  One-block teams
-// synchronise with __syncthreads only; larger teams use a per-domain barrier
-// whose waits give up after ~2 s (RBFFD_ERR_TIMEOUT).  Gathers of the iterate
-// go through L2 (.cg) because other blocks of the same launch rewrite it.
+// non-finite, divergence).  One-block teams synchronise with __syncthreads
+// and gather the iterate through L1 (their own writes are visible after the
+// barrier); larger teams use a per-domain barrier whose waits give up after
+// ~2 s (RBFFD_ERR_TIMEOUT) and gather through L2 (.cg), because other blocks
+// of the same launch rewrite the iterate.
 //
 // The per-call inputs (the caller's f / u pointers, dt, tol, step caps) are
 // copied into a device table at a fixed address, so one captured graph -
@@ -19,6 +23,8 @@
 
 #include <algorithm>
 #include <numeric>
+#include <string.h>
+
 #include <vector>
 
 #include "plan.cuh"
@@ -53,7 +59,14 @@ struct DomState {          // per-domain control, written by the kernel
     long long k;
     int done, pad;
     double res_first, res_last;
+    unsigned long long t_start, t_end;   // %globaltimer (ns) at the domain's first / last step
 };
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 struct TeamDesc {
     int dom, rank, size, pad;
@@ -69,7 +82,10 @@ struct rbffd_batch {
     rbffd::DomDesc* d_desc = nullptr;
     rbffd::DomCall* d_call = nullptr;
     rbffd::DomState* d_state = nullptr;
-    rbffd::TeamDesc* d_team = nullptr;
+    rbffd::TeamDesc* d_team = nullptr;    // assignments (CSR by block)
+    int* d_first = nullptr;
+    rbffd::TeamDesc* h_team = nullptr;    // pinned staging
+    int* h_first = nullptr;
     rbffd::DomCall* h_call = nullptr;     // pinned staging
     rbffd::DomState* h_state = nullptr;   // pinned read-back
     std::vector<rbffd::DomDesc> desc;
@@ -87,6 +103,11 @@ __device__ __forceinline__ double bld_cg(const double* p) {
     asm volatile("ld.global.cg.f64 %0, [%1];" : "=d"(v) : "l"(p));
     return v;
 }
+__device__ __forceinline__ double bld_ca(const double* p) {
+    double v;
+    asm volatile("ld.global.ca.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
 __device__ __forceinline__ double bld_cs(const double* p) {
     double v;
     asm volatile("ld.global.cs.f64 %0, [%1];" : "=d"(v) : "l"(p));
@@ -98,7 +119,7 @@ __device__ __forceinline__ int32_t bld_cs(const int32_t* p) {
     return v;
 }
 
-template <int NN>
+template <int NN, bool COH>
 __device__ __forceinline__ double brow(const double* __restrict__ w, const int32_t* __restrict__ col,
                                        const double* __restrict__ u, int n) {
     constexpr int CH = 16;
@@ -117,7 +138,7 @@ __device__ __forceinline__ double brow(const double* __restrict__ w, const int32
             if (j0 + t < nn) wv[t] = bld_cs(w + (j0 + t) * SLICE);
 #pragma unroll
         for (int t = 0; t < CH; ++t)
-            if (j0 + t < nn) uv[t] = bld_cg(u + c[t]);
+            if (j0 + t < nn) uv[t] = COH ? bld_cg(u + c[t]) : bld_ca(u + c[t]);
 #pragma unroll
         for (int t = 0; t < CH; ++t)
             if (j0 + t < nn) acc = __fma_rn(wv[t], uv[t], acc);
@@ -131,9 +152,9 @@ __device__ __forceinline__ unsigned long long babs_bits(double x) {
 }
 
 // one step of domain D over the slices of this team member; returns max |r| bits
-template <int NN>
-__device__ unsigned long long bstep(const DomDesc& D, int par, double dt, int64_t s0,
-                                    int64_t stride) {
+template <int NN, bool COH>
+__device__ __noinline__ unsigned long long bstep(const DomDesc& D, int par, double dt, int64_t s0,
+                                                 int64_t stride) {
     const int lane = threadIdx.x & 31;
     const double* uin = par ? D.u1 : D.u0;
     double* uout = par ? D.u0 : D.u1;
@@ -142,22 +163,25 @@ __device__ unsigned long long bstep(const DomDesc& D, int par, double dt, int64_
         const int64_t row = sl * SLICE + lane;
         const int64_t base = sl * (int64_t)D.n * SLICE + lane;
         if (row < D.NI) {
-            double acc = brow<NN>(D.w64 + base, D.col + base, uin, D.n);
-            double r = __dsub_rn(acc, D.fs[row]);
-            uout[row] = __fma_rn(dt, r, uin[row]);
+            const double fi = bld_cs(D.fs + row);
+            const double ui = COH ? bld_cg(uin + row) : bld_ca(uin + row);
+            double acc = brow<NN, COH>(D.w64 + base, D.col + base, uin, D.n);
+            double r = __dsub_rn(acc, fi);
+            uout[row] = __fma_rn(dt, r, ui);
             m = max(m, babs_bits(r));
         }
     }
     return m;
 }
 
+template <bool COH>
 __device__ unsigned long long bstep_any(const DomDesc& D, int par, double dt, int64_t s0,
                                         int64_t stride) {
     switch (D.n) {
-        case 12: return bstep<12>(D, par, dt, s0, stride);
-        case 30: return bstep<30>(D, par, dt, s0, stride);
-        case 56: return bstep<56>(D, par, dt, s0, stride);
-        default: return bstep<0>(D, par, dt, s0, stride);
+        case 12: return bstep<12, COH>(D, par, dt, s0, stride);
+        case 30: return bstep<30, COH>(D, par, dt, s0, stride);
+        case 56: return bstep<56, COH>(D, par, dt, s0, stride);
+        default: return bstep<0, COH>(D, par, dt, s0, stride);
     }
 }
 
@@ -192,13 +216,11 @@ __device__ bool team_sync_global(DomState* st, int size) {
     return s_ok != 0;
 }
 
-template <int MINB>
-__global__ void __launch_bounds__(BATCH_THREADS, MINB)
-    batch_kernel(const DomDesc* __restrict__ desc, const DomCall* __restrict__ call,
-                 DomState* state, const TeamDesc* __restrict__ teams) {
-    __shared__ unsigned long long wmax[BATCH_THREADS / 32];
-    __shared__ int s_stop;
-    const TeamDesc T = teams[blockIdx.x];
+// one domain's solve by one team member (rank of size blocks); returns false
+// when a team wait gave up
+__device__ bool run_domain(const TeamDesc T, const DomDesc* __restrict__ desc,
+                           const DomCall* __restrict__ call, DomState* state,
+                           unsigned long long* wmax, int* s_stop) {
     const DomDesc D = desc[T.dom];
     const DomCall C = call[T.dom];
     DomState* st = state + T.dom;
@@ -206,8 +228,10 @@ __global__ void __launch_bounds__(BATCH_THREADS, MINB)
     const int64_t s0 = (int64_t)T.rank * (BATCH_THREADS / 32) + wid;
     const int64_t stride = (int64_t)T.size * (BATCH_THREADS / 32);
     double R0 = 0.0;
+    if (threadIdx.x == 0 && T.rank == 0) st->t_start = gtimer();
     for (long long k = 0; k < C.max_steps; ++k) {
-        unsigned long long m = bstep_any(D, (int)(k & 1), C.dt, s0, stride);
+        unsigned long long m = T.size == 1 ? bstep_any<false>(D, (int)(k & 1), C.dt, s0, stride)
+                                           : bstep_any<true>(D, (int)(k & 1), C.dt, s0, stride);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
         if (lane == 0) wmax[wid] = m;
@@ -225,7 +249,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, MINB)
             }
             if (!team_sync_global(st, T.size)) {
                 if (threadIdx.x == 0) atomicExch(&st->done, DONE_TIMEOUT);
-                return;
+                return false;
             }
             volatile unsigned long long* rp = &st->res[k % 3];
             R = __longlong_as_double((long long)*rp);
@@ -238,17 +262,31 @@ __global__ void __launch_bounds__(BATCH_THREADS, MINB)
             else if (k > 0 && R0 > 0.0 && R > 1e6 * R0) dn = DONE_DIVERGED;
             else if (k + 1 >= C.max_steps) dn = DONE_CAP;
             else dn = DONE_RUNNING;
-            s_stop = dn;
+            *s_stop = dn;
             if (T.rank == 0 && dn != DONE_RUNNING) {
                 st->k = k + 1;
                 st->res_first = R0;
                 st->res_last = R;
                 st->done = dn;
+                st->t_end = gtimer();
             }
         }
         __syncthreads();
-        if (s_stop != DONE_RUNNING) return;
+        if (*s_stop != DONE_RUNNING) break;
     }
+    __syncthreads();
+    return true;
+}
+
+template <int MINB>
+__global__ void __launch_bounds__(BATCH_THREADS, MINB)
+    batch_kernel(const DomDesc* __restrict__ desc, const DomCall* __restrict__ call,
+                 DomState* state, const TeamDesc* __restrict__ assign,
+                 const int* __restrict__ first) {
+    __shared__ unsigned long long wmax[BATCH_THREADS / 32];
+    __shared__ int s_stop;
+    for (int a = first[blockIdx.x]; a < first[blockIdx.x + 1]; ++a)
+        if (!run_domain(assign[a], desc, call, state, wmax, &s_stop)) return;
 }
 
 // gather f and u of every domain into its plan (one launch for all domains)
@@ -271,6 +309,7 @@ __global__ void batch_gather(const DomDesc* desc, const DomCall* call, DomState*
             s.k = 0;
             s.done = C.max_steps <= 0 ? DONE_CAP : DONE_RUNNING;
             s.res_first = s.res_last = 0.0;
+            s.t_start = s.t_end = 0ull;
         }
     }
 }
@@ -287,7 +326,7 @@ __global__ void batch_scatter(const DomDesc* desc, const DomCall* call, const Do
     }
 }
 
-typedef void (*BatchFn)(const DomDesc*, const DomCall*, DomState*, const TeamDesc*);
+typedef void (*BatchFn)(const DomDesc*, const DomCall*, DomState*, const TeamDesc*, const int*);
 
 static BatchFn batch_fn(int minb) {
     switch (minb) {
@@ -297,30 +336,75 @@ static BatchFn batch_fn(int minb) {
     }
 }
 
-// teams: blocks per domain proportional to its bytes per step, >= 1 each,
-// summing to exactly `grid` (largest remainders get the leftovers)
-static std::vector<TeamDesc> make_teams(const std::vector<double>& work, int grid) {
+// Assignment of domains to the blocks of the persistent grid, minimising the
+// largest block load.  work[i] = cost of domain i (cost per step x step cap).
+// For a candidate load T: a domain with work > T gets a team of ceil(work/T)
+// blocks (each member carries work/size); the others are placed longest first
+// on the least-loaded block (LPT), after any team domain of that block.  T is the smallest value (binary
+// search) for which every block stays within T.  Returns per-block
+// assignment lists in CSR form.
+static bool try_assign(const std::vector<double>& work, int grid, double T,
+                       std::vector<std::vector<TeamDesc>>* out) {
     const int nd = (int)work.size();
-    std::vector<int> b(nd, 1);
-    double tot = std::accumulate(work.begin(), work.end(), 0.0);
-    int left = grid - nd;
-    if (left > 0 && tot > 0) {
-        std::vector<std::pair<double, int>> frac;
-        int used = 0;
-        for (int i = 0; i < nd; ++i) {
-            double share = work[i] / tot * left;
-            int extra = (int)floor(share);
-            b[i] += extra;
-            used += extra;
-            frac.push_back({share - extra, i});
-        }
-        std::sort(frac.begin(), frac.end(), [](auto a, auto c) { return a.first > c.first; });
-        for (int q = 0; q < left - used && q < nd; ++q) b[frac[q].second] += 1;
-    }
-    std::vector<TeamDesc> t;
+    std::vector<int> team(nd, 0);
+    long long used = 0;
     for (int i = 0; i < nd; ++i)
-        for (int r = 0; r < b[i]; ++r) t.push_back({i, r, b[i], 0});
-    return t;
+        if (work[i] > T) {
+            team[i] = (int)ceil(work[i] / T);
+            used += team[i];
+        }
+    if (used > grid) return false;
+    std::vector<int> order;
+    for (int i = 0; i < nd; ++i)
+        if (team[i] == 0) order.push_back(i);
+    std::sort(order.begin(), order.end(), [&](int a, int c) { return work[a] > work[c]; });
+    std::vector<double> load(grid, 0.0);
+    std::vector<std::vector<TeamDesc>> per(grid);
+    int b = 0;
+    for (int i = 0; i < nd; ++i)
+        for (int r = 0; r < team[i]; ++r) {
+            per[b].push_back({i, r, team[i], 0});
+            load[b] = work[i] / team[i];
+            ++b;
+        }
+    // LPT over all blocks (a heap would do; domain counts are small).  A team
+    // member runs its team's domain first - all members start it together -
+    // and then any small domains placed on its block.
+    for (int i : order) {
+        int best = 0;
+        for (int q = 1; q < grid; ++q)
+            if (load[q] < load[best]) best = q;
+        if (load[best] + work[i] > T * (1.0 + 1e-9)) return false;
+        per[best].push_back({i, 0, 1, 0});
+        load[best] += work[i];
+    }
+    if (out) out->swap(per);
+    return true;
+}
+
+static void make_assignment(const std::vector<double>& work, int grid, std::vector<TeamDesc>& asg,
+                            std::vector<int>& first) {
+    double tot = std::accumulate(work.begin(), work.end(), 0.0);
+    double mx = *std::max_element(work.begin(), work.end());
+    double lo = tot / std::max(grid, 1), hi = std::max(mx, lo) * 2.0 + 1e-300;
+    // hi is always feasible when grid >= number of domains or small domains pack;
+    // grow it until feasible
+    for (int g = 0; g < 64 && !try_assign(work, grid, hi, nullptr); ++g) hi *= 2.0;
+    for (int it = 0; it < 40; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (try_assign(work, grid, mid, nullptr)) hi = mid;
+        else lo = mid;
+    }
+    std::vector<std::vector<TeamDesc>> per;
+    try_assign(work, grid, hi, &per);
+    per.resize(grid);
+    asg.clear();
+    first.assign(grid + 1, 0);
+    for (int q = 0; q < grid; ++q) {
+        first[q] = (int)asg.size();
+        for (auto& t : per[q]) asg.push_back(t);
+    }
+    first[grid] = (int)asg.size();
 }
 
 static int batch_capture(rbffd_batch* B, cudaStream_t user) {
@@ -329,10 +413,6 @@ static int batch_capture(rbffd_batch* B, cudaStream_t user) {
         B->graph = nullptr;
     }
     BatchFn fn = batch_fn(B->minb);
-    std::vector<TeamDesc> teams = make_teams(B->work, B->grid);
-    RBFFD_CHECK_CUDA(cudaMemcpyAsync(B->d_team, teams.data(), sizeof(TeamDesc) * teams.size(),
-                                     cudaMemcpyHostToDevice, user));
-    RBFFD_CHECK_CUDA(cudaStreamSynchronize(user));
     cudaStream_t cs;
     RBFFD_CHECK_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaError_t e = cudaErrorUnknown;
@@ -354,7 +434,7 @@ static int batch_capture(rbffd_batch* B, cudaStream_t user) {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         e = cudaLaunchKernelEx(&cfg, fn, (const DomDesc*)B->d_desc, (const DomCall*)B->d_call,
-                               B->d_state, (const TeamDesc*)B->d_team);
+                               B->d_state, (const TeamDesc*)B->d_team, (const int*)B->d_first);
         if (e == cudaSuccess) {
             batch_scatter<<<gg, 256, 0, cs>>>(B->d_desc, B->d_call, B->d_state, B->ndom);
             e = cudaStreamEndCapture(cs, &g);
@@ -381,9 +461,11 @@ static int batch_capture(rbffd_batch* B, cudaStream_t user) {
 
 static void batch_free(rbffd_batch* B) {
     if (!B) return;
-    void* dv[] = {B->d_desc, B->d_call, B->d_state, B->d_team};
+    void* dv[] = {B->d_desc, B->d_call, B->d_state, B->d_team, B->d_first};
     for (void* p : dv)
         if (p) cudaFree(p);
+    if (B->h_team) cudaFreeHost(B->h_team);
+    if (B->h_first) cudaFreeHost(B->h_first);
     if (B->h_call) cudaFreeHost(B->h_call);
     if (B->h_state) cudaFreeHost(B->h_state);
     if (B->graph) cudaGraphExecDestroy((cudaGraphExec_t)B->graph);
@@ -422,7 +504,9 @@ extern "C" int rbffd_batch_create(rbffd_plan* const* plans, int ndom, int blocks
         d.n = p->n;
         d.pad = 0;
         B->desc.push_back(d);
-        B->work.push_back((double)p->NI * (12.0 * p->n + 24.0));
+        // default cost of one step: memory rounds of its slices (one per chunk of
+        // 16 neighbours plus one), which is what latency-bound blocks pay
+        B->work.push_back((double)p->nslices * (double)((p->n + 15) / 16 + 1));
     }
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMalloc((void**)&B->d_desc, sizeof(DomDesc) * ndom);
@@ -436,7 +520,11 @@ extern "C" int rbffd_batch_create(rbffd_plan* const* plans, int ndom, int blocks
         if (e == cudaSuccess) B->ev[i] = (void*)ev;
     }
     int sms = device_sm_count();
-    if (e == cudaSuccess) e = cudaMalloc((void**)&B->d_team, sizeof(TeamDesc) * (size_t)sms * 8 + sizeof(TeamDesc) * ndom);
+    const size_t max_asg = (size_t)sms * 8 + ndom;
+    if (e == cudaSuccess) e = cudaMalloc((void**)&B->d_team, sizeof(TeamDesc) * max_asg);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&B->h_team, sizeof(TeamDesc) * max_asg);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&B->d_first, sizeof(int) * ((size_t)sms * 8 + 1));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&B->h_first, sizeof(int) * ((size_t)sms * 8 + 1));
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(B->d_desc, B->desc.data(), sizeof(DomDesc) * ndom, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(B->d_state, 0, sizeof(DomState) * ndom, s);
@@ -453,7 +541,7 @@ extern "C" int rbffd_batch_create(rbffd_plan* const* plans, int ndom, int blocks
     B->minb = 2;
     B->per_sm = blocks_per_sm > 0 ? std::min(blocks_per_sm, std::max(per_sm_max, 1))
                                   : std::min(2, std::max(per_sm_max, 1));
-    B->grid = std::max(sms * B->per_sm, ndom);
+    B->grid = sms * B->per_sm;
     int maxres = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxres, (const void*)batch_fn(B->minb),
                                                   BATCH_THREADS, 0);
@@ -498,6 +586,21 @@ extern "C" int rbffd_solve_batch(rbffd_batch* B, const double* const* f, double*
     }
     RBFFD_CHECK_CUDA(cudaMemcpyAsync(B->d_call, B->h_call, sizeof(DomCall) * B->ndom,
                                      cudaMemcpyHostToDevice, s));
+    {
+        std::vector<double> work(B->ndom);
+        for (int i = 0; i < B->ndom; ++i) work[i] = B->work[i] * (double)std::max<int64_t>(max_steps[i], 1);
+        std::vector<TeamDesc> asg;
+        std::vector<int> first;
+        make_assignment(work, B->grid, asg, first);
+        // the pinned staging may still be read by a previous call's copy
+        RBFFD_CHECK_CUDA(cudaStreamSynchronize(s));
+        memcpy(B->h_team, asg.data(), sizeof(TeamDesc) * asg.size());
+        memcpy(B->h_first, first.data(), sizeof(int) * first.size());
+        RBFFD_CHECK_CUDA(cudaMemcpyAsync(B->d_team, B->h_team, sizeof(TeamDesc) * asg.size(),
+                                         cudaMemcpyHostToDevice, s));
+        RBFFD_CHECK_CUDA(cudaMemcpyAsync(B->d_first, B->h_first, sizeof(int) * first.size(),
+                                         cudaMemcpyHostToDevice, s));
+    }
     RBFFD_CHECK_CUDA(cudaEventRecord((cudaEvent_t)B->ev[0], s));
     RBFFD_CHECK_CUDA(cudaGraphLaunch((cudaGraphExec_t)B->graph, s));
     RBFFD_CHECK_CUDA(cudaEventRecord((cudaEvent_t)B->ev[1], s));
@@ -537,7 +640,7 @@ extern "C" int rbffd_batch_set_shape(rbffd_batch* B, int minb, int blocks_per_sm
     int maxres = 0;
     RBFFD_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxres, (const void*)batch_fn(minb),
                                                                    BATCH_THREADS, 0));
-    int grid = std::max(sms * blocks_per_sm, B->ndom);
+    int grid = sms * blocks_per_sm;
     if (grid > maxres * sms) {
         set_error("rbffd_batch_set_shape: %d blocks cannot be co-resident (max %d)", grid,
                   maxres * sms);
@@ -561,3 +664,39 @@ extern "C" int rbffd_batch_stats(const rbffd_batch* B, double* h_ms, int* h_shap
     }
     return RBFFD_OK;
 }
+
+extern "C" int rbffd_batch_domain_times(const rbffd_batch* B, double* h_start_ms, double* h_end_ms,
+                                        int* h_block, int* h_team) {
+    clear_error();
+    RBFFD_ARG(B && B->h_state, "rbffd_batch_domain_times: NULL batch");
+    unsigned long long t0 = ~0ull;
+    for (int i = 0; i < B->ndom; ++i)
+        if (B->h_state[i].t_start) t0 = std::min(t0, B->h_state[i].t_start);
+    for (int i = 0; i < B->ndom; ++i) {
+        const DomState& st = B->h_state[i];
+        if (h_start_ms) h_start_ms[i] = st.t_start ? (st.t_start - t0) * 1e-6 : -1.0;
+        if (h_end_ms) h_end_ms[i] = st.t_end ? (st.t_end - t0) * 1e-6 : -1.0;
+        if (h_block) h_block[i] = -1;
+        if (h_team) h_team[i] = 0;
+    }
+    for (int q = 0; q < B->grid; ++q)
+        for (int a = B->h_first[q]; a < B->h_first[q + 1]; ++a) {
+            const TeamDesc& t = B->h_team[a];
+            if (t.rank == 0) {
+                if (h_block) h_block[t.dom] = q;
+                if (h_team) h_team[t.dom] = t.size;
+            }
+        }
+    return RBFFD_OK;
+}
+
+extern "C" int rbffd_batch_set_costs(rbffd_batch* B, const double* h_cost_per_step) {
+    clear_error();
+    RBFFD_ARG(B && h_cost_per_step, "rbffd_batch_set_costs: NULL argument");
+    for (int i = 0; i < B->ndom; ++i)
+        RBFFD_ARG(h_cost_per_step[i] > 0.0 && isfinite(h_cost_per_step[i]),
+                  "rbffd_batch_set_costs: cost of domain %d must be positive", i);
+    for (int i = 0; i < B->ndom; ++i) B->work[i] = h_cost_per_step[i];
+    return RBFFD_OK;
+}
+

@@ -186,16 +186,22 @@ __device__ __forceinline__ unsigned long long step_rows(const StepArgs& A, int p
             if (MODE == MODE_SWEEP64) {
                 const double* uin = par ? A.u1 : A.u0;
                 double* uout = par ? A.u0 : A.u1;
+                // the row's own f and u are issued before the dot product, so
+                // their latency overlaps the stencil loads
+                const double fi = ld_stream(A.f + row);
+                const double ui = ld_iter<COH>(uin + row);
                 double acc = row_dot64<NN, COH>(A.w64 + base, A.col + base, uin, A.n);
-                double r = __dsub_rn(acc, A.f[row]);
-                uout[row] = __fma_rn(dt, r, uin[row]);
+                double r = __dsub_rn(acc, fi);
+                uout[row] = __fma_rn(dt, r, ui);
                 m = max(m, abs_bits(r));
             } else {
                 const float* ein = par ? A.e1 : A.e0;
                 float* eout = par ? A.e0 : A.e1;
+                const float di = ld_stream(A.d32 + row);
+                const float ei = ld_iter<COH>(ein + row);
                 float acc = row_dot32<NN, COH>(A.w32 + base, A.col + base, ein, A.n);
-                float rho = __fadd_rn(acc, A.d32[row]);
-                eout[row] = __fmaf_rn(dt32, rho, ein[row]);
+                float rho = __fadd_rn(acc, di);
+                eout[row] = __fmaf_rn(dt32, rho, ei);
                 m = max(m, abs_bits(rho));
             }
         }

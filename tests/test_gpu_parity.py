@@ -347,3 +347,12 @@ def test_pipeline_gpu_vs_oracle(rb, orc):
     ou, *_ = orc.solve_explicit(p.w, p.idx, p.interior, p.f, p.u0, dt, 400, 0.0)
     assert np.max(np.abs(H(u) - ou)) <= 1e-12 * np.max(np.abs(ou))
     plan.destroy()
+
+
+# ------------------------------------------------------------------ error metric (Eq. 8)
+def test_error_metric(rb, orc):
+    p = build(orc, 2, 30, 4, seed=91)
+    u = p.u0 + gen.random_vector(p.N, 4) * 1e-3
+    mx, mean = rb.rbffd_error(T(u), T(p.ua))
+    assert mx == np.max(np.abs(u - p.ua))
+    assert mean == pytest.approx(orc.mean_abs_error(u, p.ua), rel=1e-13)

@@ -308,6 +308,25 @@ RBFFD_API int rbffd_stable_dt(rbffd_plan* plan, const double* v0, int iters, dou
 RBFFD_API int rbffd_adjoint(rbffd_plan* plan, const double* lamK, int64_t K, double dt, double* grad_f,
                   double* grad_g, double* lam0, void* stream);
 
+/*
+ * rbffd_adjoint_w - rbffd_adjoint plus the gradient with respect to the
+ * stencil weights (not in the paper; derived from Eq. 6):
+ *   dL/dw_ij = dt sum_{k=0..K-1} lambda^{k+1}_i u^k_{idx_ij},
+ * summed for k = K-1 down to 0 as G = fma(lambda^{k+1}_i, u^k_j, G), then
+ * grad_w = dt G.  The iterates come back by sqrt(K)-style checkpointing: the
+ * caller keeps u^0, u^every, u^{2 every}, ... of its forward run (ckpt,
+ * [ceil(K/every)][N], caller order); each segment is replayed forward from its
+ * checkpoint (bit-identical to the forward sweep) into a segment buffer of
+ * every x N doubles (stream-ordered scratch), then walked backward.
+ *   f [NI] the source of the forward run; lamK [NI]; grad_w [NI][n] out
+ *   (caller layout, the row order of the plan's interior list); grad_f,
+ *   grad_g, lam0 as rbffd_adjoint.
+ */
+RBFFD_API int rbffd_adjoint_w(rbffd_plan* plan, const double* f, const double* ckpt,
+                              int64_t every, const double* lamK, int64_t K, double dt,
+                              double* grad_w, double* grad_f, double* grad_g, double* lam0,
+                              void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,6 +20,7 @@ each routine for numpy arrays.  What each routine follows in the paper:
 * ``solve_dc``         Eq. 6 in FP32 on the correction inside FP64 defect
                        correction (precision split not in the paper)
 * ``adjoint``          transpose of Eq. 6 for a sensor misfit (not in the paper)
+* ``adjoint_w``        the same plus the gradient with respect to the weights
 * ``power_rho``        spectral radius of the interior operator, from which the
                        stability bound that Eq. 7 only approximates is taken
 * ``mean_abs_error``   Eq. 8 (error)
@@ -74,6 +75,7 @@ def _load():
         "oracle_solve_dc": (i32, [P, P, P, i64, i64, i32, P, P, f64, f64, i64, i64, f64,
                                   P, P, P]),
         "oracle_adjoint": (i32, [P, P, P, i64, i64, i32, P, i64, f64, P, P, P]),
+        "oracle_adjoint_w": (i32, [P, P, P, i64, i64, i32, P, P, P, i64, f64, P, P, P, P]),
         "oracle_power_rho": (f64, [P, P, P, i64, i64, i32, P, i32]),
         "oracle_gepp_dense": (i32, [i32, P, P, P]),
         "oracle_num_threads": (i32, []),
@@ -220,6 +222,29 @@ def adjoint(w, idx, interior, N, lamK, K, dt):
     if st != 0:
         raise RuntimeError("oracle_adjoint failed")
     return gf, gg, l0
+
+
+def adjoint_w(w, idx, interior, f, u0, lamK, K, dt):
+    """Backward pass including the weight gradient.
+
+    Returns (grad_w [NI, n], grad_f [NI], grad_g [N], lam0 [NI])."""
+    w = _c(w, np.float64)
+    idx = _c(idx, np.int32)
+    interior = _c(interior, np.int32)
+    f = _c(f, np.float64)
+    u0 = _c(u0, np.float64)
+    lamK = _c(lamK, np.float64)
+    rows, n = idx.shape
+    N = len(u0)
+    gw = np.zeros((rows, n), np.float64)
+    gf = np.zeros(rows, np.float64)
+    gg = np.zeros(N, np.float64)
+    l0 = np.zeros(rows, np.float64)
+    st = _load().oracle_adjoint_w(_p(w), _p(idx), _p(interior), N, rows, n, _p(f), _p(u0),
+                                  _p(lamK), K, dt, _p(gw), _p(gf), _p(gg), _p(l0))
+    if st != 0:
+        raise RuntimeError("oracle_adjoint_w failed")
+    return gw, gf, gg, l0
 
 
 def power_rho(w, idx, interior, N, v0, iters=200):

@@ -29,6 +29,7 @@
  *   oracle_solve_dc    Eq. 6 with an FP32 inner iteration on the correction
  *                      inside an FP64 defect-correction loop (paper silent)
  *   oracle_adjoint     transpose of Eq. 6 for a sensor misfit (paper silent)
+ *   oracle_adjoint_w   the same, plus the gradient with respect to the weights
  *   oracle_power_rho   spectral-radius estimate for the stability bound that
  *                      Eq. 7 (cfl) only gives as a guideline
  *   oracle_gepp_dense  dense Gaussian elimination used by the pin tests
@@ -737,6 +738,76 @@ int oracle_adjoint(const double* w, const int32_t* idx, const int32_t* interior,
         }
     for (int64_t i = 0; i < N; ++i) grad_g[i] = (row_of[i] < 0) ? dt * acc[i] : 0.0;
     free(lam); free(acc); free(S); free(row_of);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Gradient with respect to the stencil weights (paper silent; derived from   */
+/* Eq. 6): u^{k+1}_i = u^k_i + dt (sum_j w_ij u^k_{idx_ij} - f_i) gives       */
+/* dL/dw_ij = dt sum_{k=0..K-1} lambda^{k+1}_i u^k_{idx_ij}.  The iterates   */
+/* u^0..u^{K-1} are recomputed from u0 and stored (plain, memory K x N); the */
+/* sum runs k = K-1 down to 0 as G = fma(lambda^{k+1}_i, u^k_j, G), then     */
+/* grad_w = dt * G.  lambda follows oracle_adjoint (same order, same S).     */
+/* Also returns grad_f, grad_g, lam0 as oracle_adjoint does.                 */
+/* ------------------------------------------------------------------------- */
+int oracle_adjoint_w(const double* w, const int32_t* idx, const int32_t* interior, int64_t N,
+                     int64_t NI, int n, const double* f, const double* u0, const double* lamK,
+                     int64_t K, double dt, double* grad_w, double* grad_f, double* grad_g,
+                     double* lam0)
+{
+    double* U = (double*)malloc(sizeof(double) * (size_t)(K > 0 ? K : 1) * (size_t)N);
+    double* lam = (double*)malloc(sizeof(double) * (size_t)NI);
+    double* acc = (double*)malloc(sizeof(double) * (size_t)N);
+    double* S = (double*)calloc((size_t)NI, sizeof(double));
+    double* G = (double*)calloc((size_t)(NI * n), sizeof(double));
+    int32_t* row_of = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);
+    if (!U || !lam || !acc || !S || !G || !row_of) {
+        free(U); free(lam); free(acc); free(S); free(G); free(row_of);
+        return -2;
+    }
+    for (int64_t i = 0; i < N; ++i) row_of[i] = -1;
+    for (int64_t r = 0; r < NI; ++r) row_of[interior[r]] = (int32_t)r;
+    /* forward: store u^0 .. u^{K-1} */
+    if (K > 0) memcpy(U, u0, sizeof(double) * (size_t)N);
+    for (int64_t k = 0; k + 1 < K; ++k) {
+        const double* cur = U + (size_t)k * N;
+        double* nxt = U + (size_t)(k + 1) * N;
+        memcpy(nxt, cur, sizeof(double) * (size_t)N);
+        for (int64_t r = 0; r < NI; ++r) {
+            double a = 0.0;
+            for (int j = 0; j < n; ++j) a = fma(w[r * n + j], cur[idx[r * n + j]], a);
+            double ri = a - f[r];
+            nxt[interior[r]] = fma(dt, ri, cur[interior[r]]);
+        }
+    }
+    memcpy(lam, lamK, sizeof(double) * (size_t)NI);
+    for (int64_t k = K - 1; k >= 0; --k) {
+        const double* uk = U + (size_t)k * N;
+        /* weight gradient with lambda^{k+1} and u^k */
+        for (int64_t r = 0; r < NI; ++r)
+            for (int j = 0; j < n; ++j)
+                G[r * n + j] = fma(lam[r], uk[idx[r * n + j]], G[r * n + j]);
+        /* S += lambda^{k+1}; lambda^k = lambda^{k+1} + dt W_II^T lambda^{k+1} */
+        for (int64_t r = 0; r < NI; ++r) S[r] = S[r] + lam[r];
+        for (int64_t i = 0; i < N; ++i) acc[i] = 0.0;
+        for (int64_t r = 0; r < NI; ++r)
+            for (int j = 0; j < n; ++j) {
+                int64_t col = idx[r * n + j];
+                acc[col] = fma(w[r * n + j], lam[r], acc[col]);
+            }
+        for (int64_t r = 0; r < NI; ++r) lam[r] = fma(dt, acc[interior[r]], lam[r]);
+    }
+    for (int64_t q = 0; q < NI * n; ++q) grad_w[q] = dt * G[q];
+    memcpy(lam0, lam, sizeof(double) * (size_t)NI);
+    for (int64_t r = 0; r < NI; ++r) grad_f[r] = -dt * S[r];
+    for (int64_t i = 0; i < N; ++i) acc[i] = 0.0;
+    for (int64_t r = 0; r < NI; ++r)
+        for (int j = 0; j < n; ++j) {
+            int64_t col = idx[r * n + j];
+            acc[col] = fma(w[r * n + j], S[r], acc[col]);
+        }
+    for (int64_t i = 0; i < N; ++i) grad_g[i] = (row_of[i] < 0) ? dt * acc[i] : 0.0;
+    free(U); free(lam); free(acc); free(S); free(G); free(row_of);
     return 0;
 }
 

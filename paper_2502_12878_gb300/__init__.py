@@ -48,7 +48,7 @@ EXPORTED = [
     "rbffd_solve_explicit", "rbffd_solve_dc", "rbffd_plan_set_dc", "rbffd_stable_dt",
     "rbffd_adjoint", "rbffd_plan_stats", "rbffd_knn_noalloc", "rbffd_batch_create",
     "rbffd_batch_destroy", "rbffd_solve_batch", "rbffd_batch_set_shape", "rbffd_batch_stats",
-    "rbffd_error", "rbffd_batch_domain_times", "rbffd_batch_set_costs",
+    "rbffd_error", "rbffd_batch_domain_times", "rbffd_batch_set_costs", "rbffd_adjoint_w",
 ]
 RBFFD_KNN_NOALLOC_MAX_NODES = 262144
 
@@ -102,6 +102,7 @@ def lib():
         "rbffd_error": (I, [P, P, I64, PD, PD, P]),
         "rbffd_batch_domain_times": (I, [P, P, P, P, P]),
         "rbffd_batch_set_costs": (I, [P, P]),
+        "rbffd_adjoint_w": (I, [P, P, P, I64, P, I64, D, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -295,6 +296,21 @@ class Plan:
         _check(code, (RBFFD_OK, RBFFD_NOT_CONVERGED))
         return code, outer.value, inner.value, res.value
 
+    def adjoint_w(self, f, ckpt, every, lamK, K, dt):
+        """Backward pass with the weight gradient from checkpoints ckpt [nseg, N] (caller
+        order, u^0, u^every, ...).  Returns (grad_w [NI, n], grad_f, grad_g, lam0)."""
+        f = _dev(f, torch.float64, "f")
+        ckpt = _dev(ckpt, torch.float64, "ckpt")
+        lamK = _dev(lamK, torch.float64, "lamK")
+        gw = torch.empty((self.NI, self.n), dtype=torch.float64, device=self.device)
+        gf = torch.empty(self.NI, dtype=torch.float64, device=self.device)
+        gg = torch.empty(self.N, dtype=torch.float64, device=self.device)
+        l0 = torch.empty(self.NI, dtype=torch.float64, device=self.device)
+        _check(lib().rbffd_adjoint_w(self.handle, _ptr(f), _ptr(ckpt), int(every), _ptr(lamK),
+                                     int(K), float(dt), _ptr(gw), _ptr(gf), _ptr(gg), _ptr(l0),
+                                     _stream(self.device)))
+        return gw, gf, gg, l0
+
     def stats(self):
         """(GPU ms of the last solve's step loops, their steps, kernels launched, launch shape)."""
         ms = ctypes.c_double(0.0)
@@ -447,6 +463,76 @@ class Batch:
                     json.dump(known, fh)
         self.calibrate(fs, us, dts, probe_steps)
         return best
+
+
+class ExplicitSolver:
+    """K explicit steps of Eq. 6 on a fixed node set, as a differentiable map.
+
+    ``solver(f, g, w)`` returns u^K [N] from u^0 = 0 inside and g on the boundary
+    (``g`` in the order of the boundary nodes, ascending).  Gradients flow to f, g
+    and (if it requires grad) the weights w [NI, n].  The forward keeps every
+    ``every``-th iterate (default ceil(sqrt(K))); the backward replays each
+    segment from its checkpoint to get the iterates the weight gradient needs."""
+
+    def __init__(self, xyz, is_bnd, interior, idx, K, dt, every=None, flags=0):
+        self.xyz, self.is_bnd = xyz, is_bnd
+        self.interior, self.idx = interior, idx
+        self.K, self.dt = int(K), float(dt)
+        self.every = int(every) if every else max(1, math.ceil(math.sqrt(max(self.K, 1))))
+        self.flags = flags
+        self.bnd = torch.nonzero(is_bnd).flatten()
+        self.N = xyz.shape[1]
+        self._plan, self._w_key = None, None
+
+    def plan(self, w):
+        key = (w.data_ptr(), w._version)
+        if self._plan is None or self._w_key != key:
+            if self._plan is not None:
+                self._plan.destroy()
+            self._plan = Plan(self.xyz, self.is_bnd, self.interior, self.idx, w.detach(),
+                              self.flags)
+            self._w_key = key
+        return self._plan
+
+    def __call__(self, f, g, w):
+        return RBFFDExplicit.apply(f, g, w, self)
+
+
+class RBFFDExplicit(torch.autograd.Function):
+    """u^K of Eq. 6 with the adjoint (transposed stencil sweep) as its backward."""
+
+    @staticmethod
+    def forward(ctx, f, g, w, solver):
+        plan = solver.plan(w)
+        u = torch.zeros(solver.N, dtype=torch.float64, device=f.device)
+        u[solver.bnd] = g
+        ck = []
+        done = 0
+        while done < solver.K:
+            ck.append(u.clone())
+            steps = min(solver.every, solver.K - done)
+            plan.solve_explicit(f.contiguous(), u, solver.dt, steps, 0.0)
+            done += steps
+        ckpt = torch.stack(ck) if ck else u.clone()[None]
+        ctx.solver = solver
+        ctx.save_for_backward(f, ckpt)
+        return u
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        solver = ctx.solver
+        f, ckpt = ctx.saved_tensors
+        plan = solver._plan
+        grad_u = grad_u.contiguous()
+        lamK = grad_u[solver.interior.long()].contiguous()
+        gw = None
+        if ctx.needs_input_grad[2]:
+            gw, gf, gg, _ = plan.adjoint_w(f.contiguous(), ckpt, solver.every, lamK, solver.K,
+                                           solver.dt)
+        else:
+            gf, gg, _ = plan.adjoint(lamK, solver.K, solver.dt, want_lam0=False)
+        grad_g = gg[solver.bnd] + grad_u[solver.bnd]
+        return gf, grad_g, gw, None
 
 
 def rbffd_plan_create(xyz, is_bnd, interior, idx, w, flags=0, seed=0) -> Plan:

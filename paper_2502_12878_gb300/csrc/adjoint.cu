@@ -201,6 +201,60 @@ __global__ void adj_outputs(const double* S, const double* lam, const int32_t* r
     }
 }
 
+// replay of one forward step (Eq. 6) from uin to uout, both in slot order:
+// interior rows updated, boundary slots copied (the same arithmetic as the
+// forward sweep, so the replayed iterates are the forward's bit for bit)
+__global__ void replay_step(const double* __restrict__ w64, const int32_t* __restrict__ col,
+                            const double* __restrict__ fs, const double* __restrict__ uin,
+                            double* __restrict__ uout, int64_t NI, int64_t N, int n, double dt) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        if (p >= NI) {
+            uout[p] = uin[p];
+            continue;
+        }
+        const int64_t base = (p / SLICE) * (int64_t)n * SLICE + (p % SLICE);
+        double acc = 0.0;
+        for (int j = 0; j < n; ++j)
+            acc = __fma_rn(w64[base + j * SLICE], __ldg(uin + col[base + j * SLICE]), acc);
+        double r = __dsub_rn(acc, fs[p]);
+        uout[p] = __fma_rn(dt, r, uin[p]);
+    }
+}
+
+// weight-gradient accumulation with lambda^{k+1} and u^k in the slice layout:
+// G[s][j][lane] = fma(lambda_p, u^k[col], G[s][j][lane])
+__global__ void wgrad_accum(const int32_t* __restrict__ col, const double* __restrict__ lam,
+                            const double* __restrict__ uk, double* __restrict__ G, int64_t NI,
+                            int n) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < NI;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t base = (p / SLICE) * (int64_t)n * SLICE + (p % SLICE);
+        const double lp = lam[p];
+        for (int j = 0; j < n; ++j) {
+            const int64_t q = base + j * SLICE;
+            G[q] = __fma_rn(lp, __ldg(uk + col[q]), G[q]);
+        }
+    }
+}
+
+// grad_w in the caller's layout [NI][n] = dt * G
+__global__ void wgrad_unpack(const double* __restrict__ G, const int32_t* row_of_slot, int64_t NI,
+                             int n, double dt, double* grad_w) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < NI;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t base = (p / SLICE) * (int64_t)n * SLICE + (p % SLICE);
+        const int64_t r = row_of_slot[p];
+        for (int j = 0; j < n; ++j) grad_w[r * n + j] = __dmul_rn(dt, G[base + j * SLICE]);
+    }
+}
+
+__global__ void ckpt_gather(const double* u, const int32_t* perm, int64_t N, double* out) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N;
+         p += (int64_t)gridDim.x * blockDim.x)
+        out[p] = u[perm[p]];
+}
+
 static int build_transpose(rbffd_plan* p, cudaStream_t s) {
     if (p->tr) return RBFFD_OK;
     const int64_t N = p->N, NI = p->NI;
@@ -289,3 +343,56 @@ extern "C" int rbffd_adjoint(rbffd_plan* p, const double* lamK, int64_t K, doubl
     RBFFD_CHECK_CUDA(cudaGetLastError());
     return RBFFD_OK;
 }
+
+extern "C" int rbffd_adjoint_w(rbffd_plan* p, const double* f, const double* ckpt, int64_t every,
+                               const double* lamK, int64_t K, double dt, double* grad_w,
+                               double* grad_f, double* grad_g, double* lam0, void* stream) {
+    clear_error();
+    RBFFD_ARG(p && f && ckpt && lamK && grad_w && grad_f && grad_g,
+              "rbffd_adjoint_w: NULL argument");
+    RBFFD_ARG(K >= 0 && every >= 1 && isfinite(dt), "rbffd_adjoint_w: bad K / every / dt");
+    cudaStream_t s = as_stream(stream);
+    int st = build_transpose(p, s);
+    if (st) return st;
+    Transpose& T = *p->tr;
+    const int sms = device_sm_count();
+    const unsigned G = (unsigned)sms * 8;
+    const int64_t N = p->N, NI = p->NI;
+    const int n = p->n;
+    const int64_t seg = std::min<int64_t>(every, std::max<int64_t>(K, 1));
+    Scratch segbuf, gacc;
+    RBFFD_CHECK_CUDA(segbuf.alloc(sizeof(double) * (size_t)seg * N, s));
+    RBFFD_CHECK_CUDA(gacc.alloc(sizeof(double) * (size_t)p->nslices * n * SLICE, s));
+    double* U = segbuf.as<double>();
+    double* Gw = gacc.as<double>();
+    RBFFD_CHECK_CUDA(cudaMemsetAsync(Gw, 0, sizeof(double) * (size_t)p->nslices * n * SLICE, s));
+    // f in slot order for the replays; lambda^K in slot order
+    adj_gather<<<G, 256, 0, s>>>(f, p->row_of_slot, NI, p->fs);
+    adj_gather<<<G, 256, 0, s>>>(lamK, p->row_of_slot, NI, T.lam[0]);
+    RBFFD_CHECK_CUDA(cudaMemsetAsync(T.S, 0, sizeof(double) * NI, s));
+    const int64_t nseg = (K + every - 1) / every;
+    const int64_t nsl_int = (NI + SLICE - 1) / SLICE;
+    const unsigned agrid = (unsigned)std::max<int64_t>(1, (nsl_int + 7) / 8);
+    int cur = 0;   // lambda^{k+1} lives in T.lam[cur]
+    for (int64_t sidx = nseg - 1; sidx >= 0; --sidx) {
+        const int64_t k0 = sidx * every, k1 = std::min(K, k0 + every);
+        // u^{k0} from its checkpoint, then replay u^{k0+1} .. u^{k1-1}
+        ckpt_gather<<<G, 256, 0, s>>>(ckpt + sidx * N, p->perm, N, U);
+        for (int64_t k = k0; k + 1 < k1; ++k)
+            replay_step<<<G, 256, 0, s>>>(p->w64, p->col, p->fs, U + (k - k0) * N,
+                                          U + (k - k0 + 1) * N, NI, N, n, dt);
+        for (int64_t k = k1 - 1; k >= k0; --k) {
+            wgrad_accum<<<G, 256, 0, s>>>(p->col, T.lam[cur], U + (k - k0) * N, Gw, NI, n);
+            adjoint_step<<<agrid, 256, 0, s>>>(T, NI, dt, T.lam[cur], T.lam[cur ^ 1], T.S);
+            cur ^= 1;
+        }
+        RBFFD_CHECK_CUDA(cudaGetLastError());
+    }
+    adjoint_grad_g<<<G, 256, 0, s>>>(T, NI, N, dt, T.S, p->perm, grad_g);
+    adj_outputs<<<G, 256, 0, s>>>(T.S, T.lam[cur], p->row_of_slot, p->perm, NI, dt, grad_f,
+                                  grad_g, lam0);
+    wgrad_unpack<<<G, 256, 0, s>>>(Gw, p->row_of_slot, NI, n, dt, grad_w);
+    RBFFD_CHECK_CUDA(cudaGetLastError());
+    return RBFFD_OK;
+}
+

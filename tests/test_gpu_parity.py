@@ -356,3 +356,58 @@ def test_error_metric(rb, orc):
     mx, mean = rb.rbffd_error(T(u), T(p.ua))
     assert mx == np.max(np.abs(u - p.ua))
     assert mean == pytest.approx(orc.mean_abs_error(u, p.ua), rel=1e-13)
+
+
+# ------------------------------------------------------------------ weight gradient, autograd
+def test_adjoint_w_parity_and_checkpoint_invariance(rb, orc):
+    p = build(orc, 2, 18, 4, seed=72)
+    dt = _dt(orc, p)
+    K = 60
+    lamK = np.zeros(p.NI)
+    lamK[gen.sensors(p.NI, 20, 3)] = gen.random_vector(20, 4)
+    gw, gf, gg, l0 = orc.adjoint_w(p.w, p.idx, p.interior, p.f, p.u0, lamK, K, dt)
+    plan = _plan(rb, p)
+    results = []
+    for every in (1, 7, K):
+        # checkpoints of the forward run, every `every` steps
+        u = T(p.u0)
+        ck = []
+        done = 0
+        while done < K:
+            ck.append(u.clone())
+            s = min(every, K - done)
+            plan.solve_explicit(T(p.f), u, dt, s, 0.0)
+            done += s
+        res = plan.adjoint_w(T(p.f), torch.stack(ck), every, T(lamK), K, dt)
+        results.append(res)
+        for a, b in zip(res, (gw, gf, gg, l0)):
+            assert np.max(np.abs(H(a) - b)) <= 1e-12 * np.max(np.abs(b))
+    # the replayed iterates are the forward's: checkpoint spacing changes nothing
+    for r in results[1:]:
+        for a, b in zip(r, results[0]):
+            assert torch.equal(a, b)
+    plan.destroy()
+
+
+def test_autograd_function_matches_oracle(rb, orc):
+    p = build(orc, 2, 16, 2, seed=73)
+    dt = _dt(orc, p)
+    K = 45
+    sens = gen.sensors(p.NI, 15, 6)
+    uobs = p.ua[p.interior][sens]
+    solver = rb.ExplicitSolver(T(p.xyz), T(p.is_bnd), T(p.interior), T(p.idx), K, dt)
+    bnd = np.nonzero(p.is_bnd)[0]
+    f = T(p.f).requires_grad_(True)
+    g = T(p.u0[bnd]).requires_grad_(True)
+    w = T(p.w).requires_grad_(True)
+    uK = solver(f, g, w)
+    loss = ((uK[T(p.interior).long()[T(sens).long()]] - T(uobs)) ** 2).sum()
+    loss.backward()
+    # oracle: forward, lambda^K, then the weight-aware adjoint
+    ou, *_ = orc.solve_explicit(p.w, p.idx, p.interior, p.f, p.u0, dt, K, 0.0)
+    assert np.max(np.abs(H(uK.detach()) - ou)) <= 1e-12 * np.max(np.abs(ou))
+    lamK = np.zeros(p.NI)
+    lamK[sens] = 2 * (ou[p.interior][sens] - uobs)
+    gw, gf, gg, _ = orc.adjoint_w(p.w, p.idx, p.interior, p.f, p.u0, lamK, K, dt)
+    for a, b in ((f.grad, gf), (g.grad, gg[bnd]), (w.grad, gw)):
+        assert np.max(np.abs(H(a) - b)) <= 1e-12 * np.max(np.abs(b))

@@ -173,3 +173,51 @@ def test_adjoint_matches_dense_reverse_sweep_and_fd(orc):
 def test_mean_abs_error_definition(orc):
     # Eq. 8 on a hand-made vector
     assert orc.mean_abs_error([1.0, 2.0, 3.0], [1.0, 1.5, 4.0]) == pytest.approx(0.5)
+
+
+def test_weight_gradient_matches_dense_reverse_sweep_and_fd(orc):
+    """dL/dw from a dense numpy reverse sweep over stored iterates, and central
+    differences of the loss along random weight perturbations (O(eps^2) exact)."""
+    p = build(orc, 2, 8, 2, seed=12)
+    WII, WIB, bnd = p.dense()
+    dt, K = dt_stable(orc, p), 30
+    sens = gen.sensors(p.NI, 8, 4)
+    uobs = p.ua[p.interior][sens]
+    rows = np.repeat(np.arange(p.NI), p.n)
+
+    def forward(w):
+        u = p.u0.copy()
+        U = []
+        for _ in range(K):
+            U.append(u.copy())
+            Lu = np.zeros(p.NI)
+            np.add.at(Lu, rows, (w * u[p.idx]).ravel())
+            u = u.copy()
+            u[p.interior] = u[p.interior] + dt * (Lu - p.f)
+        return u, U
+
+    def loss(w):
+        u, _ = forward(w)
+        return np.sum((u[p.interior][sens] - uobs) ** 2)
+
+    uK, U = forward(p.w)
+    lamK = np.zeros(p.NI)
+    lamK[sens] = 2 * (uK[p.interior][sens] - uobs)
+    gw, gf, gg, l0 = orc.adjoint_w(p.w, p.idx, p.interior, p.f, p.u0, lamK, K, dt)
+    # dense reverse sweep
+    lam = lamK.copy()
+    ref = np.zeros_like(p.w)
+    for k in range(K - 1, -1, -1):
+        ref += dt * lam[:, None] * U[k][p.idx]
+        lam = lam + dt * (WII.T @ lam)
+    np.testing.assert_allclose(gw, ref, rtol=1e-11, atol=1e-13 * np.abs(ref).max())
+    # the f/g gradients and lambda^0 equal the f/g-only adjoint's
+    gf2, gg2, l02 = orc.adjoint(p.w, p.idx, p.interior, p.N, lamK, K, dt)
+    assert np.array_equal(gf, gf2) and np.array_equal(gg, gg2) and np.array_equal(l0, l02)
+    rng = np.random.default_rng(1)
+    for _ in range(4):
+        v = rng.standard_normal(p.w.shape) * np.abs(p.w)
+        eps = 1e-6
+        fd = (loss(p.w + eps * v) - loss(p.w - eps * v)) / (2 * eps)
+        an = np.sum(gw * v)
+        assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-12)

@@ -78,7 +78,13 @@ RBFFD_API int rbffd_version(void);
  *            1: disk of radius 1/2 about (1/2,1/2); every grid point is
  *               jittered and kept iff it lies closer than 1/2 - h/2 to the
  *               centre; then round(pi/h) boundary nodes at equal angles.
- *   xyz      [d][cap] FP64 out, is_bnd [cap] out (1 = boundary node)
+ *            2: half cube [0,1/2]^d of the mixed-boundary variant (Sec. II-C,
+ *               text after Eq. 5): spacing h = 0.5/Kg; nodes with an index 0
+ *               are Dirichlet nodes (is_bnd 1) on the grid; other nodes with
+ *               an index Kg are Neumann nodes (is_bnd 2) whose Kg coordinates
+ *               are exactly 1/2; interior nodes are jittered as in shape 0.
+ *   xyz      [d][cap] FP64 out, is_bnd [cap] out (0 interior, 1 Dirichlet,
+ *            2 Neumann; every non-zero code is a boundary node)
  *   cap      capacity; with cap = 0 only the count is returned
  *   h_n_out  host: number of nodes.  RBFFD_ERR_CAPACITY if it exceeds cap > 0.
  */
@@ -107,6 +113,18 @@ RBFFD_API int rbffd_interior(const uint8_t* is_bnd, int64_t N, int32_t* interior
  */
 RBFFD_API int rbffd_knn(const double* xyz, int64_t N, int d, const int32_t* centres, int64_t nc, int n,
               int32_t* idx, void* stream);
+
+/*
+ * rbffd_knn_masked - rbffd_knn restricted to candidate nodes: only nodes with
+ * cand[j] != 0 (device, [N]) may appear in a support, besides the centre
+ * itself, which is always first.  Used for the supports of Neumann nodes,
+ * whose values are set from interior nodes (Sec. II-C: "values from the last
+ * step at interior nodes in the support").  RBFFD_ERR_ARG if fewer than n
+ * nodes qualify.
+ */
+RBFFD_API int rbffd_knn_masked(const double* xyz, int64_t N, int d, const uint8_t* cand,
+                               const int32_t* centres, int64_t nc, int n, int32_t* idx,
+                               void* stream);
 
 /*
  * rbffd_knn_noalloc - rbffd_knn for callers that cannot allocate device
@@ -155,6 +173,18 @@ RBFFD_API int rbffd_weights(const double* xyz, int64_t N, int d, const int32_t* 
                   void* stream);
 
 /*
+ * rbffd_weights_dir - RBF-FD weights of a directional derivative (the normal
+ * derivative of a Neumann condition, Sec. II-C), the same saddle-point system
+ * as rbffd_weights with the operator changed: right-hand side
+ * -3 |xi_j| (xi_j . dir) for phi = r^3, the dir components for the degree-1
+ * monomials, 0 for the others; w_j = x_j / sigma.  dirs [nc][d] unit vectors.
+ */
+RBFFD_API int rbffd_weights_dir(const double* xyz, int64_t N, int d, const int32_t* idx,
+                                int64_t nc, int n, int m, const double* dirs, double* w,
+                                int8_t* status, int64_t* h_n_bad, int64_t* h_first_bad,
+                                void* stream);
+
+/*
  * rbffd_apply - Eq. 1: Lu[r] = sum_j w[r][j] * u[idx[r][j]], accumulated as
  * a fused multiply-add chain in support order starting from 0.
  *   w, idx [nc][n] (row-major, as rbffd_weights / rbffd_knn give them),
@@ -180,6 +210,8 @@ RBFFD_API int rbffd_error(const double* u, const double* ua, int64_t N, double* 
  * weights for defect correction and the transposed interior operator for the
  * adjoint.  All inputs are copied; they may be freed afterwards.
  *   interior [NI] must list exactly the nodes with is_bnd == 0 (any order);
+ *   (boundary nodes, is_bnd != 0, keep their values unless set as Neumann
+ *   nodes by rbffd_plan_set_neumann);
  *   idx / w [NI][n] are the supports/weights of those rows.
  *   flags: RBFFD_ORDER_* | RBFFD_LAUNCH_*; seed is used by RBFFD_ORDER_RANDOM.
  *   *plan out.
@@ -188,6 +220,24 @@ RBFFD_API int rbffd_plan_create(const double* xyz, const uint8_t* is_bnd, int64_
                       const int32_t* interior, const int32_t* idx, const double* w, int64_t NI,
                       int n, int flags, uint64_t seed, rbffd_plan** plan, void* stream);
 RBFFD_API int rbffd_plan_destroy(rbffd_plan* plan);
+/*
+ * rbffd_plan_set_neumann - Neumann boundary nodes of the mixed-boundary
+ * variant (Sec. II-C, text after Eq. 5).  Before every explicit step each
+ * Neumann node b takes the value that meets its normal-derivative condition
+ * from the previous iterate of its other support nodes:
+ *   acc = fma-chain_{j>=1} w[b][j] u[idx[b][j]],  u_b = (g_b - acc) / w[b][0]
+ * (all from the same previous iterate; then the interior step runs on the
+ * updated values).  nodes [NN] boundary node indices, idx [NN][nn] their
+ * supports with the node first (rbffd_knn_masked over interior candidates),
+ * w [NN][nn] their normal-derivative weights (rbffd_weights_dir), g [NN]
+ * Neumann data (NULL = 0).  NN = 0 removes the Neumann nodes.  Solves with
+ * Neumann nodes run in the graph launch mode and in FP64; rbffd_stable_dt
+ * then estimates the radius of the operator with the Neumann values
+ * eliminated.  rbffd_solve_explicit also returns the Neumann node values.
+ */
+RBFFD_API int rbffd_plan_set_neumann(rbffd_plan* plan, int64_t NN, const int32_t* nodes,
+                                     const int32_t* idx, const double* w, int nn,
+                                     const double* g, void* stream);
 /* node permutation of the plan: perm [N] out, perm[p] = original index of slot p */
 RBFFD_API int rbffd_plan_perm(const rbffd_plan* plan, int32_t* perm, void* stream);
 

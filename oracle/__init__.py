@@ -15,7 +15,9 @@ each routine for numpy arrays.  What each routine follows in the paper:
 * ``knn_kdtree``       same result through a kd-tree, pinned to ``knn_brute``
 * ``weights``          RBF-FD augmented system, Eq. 2-3, phi(r) = r^3 with
                        monomials up to order m (Sec. II text after Eq. 3)
+* ``weights_dir``      the same system for a directional (normal) derivative
 * ``apply``            Eq. 1
+* ``solve_mixed``      Eq. 6 with Neumann nodes (mixed-boundary variant, Sec. II-C)
 * ``solve_explicit``   Eq. 6 (jacobi_step), time step per Eq. 7 (cfl)
 * ``solve_dc``         Eq. 6 in FP32 on the correction inside FP64 defect
                        correction (precision split not in the paper)
@@ -67,6 +69,8 @@ def _load():
         "oracle_nodes": (i64, [i32, i32, i32, f64, u64, P, P, i64]),
         "oracle_knn_brute": (i32, [P, i64, i32, P, i64, i32, P]),
         "oracle_knn_kdtree": (i32, [P, i64, i32, P, i64, i32, P]),
+        "oracle_knn_brute_masked": (i32, [P, i64, i32, P, P, i64, i32, P]),
+        "oracle_knn_kdtree_masked": (i32, [P, i64, i32, P, P, i64, i32, P]),
         "oracle_num_monomials": (i32, [i32, i32]),
         "oracle_monomials": (i32, [i32, i32, P]),
         "oracle_weights": (i64, [P, i64, i32, P, i64, i32, i32, P, P]),
@@ -77,6 +81,9 @@ def _load():
         "oracle_adjoint": (i32, [P, P, P, i64, i64, i32, P, i64, f64, P, P, P]),
         "oracle_adjoint_w": (i32, [P, P, P, i64, i64, i32, P, P, P, i64, f64, P, P, P, P]),
         "oracle_power_rho": (f64, [P, P, P, i64, i64, i32, P, i32]),
+        "oracle_weights_dir": (i64, [P, i64, i32, P, i64, i32, i32, P, P, P]),
+        "oracle_solve_mixed": (i32, [P, P, P, i64, i64, i32, P, P, P, P, i64, i32, P, P, f64,
+                                     i64, f64, P, P]),
         "oracle_gepp_dense": (i32, [i32, P, P, P]),
         "oracle_num_threads": (i32, []),
     }
@@ -131,12 +138,29 @@ def _knn(fn, xyz, centres, n):
     return idx
 
 
-def knn_brute(xyz, centres, n):
-    """n nearest nodes of every centre by the key (d^2, index), centre first."""
+def _knn_masked(fn, xyz, cand, centres, n):
+    xyz = _c(xyz, np.float64)
+    d, N = xyz.shape
+    cand = _c(cand, np.uint8)
+    centres = _c(centres, np.int32)
+    idx = np.zeros((len(centres), n), np.int32)
+    st = fn(_p(xyz), N, d, _p(cand), _p(centres), len(centres), n, _p(idx))
+    if st != 0:
+        raise ValueError(f"oracle knn failed ({st})")
+    return idx
+
+
+def knn_brute(xyz, centres, n, cand=None):
+    """n nearest nodes of every centre by the key (d^2, index), centre first.
+    With ``cand`` only nodes with cand != 0 (and the centre) are candidates."""
+    if cand is not None:
+        return _knn_masked(_load().oracle_knn_brute_masked, xyz, cand, centres, n)
     return _knn(_load().oracle_knn_brute, xyz, centres, n)
 
 
-def knn_kdtree(xyz, centres, n):
+def knn_kdtree(xyz, centres, n, cand=None):
+    if cand is not None:
+        return _knn_masked(_load().oracle_knn_kdtree_masked, xyz, cand, centres, n)
     return _knn(_load().oracle_knn_kdtree, xyz, centres, n)
 
 
@@ -160,6 +184,42 @@ def weights(xyz, idx, m: int):
     st = np.zeros(rows, np.int8)
     _load().oracle_weights(_p(xyz), N, d, _p(idx), rows, n, m, _p(w), _p(st))
     return w, st
+
+
+def weights_dir(xyz, idx, m: int, dirs):
+    """RBF-FD weights of the derivative along the unit vectors dirs [rows, d]."""
+    xyz = _c(xyz, np.float64)
+    d, N = xyz.shape
+    idx = _c(idx, np.int32)
+    dirs = _c(dirs, np.float64)
+    rows, n = idx.shape
+    w = np.zeros((rows, n), np.float64)
+    st = np.zeros(rows, np.int8)
+    _load().oracle_weights_dir(_p(xyz), N, d, _p(idx), rows, n, m, _p(dirs), _p(w), _p(st))
+    return w, st
+
+
+def solve_mixed(w, idx, interior, f, nnode, nidx, nw, g, u0, dt, max_steps, tol):
+    """Eq. 6 with Neumann nodes updated from the previous iterate before each step.
+
+    Returns (u, steps, final max-residual, status)."""
+    w = _c(w, np.float64)
+    idx = _c(idx, np.int32)
+    interior = _c(interior, np.int32)
+    f = _c(f, np.float64)
+    nnode = _c(nnode, np.int32)
+    nidx = _c(nidx, np.int32)
+    nw = _c(nw, np.float64)
+    g = _c(g, np.float64)
+    u = np.array(u0, dtype=np.float64, copy=True)
+    rows, n = idx.shape
+    NN, nn = nidx.shape
+    steps = ctypes.c_int64(0)
+    res = ctypes.c_double(0.0)
+    st = _load().oracle_solve_mixed(_p(w), _p(idx), _p(interior), len(u), rows, n, _p(f),
+                                    _p(nnode), _p(nidx), _p(nw), NN, nn, _p(g), _p(u), dt,
+                                    max_steps, tol, ctypes.byref(steps), ctypes.byref(res))
+    return u, int(steps.value), float(res.value), int(st)
 
 
 def apply(w, idx, u):

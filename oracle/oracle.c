@@ -24,8 +24,10 @@
  *   oracle_weights     RBF-FD augmented system of Eq. 2-3, phi(r)=r^3,
  *                      monomials up to order m, Gaussian elimination with
  *                      partial pivoting in FP64
+ *   oracle_weights_dir the same system for a directional (normal) derivative
  *   oracle_apply       Eq. 1 (stencil operator as a weighted sum)
  *   oracle_solve_explicit  Jacobi-style explicit step, Eq. 6 (jacobi_step)
+ *   oracle_solve_mixed the same with Neumann boundary nodes (Sec. II-C)
  *   oracle_solve_dc    Eq. 6 with an FP32 inner iteration on the correction
  *                      inside an FP64 defect-correction loop (paper silent)
  *   oracle_adjoint     transpose of Eq. 6 for a sensor misfit (paper silent)
@@ -123,13 +125,18 @@ static int64_t disk_nb(int Kg)
     return (int64_t)floor((two_pi * 0.5) / h + 0.5);
 }
 
+/* shape 2 (half cube [0, 1/2]^d, the mixed-boundary variant of Sec. II-C):  */
+/*   spacing h = 0.5/Kg; a node with an index 0 is a Dirichlet node (code 1)   */
+/*   at (i*h); otherwise a node with an index Kg is a Neumann node (code 2),   */
+/*   whose Kg coordinates are exactly 1/2 and the others i*h; interior nodes   */
+/*   are jittered as in shape 0.                                               */
 /* returns the node count; writes at most cap nodes (SoA, xyz[axis*cap + i]) */
 int64_t oracle_nodes(int d, int shape, int Kg, double jf, uint64_t seed,
                      double* xyz, uint8_t* is_bnd, int64_t cap)
 {
-    if (d < 1 || d > 3 || Kg < 2) return -1;
+    if (d < 1 || d > 3 || Kg < 2 || shape < 0 || shape > 2) return -1;
     if (shape == 1 && d != 2) return -1;
-    double h = 1.0 / (double)Kg;
+    double h = (shape == 2 ? 0.5 : 1.0) / (double)Kg;
     double amp = jf * h;
     int64_t side = (int64_t)Kg + 1;
     int64_t total = 1;
@@ -140,12 +147,17 @@ int64_t oracle_nodes(int d, int shape, int Kg, double jf, uint64_t seed,
         int64_t gi[3] = {0, 0, 0};
         int64_t rem = lin;
         for (int a = d - 1; a >= 0; --a) { gi[a] = rem % side; rem /= side; }
-        int bnd = 0;
-        for (int a = 0; a < d; ++a)
+        int bnd = 0, lo = 0;
+        for (int a = 0; a < d; ++a) {
             if (gi[a] == 0 || gi[a] == Kg) bnd = 1;
+            if (gi[a] == 0) lo = 1;
+        }
         double p[3];
         if (shape == 0 && bnd) {
             for (int a = 0; a < d; ++a) p[a] = (double)gi[a] * h;
+        } else if (shape == 2 && bnd) {
+            for (int a = 0; a < d; ++a) p[a] = (gi[a] == Kg) ? 0.5 : (double)gi[a] * h;
+            bnd = lo ? 1 : 2;
         } else {
             for (int a = 0; a < d; ++a) {
                 double U = u01(seed, (uint64_t)lin * (uint64_t)d + (uint64_t)a);
@@ -219,8 +231,19 @@ static void topn_insert(double* bd, int32_t* bj, int* len, int n, double dd, int
 
 /* Support of each centre: the n nodes with the smallest (d2, index) key,    */
 /* listed in increasing key order, so the centre itself comes first.          */
+/* cand (may be NULL): only nodes with cand[j] != 0 are candidates, besides
+ * the centre itself, which is always its own first support node */
+int oracle_knn_brute_masked(const double* xyz, int64_t N, int d, const uint8_t* cand,
+                            const int32_t* centres, int64_t nc, int n, int32_t* idx);
+
 int oracle_knn_brute(const double* xyz, int64_t N, int d, const int32_t* centres,
                      int64_t nc, int n, int32_t* idx)
+{
+    return oracle_knn_brute_masked(xyz, N, d, NULL, centres, nc, n, idx);
+}
+
+int oracle_knn_brute_masked(const double* xyz, int64_t N, int d, const uint8_t* cand,
+                            const int32_t* centres, int64_t nc, int n, int32_t* idx)
 {
     if (n < 1 || n > N) return -1;
     int bad = 0;
@@ -233,7 +256,9 @@ int oracle_knn_brute(const double* xyz, int64_t N, int d, const int32_t* centres
         int len = 0;
         if (!bd) { bad = 1; continue; }
         for (int64_t j = 0; j < N; ++j)
-            topn_insert(bd, idx + r * n, &len, n, dist2(xyz, N, d, j, q), j);
+            if (!cand || cand[j] || j == c)
+                topn_insert(bd, idx + r * n, &len, n, dist2(xyz, N, d, j, q), j);
+        if (len < n) bad = 1;
         free(bd);
     }
     return bad ? -2 : 0;
@@ -251,6 +276,8 @@ typedef struct {
     const double* xyz;
     int64_t N;
     int d;
+    const uint8_t* cand;
+    int64_t self;
     int64_t* perm;
     kd_node* nodes;
     int64_t count;
@@ -303,6 +330,7 @@ static void kd_query(const kd_tree* t, int64_t ni, const double* q, double* bd,
     if (nd->axis < 0) {
         for (int64_t p = nd->lo; p < nd->hi; ++p) {
             int64_t j = t->perm[p];
+            if (t->cand && !t->cand[j] && j != t->self) continue;
             topn_insert(bd, bj, len, n, dist2(t->xyz, t->N, t->d, j, q), j);
         }
         return;
@@ -315,14 +343,25 @@ static void kd_query(const kd_tree* t, int64_t ni, const double* q, double* bd,
     if (*len < n || !(lb > bd[n - 1])) kd_query(t, far, q, bd, bj, len, n);
 }
 
+int oracle_knn_kdtree_masked(const double* xyz, int64_t N, int d, const uint8_t* cand,
+                             const int32_t* centres, int64_t nc, int n, int32_t* idx);
+
 int oracle_knn_kdtree(const double* xyz, int64_t N, int d, const int32_t* centres,
                       int64_t nc, int n, int32_t* idx)
+{
+    return oracle_knn_kdtree_masked(xyz, N, d, NULL, centres, nc, n, idx);
+}
+
+int oracle_knn_kdtree_masked(const double* xyz, int64_t N, int d, const uint8_t* cand,
+                             const int32_t* centres, int64_t nc, int n, int32_t* idx)
 {
     if (n < 1 || n > N) return -1;
     kd_tree t;
     t.xyz = xyz;
     t.N = N;
     t.d = d;
+    t.cand = cand;
+    t.self = -1;
     t.perm = (int64_t*)malloc(sizeof(int64_t) * (size_t)N);
     t.nodes = (kd_node*)malloc(sizeof(kd_node) * (size_t)(2 * N / 4 + 64));
     t.count = 0;
@@ -338,7 +377,10 @@ int oracle_knn_kdtree(const double* xyz, int64_t N, int d, const int32_t* centre
         double* bd = (double*)malloc(sizeof(double) * (size_t)n);
         if (!bd) { bad = 1; continue; }
         int len = 0;
-        kd_query(&t, 0, q, bd, idx + r * n, &len, n);
+        kd_tree tl = t;      /* per-centre copy: the centre is always a candidate */
+        tl.self = c;
+        kd_query(&tl, 0, q, bd, idx + r * n, &len, n);
+        if (len < n) bad = 1;
         free(bd);
     }
     free(t.perm);
@@ -451,9 +493,23 @@ int oracle_gepp_solve(int s, double* G, double* x)
     return 0;
 }
 
-/* one stencil; xyz is SoA with stride N; sup holds n node indices */
+/* one stencil; xyz is SoA with stride N; sup holds n node indices.
+ * op 0: Laplacian (Eq. 2-3 as above).  op 1: derivative along the unit vector
+ * dir (the normal derivative of a Neumann condition): (L Phi)_j = grad of
+ * r^3 about x_j at x_c along dir = 3 |x_c - x_j| (x_c - x_j).dir, i.e.
+ * -3 |xi_j| (xi_j . dir) in scaled coordinates; (L p)_a = dir component for
+ * the degree-1 monomials, 0 otherwise; w_j = x_j / sigma. */
+int oracle_weights_op(const double* xyz, int64_t N, int d, const int32_t* sup, int n, int m,
+                      int op, const double* dir, double* w_out);
+
 int oracle_weights_one(const double* xyz, int64_t N, int d, const int32_t* sup, int n,
                        int m, double* w_out)
+{
+    return oracle_weights_op(xyz, N, d, sup, n, m, 0, NULL, w_out);
+}
+
+int oracle_weights_op(const double* xyz, int64_t N, int d, const int32_t* sup, int n, int m,
+                      int op, const double* dir, double* w_out)
 {
     int ex[3 * 400];
     if (oracle_num_monomials(d, m) > 400) return 2;
@@ -509,18 +565,34 @@ int oracle_weights_one(const double* xyz, int64_t N, int d, const int32_t* sup, 
             double sq = xi[3 * j + a] * xi[3 * j + a];
             rc2 = (a == 0) ? sq : rc2 + sq;
         }
-        G[(int64_t)j * W + s] = (double)(3 * (d + 1)) * sqrt(rc2);
+        if (op == 0) {
+            G[(int64_t)j * W + s] = (double)(3 * (d + 1)) * sqrt(rc2);
+        } else {
+            double dot = 0.0;
+            for (int a = 0; a < d; ++a) {
+                double t = xi[3 * j + a] * dir[a];
+                dot = (a == 0) ? t : dot + t;
+            }
+            G[(int64_t)j * W + s] = -((3.0 * sqrt(rc2)) * dot);
+        }
     }
     for (int al = 0; al < M; ++al) {
         int deg = ex[3 * al] + ex[3 * al + 1] + ex[3 * al + 2];
-        int pure2 = (deg == 2) && (ex[3 * al] == 2 || ex[3 * al + 1] == 2 || ex[3 * al + 2] == 2);
-        G[(int64_t)(n + al) * W + s] = pure2 ? 2.0 : 0.0;
+        double v = 0.0;
+        if (op == 0) {
+            int pure2 = (deg == 2) && (ex[3 * al] == 2 || ex[3 * al + 1] == 2 || ex[3 * al + 2] == 2);
+            v = pure2 ? 2.0 : 0.0;
+        } else if (deg == 1) {
+            for (int a = 0; a < d; ++a)
+                if (ex[3 * al + a] == 1) v = dir[a];
+        }
+        G[(int64_t)(n + al) * W + s] = v;
     }
 
     int st = oracle_gepp_solve(s, G, x);
     if (st == 0) {
-        double sig2 = sigma * sigma;
-        for (int j = 0; j < n; ++j) w_out[j] = x[j] / sig2;
+        double scale = (op == 0) ? sigma * sigma : sigma;
+        for (int j = 0; j < n; ++j) w_out[j] = x[j] / scale;
     }
     free(xi);
     free(G);
@@ -537,6 +609,23 @@ int64_t oracle_weights(const double* xyz, int64_t N, int d, const int32_t* idx, 
 #pragma omp parallel for schedule(dynamic, 64) reduction(+ : bad)
     for (int64_t r = 0; r < nc; ++r) {
         int st = oracle_weights_one(xyz, N, d, idx + r * n, n, m, w + r * n);
+        status[r] = (int8_t)st;
+        if (st) {
+            bad += 1;
+            for (int j = 0; j < n; ++j) w[r * n + j] = 0.0;
+        }
+    }
+    return bad;
+}
+
+/* directional-derivative weights for each row; dirs [nc][d] unit vectors */
+int64_t oracle_weights_dir(const double* xyz, int64_t N, int d, const int32_t* idx, int64_t nc,
+                           int n, int m, const double* dirs, double* w, int8_t* status)
+{
+    int64_t bad = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : bad)
+    for (int64_t r = 0; r < nc; ++r) {
+        int st = oracle_weights_op(xyz, N, d, idx + r * n, n, m, 1, dirs + r * d, w + r * n);
         status[r] = (int8_t)st;
         if (st) {
             bad += 1;
@@ -604,6 +693,66 @@ int oracle_solve_explicit(const double* w, const int32_t* idx, const int32_t* in
     }
     if (cur != u) memcpy(u, cur, sizeof(double) * (size_t)N);
     free(v);
+    *steps_out = k;
+    *res_out = R;
+    return status;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Eq. 6 with Neumann boundary nodes (mixed-boundary variant, Sec. II-C).    */
+/* Before each step the value of every Neumann node b is set so that its    */
+/* normal-derivative stencil (support nidx[b][0..nn), nidx[b][0] = b, weights */
+/* nw) meets the Neumann data g_b, using the previous iterate for the other  */
+/* support nodes:  acc = fma-chain_{j>=1} nw_bj u_j,  u_b = (g_b - acc)/nw_b0 */
+/* (all Neumann values from the same previous iterate).  Then the interior   */
+/* step of oracle_solve_explicit runs on the updated values; the stop rule,  */
+/* statuses and outputs are the same.                                        */
+/* ------------------------------------------------------------------------- */
+int oracle_solve_mixed(const double* w, const int32_t* idx, const int32_t* interior, int64_t N,
+                       int64_t NI, int n, const double* f, const int32_t* nnode,
+                       const int32_t* nidx, const double* nw, int64_t NN, int nn,
+                       const double* g, double* u, double dt, int64_t max_steps, double tol,
+                       int64_t* steps_out, double* res_out)
+{
+    double* v = (double*)malloc(sizeof(double) * (size_t)N);
+    double* un = (double*)malloc(sizeof(double) * (size_t)(NN > 0 ? NN : 1));
+    if (!v || !un) { free(v); free(un); return -2; }
+    memcpy(v, u, sizeof(double) * (size_t)N);
+    double* cur = u;
+    double* nxt = v;
+    int status = 1;
+    int64_t k = 0;
+    double R = 0.0;
+    for (k = 0; k < max_steps; ++k) {
+        for (int64_t b = 0; b < NN; ++b) {
+            double acc = 0.0;
+            for (int j = 1; j < nn; ++j) acc = fma(nw[b * nn + j], cur[nidx[b * nn + j]], acc);
+            un[b] = (g[b] - acc) / nw[b * nn];
+        }
+        for (int64_t b = 0; b < NN; ++b) {
+            cur[nnode[b]] = un[b];
+            nxt[nnode[b]] = un[b];
+        }
+        R = 0.0;
+        int nonfinite = 0;
+#pragma omp parallel for schedule(static) reduction(max : R) reduction(| : nonfinite)
+        for (int64_t r = 0; r < NI; ++r) {
+            double acc = 0.0;
+            for (int j = 0; j < n; ++j) acc = fma(w[r * n + j], cur[idx[r * n + j]], acc);
+            double ri = acc - f[r];
+            int64_t i = interior[r];
+            nxt[i] = fma(dt, ri, cur[i]);
+            double a = fabs(ri);
+            if (!isfinite(a)) nonfinite = 1;
+            else if (a > R) R = a;
+        }
+        double* t = cur; cur = nxt; nxt = t;
+        if (nonfinite) { status = 2; R = INFINITY; ++k; break; }
+        if (R < tol) { status = 0; ++k; break; }
+    }
+    if (cur != u) memcpy(u, cur, sizeof(double) * (size_t)N);
+    free(v);
+    free(un);
     *steps_out = k;
     *res_out = R;
     return status;

@@ -49,6 +49,7 @@ EXPORTED = [
     "rbffd_adjoint", "rbffd_plan_stats", "rbffd_knn_noalloc", "rbffd_batch_create",
     "rbffd_batch_destroy", "rbffd_solve_batch", "rbffd_batch_set_shape", "rbffd_batch_stats",
     "rbffd_error", "rbffd_batch_domain_times", "rbffd_batch_set_costs", "rbffd_adjoint_w",
+    "rbffd_knn_masked", "rbffd_weights_dir", "rbffd_plan_set_neumann",
 ]
 RBFFD_KNN_NOALLOC_MAX_NODES = 262144
 
@@ -103,6 +104,9 @@ def lib():
         "rbffd_batch_domain_times": (I, [P, P, P, P, P]),
         "rbffd_batch_set_costs": (I, [P, P]),
         "rbffd_adjoint_w": (I, [P, P, P, I64, P, I64, D, P, P, P, P, P]),
+        "rbffd_knn_masked": (I, [P, I64, I, P, P, I64, I, P, P]),
+        "rbffd_weights_dir": (I, [P, I64, I, P, I64, I, I, P, P, P, PI64, PI64, P]),
+        "rbffd_plan_set_neumann": (I, [P, I64, P, P, P, I, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -171,6 +175,38 @@ def rbffd_knn(xyz: torch.Tensor, centres: torch.Tensor, n: int) -> torch.Tensor:
     _check(lib().rbffd_knn(_ptr(xyz), N, d, _ptr(centres), centres.numel(), n, _ptr(idx),
                            _stream(xyz.device)))
     return idx
+
+
+def rbffd_knn_masked(xyz: torch.Tensor, cand: torch.Tensor, centres: torch.Tensor,
+                     n: int) -> torch.Tensor:
+    """rbffd_knn over candidate nodes only (cand != 0), the centre always first."""
+    xyz = _dev(xyz, torch.float64, "xyz")
+    cand = _dev(cand, torch.uint8, "cand")
+    centres = _dev(centres, torch.int32, "centres")
+    d, N = xyz.shape
+    idx = torch.empty((centres.numel(), n), dtype=torch.int32, device=xyz.device)
+    _check(lib().rbffd_knn_masked(_ptr(xyz), N, d, _ptr(cand), _ptr(centres), centres.numel(), n,
+                                  _ptr(idx), _stream(xyz.device)))
+    return idx
+
+
+def rbffd_weights_dir(xyz: torch.Tensor, idx: torch.Tensor, m: int, dirs: torch.Tensor,
+                      check: bool = True):
+    """RBF-FD weights of the derivative along dirs [rows, d] (unit vectors)."""
+    xyz = _dev(xyz, torch.float64, "xyz")
+    idx = _dev(idx, torch.int32, "idx")
+    dirs = _dev(dirs, torch.float64, "dirs")
+    d, N = xyz.shape
+    rows, n = idx.shape
+    w = torch.empty((rows, n), dtype=torch.float64, device=xyz.device)
+    st = torch.empty(rows, dtype=torch.int8, device=xyz.device)
+    nbad = ctypes.c_int64(0)
+    first = ctypes.c_int64(0)
+    code = lib().rbffd_weights_dir(_ptr(xyz), N, d, _ptr(idx), rows, n, m, _ptr(dirs), _ptr(w),
+                                   _ptr(st), ctypes.byref(nbad), ctypes.byref(first),
+                                   _stream(xyz.device))
+    _check(code, (RBFFD_OK,) if check else (RBFFD_OK, RBFFD_ERR_SINGULAR))
+    return w, st
 
 
 def rbffd_knn_noalloc(xyz: torch.Tensor, centres: torch.Tensor, idx: torch.Tensor) -> torch.Tensor:
@@ -320,6 +356,16 @@ class Plan:
         _check(lib().rbffd_plan_stats(self.handle, ctypes.byref(ms), ctypes.byref(steps),
                                       ctypes.byref(launches), shape))
         return ms.value, steps.value, launches.value, list(shape)
+
+    def set_neumann(self, nodes, idx, w, g=None):
+        """Neumann nodes (ids [NN]), their supports idx [NN, nn] (node first) and
+        normal-derivative weights w [NN, nn]; data g [NN] (default 0)."""
+        nodes = _dev(nodes, torch.int32, "nodes")
+        idx = _dev(idx, torch.int32, "idx")
+        w = _dev(w, torch.float64, "w")
+        g = _dev(g, torch.float64, "g") if g is not None else None
+        _check(lib().rbffd_plan_set_neumann(self.handle, nodes.numel(), _ptr(nodes), _ptr(idx),
+                                            _ptr(w), idx.shape[1], _ptr(g), _stream(self.device)))
 
     def set_dc(self, K_in, rho_in):
         _check(lib().rbffd_plan_set_dc(self.handle, int(K_in), float(rho_in)))

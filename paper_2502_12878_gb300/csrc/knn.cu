@@ -42,6 +42,7 @@ struct KnnArgs {
     GridGeom g;
     const int32_t* cell_start;
     const int32_t* sorted;
+    const uint8_t* cand;   // NULL, or only nodes with cand != 0 (and the centre) qualify
     int r0;
     int* err;
 };
@@ -172,6 +173,7 @@ __global__ void __launch_bounds__(32 * KNN_WARPS) knn_kernel(KnnArgs A) {
                         jv = A.sorted[sm.rb[k] + off];
                         dv = sqdist(A.xyz, A.N, d, jv, q);
                         acc = (nb < n) || kless(dv, jv, sm.bd[cur][n - 1], sm.bj[cur][n - 1]);
+                        if (A.cand && !A.cand[jv] && jv != c) acc = false;
                     }
                     unsigned m = __ballot_sync(0xffffffffu, acc);
                     if (acc) {
@@ -219,6 +221,7 @@ __global__ void __launch_bounds__(32 * KNN_WARPS) knn_kernel(KnnArgs A) {
             }
         }
         if (!done && lane == 0) atomicExch(A.err, 1);
+        if (done && nb < n && lane == 0) atomicExch(A.err, 2);   // too few candidates
         __syncwarp();
         for (int k = lane; k < n; k += 32)
             A.idx[qi * n + k] = k < nb ? sm.bj[cur][k] : -1;
@@ -230,9 +233,8 @@ __global__ void __launch_bounds__(32 * KNN_WARPS) knn_kernel(KnnArgs A) {
 
 using namespace rbffd;
 
-extern "C" int rbffd_knn(const double* xyz, int64_t N, int d, const int32_t* centres, int64_t nc,
-                         int n, int32_t* idx, void* stream) {
-    clear_error();
+static int knn_impl(const double* xyz, int64_t N, int d, const uint8_t* cand,
+                    const int32_t* centres, int64_t nc, int n, int32_t* idx, void* stream) {
     RBFFD_ARG(nc >= 0, "rbffd_knn: negative centre count");
     if (nc == 0) return RBFFD_OK;
     RBFFD_ARG(xyz && centres && idx, "rbffd_knn: NULL argument");
@@ -268,6 +270,7 @@ extern "C" int rbffd_knn(const double* xyz, int64_t N, int d, const int32_t* cen
     A.g = g;
     A.cell_start = start.as<int32_t>();
     A.sorted = sorted.as<int32_t>();
+    A.cand = cand;
     A.r0 = (int)ceil(rad) > 1 ? (int)ceil(rad) : 1;
     A.err = err.as<int>();
     int sms = device_sm_count();
@@ -278,12 +281,32 @@ extern "C" int rbffd_knn(const double* xyz, int64_t N, int d, const int32_t* cen
     int herr = 0;
     RBFFD_CHECK_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     RBFFD_CHECK_CUDA(cudaStreamSynchronize(s));
+    if (herr == 2) {
+        set_error("rbffd_knn: fewer than n candidate nodes");
+        return RBFFD_ERR_ARG;
+    }
     if (herr) {
         set_error("rbffd_knn: ring search did not terminate");
         return RBFFD_ERR_CAPACITY;
     }
     return RBFFD_OK;
 }
+
+extern "C" int rbffd_knn(const double* xyz, int64_t N, int d, const int32_t* centres, int64_t nc,
+                         int n, int32_t* idx, void* stream) {
+    clear_error();
+    return knn_impl(xyz, N, d, nullptr, centres, nc, n, idx, stream);
+}
+
+extern "C" int rbffd_knn_masked(const double* xyz, int64_t N, int d, const uint8_t* cand,
+                                const int32_t* centres, int64_t nc, int n, int32_t* idx,
+                                void* stream) {
+    clear_error();
+    RBFFD_ARG(cand != nullptr || nc == 0, "rbffd_knn_masked: NULL candidate mask");
+    return knn_impl(xyz, N, d, cand, centres, nc, n, idx, stream);
+}
+
+
 
 // ---------------------------------------------------------------------------
 // rbffd_knn_noalloc: the same support selection for callers that cannot
@@ -417,6 +440,7 @@ extern "C" int rbffd_knn_noalloc(const double* xyz, int64_t N, int d, const int3
     A.g = g;
     A.cell_start = start;
     A.sorted = sorted;
+    A.cand = nullptr;
     A.r0 = (int)ceil(rad) > 1 ? (int)ceil(rad) : 1;
     A.err = err;
     int64_t blocks = (nc + KNN_WARPS - 1) / KNN_WARPS;

@@ -30,7 +30,9 @@ struct NodeGen {
     int64_t side;
 };
 
-// position of generator point `lin`; returns the boundary flag of the cube rule
+// position of generator point `lin`; returns the boundary code: 0 interior,
+// 1 Dirichlet (any index 0, or any index Kg in the unit cube), 2 Neumann
+// (half cube: an index Kg and no index 0; those coordinates are exactly 1/2)
 __device__ int grid_point(const NodeGen& g, int64_t lin, double* p) {
     int64_t gi[3] = {0, 0, 0};
     int64_t rem = lin;
@@ -38,13 +40,18 @@ __device__ int grid_point(const NodeGen& g, int64_t lin, double* p) {
         gi[a] = rem % g.side;
         rem /= g.side;
     }
-    int bnd = 0;
-    for (int a = 0; a < g.d; ++a)
+    int bnd = 0, lo = 0;
+    for (int a = 0; a < g.d; ++a) {
         if (gi[a] == 0 || gi[a] == g.Kg) bnd = 1;
+        if (gi[a] == 0) lo = 1;
+    }
+    if (g.shape == 2 && bnd) bnd = lo ? 1 : 2;
     for (int a = 0; a < g.d; ++a) {
         double base = __dmul_rn((double)gi[a], g.h);
         if (g.shape == 0 && bnd) {
             p[a] = base;
+        } else if (g.shape == 2 && bnd) {
+            p[a] = gi[a] == g.Kg ? 0.5 : base;
         } else {
             double U = unit_draw(g.seed, (uint64_t)lin * (uint64_t)g.d + (uint64_t)a);
             double t = __dsub_rn(__dmul_rn(2.0, U), 1.0);
@@ -154,8 +161,9 @@ extern "C" int rbffd_nodes(int d, int shape, int Kg, double jitter_frac, uint64_
                            void* stream) {
     clear_error();
     RBFFD_ARG(h_n_out != nullptr, "rbffd_nodes: h_n_out is NULL");
-    RBFFD_ARG(shape == 0 || shape == 1, "rbffd_nodes: shape must be 0 (cube) or 1 (disk)");
-    RBFFD_ARG(shape == 0 ? (d >= 1 && d <= 3) : d == 2, "rbffd_nodes: bad dimension %d", d);
+    RBFFD_ARG(shape >= 0 && shape <= 2,
+              "rbffd_nodes: shape must be 0 (cube), 1 (disk) or 2 (half cube)");
+    RBFFD_ARG(shape != 1 ? (d >= 1 && d <= 3) : d == 2, "rbffd_nodes: bad dimension %d", d);
     RBFFD_ARG(Kg >= 2 && Kg <= (1 << 20), "rbffd_nodes: Kg must be in [2, 2^20]");
     RBFFD_ARG(jitter_frac >= 0.0 && jitter_frac < 0.5, "rbffd_nodes: jitter_frac in [0, 0.5)");
     RBFFD_ARG(cap >= 0, "rbffd_nodes: negative capacity");
@@ -164,7 +172,7 @@ extern "C" int rbffd_nodes(int d, int shape, int Kg, double jitter_frac, uint64_
     g.d = d;
     g.shape = shape;
     g.Kg = Kg;
-    g.h = 1.0 / (double)Kg;
+    g.h = (shape == 2 ? 0.5 : 1.0) / (double)Kg;
     g.amp = jitter_frac * g.h;
     g.seed = seed;
     g.side = (int64_t)Kg + 1;
@@ -172,7 +180,7 @@ extern "C" int rbffd_nodes(int d, int shape, int Kg, double jitter_frac, uint64_
     for (int a = 0; a < d; ++a) total *= g.side;
     RBFFD_ARG(total < (int64_t(1) << 31), "rbffd_nodes: more than 2^31 grid points");
     int sms = device_sm_count();
-    if (shape == 0) {
+    if (shape != 1) {
         *h_n_out = total;
         if (cap == 0) return RBFFD_OK;
         if (total > cap) {

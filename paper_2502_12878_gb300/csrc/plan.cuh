@@ -76,4 +76,14 @@ struct rbffd_plan {
     long long last_loop_steps = 0;
     long long last_launches = 0;
     rbffd::Transpose* tr = nullptr;
+    // Neumann boundary nodes (mixed-boundary variant): slots, supports (slots),
+    // normal-derivative weights, data, scratch for the new values
+    int64_t NN = 0;
+    int nn = 0;
+    int32_t* nslot = nullptr;
+    int32_t* ncol = nullptr;
+    double* nw = nullptr;
+    double* ng = nullptr;
+    double* ng0 = nullptr;          // zeros (homogeneous data, for the power iteration)
+    double* uN = nullptr;
 };

@@ -563,6 +563,55 @@ __global__ void scatter_u(const double* us, const int32_t* perm, int64_t NI, dou
         u[perm[p]] = us[p];
 }
 
+// ---------------------------------------------------- Neumann boundary nodes
+// Before each step, every Neumann node b takes the value that meets its
+// normal-derivative condition with the previous iterate of its other support
+// nodes: acc = fma-chain_{j>=1} nw_bj u_j, u_b = (g_b - acc) / nw_b0.  Two
+// kernels (new values into uN, then into both iterate buffers), so supports
+// that contain other Neumann nodes read their previous values.
+__global__ void neumann_update(const int32_t* __restrict__ ncol, const double* __restrict__ nw,
+                               const double* __restrict__ ng, int64_t NN, int nn,
+                               const double* u0, const double* u1, double* uN, StepCtrl* c) {
+    __shared__ int s_skip, s_par;
+    if (threadIdx.x == 0) {
+        volatile StepCtrl* vc = c;
+        s_skip = c ? ((vc->done != DONE_RUNNING) || (vc->k >= vc->max_steps)) : 0;
+        s_par = c ? (int)(vc->k & 1) : 0;
+    }
+    __syncthreads();
+    if (s_skip) return;
+    const double* uin = s_par ? u1 : u0;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < NN;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int j = 1; j < nn; ++j) acc = __fma_rn(nw[b * nn + j], uin[ncol[b * nn + j]], acc);
+        uN[b] = __ddiv_rn(__dsub_rn(ng[b], acc), nw[b * nn]);
+    }
+}
+
+__global__ void neumann_scatter(const int32_t* __restrict__ nslot, const double* __restrict__ uN,
+                                int64_t NN, double* u0, double* u1, const StepCtrl* c) {
+    __shared__ int s_skip;
+    if (threadIdx.x == 0) {
+        const volatile StepCtrl* vc = c;
+        s_skip = c ? ((vc->done != DONE_RUNNING) || (vc->k >= vc->max_steps)) : 0;
+    }
+    __syncthreads();
+    if (s_skip) return;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < NN;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        u0[nslot[b]] = uN[b];
+        if (u1) u1[nslot[b]] = uN[b];
+    }
+}
+
+__global__ void neumann_out(const int32_t* nslot, const double* us, const int32_t* perm,
+                            int64_t NN, double* u) {
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < NN;
+         b += (int64_t)gridDim.x * blockDim.x)
+        u[perm[nslot[b]]] = us[nslot[b]];
+}
+
 // --------------------------------------------------------- DC kernels
 // d = W u - f (FP64 chain), d32 = (float) d; max |d| into *dmax (bits)
 template <int NN>
@@ -708,7 +757,8 @@ static StepArgs make_args(const rbffd_plan* p) {
 static void free_plan(rbffd_plan* p) {
     if (!p) return;
     void* bufs[] = {p->perm, p->inv, p->row_of_slot, p->w64, p->w32, p->col, p->u[0], p->u[1],
-                    p->fs, p->e[0], p->e[1], p->d32, p->scratch, p->ctrl};
+                    p->fs, p->e[0], p->e[1], p->d32, p->scratch, p->ctrl, p->nslot, p->ncol,
+                    p->nw, p->ng, p->ng0, p->uN};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (p->graph64) cudaGraphExecDestroy((cudaGraphExec_t)p->graph64);
@@ -836,7 +886,16 @@ static int ensure_graph(rbffd_plan* p, int mode, cudaStream_t s) {
     cudaGraph_t g;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        for (int i = 0; i < p->graph_chunk; ++i) fn<<<grid, STEP_THREADS, 0, cs>>>(A, p->ctrl);
+        const unsigned ng = (unsigned)std::max<int64_t>(1, std::min<int64_t>((p->NN + 255) / 256, 1024));
+        for (int i = 0; i < p->graph_chunk; ++i) {
+            if (mode == MODE_SWEEP64 && p->NN > 0) {
+                neumann_update<<<ng, 256, 0, cs>>>(p->ncol, p->nw, p->ng, p->NN, p->nn, p->u[0],
+                                                   p->u[1], p->uN, p->ctrl);
+                neumann_scatter<<<ng, 256, 0, cs>>>(p->nslot, p->uN, p->NN, p->u[0], p->u[1],
+                                                    p->ctrl);
+            }
+            fn<<<grid, STEP_THREADS, 0, cs>>>(A, p->ctrl);
+        }
         e = cudaStreamEndCapture(cs, &g);
     }
     if (e == cudaSuccess) {
@@ -858,7 +917,8 @@ static int run_steps(rbffd_plan* p, int mode, double dt, double tol, long long m
     if (st) return st;
     StepCtrl h;
     if (max_steps > 0) {
-        bool persistent = (p->flags & RBFFD_LAUNCH_PERSISTENT) != 0;
+        // the persistent kernel has no Neumann phase: Neumann plans replay graphs
+        bool persistent = (p->flags & RBFFD_LAUNCH_PERSISTENT) != 0 && p->NN == 0;
         if (persistent) {
             const int mi = mode == MODE_SWEEP64 ? 0 : 1;
             if (!p->tuned[mi]) {
@@ -1185,6 +1245,7 @@ extern "C" int rbffd_solve_dc(rbffd_plan* p, const double* f, double* u, double 
     RBFFD_ARG(p && f && u, "rbffd_solve_dc: NULL argument");
     RBFFD_ARG(dt > 0.0 && isfinite(dt) && tol >= 0.0, "rbffd_solve_dc: bad dt / tol");
     RBFFD_ARG(max_outer >= 0 && K_in >= 1 && rho_in >= 0.0, "rbffd_solve_dc: bad loop limits");
+    RBFFD_ARG(p->NN == 0, "rbffd_solve_dc: plans with Neumann nodes use FP64 sweeps only");
     cudaStream_t s = as_stream(stream);
     int st = load_problem(p, f, u, s);
     if (st) return st;
@@ -1281,6 +1342,10 @@ extern "C" int rbffd_solve_explicit(rbffd_plan* p, const double* f, double* u, d
     int sms = device_sm_count();
     scatter_u<<<sms * 8, 256, 0, s>>>(p->u[steps & 1], p->perm, p->NI, u);
     p->last_launches += 1;
+    if (p->NN > 0) {
+        neumann_out<<<sms * 2, 256, 0, s>>>(p->nslot, p->u[steps & 1], p->perm, p->NN, u);
+        p->last_launches += 1;
+    }
     RBFFD_CHECK_CUDA(cudaGetLastError());
     RBFFD_CHECK_CUDA(cudaStreamSynchronize(s));
     if (h_steps_out) *h_steps_out = steps;
@@ -1319,6 +1384,12 @@ extern "C" int rbffd_stable_dt(rbffd_plan* p, const double* v0, int iters, doubl
     }
     const int grid = std::min(step_grid(p), nparts);
     for (int it = 0; it < iters; ++it) {
+        if (p->NN > 0) {   // Neumann values of v from its interior values (data 0)
+            const unsigned ngr = (unsigned)std::max<int64_t>(1, std::min<int64_t>((p->NN + 255) / 256, 1024));
+            neumann_update<<<ngr, 256, 0, s>>>(p->ncol, p->nw, p->ng0, p->NN, p->nn, v, v, p->uN,
+                                               nullptr);
+            neumann_scatter<<<ngr, 256, 0, s>>>(p->nslot, p->uN, p->NN, v, nullptr, nullptr);
+        }
         pf<<<grid, STEP_THREADS, 0, s>>>(A, v, y, part);
         sum_to_norm<<<1, 256, 0, s>>>(part, grid, nrm);
         power_scale<<<sms * 8, 256, 0, s>>>(nrm, y, v, p->NI);
@@ -1351,3 +1422,83 @@ extern "C" int rbffd_plan_stats(const rbffd_plan* p, double* h_loop_ms, int64_t*
     }
     return RBFFD_OK;
 }
+
+namespace rbffd {
+__global__ void neumann_map(const int32_t* nodes, const int32_t* idx, const double* w,
+                            const double* g, int64_t NN, int nn, int64_t NI, int64_t N,
+                            const int32_t* inv, int32_t* nslot, int32_t* ncol, double* nw,
+                            double* ng, double* ng0, int* err) {
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < NN;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        int32_t node = nodes[b];
+        if (node < 0 || node >= N || idx[b * nn] != node || inv[node] < NI) {
+            atomicExch(err, 1);   // not a boundary node, or not first in its support
+            continue;
+        }
+        nslot[b] = inv[node];
+        for (int j = 0; j < nn; ++j) {
+            int32_t q = idx[b * nn + j];
+            if (q < 0 || q >= N) {
+                atomicExch(err, 2);
+                q = node;
+            }
+            ncol[b * nn + j] = inv[q];
+            nw[b * nn + j] = w[b * nn + j];
+        }
+        ng[b] = g ? g[b] : 0.0;
+        ng0[b] = 0.0;
+    }
+}
+}  // namespace rbffd
+
+extern "C" int rbffd_plan_set_neumann(rbffd_plan* p, int64_t NN, const int32_t* nodes,
+                                      const int32_t* idx, const double* w, int nn, const double* g,
+                                      void* stream) {
+    clear_error();
+    RBFFD_ARG(p && NN >= 0 && (NN == 0 || (nodes && idx && w && nn >= 2)),
+              "rbffd_plan_set_neumann: bad argument");
+    cudaStream_t s = as_stream(stream);
+    void* old[] = {p->nslot, p->ncol, p->nw, p->ng, p->ng0, p->uN};
+    RBFFD_CHECK_CUDA(cudaStreamSynchronize(s));
+    for (void* o : old)
+        if (o) cudaFree(o);
+    p->nslot = p->ncol = nullptr;
+    p->nw = p->ng = p->ng0 = p->uN = nullptr;
+    p->NN = 0;
+    p->nn = 0;
+    // captured graphs include (or not) the Neumann phase: capture again
+    if (p->graph64) {
+        cudaGraphExecDestroy((cudaGraphExec_t)p->graph64);
+        p->graph64 = nullptr;
+    }
+    if (NN == 0) return RBFFD_OK;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc((void**)&p->nslot, sizeof(int32_t) * NN);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&p->ncol, sizeof(int32_t) * NN * nn);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&p->nw, sizeof(double) * NN * nn);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&p->ng, sizeof(double) * NN);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&p->ng0, sizeof(double) * NN);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&p->uN, sizeof(double) * NN);
+    RBFFD_CHECK_CUDA(e);
+    Scratch err;
+    RBFFD_CHECK_CUDA(err.alloc(sizeof(int), s));
+    RBFFD_CHECK_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+    int sms = device_sm_count();
+    neumann_map<<<sms * 2, 256, 0, s>>>(nodes, idx, w, g, NN, nn, p->NI, p->N, p->inv, p->nslot,
+                                        p->ncol, p->nw, p->ng, p->ng0, err.as<int>());
+    RBFFD_CHECK_CUDA(cudaGetLastError());
+    int herr = 0;
+    RBFFD_CHECK_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    RBFFD_CHECK_CUDA(cudaStreamSynchronize(s));
+    p->NN = NN;
+    p->nn = nn;
+    if (herr) {
+        set_error(herr == 1 ? "rbffd_plan_set_neumann: each Neumann node must be a boundary node "
+                              "and the first entry of its own support"
+                            : "rbffd_plan_set_neumann: support index out of range");
+        rbffd_plan_set_neumann(p, 0, nullptr, nullptr, nullptr, 0, nullptr, stream);
+        return RBFFD_ERR_ARG;
+    }
+    return RBFFD_OK;
+}
+

@@ -35,6 +35,8 @@ struct WeightArgs {
     int8_t* status;
     unsigned char ex[W_SMAX][3];   // monomial exponents, graded order
     double lap_phi;                // 3 (d + 1): Laplacian of r^3 is 3(d+1) r
+    int op;                        // 0 Laplacian, 1 derivative along dirs[row]
+    const double* dirs;            // [nc][d] unit vectors (op 1)
 };
 
 __device__ __forceinline__ double powi(double x, int e) {
@@ -179,18 +181,35 @@ __global__ void __launch_bounds__(256) weights_kernel(WeightArgs A, int teams_pe
             int a1 = e / M, a2 = e - a1 * M;
             G[(n + a1) * P + n + a2] = 0.0;
         }
+        const double* dir = A.op == 1 ? A.dirs + r * d : nullptr;
         for (int j = tid; j < n; j += T) {
             double rc2 = 0.0;
             for (int a = 0; a < d; ++a) {
                 double sq = __dmul_rn(xi[3 * j + a], xi[3 * j + a]);
                 rc2 = a == 0 ? sq : __dadd_rn(rc2, sq);
             }
-            G[j * P + s] = __dmul_rn(A.lap_phi, __dsqrt_rn(rc2));
+            if (A.op == 0) {
+                G[j * P + s] = __dmul_rn(A.lap_phi, __dsqrt_rn(rc2));
+            } else {
+                // derivative of r^3 about x_j at x_c along dir: -3 |xi_j| (xi_j . dir)
+                double dot = 0.0;
+                for (int a = 0; a < d; ++a) {
+                    double t = __dmul_rn(xi[3 * j + a], dir[a]);
+                    dot = a == 0 ? t : __dadd_rn(dot, t);
+                }
+                G[j * P + s] = -__dmul_rn(__dmul_rn(3.0, __dsqrt_rn(rc2)), dot);
+            }
         }
         for (int al = tid; al < M; al += T) {
             int e0 = A.ex[al][0], e1 = A.ex[al][1], e2 = A.ex[al][2];
-            bool pure2 = (e0 + e1 + e2 == 2) && (e0 == 2 || e1 == 2 || e2 == 2);
-            G[(n + al) * P + s] = pure2 ? 2.0 : 0.0;
+            double v;
+            if (A.op == 0) {
+                bool pure2 = (e0 + e1 + e2 == 2) && (e0 == 2 || e1 == 2 || e2 == 2);
+                v = pure2 ? 2.0 : 0.0;
+            } else {
+                v = (e0 + e1 + e2 == 1) ? (e0 ? dir[0] : (e1 ? dir[1] : dir[2])) : 0.0;
+            }
+            G[(n + al) * P + s] = v;
         }
         team_sync<TW>();
         // scale of the assembled matrix for the relative pivot test
@@ -266,8 +285,9 @@ __global__ void __launch_bounds__(256) weights_kernel(WeightArgs A, int teams_pe
                 team_sync<TW>();
             }
         }
-        const double sig2 = __dmul_rn(sig, sig);
-        for (int j = tid; j < n; j += T) A.w[r * n + j] = bad ? 0.0 : __ddiv_rn(G[j * P + s], sig2);
+        // the Laplacian scales as 1/sigma^2, a first derivative as 1/sigma
+        const double scl = A.op == 0 ? __dmul_rn(sig, sig) : sig;
+        for (int j = tid; j < n; j += T) A.w[r * n + j] = bad ? 0.0 : __ddiv_rn(G[j * P + s], scl);
         if (tid == 0) A.status[r] = (int8_t)bad;
         team_sync<TW>();
     }
@@ -306,10 +326,9 @@ static int graded_monomials(int d, int m, unsigned char ex[][3], int cap) {
 
 using namespace rbffd;
 
-extern "C" int rbffd_weights(const double* xyz, int64_t N, int d, const int32_t* idx, int64_t nc,
-                             int n, int m, double* w, int8_t* status, int64_t* h_n_bad,
-                             int64_t* h_first_bad, void* stream) {
-    clear_error();
+static int weights_impl(const double* xyz, int64_t N, int d, const int32_t* idx, int64_t nc,
+                        int n, int m, int op, const double* dirs, double* w, int8_t* status,
+                        int64_t* h_n_bad, int64_t* h_first_bad, void* stream) {
     if (nc == 0 && n >= 1) {
         if (h_n_bad) *h_n_bad = 0;
         if (h_first_bad) *h_first_bad = -1;
@@ -338,6 +357,8 @@ extern "C" int rbffd_weights(const double* xyz, int64_t N, int d, const int32_t*
     A.w = w;
     A.status = status;
     A.lap_phi = (double)(3 * (d + 1));
+    A.op = op;
+    A.dirs = dirs;
     const size_t per_team = sizeof(double) * ((size_t)A.s * A.pitch + 3 * (size_t)n);
     const int sms = device_sm_count();
     const bool big = A.s > 48;
@@ -374,3 +395,22 @@ extern "C" int rbffd_weights(const double* xyz, int64_t N, int d, const int32_t*
     }
     return RBFFD_OK;
 }
+
+extern "C" int rbffd_weights(const double* xyz, int64_t N, int d, const int32_t* idx, int64_t nc,
+                             int n, int m, double* w, int8_t* status, int64_t* h_n_bad,
+                             int64_t* h_first_bad, void* stream) {
+    clear_error();
+    return weights_impl(xyz, N, d, idx, nc, n, m, 0, nullptr, w, status, h_n_bad, h_first_bad,
+                        stream);
+}
+
+extern "C" int rbffd_weights_dir(const double* xyz, int64_t N, int d, const int32_t* idx,
+                                 int64_t nc, int n, int m, const double* dirs, double* w,
+                                 int8_t* status, int64_t* h_n_bad, int64_t* h_first_bad,
+                                 void* stream) {
+    clear_error();
+    RBFFD_ARG(dirs != nullptr || nc == 0, "rbffd_weights_dir: NULL directions");
+    return weights_impl(xyz, N, d, idx, nc, n, m, 1, dirs, w, status, h_n_bad, h_first_bad,
+                        stream);
+}
+

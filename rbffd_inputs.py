@@ -35,10 +35,20 @@ def source(xyz: np.ndarray, interior: np.ndarray) -> np.ndarray:
 
 
 def start_iterate(xyz: np.ndarray, is_bnd: np.ndarray) -> np.ndarray:
-    """u^0: Dirichlet data g = u^a on boundary nodes, 0 at interior nodes."""
+    """u^0: Dirichlet data g = u^a on Dirichlet nodes (code 1), 0 elsewhere (interior
+    nodes, and Neumann nodes, code 2, whose values the solver sets)."""
     u = exact_solution(xyz)
-    u[np.asarray(is_bnd) == 0] = 0.0
+    u[np.asarray(is_bnd) != 1] = 0.0
     return u
+
+
+def neumann_nodes(xyz: np.ndarray, is_bnd: np.ndarray):
+    """Neumann nodes (boundary code 2) of the half cube [0, 1/2]^d and their outward unit
+    normals: the normal of a face x_a = 1/2 is +e_a; nodes on several such faces take the
+    normalised sum.  Returns (node ids ascending, normals [NN, d])."""
+    ids = np.nonzero(np.asarray(is_bnd) == 2)[0].astype(np.int32)
+    on = (np.asarray(xyz)[:, ids] == 0.5).T.astype(np.float64)
+    return ids, on / np.sqrt(on.sum(axis=1, keepdims=True))
 
 
 def interior_ids(is_bnd: np.ndarray) -> np.ndarray:

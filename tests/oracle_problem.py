@@ -68,3 +68,35 @@ def dt_guideline(p: Problem, alpha=0.3) -> float:
 def dt_stable(orc, p: Problem, frac=0.9, seed=12345) -> float:
     """frac x the explicit-Euler bound 2/rho(W_II), rho from 200 power iterations x 1.05."""
     return frac * orc.stable_dt(p.w, p.idx, p.interior, p.N, gen.random_vector(p.NI, seed), 200)
+
+
+@dataclass
+class MixedProblem:
+    base: Problem
+    nnode: np.ndarray      # Neumann node ids
+    normals: np.ndarray
+    nidx: np.ndarray       # their supports
+    nw: np.ndarray         # their normal-derivative weights
+    g: np.ndarray          # Neumann data (du/dn = 0 on the faces at 1/2)
+
+
+def build_mixed(orc, d=2, Kg=12, m=2, seed=1, n=None, nn=None) -> MixedProblem:
+    """The mixed-boundary variant of Sec. II-C on the half cube [0, 1/2]^d."""
+    xyz, is_bnd = orc.nodes(d, 2, Kg, 0.3, seed)
+    interior = gen.interior_ids(is_bnd)
+    n = n or gen.stencil_size(d, m)
+    nn = nn or n
+    idx = orc.knn_kdtree(xyz, interior, n)
+    w, st = orc.weights(xyz, idx, m)
+    assert np.all(st == 0)
+    nnode, normals = gen.neumann_nodes(xyz, is_bnd)
+    # a Neumann node's support: itself and its nearest interior nodes (its value is
+    # set from interior values of the previous step, Sec. II-C)
+    nidx = orc.knn_kdtree(xyz, nnode, nn, cand=(is_bnd == 0).astype(np.uint8))
+    nw, st2 = orc.weights_dir(xyz, nidx, m, normals)
+    assert np.all(st2 == 0)
+    f = gen.source(xyz, interior)
+    u0 = gen.start_iterate(xyz, is_bnd)
+    ua = gen.exact_solution(xyz)
+    base = Problem(d, Kg, m, n, xyz, is_bnd, interior, idx, w, f, u0, ua)
+    return MixedProblem(base, nnode, normals, nidx, nw, np.zeros(len(nnode)))

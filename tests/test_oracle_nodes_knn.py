@@ -107,3 +107,23 @@ def test_knn_kdtree_large_sampled(orc):
     xyz, bnd = orc.nodes(2, 0, 300, 0.3, 4)
     centres = np.random.default_rng(0).choice(xyz.shape[1], 300, replace=False).astype(np.int32)
     assert np.array_equal(orc.knn_kdtree(xyz, centres, 30), orc.knn_brute(xyz, centres, 30))
+
+
+def test_knn_candidate_mask(orc):
+    """Masked supports: the centre plus the nearest candidates only, all three ways."""
+    xyz, bnd = orc.nodes(2, 2, 20, 0.3, 8)
+    cand = (bnd == 0).astype(np.uint8)
+    centres = np.nonzero(bnd == 2)[0].astype(np.int32)
+    n = 12
+    b = orc.knn_brute(xyz, centres, n, cand=cand)
+    k = orc.knn_kdtree(xyz, centres, n, cand=cand)
+    ref = []
+    for c in centres:
+        t0 = xyz[0] - xyz[0, c]
+        t1 = xyz[1] - xyz[1, c]
+        d2 = t0 * t0 + t1 * t1
+        ok = (cand == 1) | (np.arange(xyz.shape[1]) == c)
+        ids = np.nonzero(ok)[0]
+        ref.append(ids[np.lexsort((ids, d2[ids]))][:n])
+    assert np.array_equal(b, np.array(ref)) and np.array_equal(k, b)
+    assert np.all(b[:, 0] == centres) and np.all(bnd[b[:, 1:]] == 0)

@@ -73,6 +73,16 @@ def _traffic():
     return None
 
 
+def max_over_ranks(seconds: float, dist, device=None) -> float:
+    """The slowest rank's time (every rank calls this; the value is the same on all)."""
+    if dist is None:
+        return seconds
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _dist():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -207,14 +217,14 @@ def run_reference(args):
             return
     import oracle
     oracle.build()
-    xyz, bnd = oracle.nodes(D, 0, KG, 0.3, SEED)
+    xyz, bnd = oracle.nodes(D, 0, args.Kg, 0.3, SEED)
     inter = gen.interior_ids(bnd)
-    n = gen.stencil_size(D, M)
+    n = gen.stencil_size(D, args.m)
     idx = oracle.knn_kdtree(xyz, inter, n)
-    w, st = oracle.weights(xyz, idx, M)
+    w, st = oracle.weights(xyz, idx, args.m)
     f = gen.source(xyz, inter)
     u = gen.start_iterate(xyz, bnd)
-    dt = 3.7e-8
+    dt = 0.037 / args.Kg ** 2
     t0 = time.perf_counter()
     oracle.solve_explicit(w, idx, inter, f, u, dt, 2, 0.0)
     per = (time.perf_counter() - t0) / 2
@@ -231,12 +241,12 @@ def run_reference(args):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
-           "config": {"workload": "2D unit square, 1,002,001 jittered nodes, m=4 (n=30), FP64 "
-                                  "explicit sweeps", "sweeps_per_step": S,
+           "config": {"workload": f"2D unit square, {xyz.shape[1]:,} jittered nodes, m={args.m} "
+                                  f"(n={n}), FP64 explicit sweeps", "sweeps_per_step": S,
                       "l2": "inputs larger than L2"},
            "cpu_baseline": {"kind": "oracle", "cores": oracle.num_threads(), "value": v,
                             "unit": UNIT,
-                            "sample": f"{S} sweeps of the full 998,001-row problem per step"},
+                            "sample": f"{S} sweeps of the full {len(inter):,}-row problem per step"},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
     if world > 1:
@@ -445,15 +455,76 @@ def run_workload(args):
                "fd_directions": 20, "fd_max_rel_err": max(rel), "fd_median_rel_err": float(np.median(rel))})
         return
 
+    if args.workload == "mixed1M_m4":
+        # half square [0, 1/2]^2, 1,002,001 nodes, u = 0 on x=0 / y=0, du/dn = 0 on x=1/2 / y=1/2
+        xyz, bnd = rb.rbffd_nodes(2, 2, 1000, 0.3, 6, device=dev)
+        n = gen.stencil_size(2, 4)
+        inter = rb.rbffd_interior(bnd)
+        idx = rb.rbffd_knn(xyz, inter, n)
+        w, st = rb.rbffd_weights(xyz, idx, 4)
+        xyz_h, bnd_h, inter_h = xyz.cpu().numpy(), bnd.cpu().numpy(), inter.cpu().numpy()
+        nnode, normals = gen.neumann_nodes(xyz_h, bnd_h)
+        nidx = rb.rbffd_knn_masked(xyz, (bnd == 0).to(torch.uint8),
+                                   torch.from_numpy(nnode).to(dev), n)
+        nw, nst = rb.rbffd_weights_dir(xyz, nidx, 4, torch.from_numpy(normals).to(dev))
+        plan = rb.Plan(xyz, bnd, inter, idx, w)
+        plan.set_neumann(torch.from_numpy(nnode).to(dev), nidx, nw)
+        f = torch.from_numpy(gen.source(xyz_h, inter_h)).to(dev)
+        u0 = torch.from_numpy(gen.start_iterate(xyz_h, bnd_h)).to(dev)
+        NI = len(inter_h)
+        dt, rho = plan.stable_dt(torch.from_numpy(gen.random_vector(NI, 7)).to(dev), 200)
+        dt *= 0.9
+        u = u0.clone()
+        plan.solve_explicit(f, u, dt, 64, 0.0)
+        S = 200
+        plan.solve_explicit(f, u, dt, S, 0.0)
+        ms, k, nl, shape = plan.stats()
+        per = ms * 1e-3 / k
+        _line("mixed boundary: half square [0,1/2]^2, 1,002,001 nodes (1,998 Neumann), m=4 (n=30), "
+              "FP64, Neumann update before every step", NI / per, UNIT, per * 1e3 * S, S, 64,
+              {"alg_GBps": NI * (12 * n + 24) / per / 1e9, "neumann_nodes": len(nnode),
+               "rho_h2": rho * (0.5 / 1000) ** 2, "dt": dt})
+        plan.destroy()
+        return
+
+    if args.workload == "support_sweep":
+        # the support-size study at m = 2 (n > 2M), 2D square 1,002,001 nodes
+        xyz, bnd = rb.rbffd_nodes(2, 0, 1000, 0.3, 2, device=dev)
+        inter = rb.rbffd_interior(bnd)
+        NI = inter.numel()
+        xyz_h, bnd_h, inter_h = xyz.cpu().numpy(), bnd.cpu().numpy(), inter.cpu().numpy()
+        f = torch.from_numpy(gen.source(xyz_h, inter_h)).to(dev)
+        u0 = torch.from_numpy(gen.start_iterate(xyz_h, bnd_h)).to(dev)
+        rows = {}
+        for n in (12, 13, 16, 20, 24, 30, 40, 48, 56):
+            idx = rb.rbffd_knn(xyz, inter, n)
+            w, st = rb.rbffd_weights(xyz, idx, 2)
+            plan = rb.Plan(xyz, bnd, inter, idx, w)
+            u = u0.clone()
+            plan.solve_explicit(f, u, 1e-9, 64, 0.0)
+            plan.solve_explicit(f, u, 1e-9, 200, 0.0)
+            ms, k, nl, shape = plan.stats()
+            per = ms * 1e-3 / k
+            rows[n] = {"node_updates_per_s": NI / per, "alg_GBps": NI * (12 * n + 24) / per / 1e9,
+                       "frac_hbm": NI * (12 * n + 24) / per / 1e9 / hbm, "launch_shape": shape}
+            plan.destroy()
+        _line("support-size sweep, m=2, n = 12..56, 2D square 1,002,001 nodes, FP64",
+              rows[12]["node_updates_per_s"], UNIT, 0.0, 200, 64, {"by_n": rows})
+        return
+
     if args.workload == "tta":
         out = {}
         for Kg in (100, 200, 300):
             xyz, bnd = rb.rbffd_nodes(2, 0, Kg, 0.3, 1, device=dev)
             Q = _gpu_problem_from_nodes(rb, torch, xyz, bnd, 4, dev)
-            plan = Q["plan"]
             chunk, target, cap = 1000, 1e-6, 4_000_000
             row = {}
-            for prec in ("fp64", "fp32_dc"):
+            for prec in ("fp64", "fp32_dc", "fp64_persistent"):
+                if prec == "fp64_persistent":
+                    plan = rb.Plan(Q["xyz"], Q["bnd"], Q["inter"], Q["idx"], Q["w"],
+                                   rb.RBFFD_ORDER_MORTON | rb.RBFFD_LAUNCH_PERSISTENT)
+                else:
+                    plan = Q["plan"]
                 u = Q["u0"].clone()
                 plan.solve_explicit(Q["f"], u.clone(), Q["dt"], 64, 0.0)   # warm graph/tuner
                 plan.solve_dc(Q["f"], u.clone(), Q["dt"], 0.0, 1, 64, 0.0)
@@ -461,7 +532,7 @@ def run_workload(args):
                 t0 = time.perf_counter()
                 steps, err = 0, 1.0
                 while steps < cap:
-                    if prec == "fp64":
+                    if prec != "fp32_dc":
                         plan.solve_explicit(Q["f"], u, Q["dt"], chunk, 0.0)
                     else:
                         plan.solve_dc(Q["f"], u, Q["dt"], 0.0, 1, chunk, 0.0)
@@ -473,9 +544,11 @@ def run_workload(args):
                 el = time.perf_counter() - t0
                 row[prec] = {"seconds": el, "steps": steps, "max_err": err, "mean_abs_err": mean,
                              "reached": err <= target}
+                if prec == "fp64_persistent":
+                    plan.destroy()
             row["speedup_fp32_dc"] = row["fp64"]["seconds"] / row["fp32_dc"]["seconds"]
             out[f"Kg{Kg}_N{Q['N']}"] = row
-            plan.destroy()
+            Q["plan"].destroy()
         first = out[next(iter(out))]
         _line("time to max error 1e-6 vs u = sin(pi x) sin(pi y), 2D squares K_g 100/200/300, "
               "m=4, error checked every 1,000 steps (included)", first["fp64"]["seconds"],
@@ -526,7 +599,8 @@ def main():
     ap.add_argument("--sweeps", type=int, default=5, help="sweeps in --mode sweep")
     ap.add_argument("--batch-cap", type=int, default=20000, help="step cap per domain (batched256)")
     ap.add_argument("--workload", default="square1M_m4",
-                    choices=["square1M_m4", "batched256", "cube8M_m4", "adjoint1M_m4", "tta"],
+                    choices=["square1M_m4", "batched256", "cube8M_m4", "adjoint1M_m4", "tta",
+                             "mixed1M_m4", "support_sweep"],
                     help="square1M_m4 is the headline; the others measure the other workloads")
     args = ap.parse_args()
     if args.workload != "square1M_m4":
@@ -577,11 +651,7 @@ def main():
             launches += nl
         ev1.record()
         barrier()
-    el = ev0.elapsed_time(ev1) * 1e-3
-    if dist is not None:
-        t = torch.tensor([el], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el = float(t.item())
+    el = max_over_ranks(ev0.elapsed_time(ev1) * 1e-3, dist, dev)
     updates = NI * SWEEPS * args.steps * world
     value = updates / el
     clocks = clk.summary()

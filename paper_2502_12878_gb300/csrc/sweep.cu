@@ -297,7 +297,6 @@ __device__ bool grid_sync(StepCtrl* c) {
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
             }
         }
         __threadfence();
@@ -380,9 +379,13 @@ static StepFn pick_step_m(int n, bool persistent) {
         RBFFD_CASE(6)
         RBFFD_CASE(12)
         RBFFD_CASE(13)
+        RBFFD_CASE(16)
         RBFFD_CASE(20)
+        RBFFD_CASE(24)
         RBFFD_CASE(30)
         RBFFD_CASE(31)
+        RBFFD_CASE(40)
+        RBFFD_CASE(48)
         RBFFD_CASE(56)
         RBFFD_CASE(57)
         RBFFD_CASE(70)
@@ -779,13 +782,15 @@ static int grid_for(const rbffd_plan* p, int per_sm) {
 }
 static int step_grid(const rbffd_plan* p) { return grid_for(p, p->grid_steps); }
 
-static int persistent_grid(StepFn fn) {
+// resident blocks of a persistent launch, no more than the slices need
+static int persistent_grid(StepFn fn, int64_t nslices) {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)fn, STEP_THREADS, 0) !=
             cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
-    return per_sm * device_sm_count();
+    int64_t need = (nslices + STEP_THREADS / 32 - 1) / (STEP_THREADS / 32);
+    return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * device_sm_count(), need));
 }
 
 // reset the control block for a run of at most max_steps steps
@@ -819,19 +824,43 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
     RBFFD_CHECK_CUDA(cudaEventCreate(&e1));
     StepArgs A = make_args(p);
     // enough steps to time reliably on small plans, few on large ones
-    const long long reps = std::max<long long>(3, std::min<long long>(40, 20000000 / (p->NI * p->n + 1)));
+    const long long reps = std::max<long long>(10, std::min<long long>(60, 40000000 / (p->NI * p->n + 1)));
     float best = 1e30f;
     int bm = 2, bg = 2;
     int st = RBFFD_OK;
     for (int minb = 1; minb <= N_MINB && st == RBFFD_OK; ++minb) {
         StepFn fn = pick(mode, p->n, persistent, minb);
         for (int per_sm = 1; per_sm <= (persistent ? 1 : 4); ++per_sm) {
-            int grid = persistent
-                           ? (int)std::min<int64_t>(persistent_grid(fn), std::max<int64_t>(1, p->nslices))
-                           : grid_for(p, per_sm);
-            float ms = 0.f;
-            for (int pass = 0; pass < 2; ++pass) {   // pass 0 warms up
-                if ((st = ctrl_reset(p, 0.0, 0.0, pass ? reps : 2, s))) break;
+            int grid = persistent ? persistent_grid(fn, p->nslices) : grid_for(p, per_sm);
+            // pass 0 warms up; passes 1 and 2 are timed, the faster one counts.  Graph
+            // mode times a captured chunk of launches: exactly what solves replay.
+            float ms = 1e30f;
+            cudaGraphExec_t gx = nullptr;
+            if (!persistent) {
+                cudaStream_t cs;
+                cudaGraph_t gg;
+                cudaError_t ce = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+                if (ce == cudaSuccess) {
+                    ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+                    if (ce == cudaSuccess) {
+                        for (long long i = 0; i < reps; ++i)
+                            fn<<<grid, STEP_THREADS, 0, cs>>>(A, p->ctrl);
+                        ce = cudaStreamEndCapture(cs, &gg);
+                        if (ce == cudaSuccess) {
+                            ce = cudaGraphInstantiate(&gx, gg, 0);
+                            cudaGraphDestroy(gg);
+                        }
+                    }
+                    cudaStreamDestroy(cs);
+                }
+                if (ce != cudaSuccess) {
+                    set_error("autotune: capture: %s", cudaGetErrorString(ce));
+                    st = RBFFD_ERR_CUDA;
+                    break;
+                }
+            }
+            for (int pass = 0; pass < 3; ++pass) {
+                if ((st = ctrl_reset(p, 0.0, 0.0, reps, s))) break;
                 cudaEventRecord(e0, s);
                 if (persistent) {
                     StepCtrl* c = p->ctrl;
@@ -839,20 +868,22 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
                     cudaLaunchCooperativeKernel((const void*)fn, dim3(grid), dim3(STEP_THREADS), args,
                                                 0, s);
                 } else {
-                    for (long long i = 0; i < (pass ? reps : 2); ++i)
-                        fn<<<grid, STEP_THREADS, 0, s>>>(A, p->ctrl);
+                    cudaGraphLaunch(gx, s);
                 }
                 cudaEventRecord(e1, s);
+                cudaError_t e = cudaEventSynchronize(e1);
+                if (e == cudaSuccess) e = cudaGetLastError();
+                if (e != cudaSuccess) {
+                    set_error("autotune: %s", cudaGetErrorString(e));
+                    st = RBFFD_ERR_CUDA;
+                    break;
+                }
+                float t = 0.f;
+                cudaEventElapsedTime(&t, e0, e1);
+                if (pass) ms = std::min(ms, t);
             }
+            if (gx) cudaGraphExecDestroy(gx);
             if (st) break;
-            cudaError_t e = cudaEventSynchronize(e1);
-            if (e == cudaSuccess) e = cudaGetLastError();
-            if (e != cudaSuccess) {
-                set_error("autotune: %s", cudaGetErrorString(e));
-                st = RBFFD_ERR_CUDA;
-                break;
-            }
-            cudaEventElapsedTime(&ms, e0, e1);
             if (ms < best) {
                 best = ms;
                 bm = minb;
@@ -945,7 +976,7 @@ static int run_steps(rbffd_plan* p, int mode, double dt, double tol, long long m
                 if (st) return st;
             }
             StepFn fn = pick(mode, p->n, true, p->minb[mi]);
-            int grid = std::min<int64_t>(persistent_grid(fn), std::max<int64_t>(1, p->nslices));
+            int grid = persistent_grid(fn, p->nslices);
             StepArgs A = make_args(p);
             StepCtrl* c = p->ctrl;
             void* args[] = {(void*)&A, (void*)&c};

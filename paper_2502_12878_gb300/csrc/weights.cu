@@ -66,11 +66,14 @@ __device__ __forceinline__ double team_max(double v, double* red) {
     return m;
 }
 
+// argmax of |value| as IEEE bits (non-negative doubles order like integers;
+// NaN is mapped to -1 by the caller and never wins); ties -> lower index.
+// Integer compares keep the FP64 pipe for the elimination's multiply-adds.
 template <int TW>
-__device__ __forceinline__ void team_argmax(double& bv, int& bi, double* redv, int* redi) {
+__device__ __forceinline__ void team_argmax(long long& bv, int& bi, long long* redv, int* redi) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
         int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ov > bv || (ov == bv && oi < bi)) {
             bv = ov;
@@ -94,11 +97,18 @@ __device__ __forceinline__ void team_argmax(double& bv, int& bi, double* redv, i
     __syncthreads();
 }
 
+__device__ __forceinline__ long long abs_key(double x) {
+    long long b = __double_as_longlong(x) & 0x7fffffffffffffffll;
+    return b > 0x7ff0000000000000ll ? -1ll : b;    // NaN: never the largest
+}
+
 template <int TW>
 __global__ void __launch_bounds__(256) weights_kernel(WeightArgs A, int teams_per_block) {
     extern __shared__ double wsm[];
     __shared__ double redv[8];
+    __shared__ long long redk[8];
     __shared__ int redi[8];
+    __shared__ double bcast[8];   // per-team scalar broadcast (reciprocal pivot, x_j)
     constexpr int T = 32 * TW;
     const int tid = threadIdx.x % T;
     const int team = threadIdx.x / T;
@@ -212,13 +222,21 @@ __global__ void __launch_bounds__(256) weights_kernel(WeightArgs A, int teams_pe
             G[(n + al) * P + s] = v;
         }
         team_sync<TW>();
-        // scale of the assembled matrix for the relative pivot test
-        double gmax = 0.0;
+        // scale of the assembled matrix for the relative pivot test (max |entry|
+        // over IEEE bits; NaN entries ignored)
+        long long gk = 0;
         for (int e = tid; e < s * s; e += T) {
             int i = e / s, j = e - i * s;
-            gmax = fmax(gmax, fabs(G[i * P + j]));
+            gk = max(gk, abs_key(G[i * P + j]));
         }
-        gmax = team_max<TW>(gmax, redv);
+        long long gkb = 0;
+        {
+            long long bk = gk;
+            int bi_dummy = 0;
+            team_argmax<TW>(bk, bi_dummy, redk, redi);
+            gkb = bk;
+        }
+        const double gmax = __longlong_as_double(gkb < 0 ? 0ll : gkb);
         const double tiny = __dmul_rn(1e-13, gmax);
 
         // elimination with partial pivoting
@@ -227,20 +245,25 @@ __global__ void __launch_bounds__(256) weights_kernel(WeightArgs A, int teams_pe
             // pivot: the first row of largest |a_ik| (NaN entries never win;
             // a NaN on the diagonal leaves no usable pivot)
             const bool diag_nan = isnan(G[k * P + k]);
-            double bv = -1.0;
+            long long bk = -2;
             int bi = s;
             for (int i = k + tid; i < s; i += T) {
-                double v = fabs(G[i * P + k]);
-                if (v != v) v = -1.0;
-                if (v > bv) {
-                    bv = v;
+                long long v = abs_key(G[i * P + k]);
+                if (v > bk) {
+                    bk = v;
                     bi = i;
                 }
             }
-            team_argmax<TW>(bv, bi, redv, redi);
+            team_argmax<TW>(bk, bi, redk, redi);
+            const double bv = bk < 0 ? -1.0 : __longlong_as_double(bk);
             if (diag_nan || !(bv > tiny) || !(bv > 1e-300) || isinf(bv)) {
                 bad = 1;
                 break;
+            }
+            // reciprocal pivot by one warp of the team, broadcast after the swap
+            if ((tid >> 5) == 0) {
+                const double t = __drcp_rn(G[bi * P + k]);
+                if (tid == 0) bcast[team] = t;
             }
             if (bi != k)
                 for (int j = k + tid; j <= s; j += T) {
@@ -249,7 +272,7 @@ __global__ void __launch_bounds__(256) weights_kernel(WeightArgs A, int teams_pe
                     G[bi * P + j] = t;
                 }
             team_sync<TW>();
-            const double rp = __drcp_rn(G[k * P + k]);
+            const double rp = bcast[team];
             for (int i = k + 1 + tid; i < s; i += T) G[i * P + k] = __dmul_rn(G[i * P + k], rp);
             team_sync<TW>();
             // trailing update over (row, column) pairs: rows k+1..s-1,
@@ -273,17 +296,22 @@ __global__ void __launch_bounds__(256) weights_kernel(WeightArgs A, int teams_pe
         if (!bad) {
             // back substitution by columns; x_j overwrites the rhs entry of row j
             for (int j = s - 1; j >= 0; --j) {
-                double xj = __ddiv_rn(G[j * P + s], G[j * P + j]);
+                if ((tid >> 5) == 0) {   // one warp divides, the team reads the result
+                    const double t = __ddiv_rn(G[j * P + s], G[j * P + j]);
+                    if (tid == 0) bcast[team] = t;
+                }
+                team_sync<TW>();
+                const double xj = bcast[team];
                 if (!isfinite(xj)) {
                     bad = 1;
                     break;
                 }
-                team_sync<TW>();
                 for (int i = tid; i < j; i += T)
                     G[i * P + s] = __fma_rn(-G[i * P + j], xj, G[i * P + s]);
-                if (tid == 0) G[j * P + s] = xj;
                 team_sync<TW>();
+                if (tid == 0) G[j * P + s] = xj;
             }
+            team_sync<TW>();
         }
         // the Laplacian scales as 1/sigma^2, a first derivative as 1/sigma
         const double scl = A.op == 0 ? __dmul_rn(sig, sig) : sig;

@@ -143,11 +143,35 @@ __global__ void scan64_single(const int64_t* in, int64_t n, int64_t* out) {
     if (threadIdx.x == 0) out[n] = carry;
 }
 
+// Ordered streaming loads: asm volatile keeps the loads of one phase ahead of
+// the first use, so each thread has 2*CH loads and then CH gathers in flight
+// (plain loads were issued one dependent pair at a time).  CH = 8 with four
+// 256-thread blocks per SM fits 64 registers without spills.
+__device__ __forceinline__ double adj_ld_cs(const double* p) {
+    double v;
+    asm volatile("ld.global.cs.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ int32_t adj_ld_cs(const int32_t* p) {
+    int32_t v;
+    asm volatile("ld.global.cs.s32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ double adj_ld_nc(const double* p) {
+    double v;
+    asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+
 // one reverse step over interior columns c < NI:
 //   S_c += lam_c;  lam'_c = fma(dt, sum_rows w_rc lam_r, lam_c)
-__global__ void adjoint_step(const Transpose T, const int64_t NI, const double dt,
-                             const double* __restrict__ lam, double* __restrict__ lam_out,
-                             double* __restrict__ S) {
+// the column sum is an fma chain from 0 over the column's entries in order
+// (padding entries carry weight 0 and row 0, so they add exact zeros)
+__global__ void __launch_bounds__(256, 4)
+adjoint_step(const Transpose T, const int64_t NI, const double dt,
+             const double* __restrict__ lam, double* __restrict__ lam_out,
+             double* __restrict__ S) {
+    constexpr int CH = 8;
     const int lane = threadIdx.x & 31;
     const int64_t nsl_int = (NI + SLICE - 1) / SLICE;
     for (int64_t s = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); s < nsl_int;
@@ -155,11 +179,25 @@ __global__ void adjoint_step(const Transpose T, const int64_t NI, const double d
         const int64_t c = s * SLICE + lane;
         if (c >= NI) continue;
         const int L = T.len[s];
-        const int64_t o = T.off[s] + lane;
+        const double* wp = T.w + T.off[s] + lane;
+        const int32_t* rp = T.row + T.off[s] + lane;
         double acc = 0.0;
-        for (int j = 0; j < L; ++j)
-            acc = __fma_rn(__ldcs(T.w + o + (int64_t)j * SLICE),
-                           __ldg(lam + __ldcs(T.row + o + (int64_t)j * SLICE)), acc);
+        for (int j0 = 0; j0 < L; j0 += CH) {
+            int32_t r[CH];
+            double wv[CH], lv[CH];
+#pragma unroll
+            for (int t = 0; t < CH; ++t)
+                if (j0 + t < L) r[t] = adj_ld_cs(rp + (int64_t)(j0 + t) * SLICE);
+#pragma unroll
+            for (int t = 0; t < CH; ++t)
+                if (j0 + t < L) wv[t] = adj_ld_cs(wp + (int64_t)(j0 + t) * SLICE);
+#pragma unroll
+            for (int t = 0; t < CH; ++t)
+                if (j0 + t < L) lv[t] = adj_ld_nc(lam + r[t]);
+#pragma unroll
+            for (int t = 0; t < CH; ++t)
+                if (j0 + t < L) acc = __fma_rn(wv[t], lv[t], acc);
+        }
         const double lc = lam[c];
         S[c] = __dadd_rn(S[c], lc);
         lam_out[c] = __fma_rn(dt, acc, lc);
@@ -204,9 +242,11 @@ __global__ void adj_outputs(const double* S, const double* lam, const int32_t* r
 // replay of one forward step (Eq. 6) from uin to uout, both in slot order:
 // interior rows updated, boundary slots copied (the same arithmetic as the
 // forward sweep, so the replayed iterates are the forward's bit for bit)
-__global__ void replay_step(const double* __restrict__ w64, const int32_t* __restrict__ col,
-                            const double* __restrict__ fs, const double* __restrict__ uin,
-                            double* __restrict__ uout, int64_t NI, int64_t N, int n, double dt) {
+__global__ void __launch_bounds__(256, 4)
+replay_step(const double* __restrict__ w64, const int32_t* __restrict__ col,
+            const double* __restrict__ fs, const double* __restrict__ uin,
+            double* __restrict__ uout, int64_t NI, int64_t N, int n, double dt) {
+    constexpr int CH = 8;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N;
          p += (int64_t)gridDim.x * blockDim.x) {
         if (p >= NI) {
@@ -215,8 +255,22 @@ __global__ void replay_step(const double* __restrict__ w64, const int32_t* __res
         }
         const int64_t base = (p / SLICE) * (int64_t)n * SLICE + (p % SLICE);
         double acc = 0.0;
-        for (int j = 0; j < n; ++j)
-            acc = __fma_rn(w64[base + j * SLICE], __ldg(uin + col[base + j * SLICE]), acc);
+        for (int j0 = 0; j0 < n; j0 += CH) {
+            int32_t c[CH];
+            double wv[CH], uv[CH];
+#pragma unroll
+            for (int t = 0; t < CH; ++t)
+                if (j0 + t < n) c[t] = adj_ld_cs(col + base + (int64_t)(j0 + t) * SLICE);
+#pragma unroll
+            for (int t = 0; t < CH; ++t)
+                if (j0 + t < n) wv[t] = adj_ld_cs(w64 + base + (int64_t)(j0 + t) * SLICE);
+#pragma unroll
+            for (int t = 0; t < CH; ++t)
+                if (j0 + t < n) uv[t] = adj_ld_nc(uin + c[t]);
+#pragma unroll
+            for (int t = 0; t < CH; ++t)
+                if (j0 + t < n) acc = __fma_rn(wv[t], uv[t], acc);
+        }
         double r = __dsub_rn(acc, fs[p]);
         uout[p] = __fma_rn(dt, r, uin[p]);
     }
@@ -224,16 +278,29 @@ __global__ void replay_step(const double* __restrict__ w64, const int32_t* __res
 
 // weight-gradient accumulation with lambda^{k+1} and u^k in the slice layout:
 // G[s][j][lane] = fma(lambda_p, u^k[col], G[s][j][lane])
-__global__ void wgrad_accum(const int32_t* __restrict__ col, const double* __restrict__ lam,
-                            const double* __restrict__ uk, double* __restrict__ G, int64_t NI,
-                            int n) {
+__global__ void __launch_bounds__(256, 4)
+wgrad_accum(const int32_t* __restrict__ col, const double* __restrict__ lam,
+            const double* __restrict__ uk, double* __restrict__ G, int64_t NI, int n) {
+    constexpr int CH = 8;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < NI;
          p += (int64_t)gridDim.x * blockDim.x) {
         const int64_t base = (p / SLICE) * (int64_t)n * SLICE + (p % SLICE);
         const double lp = lam[p];
-        for (int j = 0; j < n; ++j) {
-            const int64_t q = base + j * SLICE;
-            G[q] = __fma_rn(lp, __ldg(uk + col[q]), G[q]);
+        for (int j0 = 0; j0 < n; j0 += CH) {
+            int32_t c[CH];
+            double gv[CH], uv[CH];
+#pragma unroll
+            for (int t = 0; t < CH; ++t)
+                if (j0 + t < n) c[t] = adj_ld_cs(col + base + (int64_t)(j0 + t) * SLICE);
+#pragma unroll
+            for (int t = 0; t < CH; ++t)
+                if (j0 + t < n) gv[t] = G[base + (int64_t)(j0 + t) * SLICE];
+#pragma unroll
+            for (int t = 0; t < CH; ++t)
+                if (j0 + t < n) uv[t] = adj_ld_nc(uk + c[t]);
+#pragma unroll
+            for (int t = 0; t < CH; ++t)
+                if (j0 + t < n) G[base + (int64_t)(j0 + t) * SLICE] = __fma_rn(lp, uv[t], gv[t]);
         }
     }
 }

@@ -23,10 +23,13 @@ static constexpr int KNN_NMAX = 128;
 static constexpr int KNN_BUF = 64;
 static constexpr int KNN_WARPS = 4;
 
+// distances are kept as the IEEE bits of d2: for non-negative doubles the
+// unsigned integer order is the numeric order, so the (d2, index) key
+// comparisons of the merges run on the integer pipes, not the FP64 pipe
 struct KnnSmem {
-    double bd[2][KNN_NMAX];
+    unsigned long long bd[2][KNN_NMAX];
     int32_t bj[2][KNN_NMAX];
-    double cd[KNN_BUF];
+    unsigned long long cd[KNN_BUF];
     int32_t cj[KNN_BUF];
     int32_t rb[32], rpre[32];   // range begin, inclusive prefix of lengths
 };
@@ -47,7 +50,8 @@ struct KnnArgs {
     int* err;
 };
 
-__device__ __forceinline__ bool kless(double da, int32_t ja, double db, int32_t jb) {
+__device__ __forceinline__ bool kless(unsigned long long da, int32_t ja, unsigned long long db,
+                                      int32_t jb) {
     return da < db || (da == db && ja < jb);
 }
 
@@ -67,7 +71,7 @@ __device__ void knn_merge(KnnSmem& sm, int& cur, int& nb, int nbuf, int n, int l
     __syncwarp();
     int L = nb + nbuf;
     for (int e = lane; e < L; e += 32) {
-        double de = e < nb ? sm.bd[cur][e] : sm.cd[e - nb];
+        unsigned long long de = e < nb ? sm.bd[cur][e] : sm.cd[e - nb];
         int32_t je = e < nb ? sm.bj[cur][e] : sm.cj[e - nb];
         int rank = 0;
         for (int f = 0; f < nb; ++f) rank += kless(sm.bd[cur][f], sm.bj[cur][f], de, je);
@@ -163,7 +167,7 @@ __global__ void __launch_bounds__(32 * KNN_WARPS) knn_kernel(KnnArgs A) {
                     }
                     int32_t v = v0 + lane;
                     bool acc = false;
-                    double dv = 0.0;
+                    unsigned long long dv = 0;
                     int32_t jv = 0;
                     if (v < total) {
                         int k = 0;   // first slot with inclusive prefix > v
@@ -171,7 +175,7 @@ __global__ void __launch_bounds__(32 * KNN_WARPS) knn_kernel(KnnArgs A) {
                             if (sm.rpre[k + step - 1] <= v) k += step;
                         int32_t off = v - (k ? sm.rpre[k - 1] : 0);
                         jv = A.sorted[sm.rb[k] + off];
-                        dv = sqdist(A.xyz, A.N, d, jv, q);
+                        dv = (unsigned long long)__double_as_longlong(sqdist(A.xyz, A.N, d, jv, q));
                         acc = (nb < n) || kless(dv, jv, sm.bd[cur][n - 1], sm.bj[cur][n - 1]);
                         if (A.cand && !A.cand[jv] && jv != c) acc = false;
                     }
@@ -207,7 +211,7 @@ __global__ void __launch_bounds__(32 * KNN_WARPS) knn_kernel(KnnArgs A) {
                 done = true;
             } else if (nb == n) {
                 double be = bound - 1e-6 * g.cs;
-                double worst = sm.bd[cur][n - 1];
+                double worst = __longlong_as_double((long long)sm.bd[cur][n - 1]);
                 if (be > 0.0 && worst < be * be * (1.0 - 1e-12)) {
                     done = true;
                 } else {

@@ -57,6 +57,7 @@ extern "C" {
 #define RBFFD_ORDER_RANDOM 2       /* interior nodes first, seeded random order */
 #define RBFFD_LAUNCH_GRAPH 0       /* one kernel per step, replayed from a CUDA graph */
 #define RBFFD_LAUNCH_PERSISTENT 16 /* one cooperative kernel runs many steps */
+#define RBFFD_PACK_IDX32 32        /* keep int32 neighbour indices only (no 16-bit codes) */
 
 typedef struct rbffd_plan rbffd_plan;
 
@@ -213,8 +214,13 @@ RBFFD_API int rbffd_error(const double* u, const double* ua, int64_t N, double* 
  *   (boundary nodes, is_bnd != 0, keep their values unless set as Neumann
  *   nodes by rbffd_plan_set_neumann);
  *   idx / w [NI][n] are the supports/weights of those rows.
- *   flags: RBFFD_ORDER_* | RBFFD_LAUNCH_*; seed is used by RBFFD_ORDER_RANDOM.
+ *   flags: RBFFD_ORDER_* | RBFFD_LAUNCH_* | RBFFD_PACK_IDX32; seed is used by
+ *   RBFFD_ORDER_RANDOM.
  *   *plan out.
+ * Unless RBFFD_PACK_IDX32 is set, the step kernels read the neighbour indices
+ * of a slice as 16-bit codes against up to four window bases of 2^14 slots
+ * (a slice whose supports need more windows keeps 32-bit indices); the codes
+ * name the same neighbours, so the results are the same bit for bit.
  */
 RBFFD_API int rbffd_plan_create(const double* xyz, const uint8_t* is_bnd, int64_t N, int d,
                       const int32_t* interior, const int32_t* idx, const double* w, int64_t NI,
@@ -273,6 +279,17 @@ RBFFD_API int rbffd_solve_explicit(rbffd_plan* plan, const double* f, double* u,
  */
 RBFFD_API int rbffd_plan_stats(const rbffd_plan* plan, double* h_loop_ms, int64_t* h_loop_steps,
                                int64_t* h_launches, int* h_shape);
+
+/*
+ * rbffd_plan_layout - the packed layout's size (host outputs, may be NULL):
+ * h_nslices, 32-row slices; h_rows16, interior rows whose slice uses 16-bit
+ * index codes; h_bytes64 / h_bytes32, the bytes one FP64 sweep / one FP32
+ * inner sweep streams when every gathered neighbour is served from cache
+ * (weights, index codes or indices, window bases, and per row f or d, the
+ * row's old value and its new value).
+ */
+RBFFD_API int rbffd_plan_layout(const rbffd_plan* plan, int64_t* h_nslices, int64_t* h_rows16,
+                                double* h_bytes64, double* h_bytes32);
 
 /*
  * rbffd_solve_dc - defect correction (the precision split is not in the

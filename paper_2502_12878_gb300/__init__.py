@@ -41,6 +41,7 @@ RBFFD_ORDER_INPUT = 1
 RBFFD_ORDER_RANDOM = 2
 RBFFD_LAUNCH_GRAPH = 0
 RBFFD_LAUNCH_PERSISTENT = 16
+RBFFD_PACK_IDX32 = 32
 
 EXPORTED = [
     "rbffd_last_error", "rbffd_version", "rbffd_nodes", "rbffd_interior", "rbffd_knn",
@@ -49,7 +50,7 @@ EXPORTED = [
     "rbffd_adjoint", "rbffd_plan_stats", "rbffd_knn_noalloc", "rbffd_batch_create",
     "rbffd_batch_destroy", "rbffd_solve_batch", "rbffd_batch_set_shape", "rbffd_batch_stats",
     "rbffd_error", "rbffd_batch_domain_times", "rbffd_batch_set_costs", "rbffd_adjoint_w",
-    "rbffd_knn_masked", "rbffd_weights_dir", "rbffd_plan_set_neumann",
+    "rbffd_knn_masked", "rbffd_weights_dir", "rbffd_plan_set_neumann", "rbffd_plan_layout",
 ]
 RBFFD_KNN_NOALLOC_MAX_NODES = 262144
 
@@ -107,6 +108,7 @@ def lib():
         "rbffd_knn_masked": (I, [P, I64, I, P, P, I64, I, P, P]),
         "rbffd_weights_dir": (I, [P, I64, I, P, I64, I, I, P, P, P, PI64, PI64, P]),
         "rbffd_plan_set_neumann": (I, [P, I64, P, P, P, I, P, P]),
+        "rbffd_plan_layout": (I, [P, PI64, PI64, PD, PD]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -356,6 +358,16 @@ class Plan:
         _check(lib().rbffd_plan_stats(self.handle, ctypes.byref(ms), ctypes.byref(steps),
                                       ctypes.byref(launches), shape))
         return ms.value, steps.value, launches.value, list(shape)
+
+    def layout(self):
+        """Packed layout: dict(nslices, rows16 = interior rows with 16-bit index codes,
+        bytes64 / bytes32 = bytes one FP64 / FP32 sweep streams)."""
+        ns, r16 = ctypes.c_int64(0), ctypes.c_int64(0)
+        b64, b32 = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        _check(lib().rbffd_plan_layout(self.handle, ctypes.byref(ns), ctypes.byref(r16),
+                                       ctypes.byref(b64), ctypes.byref(b32)))
+        return {"nslices": ns.value, "rows16": r16.value, "bytes64": b64.value,
+                "bytes32": b32.value}
 
     def set_neumann(self, nodes, idx, w, g=None):
         """Neumann nodes (ids [NN]), their supports idx [NN, nn] (node first) and

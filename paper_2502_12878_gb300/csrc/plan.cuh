@@ -51,6 +51,12 @@ struct rbffd_plan {
     double* w64 = nullptr;          // [nslices][n][32]
     float* w32 = nullptr;           // [nslices][n][32]
     int32_t* col = nullptr;         // [nslices][n][32] neighbour slots
+    // compact neighbour indices: per slice up to four window bases (int4,
+    // x = -1 marks a slice that keeps the int32 form) and per entry a 16-bit
+    // code, window k in bits 15..14 and the offset from that base in 13..0
+    uint16_t* col16 = nullptr;      // [nslices][n][32] (NULL with RBFFD_PACK_IDX32)
+    int4* sbase = nullptr;          // [nslices]
+    int64_t rows16 = 0;             // interior rows in compact slices
     double* u[2] = {nullptr, nullptr};   // iterates in slot order [N]
     double* fs = nullptr;           // f in slot order [NI]
     float* e[2] = {nullptr, nullptr};    // DC correction [N]

@@ -79,6 +79,11 @@ __device__ __forceinline__ int32_t ld_stream(const int32_t* p) {
     asm volatile("ld.global.cs.s32 %0, [%1];" : "=r"(v) : "l"(p));
     return v;
 }
+__device__ __forceinline__ uint32_t ld_stream(const uint16_t* p) {
+    unsigned short v;
+    asm volatile("ld.global.cs.u16 %0, [%1];" : "=h"(v) : "l"(p));
+    return (uint32_t)v;
+}
 // Gather of the iterate.  Within one launch per step the iterate is
 // read-only, so the non-coherent path (L1) is used; a persistent launch
 // rewrites it between steps from other SMs, so it reads through L2 (.cg).
@@ -97,12 +102,21 @@ __device__ __forceinline__ float ld_iter(const float* p) {
     return v;
 }
 
+// compact index: window k = code >> 14 selects one of the slice's four bases
+// (three selects on the integer pipe), plus the 14-bit offset
+__device__ __forceinline__ int32_t decode16(uint32_t v, const int4& b) {
+    const uint32_t k = v >> 14;
+    const int32_t base = (k & 2u) ? ((k & 1u) ? b.w : b.z) : ((k & 1u) ? b.y : b.x);
+    return base + (int32_t)(v & 0x3fffu);
+}
+
 // sum_j w_j u[col_j] as an fma chain from 0, j ascending.  Loads are issued
 // in phases of CH (indices, weights, then the gathers) so each thread keeps
-// 2*CH streaming loads and CH gathers in flight.
-template <int NN, bool COH, class T>
-__device__ __forceinline__ T row_dot(const T* __restrict__ w, const int32_t* __restrict__ col,
-                                     const T* __restrict__ u, int n) {
+// 2*CH streaming loads and CH gathers in flight.  I16: the indices come as
+// 16-bit codes against the slice's bases `sb` (same columns, fewer bytes).
+template <int NN, bool COH, bool I16, class T>
+__device__ __forceinline__ T row_dot(const T* __restrict__ w, const void* __restrict__ colp,
+                                     const int4& sb, const T* __restrict__ u, int n) {
     constexpr int CH = 16;
     T acc = T(0);
     const int nn = NN > 0 ? NN : n;
@@ -113,10 +127,20 @@ __device__ __forceinline__ T row_dot(const T* __restrict__ w, const int32_t* __r
         T wv[CH], uv[CH];
 #pragma unroll
         for (int t = 0; t < CH; ++t)
-            if (j0 + t < nn) c[t] = ld_stream(col + (j0 + t) * SLICE);
+            if (j0 + t < nn) {
+                if constexpr (I16)
+                    c[t] = (int32_t)ld_stream((const uint16_t*)colp + (j0 + t) * SLICE);
+                else
+                    c[t] = ld_stream((const int32_t*)colp + (j0 + t) * SLICE);
+            }
 #pragma unroll
         for (int t = 0; t < CH; ++t)
             if (j0 + t < nn) wv[t] = ld_stream(w + (j0 + t) * SLICE);
+        if constexpr (I16) {
+#pragma unroll
+            for (int t = 0; t < CH; ++t)
+                if (j0 + t < nn) c[t] = decode16((uint32_t)c[t], sb);
+        }
 #pragma unroll
         for (int t = 0; t < CH; ++t)
             if (j0 + t < nn) uv[t] = ld_iter<COH>(u + c[t]);
@@ -144,14 +168,8 @@ template <int NN, bool COH = false>
 __device__ __forceinline__ double row_dot64(const double* __restrict__ w,
                                             const int32_t* __restrict__ col,
                                             const double* __restrict__ u, int n) {
-    return row_dot<NN, COH, double>(w, col, u, n);
-}
-
-template <int NN, bool COH = false>
-__device__ __forceinline__ float row_dot32(const float* __restrict__ w,
-                                           const int32_t* __restrict__ col,
-                                           const float* __restrict__ e, int n) {
-    return row_dot<NN, COH, float>(w, col, e, n);
+    const int4 none = make_int4(0, 0, 0, 0);
+    return row_dot<NN, COH, false, double>(w, col, none, u, n);
 }
 
 enum : int { MODE_SWEEP64 = 0, MODE_INNER32 = 1 };
@@ -160,6 +178,8 @@ struct StepArgs {
     const double* w64;
     const float* w32;
     const int32_t* col;
+    const uint16_t* col16;   // compact codes, NULL when the plan keeps int32 only
+    const int4* sbase;       // [nslices] window bases; x < 0: the slice uses col
     const double* f;      // FP64 sweep: f in slot order
     float* d32;           // FP32 inner: defect in slot order
     double* u0;
@@ -182,6 +202,7 @@ __device__ __forceinline__ unsigned long long step_rows(const StepArgs& A, int p
     for (int64_t sl = slice0; sl < A.nslices; sl += stride) {
         const int64_t row = sl * SLICE + lane;
         const int64_t base = sl * (int64_t)A.n * SLICE + lane;
+        const int4 sb = A.col16 ? __ldg(A.sbase + sl) : make_int4(-1, -1, -1, -1);
         if (row < A.NI) {
             if (MODE == MODE_SWEEP64) {
                 const double* uin = par ? A.u1 : A.u0;
@@ -190,7 +211,13 @@ __device__ __forceinline__ unsigned long long step_rows(const StepArgs& A, int p
                 // their latency overlaps the stencil loads
                 const double fi = ld_stream(A.f + row);
                 const double ui = ld_iter<COH>(uin + row);
-                double acc = row_dot64<NN, COH>(A.w64 + base, A.col + base, uin, A.n);
+                double acc;
+                if (sb.x >= 0)
+                    acc = row_dot<NN, COH, true, double>(A.w64 + base, A.col16 + base, sb, uin,
+                                                         A.n);
+                else
+                    acc = row_dot<NN, COH, false, double>(A.w64 + base, A.col + base, sb, uin,
+                                                          A.n);
                 double r = __dsub_rn(acc, fi);
                 uout[row] = __fma_rn(dt, r, ui);
                 m = max(m, abs_bits(r));
@@ -199,7 +226,13 @@ __device__ __forceinline__ unsigned long long step_rows(const StepArgs& A, int p
                 float* eout = par ? A.e0 : A.e1;
                 const float di = ld_stream(A.d32 + row);
                 const float ei = ld_iter<COH>(ein + row);
-                float acc = row_dot32<NN, COH>(A.w32 + base, A.col + base, ein, A.n);
+                float acc;
+                if (sb.x >= 0)
+                    acc = row_dot<NN, COH, true, float>(A.w32 + base, A.col16 + base, sb, ein,
+                                                        A.n);
+                else
+                    acc = row_dot<NN, COH, false, float>(A.w32 + base, A.col + base, sb, ein,
+                                                         A.n);
                 float rho = __fadd_rn(acc, di);
                 eout[row] = __fmaf_rn(dt32, rho, ei);
                 m = max(m, abs_bits(rho));
@@ -545,6 +578,63 @@ __global__ void pack_stencils(const int32_t* row_of_slot, const int32_t* inv, co
     }
 }
 
+// Compact form of one slice's neighbour slots (one warp per slice).  The
+// windows are chosen greedily from the left: base b0 = the smallest slot the
+// slice's rows use, b1 = the smallest slot >= b0 + 2^14, and so on; a slice
+// whose slots need more than four windows keeps the int32 form (x = -1).
+// Greedy from the left covers with the fewest windows, and every slot v of a
+// compact slice lies in window k = #{bases <= v} - 1 at offset v - b_k < 2^14.
+static constexpr int32_t IDX16_WINDOW = 1 << 14;
+
+__global__ void pack_idx16(const int32_t* __restrict__ col, int64_t NI, int64_t nslices, int n,
+                           uint16_t* __restrict__ col16, int4* __restrict__ sbase,
+                           unsigned long long* rows16, int* err) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t sl = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); sl < nslices;
+         sl += nw) {
+        const bool valid = sl * SLICE + lane < NI;
+        const int64_t base = sl * (int64_t)n * SLICE + lane;
+        int32_t b[4];
+        int64_t thr = INT64_MIN;   // slots >= thr are not yet covered
+        int used = 0;
+        for (int k = 0; k < 4; ++k) {
+            int32_t mn = INT32_MAX;
+            if (valid)
+                for (int j = 0; j < n; ++j) {
+                    const int32_t v = col[base + (int64_t)j * SLICE];
+                    if ((int64_t)v >= thr) mn = min(mn, v);
+                }
+            mn = __reduce_min_sync(0xffffffffu, mn);
+            if (mn == INT32_MAX) break;   // warp-uniform
+            b[k] = mn;
+            used = k + 1;
+            thr = (int64_t)mn + IDX16_WINDOW;
+        }
+        for (int k = used; k < 4; ++k) b[k] = used ? b[used - 1] : 0;
+        bool left = false;
+        if (valid)
+            for (int j = 0; j < n; ++j) left |= (int64_t)col[base + (int64_t)j * SLICE] >= thr;
+        const bool wide = __any_sync(0xffffffffu, left) && used == 4;
+        if (lane == 0)
+            sbase[sl] = wide ? make_int4(-1, -1, -1, -1) : make_int4(b[0], b[1], b[2], b[3]);
+        if (wide) continue;
+        const unsigned nvalid = __popc(__ballot_sync(0xffffffffu, valid));
+        if (lane == 0) atomicAdd(rows16, (unsigned long long)nvalid);
+        for (int j = 0; j < n; ++j) {
+            uint16_t code = 0;
+            if (valid) {
+                const int32_t v = col[base + (int64_t)j * SLICE];
+                const int k = (v >= b[1]) + (v >= b[2]) + (v >= b[3]);
+                const int32_t off = v - (k == 0 ? b[0] : k == 1 ? b[1] : k == 2 ? b[2] : b[3]);
+                if (off < 0 || off >= IDX16_WINDOW) atomicExch(err, 4);   // cannot happen
+                code = (uint16_t)(((uint32_t)k << 14) | ((uint32_t)off & 0x3fffu));
+            }
+            col16[base + (int64_t)j * SLICE] = code;
+        }
+    }
+}
+
 __global__ void gather_f(const double* f, const int32_t* row_of_slot, int64_t NI, double* fs) {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < NI;
          p += (int64_t)gridDim.x * blockDim.x)
@@ -745,6 +835,8 @@ static StepArgs make_args(const rbffd_plan* p) {
     A.w64 = p->w64;
     A.w32 = p->w32;
     A.col = p->col;
+    A.col16 = p->col16;
+    A.sbase = p->sbase;
     A.f = p->fs;
     A.d32 = p->d32;
     A.u0 = p->u[0];
@@ -761,7 +853,7 @@ static void free_plan(rbffd_plan* p) {
     if (!p) return;
     void* bufs[] = {p->perm, p->inv, p->row_of_slot, p->w64, p->w32, p->col, p->u[0], p->u[1],
                     p->fs, p->e[0], p->e[1], p->d32, p->scratch, p->ctrl, p->nslot, p->ncol,
-                    p->nw, p->ng, p->ng0, p->uN};
+                    p->nw, p->ng, p->ng0, p->uN, p->col16, p->sbase};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (p->graph64) cudaGraphExecDestroy((cudaGraphExec_t)p->graph64);
@@ -1219,6 +1311,27 @@ extern "C" int rbffd_plan_create(const double* xyz, const uint8_t* is_bnd, int64
                                 : "rbffd_plan_create: `interior` must list each non-boundary node "
                                   "exactly once (NI = number of interior nodes)");
             st = RBFFD_ERR_ARG;
+            break;
+        }
+        if (!(flags & RBFFD_PACK_IDX32)) {
+            if ((e = cudaMalloc((void**)&p->col16, sizeof(uint16_t) * ell)) != cudaSuccess) break;
+            if ((e = cudaMalloc((void**)&p->sbase, sizeof(int4) * p->nslices)) != cudaSuccess)
+                break;
+            if ((e = cudaMemsetAsync(err.p, 0, 4 * sizeof(unsigned long long), s)) != cudaSuccess)
+                break;
+            pack_idx16<<<G, 256, 0, s>>>(p->col, NI, p->nslices, n, p->col16, p->sbase,
+                                         err.as<unsigned long long>() + 1, err.as<int>());
+            if ((e = cudaGetLastError()) != cudaSuccess) break;
+            if ((e = cudaMemcpyAsync(hv, err.p, sizeof(hv), cudaMemcpyDeviceToHost, s)) !=
+                cudaSuccess)
+                break;
+            if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
+            if (hv[0] & 0xffffffffull) {
+                set_error("rbffd_plan_create: compact index packing failed");
+                st = RBFFD_ERR_CUDA;
+                break;
+            }
+            p->rows16 = (int64_t)hv[1];
         }
     } while (0);
     if (e != cudaSuccess && st == RBFFD_OK) {
@@ -1451,6 +1564,21 @@ extern "C" int rbffd_plan_stats(const rbffd_plan* p, double* h_loop_ms, int64_t*
         h_shape[2] = p->minb[1];
         h_shape[3] = p->per_sm[1];
     }
+    return RBFFD_OK;
+}
+
+extern "C" int rbffd_plan_layout(const rbffd_plan* p, int64_t* h_nslices, int64_t* h_rows16,
+                                 double* h_bytes64, double* h_bytes32) {
+    clear_error();
+    RBFFD_ARG(p, "rbffd_plan_layout: NULL plan");
+    const double NI = (double)p->NI, n = (double)p->n, r16 = (double)p->rows16;
+    // index bytes streamed per step: 2 per entry of a compact row, 4 otherwise,
+    // plus the slices' window bases
+    const double idx = 2.0 * n * r16 + 4.0 * n * (NI - r16) + (p->col16 ? 16.0 * p->nslices : 0.0);
+    if (h_nslices) *h_nslices = p->nslices;
+    if (h_rows16) *h_rows16 = p->rows16;
+    if (h_bytes64) *h_bytes64 = NI * (8.0 * n + 24.0) + idx;
+    if (h_bytes32) *h_bytes32 = NI * (4.0 * n + 12.0) + idx;
     return RBFFD_OK;
 }
 

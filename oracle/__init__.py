@@ -67,6 +67,8 @@ def _load():
     sig = {
         "sm64_at": (u64, [u64, u64]),
         "oracle_nodes": (i64, [i32, i32, i32, f64, u64, P, P, i64]),
+        "oracle_nodes_pds": (i64, [i32, i32, i32, f64, u64, i32, P, P, i64]),
+        "oracle_nodes_pds_cap": (i64, [i32, f64]),
         "oracle_knn_brute": (i32, [P, i64, i32, P, i64, i32, P]),
         "oracle_knn_kdtree": (i32, [P, i64, i32, P, i64, i32, P]),
         "oracle_knn_brute_masked": (i32, [P, i64, i32, P, P, i64, i32, P]),
@@ -125,6 +127,27 @@ def nodes(d: int, shape: int, Kg: int, jitter_frac: float, seed: int):
     N2 = lib.oracle_nodes(d, shape, Kg, jitter_frac, seed, _p(xyz), _p(is_bnd), N)
     assert N2 == N
     return xyz, is_bnd
+
+
+PDS_K = 15
+PDS_ZETA = 1.0 - 1e-10
+
+
+def nodes_pds(shape: int, Kg: int, seed: int, K: int = PDS_K, zeta: float = PDS_ZETA,
+              brute: bool = False):
+    """Poisson-disc node set in 2D (unit square or disk), spacing 1/Kg, boundary
+    seeds first.  Returns (xyz [2, N] float64, is_bnd [N] uint8)."""
+    lib = _load()
+    cap = lib.oracle_nodes_pds_cap(Kg, zeta)
+    if cap < 0:
+        raise ValueError("oracle_nodes_pds: bad arguments")
+    xyz = np.zeros((2, cap), np.float64)
+    is_bnd = np.zeros(cap, np.uint8)
+    N = lib.oracle_nodes_pds(shape, Kg, K, zeta, seed, 1 if brute else 0, _p(xyz), _p(is_bnd),
+                             cap)
+    if N < 0:
+        raise ValueError(f"oracle_nodes_pds failed ({N})")
+    return np.ascontiguousarray(xyz[:, :N]), is_bnd[:N].copy()
 
 
 def _knn(fn, xyz, centres, n):

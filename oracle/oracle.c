@@ -18,6 +18,9 @@
  *   sm64_at            SplitMix64 (Steele, Lea & Flood 2014), counter form
  *   oracle_nodes       jittered-grid stand-in for the Poisson-disc sampler
  *                      of Sec. II-C (test problem); unit d-cube or disk
+ *   oracle_nodes_pds   the Poisson-disc sampler itself (Sec. II-C, last
+ *                      paragraph): boundary seeds, candidates at distance h
+ *                      around each node in first-in first-out order
  *   oracle_knn_brute   support = n nearest nodes incl. the centre (Sec. II,
  *                      text after Eq. 1), ties by lower index
  *   oracle_knn_kdtree  the same set, via a kd-tree (pinned to brute force)
@@ -190,6 +193,172 @@ int64_t oracle_nodes(int d, int shape, int Kg, double jf, uint64_t seed,
         }
     }
     return out;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Poisson-disc node placement (Sec. II-C, last paragraph, after the cited    */
+/* method of Slak and Kosec), 2D, constant spacing h = 1/Kg.                  */
+/*                                                                           */
+/* The node list starts with the seeds, the boundary nodes:                  */
+/*   shape 0 (unit square): the grid points (i*h, j*h) with i or j in {0,Kg}, */
+/*     in row-major order (j fastest), as in oracle_nodes;                     */
+/*   shape 1 (disk, centre (1/2,1/2), R = 1/2): Nb = round(2 pi R / h) nodes  */
+/*     at angles 2 pi k / Nb, as in oracle_nodes.                             */
+/* Then the list is walked in order (first in, first out; nodes appended     */
+/* during the walk are walked too).  Node p proposes K candidates            */
+/*   c_j = p + h u_j,  u_j = R(phi_p) e_j,  e_j at angle 2 pi j / K,         */
+/* with phi_p = 2 pi U_p, U_p the p-th SplitMix64 draw of `seed` (a random   */
+/* rotation of a fixed candidate set per node), j = 0..K-1 in order.  A      */
+/* candidate is appended (as an interior node) when it lies inside the       */
+/* domain (0 < x, y < 1 for the square; |c - centre|^2 < R^2 for the disk)   */
+/* and every node in the list so far is at squared distance >= (zeta h)^2.   */
+/*                                                                           */
+/* Unit vectors: angle reduced to a quadrant, sin/cos by taylor_sincos; the  */
+/* rotation ux = cphi ex - sphi ey, uy = sphi ex + cphi ey; then             */
+/* cx = px + h ux.  Every operation separately rounded.                      */
+/*                                                                           */
+/* Proximity test: with brute != 0 against every node in the list; else via  */
+/* a uniform grid of cells of side cs = (0.99 zeta h)/sqrt(2), which holds at */
+/* most one node per cell (two nodes in one cell would be closer than zeta h),*/
+/* searching the 5 x 5 cells around the candidate's (2 cs > zeta h).  Both   */
+/* ways test the same set of pairs that can be closer than zeta h.           */
+/* Returns N (writes min(N, cap) nodes, SoA xyz[axis*cap + i]), -1 on bad     */
+/* arguments, -2 if a grid cell would hold two nodes.                         */
+/* ------------------------------------------------------------------------- */
+static void unit_dir(double a, double* ux, double* uy)
+{
+    const double half_pi = 1.5707963267948966;
+    int q = (int)(a / half_pi);
+    if (q > 3) q = 3;
+    double r = a - (double)q * half_pi;
+    if (r < 0.0) r = 0.0;
+    double s, c;
+    taylor_sincos(r, &s, &c);
+    switch (q) {
+        case 0: *ux = c;  *uy = s;  break;
+        case 1: *ux = -s; *uy = c;  break;
+        case 2: *ux = -c; *uy = -s; break;
+        default: *ux = s; *uy = -c; break;
+    }
+}
+
+static double pds_cell_side(double zeta, double h)
+{
+    return (0.99 * (zeta * h)) / 1.4142135623730951;
+}
+
+/* grid cells per axis on [0, 1]; also a bound on the node count per axis^2 */
+int64_t oracle_nodes_pds_cap(int Kg, double zeta)
+{
+    if (Kg < 2 || !(zeta > 0.0 && zeta <= 1.0)) return -1;
+    double cs = pds_cell_side(zeta, 1.0 / (double)Kg);
+    int64_t G = (int64_t)(1.0 / cs) + 1;
+    return G * G;
+}
+
+int64_t oracle_nodes_pds(int shape, int Kg, int K, double zeta, uint64_t seed, int brute,
+                         double* xyz, uint8_t* is_bnd, int64_t cap)
+{
+    const double two_pi = 6.283185307179586;
+    if ((shape != 0 && shape != 1) || Kg < 2 || K < 1 || K > 64) return -1;
+    if (!(zeta > 0.0 && zeta <= 1.0)) return -1;
+    const double h = 1.0 / (double)Kg;
+    const double cs = pds_cell_side(zeta, h);
+    const int64_t G = (int64_t)(1.0 / cs) + 1;
+    const int64_t maxn = G * G;
+    const double t = zeta * h;
+    const double r2 = t * t;
+    double* X = (double*)malloc(sizeof(double) * (size_t)maxn);
+    double* Y = (double*)malloc(sizeof(double) * (size_t)maxn);
+    uint8_t* B = (uint8_t*)malloc((size_t)maxn);
+    int32_t* cell = (int32_t*)malloc(sizeof(int32_t) * (size_t)maxn);
+    double* ex = (double*)malloc(sizeof(double) * (size_t)K);
+    double* ey = (double*)malloc(sizeof(double) * (size_t)K);
+    int64_t N = 0, ret = 0;
+    if (!X || !Y || !B || !cell || !ex || !ey) { ret = -1; goto done; }
+    for (int64_t c = 0; c < maxn; ++c) cell[c] = -1;
+    for (int j = 0; j < K; ++j) unit_dir((two_pi * (double)j) / (double)K, &ex[j], &ey[j]);
+
+    /* seeds */
+    if (shape == 0) {
+        for (int64_t i = 0; i <= Kg; ++i)
+            for (int64_t j = 0; j <= Kg; ++j) {
+                if (!(i == 0 || i == Kg || j == 0 || j == Kg)) continue;
+                X[N] = (double)i * h;
+                Y[N] = (double)j * h;
+                B[N] = 1;
+                ++N;
+            }
+    } else {
+        int64_t Nb = disk_nb(Kg);
+        for (int64_t k = 0; k < Nb; ++k) {
+            disk_point(k, Nb, 0.5, &X[N], &Y[N]);
+            B[N] = 1;
+            ++N;
+        }
+    }
+    for (int64_t i = 0; i < N; ++i) {
+        int64_t gx = (int64_t)(X[i] / cs), gy = (int64_t)(Y[i] / cs);
+        if (cell[gx * G + gy] >= 0) { ret = -2; goto done; }
+        cell[gx * G + gy] = (int32_t)i;
+    }
+
+    /* walk the list in order */
+    for (int64_t p = 0; p < N; ++p) {
+        double ux0, uy0;
+        unit_dir(two_pi * u01(seed, (uint64_t)p), &ux0, &uy0);
+        for (int j = 0; j < K; ++j) {
+            double ux = ux0 * ex[j] - uy0 * ey[j];
+            double uy = uy0 * ex[j] + ux0 * ey[j];
+            double cx = X[p] + h * ux;
+            double cy = Y[p] + h * uy;
+            int inside;
+            if (shape == 0) {
+                inside = cx > 0.0 && cx < 1.0 && cy > 0.0 && cy < 1.0;
+            } else {
+                double dx = cx - 0.5, dy = cy - 0.5;
+                inside = dx * dx + dy * dy < 0.25;
+            }
+            if (!inside) continue;
+            int far = 1;
+            if (brute) {
+                for (int64_t q = 0; q < N && far; ++q) {
+                    double dx = cx - X[q], dy = cy - Y[q];
+                    if (dx * dx + dy * dy < r2) far = 0;
+                }
+            } else {
+                int64_t gx = (int64_t)(cx / cs), gy = (int64_t)(cy / cs);
+                for (int64_t a = gx - 2; a <= gx + 2 && far; ++a) {
+                    if (a < 0 || a >= G) continue;
+                    for (int64_t b = gy - 2; b <= gy + 2 && far; ++b) {
+                        if (b < 0 || b >= G) continue;
+                        int32_t q = cell[a * G + b];
+                        if (q < 0) continue;
+                        double dx = cx - X[q], dy = cy - Y[q];
+                        if (dx * dx + dy * dy < r2) far = 0;
+                    }
+                }
+            }
+            if (!far) continue;
+            if (N >= maxn) { ret = -2; goto done; }
+            int64_t gx = (int64_t)(cx / cs), gy = (int64_t)(cy / cs);
+            if (cell[gx * G + gy] >= 0) { ret = -2; goto done; }
+            cell[gx * G + gy] = (int32_t)N;
+            X[N] = cx;
+            Y[N] = cy;
+            B[N] = 0;
+            ++N;
+        }
+    }
+    for (int64_t i = 0; i < N && i < cap; ++i) {
+        xyz[i] = X[i];
+        xyz[cap + i] = Y[i];
+        is_bnd[i] = B[i];
+    }
+    ret = N;
+done:
+    free(X); free(Y); free(B); free(cell); free(ex); free(ey);
+    return ret;
 }
 
 /* ------------------------------------------------------------------------- */

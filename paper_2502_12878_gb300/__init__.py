@@ -51,6 +51,7 @@ EXPORTED = [
     "rbffd_batch_destroy", "rbffd_solve_batch", "rbffd_batch_set_shape", "rbffd_batch_stats",
     "rbffd_error", "rbffd_batch_domain_times", "rbffd_batch_set_costs", "rbffd_adjoint_w",
     "rbffd_knn_masked", "rbffd_weights_dir", "rbffd_plan_set_neumann", "rbffd_plan_layout",
+    "rbffd_nodes_pds", "rbffd_nodes_pds_cap",
 ]
 RBFFD_KNN_NOALLOC_MAX_NODES = 262144
 
@@ -109,6 +110,8 @@ def lib():
         "rbffd_weights_dir": (I, [P, I64, I, P, I64, I, I, P, P, P, PI64, PI64, P]),
         "rbffd_plan_set_neumann": (I, [P, I64, P, P, P, I, P, P]),
         "rbffd_plan_layout": (I, [P, PI64, PI64, PD, PD]),
+        "rbffd_nodes_pds": (I, [I, I, I, I, D, U64, P, P, I64, PI64, PI64, P]),
+        "rbffd_nodes_pds_cap": (I, [I, D, PI64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -156,6 +159,27 @@ def rbffd_nodes(d: int, shape: int, Kg: int, jitter_frac: float, seed: int, devi
     _check(L.rbffd_nodes(d, shape, Kg, jitter_frac, seed, _ptr(xyz), _ptr(bnd), N,
                          ctypes.byref(n), s))
     return xyz, bnd
+
+
+PDS_K = 15
+PDS_ZETA = 1.0 - 1e-10
+
+
+def rbffd_nodes_pds(shape: int, Kg: int, seed: int, K: int = PDS_K, zeta: float = PDS_ZETA,
+                    device="cuda"):
+    """Poisson-disc node set in 2D (unit square or disk), spacing 1/Kg, boundary seeds
+    first.  Returns (xyz [2, N] float64, is_bnd [N] uint8, generations walked)."""
+    L = lib()
+    cap = ctypes.c_int64(0)
+    _check(L.rbffd_nodes_pds_cap(Kg, zeta, ctypes.byref(cap)))
+    xyz = torch.empty((2, cap.value), dtype=torch.float64, device=device)
+    bnd = torch.empty(cap.value, dtype=torch.uint8, device=device)
+    n = ctypes.c_int64(0)
+    rounds = (ctypes.c_int64 * 2)()
+    _check(L.rbffd_nodes_pds(2, shape, Kg, K, zeta, seed, _ptr(xyz), _ptr(bnd), cap.value,
+                             ctypes.byref(n), rounds, _stream(device)))
+    N = n.value
+    return xyz[:, :N].contiguous(), bnd[:N].clone(), rounds[0]
 
 
 def rbffd_interior(is_bnd: torch.Tensor) -> torch.Tensor:

@@ -7,21 +7,9 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "nodegen.cuh"
 
 namespace rbffd {
-
-// SplitMix64 (Steele, Lea & Flood 2014): the c-th output of the generator
-// seeded with `seed`, i.e. the finaliser applied to seed + (c+1)*golden.
-__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t c) {
-    uint64_t z = seed + (c + 1ull) * 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
-__device__ __forceinline__ double unit_draw(uint64_t seed, uint64_t c) {
-    return __dmul_rn((double)(splitmix64_at(seed, c) >> 11), 1.0 / 9007199254740992.0);
-}
 
 struct NodeGen {
     int d, shape, Kg;
@@ -100,39 +88,14 @@ __global__ void nodes_disk_write(NodeGen g, int64_t total, const int32_t* pos, d
     }
 }
 
-// sin and cos on [0, pi/2]: Taylor series through x^21 / x^20 in Horner form
-__device__ void series_sincos(double x, double* s, double* c) {
-    double x2 = __dmul_rn(x, x);
-    double ps = 1.0, pc = 1.0;
-    for (int k = 10; k >= 1; --k) {
-        double den_s = (double)((2 * k) * (2 * k + 1));
-        double den_c = (double)((2 * k - 1) * (2 * k));
-        ps = __dsub_rn(1.0, __dmul_rn(__ddiv_rn(x2, den_s), ps));
-        pc = __dsub_rn(1.0, __dmul_rn(__ddiv_rn(x2, den_c), pc));
-    }
-    *s = __dmul_rn(x, ps);
-    *c = pc;
-}
-
 __global__ void nodes_disk_boundary(int64_t Nb, int64_t first, double* xyz, uint8_t* is_bnd,
                                     int64_t cap) {
     const double two_pi = 6.283185307179586;
-    const double half_pi = 1.5707963267948966;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < Nb;
          k += (int64_t)gridDim.x * blockDim.x) {
         double a = __ddiv_rn(__dmul_rn(two_pi, (double)k), (double)Nb);
-        int q = (int)__ddiv_rn(a, half_pi);
-        if (q > 3) q = 3;
-        double r = __dsub_rn(a, __dmul_rn((double)q, half_pi));
-        if (r < 0.0) r = 0.0;
-        double s, c, cx, cy;
-        series_sincos(r, &s, &c);
-        switch (q) {
-            case 0: cx = c; cy = s; break;
-            case 1: cx = -s; cy = c; break;
-            case 2: cx = -c; cy = -s; break;
-            default: cx = s; cy = -c; break;
-        }
+        double cx, cy;
+        unit_dir(a, &cx, &cy);
         int64_t o = first + k;
         xyz[o] = __dadd_rn(0.5, __dmul_rn(0.5, cx));
         xyz[cap + o] = __dadd_rn(0.5, __dmul_rn(0.5, cy));

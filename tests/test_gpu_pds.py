@@ -1,0 +1,101 @@
+"""Poisson-disc node placement on the GPU against the oracle's sequential walk.
+
+The GPU walks one generation at a time (candidates tested in parallel, the
+conflicts among a generation's candidates resolved in key order); the node
+list must equal the oracle's first-in first-out walk bit for bit: same
+count, same coordinates, same order, same boundary flags.  Also: the error
+paths, and the explicit solve on a Poisson-disc node set against the oracle.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import rbffd_inputs as gen
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_12878_gb300 import build as nvbuild
+    nvbuild.build()
+    import paper_2502_12878_gb300 as m
+    m.lib()
+    return m
+
+
+def H(t):
+    return t.cpu().numpy()
+
+
+@pytest.mark.parametrize("shape,Kg,seed,K,zeta", [
+    (0, 40, 1, 15, 1 - 1e-10),
+    (0, 123, 2, 15, 1 - 1e-10),
+    (1, 60, 3, 15, 1 - 1e-10),
+    (1, 151, 4, 15, 1 - 1e-10),
+    (0, 90, 5, 9, 1 - 1e-10),
+    (0, 90, 6, 24, 0.8),
+    (1, 2, 7, 15, 1 - 1e-10),          # tiny: the disk boundary alone nearly fills it
+])
+def test_pds_bit_exact(rb, orc, shape, Kg, seed, K, zeta):
+    xyz, bnd, rounds = rb.rbffd_nodes_pds(shape, Kg, seed, K=K, zeta=zeta)
+    oxyz, obnd = orc.nodes_pds(shape, Kg, seed, K=K, zeta=zeta)
+    assert xyz.shape == oxyz.shape
+    assert np.array_equal(H(xyz), oxyz) and np.array_equal(H(bnd), obnd)
+    assert rounds >= 1
+
+
+def test_pds_full_size_bit_exact(rb, orc):
+    """h = 1e-3 on the unit square: 873,547 nodes, several hundred generations."""
+    xyz, bnd, rounds = rb.rbffd_nodes_pds(0, 1000, 2)
+    oxyz, obnd = orc.nodes_pds(0, 1000, 2)
+    assert np.array_equal(H(xyz), oxyz) and np.array_equal(H(bnd), obnd)
+    assert 300 < rounds < 2000
+
+
+def test_pds_errors(rb):
+    L = rb.lib()
+    n, r = ctypes.c_int64(0), (ctypes.c_int64 * 2)()
+    buf = torch.empty((2, 10), dtype=torch.float64, device="cuda")
+    b = torch.empty(10, dtype=torch.uint8, device="cuda")
+    s = rb._stream("cuda")
+    code = L.rbffd_nodes_pds(2, 0, 20, 15, 1 - 1e-10, 1, rb._ptr(buf), rb._ptr(b), 10,
+                             ctypes.byref(n), r, s)
+    assert code == rb.RBFFD_ERR_CAPACITY and n.value > 10
+    for args in ((3, 0, 20, 15, 0.9), (2, 2, 20, 15, 0.9), (2, 0, 20, 0, 0.9),
+                 (2, 0, 20, 65, 0.9), (2, 0, 20, 15, 0.0), (2, 0, 1, 15, 0.9)):
+        code = L.rbffd_nodes_pds(*args, 1, rb._ptr(buf), rb._ptr(b), 10, ctypes.byref(n),
+                                 r, s)
+        assert code == rb.RBFFD_ERR_ARG
+
+
+def test_solve_on_pds_nodes(rb, orc):
+    """Supports, weights and 300 explicit steps on a Poisson-disc node set (m=4)."""
+    Kg, m, seed = 50, 4, 9
+    n = gen.stencil_size(2, m)
+    xyz, bnd, _ = rb.rbffd_nodes_pds(0, Kg, seed)
+    oxyz, obnd = orc.nodes_pds(0, Kg, seed)
+    inter = rb.rbffd_interior(bnd)
+    ointer = gen.interior_ids(obnd)
+    idx = rb.rbffd_knn(xyz, inter, n)
+    oidx = orc.knn_kdtree(oxyz, ointer, n)
+    assert np.array_equal(H(idx), oidx)
+    w, st = rb.rbffd_weights(xyz, idx, m)
+    ow, ost = orc.weights(oxyz, oidx, m)
+    assert np.all(ost == 0) and np.array_equal(H(st), ost)
+    assert np.all(np.abs(H(w) - ow) <= 1e-12 * np.abs(ow).max(axis=1, keepdims=True))
+    f = gen.source(oxyz, ointer)
+    u0 = gen.start_iterate(oxyz, obnd)
+    dt = 0.9 * orc.stable_dt(ow, oidx, ointer, oxyz.shape[1], gen.random_vector(len(ointer), 3),
+                             200)
+    ou, osteps, ores, _ = orc.solve_explicit(ow, oidx, ointer, f, u0, dt, 300, 0.0)
+    plan = rb.Plan(xyz, bnd, inter, idx, w)
+    u = torch.from_numpy(u0).cuda()
+    code, steps, res = plan.solve_explicit(torch.from_numpy(f).cuda(), u, dt, 300, 0.0)
+    assert steps == osteps == 300
+    assert np.max(np.abs(H(u) - ou)) <= 1e-12 * np.max(np.abs(ou))
+    plan.destroy()

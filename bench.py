@@ -494,6 +494,45 @@ def run_workload(args):
         plan.destroy()
         return
 
+    if args.workload == "pds1M_m4":
+        # the paper's node placement (Sec. II-C): Poisson-disc fill of the unit square
+        # from boundary seeds, h = 1/1070 (1,000,188 nodes), then FP64 sweeps on it
+        Kg, seed = 1070, 2
+        rb.rbffd_nodes_pds(0, 100, seed)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xyz, bnd, rounds = rb.rbffd_nodes_pds(0, Kg, seed)
+        torch.cuda.synchronize()
+        gen_ms = (time.perf_counter() - t0) * 1e3
+        cpu = None
+        if not args.no_cpu_baseline:
+            import oracle
+            t0 = time.perf_counter()
+            oxyz, obnd = oracle.nodes_pds(0, Kg, seed)
+            cpu_ms = (time.perf_counter() - t0) * 1e3
+            cpu = {"value": cpu_ms, "unit": "ms (node placement)", "cores": 1, "kind": "oracle",
+                   "sample": f"the whole sequential walk, {oxyz.shape[1]} nodes",
+                   "bit_equal_to_gpu": bool(np.array_equal(oxyz, xyz.cpu().numpy()))}
+        Q = _gpu_problem_from_nodes(rb, torch, xyz, bnd, 4, dev)
+        plan, f, u0, NI = Q["plan"], Q["f"], Q["u0"], Q["NI"]
+        u = u0.clone()
+        plan.solve_explicit(f, u, Q["dt"], 64, 0.0)
+        S = 200
+        plan.solve_explicit(f, u, Q["dt"], S, 0.0)
+        ms, k, nl, shape = plan.stats()
+        per = ms * 1e-3 / k
+        lay = plan.layout()
+        _line(f"Poisson-disc nodes (Sec. II-C): 2D unit square, h = 1/{Kg}, {Q['N']:,} nodes "
+              f"({NI:,} interior), m=4 (n=30), FP64 sweeps, Morton-packed plan",
+              NI / per, UNIT, per * 1e3 * S, S, 64,
+              {"node_placement_gpu_ms": gen_ms, "generations": rounds,
+               "alg_GBps": lay["bytes64"] / per / 1e9,
+               "frac_hbm": lay["bytes64"] / per / 1e9 / hbm,
+               "rows16_frac": lay["rows16"] / NI, "rho_h2": Q["rho"] / Kg ** 2,
+               "launch_shape": shape, "cpu_baseline": cpu})
+        plan.destroy()
+        return
+
     if args.workload == "support_sweep":
         # the support-size study at m = 2 (n > 2M), 2D square 1,002,001 nodes
         xyz, bnd = rb.rbffd_nodes(2, 0, 1000, 0.3, 2, device=dev)
@@ -587,6 +626,14 @@ def run_stage(args):
         torch.cuda.synchronize()
         batch.destroy()
         return
+    if args.mode == "pds":
+        rb.rbffd_nodes_pds(0, args.Kg, SEED)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        rb.rbffd_nodes_pds(0, args.Kg, SEED)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        return
     n = gen.stencil_size(D, args.m)
     xyz, bnd = rb.rbffd_nodes(D, 0, args.Kg, 0.3, SEED, device=dev)
     inter = rb.rbffd_interior(bnd)
@@ -631,10 +678,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--mode", default="bench",
-                    choices=["bench", "sweep", "weights", "knn", "adjoint", "batch", "dc"],
+                    choices=["bench", "sweep", "weights", "knn", "adjoint", "batch", "dc", "pds"],
                     help="build the workload and run only that stage: FP64 sweeps, weights, "
-                         "kNN, reverse sweeps, batched solve, or FP32 inner sweeps of one "
-                         "defect correction (driver for profiler captures; prints nothing)")
+                         "kNN, reverse sweeps, batched solve, FP32 inner sweeps of one "
+                         "defect correction, or Poisson-disc node placement of the unit "
+                         "square with h = 1/Kg (driver for profiler captures; prints nothing)")
     ap.add_argument("--m", type=int, default=M, help="monomial order of the workload")
     ap.add_argument("--Kg", type=int, default=KG, help="grid cells per side of the workload")
     ap.add_argument("--sweeps", type=int, default=5, help="sweeps in --mode sweep")
@@ -642,7 +690,7 @@ def main():
     ap.add_argument("--batch-domains", type=int, default=256, help="domains in --mode batch")
     ap.add_argument("--workload", default="square1M_m4",
                     choices=["square1M_m4", "batched256", "cube8M_m4", "adjoint1M_m4", "tta",
-                             "mixed1M_m4", "support_sweep"],
+                             "mixed1M_m4", "support_sweep", "pds1M_m4"],
                     help="square1M_m4 is the headline; the others measure the other workloads")
     args = ap.parse_args()
     if args.workload != "square1M_m4":

@@ -42,7 +42,7 @@ namespace rbffd {
 static constexpr int PDS_KMAX = 64;
 static constexpr int PDS_BLOCK = 1024;
 
-enum : signed char { PDS_UND = 0, PDS_IN = 1, PDS_OUT = 2 };
+enum : int { PDS_UND = 0, PDS_IN = 1, PDS_OUT = 2 };
 
 struct PdsCtrl {
     long long lo, hi;   // the generation being walked: nodes [lo, hi)
@@ -59,17 +59,19 @@ struct PdsArgs {
     double* X;
     double* Y;
     uint8_t* B;
-    double* rc;          // [maxn] cos of each node's rotation angle
+    double* rc;          // [maxn] cos of each node's rotation angle (set when it is added)
     double* rs;          // [maxn] sin
     int32_t* cell;       // [G*G] node id per cell, -1 empty
     int32_t* chead;      // [G*G] candidate list heads, -1 empty
     int32_t* cnext;      // [capC]
     double* cx;          // [capC] candidates of the generation, index a*K + j
     double* cy;
+    int32_t* ccell;      // [capC] grid cell of each candidate inside the domain
     uint8_t* cflag;      // [capC] passed the domain and earlier-generation tests
     int32_t* V;          // [capC] keys of the passing candidates, ascending
-    signed char* state;  // [capC] by position in V (when shared memory is too small)
-    int32_t* deg;        // [capC] lower-key conflicts of each passing candidate
+    int32_t* state;      // [capC] by position in V (when shared memory is too small)
+    int32_t* deg;        // [capC] lower-key conflicts of each passing candidate; after the
+                         // passes, the rank of an accepted candidate (-1 otherwise)
     int32_t* off;        // [capC + 1] their CSR offsets
     int32_t* adj;        // [capA] the conflicting lower-key positions
     const double* ex;    // [K] fixed candidate directions
@@ -77,6 +79,7 @@ struct PdsArgs {
     PdsCtrl* ctrl;
     int shape, K;
     double h, cs, r2;
+    float inv_cs;        // 1 / cs in FP32, for grid cells
     int64_t G, maxn, capF, capA;
     uint64_t seed;
 };
@@ -92,8 +95,25 @@ __device__ __forceinline__ double pds_d2(double ax, double ay, double bx, double
     return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
 }
 
+// Grid cell of a point in [0, 1]^2, in FP32.  The grid only accelerates the
+// proximity tests (every decision compares exact FP64 squared distances), so
+// any cell map keeping two properties gives the same node list: at most one
+// node per cell and every node within zeta h of a point inside the 5 x 5
+// cells around the point's cell.  With cells of side 0.99 zeta h / sqrt 2,
+// FP32 rounding (below 1e-7 in the unit square, h >= 5e-5) moves a point by
+// far less than the 1 % margin on both.  One FP64 division per axis would
+// cost more than the rest of a candidate's work on this GPU's FP64 pipe.
+__device__ __forceinline__ void pds_cell_xy(const PdsArgs& A, double x, double y, int64_t* gx,
+                                            int64_t* gy) {
+    int64_t a = (int64_t)__fmul_rn(__double2float_rn(x), A.inv_cs);
+    int64_t b = (int64_t)__fmul_rn(__double2float_rn(y), A.inv_cs);
+    *gx = a < 0 ? 0 : (a >= A.G ? A.G - 1 : a);
+    *gy = b < 0 ? 0 : (b >= A.G ? A.G - 1 : b);
+}
+
 __device__ __forceinline__ int64_t pds_cell_of(const PdsArgs& A, double x, double y) {
-    int64_t gx = (int64_t)__ddiv_rn(x, A.cs), gy = (int64_t)__ddiv_rn(y, A.cs);
+    int64_t gx, gy;
+    pds_cell_xy(A, x, y, &gx, &gy);
     return gx * A.G + gy;
 }
 
@@ -132,6 +152,7 @@ __global__ void pds_seeds(PdsArgs A, int Kg, int64_t nb) {
         A.B[s] = 1;
         if (atomicCAS(&A.cell[pds_cell_of(A, x, y)], -1, (int32_t)s) != -1)
             atomicExch(&A.ctrl->err, 1);
+        unit_dir(__dmul_rn(two_pi, unit_draw(A.seed, (uint64_t)s)), &A.rc[s], &A.rs[s]);
     }
 }
 
@@ -142,22 +163,10 @@ __global__ void pds_dirs(int K, double* ex, double* ey) {
     if (j < K) unit_dir(__ddiv_rn(__dmul_rn(two_pi, (double)j), (double)K), &ex[j], &ey[j]);
 }
 
-// rotation of each node of the generation: angle 2 pi U_p
-__global__ void pds_rot(PdsArgs A) {
-    const double two_pi = 6.283185307179586;
-    const long long lo = A.ctrl->lo, hi = A.ctrl->hi;
-    if (A.ctrl->err) return;
-    for (long long p = lo + (long long)blockIdx.x * blockDim.x + threadIdx.x; p < hi;
-         p += (long long)gridDim.x * blockDim.x) {
-        double c, s;
-        unit_dir(__dmul_rn(two_pi, unit_draw(A.seed, (uint64_t)p)), &c, &s);
-        A.rc[p] = c;
-        A.rs[p] = s;
-    }
-}
-
 // candidates of the generation, tested against the domain and the nodes of
-// earlier generations (5 x 5 cells: 2 cs > zeta h)
+// earlier generations (5 x 5 cells: 2 cs > zeta h); one thread per candidate
+// (a warp-wide FP64 instruction costs the FP64 pipe the same whatever the
+// number of active lanes, so the lanes each take a candidate)
 __global__ void pds_gen(PdsArgs A) {
     const long long lo = A.ctrl->lo, hi = A.ctrl->hi;
     if (A.ctrl->err || hi <= lo) return;
@@ -179,7 +188,9 @@ __global__ void pds_gen(PdsArgs A) {
         A.cy[e] = y;
         bool ok = pds_inside(A.shape, x, y);
         if (ok) {
-            const int64_t gx = (int64_t)__ddiv_rn(x, A.cs), gy = (int64_t)__ddiv_rn(y, A.cs);
+            int64_t gx, gy;
+            pds_cell_xy(A, x, y, &gx, &gy);
+            A.ccell[e] = (int32_t)(gx * A.G + gy);
             for (int64_t a = gx - 2; a <= gx + 2 && ok; ++a) {
                 if (a < 0 || a >= A.G) continue;
                 for (int64_t b = gy - 2; b <= gy + 2 && ok; ++b) {
@@ -222,8 +233,9 @@ __device__ long long block_excl_scan(long long v, long long* total) {
     return before;
 }
 
-// one generation, step 1 (one block): the passing candidates in key order,
-// and per grid cell the list of them
+// one generation, step 1 (one block): the passing candidates in key order
+// (flags read four at a time, tiles of 4 x PDS_BLOCK keys), and per grid cell
+// the list of them
 __global__ void __launch_bounds__(PDS_BLOCK, 1) pds_compact(PdsArgs A) {
     __shared__ long long s_total;
     __shared__ int s_skip;
@@ -237,44 +249,59 @@ __global__ void __launch_bounds__(PDS_BLOCK, 1) pds_compact(PdsArgs A) {
     __syncthreads();
     if (s_skip) return;
     const long long total = s_total;
-    const long long per = (total + PDS_BLOCK - 1) / PDS_BLOCK;
-    const long long e0 = min(total, (long long)t * per), e1 = min(total, e0 + per);
-    long long cnt = 0;
-    for (long long e = e0; e < e1; ++e) cnt += A.cflag[e];
-    long long nv;
-    long long pos = block_excl_scan(cnt, &nv);
-    for (long long e = e0; e < e1; ++e)
-        if (A.cflag[e]) A.V[pos++] = (int32_t)e;
+    long long nv = 0;
+    for (long long base = 0; base < total; base += 4 * PDS_BLOCK) {
+        const long long e = base + 4 * (long long)t;
+        unsigned f = 0;
+        if (e + 3 < total) {
+            const uchar4 q = *reinterpret_cast<const uchar4*>(A.cflag + e);
+            f = (q.x ? 1u : 0u) | (q.y ? 2u : 0u) | (q.z ? 4u : 0u) | (q.w ? 8u : 0u);
+        } else {
+            for (int i = 0; i < 4; ++i)
+                if (e + i < total && A.cflag[e + i]) f |= 1u << i;
+        }
+        long long tile_n;
+        long long pos = nv + block_excl_scan(__popc(f), &tile_n);
+        for (int i = 0; i < 4; ++i)
+            if (f & (1u << i)) A.V[pos++] = (int32_t)(e + i);
+        nv += tile_n;
+    }
     __syncthreads();
     for (long long v = t; v < nv; v += PDS_BLOCK) {
         const int32_t e = A.V[v];
-        A.cnext[v] = atomicExch(&A.chead[pds_cell_of(A, A.cx[e], A.cy[e])], (int32_t)v);
+        A.cnext[v] = atomicExch(&A.chead[A.ccell[e]], (int32_t)v);
     }
     if (t == 0) A.ctrl->nv = nv;
 }
 
 // step 2 (whole grid): the lower-key conflicts of each passing candidate;
-// FILL = false counts them, FILL = true writes them at the CSR offsets
+// FILL = false counts them, FILL = true writes them at the CSR offsets.  One
+// thread per candidate: the 25 list heads are loaded first (independent
+// loads), then the few non-empty lists are walked.
 template <bool FILL>
 __global__ void pds_conflicts(PdsArgs A) {
     const long long nv = ((volatile PdsCtrl*)A.ctrl)->nv;
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nv;
          v += (long long)gridDim.x * blockDim.x) {
-        const int32_t e = A.V[v];
-        const double x = A.cx[e], y = A.cy[e];
-        const int64_t gx = (int64_t)__ddiv_rn(x, A.cs), gy = (int64_t)__ddiv_rn(y, A.cs);
+        const int32_t ev = A.V[v];
+        const double x = A.cx[ev], y = A.cy[ev];
+        const int32_t cv = A.ccell[ev];
+        const long long gx = cv / A.G, gy = cv % A.G;
+        int32_t head[25];
+#pragma unroll
+        for (int l = 0; l < 25; ++l) {
+            const long long a = gx - 2 + l / 5, b = gy - 2 + l % 5;
+            head[l] = (a >= 0 && a < A.G && b >= 0 && b < A.G) ? A.chead[a * A.G + b] : -1;
+        }
         int32_t k = FILL ? A.off[v] : 0;
-        for (int64_t a = gx - 2; a <= gx + 2; ++a) {
-            if (a < 0 || a >= A.G) continue;
-            for (int64_t b = gy - 2; b <= gy + 2; ++b) {
-                if (b < 0 || b >= A.G) continue;
-                for (int32_t w = A.chead[a * A.G + b]; w >= 0; w = A.cnext[w]) {
-                    if (w >= v) continue;
-                    const int32_t ew = A.V[w];
-                    if (!(pds_d2(x, y, A.cx[ew], A.cy[ew]) < A.r2)) continue;
-                    if (FILL) A.adj[k] = w;
-                    ++k;
-                }
+#pragma unroll
+        for (int l = 0; l < 25; ++l) {
+            for (int32_t w = head[l]; w >= 0; w = A.cnext[w]) {
+                if (w >= v) continue;
+                const int32_t ew = A.V[w];
+                if (!(pds_d2(x, y, A.cx[ew], A.cy[ew]) < A.r2)) continue;
+                if (FILL) A.adj[k] = w;
+                ++k;
             }
         }
         if (!FILL) A.deg[v] = k;
@@ -305,10 +332,52 @@ __global__ void __launch_bounds__(PDS_BLOCK, 1) pds_offsets(PdsArgs A) {
     }
 }
 
+// The passes of the walk's choice over states st, CSR lists off/adj; thread t
+// walks keys [t*per, (t+1)*per) in ascending order.  Returns the number of
+// passes.  Each candidate is a chain of dependent loads (its state, its list
+// bounds, a neighbour, the neighbour's state), so the loads' latency is the
+// cost: the range length is odd, so the 32 lanes of a warp read 32 different
+// shared-memory banks, and states are whole words.  A thread need not see the
+// other threads' updates within a pass (only its own, in program order, and
+// all of them after the barrier), so the states are plain memory.
+__device__ __forceinline__ int resolve_passes(int32_t* st, const int32_t* off,
+                                              const int32_t* adj, int nv, int t) {
+    // ranges of about 32 keys: long enough that most conflict chains stay
+    // inside one range, short enough that the passes are short
+    int per = (nv + PDS_BLOCK - 1) / PDS_BLOCK;
+    per = per < 31 ? 31 : per;
+    per |= 1;
+    const int v0 = min(nv, t * per), v1 = min(nv, v0 + per);
+    int pass = 0;
+    for (; pass <= nv; ++pass) {
+        int open = 0;
+        for (int v = v0; v < v1; ++v) {
+            if (st[v] != PDS_UND) continue;
+            bool in_lower = false, und_lower = false;
+            const int k1 = off[v + 1];
+            for (int k = off[v]; k < k1; ++k) {
+                const int sw = st[adj[k]];
+                if (sw == PDS_IN) {
+                    in_lower = true;
+                    break;
+                }
+                if (sw == PDS_UND) und_lower = true;
+            }
+            if (in_lower) st[v] = PDS_OUT;
+            else if (!und_lower) st[v] = PDS_IN;
+            else open = 1;
+        }
+        if (!__syncthreads_or(open)) break;
+    }
+    return pass + 1;
+}
+
 // step 4 (one block): the walk's choice, then the accepted candidates
-// appended in key order; dynamic shared memory holds the states
-__global__ void __launch_bounds__(PDS_BLOCK, 1) pds_resolve(PdsArgs A, int smem_states) {
-    extern __shared__ signed char s_state[];
+// appended in key order.  Dynamic shared memory holds the states and, when
+// it fits, a copy of the conflict lists (the passes then read shared memory
+// only); otherwise both stay in global memory.
+__global__ void __launch_bounds__(PDS_BLOCK, 1) pds_resolve(PdsArgs A, int smem_bytes) {
+    extern __shared__ int4 s_dyn[];
     __shared__ long long s_N, s_nv;
     __shared__ int s_skip;
     const int t = threadIdx.x;
@@ -321,73 +390,87 @@ __global__ void __launch_bounds__(PDS_BLOCK, 1) pds_resolve(PdsArgs A, int smem_
     __syncthreads();
     if (s_skip) return;
     const long long nv = s_nv;
-    volatile signed char* st = nv <= smem_states ? s_state : A.state;
-    for (long long v = t; v < nv; v += PDS_BLOCK) st[v] = PDS_UND;
-    __syncthreads();
-    // ranges of about 32 keys: long enough that most conflict chains stay
-    // inside one range, short enough that the passes are short
-    long long T = (nv + 31) / 32;
-    T = T < 32 ? 32 : (T > PDS_BLOCK ? PDS_BLOCK : T);
-    long long per = (nv + T - 1) / T;
-    long long v0 = t < T ? min(nv, (long long)t * per) : nv;
-    long long v1 = t < T ? min(nv, v0 + per) : nv;
-    long long pass = 0;
-    for (; pass <= nv; ++pass) {
-        int open = 0;
-        for (long long v = v0; v < v1; ++v) {
-            if (st[v] != PDS_UND) continue;
-            bool in_lower = false, und_lower = false;
-            const int32_t k1 = A.off[v + 1];
-            for (int32_t k = A.off[v]; k < k1; ++k) {
-                const signed char sw = st[A.adj[k]];
-                if (sw == PDS_IN) {
-                    in_lower = true;
-                    break;
-                }
-                if (sw == PDS_UND) und_lower = true;
+    const long long nnz = nv ? A.off[nv] : 0;   // no offsets are written for nv = 0
+    const long long st_bytes = (4 * nv + 15) / 16 * 16;
+    const long long off4 = (nv + 1 + 3) / 4, adj4 = (nnz + 3) / 4;   // int4 units
+    const bool fit = st_bytes + 16 * (off4 + adj4) <= (long long)smem_bytes;
+    int32_t* st;
+    int passes;
+    if (fit) {
+        signed char* base = reinterpret_cast<signed char*>(s_dyn);
+        int32_t* sst = reinterpret_cast<int32_t*>(base);
+        int4* so = reinterpret_cast<int4*>(base + st_bytes);
+        // the conflict lists into shared memory, four independent 16-byte loads
+        // per thread in flight (the buffers are padded to whole int4s)
+        const int4* go = reinterpret_cast<const int4*>(A.off);
+        const int4* ga = reinterpret_cast<const int4*>(A.adj);
+        for (long long i = t; i < off4 + adj4; i += 4 * PDS_BLOCK) {
+            int4 r[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const long long k = i + (long long)u * PDS_BLOCK;
+                if (k < off4 + adj4) r[u] = __ldcg(k < off4 ? go + k : ga + (k - off4));
             }
-            if (in_lower) st[v] = PDS_OUT;
-            else if (!und_lower) st[v] = PDS_IN;
-            else open = 1;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const long long k = i + (long long)u * PDS_BLOCK;
+                if (k < off4 + adj4) so[k] = r[u];
+            }
         }
-        __threadfence_block();
-        if (!__syncthreads_or(open)) break;
+        for (long long v = t; v < nv; v += PDS_BLOCK) sst[v] = PDS_UND;
+        __syncthreads();
+        passes = resolve_passes(sst, reinterpret_cast<const int32_t*>(so),
+                                reinterpret_cast<const int32_t*>(so + off4), (int)nv, t);
+        st = sst;
+    } else {
+        for (long long v = t; v < nv; v += PDS_BLOCK) A.state[v] = PDS_UND;
+        __syncthreads();
+        passes = resolve_passes(A.state, A.off, A.adj, (int)nv, t);
+        st = A.state;
     }
-    // append the accepted in key order
-    per = (nv + PDS_BLOCK - 1) / PDS_BLOCK;
-    v0 = min(nv, (long long)t * per);
-    v1 = min(nv, v0 + per);
+    // rank of each accepted candidate in key order (its place in the list);
+    // the appending is left to pds_commit (many blocks)
+    const long long per = (nv + PDS_BLOCK - 1) / PDS_BLOCK;
+    const long long v0 = min(nv, (long long)t * per), v1 = min(nv, v0 + per);
     long long cnt = 0;
     for (long long v = v0; v < v1; ++v) cnt += st[v] == PDS_IN;
     long long nacc;
     long long pos = block_excl_scan(cnt, &nacc);
-    for (long long v = v0; v < v1; ++v) {
-        if (st[v] != PDS_IN) continue;
-        const long long id = s_N + pos++;
-        if (id >= A.maxn) {
-            atomicExch(&A.ctrl->err, 3);
-            continue;
-        }
-        const int32_t e = A.V[v];
-        const double x = A.cx[e], y = A.cy[e];
-        A.X[id] = x;
-        A.Y[id] = y;
-        A.B[id] = 0;
-        if (atomicCAS(&A.cell[pds_cell_of(A, x, y)], -1, (int32_t)id) != -1)
-            atomicExch(&A.ctrl->err, 1);
-    }
-    __syncthreads();
-    // empty the candidate lists
-    for (long long v = t; v < nv; v += PDS_BLOCK) {
-        const int32_t e = A.V[v];
-        A.chead[pds_cell_of(A, A.cx[e], A.cy[e])] = -1;
-    }
+    for (long long v = v0; v < v1; ++v) A.deg[v] = st[v] == PDS_IN ? (int32_t)pos++ : -1;
     if (t == 0) {
         A.ctrl->lo = s_N;
         A.ctrl->hi = s_N + nacc;
         A.ctrl->N = s_N + nacc;
         A.ctrl->rounds += 1;
-        A.ctrl->passes += pass + 1;
+        A.ctrl->passes += passes;
+    }
+}
+
+// step 5 (whole grid): append the accepted candidates at their ranks (the
+// new generation [lo, hi)), with their rotation angles 2 pi U_id; empty the
+// candidate lists
+__global__ void pds_commit(PdsArgs A) {
+    const double two_pi = 6.283185307179586;
+    volatile PdsCtrl* c = A.ctrl;
+    if (c->err) return;
+    const long long nv = c->nv, lo = c->lo;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nv;
+         v += (long long)gridDim.x * blockDim.x) {
+        const int32_t e = A.V[v];
+        const int32_t cell = A.ccell[e];
+        A.chead[cell] = -1;
+        const int32_t r = A.deg[v];
+        if (r < 0) continue;
+        const long long id = lo + r;
+        if (id >= A.maxn) {
+            atomicExch(&A.ctrl->err, 3);
+            continue;
+        }
+        A.X[id] = A.cx[e];
+        A.Y[id] = A.cy[e];
+        A.B[id] = 0;
+        if (atomicCAS(&A.cell[cell], -1, (int32_t)id) != -1) atomicExch(&A.ctrl->err, 1);
+        unit_dir(__dmul_rn(two_pi, unit_draw(A.seed, (uint64_t)id)), &A.rc[id], &A.rs[id]);
     }
 }
 
@@ -405,8 +488,9 @@ static double pds_cell_side(double zeta, double h) {
     return (0.99 * (zeta * h)) / 1.4142135623730951;
 }
 
+// cells per axis over [0, 1] (one spare column for FP32 rounding at x = 1)
 static int64_t pds_cells_per_axis(int Kg, double zeta) {
-    return (int64_t)(1.0 / pds_cell_side(zeta, 1.0 / (double)Kg)) + 1;
+    return (int64_t)(1.0 / pds_cell_side(zeta, 1.0 / (double)Kg)) + 2;
 }
 
 // one attempt with room for generations of at most capF nodes; returns
@@ -425,6 +509,7 @@ static int pds_run(int shape, int Kg, int K, double zeta, uint64_t seed, int64_t
     A.K = K;
     A.h = h;
     A.cs = pds_cell_side(zeta, h);
+    A.inv_cs = (float)(1.0 / A.cs);
     A.r2 = t * t;
     A.G = G;
     A.maxn = maxn;
@@ -432,10 +517,11 @@ static int pds_run(int shape, int Kg, int K, double zeta, uint64_t seed, int64_t
     A.capA = capA;
     A.seed = seed;
     Scratch bX, bY, bB, brc, brs, bcell, bhead, bnext, bcx, bcy, bflag, bV, bst, bdir, bctl;
-    Scratch bdeg, boff, badj;
+    Scratch bdeg, boff, badj, bccell;
+    RBFFD_CHECK_CUDA(bccell.alloc(sizeof(int32_t) * capC, s));
     RBFFD_CHECK_CUDA(bdeg.alloc(sizeof(int32_t) * capC, s));
-    RBFFD_CHECK_CUDA(boff.alloc(sizeof(int32_t) * (capC + 1), s));
-    RBFFD_CHECK_CUDA(badj.alloc(sizeof(int32_t) * capA, s));
+    RBFFD_CHECK_CUDA(boff.alloc(sizeof(int32_t) * (capC + 8), s));   // padded to whole int4s
+    RBFFD_CHECK_CUDA(badj.alloc(sizeof(int32_t) * (capA + 8), s));
     RBFFD_CHECK_CUDA(bX.alloc(sizeof(double) * maxn, s));
     RBFFD_CHECK_CUDA(bY.alloc(sizeof(double) * maxn, s));
     RBFFD_CHECK_CUDA(bB.alloc(maxn, s));
@@ -448,7 +534,7 @@ static int pds_run(int shape, int Kg, int K, double zeta, uint64_t seed, int64_t
     RBFFD_CHECK_CUDA(bcy.alloc(sizeof(double) * capC, s));
     RBFFD_CHECK_CUDA(bflag.alloc(capC, s));
     RBFFD_CHECK_CUDA(bV.alloc(sizeof(int32_t) * capC, s));
-    RBFFD_CHECK_CUDA(bst.alloc(capC, s));
+    RBFFD_CHECK_CUDA(bst.alloc(sizeof(int32_t) * capC, s));
     RBFFD_CHECK_CUDA(bdir.alloc(sizeof(double) * 2 * PDS_KMAX, s));
     RBFFD_CHECK_CUDA(bctl.alloc(sizeof(PdsCtrl), s));
     A.X = bX.as<double>();
@@ -463,10 +549,11 @@ static int pds_run(int shape, int Kg, int K, double zeta, uint64_t seed, int64_t
     A.cy = bcy.as<double>();
     A.cflag = bflag.as<uint8_t>();
     A.V = bV.as<int32_t>();
-    A.state = bst.as<signed char>();
+    A.state = bst.as<int32_t>();
     A.ex = bdir.as<double>();
     A.ey = bdir.as<double>() + PDS_KMAX;
     A.ctrl = bctl.as<PdsCtrl>();
+    A.ccell = bccell.as<int32_t>();
     A.deg = bdeg.as<int32_t>();
     A.off = boff.as<int32_t>();
     A.adj = badj.as<int32_t>();
@@ -480,23 +567,23 @@ static int pds_run(int shape, int Kg, int K, double zeta, uint64_t seed, int64_t
     pds_seeds<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(A, Kg, nb);
     RBFFD_CHECK_CUDA(cudaGetLastError());
     const unsigned grid = (unsigned)device_sm_count() * 4;
-    // states of up to this many candidates in shared memory
-    const int smem_states = 160 * 1024;
+    // shared memory of the resolving block: states and conflict lists
+    const int smem_bytes = 200 * 1024;
     RBFFD_CHECK_CUDA(cudaFuncSetAttribute(pds_resolve,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          smem_states));
+                                          smem_bytes));
     PdsCtrl hc = c0;
     // each generation appends at least one node until the walk ends, so the
     // walk takes at most maxn generations
     for (int64_t r = 0; r < maxn; r += 16) {
         for (int b = 0; b < 16; ++b) {
-            pds_rot<<<grid, 256, 0, s>>>(A);
             pds_gen<<<grid, 256, 0, s>>>(A);
             pds_compact<<<1, PDS_BLOCK, 0, s>>>(A);
             pds_conflicts<false><<<grid, 256, 0, s>>>(A);
             pds_offsets<<<1, PDS_BLOCK, 0, s>>>(A);
             pds_conflicts<true><<<grid, 256, 0, s>>>(A);
-            pds_resolve<<<1, PDS_BLOCK, smem_states, s>>>(A, smem_states);
+            pds_resolve<<<1, PDS_BLOCK, smem_bytes, s>>>(A, smem_bytes);
+            pds_commit<<<grid, 256, 0, s>>>(A);
         }
         RBFFD_CHECK_CUDA(cudaGetLastError());
         RBFFD_CHECK_CUDA(cudaMemcpyAsync(&hc, A.ctrl, sizeof(hc), cudaMemcpyDeviceToHost, s));

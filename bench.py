@@ -836,7 +836,8 @@ def main():
            "config": {"workload": "2D unit square, 1,002,001 jittered nodes (998,001 interior), "
                                   "m=4 (n=30), FP64 explicit sweeps, Morton-packed plan",
                       "sweeps_per_step": SWEEPS, "dt": P["dt"],
-                      "l2": "inputs larger than L2 (stencils 360 MB per sweep)",
+                      "l2": f"inputs larger than L2 (packed stencils {alg_bytes / 1e6:.0f} MB "
+                            f"streamed per sweep, L2 126 MB); no flush needed",
                       "parallelism": f"replicas x{world}"},
            "roofline": roof, "e2e": e2e, "clocks": clocks,
            "gpu_launches": int(launches), "extras": extras}

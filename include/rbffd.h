@@ -358,11 +358,15 @@ RBFFD_API int rbffd_plan_set_dc(rbffd_plan* plan, int64_t K_in, double rho_in);
  *   tol are host arrays [ndom].  Per domain (host outputs, may be NULL):
  *   steps taken, last residual max-norm, status (RBFFD_OK, RBFFD_NOT_CONVERGED
  *   or an error).  Returns the most severe per-domain status.
- * rbffd_batch_set_shape - register budget (min resident blocks per SM, 1..3)
- *   and blocks per SM of the persistent grid (re-captures the graph); the
- *   binding's autotuner times candidates through it.
+ * rbffd_batch_set_shape - launch shape of the persistent grid (re-captures the
+ *   graph): threads per block (256, 512 or 1024), register budget minb (min
+ *   resident blocks per SM: 1..3 at 256 threads, 1..2 at 512, 1 at 1024) and
+ *   blocks per SM; RBFFD_ERR_ARG for other combinations, RBFFD_ERR_CAPACITY
+ *   when the grid cannot be co-resident.  The binding's autotuner times
+ *   candidates through it.
  * rbffd_batch_stats - GPU ms of the last batched solve (events around the
- *   graph launch) and the shape {minb, blocks_per_sm, grid, cooperative}.
+ *   graph launch) and the shape h_shape[5] = {minb, blocks_per_sm, grid,
+ *   cooperative, threads}.
  */
 typedef struct rbffd_batch rbffd_batch;
 RBFFD_API int rbffd_batch_create(rbffd_plan* const* plans, int ndom, int blocks_per_sm,
@@ -371,7 +375,7 @@ RBFFD_API int rbffd_batch_destroy(rbffd_batch* batch);
 RBFFD_API int rbffd_solve_batch(rbffd_batch* batch, const double* const* f, double* const* u,
                                 const double* dt, const int64_t* max_steps, const double* tol,
                                 int64_t* h_steps, double* h_res, int* h_status, void* stream);
-RBFFD_API int rbffd_batch_set_shape(rbffd_batch* batch, int minb, int blocks_per_sm,
+RBFFD_API int rbffd_batch_set_shape(rbffd_batch* batch, int minb, int blocks_per_sm, int threads,
                                     void* stream);
 RBFFD_API int rbffd_batch_stats(const rbffd_batch* batch, double* h_ms, int* h_shape);
 /* relative cost of one step of each domain (host [ndom], > 0), used to size the

@@ -100,7 +100,7 @@ def lib():
         "rbffd_batch_create": (I, [P, I, I, ctypes.POINTER(ctypes.c_void_p), P]),
         "rbffd_batch_destroy": (I, [P]),
         "rbffd_solve_batch": (I, [P, P, P, P, P, P, P, P, P, P]),
-        "rbffd_batch_set_shape": (I, [P, I, I, P]),
+        "rbffd_batch_set_shape": (I, [P, I, I, I, P]),
         "rbffd_batch_stats": (I, [P, PD, P]),
         "rbffd_error": (I, [P, P, I64, PD, PD, P]),
         "rbffd_batch_domain_times": (I, [P, P, P, P, P]),
@@ -470,13 +470,14 @@ class Batch:
         _check(code, (RBFFD_OK, RBFFD_NOT_CONVERGED))
         return code, list(steps), list(res), list(st)
 
-    def set_shape(self, minb, blocks_per_sm):
-        _check(lib().rbffd_batch_set_shape(self._h, int(minb), int(blocks_per_sm),
+    def set_shape(self, minb, blocks_per_sm, threads=256):
+        _check(lib().rbffd_batch_set_shape(self._h, int(minb), int(blocks_per_sm), int(threads),
                                            _stream(self.device)))
 
     def stats(self):
+        """(GPU ms of the last solve, [minb, blocks/SM, grid, cooperative, threads])."""
         ms = ctypes.c_double(0.0)
-        shape = (ctypes.c_int * 4)()
+        shape = (ctypes.c_int * 5)()
         _check(lib().rbffd_batch_stats(self._h, ctypes.byref(ms), shape))
         return ms.value, list(shape)
 
@@ -523,11 +524,14 @@ class Batch:
             best = tuple(known[key])
             self.set_shape(*best)
         else:
-            cands = candidates or [(m, b) for m in (1, 2, 3) for b in (1, 2, 3, 4) if b >= m - 1]
+            cands = candidates or (
+                [(m, b, 256) for m in (1, 2, 3) for b in (1, 2, 3, 4) if b >= m - 1]
+                + [(m, b, 512) for m in (1, 2) for b in (1, 2) if b >= m - 1]
+                + [(1, 1, 1024)])
             best, best_ms = None, float("inf")
-            for (m, b) in cands:
+            for (m, b, th) in cands:
                 try:
-                    self.set_shape(m, b)
+                    self.set_shape(m, b, th)
                 except RbffdError:
                     continue
                 # costs measured at this shape, then a timed probe with them
@@ -535,7 +539,7 @@ class Batch:
                 self.solve(fs, us, dts, [probe_steps] * self.ndom, [0.0] * self.ndom)
                 ms, _ = self.stats()
                 if ms < best_ms:
-                    best, best_ms = (m, b), ms
+                    best, best_ms = (m, b, th), ms
             if best is None:
                 raise RbffdError(RBFFD_ERR_CAPACITY, "no launch shape fits")
             self.set_shape(*best)

@@ -31,7 +31,7 @@
 
 namespace rbffd {
 
-static constexpr int BATCH_THREADS = 256;
+static constexpr int BATCH_MAX_WARPS = 32;   // blocks of 256, 512 or 1024 threads
 static constexpr long long BATCH_SPIN_CYCLES = 4000000000LL;
 
 struct DomDesc {           // static part (from the plan)
@@ -79,6 +79,7 @@ struct rbffd_batch {
     int grid = 0;
     int minb = 2;
     int per_sm = 2;
+    int threads = 256;                    // block size
     rbffd::DomDesc* d_desc = nullptr;
     rbffd::DomCall* d_call = nullptr;
     rbffd::DomState* d_state = nullptr;
@@ -119,10 +120,9 @@ __device__ __forceinline__ int32_t bld_cs(const int32_t* p) {
     return v;
 }
 
-template <int NN, bool COH>
+template <int NN, bool COH, int CH>
 __device__ __forceinline__ double brow(const double* __restrict__ w, const int32_t* __restrict__ col,
                                        const double* __restrict__ u, int n) {
-    constexpr int CH = 16;
     double acc = 0.0;
     const int nn = NN > 0 ? NN : n;
 #pragma unroll
@@ -152,7 +152,7 @@ __device__ __forceinline__ unsigned long long babs_bits(double x) {
 }
 
 // one step of domain D over the slices of this team member; returns max |r| bits
-template <int NN, bool COH>
+template <int NN, bool COH, int CH>
 __device__ __noinline__ unsigned long long bstep(const DomDesc& D, int par, double dt, int64_t s0,
                                                  int64_t stride) {
     const int lane = threadIdx.x & 31;
@@ -165,7 +165,7 @@ __device__ __noinline__ unsigned long long bstep(const DomDesc& D, int par, doub
         if (row < D.NI) {
             const double fi = bld_cs(D.fs + row);
             const double ui = COH ? bld_cg(uin + row) : bld_ca(uin + row);
-            double acc = brow<NN, COH>(D.w64 + base, D.col + base, uin, D.n);
+            double acc = brow<NN, COH, CH>(D.w64 + base, D.col + base, uin, D.n);
             double r = __dsub_rn(acc, fi);
             uout[row] = __fma_rn(dt, r, ui);
             m = max(m, babs_bits(r));
@@ -174,14 +174,14 @@ __device__ __noinline__ unsigned long long bstep(const DomDesc& D, int par, doub
     return m;
 }
 
-template <bool COH>
+template <bool COH, int CH>
 __device__ unsigned long long bstep_any(const DomDesc& D, int par, double dt, int64_t s0,
                                         int64_t stride) {
     switch (D.n) {
-        case 12: return bstep<12, COH>(D, par, dt, s0, stride);
-        case 30: return bstep<30, COH>(D, par, dt, s0, stride);
-        case 56: return bstep<56, COH>(D, par, dt, s0, stride);
-        default: return bstep<0, COH>(D, par, dt, s0, stride);
+        case 12: return bstep<12, COH, CH>(D, par, dt, s0, stride);
+        case 30: return bstep<30, COH, CH>(D, par, dt, s0, stride);
+        case 56: return bstep<56, COH, CH>(D, par, dt, s0, stride);
+        default: return bstep<0, COH, CH>(D, par, dt, s0, stride);
     }
 }
 
@@ -217,7 +217,9 @@ __device__ bool team_sync_global(DomState* st, int size) {
 }
 
 // one domain's solve by one team member (rank of size blocks); returns false
-// when a team wait gave up
+// when a team wait gave up.  CH: neighbours per load phase (8 where the
+// register budget is 64 per thread).
+template <int CH>
 __device__ bool run_domain(const TeamDesc T, const DomDesc* __restrict__ desc,
                            const DomCall* __restrict__ call, DomState* state,
                            unsigned long long* wmax, int* s_stop) {
@@ -225,20 +227,22 @@ __device__ bool run_domain(const TeamDesc T, const DomDesc* __restrict__ desc,
     const DomCall C = call[T.dom];
     DomState* st = state + T.dom;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t s0 = (int64_t)T.rank * (BATCH_THREADS / 32) + wid;
-    const int64_t stride = (int64_t)T.size * (BATCH_THREADS / 32);
+    const int nw = (int)(blockDim.x >> 5);
+    const int64_t s0 = (int64_t)T.rank * nw + wid;
+    const int64_t stride = (int64_t)T.size * nw;
     double R0 = 0.0;
     if (threadIdx.x == 0 && T.rank == 0) st->t_start = gtimer();
     for (long long k = 0; k < C.max_steps; ++k) {
-        unsigned long long m = T.size == 1 ? bstep_any<false>(D, (int)(k & 1), C.dt, s0, stride)
-                                           : bstep_any<true>(D, (int)(k & 1), C.dt, s0, stride);
+        unsigned long long m = T.size == 1
+                                   ? bstep_any<false, CH>(D, (int)(k & 1), C.dt, s0, stride)
+                                   : bstep_any<true, CH>(D, (int)(k & 1), C.dt, s0, stride);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
         if (lane == 0) wmax[wid] = m;
         __syncthreads();
         unsigned long long bm = 0;
         if (threadIdx.x == 0)
-            for (int w = 0; w < BATCH_THREADS / 32; ++w) bm = max(bm, wmax[w]);
+            for (int w = 0; w < nw; ++w) bm = max(bm, wmax[w]);
         double R;
         if (T.size == 1) {
             R = __longlong_as_double((long long)bm);
@@ -278,15 +282,16 @@ __device__ bool run_domain(const TeamDesc T, const DomDesc* __restrict__ desc,
     return true;
 }
 
-template <int MINB>
-__global__ void __launch_bounds__(BATCH_THREADS, MINB)
+template <int MINB, int TH>
+__global__ void __launch_bounds__(TH, MINB)
     batch_kernel(const DomDesc* __restrict__ desc, const DomCall* __restrict__ call,
                  DomState* state, const TeamDesc* __restrict__ assign,
                  const int* __restrict__ first) {
-    __shared__ unsigned long long wmax[BATCH_THREADS / 32];
+    constexpr int CH = 65536 / (TH * MINB) >= 128 ? 16 : 8;
+    __shared__ unsigned long long wmax[BATCH_MAX_WARPS];
     __shared__ int s_stop;
     for (int a = first[blockIdx.x]; a < first[blockIdx.x + 1]; ++a)
-        if (!run_domain(assign[a], desc, call, state, wmax, &s_stop)) return;
+        if (!run_domain<CH>(assign[a], desc, call, state, wmax, &s_stop)) return;
 }
 
 // gather f and u of every domain into its plan (one launch for all domains)
@@ -328,11 +333,19 @@ __global__ void batch_scatter(const DomDesc* desc, const DomCall* call, const Do
 
 typedef void (*BatchFn)(const DomDesc*, const DomCall*, DomState*, const TeamDesc*, const int*);
 
-static BatchFn batch_fn(int minb) {
+// launch shapes: (register budget, block size) with TH x MINB <= 1024 threads
+static bool batch_shape_ok(int minb, int threads) {
+    return (threads == 256 && minb >= 1 && minb <= 3) || (threads == 512 && minb >= 1 && minb <= 2) ||
+           (threads == 1024 && minb == 1);
+}
+
+static BatchFn batch_fn(int minb, int threads) {
+    if (threads == 1024) return batch_kernel<1, 1024>;
+    if (threads == 512) return minb == 2 ? batch_kernel<2, 512> : batch_kernel<1, 512>;
     switch (minb) {
-        case 1: return batch_kernel<1>;
-        case 3: return batch_kernel<3>;
-        default: return batch_kernel<2>;
+        case 1: return batch_kernel<1, 256>;
+        case 3: return batch_kernel<3, 256>;
+        default: return batch_kernel<2, 256>;
     }
 }
 
@@ -412,7 +425,7 @@ static int batch_capture(rbffd_batch* B, cudaStream_t user) {
         cudaGraphExecDestroy((cudaGraphExec_t)B->graph);
         B->graph = nullptr;
     }
-    BatchFn fn = batch_fn(B->minb);
+    BatchFn fn = batch_fn(B->minb, B->threads);
     cudaStream_t cs;
     RBFFD_CHECK_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaError_t e = cudaErrorUnknown;
@@ -426,7 +439,7 @@ static int batch_capture(rbffd_batch* B, cudaStream_t user) {
         batch_gather<<<gg, 256, 0, cs>>>(B->d_desc, B->d_call, B->d_state, B->ndom);
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(B->grid);
-        cfg.blockDim = dim3(BATCH_THREADS);
+        cfg.blockDim = dim3(B->threads);
         cfg.stream = cs;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeCooperative;
@@ -536,15 +549,16 @@ extern "C" int rbffd_batch_create(rbffd_plan* const* plans, int ndom, int blocks
     // launch shape: register budget minb and blocks per SM; blocks_per_sm = 0 -> tune
     // (the tuner times one short solve per candidate in rbffd_batch_tune)
     int per_sm_max = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_max, (const void*)batch_fn(2),
-                                                  BATCH_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_max, (const void*)batch_fn(2, 256), 256,
+                                                  0);
     B->minb = 2;
+    B->threads = 256;
     B->per_sm = blocks_per_sm > 0 ? std::min(blocks_per_sm, std::max(per_sm_max, 1))
                                   : std::min(2, std::max(per_sm_max, 1));
     B->grid = sms * B->per_sm;
     int maxres = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxres, (const void*)batch_fn(B->minb),
-                                                  BATCH_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxres, (const void*)batch_fn(B->minb, 256), 256,
+                                                  0);
     if (B->grid > maxres * sms) {
         set_error("rbffd_batch_create: %d domains need %d co-resident blocks, the device holds %d",
                   ndom, B->grid, maxres * sms);
@@ -632,14 +646,15 @@ extern "C" int rbffd_solve_batch(rbffd_batch* B, const double* const* f, double*
     return worst;
 }
 
-extern "C" int rbffd_batch_set_shape(rbffd_batch* B, int minb, int blocks_per_sm, void* stream) {
+extern "C" int rbffd_batch_set_shape(rbffd_batch* B, int minb, int blocks_per_sm, int threads,
+                                     void* stream) {
     clear_error();
-    RBFFD_ARG(B && minb >= 1 && minb <= 3 && blocks_per_sm >= 1 && blocks_per_sm <= 8,
+    RBFFD_ARG(B && blocks_per_sm >= 1 && blocks_per_sm <= 8 && batch_shape_ok(minb, threads),
               "rbffd_batch_set_shape: bad argument");
     int sms = device_sm_count();
     int maxres = 0;
-    RBFFD_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxres, (const void*)batch_fn(minb),
-                                                                   BATCH_THREADS, 0));
+    RBFFD_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &maxres, (const void*)batch_fn(minb, threads), threads, 0));
     int grid = sms * blocks_per_sm;
     if (grid > maxres * sms) {
         set_error("rbffd_batch_set_shape: %d blocks cannot be co-resident (max %d)", grid,
@@ -648,6 +663,7 @@ extern "C" int rbffd_batch_set_shape(rbffd_batch* B, int minb, int blocks_per_sm
     }
     B->minb = minb;
     B->per_sm = blocks_per_sm;
+    B->threads = threads;
     B->grid = grid;
     return batch_capture(B, as_stream(stream));
 }
@@ -661,6 +677,7 @@ extern "C" int rbffd_batch_stats(const rbffd_batch* B, double* h_ms, int* h_shap
         h_shape[1] = B->per_sm;
         h_shape[2] = B->grid;
         h_shape[3] = B->coop;
+        h_shape[4] = B->threads;
     }
     return RBFFD_OK;
 }

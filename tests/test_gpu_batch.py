@@ -25,6 +25,10 @@ def T(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
+def H(t):
+    return t.cpu().numpy()
+
+
 def _domains(orc):
     specs = [(0, 14, 2), (1, 20, 4), (0, 25, 6), (1, 30, 2), (0, 9, 4), (1, 24, 6), (0, 40, 4)]
     out = []
@@ -73,7 +77,21 @@ def test_batch_autotune_and_errors(rb, orc):
     us = [T(p.u0) for p, _ in doms]
     best = batch.tune(fs, us, [dt for _, dt in doms], probe_steps=50)
     ms, shape = batch.stats()
-    assert tuple(shape[:2]) == best and ms > 0
+    assert (shape[0], shape[1], shape[4]) == best and ms > 0
+    # every block size gives the same iterates; bad shapes are refused
+    ref = None
+    for th in (256, 512, 1024):
+        batch.set_shape(1, 1, th)
+        uu = [T(p.u0) for p, _ in doms]
+        batch.solve(fs, uu, [dt for _, dt in doms], [80] * 3, [0.0] * 3)
+        if ref is None:
+            ref = [H(u) for u in uu]
+        else:
+            assert all(np.array_equal(H(u), r) for u, r in zip(uu, ref))
+    for bad in ((2, 1, 1024), (3, 1, 512), (1, 1, 128)):
+        with pytest.raises(rb.RbffdError):
+            batch.set_shape(*bad)
+    batch.set_shape(*best)
     # a non-finite source in one domain stops that domain only
     f_bad = [t.clone() for t in fs]
     f_bad[1][3] = float("nan")

@@ -69,6 +69,8 @@ def _load():
         "oracle_nodes": (i64, [i32, i32, i32, f64, u64, P, P, i64]),
         "oracle_nodes_pds": (i64, [i32, i32, i32, f64, u64, i32, P, P, i64]),
         "oracle_nodes_pds_cap": (i64, [i32, f64]),
+        "oracle_nodes_pds3": (i64, [i32, i32, f64, u64, i32, P, P, i64]),
+        "oracle_nodes_pds3_cap": (i64, [i32, f64]),
         "oracle_knn_brute": (i32, [P, i64, i32, P, i64, i32, P]),
         "oracle_knn_kdtree": (i32, [P, i64, i32, P, i64, i32, P]),
         "oracle_knn_brute_masked": (i32, [P, i64, i32, P, P, i64, i32, P]),
@@ -147,6 +149,24 @@ def nodes_pds(shape: int, Kg: int, seed: int, K: int = PDS_K, zeta: float = PDS_
                              cap)
     if N < 0:
         raise ValueError(f"oracle_nodes_pds failed ({N})")
+    return np.ascontiguousarray(xyz[:, :N]), is_bnd[:N].copy()
+
+
+PDS3_K = 50
+
+
+def nodes_pds3(Kg: int, seed: int, K: int = PDS3_K, zeta: float = PDS_ZETA, brute: bool = False):
+    """Poisson-disc node set in the unit cube, spacing 1/Kg, boundary seeds first.
+    Returns (xyz [3, N] float64, is_bnd [N] uint8)."""
+    lib = _load()
+    cap = lib.oracle_nodes_pds3_cap(Kg, zeta)
+    if cap < 0:
+        raise ValueError("oracle_nodes_pds3: bad arguments")
+    xyz = np.zeros((3, cap), np.float64)
+    is_bnd = np.zeros(cap, np.uint8)
+    N = lib.oracle_nodes_pds3(Kg, K, zeta, seed, 1 if brute else 0, _p(xyz), _p(is_bnd), cap)
+    if N < 0:
+        raise ValueError(f"oracle_nodes_pds3 failed ({N})")
     return np.ascontiguousarray(xyz[:, :N]), is_bnd[:N].copy()
 
 

@@ -21,6 +21,8 @@
  *   oracle_nodes_pds   the Poisson-disc sampler itself (Sec. II-C, last
  *                      paragraph): boundary seeds, candidates at distance h
  *                      around each node in first-in first-out order
+ *   oracle_nodes_pds3  the same in the unit cube (candidates on a sphere,
+ *                      randomly rotated per node)
  *   oracle_knn_brute   support = n nearest nodes incl. the centre (Sec. II,
  *                      text after Eq. 1), ties by lower index
  *   oracle_knn_kdtree  the same set, via a kd-tree (pinned to brute force)
@@ -358,6 +360,167 @@ int64_t oracle_nodes_pds(int shape, int Kg, int K, double zeta, uint64_t seed, i
     ret = N;
 done:
     free(X); free(Y); free(B); free(cell); free(ex); free(ey);
+    return ret;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Poisson-disc node placement in 3D: the unit cube, spacing h = 1/Kg.       */
+/*                                                                           */
+/* Seeds: the boundary grid points (i h, j h, k h) with some index 0 or Kg,   */
+/* in row-major order (k fastest).  The list is walked first in, first out;  */
+/* node p proposes K candidates c_j = p + h R_p e_j where                     */
+/*   e_j  the j-th point of a Fibonacci sphere: z = 1 - (2j+1)/K,            */
+/*        rho = sqrt(1 - z^2), angle phi = j*GA - 2 pi floor(j*GA / 2 pi)    */
+/*        (GA = pi (3 - sqrt 5)), e_j = (rho cos phi, rho sin phi, z);       */
+/*   R_p  the rotation of the unit quaternion (x, y, z, w) =                  */
+/*        (s1 sin a2, s1 cos a2, s2 sin a3, s2 cos a3), s1 = sqrt(1 - u1),    */
+/*        s2 = sqrt(u1), a2 = 2 pi u2, a3 = 2 pi u3, with u1, u2, u3 the      */
+/*        (3p)-th, (3p+1)-th and (3p+2)-th SplitMix64 draws (Shoemake's       */
+/*        uniform random rotation), as the usual matrix                       */
+/*        [1-2(y2+z2), 2(xy-zw), 2(xz+yw); 2(xy+zw), 1-2(x2+z2), 2(yz-xw);    */
+/*         2(xz-yw), 2(yz+xw), 1-2(x2+y2)], y2 = y*y etc.                     */
+/* A candidate inside the open cube is appended when every node in the list  */
+/* is at squared distance >= (zeta h)^2.  Grid cells of side                 */
+/* (0.99 zeta h)/sqrt 3 hold at most one node; the 5x5x5 cells around a      */
+/* candidate are searched (2 cs > zeta h).  Returns as oracle_nodes_pds.     */
+/* ------------------------------------------------------------------------- */
+static void fib_dir(int j, int K, double* ex, double* ey, double* ez)
+{
+    const double two_pi = 6.283185307179586;
+    const double ga = 2.399963229728653;   /* pi (3 - sqrt 5) */
+    double z = 1.0 - (double)(2 * j + 1) / (double)K;
+    double rho = sqrt(1.0 - z * z);
+    double t = (double)j * ga;
+    double phi = t - floor(t / two_pi) * two_pi;
+    double c, s;
+    unit_dir(phi, &c, &s);
+    *ex = rho * c;
+    *ey = rho * s;
+    *ez = z;
+}
+
+static void rand_rotation(uint64_t seed, uint64_t p, double R[9])
+{
+    const double two_pi = 6.283185307179586;
+    double u1 = u01(seed, 3 * p), u2 = u01(seed, 3 * p + 1), u3 = u01(seed, 3 * p + 2);
+    double s1 = sqrt(1.0 - u1), s2 = sqrt(u1);
+    double c2, n2, c3, n3;                 /* cos and sin of a2, a3 */
+    unit_dir(two_pi * u2, &c2, &n2);
+    unit_dir(two_pi * u3, &c3, &n3);
+    double x = s1 * n2, y = s1 * c2, z = s2 * n3, w = s2 * c3;
+    double xx = x * x, yy = y * y, zz = z * z;
+    double xy = x * y, xz = x * z, yz = y * z, xw = x * w, yw = y * w, zw = z * w;
+    R[0] = 1.0 - 2.0 * (yy + zz); R[1] = 2.0 * (xy - zw);         R[2] = 2.0 * (xz + yw);
+    R[3] = 2.0 * (xy + zw);         R[4] = 1.0 - 2.0 * (xx + zz); R[5] = 2.0 * (yz - xw);
+    R[6] = 2.0 * (xz - yw);         R[7] = 2.0 * (yz + xw);         R[8] = 1.0 - 2.0 * (xx + yy);
+}
+
+static double pds3_cell_side(double zeta, double h)
+{
+    return (0.99 * (zeta * h)) / 1.7320508075688772;
+}
+
+int64_t oracle_nodes_pds3_cap(int Kg, double zeta)
+{
+    if (Kg < 2 || !(zeta > 0.0 && zeta <= 1.0)) return -1;
+    double cs = pds3_cell_side(zeta, 1.0 / (double)Kg);
+    int64_t G = (int64_t)(1.0 / cs) + 1;
+    return G * G * G;
+}
+
+int64_t oracle_nodes_pds3(int Kg, int K, double zeta, uint64_t seed, int brute, double* xyz,
+                          uint8_t* is_bnd, int64_t cap)
+{
+    if (Kg < 2 || K < 1 || K > 256 || !(zeta > 0.0 && zeta <= 1.0)) return -1;
+    const double h = 1.0 / (double)Kg;
+    const double cs = pds3_cell_side(zeta, h);
+    const int64_t G = (int64_t)(1.0 / cs) + 1;
+    const int64_t maxn = G * G * G;
+    const double t = zeta * h;
+    const double r2 = t * t;
+    double* P = (double*)malloc(sizeof(double) * 3 * (size_t)maxn);
+    uint8_t* B = (uint8_t*)malloc((size_t)maxn);
+    int32_t* cell = (int32_t*)malloc(sizeof(int32_t) * (size_t)maxn);
+    double* E = (double*)malloc(sizeof(double) * 3 * (size_t)K);
+    int64_t N = 0, ret = 0;
+    if (!P || !B || !cell || !E) { ret = -1; goto done; }
+    for (int64_t c = 0; c < maxn; ++c) cell[c] = -1;
+    for (int j = 0; j < K; ++j) fib_dir(j, K, &E[3 * j], &E[3 * j + 1], &E[3 * j + 2]);
+    for (int64_t i = 0; i <= Kg; ++i)
+        for (int64_t j = 0; j <= Kg; ++j)
+            for (int64_t k = 0; k <= Kg; ++k) {
+                if (!(i == 0 || i == Kg || j == 0 || j == Kg || k == 0 || k == Kg)) continue;
+                P[3 * N] = (double)i * h;
+                P[3 * N + 1] = (double)j * h;
+                P[3 * N + 2] = (double)k * h;
+                B[N] = 1;
+                ++N;
+            }
+    for (int64_t i = 0; i < N; ++i) {
+        int64_t g = ((int64_t)(P[3 * i] / cs) * G + (int64_t)(P[3 * i + 1] / cs)) * G +
+                    (int64_t)(P[3 * i + 2] / cs);
+        if (cell[g] >= 0) { ret = -2; goto done; }
+        cell[g] = (int32_t)i;
+    }
+    for (int64_t p = 0; p < N; ++p) {
+        double R[9];
+        rand_rotation(seed, (uint64_t)p, R);
+        for (int j = 0; j < K; ++j) {
+            const double* e = &E[3 * j];
+            double c[3];
+            for (int a = 0; a < 3; ++a) {
+                double u = (R[3 * a] * e[0] + R[3 * a + 1] * e[1]) + R[3 * a + 2] * e[2];
+                c[a] = P[3 * p + a] + h * u;
+            }
+            if (!(c[0] > 0.0 && c[0] < 1.0 && c[1] > 0.0 && c[1] < 1.0 && c[2] > 0.0 &&
+                  c[2] < 1.0))
+                continue;
+            int far = 1;
+            if (brute) {
+                for (int64_t q = 0; q < N && far; ++q) {
+                    double dx = c[0] - P[3 * q], dy = c[1] - P[3 * q + 1], dz = c[2] - P[3 * q + 2];
+                    if ((dx * dx + dy * dy) + dz * dz < r2) far = 0;
+                }
+            } else {
+                int64_t g0 = (int64_t)(c[0] / cs), g1 = (int64_t)(c[1] / cs),
+                        g2 = (int64_t)(c[2] / cs);
+                for (int64_t a = g0 - 2; a <= g0 + 2 && far; ++a) {
+                    if (a < 0 || a >= G) continue;
+                    for (int64_t b = g1 - 2; b <= g1 + 2 && far; ++b) {
+                        if (b < 0 || b >= G) continue;
+                        for (int64_t e2 = g2 - 2; e2 <= g2 + 2 && far; ++e2) {
+                            if (e2 < 0 || e2 >= G) continue;
+                            int32_t q = cell[(a * G + b) * G + e2];
+                            if (q < 0) continue;
+                            double dx = c[0] - P[3 * q], dy = c[1] - P[3 * q + 1],
+                                   dz = c[2] - P[3 * q + 2];
+                            if ((dx * dx + dy * dy) + dz * dz < r2) far = 0;
+                        }
+                    }
+                }
+            }
+            if (!far) continue;
+            if (N >= maxn) { ret = -2; goto done; }
+            int64_t g = ((int64_t)(c[0] / cs) * G + (int64_t)(c[1] / cs)) * G +
+                        (int64_t)(c[2] / cs);
+            if (cell[g] >= 0) { ret = -2; goto done; }
+            cell[g] = (int32_t)N;
+            P[3 * N] = c[0];
+            P[3 * N + 1] = c[1];
+            P[3 * N + 2] = c[2];
+            B[N] = 0;
+            ++N;
+        }
+    }
+    for (int64_t i = 0; i < N && i < cap; ++i) {
+        xyz[i] = P[3 * i];
+        xyz[cap + i] = P[3 * i + 1];
+        xyz[2 * cap + i] = P[3 * i + 2];
+        is_bnd[i] = B[i];
+    }
+    ret = N;
+done:
+    free(P); free(B); free(cell); free(E);
     return ret;
 }
 

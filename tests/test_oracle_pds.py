@@ -133,3 +133,87 @@ def test_pds_parameters_change_the_set(orc):
     assert not np.array_equal(a, b) and not np.array_equal(a[:, :200], c[:, :200])
     with pytest.raises(ValueError):
         orc.nodes_pds(2, 30, 1)
+
+
+# ---------------------------------------------------------------- 3D (unit cube)
+K3 = 50
+
+
+def _rotation(orc, seed, p):
+    """Shoemake's uniform rotation from the (3p..3p+2)-th draws, in numpy arithmetic."""
+    u1, u2, u3 = (_u01(orc, seed, 3 * p + i) for i in range(3))
+    s1, s2 = math.sqrt(1 - u1), math.sqrt(u1)
+    x, y = s1 * math.sin(2 * math.pi * u2), s1 * math.cos(2 * math.pi * u2)
+    z, w = s2 * math.sin(2 * math.pi * u3), s2 * math.cos(2 * math.pi * u3)
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)],
+                     [2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)],
+                     [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)]])
+
+
+def _fibonacci(K):
+    j = np.arange(K)
+    z = 1 - (2 * j + 1) / K
+    rho = np.sqrt(1 - z * z)
+    phi = j * math.pi * (3 - math.sqrt(5))
+    return np.stack([rho * np.cos(phi), rho * np.sin(phi), z], axis=1)
+
+
+@pytest.mark.parametrize("Kg,seed", [(6, 1), (9, 2)])
+def test_pds3_grid_equals_brute_force(orc, Kg, seed):
+    a = orc.nodes_pds3(Kg, seed)
+    b = orc.nodes_pds3(Kg, seed, brute=True)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_pds3_seeds_separation_construction_saturation(orc):
+    Kg, seed = 14, 3
+    h = 1.0 / Kg
+    xyz, bnd = orc.nodes_pds3(Kg, seed)
+    P = xyz.T
+    N = len(P)
+    ijk = [(i, j, k) for i in range(Kg + 1) for j in range(Kg + 1) for k in range(Kg + 1)
+           if Kg in (i, j, k) or 0 in (i, j, k)]
+    nb = len(ijk)
+    assert np.all(bnd[:nb] == 1) and np.all(bnd[nb:] == 0)
+    assert np.array_equal(P[:nb], np.array(ijk, dtype=np.float64) * h)
+    inner = np.arange(nb, N)
+    assert np.all((P[inner] > 0) & (P[inner] < 1))
+    tree = cKDTree(P)
+    d, _ = tree.query(P[inner], k=2)
+    assert d[:, 1].min() >= ZETA * h * (1 - 1e-12)
+    E = _fibonacci(K3)
+    parents, dirs = [], []
+    for i in inner:
+        cand = tree.query_ball_point(P[i], h * (1 + 1e-9))
+        at_h = [q for q in cand if abs(np.linalg.norm(P[i] - P[q]) - h) <= 1e-9 * h]
+        assert at_h
+        p = min(at_h)
+        assert p < i
+        v = (P[i] - P[p]) / h
+        err = np.linalg.norm(_rotation(orc, seed, p) @ E.T - v[:, None], axis=0)
+        j = int(np.argmin(err))
+        assert err[j] < 1e-9
+        parents.append(p)
+        dirs.append(j)
+    parents, dirs = np.array(parents), np.array(dirs)
+    assert np.all(np.diff(parents) >= 0)
+    same = np.diff(parents) == 0
+    assert np.all(np.diff(dirs)[same] > 0)
+    assert set(dirs.tolist()) == set(range(K3))
+    # saturation
+    for p in range(N):
+        C = P[p] + h * (_rotation(orc, seed, p) @ E.T).T
+        dist, _ = tree.query(C)
+        inside = np.all((C > 1e-12) & (C < 1 - 1e-12), axis=1)
+        assert np.all(~inside | (dist < ZETA * h * (1 + 1e-9)))
+
+
+def test_pds3_kepler_bound(orc):
+    # mutual distance >= d inside the unit cube: the periodic extension with period 1 + d
+    # is a packing of balls of diameter d, so N (pi/6) d^3 <= (pi/sqrt 18)(1 + d)^3 (Hales)
+    for Kg in (8, 20):
+        h = 1.0 / Kg
+        xyz, _ = orc.nodes_pds3(Kg, 4)
+        d = ZETA * h
+        assert xyz.shape[1] <= math.sqrt(2) * (1 + d) ** 3 / d ** 3
+        assert xyz.shape[1] > 0.5 / h ** 3

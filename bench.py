@@ -533,6 +533,46 @@ def run_workload(args):
         plan.destroy()
         return
 
+    if args.workload == "pds3_cube_m4":
+        # Poisson-disc fill of the unit cube (Sec. II-C), h = 1/200, then FP64 sweeps, m = 4
+        Kg, seed = 200, 3
+        rb.rbffd_nodes_pds(0, 20, seed, d=3)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xyz, bnd, rounds = rb.rbffd_nodes_pds(0, Kg, seed, d=3)
+        torch.cuda.synchronize()
+        gen_ms = (time.perf_counter() - t0) * 1e3
+        cpu = None
+        if not args.no_cpu_baseline:
+            import oracle
+            Ks = 100   # a bounded sample: the oracle's walk of the h = 1/100 cube
+            t0 = time.perf_counter()
+            oxyz, _ = oracle.nodes_pds3(Ks, seed)
+            cpu_s = time.perf_counter() - t0
+            cpu = {"value": oxyz.shape[1] / cpu_s, "unit": "nodes placed / s", "cores": 1,
+                   "kind": "oracle", "sample": f"the sequential walk of the h = 1/{Ks} cube "
+                                               f"({oxyz.shape[1]} nodes, {cpu_s:.1f} s)",
+                   "gpu_same_workload": xyz.shape[1] / (gen_ms * 1e-3)}
+        Q = _gpu_problem_from_nodes(rb, torch, xyz, bnd, 4, dev, power_iters=100)
+        plan, f, u0, NI = Q["plan"], Q["f"], Q["u0"], Q["NI"]
+        u = u0.clone()
+        plan.solve_explicit(f, u, Q["dt"], 10, 0.0)
+        S = 50
+        plan.solve_explicit(f, u, Q["dt"], S, 0.0)
+        ms, k, nl, shape = plan.stats()
+        per = ms * 1e-3 / k
+        lay = plan.layout()
+        _line(f"Poisson-disc nodes (Sec. II-C): 3D unit cube, h = 1/{Kg}, {Q['N']:,} nodes "
+              f"({NI:,} interior), m=4 (n=70), FP64 sweeps, Morton-packed plan",
+              NI / per, UNIT, per * 1e3 * S, S, 10,
+              {"node_placement_gpu_ms": gen_ms, "generations": rounds,
+               "alg_GBps": lay["bytes64"] / per / 1e9,
+               "frac_hbm": lay["bytes64"] / per / 1e9 / hbm,
+               "rows16_frac": lay["rows16"] / NI, "rho_h2": Q["rho"] / Kg ** 2,
+               "launch_shape": shape, "cpu_baseline": cpu})
+        plan.destroy()
+        return
+
     if args.workload == "support_sweep":
         # the support-size study at m = 2 (n > 2M), 2D square 1,002,001 nodes
         xyz, bnd = rb.rbffd_nodes(2, 0, 1000, 0.3, 2, device=dev)
@@ -690,7 +730,7 @@ def main():
     ap.add_argument("--batch-domains", type=int, default=256, help="domains in --mode batch")
     ap.add_argument("--workload", default="square1M_m4",
                     choices=["square1M_m4", "batched256", "cube8M_m4", "adjoint1M_m4", "tta",
-                             "mixed1M_m4", "support_sweep", "pds1M_m4"],
+                             "mixed1M_m4", "support_sweep", "pds1M_m4", "pds3_cube_m4"],
                     help="square1M_m4 is the headline; the others measure the other workloads")
     args = ap.parse_args()
     if args.workload != "square1M_m4":

@@ -94,35 +94,41 @@ RBFFD_API int rbffd_nodes(int d, int shape, int Kg, double jitter_frac, uint64_t
 
 /*
  * rbffd_nodes_pds - Poisson-disc node placement (Sec. II-C, last paragraph:
- * the method of Slak and Kosec that the paper uses), 2D, spacing h = 1/Kg.
- * The node list starts with the boundary nodes as seeds (shape 0, unit
+ * the method of Slak and Kosec that the paper uses), spacing h = 1/Kg.
+ * The node list starts with the boundary nodes as seeds (d = 2, shape 0, unit
  * square: the grid points (i h, j h) with i or j in {0, Kg}, row-major;
  * shape 1, disk of radius 1/2 about (1/2,1/2): round(pi/h) nodes at angles
- * 2 pi k / Nb) and is walked first in, first out: node p proposes K
- * candidates c_j = p + h R(2 pi U_p) e_j, e_j the unit vector at angle
- * 2 pi j / K, U_p the p-th SplitMix64(seed) draw in [0,1); a candidate inside
- * the domain (0 < x, y < 1, or |c - centre|^2 < 1/4) is appended when every
+ * 2 pi k / Nb; d = 3, unit cube: the grid points with some index 0 or Kg,
+ * row-major) and is walked first in, first out: node p proposes K
+ * candidates at distance h - in 2D c_j = p + h R(2 pi U_p) e_j, e_j the unit
+ * vector at angle 2 pi j / K, U_p the p-th SplitMix64(seed) draw in [0,1);
+ * in 3D c_j = p + h R_p e_j, e_j the j-th of K Fibonacci-sphere points
+ * (z = 1 - (2j+1)/K, angle j pi (3 - sqrt 5)), R_p the rotation of
+ * Shoemake's uniform quaternion from the (3p..3p+2)-th draws.  A candidate
+ * inside the open domain (or |c - centre|^2 < 1/4) is appended when every
  * node already in the list is at squared distance >= (zeta h)^2.  The walk
  * ends when every node has been walked.  The GPU walks one generation at a
  * time and reproduces the sequential list bit for bit (angles from the
  * Taylor series of sin/cos, every operation separately rounded).
- *   d        2 (other values: RBFFD_ERR_ARG)
- *   K        candidates per node, 1..64 (the method's default is 15)
+ *   d        2 or 3 (3: shape 0 only, Kg <= 1000)
+ *   K        candidates per node, 1..64 in 2D, 1..256 in 3D (the defaults of
+ *            the binding: 15 in 2D, 50 in 3D)
  *   zeta     proximity factor in (0, 1] (default 1 - 1e-10)
- *   xyz      [2][cap] FP64 device out; is_bnd [cap] device out (1 seeds,
+ *   xyz      [d][cap] FP64 device out; is_bnd [cap] device out (1 seeds,
  *            0 the rest); seeds first, then the walk's appends in order
  *   h_n_out  host: number of nodes; RBFFD_ERR_CAPACITY if it exceeds cap
  *   h_rounds host [2] (may be NULL): generations walked, and conflict-
  *            resolution passes over all generations
- * Synchronises `stream` once per 16 generations (to see whether the walk
- * has ended); scratch comes from cudaMallocAsync on `stream`.
+ * Synchronises `stream` (2D: once per 16 generations; 3D: a few times per
+ * generation); scratch comes from cudaMallocAsync on `stream`.
  */
 RBFFD_API int rbffd_nodes_pds(int d, int shape, int Kg, int K, double zeta, uint64_t seed,
                               double* xyz, uint8_t* is_bnd, int64_t cap, int64_t* h_n_out,
                               int64_t* h_rounds, void* stream);
-/* an upper bound on the node count of rbffd_nodes_pds (one node per grid cell
- * of side 0.99 zeta h / sqrt 2 over the unit square) */
-RBFFD_API int rbffd_nodes_pds_cap(int Kg, double zeta, int64_t* h_cap);
+/* an upper bound on the node count of rbffd_nodes_pds: d = 2, one node per
+ * grid cell of side 0.99 zeta h / sqrt 2 over the unit square; d = 3, the
+ * packing bound sqrt 2 (1 + zeta h)^3 / (zeta h)^3 (Hales) plus a margin */
+RBFFD_API int rbffd_nodes_pds_cap(int d, int Kg, double zeta, int64_t* h_cap);
 
 /*
  * rbffd_interior - ascending list of the interior (non-boundary) node indices.

@@ -111,7 +111,7 @@ def lib():
         "rbffd_plan_set_neumann": (I, [P, I64, P, P, P, I, P, P]),
         "rbffd_plan_layout": (I, [P, PI64, PI64, PD, PD]),
         "rbffd_nodes_pds": (I, [I, I, I, I, D, U64, P, P, I64, PI64, PI64, P]),
-        "rbffd_nodes_pds_cap": (I, [I, D, PI64]),
+        "rbffd_nodes_pds_cap": (I, [I, I, D, PI64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -162,21 +162,25 @@ def rbffd_nodes(d: int, shape: int, Kg: int, jitter_frac: float, seed: int, devi
 
 
 PDS_K = 15
+PDS3_K = 50
 PDS_ZETA = 1.0 - 1e-10
 
 
-def rbffd_nodes_pds(shape: int, Kg: int, seed: int, K: int = PDS_K, zeta: float = PDS_ZETA,
-                    device="cuda"):
-    """Poisson-disc node set in 2D (unit square or disk), spacing 1/Kg, boundary seeds
-    first.  Returns (xyz [2, N] float64, is_bnd [N] uint8, generations walked)."""
+def rbffd_nodes_pds(shape: int, Kg: int, seed: int, K: int | None = None,
+                    zeta: float = PDS_ZETA, d: int = 2, device="cuda"):
+    """Poisson-disc node set (unit square or disk in 2D, unit cube in 3D), spacing
+    1/Kg, boundary seeds first.  Returns (xyz [d, N] float64, is_bnd [N] uint8,
+    generations walked)."""
     L = lib()
+    if K is None:
+        K = PDS_K if d == 2 else PDS3_K
     cap = ctypes.c_int64(0)
-    _check(L.rbffd_nodes_pds_cap(Kg, zeta, ctypes.byref(cap)))
-    xyz = torch.empty((2, cap.value), dtype=torch.float64, device=device)
+    _check(L.rbffd_nodes_pds_cap(d, Kg, zeta, ctypes.byref(cap)))
+    xyz = torch.empty((d, cap.value), dtype=torch.float64, device=device)
     bnd = torch.empty(cap.value, dtype=torch.uint8, device=device)
     n = ctypes.c_int64(0)
     rounds = (ctypes.c_int64 * 2)()
-    _check(L.rbffd_nodes_pds(2, shape, Kg, K, zeta, seed, _ptr(xyz), _ptr(bnd), cap.value,
+    _check(L.rbffd_nodes_pds(d, shape, Kg, K, zeta, seed, _ptr(xyz), _ptr(bnd), cap.value,
                              ctypes.byref(n), rounds, _stream(device)))
     N = n.value
     return xyz[:, :N].contiguous(), bnd[:N].clone(), rounds[0]

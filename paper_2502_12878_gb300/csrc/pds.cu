@@ -619,15 +619,25 @@ static int pds_run(int shape, int Kg, int K, double zeta, uint64_t seed, int64_t
     return RBFFD_OK;
 }
 
+// the 3D walk (pds3.cu)
+int pds3_run(int Kg, int K, double zeta, uint64_t seed, double* xyz, uint8_t* is_bnd,
+             int64_t cap, int64_t* h_n, int64_t* h_rounds, cudaStream_t s);
+int64_t pds3_node_bound(int Kg, double zeta);
+
 }  // namespace rbffd
 
 using namespace rbffd;
 
-extern "C" int rbffd_nodes_pds_cap(int Kg, double zeta, int64_t* h_cap) {
+extern "C" int rbffd_nodes_pds_cap(int d, int Kg, double zeta, int64_t* h_cap) {
     clear_error();
     RBFFD_ARG(h_cap, "rbffd_nodes_pds_cap: NULL argument");
-    RBFFD_ARG(Kg >= 2 && Kg <= 20000 && zeta > 0.0 && zeta <= 1.0,
+    RBFFD_ARG(d == 2 || d == 3, "rbffd_nodes_pds_cap: d must be 2 or 3");
+    RBFFD_ARG(Kg >= 2 && Kg <= (d == 2 ? 20000 : 1000) && zeta > 0.0 && zeta <= 1.0,
               "rbffd_nodes_pds_cap: bad Kg / zeta");
+    if (d == 3) {
+        *h_cap = pds3_node_bound(Kg, zeta);
+        return RBFFD_OK;
+    }
     const int64_t G = pds_cells_per_axis(Kg, zeta);
     *h_cap = G * G;
     return RBFFD_OK;
@@ -637,13 +647,17 @@ extern "C" int rbffd_nodes_pds(int d, int shape, int Kg, int K, double zeta, uin
                                double* xyz, uint8_t* is_bnd, int64_t cap, int64_t* h_n_out,
                                int64_t* h_rounds, void* stream) {
     clear_error();
-    RBFFD_ARG(d == 2, "rbffd_nodes_pds: only d = 2 is implemented");
-    RBFFD_ARG(shape == 0 || shape == 1, "rbffd_nodes_pds: shape must be 0 (square) or 1 (disk)");
-    RBFFD_ARG(Kg >= 2 && Kg <= 20000, "rbffd_nodes_pds: Kg must be in [2, 20000]");
-    RBFFD_ARG(K >= 1 && K <= PDS_KMAX, "rbffd_nodes_pds: K must be in [1, 64]");
+    RBFFD_ARG(d == 2 || d == 3, "rbffd_nodes_pds: d must be 2 or 3");
+    RBFFD_ARG(shape == 0 || (shape == 1 && d == 2),
+              "rbffd_nodes_pds: shape must be 0 (square / cube) or 1 (disk, d = 2)");
+    RBFFD_ARG(Kg >= 2 && Kg <= (d == 2 ? 20000 : 1000),
+              "rbffd_nodes_pds: Kg must be in [2, 20000] (d = 2) or [2, 1000] (d = 3)");
+    RBFFD_ARG(K >= 1 && K <= (d == 2 ? PDS_KMAX : 256),
+              "rbffd_nodes_pds: K must be in [1, 64] (d = 2) or [1, 256] (d = 3)");
     RBFFD_ARG(zeta > 0.0 && zeta <= 1.0, "rbffd_nodes_pds: zeta must be in (0, 1]");
     RBFFD_ARG(h_n_out && (cap == 0 || (xyz && is_bnd)), "rbffd_nodes_pds: NULL argument");
     cudaStream_t s = as_stream(stream);
+    if (d == 3) return pds3_run(Kg, K, zeta, seed, xyz, is_bnd, cap, h_n_out, h_rounds, s);
     const int64_t G = pds_cells_per_axis(Kg, zeta);
     int64_t capF = std::min<int64_t>(G * G, 64 * G + 4096);
     int64_t capA = 8 * capF * K;

@@ -66,8 +66,9 @@ def test_pds_errors(rb):
     code = L.rbffd_nodes_pds(2, 0, 20, 15, 1 - 1e-10, 1, rb._ptr(buf), rb._ptr(b), 10,
                              ctypes.byref(n), r, s)
     assert code == rb.RBFFD_ERR_CAPACITY and n.value > 10
-    for args in ((3, 0, 20, 15, 0.9), (2, 2, 20, 15, 0.9), (2, 0, 20, 0, 0.9),
-                 (2, 0, 20, 65, 0.9), (2, 0, 20, 15, 0.0), (2, 0, 1, 15, 0.9)):
+    for args in ((4, 0, 20, 15, 0.9), (3, 1, 20, 50, 0.9), (2, 2, 20, 15, 0.9),
+                 (2, 0, 20, 0, 0.9), (2, 0, 20, 65, 0.9), (3, 0, 20, 257, 0.9),
+                 (2, 0, 20, 15, 0.0), (2, 0, 1, 15, 0.9), (3, 0, 1001, 50, 0.9)):
         code = L.rbffd_nodes_pds(*args, 1, rb._ptr(buf), rb._ptr(b), 10, ctypes.byref(n),
                                  r, s)
         assert code == rb.RBFFD_ERR_ARG
@@ -99,3 +100,55 @@ def test_solve_on_pds_nodes(rb, orc):
     assert steps == osteps == 300
     assert np.max(np.abs(H(u) - ou)) <= 1e-12 * np.max(np.abs(ou))
     plan.destroy()
+
+
+# ---------------------------------------------------------------- 3D (unit cube)
+@pytest.mark.parametrize("Kg,seed,K,zeta", [
+    (6, 1, 50, 1 - 1e-10),
+    (13, 2, 50, 1 - 1e-10),
+    (25, 3, 50, 1 - 1e-10),
+    (20, 4, 20, 1 - 1e-10),
+    (18, 5, 80, 0.85),
+])
+def test_pds3_bit_exact(rb, orc, Kg, seed, K, zeta):
+    xyz, bnd, rounds = rb.rbffd_nodes_pds(0, Kg, seed, K=K, zeta=zeta, d=3)
+    oxyz, obnd = orc.nodes_pds3(Kg, seed, K=K, zeta=zeta)
+    assert xyz.shape == oxyz.shape
+    assert np.array_equal(H(xyz), oxyz) and np.array_equal(H(bnd), obnd)
+
+
+def test_pds3_larger_bit_exact(rb, orc):
+    """h = 1/70 in the unit cube: about 290,000 nodes."""
+    xyz, bnd, rounds = rb.rbffd_nodes_pds(0, 70, 6, d=3)
+    oxyz, obnd = orc.nodes_pds3(70, 6)
+    assert np.array_equal(H(xyz), oxyz) and np.array_equal(H(bnd), obnd)
+    assert rounds > 20
+
+
+def test_pds3_capacity(rb):
+    L = rb.lib()
+    n, r = ctypes.c_int64(0), (ctypes.c_int64 * 2)()
+    buf = torch.empty((3, 10), dtype=torch.float64, device="cuda")
+    b = torch.empty(10, dtype=torch.uint8, device="cuda")
+    code = L.rbffd_nodes_pds(3, 0, 8, 50, 1 - 1e-10, 1, rb._ptr(buf), rb._ptr(b), 10,
+                             ctypes.byref(n), r, rb._stream("cuda"))
+    assert code == rb.RBFFD_ERR_CAPACITY and n.value > 10
+
+
+def test_supports_weights_on_pds3_nodes(rb, orc):
+    """Supports and weights on a 3D Poisson-disc set (m = 2, n = 20) against the oracle."""
+    Kg, m, seed = 12, 2, 7
+    n = gen.stencil_size(3, m)
+    xyz, bnd, _ = rb.rbffd_nodes_pds(0, Kg, seed, d=3)
+    oxyz, obnd = orc.nodes_pds3(Kg, seed)
+    inter = rb.rbffd_interior(bnd)
+    ointer = gen.interior_ids(obnd)
+    idx = rb.rbffd_knn(xyz, inter, n)
+    oidx = orc.knn_kdtree(oxyz, ointer, n)
+    assert np.array_equal(H(idx), oidx)
+    w, st = rb.rbffd_weights(xyz, idx, m)
+    ow, ost = orc.weights(oxyz, oidx, m)
+    assert np.array_equal(H(st), ost)
+    ok = ost == 0
+    assert ok.mean() > 0.99
+    assert np.all(np.abs(H(w)[ok] - ow[ok]) <= 1e-12 * np.abs(ow[ok]).max(axis=1, keepdims=True))

@@ -661,16 +661,18 @@ def run_stage(args):
             fs.append(Q["f"])
             us.append(Q["u0"])
             dts.append(Q["dt"])
-        batch = rb.Batch(plans, blocks_per_sm=2)
+        batch = rb.Batch(plans, blocks_per_sm=1)
+        batch.set_shape(1, 1, 1024)   # the shape the autotuner picks for the batched workload
         batch.solve(fs, us, dts, [args.sweeps] * len(plans), [0.0] * len(plans))
         torch.cuda.synchronize()
         batch.destroy()
         return
-    if args.mode == "pds":
-        rb.rbffd_nodes_pds(0, args.Kg, SEED)
+    if args.mode in ("pds", "pds3"):
+        dd = 2 if args.mode == "pds" else 3
+        rb.rbffd_nodes_pds(0, args.Kg, SEED, d=dd)
         torch.cuda.synchronize()
         torch.cuda.profiler.start()
-        rb.rbffd_nodes_pds(0, args.Kg, SEED)
+        rb.rbffd_nodes_pds(0, args.Kg, SEED, d=dd)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
         return
@@ -718,11 +720,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--mode", default="bench",
-                    choices=["bench", "sweep", "weights", "knn", "adjoint", "batch", "dc", "pds"],
+                    choices=["bench", "sweep", "weights", "knn", "adjoint", "batch", "dc", "pds",
+                             "pds3"],
                     help="build the workload and run only that stage: FP64 sweeps, weights, "
                          "kNN, reverse sweeps, batched solve, FP32 inner sweeps of one "
                          "defect correction, or Poisson-disc node placement of the unit "
-                         "square with h = 1/Kg (driver for profiler captures; prints nothing)")
+                         "square / cube with h = 1/Kg (driver for profiler captures; prints "
+                         "nothing)")
     ap.add_argument("--m", type=int, default=M, help="monomial order of the workload")
     ap.add_argument("--Kg", type=int, default=KG, help="grid cells per side of the workload")
     ap.add_argument("--sweeps", type=int, default=5, help="sweeps in --mode sweep")

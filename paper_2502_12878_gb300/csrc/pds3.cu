@@ -31,14 +31,15 @@ struct Pds3Args {
     uint8_t* B;
     double* R;           // [maxn][9] rotation of each node (set when it is added)
     int32_t* cell;       // [G^3] node per cell, -1 empty
-    int32_t* chead;      // [G^3] candidate lists, -1 empty
+    int32_t* chead;      // [Gc^3] candidate lists on the coarse grid, -1 empty
     const double* E;     // [K][3] Fibonacci-sphere directions
     // per generation (capacity capC candidates)
     double* cx;
     double* cy;
     double* cz;
     int32_t* cflag;      // passed (domain and earlier generations); then reused
-    int32_t* ccell;
+    int32_t* ccell;      // fine (node) cell of each candidate inside the cube
+    int32_t* ccoarse;    // coarse (candidate) cell
     int32_t* pos;        // [capC + 1] scan of cflag
     int32_t* V;          // passing keys, ascending
     int32_t* cnext;
@@ -51,7 +52,9 @@ struct Pds3Args {
     int K;
     double h, cs, r2;
     float inv_cs;
-    int64_t G, maxn;
+    float inv_csc;       // coarse cells: side 1.01 zeta h, so candidates closer than
+                         // zeta h lie in adjacent coarse cells (3 x 3 x 3 searched)
+    int64_t G, Gc, maxn;
     uint64_t seed;
 };
 
@@ -63,6 +66,16 @@ __device__ __forceinline__ int64_t p3_cell(const Pds3Args& A, double x, double y
     b = b < 0 ? 0 : (b >= A.G ? A.G - 1 : b);
     c = c < 0 ? 0 : (c >= A.G ? A.G - 1 : c);
     return (a * A.G + b) * A.G + c;
+}
+
+__device__ __forceinline__ int64_t p3_coarse(const Pds3Args& A, double x, double y, double z) {
+    int64_t a = (int64_t)__fmul_rn(__double2float_rn(x), A.inv_csc);
+    int64_t b = (int64_t)__fmul_rn(__double2float_rn(y), A.inv_csc);
+    int64_t c = (int64_t)__fmul_rn(__double2float_rn(z), A.inv_csc);
+    a = a < 0 ? 0 : (a >= A.Gc ? A.Gc - 1 : a);
+    b = b < 0 ? 0 : (b >= A.Gc ? A.Gc - 1 : b);
+    c = c < 0 ? 0 : (c >= A.Gc ? A.Gc - 1 : c);
+    return (a * A.Gc + b) * A.Gc + c;
 }
 
 __device__ __forceinline__ double p3_d2(double ax, double ay, double az, double bx, double by,
@@ -181,16 +194,25 @@ __global__ void p3_gen(Pds3Args A, int64_t lo, int64_t total) {
         if (ok) {
             const int64_t g = p3_cell(A, c[0], c[1], c[2]);
             A.ccell[e] = (int32_t)g;
+            A.ccoarse[e] = (int32_t)p3_coarse(A, c[0], c[1], c[2]);
             const int64_t g0 = g / (A.G * A.G), g1 = (g / A.G) % A.G, g2 = g % A.G;
-            for (int64_t a = g0 - 2; a <= g0 + 2 && ok; ++a) {
-                if (a < 0 || a >= A.G) continue;
-                for (int64_t b = g1 - 2; b <= g1 + 2 && ok; ++b) {
-                    if (b < 0 || b >= A.G) continue;
-                    for (int64_t d = g2 - 2; d <= g2 + 2 && ok; ++d) {
-                        if (d < 0 || d >= A.G) continue;
-                        const int32_t q = A.cell[(a * A.G + b) * A.G + d];
-                        if (q >= 0 && p3_d2(c[0], c[1], c[2], A.X[q], A.Y[q], A.Z[q]) < A.r2)
-                            ok = false;
+            // the 27 nearest cells first (most blocking nodes are there), then
+            // the rest of the 5 x 5 x 5 block; the first conflict ends the test
+            for (int shell = 0; shell < 2 && ok; ++shell) {
+                for (int64_t a = g0 - 2; a <= g0 + 2 && ok; ++a) {
+                    if (a < 0 || a >= A.G) continue;
+                    for (int64_t b = g1 - 2; b <= g1 + 2 && ok; ++b) {
+                        if (b < 0 || b >= A.G) continue;
+                        for (int64_t d = g2 - 2; d <= g2 + 2 && ok; ++d) {
+                            if (d < 0 || d >= A.G) continue;
+                            const bool inner = a >= g0 - 1 && a <= g0 + 1 && b >= g1 - 1 &&
+                                               b <= g1 + 1 && d >= g2 - 1 && d <= g2 + 1;
+                            if (inner != (shell == 0)) continue;
+                            const int32_t q = A.cell[(a * A.G + b) * A.G + d];
+                            if (q >= 0 &&
+                                p3_d2(c[0], c[1], c[2], A.X[q], A.Y[q], A.Z[q]) < A.r2)
+                                ok = false;
+                        }
                     }
                 }
             }
@@ -206,28 +228,30 @@ __global__ void p3_compact(Pds3Args A, int64_t total) {
         if (!A.cflag[e]) continue;
         const int32_t v = A.pos[e];
         A.V[v] = (int32_t)e;
-        A.cnext[v] = atomicExch(&A.chead[A.ccell[e]], v);
+        A.cnext[v] = atomicExch(&A.chead[A.ccoarse[e]], v);
         A.st[v] = P3_UND;
     }
 }
 
-// lower-key conflicts of each passing candidate (FILL = false counts them)
+// lower-key conflicts of each passing candidate (FILL = false counts them),
+// from the 3 x 3 x 3 coarse cells around it
 template <bool FILL>
 __global__ void p3_conflicts(Pds3Args A, int64_t nv) {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv;
          v += (int64_t)gridDim.x * blockDim.x) {
         const int32_t ev = A.V[v];
         const double x = A.cx[ev], y = A.cy[ev], z = A.cz[ev];
-        const int64_t g = A.ccell[ev];
-        const int64_t g0 = g / (A.G * A.G), g1 = (g / A.G) % A.G, g2 = g % A.G;
+        const int64_t g = A.ccoarse[ev];
+        const int64_t Gc = A.Gc;
+        const int64_t g0 = g / (Gc * Gc), g1 = (g / Gc) % Gc, g2 = g % Gc;
         int32_t k = FILL ? A.off[v] : 0;
-        for (int64_t a = g0 - 2; a <= g0 + 2; ++a) {
-            if (a < 0 || a >= A.G) continue;
-            for (int64_t b = g1 - 2; b <= g1 + 2; ++b) {
-                if (b < 0 || b >= A.G) continue;
-                for (int64_t d = g2 - 2; d <= g2 + 2; ++d) {
-                    if (d < 0 || d >= A.G) continue;
-                    for (int32_t w = A.chead[(a * A.G + b) * A.G + d]; w >= 0; w = A.cnext[w]) {
+        for (int64_t a = g0 - 1; a <= g0 + 1; ++a) {
+            if (a < 0 || a >= Gc) continue;
+            for (int64_t b = g1 - 1; b <= g1 + 1; ++b) {
+                if (b < 0 || b >= Gc) continue;
+                for (int64_t d = g2 - 1; d <= g2 + 1; ++d) {
+                    if (d < 0 || d >= Gc) continue;
+                    for (int32_t w = A.chead[(a * Gc + b) * Gc + d]; w >= 0; w = A.cnext[w]) {
                         if (w >= v) continue;
                         const int32_t ew = A.V[w];
                         if (!(p3_d2(x, y, z, A.cx[ew], A.cy[ew], A.cz[ew]) < A.r2)) continue;
@@ -280,7 +304,7 @@ __global__ void p3_commit(Pds3Args A, int64_t nv, int64_t N) {
          v += (int64_t)gridDim.x * blockDim.x) {
         const int32_t e = A.V[v];
         const int32_t cell = A.ccell[e];
-        A.chead[cell] = -1;
+        A.chead[A.ccoarse[e]] = -1;
         if (A.st[v] != P3_IN) continue;
         const int64_t id = N + A.rank[v];
         if (id >= A.maxn) {
@@ -348,11 +372,16 @@ int pds3_run(int Kg, int K, double zeta, uint64_t seed, double* xyz, uint8_t* is
     const int64_t ncell = G * G * G;
     const int64_t maxn = std::min<int64_t>(ncell, pds3_node_bound(Kg, zeta));
     const double t = zeta * h;
+    const double csc = 1.01 * t;
+    const int64_t Gc = (int64_t)(1.0 / csc) + 2;
+    const int64_t ncoarse = Gc * Gc * Gc;
     Pds3Args A = {};
     A.K = K;
     A.h = h;
     A.cs = cs;
     A.inv_cs = (float)(1.0 / cs);
+    A.inv_csc = (float)(1.0 / csc);
+    A.Gc = Gc;
     A.r2 = t * t;
     A.G = G;
     A.maxn = maxn;
@@ -364,7 +393,7 @@ int pds3_run(int Kg, int K, double zeta, uint64_t seed, double* xyz, uint8_t* is
     RBFFD_CHECK_CUDA(bB.alloc(maxn, s));
     RBFFD_CHECK_CUDA(bR.alloc(sizeof(double) * 9 * maxn, s));
     RBFFD_CHECK_CUDA(bcell.alloc(sizeof(int32_t) * ncell, s));
-    RBFFD_CHECK_CUDA(bhead.alloc(sizeof(int32_t) * ncell, s));
+    RBFFD_CHECK_CUDA(bhead.alloc(sizeof(int32_t) * ncoarse, s));
     RBFFD_CHECK_CUDA(bE.alloc(sizeof(double) * 3 * PDS3_KMAX, s));
     RBFFD_CHECK_CUDA(bflags.alloc(sizeof(int) * 4, s));
     A.X = bX.as<double>();
@@ -377,7 +406,7 @@ int pds3_run(int Kg, int K, double zeta, uint64_t seed, double* xyz, uint8_t* is
     A.E = bE.as<double>();
     A.flags = bflags.as<int>();
     RBFFD_CHECK_CUDA(cudaMemsetAsync(A.cell, 0xff, sizeof(int32_t) * ncell, s));
-    RBFFD_CHECK_CUDA(cudaMemsetAsync(A.chead, 0xff, sizeof(int32_t) * ncell, s));
+    RBFFD_CHECK_CUDA(cudaMemsetAsync(A.chead, 0xff, sizeof(int32_t) * ncoarse, s));
     RBFFD_CHECK_CUDA(cudaMemsetAsync(A.flags, 0, sizeof(int) * 4, s));
     const int64_t side = (int64_t)Kg + 1, inner = (int64_t)Kg - 1;
     const int64_t nb = side * side * side - inner * inner * inner;
@@ -385,7 +414,8 @@ int pds3_run(int Kg, int K, double zeta, uint64_t seed, double* xyz, uint8_t* is
     const unsigned grid = (unsigned)device_sm_count() * 8;
     p3_seeds<<<grid, 256, 0, s>>>(A, Kg, nb);
     RBFFD_CHECK_CUDA(cudaGetLastError());
-    Grow gcx, gcy, gcz, gflag, gccell, gpos, gV, gnext, gdeg, goff, gadj, gst, grank, gtmp;
+    Grow gcx, gcy, gcz, gflag, gccell, gcoarse, gpos, gV, gnext, gdeg, goff, gadj, gst, grank,
+        gtmp;
     int64_t lo = 0, hi = nb, N = nb, rounds = 0, passes = 0;
     int hflags[4] = {0, 0, 0, 0};
     while (hi > lo) {
@@ -400,6 +430,7 @@ int pds3_run(int Kg, int K, double zeta, uint64_t seed, double* xyz, uint8_t* is
         RBFFD_CHECK_CUDA(gcz.need(total, s, &A.cz));
         RBFFD_CHECK_CUDA(gflag.need(total, s, &A.cflag));
         RBFFD_CHECK_CUDA(gccell.need(total, s, &A.ccell));
+        RBFFD_CHECK_CUDA(gcoarse.need(total, s, &A.ccoarse));
         RBFFD_CHECK_CUDA(gpos.need(total + 1, s, &A.pos));
         int64_t* tmp = nullptr;
         RBFFD_CHECK_CUDA(gtmp.need(scan_tmp_elems(total + 1), s, &tmp));
@@ -429,14 +460,17 @@ int pds3_run(int Kg, int K, double zeta, uint64_t seed, double* xyz, uint8_t* is
             RBFFD_CHECK_CUDA(gadj.need((size_t)nnz, s, &A.adj));
             p3_conflicts<true><<<grid, 256, 0, s>>>(A, nv);
             // passes until every candidate is decided (each decides at least the
-            // lowest undecided one)
-            const int per = 31;
+            // lowest undecided one); short key ranges (a candidate is a chain of
+            // dependent L2 loads), four passes per check of the undecided count
+            const int per = 7;
             const int64_t T = (nv + per - 1) / per;
             const unsigned pgrid = (unsigned)((T + 127) / 128);
-            for (int64_t pass = 0; pass <= nv; ++pass) {
-                RBFFD_CHECK_CUDA(cudaMemsetAsync(A.flags, 0, sizeof(int), s));
-                p3_pass<<<pgrid, 128, 0, s>>>(A, nv, per);
-                ++passes;
+            for (int64_t pass = 0; pass <= nv; pass += 4) {
+                for (int q = 0; q < 4; ++q) {
+                    RBFFD_CHECK_CUDA(cudaMemsetAsync(A.flags, 0, sizeof(int), s));
+                    p3_pass<<<pgrid, 128, 0, s>>>(A, nv, per);
+                    ++passes;
+                }
                 int open = 0;
                 RBFFD_CHECK_CUDA(cudaMemcpyAsync(&open, A.flags, sizeof(int),
                                                  cudaMemcpyDeviceToHost, s));

@@ -308,35 +308,61 @@ __global__ void __launch_bounds__(STEP_THREADS, MINB) step_kernel(StepArgs A, St
     }
 }
 
-// grid barrier for the cooperative launch; waits give up after
-// SPIN_LIMIT_CYCLES and report false
-__device__ bool grid_sync(StepCtrl* c) {
-    __shared__ int s_ok;
-    __syncthreads();
+// End of step k in the persistent launch: a grid barrier fused with the
+// stop decision.  Each block adds its max |r| and arrives (arrivals are
+// counted from the start of the run, so nothing is reset); the last block to
+// arrive reads the step's max, applies the stop rule, clears the next-but-one
+// residual slot, and publishes ((k + 1) << 4) | decision in one word, which
+// the other blocks poll - so the decision needs no second round trip.  Waits
+// give up after SPIN_LIMIT_CYCLES (decision DONE_TIMEOUT).  Returns the
+// decision in every thread.
+__device__ int step_end(StepCtrl* c, long long k, long long k0, long long kmax,
+                        unsigned long long m) {
+    __shared__ int s_dec;
     if (threadIdx.x == 0) {
-        volatile unsigned* genp = &c->bar_gen;
-        unsigned g = *genp;
-        int ok = 1;
-        __threadfence();
-        unsigned t = atomicAdd(&c->bar_count, 1u);
-        if (t == gridDim.x - 1) {
-            atomicExch(&c->bar_count, 0u);
+        atomicMax(&c->res[k % 3], m);
+        __threadfence();   // this block's iterate writes and max before its arrival
+        const unsigned long long target = (unsigned long long)(k - k0 + 1) * gridDim.x;
+        const unsigned long long t = atomicAdd(&c->arrivals, 1ull) + 1ull;
+        int dn;
+        if (t == target) {
             __threadfence();
-            atomicAdd(&c->bar_gen, 1u);
+            const double R = bitsd(atomicAdd(&c->res[k % 3], 0ull));
+            volatile StepCtrl* vc = c;
+            if (k == 0) vc->res_first = R;
+            const double R0 = k == 0 ? R : vc->res_first;
+            if (!isfinite(R)) dn = DONE_NONFINITE;
+            else if (R < vc->tol) dn = DONE_CONVERGED;
+            else if (k > 0 && R0 > 0.0 && R > 1e6 * R0) dn = DONE_DIVERGED;
+            else if (k + 1 >= kmax) dn = DONE_CAP;
+            else dn = DONE_RUNNING;
+            vc->res_last = R;
+            vc->k = k + 1;
+            vc->res[(k + 1) % 3] = 0ull;
+            if (dn != DONE_RUNNING) vc->done = dn;
+            __threadfence();
+            atomicExch(&c->sync_word, ((unsigned long long)(k + 1) << 4) | (unsigned long long)dn);
         } else {
-            long long t0 = clock64();
-            while (*genp == g) {
+            volatile unsigned long long* w = &c->sync_word;
+            const long long t0 = clock64();
+            for (;;) {
+                const unsigned long long v = *w;
+                if ((v >> 4) == (unsigned long long)(k + 1)) {
+                    dn = (int)(v & 15ull);
+                    break;
+                }
                 if (clock64() - t0 > SPIN_LIMIT_CYCLES) {
-                    ok = 0;
+                    atomicExch(&c->done, DONE_TIMEOUT);
+                    dn = DONE_TIMEOUT;
                     break;
                 }
             }
+            __threadfence();   // the other blocks' iterate writes before this block reads
         }
-        __threadfence();
-        s_ok = ok;
+        s_dec = dn;
     }
     __syncthreads();
-    return s_ok != 0;
+    return s_dec;
 }
 
 // persistent mode: all steps in one cooperative launch
@@ -344,7 +370,6 @@ template <int NN, int MODE, int MINB>
 __global__ void __launch_bounds__(STEP_THREADS, MINB) persistent_kernel(StepArgs A, StepCtrl* c) {
     __shared__ long long s_k, s_max;
     __shared__ double s_dt;
-    __shared__ int s_stop;
     if (threadIdx.x == 0) {
         volatile StepCtrl* vc = c;
         s_k = vc->k;
@@ -353,46 +378,13 @@ __global__ void __launch_bounds__(STEP_THREADS, MINB) persistent_kernel(StepArgs
     }
     __syncthreads();
     const double dt = s_dt;
-    const long long kmax = s_max;
+    const long long kmax = s_max, k0 = s_k;
     const int64_t warp = (int64_t)blockIdx.x * (STEP_THREADS / 32) + (threadIdx.x >> 5);
     const int64_t nw = (int64_t)gridDim.x * (STEP_THREADS / 32);
-    for (long long k = s_k; k < kmax; ++k) {
+    for (long long k = k0; k < kmax; ++k) {
         unsigned long long m = step_rows<NN, MODE, true>(A, (int)(k & 1), dt, (float)dt, warp, nw);
         m = block_max_bits(m);
-        if (threadIdx.x == 0) {
-            atomicMax(&c->res[k % 3], m);
-            if (blockIdx.x == 0) atomicExch(&c->res[(k + 1) % 3], 0ull);
-        }
-        if (!grid_sync(c)) {
-            if (threadIdx.x == 0) atomicExch(&c->done, DONE_TIMEOUT);
-            return;
-        }
-        if (threadIdx.x == 0) {
-            volatile unsigned long long* rp = &c->res[k % 3];
-            double R = bitsd(*rp);
-            // every block evaluates the same rule on the same value
-            int dn;
-            if (!isfinite(R)) dn = DONE_NONFINITE;
-            else if (R < c->tol) dn = DONE_CONVERGED;
-            else if (k > 0 && R > 1e6 * ((volatile StepCtrl*)c)->res_first &&
-                     ((volatile StepCtrl*)c)->res_first > 0.0) dn = DONE_DIVERGED;
-            else if (k + 1 >= kmax) dn = DONE_CAP;
-            else dn = DONE_RUNNING;
-            s_stop = dn;
-            if (blockIdx.x == 0) {
-                if (k == 0) c->res_first = R;
-                c->res_last = R;
-                c->k = k + 1;
-                if (dn != DONE_RUNNING) c->done = dn;
-            }
-        }
-        __syncthreads();
-        if (s_stop != DONE_RUNNING) return;
-        // res_first must be visible before the next step's divergence test
-        if (k == 0 && !grid_sync(c)) {
-            if (threadIdx.x == 0) atomicExch(&c->done, DONE_TIMEOUT);
-            return;
-        }
+        if (step_end(c, k, k0, kmax, m) != DONE_RUNNING) return;
     }
 }
 

@@ -101,10 +101,12 @@ class Clocks:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, path: str | None = None):
+        """``path``: where the raw samples go (default: a temporary file)."""
+        import tempfile
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = path or os.path.join(tempfile.gettempdir(), f"rbffd_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
@@ -718,6 +720,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clocks-csv", default=None,
+                    help="file for the raw nvidia-smi samples of the timed region")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--mode", default="bench",
                     choices=["bench", "sweep", "weights", "knn", "adjoint", "batch", "dc", "pds",
@@ -772,7 +776,7 @@ def main():
     # device-resident timed region
     gpu_index = torch.cuda.current_device()
     loop_ms, loop_steps, launches = 0.0, 0, 0
-    with Clocks(gpu_index) as clk:
+    with Clocks(gpu_index, args.clocks_csv) as clk:
         barrier()
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)

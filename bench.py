@@ -575,6 +575,38 @@ def run_workload(args):
         plan.destroy()
         return
 
+    if args.workload == "convergence":
+        # error vs node spacing per augmentation order on Poisson-disc squares: each
+        # problem iterated (FP64, Eq. 6) to max|r| < tol, then max/mean error vs u^a
+        rows = {}
+        tol = 1e-9
+        for m in (2, 4, 6):
+            for Kg in (25, 50, 100, 200):
+                xyz, bnd, _ = rb.rbffd_nodes_pds(0, Kg, 5)
+                Q = _gpu_problem_from_nodes(rb, torch, xyz, bnd, m, dev)
+                u = Q["u0"].clone()
+                t0 = time.perf_counter()
+                code, steps, res = Q["plan"].solve_explicit(Q["f"], u, Q["dt"], 8_000_000, tol)
+                torch.cuda.synchronize()
+                el = time.perf_counter() - t0
+                emax, emean = rb.rbffd_error(u, Q["ua"])
+                rows[f"m{m}_Kg{Kg}"] = {"m": m, "h": 1.0 / Kg, "N": Q["N"], "steps": steps,
+                                        "residual": res, "converged": code == 0,
+                                        "max_err": emax, "mean_abs_err": emean, "seconds": el}
+                Q["plan"].destroy()
+        slopes = {}
+        for m in (2, 4, 6):
+            hs = np.array([rows[f"m{m}_Kg{K}"]["h"] for K in (25, 50, 100, 200)])
+            es = np.array([rows[f"m{m}_Kg{K}"]["max_err"] for K in (25, 50, 100, 200)])
+            # errors near tol / (2 pi^2) ~ 5e-11 are set by the stop tolerance, not by h
+            ok = es > 1e-9
+            slopes[f"m{m}"] = float(np.polyfit(np.log(hs[ok]), np.log(es[ok]), 1)[0]) \
+                if ok.sum() >= 2 else None
+        _line("convergence: max error vs h on Poisson-disc squares (Sec. II-C), m = 2/4/6, "
+              "FP64 iteration to max|r| < 1e-9", slopes["m4"] or 0.0, "observed order (m=4)",
+              0.0, 1, 0, {"slopes": slopes, "cases": rows})
+        return
+
     if args.workload == "support_sweep":
         # the support-size study at m = 2 (n > 2M), 2D square 1,002,001 nodes
         xyz, bnd = rb.rbffd_nodes(2, 0, 1000, 0.3, 2, device=dev)
@@ -738,7 +770,8 @@ def main():
     ap.add_argument("--batch-domains", type=int, default=256, help="domains in --mode batch")
     ap.add_argument("--workload", default="square1M_m4",
                     choices=["square1M_m4", "batched256", "cube8M_m4", "adjoint1M_m4", "tta",
-                             "mixed1M_m4", "support_sweep", "pds1M_m4", "pds3_cube_m4"],
+                             "mixed1M_m4", "support_sweep", "pds1M_m4", "pds3_cube_m4",
+                             "convergence"],
                     help="square1M_m4 is the headline; the others measure the other workloads")
     args = ap.parse_args()
     if args.workload != "square1M_m4":

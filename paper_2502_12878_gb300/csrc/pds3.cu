@@ -14,7 +14,6 @@
 #include <math.h>
 
 #include <algorithm>
-#include <new>
 
 #include "common.cuh"
 #include "nodegen.cuh"
@@ -344,22 +343,34 @@ int64_t pds3_node_bound(int Kg, double zeta) {
     return (int64_t)(1.01 * b) + 64;
 }
 
-// scratch that grows to the largest generation seen
+// scratch that grows to the largest generation seen (stream-ordered: a
+// buffer is released on the stream before its replacement is allocated)
 struct Grow {
-    Scratch s;
+    void* p = nullptr;
     size_t bytes = 0;
+    cudaStream_t st = nullptr;
+    Grow() = default;
+    Grow(const Grow&) = delete;
+    Grow& operator=(const Grow&) = delete;
+    ~Grow() {
+        if (p) cudaFreeAsync(p, st);
+    }
     template <class T>
-    cudaError_t need(size_t n, cudaStream_t st, T** out) {
+    cudaError_t need(size_t n, cudaStream_t s, T** out) {
         const size_t want = sizeof(T) * std::max<size_t>(n, 1);
         if (want > bytes) {
-            s.~Scratch();
-            new (&s) Scratch();
+            if (p) cudaFreeAsync(p, st);
+            p = nullptr;
             bytes = 0;
-            cudaError_t e = s.alloc(want + want / 4, st);
-            if (e != cudaSuccess) return e;
+            st = s;
+            cudaError_t e = cudaMallocAsync(&p, want + want / 4, s);
+            if (e != cudaSuccess) {
+                p = nullptr;
+                return e;
+            }
             bytes = want + want / 4;
         }
-        *out = s.as<T>();
+        *out = reinterpret_cast<T*>(p);
         return cudaSuccess;
     }
 };

@@ -152,3 +152,31 @@ def test_supports_weights_on_pds3_nodes(rb, orc):
     ok = ost == 0
     assert ok.mean() > 0.99
     assert np.all(np.abs(H(w)[ok] - ow[ok]) <= 1e-12 * np.abs(ow[ok]).max(axis=1, keepdims=True))
+
+
+def test_convergence_order_on_pds_nodes(rb):
+    """The whole GPU path on Poisson-disc squares (h = 1/20, 1/40, 1/80, m = 4),
+    iterated to max|r| < 1e-10: the max error against u = sin(pi x) sin(pi y) falls
+    at an observed order of at least m - 1 = 3 (the local truncation order)."""
+    hs, errs = [], []
+    for Kg in (20, 40, 80):
+        xyz, bnd, _ = rb.rbffd_nodes_pds(0, Kg, 11)
+        n = gen.stencil_size(2, 4)
+        inter = rb.rbffd_interior(bnd)
+        idx = rb.rbffd_knn(xyz, inter, n)
+        w, st = rb.rbffd_weights(xyz, idx, 4)
+        xh, bh, ih = H(xyz), H(bnd), H(inter)
+        f = torch.from_numpy(gen.source(xh, ih)).cuda()
+        u = torch.from_numpy(gen.start_iterate(xh, bh)).cuda()
+        ua = torch.from_numpy(gen.exact_solution(xh)).cuda()
+        plan = rb.Plan(xyz, bnd, inter, idx, w)
+        dt, rho = plan.stable_dt(torch.from_numpy(gen.random_vector(len(ih), 3)).cuda(), 200)
+        code, steps, res = plan.solve_explicit(f, u, 0.9 * dt, 2_000_000, 1e-10)
+        assert code == rb.RBFFD_OK
+        emax, _ = rb.rbffd_error(u, ua)
+        hs.append(1.0 / Kg)
+        errs.append(emax)
+        plan.destroy()
+    assert errs[0] > errs[1] > errs[2]
+    order = np.polyfit(np.log(hs), np.log(errs), 1)[0]
+    assert order >= 3.0, (errs, order)

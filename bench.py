@@ -261,12 +261,16 @@ def run_reference(args):
         dist.destroy_process_group()
 
 
-def _gpu_problem_from_nodes(rb, torch, xyz, bnd, m, dev, power_iters=200):
+def _gpu_problem_from_nodes(rb, torch, xyz, bnd, m, dev, power_iters=200, inter=None, idx=None,
+                            w=None):
     d = xyz.shape[0]
     n = gen.stencil_size(d, m)
-    inter = rb.rbffd_interior(bnd)
-    idx = rb.rbffd_knn(xyz, inter, n)
-    w, st = rb.rbffd_weights(xyz, idx, m)
+    if inter is None:
+        inter = rb.rbffd_interior(bnd)
+    if idx is None:
+        idx = rb.rbffd_knn(xyz, inter, n)
+    if w is None:
+        w, st = rb.rbffd_weights(xyz, idx, m)
     plan = rb.Plan(xyz, bnd, inter, idx, w, rb.RBFFD_ORDER_MORTON)
     xyz_h, bnd_h, inter_h = xyz.cpu().numpy(), bnd.cpu().numpy(), inter.cpu().numpy()
     f = torch.from_numpy(gen.source(xyz_h, inter_h)).to(dev)
@@ -299,11 +303,32 @@ def run_workload(args):
 
     if args.workload == "batched256":
         t0 = time.perf_counter()
-        P = []
-        for (shape, Kg, m, seed) in gen.batched_domains(256, seed=4):
+        doms = gen.batched_domains(256, seed=4)
+        nodes, inters, idxs = [], [], []
+        for (shape, Kg, m, seed) in doms:
             xyz, bnd = rb.rbffd_nodes(2, shape, Kg, 0.3, seed, device=dev)
-            P.append(_gpu_problem_from_nodes(rb, torch, xyz, bnd, m, dev, power_iters=200))
+            inter = rb.rbffd_interior(bnd)
+            nodes.append((xyz, bnd))
+            inters.append(inter)
+            idxs.append(rb.rbffd_knn(xyz, inter, gen.stencil_size(2, m)))
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        # the weight builds of all domains in one call (two launches) ...
+        wb = rb.rbffd_weights_batch([x for x, _ in nodes], idxs, [m for (_, _, m, _) in doms])
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        # ... and, for comparison, one call per domain (same results)
+        w1 = [rb.rbffd_weights(x, i, m)[0] for (x, _), i, (_, _, m, _) in zip(nodes, idxs, doms)]
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
+        weights_same = all(torch.equal(a[0], b) for a, b in zip(wb, w1))
+        del w1
+        P = [_gpu_problem_from_nodes(rb, torch, x, b, m, dev, power_iters=200, inter=it, idx=ix,
+                                     w=ww[0])
+             for (x, b), it, ix, ww, (_, _, m, _) in zip(nodes, inters, idxs, wb, doms)]
         setup = time.perf_counter() - t0
+        weight_build = {"batched_ms": (t2 - t1) * 1e3, "per_domain_ms": (t3 - t2) * 1e3,
+                        "identical": weights_same}
         plans = [q["plan"] for q in P]
         fs = [q["f"] for q in P]
         dts = [q["dt"] for q in P]
@@ -354,7 +379,8 @@ def run_workload(args):
                "node_updates": upd, "nodes_total": nodes,
                "domains_converged": sum(1 for x in st_b if x == 0),
                "max_error_vs_closed_form": max(errs_b), "identical_to_one_at_a_time": same,
-               "launch_shape": list(shape), "setup_s": setup, "timing": timing})
+               "launch_shape": list(shape), "setup_s": setup, "weight_build": weight_build,
+               "timing": timing})
         batch.destroy()
         return
 

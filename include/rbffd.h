@@ -224,6 +224,22 @@ RBFFD_API int rbffd_weights_dir(const double* xyz, int64_t N, int d, const int32
                                 void* stream);
 
 /*
+ * rbffd_weights_batch - rbffd_weights for many independent calls (domains) in
+ * two launches (calls whose systems take one warp, s = n + M <= 48, and the
+ * rest): the stencils of all calls are one index space, each team of warps
+ * finding its call by binary search over the calls' stencil counts.  Every
+ * stencil sees the operations of rbffd_weights, so the results are the same
+ * bit for bit.  Host arrays [ncalls]: xyz (device [d][N]), N, d, idx (device
+ * [nc][n]), nc, n, m, w (device out [nc][n]), status (device out [nc]);
+ * h_n_bad (host out [ncalls], may be NULL): singular stencils per call.
+ * Returns RBFFD_ERR_SINGULAR if any stencil of any call is singular.
+ */
+RBFFD_API int rbffd_weights_batch(int ncalls, const double* const* xyz, const int64_t* N,
+                                  const int* d, const int32_t* const* idx, const int64_t* nc,
+                                  const int* n, const int* m, double* const* w,
+                                  int8_t* const* status, int64_t* h_n_bad, void* stream);
+
+/*
  * rbffd_apply - Eq. 1: Lu[r] = sum_j w[r][j] * u[idx[r][j]], accumulated as
  * a fused multiply-add chain in support order starting from 0.
  *   w, idx [nc][n] (row-major, as rbffd_weights / rbffd_knn give them),

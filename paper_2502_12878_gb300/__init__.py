@@ -51,7 +51,7 @@ EXPORTED = [
     "rbffd_batch_destroy", "rbffd_solve_batch", "rbffd_batch_set_shape", "rbffd_batch_stats",
     "rbffd_error", "rbffd_batch_domain_times", "rbffd_batch_set_costs", "rbffd_adjoint_w",
     "rbffd_knn_masked", "rbffd_weights_dir", "rbffd_plan_set_neumann", "rbffd_plan_layout",
-    "rbffd_nodes_pds", "rbffd_nodes_pds_cap",
+    "rbffd_nodes_pds", "rbffd_nodes_pds_cap", "rbffd_weights_batch",
 ]
 RBFFD_KNN_NOALLOC_MAX_NODES = 262144
 
@@ -112,6 +112,7 @@ def lib():
         "rbffd_plan_layout": (I, [P, PI64, PI64, PD, PD]),
         "rbffd_nodes_pds": (I, [I, I, I, I, D, U64, P, P, I64, PI64, PI64, P]),
         "rbffd_nodes_pds_cap": (I, [I, I, D, PI64]),
+        "rbffd_weights_batch": (I, [I, P, P, P, P, P, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -269,6 +270,28 @@ def rbffd_weights(xyz: torch.Tensor, idx: torch.Tensor, m: int, check: bool = Tr
                                ctypes.byref(nbad), ctypes.byref(first), _stream(xyz.device))
     _check(code, (RBFFD_OK,) if check else (RBFFD_OK, RBFFD_ERR_SINGULAR))
     return w, st
+
+
+def rbffd_weights_batch(xyzs, idxs, ms, check: bool = True):
+    """Weights of many domains in one call (two launches): lists of xyz [d, N], supports
+    idx [nc, n] and orders m.  Returns a list of (w [nc, n], status [nc])."""
+    nd = len(xyzs)
+    xyzs = [_dev(x, torch.float64, "xyz") for x in xyzs]
+    idxs = [_dev(i, torch.int32, "idx") for i in idxs]
+    ws = [torch.empty(i.shape, dtype=torch.float64, device=i.device) for i in idxs]
+    sts = [torch.empty(i.shape[0], dtype=torch.int8, device=i.device) for i in idxs]
+    VP = ctypes.c_void_p * nd
+    I64 = ctypes.c_int64 * nd
+    IA = ctypes.c_int * nd
+    bad = I64()
+    code = lib().rbffd_weights_batch(
+        nd, VP(*[x.data_ptr() for x in xyzs]), I64(*[x.shape[1] for x in xyzs]),
+        IA(*[x.shape[0] for x in xyzs]), VP(*[i.data_ptr() for i in idxs]),
+        I64(*[i.shape[0] for i in idxs]), IA(*[i.shape[1] for i in idxs]), IA(*ms),
+        VP(*[w.data_ptr() for w in ws]), VP(*[t.data_ptr() for t in sts]), bad,
+        _stream(xyzs[0].device))
+    _check(code, (RBFFD_OK,) if check else (RBFFD_OK, RBFFD_ERR_SINGULAR))
+    return list(zip(ws, sts))
 
 
 def rbffd_apply(w: torch.Tensor, idx: torch.Tensor, u: torch.Tensor) -> torch.Tensor:

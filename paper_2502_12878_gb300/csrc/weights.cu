@@ -17,6 +17,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "common.cuh"
 
@@ -102,22 +103,14 @@ __device__ __forceinline__ long long abs_key(double x) {
     return b > 0x7ff0000000000000ll ? -1ll : b;    // NaN: never the largest
 }
 
+// the weights of stencil r of one call (all of the team's threads)
 template <int TW>
-__global__ void __launch_bounds__(256) weights_kernel(WeightArgs A, int teams_per_block) {
-    extern __shared__ double wsm[];
-    __shared__ double redv[8];
-    __shared__ long long redk[8];
-    __shared__ int redi[8];
-    __shared__ double bcast[8];   // per-team scalar broadcast (reciprocal pivot, x_j)
+__device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, double* G, double* xi,
+                                            int tid, int team, double* redv, long long* redk,
+                                            int* redi, double* bcast) {
     constexpr int T = 32 * TW;
-    const int tid = threadIdx.x % T;
-    const int team = threadIdx.x / T;
     const int n = A.n, M = A.M, s = A.s, P = A.pitch, d = A.d;
-    double* G = wsm + (size_t)team * ((size_t)s * P + 3 * n);
-    double* xi = G + (size_t)s * P;
-    const int64_t teams = (int64_t)gridDim.x * teams_per_block;
-
-    for (int64_t r = (int64_t)blockIdx.x * teams_per_block + team; r < A.nc; r += teams) {
+    do {
         const int32_t* sup = A.idx + r * n;
         const int32_t c = sup[0];
         // scale sigma = max_j |x_j - x_c|
@@ -137,7 +130,7 @@ __global__ void __launch_bounds__(256) weights_kernel(WeightArgs A, int teams_pe
             for (int j = tid; j < n; j += T) A.w[r * n + j] = 0.0;
             if (tid == 0) A.status[r] = 1;
             team_sync<TW>();
-            continue;
+            break;
         }
         for (int j = tid; j < n; j += T) {
             int32_t id = sup[j];
@@ -318,6 +311,54 @@ __global__ void __launch_bounds__(256) weights_kernel(WeightArgs A, int teams_pe
         for (int j = tid; j < n; j += T) A.w[r * n + j] = bad ? 0.0 : __ddiv_rn(G[j * P + s], scl);
         if (tid == 0) A.status[r] = (int8_t)bad;
         team_sync<TW>();
+    } while (0);
+}
+
+template <int TW>
+__global__ void __launch_bounds__(256) weights_kernel(WeightArgs A, int teams_per_block) {
+    extern __shared__ double wsm[];
+    __shared__ double redv[8];
+    __shared__ long long redk[8];
+    __shared__ int redi[8];
+    __shared__ double bcast[8];   // per-team scalar broadcast (reciprocal pivot, x_j)
+    constexpr int T = 32 * TW;
+    const int tid = threadIdx.x % T;
+    const int team = threadIdx.x / T;
+    double* G = wsm + (size_t)team * ((size_t)A.s * A.pitch + 3 * A.n);
+    double* xi = G + (size_t)A.s * A.pitch;
+    const int64_t teams = (int64_t)gridDim.x * teams_per_block;
+    for (int64_t r = (int64_t)blockIdx.x * teams_per_block + team; r < A.nc; r += teams)
+        weights_one<TW>(A, r, G, xi, tid, team, redv, redk, redi, bcast);
+}
+
+// many calls in one launch: stencil number g of the concatenation belongs to
+// the call dI with off[dI] <= g < off[dI + 1]; a team's shared memory holds
+// the largest system of the launch (team_doubles)
+template <int TW>
+__global__ void __launch_bounds__(256)
+    weights_multi_kernel(const WeightArgs* __restrict__ calls, const int64_t* __restrict__ off,
+                         int ncalls, int teams_per_block, int64_t team_doubles) {
+    extern __shared__ double wsm[];
+    __shared__ double redv[8];
+    __shared__ long long redk[8];
+    __shared__ int redi[8];
+    __shared__ double bcast[8];
+    constexpr int T = 32 * TW;
+    const int tid = threadIdx.x % T;
+    const int team = threadIdx.x / T;
+    double* G = wsm + (size_t)team * (size_t)team_doubles;
+    const int64_t total = off[ncalls];
+    const int64_t teams = (int64_t)gridDim.x * teams_per_block;
+    for (int64_t g = (int64_t)blockIdx.x * teams_per_block + team; g < total; g += teams) {
+        int lo = 0, hi = ncalls - 1;   // last call with off <= g
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (off[mid] <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        const WeightArgs& A = calls[lo];
+        double* xi = G + (size_t)A.s * A.pitch;
+        weights_one<TW>(A, g - off[lo], G, xi, tid, team, redv, redk, redi, bcast);
     }
 }
 
@@ -329,6 +370,19 @@ __global__ void count_bad(const int8_t* st, int64_t nc, unsigned long long* cnt,
             atomicAdd(cnt, 1ull);
             atomicMin(first, (unsigned long long)r);
         }
+}
+
+// singular stencils per call: blockIdx.y = call
+__global__ void count_bad_multi(int8_t* const* status, const int64_t* nc, int ncalls,
+                                unsigned long long* cnt) {
+    for (int c = blockIdx.y; c < ncalls; c += gridDim.y) {
+        const int8_t* st = status[c];
+        unsigned long long k = 0;
+        for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nc[c];
+             r += (int64_t)gridDim.x * blockDim.x)
+            k += st[r] != 0;
+        if (k) atomicAdd(&cnt[c], k);
+    }
 }
 
 // monomial exponents of degree <= m in graded order: degree ascending, then
@@ -442,3 +496,106 @@ extern "C" int rbffd_weights_dir(const double* xyz, int64_t N, int d, const int3
                         stream);
 }
 
+
+extern "C" int rbffd_weights_batch(int ncalls, const double* const* xyz, const int64_t* N,
+                                   const int* d, const int32_t* const* idx, const int64_t* nc,
+                                   const int* n, const int* m, double* const* w,
+                                   int8_t* const* status, int64_t* h_n_bad, void* stream) {
+    clear_error();
+    RBFFD_ARG(ncalls >= 1 && xyz && N && d && idx && nc && n && m && w && status,
+              "rbffd_weights_batch: NULL argument");
+    cudaStream_t s = as_stream(stream);
+    std::vector<WeightArgs> calls(ncalls);
+    for (int c = 0; c < ncalls; ++c) {
+        RBFFD_ARG(d[c] >= 1 && d[c] <= 3 && m[c] >= 0 && m[c] <= 12 && n[c] >= 1 && nc[c] >= 0 &&
+                      N[c] >= 1,
+                  "rbffd_weights_batch: bad sizes of call %d", c);
+        RBFFD_ARG(nc[c] == 0 || (xyz[c] && idx[c] && w[c] && status[c]),
+                  "rbffd_weights_batch: NULL array of call %d", c);
+        WeightArgs& A = calls[c];
+        const int M = graded_monomials(d[c], m[c], A.ex, W_SMAX);
+        RBFFD_ARG(n[c] + M <= W_SMAX, "rbffd_weights_batch: n + M = %d exceeds %d (call %d)",
+                  n[c] + M, W_SMAX, c);
+        A.xyz = xyz[c];
+        A.N = N[c];
+        A.d = d[c];
+        A.idx = idx[c];
+        A.nc = nc[c];
+        A.n = n[c];
+        A.M = M;
+        A.s = n[c] + M;
+        A.pitch = (A.s + 1) | 1;
+        A.w = w[c];
+        A.status = status[c];
+        A.lap_phi = (double)(3 * (d[c] + 1));
+        A.op = 0;
+        A.dirs = nullptr;
+    }
+    const int sms = device_sm_count();
+    // two launches: calls whose systems take one-warp teams (s <= 48), and the rest
+    for (int cls = 0; cls < 2; ++cls) {
+        std::vector<WeightArgs> sel;
+        std::vector<int64_t> off(1, 0);
+        size_t team_doubles = 0;
+        int max_n = 0;
+        for (const WeightArgs& A : calls) {
+            if ((A.s > 48) != (cls == 1) || A.nc == 0) continue;
+            sel.push_back(A);
+            off.push_back(off.back() + A.nc);
+            team_doubles = std::max(team_doubles, (size_t)A.s * A.pitch + 3 * (size_t)A.n);
+            max_n = std::max(max_n, A.n);
+        }
+        if (sel.empty()) continue;
+        Scratch dcalls, doff;
+        RBFFD_CHECK_CUDA(dcalls.alloc(sizeof(WeightArgs) * sel.size(), s));
+        RBFFD_CHECK_CUDA(doff.alloc(sizeof(int64_t) * off.size(), s));
+        RBFFD_CHECK_CUDA(cudaMemcpyAsync(dcalls.p, sel.data(), sizeof(WeightArgs) * sel.size(),
+                                         cudaMemcpyHostToDevice, s));
+        RBFFD_CHECK_CUDA(cudaMemcpyAsync(doff.p, off.data(), sizeof(int64_t) * off.size(),
+                                         cudaMemcpyHostToDevice, s));
+        const size_t per_team = sizeof(double) * team_doubles;
+        int tpb = cls ? 1 : (int)std::min<size_t>(8, (200 * 1024) / per_team);
+        if (tpb < 1) tpb = 1;
+        const size_t smem = per_team * tpb;
+        const int threads = cls ? 128 : 32 * tpb;
+        auto kern = cls ? weights_multi_kernel<4> : weights_multi_kernel<1>;
+        RBFFD_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)std::max<size_t>(smem, 48 * 1024)));
+        int per_sm = 0;
+        RBFFD_CHECK_CUDA(
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+        per_sm = std::max(per_sm, 1);
+        const int64_t want = (off.back() + tpb - 1) / tpb;
+        const int64_t grid = std::min<int64_t>(want, (int64_t)sms * per_sm);
+        kern<<<(unsigned)grid, threads, smem, s>>>(dcalls.as<WeightArgs>(), doff.as<int64_t>(),
+                                                   (int)sel.size(), tpb, (int64_t)team_doubles);
+        RBFFD_CHECK_CUDA(cudaGetLastError());
+    }
+    // singular stencils per call
+    Scratch dst, dnc, dcnt;
+    RBFFD_CHECK_CUDA(dst.alloc(sizeof(int8_t*) * ncalls, s));
+    RBFFD_CHECK_CUDA(dnc.alloc(sizeof(int64_t) * ncalls, s));
+    RBFFD_CHECK_CUDA(dcnt.alloc(sizeof(unsigned long long) * ncalls, s));
+    RBFFD_CHECK_CUDA(cudaMemcpyAsync(dst.p, status, sizeof(int8_t*) * ncalls,
+                                     cudaMemcpyHostToDevice, s));
+    RBFFD_CHECK_CUDA(cudaMemcpyAsync(dnc.p, nc, sizeof(int64_t) * ncalls, cudaMemcpyHostToDevice,
+                                     s));
+    RBFFD_CHECK_CUDA(cudaMemsetAsync(dcnt.p, 0, sizeof(unsigned long long) * ncalls, s));
+    count_bad_multi<<<dim3(16, (unsigned)std::min(ncalls, 65535)), 256, 0, s>>>(
+        dst.as<int8_t*>(), dnc.as<int64_t>(), ncalls, dcnt.as<unsigned long long>());
+    RBFFD_CHECK_CUDA(cudaGetLastError());
+    std::vector<unsigned long long> bad(ncalls);
+    RBFFD_CHECK_CUDA(cudaMemcpyAsync(bad.data(), dcnt.p, sizeof(unsigned long long) * ncalls,
+                                     cudaMemcpyDeviceToHost, s));
+    RBFFD_CHECK_CUDA(cudaStreamSynchronize(s));
+    unsigned long long tot = 0;
+    for (int c = 0; c < ncalls; ++c) {
+        if (h_n_bad) h_n_bad[c] = (int64_t)bad[c];
+        tot += bad[c];
+    }
+    if (tot) {
+        set_error("rbffd_weights_batch: %llu singular stencils", tot);
+        return RBFFD_ERR_SINGULAR;
+    }
+    return RBFFD_OK;
+}

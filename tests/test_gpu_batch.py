@@ -116,3 +116,43 @@ def test_batch_autotune_and_errors(rb, orc):
     batch.destroy()
     for pl in plans:
         pl.destroy()
+
+
+def test_weights_batch_equals_per_domain(rb, orc):
+    """rbffd_weights_batch (all domains in two launches) = rbffd_weights per domain, bit
+    for bit, and = the oracle within 1e-12 per stencil; mixed orders, shapes, a 3D set,
+    a domain with no stencils, and a singular stencil reported for its own domain only."""
+    specs = [(2, 0, 30, 2), (2, 1, 40, 4), (2, 0, 25, 6), (3, 0, 8, 4), (2, 1, 22, 2),
+             (2, 0, 12, 6)]
+    xyzs, idxs, ms, ohs = [], [], [], []
+    for i, (d, shape, Kg, m) in enumerate(specs):
+        xyz, bnd = rb.rbffd_nodes(d, shape, Kg, 0.3, 20 + i)
+        inter = rb.rbffd_interior(bnd)
+        n = gen.stencil_size(d, m)
+        xyzs.append(xyz)
+        idxs.append(rb.rbffd_knn(xyz, inter, n))
+        ms.append(m)
+    # an empty call
+    xyzs.append(xyzs[0])
+    idxs.append(idxs[0][:0])
+    ms.append(2)
+    out = rb.rbffd_weights_batch(xyzs, idxs, ms)
+    for (w, st), xyz, idx, m in zip(out, xyzs, idxs, ms):
+        if idx.shape[0] == 0:
+            assert w.shape[0] == 0
+            continue
+        w1, st1 = rb.rbffd_weights(xyz, idx, m)
+        assert torch.equal(w, w1) and torch.equal(st, st1)
+        rows = np.arange(0, idx.shape[0], max(1, idx.shape[0] // 40))
+        ow, ost = orc.weights(H(xyz), H(idx)[rows], m)
+        assert np.all(ost == 0)
+        assert np.all(np.abs(H(w)[rows] - ow) <= 1e-12 * np.abs(ow).max(axis=1, keepdims=True))
+    # duplicate nodes make one stencil singular: only its domain reports it
+    xyz_bad = xyzs[0].clone()
+    idx_bad = idxs[0].clone()
+    idx_bad[5, 1] = idx_bad[5, 0]
+    res = rb.rbffd_weights_batch([xyzs[1], xyz_bad], [idxs[1], idx_bad], [4, 2], check=False)
+    assert int((res[0][1] != 0).sum()) == 0
+    assert int(res[1][1][5]) == 1 and int((res[1][1] != 0).sum()) == 1
+    with pytest.raises(rb.RbffdError):
+        rb.rbffd_weights_batch([xyz_bad], [idx_bad], [2])

@@ -17,20 +17,30 @@
 
 namespace rbffd {
 
+// Interior columns are placed within windows of TR_WINDOW consecutive slots by
+// decreasing length (ties by slot), so a slice holds columns of nearly equal
+// length and little padding; a window of consecutive Morton slots is a small
+// patch of the domain, so the gathers stay local.  Everything indexed by an
+// interior column or row (lambda, S, the rows of the entries) is held in that
+// placed order; boundary columns keep their slots.
+static constexpr int TR_WINDOW = 256;
+
 struct Transpose {
-    int64_t nslices = 0;      // over all N columns
+    int64_t nslices = 0;      // over all N columns (placed order)
     int64_t* off = nullptr;   // [nslices + 1] element offset of each slice
     int32_t* len = nullptr;   // [nslices] padded length of each slice
-    int32_t* row = nullptr;   // row slot of each entry
+    int32_t* row = nullptr;   // placed position of each entry's row
     double* w = nullptr;      // weight of each entry (0 for padding)
-    double* lam[2] = {nullptr, nullptr};   // [NI]
-    double* S = nullptr;      // [NI] sum of lambda^k
+    int32_t* colof = nullptr; // [N] slot of the column at each placed position
+    int32_t* posof = nullptr; // [N] placed position of each slot
+    double* lam[2] = {nullptr, nullptr};   // [NI] placed order
+    double* S = nullptr;      // [NI] sum of lambda^k, placed order
 };
 
 void free_transpose(rbffd_plan* p) {
     if (!p || !p->tr) return;
     Transpose* t = p->tr;
-    void* b[] = {t->off, t->len, t->row, t->w, t->lam[0], t->lam[1], t->S};
+    void* b[] = {t->off, t->len, t->row, t->w, t->colof, t->posof, t->lam[0], t->lam[1], t->S};
     for (void* x : b)
         if (x) cudaFree(x);
     delete t;
@@ -83,33 +93,65 @@ __global__ void tr_sort(const int32_t* start, int64_t N, int32_t* erow, int32_t*
     }
 }
 
-__global__ void tr_slice_len(const int32_t* start, int64_t N, int64_t nsl, int32_t* len,
-                             int64_t* size) {
+// placement of the interior columns: one warp per window ranks each column
+// by (length descending, slot ascending); boundary columns stay in place
+__global__ void tr_place(const int32_t* start, int64_t NI, int64_t N, int32_t* colof,
+                         int32_t* posof) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t nwin = (NI + TR_WINDOW - 1) / TR_WINDOW;
+    for (int64_t win = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); win < nwin;
+         win += nw) {
+        const int64_t c0 = win * TR_WINDOW, c1 = min(NI, c0 + TR_WINDOW);
+        for (int64_t c = c0 + lane; c < c1; c += 32) {
+            const int lc = start[c + 1] - start[c];
+            int rank = 0;
+            for (int64_t q = c0; q < c1; ++q) {
+                const int lq = start[q + 1] - start[q];
+                rank += (lq > lc) || (lq == lc && q < c);
+            }
+            colof[c0 + rank] = (int32_t)c;
+            posof[c] = (int32_t)(c0 + rank);
+        }
+    }
+    for (int64_t c = NI + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < N;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        colof[c] = (int32_t)c;
+        posof[c] = (int32_t)c;
+    }
+}
+
+__global__ void tr_slice_len(const int32_t* start, const int32_t* colof, int64_t N, int64_t nsl,
+                             int32_t* len, int64_t* size) {
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < nsl;
          s += (int64_t)gridDim.x * blockDim.x) {
         int L = 0;
         for (int l = 0; l < SLICE; ++l) {
-            int64_t c = s * SLICE + l;
-            if (c < N) L = max(L, start[c + 1] - start[c]);
+            int64_t q = s * SLICE + l;
+            if (q < N) {
+                const int32_t c = colof[q];
+                L = max(L, start[c + 1] - start[c]);
+            }
         }
         len[s] = L;
         size[s] = (int64_t)L * SLICE;
     }
 }
 
-__global__ void tr_fill(const int32_t* start, const int32_t* erow, const double* ew, int64_t N,
-                        int64_t nsl, const int64_t* off, const int32_t* len, int32_t* trow,
-                        double* tw) {
+__global__ void tr_fill(const int32_t* start, const int32_t* erow, const double* ew,
+                        const int32_t* colof, const int32_t* posof, int64_t N, int64_t nsl,
+                        const int64_t* off, const int32_t* len, int32_t* trow, double* tw) {
     const int64_t total = nsl * SLICE;
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < total;
-         c += (int64_t)gridDim.x * blockDim.x) {
-        int64_t s = c / SLICE, l = c % SLICE;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        int64_t s = q / SLICE, l = q % SLICE;
         int L = len[s];
-        int b = c < N ? start[c] : 0, e = c < N ? start[c + 1] : 0;
+        const int32_t c = q < N ? colof[q] : 0;
+        int b = q < N ? start[c] : 0, e = q < N ? start[c + 1] : 0;
         for (int j = 0; j < L; ++j) {
             int64_t o = off[s] + (int64_t)j * SLICE + l;
             if (b + j < e) {
-                trow[o] = erow[b + j];
+                trow[o] = posof[erow[b + j]];
                 tw[o] = ew[b + j];
             } else {
                 trow[o] = 0;
@@ -227,15 +269,25 @@ __global__ void adj_gather(const double* src, const int32_t* row_of_slot, int64_
         dst[p] = src[row_of_slot[p]];
 }
 
+// lambda^K (caller's interior-list order) into the placed order
+__global__ void adj_gather_placed(const double* src, const int32_t* row_of_slot,
+                                  const int32_t* colof, int64_t NI, double* dst) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < NI;
+         q += (int64_t)gridDim.x * blockDim.x)
+        dst[q] = src[row_of_slot[colof[q]]];
+}
+
+// S and lambda^0 (placed order) out to the caller's order
 __global__ void adj_outputs(const double* S, const double* lam, const int32_t* row_of_slot,
-                            const int32_t* perm, int64_t NI, double dt, double* grad_f,
-                            double* grad_g, double* lam0) {
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < NI;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        int32_t r = row_of_slot[p];
-        grad_f[r] = __dmul_rn(-dt, S[p]);
-        grad_g[perm[p]] = 0.0;
-        if (lam0) lam0[r] = lam[p];
+                            const int32_t* colof, const int32_t* perm, int64_t NI, double dt,
+                            double* grad_f, double* grad_g, double* lam0) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < NI;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = colof[q];
+        const int32_t r = row_of_slot[c];
+        grad_f[r] = __dmul_rn(-dt, S[q]);
+        grad_g[perm[c]] = 0.0;
+        if (lam0) lam0[r] = lam[q];
     }
 }
 
@@ -280,12 +332,13 @@ replay_step(const double* __restrict__ w64, const int32_t* __restrict__ col,
 // G[s][j][lane] = fma(lambda_p, u^k[col], G[s][j][lane])
 __global__ void __launch_bounds__(256, 4)
 wgrad_accum(const int32_t* __restrict__ col, const double* __restrict__ lam,
-            const double* __restrict__ uk, double* __restrict__ G, int64_t NI, int n) {
+            const int32_t* __restrict__ posof, const double* __restrict__ uk,
+            double* __restrict__ G, int64_t NI, int n) {
     constexpr int CH = 8;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < NI;
          p += (int64_t)gridDim.x * blockDim.x) {
         const int64_t base = (p / SLICE) * (int64_t)n * SLICE + (p % SLICE);
-        const double lp = lam[p];
+        const double lp = lam[posof[p]];   // lambda is held in the placed order
         for (int j0 = 0; j0 < n; j0 += CH) {
             int32_t c[CH];
             double gv[CH], uv[CH];
@@ -356,8 +409,11 @@ static int build_transpose(rbffd_plan* p, cudaStream_t s) {
                                            ekey.as<int32_t>(), ew.as<double>());
         tr_sort<<<sms * 8, 256, 0, s>>>(start.as<int32_t>(), N, erow.as<int32_t>(),
                                         ekey.as<int32_t>(), ew.as<double>());
-        tr_slice_len<<<sms * 4, 256, 0, s>>>(start.as<int32_t>(), N, t->nslices, t->len,
-                                             size.as<int64_t>());
+        if ((e = cudaMalloc((void**)&t->colof, sizeof(int32_t) * N))) break;
+        if ((e = cudaMalloc((void**)&t->posof, sizeof(int32_t) * N))) break;
+        tr_place<<<sms * 8, 256, 0, s>>>(start.as<int32_t>(), NI, N, t->colof, t->posof);
+        tr_slice_len<<<sms * 4, 256, 0, s>>>(start.as<int32_t>(), t->colof, N, t->nslices,
+                                             t->len, size.as<int64_t>());
         scan64_single<<<1, 256, 0, s>>>(size.as<int64_t>(), t->nslices, t->off);
         if ((e = cudaGetLastError())) break;
         if ((e = cudaMemcpyAsync(&total, t->off + t->nslices, sizeof(int64_t),
@@ -370,7 +426,8 @@ static int build_transpose(rbffd_plan* p, cudaStream_t s) {
         if ((e = cudaMalloc((void**)&t->lam[1], sizeof(double) * NI))) break;
         if ((e = cudaMalloc((void**)&t->S, sizeof(double) * NI))) break;
         tr_fill<<<sms * 8, 256, 0, s>>>(start.as<int32_t>(), erow.as<int32_t>(), ew.as<double>(),
-                                        N, t->nslices, t->off, t->len, t->row, t->w);
+                                        t->colof, t->posof, N, t->nslices, t->off, t->len, t->row,
+                                        t->w);
         e = cudaGetLastError();
     } while (0);
     p->tr = t;
@@ -397,7 +454,7 @@ extern "C" int rbffd_adjoint(rbffd_plan* p, const double* lamK, int64_t K, doubl
     Transpose& T = *p->tr;
     const int sms = device_sm_count();
     const unsigned G = (unsigned)sms * 8;
-    adj_gather<<<G, 256, 0, s>>>(lamK, p->row_of_slot, p->NI, T.lam[0]);
+    adj_gather_placed<<<G, 256, 0, s>>>(lamK, p->row_of_slot, T.colof, p->NI, T.lam[0]);
     RBFFD_CHECK_CUDA(cudaMemsetAsync(T.S, 0, sizeof(double) * p->NI, s));
     const int64_t nsl_int = (p->NI + SLICE - 1) / SLICE;
     const unsigned grid = (unsigned)std::max<int64_t>(1, (nsl_int + 7) / 8);
@@ -405,7 +462,8 @@ extern "C" int rbffd_adjoint(rbffd_plan* p, const double* lamK, int64_t K, doubl
         adjoint_step<<<grid, 256, 0, s>>>(T, p->NI, dt, T.lam[k & 1], T.lam[(k + 1) & 1], T.S);
     RBFFD_CHECK_CUDA(cudaGetLastError());
     adjoint_grad_g<<<G, 256, 0, s>>>(T, p->NI, p->N, dt, T.S, p->perm, grad_g);
-    adj_outputs<<<G, 256, 0, s>>>(T.S, T.lam[K & 1], p->row_of_slot, p->perm, p->NI, dt, grad_f,
+    adj_outputs<<<G, 256, 0, s>>>(T.S, T.lam[K & 1], p->row_of_slot, T.colof, p->perm, p->NI,
+                                  dt, grad_f,
                                   grad_g, lam0);
     RBFFD_CHECK_CUDA(cudaGetLastError());
     return RBFFD_OK;
@@ -435,7 +493,7 @@ extern "C" int rbffd_adjoint_w(rbffd_plan* p, const double* f, const double* ckp
     RBFFD_CHECK_CUDA(cudaMemsetAsync(Gw, 0, sizeof(double) * (size_t)p->nslices * n * SLICE, s));
     // f in slot order for the replays; lambda^K in slot order
     adj_gather<<<G, 256, 0, s>>>(f, p->row_of_slot, NI, p->fs);
-    adj_gather<<<G, 256, 0, s>>>(lamK, p->row_of_slot, NI, T.lam[0]);
+    adj_gather_placed<<<G, 256, 0, s>>>(lamK, p->row_of_slot, T.colof, NI, T.lam[0]);
     RBFFD_CHECK_CUDA(cudaMemsetAsync(T.S, 0, sizeof(double) * NI, s));
     const int64_t nseg = (K + every - 1) / every;
     const int64_t nsl_int = (NI + SLICE - 1) / SLICE;
@@ -449,14 +507,16 @@ extern "C" int rbffd_adjoint_w(rbffd_plan* p, const double* f, const double* ckp
             replay_step<<<G, 256, 0, s>>>(p->w64, p->col, p->fs, U + (k - k0) * N,
                                           U + (k - k0 + 1) * N, NI, N, n, dt);
         for (int64_t k = k1 - 1; k >= k0; --k) {
-            wgrad_accum<<<G, 256, 0, s>>>(p->col, T.lam[cur], U + (k - k0) * N, Gw, NI, n);
+            wgrad_accum<<<G, 256, 0, s>>>(p->col, T.lam[cur], T.posof, U + (k - k0) * N, Gw, NI,
+                                          n);
             adjoint_step<<<agrid, 256, 0, s>>>(T, NI, dt, T.lam[cur], T.lam[cur ^ 1], T.S);
             cur ^= 1;
         }
         RBFFD_CHECK_CUDA(cudaGetLastError());
     }
     adjoint_grad_g<<<G, 256, 0, s>>>(T, NI, N, dt, T.S, p->perm, grad_g);
-    adj_outputs<<<G, 256, 0, s>>>(T.S, T.lam[cur], p->row_of_slot, p->perm, NI, dt, grad_f,
+    adj_outputs<<<G, 256, 0, s>>>(T.S, T.lam[cur], p->row_of_slot, T.colof, p->perm, NI, dt,
+                                  grad_f,
                                   grad_g, lam0);
     wgrad_unpack<<<G, 256, 0, s>>>(Gw, p->row_of_slot, NI, n, dt, grad_w);
     RBFFD_CHECK_CUDA(cudaGetLastError());

@@ -425,6 +425,11 @@ static StepFn pick_step(int n, bool persistent, int minb) {
     switch (minb) {
         case 1: return pick_step_m<MODE, 1>(n, persistent);
         case 3: return pick_step_m<MODE, 3>(n, persistent);
+        case 4:
+            // a fourth register budget (64) only for the FP32 inner sweep, whose
+            // rows need half the registers of the FP64 ones
+            if constexpr (MODE == MODE_INNER32) return pick_step_m<MODE, 4>(n, persistent);
+            else return pick_step_m<MODE, 3>(n, persistent);
         default: return pick_step_m<MODE, 2>(n, persistent);
     }
 }
@@ -912,7 +917,8 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
     float best = 1e30f;
     int bm = 2, bg = 2;
     int st = RBFFD_OK;
-    for (int minb = 1; minb <= N_MINB && st == RBFFD_OK; ++minb) {
+    const int n_minb = mode == MODE_INNER32 ? N_MINB + 1 : N_MINB;
+    for (int minb = 1; minb <= n_minb && st == RBFFD_OK; ++minb) {
         StepFn fn = pick(mode, p->n, persistent, minb);
         for (int per_sm = 1; per_sm <= (persistent ? 1 : 4); ++per_sm) {
             int grid = persistent ? persistent_grid(fn, p->nslices) : grid_for(p, per_sm);

@@ -69,7 +69,7 @@ def _traffic():
             if "=" in line and not line.startswith("#"):
                 k, v = line.split("=", 1)
                 rec[k.strip()] = v.strip()
-        src = os.path.join(ROOT, "paper_2502_12878_gb300", "csrc", "sweep.cu")
+        src = os.path.join(ROOT, "paper_2502_12878_gb300", "csrc", "step.cuh")
         sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
         if rec.get("kernel_source_sha1") == sha:
             return int(rec["traffic_bytes_per_launch"])

@@ -60,7 +60,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
         return obj, r.stderr
 
     srcs = sources()
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(os.cpu_count() or 8, len(srcs))) as ex:
         results = list(ex.map(compile_one, srcs))
     if verbose or ptxas_v:
         for _, err in results:

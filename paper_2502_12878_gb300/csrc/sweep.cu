@@ -29,414 +29,32 @@
 #include <algorithm>
 #include <vector>
 
-#include "plan.cuh"
+#include "step.cuh"
 
 namespace rbffd {
 
-static constexpr int STEP_THREADS = 256;
-static constexpr long long SPIN_LIMIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
-
-// ------------------------------------------------------------- utilities
-__device__ __forceinline__ unsigned long long dbits(double x) {
-    return (unsigned long long)__double_as_longlong(x);
-}
-__device__ __forceinline__ double bitsd(unsigned long long b) {
-    return __longlong_as_double((long long)b);
-}
-
-// block max of a non-negative value (NaN mapped to +Inf by the caller);
-// valid in thread 0
-__device__ __forceinline__ double block_max(double v) {
-    __shared__ double wm[32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) wm[wid] = v;
-    __syncthreads();
-    double m = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, wm[w]);
-    __syncthreads();
-    return m;
-}
-
-// ---------------------------------------------------------- row kernels
-// Streaming loads of the stencil planes (read once per step: evict-first).
-// Ordered asm: the compiler keeps them in program order, so the phases of
-// row_dot below really put 2*CH loads in flight before the first use.
-__device__ __forceinline__ double ld_stream(const double* p) {
-    double v;
-    asm volatile("ld.global.cs.f64 %0, [%1];" : "=d"(v) : "l"(p));
-    return v;
-}
-__device__ __forceinline__ float ld_stream(const float* p) {
-    float v;
-    asm volatile("ld.global.cs.f32 %0, [%1];" : "=f"(v) : "l"(p));
-    return v;
-}
-__device__ __forceinline__ int32_t ld_stream(const int32_t* p) {
-    int32_t v;
-    asm volatile("ld.global.cs.s32 %0, [%1];" : "=r"(v) : "l"(p));
-    return v;
-}
-__device__ __forceinline__ uint32_t ld_stream(const uint16_t* p) {
-    unsigned short v;
-    asm volatile("ld.global.cs.u16 %0, [%1];" : "=h"(v) : "l"(p));
-    return (uint32_t)v;
-}
-// Gather of the iterate.  Within one launch per step the iterate is
-// read-only, so the non-coherent path (L1) is used; a persistent launch
-// rewrites it between steps from other SMs, so it reads through L2 (.cg).
-template <bool COHERENT>
-__device__ __forceinline__ double ld_iter(const double* p) {
-    double v;
-    if (COHERENT) asm volatile("ld.global.cg.f64 %0, [%1];" : "=d"(v) : "l"(p));
-    else asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
-    return v;
-}
-template <bool COHERENT>
-__device__ __forceinline__ float ld_iter(const float* p) {
-    float v;
-    if (COHERENT) asm volatile("ld.global.cg.f32 %0, [%1];" : "=f"(v) : "l"(p));
-    else asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
-    return v;
-}
-
-// compact index: window k = code >> 14 selects one of the slice's four bases
-// (three selects on the integer pipe), plus the 14-bit offset
-__device__ __forceinline__ int32_t decode16(uint32_t v, const int4& b) {
-    const uint32_t k = v >> 14;
-    const int32_t base = (k & 2u) ? ((k & 1u) ? b.w : b.z) : ((k & 1u) ? b.y : b.x);
-    return base + (int32_t)(v & 0x3fffu);
-}
-
-// sum_j w_j u[col_j] as an fma chain from 0, j ascending.  Loads are issued
-// in phases of CH (indices, weights, then the gathers) so each thread keeps
-// 2*CH streaming loads and CH gathers in flight.  I16: the indices come as
-// 16-bit codes against the slice's bases `sb` (same columns, fewer bytes).
-template <int NN, bool COH, bool I16, class T>
-__device__ __forceinline__ T row_dot(const T* __restrict__ w, const void* __restrict__ colp,
-                                     const int4& sb, const T* __restrict__ u, int n) {
-    constexpr int CH = 16;
-    T acc = T(0);
-    const int nn = NN > 0 ? NN : n;
-#pragma unroll
-    for (int j0 = 0; j0 < (NN > 0 ? NN : 1 << 30); j0 += CH) {
-        if (NN == 0 && j0 >= nn) break;
-        int32_t c[CH];
-        T wv[CH], uv[CH];
-#pragma unroll
-        for (int t = 0; t < CH; ++t)
-            if (j0 + t < nn) {
-                if constexpr (I16)
-                    c[t] = (int32_t)ld_stream((const uint16_t*)colp + (j0 + t) * SLICE);
-                else
-                    c[t] = ld_stream((const int32_t*)colp + (j0 + t) * SLICE);
-            }
-#pragma unroll
-        for (int t = 0; t < CH; ++t)
-            if (j0 + t < nn) wv[t] = ld_stream(w + (j0 + t) * SLICE);
-        if constexpr (I16) {
-#pragma unroll
-            for (int t = 0; t < CH; ++t)
-                if (j0 + t < nn) c[t] = decode16((uint32_t)c[t], sb);
-        }
-#pragma unroll
-        for (int t = 0; t < CH; ++t)
-            if (j0 + t < nn) uv[t] = ld_iter<COH>(u + c[t]);
-#pragma unroll
-        for (int t = 0; t < CH; ++t)
-            if (j0 + t < nn) {
-                if constexpr (sizeof(T) == 8) acc = __fma_rn(wv[t], uv[t], acc);
-                else acc = __fmaf_rn(wv[t], uv[t], acc);
-            }
-    }
-    return acc;
-}
-
-// |x| as IEEE bits, NaN mapped to +Inf: integer ops only (keeps the FP64
-// pipe for the multiply-adds)
-__device__ __forceinline__ unsigned long long abs_bits(double x) {
-    unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
-    return b > 0x7ff0000000000000ull ? 0x7ff0000000000000ull : b;
-}
-__device__ __forceinline__ unsigned long long abs_bits(float x) {
-    return abs_bits((double)x);
-}
-
-template <int NN, bool COH = false>
-__device__ __forceinline__ double row_dot64(const double* __restrict__ w,
-                                            const int32_t* __restrict__ col,
-                                            const double* __restrict__ u, int n) {
-    const int4 none = make_int4(0, 0, 0, 0);
-    return row_dot<NN, COH, false, double>(w, col, none, u, n);
-}
-
-enum : int { MODE_SWEEP64 = 0, MODE_INNER32 = 1 };
-
-struct StepArgs {
-    const double* w64;
-    const float* w32;
-    const int32_t* col;
-    const uint16_t* col16;   // compact codes, NULL when the plan keeps int32 only
-    const int4* sbase;       // [nslices] window bases; x < 0: the slice uses col
-    const double* f;      // FP64 sweep: f in slot order
-    float* d32;           // FP32 inner: defect in slot order
-    double* u0;
-    double* u1;
-    float* e0;
-    float* e1;
-    int64_t NI;
-    int64_t nslices;
-    int n;
-};
-
-// one step over the slices owned by this warp (slice0, slice0 + stride, ...);
-// returns this thread's max |r| with NaN -> +Inf
-template <int NN, int MODE, bool COH>
-__device__ __forceinline__ unsigned long long step_rows(const StepArgs& A, int par, double dt,
-                                                        float dt32, int64_t slice0,
-                                                        int64_t stride) {
-    const int lane = threadIdx.x & 31;
-    unsigned long long m = 0;
-    for (int64_t sl = slice0; sl < A.nslices; sl += stride) {
-        const int64_t row = sl * SLICE + lane;
-        const int64_t base = sl * (int64_t)A.n * SLICE + lane;
-        const int4 sb = A.col16 ? __ldg(A.sbase + sl) : make_int4(-1, -1, -1, -1);
-        if (row < A.NI) {
-            if (MODE == MODE_SWEEP64) {
-                const double* uin = par ? A.u1 : A.u0;
-                double* uout = par ? A.u0 : A.u1;
-                // the row's own f and u are issued before the dot product, so
-                // their latency overlaps the stencil loads
-                const double fi = ld_stream(A.f + row);
-                const double ui = ld_iter<COH>(uin + row);
-                double acc;
-                if (sb.x >= 0)
-                    acc = row_dot<NN, COH, true, double>(A.w64 + base, A.col16 + base, sb, uin,
-                                                         A.n);
-                else
-                    acc = row_dot<NN, COH, false, double>(A.w64 + base, A.col + base, sb, uin,
-                                                          A.n);
-                double r = __dsub_rn(acc, fi);
-                uout[row] = __fma_rn(dt, r, ui);
-                m = max(m, abs_bits(r));
-            } else {
-                const float* ein = par ? A.e1 : A.e0;
-                float* eout = par ? A.e0 : A.e1;
-                const float di = ld_stream(A.d32 + row);
-                const float ei = ld_iter<COH>(ein + row);
-                float acc;
-                if (sb.x >= 0)
-                    acc = row_dot<NN, COH, true, float>(A.w32 + base, A.col16 + base, sb, ein,
-                                                        A.n);
-                else
-                    acc = row_dot<NN, COH, false, float>(A.w32 + base, A.col + base, sb, ein,
-                                                         A.n);
-                float rho = __fadd_rn(acc, di);
-                eout[row] = __fmaf_rn(dt32, rho, ei);
-                m = max(m, abs_bits(rho));
-            }
-        }
-    }
-    return m;
-}
-
-// block max of IEEE bits; valid in thread 0
-__device__ __forceinline__ unsigned long long block_max_bits(unsigned long long v) {
-    __shared__ unsigned long long wm[32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) wm[wid] = v;
-    __syncthreads();
-    unsigned long long m = 0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, wm[w]);
-    return m;
-}
-
-// decision after step k with residual R (same rule in both launch modes);
-// returns the new `done` code
-__device__ __forceinline__ int decide(StepCtrl* c, long long k, double R) {
-    if (k == 0) c->res_first = R;
-    c->res_last = R;
-    c->k = k + 1;
-    if (!isfinite(R)) return DONE_NONFINITE;
-    if (R < c->tol) return DONE_CONVERGED;
-    double R0 = (k == 0) ? R : c->res_first;
-    if (R > 1e6 * R0 && R0 > 0.0) return DONE_DIVERGED;
-    if (k + 1 >= c->max_steps) return DONE_CAP;
-    return DONE_RUNNING;
-}
-
-// graph mode: one step per launch, one slice per warp
-template <int NN, int MODE, int MINB>
-__global__ void __launch_bounds__(STEP_THREADS, MINB) step_kernel(StepArgs A, StepCtrl* c) {
-    __shared__ long long s_k;
-    __shared__ int s_skip;
-    __shared__ double s_dt;
-    if (threadIdx.x == 0) {
-        volatile StepCtrl* vc = c;
-        long long k = vc->k;
-        s_k = k;
-        s_skip = (vc->done != DONE_RUNNING) || (k >= vc->max_steps);
-        s_dt = vc->dt;
-    }
-    __syncthreads();
-    if (s_skip) return;
-    const long long k = s_k;
-    const int par = (int)(k & 1);
-    const int64_t warp = (int64_t)blockIdx.x * (STEP_THREADS / 32) + (threadIdx.x >> 5);
-    unsigned long long m = step_rows<NN, MODE, false>(A, par, s_dt, (float)s_dt, warp,
-                                                      (int64_t)gridDim.x * (STEP_THREADS / 32));
-    m = block_max_bits(m);
-    if (threadIdx.x == 0) {
-        const int slot = (int)(k % 3);
-        atomicMax(&c->res[slot], m);
-        __threadfence();
-        unsigned t = atomicAdd(&c->arrive[slot], 1u);
-        if (t == gridDim.x - 1) {
-            __threadfence();
-            double R = bitsd(atomicAdd(&c->res[slot], 0ull));
-            int dn = decide(c, k, R);
-            c->res[slot] = 0ull;
-            c->arrive[slot] = 0u;
-            __threadfence();
-            c->done = dn;
-        }
-    }
-}
-
-// End of step k in the persistent launch: a grid barrier fused with the
-// stop decision.  Each block adds its max |r| and arrives (arrivals are
-// counted from the start of the run, so nothing is reset); the last block to
-// arrive reads the step's max, applies the stop rule, clears the next-but-one
-// residual slot, and publishes ((k + 1) << 4) | decision in one word, which
-// the other blocks poll - so the decision needs no second round trip.  Waits
-// give up after SPIN_LIMIT_CYCLES (decision DONE_TIMEOUT).  Returns the
-// decision in every thread.
-__device__ int step_end(StepCtrl* c, long long k, long long k0, long long kmax,
-                        unsigned long long m) {
-    __shared__ int s_dec;
-    if (threadIdx.x == 0) {
-        atomicMax(&c->res[k % 3], m);
-        __threadfence();   // this block's iterate writes and max before its arrival
-        const unsigned long long target = (unsigned long long)(k - k0 + 1) * gridDim.x;
-        const unsigned long long t = atomicAdd(&c->arrivals, 1ull) + 1ull;
-        int dn;
-        if (t == target) {
-            __threadfence();
-            const double R = bitsd(atomicAdd(&c->res[k % 3], 0ull));
-            volatile StepCtrl* vc = c;
-            if (k == 0) vc->res_first = R;
-            const double R0 = k == 0 ? R : vc->res_first;
-            if (!isfinite(R)) dn = DONE_NONFINITE;
-            else if (R < vc->tol) dn = DONE_CONVERGED;
-            else if (k > 0 && R0 > 0.0 && R > 1e6 * R0) dn = DONE_DIVERGED;
-            else if (k + 1 >= kmax) dn = DONE_CAP;
-            else dn = DONE_RUNNING;
-            vc->res_last = R;
-            vc->k = k + 1;
-            vc->res[(k + 1) % 3] = 0ull;
-            if (dn != DONE_RUNNING) vc->done = dn;
-            __threadfence();
-            atomicExch(&c->sync_word, ((unsigned long long)(k + 1) << 4) | (unsigned long long)dn);
-        } else {
-            volatile unsigned long long* w = &c->sync_word;
-            const long long t0 = clock64();
-            for (;;) {
-                const unsigned long long v = *w;
-                if ((v >> 4) == (unsigned long long)(k + 1)) {
-                    dn = (int)(v & 15ull);
-                    break;
-                }
-                if (clock64() - t0 > SPIN_LIMIT_CYCLES) {
-                    atomicExch(&c->done, DONE_TIMEOUT);
-                    dn = DONE_TIMEOUT;
-                    break;
-                }
-            }
-            __threadfence();   // the other blocks' iterate writes before this block reads
-        }
-        s_dec = dn;
-    }
-    __syncthreads();
-    return s_dec;
-}
-
-// persistent mode: all steps in one cooperative launch
-template <int NN, int MODE, int MINB>
-__global__ void __launch_bounds__(STEP_THREADS, MINB) persistent_kernel(StepArgs A, StepCtrl* c) {
-    __shared__ long long s_k, s_max;
-    __shared__ double s_dt;
-    if (threadIdx.x == 0) {
-        volatile StepCtrl* vc = c;
-        s_k = vc->k;
-        s_max = vc->max_steps;
-        s_dt = vc->dt;
-    }
-    __syncthreads();
-    const double dt = s_dt;
-    const long long kmax = s_max, k0 = s_k;
-    const int64_t warp = (int64_t)blockIdx.x * (STEP_THREADS / 32) + (threadIdx.x >> 5);
-    const int64_t nw = (int64_t)gridDim.x * (STEP_THREADS / 32);
-    for (long long k = k0; k < kmax; ++k) {
-        unsigned long long m = step_rows<NN, MODE, true>(A, (int)(k & 1), dt, (float)dt, warp, nw);
-        m = block_max_bits(m);
-        if (step_end(c, k, k0, kmax, m) != DONE_RUNNING) return;
-    }
-}
-
-// ------------------------------------------------------ dispatch by n
-typedef void (*StepFn)(StepArgs, StepCtrl*);
-
+// ------------------------------------------------------ dispatch
 // launch shape of a step kernel: the register budget (min resident blocks per
 // SM the compiler must allow: more blocks = fewer registers = fewer loads in
-// flight per thread) and the grid (blocks per SM of the grid-stride sweep)
+// flight per thread) and the grid (blocks per SM of the grid-stride sweep).
+// A fourth budget (64 registers) exists only for the FP32 inner sweep, whose
+// rows need half the registers of the FP64 ones.
 static constexpr int N_MINB = 3;
 
-template <int MODE, int MINB>
-static StepFn pick_step_m(int n, bool persistent) {
-#define RBFFD_CASE(NN) \
-    case NN: return persistent ? persistent_kernel<NN, MODE, MINB> : step_kernel<NN, MODE, MINB>;
-    switch (n) {
-        RBFFD_CASE(6)
-        RBFFD_CASE(12)
-        RBFFD_CASE(13)
-        RBFFD_CASE(16)
-        RBFFD_CASE(20)
-        RBFFD_CASE(24)
-        RBFFD_CASE(30)
-        RBFFD_CASE(31)
-        RBFFD_CASE(40)
-        RBFFD_CASE(48)
-        RBFFD_CASE(56)
-        RBFFD_CASE(57)
-        RBFFD_CASE(70)
-        RBFFD_CASE(71)
-        default: return persistent ? persistent_kernel<0, MODE, MINB> : step_kernel<0, MODE, MINB>;
-    }
-#undef RBFFD_CASE
-}
-
-template <int MODE>
-static StepFn pick_step(int n, bool persistent, int minb) {
-    switch (minb) {
-        case 1: return pick_step_m<MODE, 1>(n, persistent);
-        case 3: return pick_step_m<MODE, 3>(n, persistent);
-        case 4:
-            // a fourth register budget (64) only for the FP32 inner sweep, whose
-            // rows need half the registers of the FP64 ones
-            if constexpr (MODE == MODE_INNER32) return pick_step_m<MODE, 4>(n, persistent);
-            else return pick_step_m<MODE, 3>(n, persistent);
-        default: return pick_step_m<MODE, 2>(n, persistent);
-    }
-}
-
 static StepFn pick(int mode, int n, bool persistent, int minb) {
-    return mode == MODE_SWEEP64 ? pick_step<MODE_SWEEP64>(n, persistent, minb)
-                                : pick_step<MODE_INNER32>(n, persistent, minb);
+    if (mode == MODE_SWEEP64) {
+        switch (minb) {
+            case 1: return pick_step_f64_b1(n, persistent);
+            case 2: return pick_step_f64_b2(n, persistent);
+            default: return pick_step_f64_b3(n, persistent);
+        }
+    }
+    switch (minb) {
+        case 1: return pick_step_f32_b1(n, persistent);
+        case 2: return pick_step_f32_b2(n, persistent);
+        case 3: return pick_step_f32_b3(n, persistent);
+        default: return pick_step_f32_b4(n, persistent);
+    }
 }
 
 // ------------------------------------------------------- plan building

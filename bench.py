@@ -741,8 +741,8 @@ def run_stage(args):
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
         return
-    n = gen.stencil_size(D, args.m)
-    xyz, bnd = rb.rbffd_nodes(D, 0, args.Kg, 0.3, SEED, device=dev)
+    n = gen.stencil_size(args.dim, args.m)
+    xyz, bnd = rb.rbffd_nodes(args.dim, 0, args.Kg, 0.3, SEED, device=dev)
     inter = rb.rbffd_interior(bnd)
     idx = rb.rbffd_knn(xyz, inter, n)
     if args.mode == "knn":
@@ -797,6 +797,8 @@ def main():
     ap.add_argument("--m", type=int, default=M, help="monomial order of the workload")
     ap.add_argument("--Kg", type=int, default=KG, help="grid cells per side of the workload")
     ap.add_argument("--sweeps", type=int, default=5, help="sweeps in --mode sweep")
+    ap.add_argument("--dim", type=int, default=D, choices=[2, 3],
+                    help="dimension of the unit square/cube in --mode knn/weights/sweep/...")
     ap.add_argument("--batch-cap", type=int, default=20000, help="step cap per domain (batched256)")
     ap.add_argument("--batch-domains", type=int, default=256, help="domains in --mode batch")
     ap.add_argument("--workload", default="square1M_m4",

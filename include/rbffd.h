@@ -225,9 +225,10 @@ RBFFD_API int rbffd_weights_dir(const double* xyz, int64_t N, int d, const int32
 
 /*
  * rbffd_weights_batch - rbffd_weights for many independent calls (domains) in
- * two launches (calls whose systems take one warp, s = n + M <= 48, and the
- * rest): the stencils of all calls are one index space, each team of warps
- * finding its call by binary search over the calls' stencil counts.  Every
+ * at most three launches, one per team size (calls whose systems s = n + M
+ * are <= 32, <= 48, larger): the stencils of a launch's calls are one index
+ * space, each team finding its call by binary search over the calls'
+ * stencil counts.  Every
  * stencil sees the operations of rbffd_weights, so the results are the same
  * bit for bit.  Host arrays [ncalls]: xyz (device [d][N]), N, d, idx (device
  * [nc][n]), nc, n, m, w (device out [nc][n]), status (device out [nc]);

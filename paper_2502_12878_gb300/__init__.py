@@ -273,7 +273,7 @@ def rbffd_weights(xyz: torch.Tensor, idx: torch.Tensor, m: int, check: bool = Tr
 
 
 def rbffd_weights_batch(xyzs, idxs, ms, check: bool = True):
-    """Weights of many domains in one call (two launches): lists of xyz [d, N], supports
+    """Weights of many domains in one call (one launch per team size): lists of xyz [d, N], supports
     idx [nc, n] and orders m.  Returns a list of (w [nc, n], status [nc])."""
     nd = len(xyzs)
     xyzs = [_dev(x, torch.float64, "xyz") for x in xyzs]

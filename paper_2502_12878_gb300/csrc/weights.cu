@@ -1,9 +1,13 @@
 // rbffd_weights: batched RBF-FD Laplacian weights (Eq. 2-3), phi(r) = r^3
 // augmented with every monomial of degree <= m, solved in FP64.
 //
-// A team of TW warps owns one local system at a time (TW = 1 for s <= 48,
-// several systems per block; TW = 4 above, one system per block, so large
-// systems still give every SM sub-partition warps).  The (n+M) x (n+M+1)
+// A team of TS threads owns one local system at a time: half a warp for
+// s <= 32 (two systems per warp, so the team-scalar FP64 work, one reciprocal
+// and one quotient per pivot, is shared by two systems: a warp-wide FP64
+// instruction costs the same pipe time however few lanes it has), one warp
+// for s <= 48, five warps above: a pivot warp that runs the serial pivot
+// chain one step ahead and four warps (one per SM sub-partition) that do
+// the trailing update.  The (n+M) x (n+M+1)
 // augmented matrix lives in shared memory (odd row pitch: column walks hit
 // distinct banks).  The team assembles it (the symmetric r^3 block from its
 // upper triangle), eliminates with partial pivoting, and back-substitutes by
@@ -46,56 +50,78 @@ __device__ __forceinline__ double powi(double x, int e) {
     return p;
 }
 
-template <int TW>
-__device__ __forceinline__ void team_sync() {
-    if (TW == 1) __syncwarp();
-    else __syncthreads();
+// A team is TS threads: half a warp (two systems per warp), one warp, or four
+// warps.  Lanes of a sub-warp team synchronise and shuffle under their own
+// mask only, so the two halves of a warp may diverge freely; while they run
+// in step, the team-scalar work (reciprocal pivot, back-substitution
+// quotient) is one instruction for both systems.
+template <int TS>
+__device__ __forceinline__ unsigned team_mask() {
+    if constexpr (TS >= 32) return 0xffffffffu;
+    else return ((1u << TS) - 1u) << ((threadIdx.x & 31) & ~(TS - 1));
 }
 
-// team-wide max of a double / argmax (value, lowest index on ties)
-template <int TW>
+// barrier of one team: the team's lanes of a warp, or a named barrier (one
+// per team of a block, id 1 + team) over the team's whole warps
+template <int TS>
+__device__ __forceinline__ void team_sync() {
+    if constexpr (TS <= 32) {
+        __syncwarp(team_mask<TS>());
+    } else {
+        const int id = 1 + (int)threadIdx.x / TS;
+        asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(TS) : "memory");
+    }
+}
+
+// team-wide max of a double
+template <int TS>
 __device__ __forceinline__ double team_max(double v, double* red) {
+    const unsigned mask = team_mask<TS>();
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (TW == 1) return v;
+    for (int o = (TS < 32 ? TS : 32) / 2; o > 0; o >>= 1)
+        v = fmax(v, __shfl_xor_sync(mask, v, o));
+    if constexpr (TS <= 32) return v;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int w0 = (int)(threadIdx.x / TS) * (TS / 32);   // the team's first warp
     if (lane == 0) red[wid] = v;
-    __syncthreads();
-    double m = red[0];
-    for (int q = 1; q < TW; ++q) m = fmax(m, red[q]);
-    __syncthreads();
+    team_sync<TS>();
+    double m = red[w0];
+    for (int q = 1; q < TS / 32; ++q) m = fmax(m, red[w0 + q]);
+    team_sync<TS>();
     return m;
 }
 
 // argmax of |value| as IEEE bits (non-negative doubles order like integers;
 // NaN is mapped to -1 by the caller and never wins); ties -> lower index.
 // Integer compares keep the FP64 pipe for the elimination's multiply-adds.
-template <int TW>
+template <int TS>
 __device__ __forceinline__ void team_argmax(long long& bv, int& bi, long long* redv, int* redi) {
+    const unsigned mask = team_mask<TS>();
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
-        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    for (int o = (TS < 32 ? TS : 32) / 2; o > 0; o >>= 1) {
+        long long ov = __shfl_xor_sync(mask, bv, o);
+        int oi = __shfl_xor_sync(mask, bi, o);
         if (ov > bv || (ov == bv && oi < bi)) {
             bv = ov;
             bi = oi;
         }
     }
-    if (TW == 1) return;
+    if constexpr (TS <= 32) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int w0 = (int)(threadIdx.x / TS) * (TS / 32);
     if (lane == 0) {
         redv[wid] = bv;
         redi[wid] = bi;
     }
-    __syncthreads();
-    bv = redv[0];
-    bi = redi[0];
-    for (int q = 1; q < TW; ++q)
-        if (redv[q] > bv || (redv[q] == bv && redi[q] < bi)) {
-            bv = redv[q];
-            bi = redi[q];
+    team_sync<TS>();
+    bv = redv[w0];
+    bi = redi[w0];
+    for (int q = 1; q < TS / 32; ++q)
+        if (redv[w0 + q] > bv || (redv[w0 + q] == bv && redi[w0 + q] < bi)) {
+            bv = redv[w0 + q];
+            bi = redi[w0 + q];
         }
-    __syncthreads();
+    team_sync<TS>();
 }
 
 __device__ __forceinline__ long long abs_key(double x) {
@@ -104,11 +130,11 @@ __device__ __forceinline__ long long abs_key(double x) {
 }
 
 // the weights of stencil r of one call (all of the team's threads)
-template <int TW>
+template <int TS, bool PW>
 __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, double* G, double* xi,
                                             int tid, int team, double* redv, long long* redk,
-                                            int* redi, double* bcast) {
-    constexpr int T = 32 * TW;
+                                            int* redi, double* bcast, int* spiv) {
+    constexpr int T = TS;
     const int n = A.n, M = A.M, s = A.s, P = A.pitch, d = A.d;
     do {
         const int32_t* sup = A.idx + r * n;
@@ -125,11 +151,11 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
             }
             sig = fmax(sig, __dsqrt_rn(s2));
         }
-        sig = team_max<TW>(sig, redv);
+        sig = team_max<TS>(sig, redv);
         if (!(sig > 0.0)) {
             for (int j = tid; j < n; j += T) A.w[r * n + j] = 0.0;
             if (tid == 0) A.status[r] = 1;
-            team_sync<TW>();
+            team_sync<TS>();
             break;
         }
         for (int j = tid; j < n; j += T) {
@@ -139,7 +165,7 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
                 xi[3 * j + a] = __ddiv_rn(t, sig);
             }
         }
-        team_sync<TW>();
+        team_sync<TS>();
         // assemble [[A P] [P^T 0]] | rhs; A from its strict upper triangle
         // (pairs j < k enumerated row by row), diagonal 0
         {
@@ -214,7 +240,7 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
             }
             G[(n + al) * P + s] = v;
         }
-        team_sync<TW>();
+        team_sync<TS>();
         // scale of the assembled matrix for the relative pivot test (max |entry|
         // over IEEE bits; NaN entries ignored)
         long long gk = 0;
@@ -226,7 +252,7 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
         {
             long long bk = gk;
             int bi_dummy = 0;
-            team_argmax<TW>(bk, bi_dummy, redk, redi);
+            team_argmax<TS>(bk, bi_dummy, redk, redi);
             gkb = bk;
         }
         const double gmax = __longlong_as_double(gkb < 0 ? 0ll : gkb);
@@ -234,57 +260,177 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
 
         // elimination with partial pivoting
         int bad = 0;
-        for (int k = 0; k < s; ++k) {
-            // pivot: the first row of largest |a_ik| (NaN entries never win;
-            // a NaN on the diagonal leaves no usable pivot)
-            const bool diag_nan = isnan(G[k * P + k]);
-            long long bk = -2;
-            int bi = s;
-            for (int i = k + tid; i < s; i += T) {
-                long long v = abs_key(G[i * P + k]);
-                if (v > bk) {
-                    bk = v;
-                    bi = i;
+        if constexpr (!PW) {
+            for (int k = 0; k < s; ++k) {
+                // pivot: the first row of largest |a_ik| (NaN entries never win;
+                // a NaN on the diagonal leaves no usable pivot)
+                const bool diag_nan = isnan(G[k * P + k]);
+                long long bk = -2;
+                int bi = s;
+                for (int i = k + tid; i < s; i += T) {
+                    long long v = abs_key(G[i * P + k]);
+                    if (v > bk) {
+                        bk = v;
+                        bi = i;
+                    }
                 }
-            }
-            team_argmax<TW>(bk, bi, redk, redi);
-            const double bv = bk < 0 ? -1.0 : __longlong_as_double(bk);
-            if (diag_nan || !(bv > tiny) || !(bv > 1e-300) || isinf(bv)) {
-                bad = 1;
-                break;
-            }
-            // reciprocal pivot by one warp of the team, broadcast after the swap
-            if ((tid >> 5) == 0) {
-                const double t = __drcp_rn(G[bi * P + k]);
-                if (tid == 0) bcast[team] = t;
-            }
-            if (bi != k)
-                for (int j = k + tid; j <= s; j += T) {
-                    double t = G[k * P + j];
-                    G[k * P + j] = G[bi * P + j];
-                    G[bi * P + j] = t;
+                team_argmax<TS>(bk, bi, redk, redi);
+                const double bv = bk < 0 ? -1.0 : __longlong_as_double(bk);
+                if (diag_nan || !(bv > tiny) || !(bv > 1e-300) || isinf(bv)) {
+                    bad = 1;
+                    break;
                 }
-            team_sync<TW>();
-            const double rp = bcast[team];
-            for (int i = k + 1 + tid; i < s; i += T) G[i * P + k] = __dmul_rn(G[i * P + k], rp);
-            team_sync<TW>();
-            // trailing update over (row, column) pairs: rows k+1..s-1,
-            // columns k+1..s (the right-hand side included)
-            const int cols = s - k;
-            const int total = (s - k - 1) * cols;
-            const int di = T / cols, dj = T - di * cols;
-            int ii = tid / cols, jj = tid - ii * cols;
-            for (int e = tid; e < total; e += T) {
-                const int i = k + 1 + ii, j = k + 1 + jj;
-                G[i * P + j] = __fma_rn(-G[i * P + k], G[k * P + j], G[i * P + j]);
-                ii += di;
-                jj += dj;
-                if (jj >= cols) {
-                    jj -= cols;
-                    ++ii;
+                // reciprocal pivot by one warp of the team, broadcast after the swap
+                if ((tid >> 5) == 0) {
+                    const double t = __drcp_rn(G[bi * P + k]);
+                    if (tid == 0) bcast[team] = t;
                 }
+                if (bi != k)
+                    for (int j = k + tid; j <= s; j += T) {
+                        double t = G[k * P + j];
+                        G[k * P + j] = G[bi * P + j];
+                        G[bi * P + j] = t;
+                    }
+                team_sync<TS>();
+                const double rp = bcast[team];
+                for (int i = k + 1 + tid; i < s; i += T) G[i * P + k] = __dmul_rn(G[i * P + k], rp);
+                team_sync<TS>();
+                // trailing update over (row, column) pairs: rows k+1..s-1,
+                // columns k+1..s (the right-hand side included); two pairs per
+                // iteration, both loaded before either is stored (they are distinct
+                // elements, and column k and row k are only read here)
+                const int cols = s - k;
+                const int total = (s - k - 1) * cols;
+                const int di = T / cols, dj = T - di * cols;
+                int ii = tid / cols, jj = tid - ii * cols;
+                int e = tid;
+                for (; e + T < total; e += 2 * T) {
+                    int ib = ii + di, jb = jj + dj;
+                    if (jb >= cols) {
+                        jb -= cols;
+                        ++ib;
+                    }
+                    const int ra = (k + 1 + ii) * P, ca = k + 1 + jj;
+                    const int rb = (k + 1 + ib) * P, cb = k + 1 + jb;
+                    const double la = G[ra + k], ua = G[k * P + ca], ga = G[ra + ca];
+                    const double lb = G[rb + k], ub = G[k * P + cb], gb = G[rb + cb];
+                    G[ra + ca] = __fma_rn(-la, ua, ga);
+                    G[rb + cb] = __fma_rn(-lb, ub, gb);
+                    ii = ib + di;
+                    jj = jb + dj;
+                    if (jj >= cols) {
+                        jj -= cols;
+                        ++ii;
+                    }
+                }
+                if (e < total) {
+                    const int ra = (k + 1 + ii) * P, ca = k + 1 + jj;
+                    G[ra + ca] = __fma_rn(-G[ra + k], G[k * P + ca], G[ra + ca]);
+                }
+                team_sync<TS>();
             }
-            team_sync<TW>();
+        } else {
+            // The team's first warp is the pivot warp.  At step k it updates
+            // column k+1 (rows k+1..s-1) and at once finds the pivot of step
+            // k+1 and its reciprocal, while the other warps update columns
+            // k+2..s: the serial pivot chain overlaps the trailing update.
+            // Every element still sees the same operations in the same order.
+            const int lane = tid & 31;
+            const bool pw = tid < 32;
+            constexpr int UT = TS - 32;   // update threads
+            const int ut = tid - 32;
+            // pivot of column c over rows c..s-1 (pivot warp; result in
+            // spiv[team] = row | bad << 16 and bcast[team] = reciprocal)
+            auto pivot = [&](int c) {
+                const bool diag_nan = isnan(G[c * P + c]);
+                long long bk = -2;
+                int bi = s;
+                for (int i = c + lane; i < s; i += 32) {
+                    long long v = abs_key(G[i * P + c]);
+                    if (v > bk) {
+                        bk = v;
+                        bi = i;
+                    }
+                }
+                team_argmax<32>(bk, bi, redk, redi);
+                const double bv = bk < 0 ? -1.0 : __longlong_as_double(bk);
+                const int nogo = diag_nan || !(bv > tiny) || !(bv > 1e-300) || isinf(bv);
+                const double t = nogo ? 0.0 : __drcp_rn(G[bi * P + c]);
+                if (lane == 0) {
+                    spiv[team] = bi | (nogo << 16);
+                    bcast[team] = t;
+                }
+            };
+            if (pw) pivot(0);
+            team_sync<TS>();
+            for (int k = 0; k < s; ++k) {
+                const int pv = spiv[team];
+                const double rp = bcast[team];
+                if (pv >> 16) {
+                    bad = 1;
+                    break;
+                }
+                const int bi = pv & 0xffff;
+                // row swap (columns k+1..s) and the multipliers of column k;
+                // the thread of row bi also moves the pivot into row k
+                if (bi != k)
+                    for (int j = k + 1 + tid; j <= s; j += TS) {
+                        double t = G[k * P + j];
+                        G[k * P + j] = G[bi * P + j];
+                        G[bi * P + j] = t;
+                    }
+                for (int i = k + 1 + tid; i < s; i += TS) {
+                    if (i == bi) {
+                        const double a = G[k * P + k];
+                        G[k * P + k] = G[bi * P + k];
+                        G[bi * P + k] = __dmul_rn(a, rp);
+                    } else {
+                        G[i * P + k] = __dmul_rn(G[i * P + k], rp);
+                    }
+                }
+                team_sync<TS>();
+                if (k + 1 < s) {
+                    if (pw) {
+                        const double ukc = G[k * P + k + 1];
+                        for (int i = k + 1 + lane; i < s; i += 32)
+                            G[i * P + k + 1] = __fma_rn(-G[i * P + k], ukc, G[i * P + k + 1]);
+                        __syncwarp();
+                        pivot(k + 1);
+                    } else {
+                        // rows k+1..s-1 x columns k+2..s, flattened, two
+                        // pairs per iteration as above
+                        const int cols = s - k - 1;
+                        const int total = (s - k - 1) * cols;
+                        const int di = UT / cols, dj = UT - di * cols;
+                        int ii = ut / cols, jj = ut - ii * cols;
+                        int e = ut;
+                        for (; e + UT < total; e += 2 * UT) {
+                            int ib = ii + di, jb = jj + dj;
+                            if (jb >= cols) {
+                                jb -= cols;
+                                ++ib;
+                            }
+                            const int ra = (k + 1 + ii) * P, ca = k + 2 + jj;
+                            const int rb = (k + 1 + ib) * P, cb = k + 2 + jb;
+                            const double la = G[ra + k], ua = G[k * P + ca], ga = G[ra + ca];
+                            const double lb = G[rb + k], ub = G[k * P + cb], gb = G[rb + cb];
+                            G[ra + ca] = __fma_rn(-la, ua, ga);
+                            G[rb + cb] = __fma_rn(-lb, ub, gb);
+                            ii = ib + di;
+                            jj = jb + dj;
+                            if (jj >= cols) {
+                                jj -= cols;
+                                ++ii;
+                            }
+                        }
+                        if (e < total) {
+                            const int ra = (k + 1 + ii) * P, ca = k + 2 + jj;
+                            G[ra + ca] = __fma_rn(-G[ra + k], G[k * P + ca], G[ra + ca]);
+                        }
+                    }
+                }
+                team_sync<TS>();
+            }
         }
         if (!bad) {
             // back substitution by columns; x_j overwrites the rhs entry of row j
@@ -293,7 +439,7 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
                     const double t = __ddiv_rn(G[j * P + s], G[j * P + j]);
                     if (tid == 0) bcast[team] = t;
                 }
-                team_sync<TW>();
+                team_sync<TS>();
                 const double xj = bcast[team];
                 if (!isfinite(xj)) {
                     bad = 1;
@@ -301,40 +447,40 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
                 }
                 for (int i = tid; i < j; i += T)
                     G[i * P + s] = __fma_rn(-G[i * P + j], xj, G[i * P + s]);
-                team_sync<TW>();
+                team_sync<TS>();
                 if (tid == 0) G[j * P + s] = xj;
             }
-            team_sync<TW>();
+            team_sync<TS>();
         }
         // the Laplacian scales as 1/sigma^2, a first derivative as 1/sigma
         const double scl = A.op == 0 ? __dmul_rn(sig, sig) : sig;
         for (int j = tid; j < n; j += T) A.w[r * n + j] = bad ? 0.0 : __ddiv_rn(G[j * P + s], scl);
         if (tid == 0) A.status[r] = (int8_t)bad;
-        team_sync<TW>();
+        team_sync<TS>();
     } while (0);
 }
 
-template <int TW>
+template <int TS, bool PW>
 __global__ void __launch_bounds__(256) weights_kernel(WeightArgs A, int teams_per_block) {
     extern __shared__ double wsm[];
     __shared__ double redv[8];
     __shared__ long long redk[8];
     __shared__ int redi[8];
-    __shared__ double bcast[8];   // per-team scalar broadcast (reciprocal pivot, x_j)
-    constexpr int T = 32 * TW;
-    const int tid = threadIdx.x % T;
-    const int team = threadIdx.x / T;
+    __shared__ double bcast[16];   // per-team scalar broadcast (reciprocal pivot, x_j)
+    __shared__ int spiv[16];       // per-team pivot row (pivot-warp teams)
+    const int tid = threadIdx.x % TS;
+    const int team = threadIdx.x / TS;
     double* G = wsm + (size_t)team * ((size_t)A.s * A.pitch + 3 * A.n);
     double* xi = G + (size_t)A.s * A.pitch;
     const int64_t teams = (int64_t)gridDim.x * teams_per_block;
     for (int64_t r = (int64_t)blockIdx.x * teams_per_block + team; r < A.nc; r += teams)
-        weights_one<TW>(A, r, G, xi, tid, team, redv, redk, redi, bcast);
+        weights_one<TS, PW>(A, r, G, xi, tid, team, redv, redk, redi, bcast, spiv);
 }
 
 // many calls in one launch: stencil number g of the concatenation belongs to
 // the call dI with off[dI] <= g < off[dI + 1]; a team's shared memory holds
 // the largest system of the launch (team_doubles)
-template <int TW>
+template <int TS, bool PW>
 __global__ void __launch_bounds__(256)
     weights_multi_kernel(const WeightArgs* __restrict__ calls, const int64_t* __restrict__ off,
                          int ncalls, int teams_per_block, int64_t team_doubles) {
@@ -342,10 +488,10 @@ __global__ void __launch_bounds__(256)
     __shared__ double redv[8];
     __shared__ long long redk[8];
     __shared__ int redi[8];
-    __shared__ double bcast[8];
-    constexpr int T = 32 * TW;
-    const int tid = threadIdx.x % T;
-    const int team = threadIdx.x / T;
+    __shared__ double bcast[16];
+    __shared__ int spiv[16];
+    const int tid = threadIdx.x % TS;
+    const int team = threadIdx.x / TS;
     double* G = wsm + (size_t)team * (size_t)team_doubles;
     const int64_t total = off[ncalls];
     const int64_t teams = (int64_t)gridDim.x * teams_per_block;
@@ -358,7 +504,7 @@ __global__ void __launch_bounds__(256)
         }
         const WeightArgs& A = calls[lo];
         double* xi = G + (size_t)A.s * A.pitch;
-        weights_one<TW>(A, g - off[lo], G, xi, tid, team, redv, redk, redi, bcast);
+        weights_one<TS, PW>(A, g - off[lo], G, xi, tid, team, redv, redk, redi, bcast, spiv);
     }
 }
 
@@ -383,6 +529,77 @@ __global__ void count_bad_multi(int8_t* const* status, const int64_t* nc, int nc
             k += st[r] != 0;
         if (k) atomicAdd(&cnt[c], k);
     }
+}
+
+// Launch shape of a weight build whose largest system is s x s (per_team
+// bytes of shared memory per team).  Team size: half a warp up to
+// W_HALF_SMAX, one warp up to 48, else a pivot warp and four update warps.
+// Measured on 1M-stencil builds (all variants give identical bits):
+// half-warp teams are 1.35-1.7x faster than one-warp teams at s = 18-30 but
+// 6 % slower at s = 45 (twelve systems per SM then fill only six warps, too
+// few to hide the shared-memory latency); at s = 45 a pivot warp plus one
+// update warp is 7 % slower than one warp; at s = 84-105 the pivot warp plus
+// four update warps is 12 % faster than four warps without one, which in
+// turn beat two or eight warps by 14-35 %.
+// Teams per block: the count that puts the most teams on an SM.
+static constexpr int W_HALF_SMAX = 32;
+
+static int weight_team_size(int s) { return s <= W_HALF_SMAX ? 16 : (s <= 48 ? 32 : 160); }
+
+typedef void (*WeightKernel)(WeightArgs, int);
+typedef void (*WeightMultiKernel)(const WeightArgs*, const int64_t*, int, int, int64_t);
+
+// the five-warp team has a pivot warp
+static WeightKernel weight_kernel_for(int ts) {
+    if (ts == 16) return weights_kernel<16, false>;
+    if (ts == 32) return weights_kernel<32, false>;
+    return weights_kernel<160, true>;
+}
+static WeightMultiKernel weight_multi_kernel_for(int ts) {
+    if (ts == 16) return weights_multi_kernel<16, false>;
+    if (ts == 32) return weights_multi_kernel<32, false>;
+    return weights_multi_kernel<160, true>;
+}
+
+struct WeightShape {
+    int ts;        // threads per team
+    int tpb;       // teams per block
+    int threads;   // threads per block
+    int per_sm;    // resident blocks per SM
+    size_t smem;   // dynamic shared memory per block
+};
+
+template <class K>
+static cudaError_t pick_weight_shape(K kern, int ts, size_t per_team, WeightShape* out) {
+    WeightShape b{};
+    b.ts = ts;
+    const int max_tpb = std::min(256 / ts, 15);   // named barriers 1..15
+    const int step = ts == 16 ? 2 : 1;             // whole warps
+    int best = -1;
+    for (int tpb = step; tpb <= max_tpb; tpb += step) {
+        const size_t smem = per_team * tpb;
+        if (smem > 227 * 1024) break;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)std::max<size_t>(smem, 48 * 1024));
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tpb * ts, smem);
+        if (e != cudaSuccess) return e;
+        if (per_sm * tpb > best) {
+            best = per_sm * tpb;
+            b.tpb = tpb;
+            b.per_sm = per_sm;
+        }
+    }
+    if (best <= 0) {   // a single team does not fit: let the launch report it
+        b.tpb = step;
+        b.per_sm = 1;
+    }
+    b.threads = b.tpb * ts;
+    b.smem = per_team * b.tpb;
+    *out = b;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)std::max<size_t>(b.smem, 48 * 1024));
 }
 
 // monomial exponents of degree <= m in graded order: degree ascending, then
@@ -443,21 +660,13 @@ static int weights_impl(const double* xyz, int64_t N, int d, const int32_t* idx,
     A.dirs = dirs;
     const size_t per_team = sizeof(double) * ((size_t)A.s * A.pitch + 3 * (size_t)n);
     const int sms = device_sm_count();
-    const bool big = A.s > 48;
-    // small systems: one warp per system, several per block; large: four warps
-    int tpb = big ? 1 : (int)std::min<size_t>(8, (200 * 1024) / per_team);
-    if (tpb < 1) tpb = 1;
-    const size_t smem = per_team * tpb;
-    const int threads = big ? 128 : 32 * tpb;
-    auto kern = big ? weights_kernel<4> : weights_kernel<1>;
-    RBFFD_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)std::max<size_t>(smem, 48 * 1024)));
-    int per_sm = 0;
-    RBFFD_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
-    per_sm = std::max(per_sm, 1);
-    int64_t want = (nc + tpb - 1) / tpb;
-    int64_t grid = std::min<int64_t>(want, (int64_t)sms * per_sm);
-    kern<<<(unsigned)grid, threads, smem, s>>>(A, tpb);
+    WeightShape ws;
+    const int ts = weight_team_size(A.s);
+    WeightKernel kern = weight_kernel_for(ts);
+    RBFFD_CHECK_CUDA(pick_weight_shape(kern, ts, per_team, &ws));
+    int64_t want = (nc + ws.tpb - 1) / ws.tpb;
+    int64_t grid = std::min<int64_t>(want, (int64_t)sms * ws.per_sm);
+    kern<<<(unsigned)grid, ws.threads, ws.smem, s>>>(A, ws.tpb);
     RBFFD_CHECK_CUDA(cudaGetLastError());
     Scratch cnt;
     RBFFD_CHECK_CUDA(cnt.alloc(2 * sizeof(unsigned long long), s));
@@ -532,18 +741,18 @@ extern "C" int rbffd_weights_batch(int ncalls, const double* const* xyz, const i
         A.dirs = nullptr;
     }
     const int sms = device_sm_count();
-    // two launches: calls whose systems take one-warp teams (s <= 48), and the rest
-    for (int cls = 0; cls < 2; ++cls) {
+    // one launch per team size: calls with s <= 32 (half-warp teams), s <= 48
+    // (one warp), and the rest (four warps)
+    for (int cls = 0; cls < 3; ++cls) {
         std::vector<WeightArgs> sel;
         std::vector<int64_t> off(1, 0);
         size_t team_doubles = 0;
-        int max_n = 0;
         for (const WeightArgs& A : calls) {
-            if ((A.s > 48) != (cls == 1) || A.nc == 0) continue;
+            const int c = A.s <= W_HALF_SMAX ? 0 : (A.s <= 48 ? 1 : 2);
+            if (c != cls || A.nc == 0) continue;
             sel.push_back(A);
             off.push_back(off.back() + A.nc);
             team_doubles = std::max(team_doubles, (size_t)A.s * A.pitch + 3 * (size_t)A.n);
-            max_n = std::max(max_n, A.n);
         }
         if (sel.empty()) continue;
         Scratch dcalls, doff;
@@ -554,21 +763,17 @@ extern "C" int rbffd_weights_batch(int ncalls, const double* const* xyz, const i
         RBFFD_CHECK_CUDA(cudaMemcpyAsync(doff.p, off.data(), sizeof(int64_t) * off.size(),
                                          cudaMemcpyHostToDevice, s));
         const size_t per_team = sizeof(double) * team_doubles;
-        int tpb = cls ? 1 : (int)std::min<size_t>(8, (200 * 1024) / per_team);
-        if (tpb < 1) tpb = 1;
-        const size_t smem = per_team * tpb;
-        const int threads = cls ? 128 : 32 * tpb;
-        auto kern = cls ? weights_multi_kernel<4> : weights_multi_kernel<1>;
-        RBFFD_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)std::max<size_t>(smem, 48 * 1024)));
-        int per_sm = 0;
-        RBFFD_CHECK_CUDA(
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
-        per_sm = std::max(per_sm, 1);
-        const int64_t want = (off.back() + tpb - 1) / tpb;
-        const int64_t grid = std::min<int64_t>(want, (int64_t)sms * per_sm);
-        kern<<<(unsigned)grid, threads, smem, s>>>(dcalls.as<WeightArgs>(), doff.as<int64_t>(),
-                                                   (int)sel.size(), tpb, (int64_t)team_doubles);
+        int max_s = 0;
+        for (const WeightArgs& A : sel) max_s = std::max(max_s, A.s);
+        WeightShape ws;
+        const int ts = weight_team_size(max_s);
+        WeightMultiKernel kern = weight_multi_kernel_for(ts);
+        RBFFD_CHECK_CUDA(pick_weight_shape(kern, ts, per_team, &ws));
+        const int64_t want = (off.back() + ws.tpb - 1) / ws.tpb;
+        const int64_t grid = std::min<int64_t>(want, (int64_t)sms * ws.per_sm);
+        kern<<<(unsigned)grid, ws.threads, ws.smem, s>>>(dcalls.as<WeightArgs>(),
+                                                         doff.as<int64_t>(), (int)sel.size(),
+                                                         ws.tpb, (int64_t)team_doubles);
         RBFFD_CHECK_CUDA(cudaGetLastError());
     }
     // singular stencils per call

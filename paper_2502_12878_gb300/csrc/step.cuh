@@ -173,19 +173,21 @@ struct StepArgs {
 };
 
 // FP32 inner sweep: bulk prefetch into L2 (one lane) of the weight and index
-// planes of slice sl, the warp's next one.  Both planes start on 16-byte
-// boundaries and their sizes (4n and 2n or 4n bytes per row, 32 rows) are
-// multiples of 16.  Measured: +10 % for the FP32 sweep (the HBM-latency-bound
-// one); two or three slices ahead gain nothing; the FP64 sweep, which the
-// FP64 pipe binds, does not prefetch (it lost 15 %).
+// planes of slice sl, the warp's next one: the 16-bit code plane when the plan
+// has one (the few slices that keep int32 indices then read theirs from HBM;
+// choosing per slice would wait on the slice's window bases first, which
+// measured 3 % slower).  Both planes start on 16-byte boundaries and their
+// sizes (4n and 2n or 4n bytes per row, 32 rows) are multiples of 16.
+// Measured: +13 % for the FP32 sweep (the HBM-latency-bound one); two or
+// three slices ahead gain nothing; the FP64 sweep, which the FP64 pipe
+// binds, does not prefetch (whole slice or weights alone, it lost 12-15 %).
 __device__ __forceinline__ void prefetch_planes(const StepArgs& A, int64_t sl) {
     if (sl >= A.nslices) return;
     const int64_t nb = sl * (int64_t)A.n * SLICE;
     const unsigned plane = (unsigned)(A.n * SLICE);
-    const int4 sb = A.col16 ? __ldg(A.sbase + sl) : make_int4(-1, -1, -1, -1);
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(A.w32 + nb), "r"(plane * 4u)
                  : "memory");
-    if (sb.x >= 0)
+    if (A.col16)
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(A.col16 + nb),
                      "r"(plane * 2u) : "memory");
     else

@@ -44,10 +44,44 @@ struct WeightArgs {
     const double* dirs;            // [nc][d] unit vectors (op 1)
 };
 
+// x^e by repeated multiplication; the leading 1 * x is exact, so it is skipped
 __device__ __forceinline__ double powi(double x, int e) {
-    double p = 1.0;
-    for (int k = 0; k < e; ++k) p = __dmul_rn(p, x);
+    if (e == 0) return 1.0;
+    double p = x;
+    for (int k = 1; k < e; ++k) p = __dmul_rn(p, x);
     return p;
+}
+
+// b / p rounded to nearest from y = RN(1/p), by Markstein's method (P.
+// Markstein, IBM J. Res. Dev. 34(1), 1990): q0 = RN(b y) lies within 1.5 ulp
+// of b/p; one correction q1 = RN(q0 + r0 y), r0 = b - p q0, leaves it within
+// half an ulp plus a term of order 2^-53 ulp, so q1 is faithful; for a
+// faithful q1 and y = RN(1/p) the exact remainder r1 = b - p q1 gives
+// RN(q1 + r1 y) = RN(b/p).  Every remainder is one fused multiply-add, exact
+// while nothing over- or underflows, so the method runs only for
+// 2^-500 <= |b|, |p| < 2^501 (else the library quotient).  Five FP64
+// instructions against about eight for the library quotient; the reciprocal
+// is the pivot's, computed during the elimination anyway.
+__device__ __forceinline__ double div_by_pivot(double b, double p, double y) {
+    const int eb = (int)((__double_as_longlong(b) >> 52) & 0x7ff);
+    const int ep = (int)((__double_as_longlong(p) >> 52) & 0x7ff);
+    if (eb < 1023 - 500 || eb > 1023 + 500 || ep < 1023 - 500 || ep > 1023 + 500)
+        return __ddiv_rn(b, p);
+    const double q0 = __dmul_rn(b, y);
+    const double r0 = __fma_rn(-q0, p, b);
+    const double q1 = __fma_rn(r0, y, q0);
+    const double r1 = __fma_rn(-q1, p, b);
+    return __fma_rn(r1, y, q1);
+}
+
+// Tests on IEEE bits with integer instructions (FP64 comparisons would occupy
+// the FP64 pipe, which the elimination needs): |x| is NaN / not finite.
+static constexpr long long W_INF_BITS = 0x7ff0000000000000ll;
+__device__ __forceinline__ bool bits_nan(double x) {
+    return (__double_as_longlong(x) & 0x7fffffffffffffffll) > W_INF_BITS;
+}
+__device__ __forceinline__ bool bits_nonfinite(double x) {
+    return (__double_as_longlong(x) & 0x7fffffffffffffffll) >= W_INF_BITS;
 }
 
 // A team is TS threads: half a warp (two systems per warp), one warp, or four
@@ -135,6 +169,7 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
                                             int tid, int team, double* redv, long long* redk,
                                             int* redi, double* bcast, int* spiv) {
     constexpr int T = TS;
+    double* rinv = xi + 3 * A.n;   // [s] reciprocal of each pivot, for the back substitution
     const int n = A.n, M = A.M, s = A.s, P = A.pitch, d = A.d;
     do {
         const int32_t* sup = A.idx + r * n;
@@ -200,9 +235,10 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
         for (int j = tid; j < n; j += T) G[j * P + j] = 0.0;
         for (int e = tid; e < n * M; e += T) {
             int j = e / M, al = e - j * M;
+            // a factor x^0 = 1 multiplies exactly, so it is skipped
             double p = powi(xi[3 * j + 0], A.ex[al][0]);
-            if (d >= 2) p = __dmul_rn(p, powi(xi[3 * j + 1], A.ex[al][1]));
-            if (d >= 3) p = __dmul_rn(p, powi(xi[3 * j + 2], A.ex[al][2]));
+            if (d >= 2 && A.ex[al][1]) p = __dmul_rn(p, powi(xi[3 * j + 1], A.ex[al][1]));
+            if (d >= 3 && A.ex[al][2]) p = __dmul_rn(p, powi(xi[3 * j + 2], A.ex[al][2]));
             G[j * P + n + al] = p;
             G[(n + al) * P + j] = p;
         }
@@ -257,14 +293,18 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
         }
         const double gmax = __longlong_as_double(gkb < 0 ? 0ll : gkb);
         const double tiny = __dmul_rn(1e-13, gmax);
-
+        // the pivot tests on |pivot| as IEEE bits (non-negative doubles order like
+        // their bits): |p| > tiny, |p| > 1e-300 and |p| finite; a key < 0 (no
+        // candidate, or NaN) fails them all
+        const long long key_tiny = __double_as_longlong(tiny);
+        const long long key_min = __double_as_longlong(1e-300);
         // elimination with partial pivoting
         int bad = 0;
         if constexpr (!PW) {
             for (int k = 0; k < s; ++k) {
                 // pivot: the first row of largest |a_ik| (NaN entries never win;
                 // a NaN on the diagonal leaves no usable pivot)
-                const bool diag_nan = isnan(G[k * P + k]);
+                const bool diag_nan = bits_nan(G[k * P + k]);
                 long long bk = -2;
                 int bi = s;
                 for (int i = k + tid; i < s; i += T) {
@@ -275,15 +315,17 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
                     }
                 }
                 team_argmax<TS>(bk, bi, redk, redi);
-                const double bv = bk < 0 ? -1.0 : __longlong_as_double(bk);
-                if (diag_nan || !(bv > tiny) || !(bv > 1e-300) || isinf(bv)) {
+                if (diag_nan || bk <= key_tiny || bk <= key_min || bk == W_INF_BITS) {
                     bad = 1;
                     break;
                 }
                 // reciprocal pivot by one warp of the team, broadcast after the swap
                 if ((tid >> 5) == 0) {
                     const double t = __drcp_rn(G[bi * P + k]);
-                    if (tid == 0) bcast[team] = t;
+                    if (tid == 0) {
+                        bcast[team] = t;
+                        rinv[k] = t;
+                    }
                 }
                 if (bi != k)
                     for (int j = k + tid; j <= s; j += T) {
@@ -342,7 +384,7 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
             // pivot of column c over rows c..s-1 (pivot warp; result in
             // spiv[team] = row | bad << 16 and bcast[team] = reciprocal)
             auto pivot = [&](int c) {
-                const bool diag_nan = isnan(G[c * P + c]);
+                const bool diag_nan = bits_nan(G[c * P + c]);
                 long long bk = -2;
                 int bi = s;
                 for (int i = c + lane; i < s; i += 32) {
@@ -353,12 +395,13 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
                     }
                 }
                 team_argmax<32>(bk, bi, redk, redi);
-                const double bv = bk < 0 ? -1.0 : __longlong_as_double(bk);
-                const int nogo = diag_nan || !(bv > tiny) || !(bv > 1e-300) || isinf(bv);
+                const int nogo =
+                    diag_nan || bk <= key_tiny || bk <= key_min || bk == W_INF_BITS;
                 const double t = nogo ? 0.0 : __drcp_rn(G[bi * P + c]);
                 if (lane == 0) {
                     spiv[team] = bi | (nogo << 16);
                     bcast[team] = t;
+                    rinv[c] = t;
                 }
             };
             if (pw) pivot(0);
@@ -436,12 +479,12 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
             // back substitution by columns; x_j overwrites the rhs entry of row j
             for (int j = s - 1; j >= 0; --j) {
                 if ((tid >> 5) == 0) {   // one warp divides, the team reads the result
-                    const double t = __ddiv_rn(G[j * P + s], G[j * P + j]);
+                    const double t = div_by_pivot(G[j * P + s], G[j * P + j], rinv[j]);
                     if (tid == 0) bcast[team] = t;
                 }
                 team_sync<TS>();
                 const double xj = bcast[team];
-                if (!isfinite(xj)) {
+                if (bits_nonfinite(xj)) {
                     bad = 1;
                     break;
                 }
@@ -470,7 +513,7 @@ __global__ void __launch_bounds__(256) weights_kernel(WeightArgs A, int teams_pe
     __shared__ int spiv[16];       // per-team pivot row (pivot-warp teams)
     const int tid = threadIdx.x % TS;
     const int team = threadIdx.x / TS;
-    double* G = wsm + (size_t)team * ((size_t)A.s * A.pitch + 3 * A.n);
+    double* G = wsm + (size_t)team * ((size_t)A.s * A.pitch + 3 * A.n + A.s);
     double* xi = G + (size_t)A.s * A.pitch;
     const int64_t teams = (int64_t)gridDim.x * teams_per_block;
     for (int64_t r = (int64_t)blockIdx.x * teams_per_block + team; r < A.nc; r += teams)
@@ -658,7 +701,7 @@ static int weights_impl(const double* xyz, int64_t N, int d, const int32_t* idx,
     A.lap_phi = (double)(3 * (d + 1));
     A.op = op;
     A.dirs = dirs;
-    const size_t per_team = sizeof(double) * ((size_t)A.s * A.pitch + 3 * (size_t)n);
+    const size_t per_team = sizeof(double) * ((size_t)A.s * A.pitch + 3 * (size_t)n + A.s);
     const int sms = device_sm_count();
     WeightShape ws;
     const int ts = weight_team_size(A.s);
@@ -752,7 +795,8 @@ extern "C" int rbffd_weights_batch(int ncalls, const double* const* xyz, const i
             if (c != cls || A.nc == 0) continue;
             sel.push_back(A);
             off.push_back(off.back() + A.nc);
-            team_doubles = std::max(team_doubles, (size_t)A.s * A.pitch + 3 * (size_t)A.n);
+            team_doubles =
+                std::max(team_doubles, (size_t)A.s * A.pitch + 3 * (size_t)A.n + (size_t)A.s);
         }
         if (sel.empty()) continue;
         Scratch dcalls, doff;

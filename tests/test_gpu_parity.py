@@ -172,6 +172,29 @@ def test_weights_singular_status(rb, orc):
     assert ei.value.code == rb.RBFFD_ERR_SINGULAR
 
 
+@pytest.mark.parametrize("d,m,Kg", [(2, 2, 20), (2, 4, 20), (2, 6, 18), (3, 4, 8)])
+def test_weights_singular_rows_every_team_size(rb, orc, d, m, Kg):
+    """A duplicated support node makes its stencil singular, for every team shape:
+    half-warp teams (s = 18), one warp (s = 45), pivot warp + four update warps
+    (s = 84, 105).  Status and weights match the oracle row by row; the singular rows
+    sit next to regular ones (same warp or block)."""
+    xyz, bnd = orc.nodes(d, 0, Kg, 0.3, 40 + m)
+    inter = gen.interior_ids(bnd)
+    n = gen.stencil_size(d, m)
+    idx = orc.knn_kdtree(xyz, inter, n)
+    for r in (0, 3, 17, len(inter) - 1):
+        idx[r, 2] = idx[r, 1]
+    ow, ost = orc.weights(xyz, idx, m)
+    w, st = rb.rbffd_weights(T(xyz), T(idx), m, check=False)
+    w, st = H(w), H(st)
+    assert np.array_equal(st, ost)
+    assert all(ost[r] == 1 for r in (0, 3, 17, len(inter) - 1))
+    assert np.all(w[ost != 0] == 0)
+    ok = ost == 0
+    scale = np.abs(ow[ok]).max(axis=1, keepdims=True)
+    assert np.all(np.abs(w[ok] - ow[ok]) <= 1e-12 * scale)
+
+
 # ------------------------------------------------------------------ apply
 def test_apply_parity(rb, orc):
     p = build(orc, 2, 50, 4, seed=31)

@@ -670,8 +670,12 @@ def run_workload(args):
             finals = {}
             pplan = rb.Plan(Q["xyz"], Q["bnd"], Q["inter"], Q["idx"], Q["w"],
                             rb.RBFFD_ORDER_MORTON | rb.RBFFD_LAUNCH_PERSISTENT)
-            for prec in ("fp64", "fp32_dc", "fp64_persistent", "fp32_dc_persistent"):
-                plan = pplan if prec.endswith("_persistent") else Q["plan"]
+            aplan = rb.Plan(Q["xyz"], Q["bnd"], Q["inter"], Q["idx"], Q["w"],
+                            rb.RBFFD_ORDER_MORTON | rb.RBFFD_LAUNCH_AUTO)
+            for prec in ("fp64", "fp32_dc", "fp64_persistent", "fp32_dc_persistent",
+                         "fp64_auto", "fp32_dc_auto"):
+                plan = (pplan if prec.endswith("_persistent")
+                        else aplan if prec.endswith("_auto") else Q["plan"])
                 u = Q["u0"].clone()
                 plan.solve_explicit(Q["f"], u.clone(), Q["dt"], 64, 0.0)   # warm graph/tuner
                 plan.solve_dc(Q["f"], u.clone(), Q["dt"], 0.0, 1, 64, 0.0)
@@ -692,7 +696,12 @@ def run_workload(args):
                 row[prec] = {"seconds": el, "steps": steps, "max_err": err, "mean_abs_err": mean,
                              "reached": err <= target}
                 finals[prec] = u
+                if prec.endswith("_auto"):
+                    shape = plan.stats()[3]
+                    row[prec]["launch"] = ("persistent" if shape[1 if prec.startswith("fp64")
+                                                              else 3] == 0 else "graph")
             pplan.destroy()
+            aplan.destroy()
             row["speedup_fp32_dc"] = row["fp64"]["seconds"] / row["fp32_dc"]["seconds"]
             # each precision in its faster launch mode
             best64 = min(row["fp64"]["seconds"], row["fp64_persistent"]["seconds"])

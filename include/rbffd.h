@@ -58,6 +58,7 @@ extern "C" {
 #define RBFFD_LAUNCH_GRAPH 0       /* one kernel per step, replayed from a CUDA graph */
 #define RBFFD_LAUNCH_PERSISTENT 16 /* one cooperative kernel runs many steps */
 #define RBFFD_PACK_IDX32 32        /* keep int32 neighbour indices only (no 16-bit codes) */
+#define RBFFD_LAUNCH_AUTO 64       /* the autotuner picks graph or persistent per arithmetic */
 
 typedef struct rbffd_plan rbffd_plan;
 
@@ -276,6 +277,11 @@ RBFFD_API int rbffd_error(const double* u, const double* ua, int64_t N, double* 
  * of a slice as 16-bit codes against up to four window bases of 2^14 slots
  * (a slice whose supports need more windows keeps 32-bit indices); the codes
  * name the same neighbours, so the results are the same bit for bit.
+ * Launch mode of the step loops: RBFFD_LAUNCH_GRAPH (default), _PERSISTENT,
+ * or _AUTO, where the first solve of each arithmetic (FP64 sweep, FP32 inner
+ * sweep) times the graph shapes and the persistent launch on the plan's own
+ * stencils and keeps the faster.  A plan with Neumann nodes always replays
+ * graphs.  Every mode gives the same results bit for bit.
  */
 RBFFD_API int rbffd_plan_create(const double* xyz, const uint8_t* is_bnd, int64_t N, int d,
                       const int32_t* interior, const int32_t* idx, const double* w, int64_t NI,
@@ -330,7 +336,8 @@ RBFFD_API int rbffd_solve_explicit(rbffd_plan* plan, const double* f, double* u,
  * events recorded on the caller's stream around the step launches;
  * h_loop_steps, the steps those loops took; h_launches, the kernels the solve
  * launched; h_shape[4], the autotuned launch shape (register budget, blocks
- * per SM) of the FP64 sweep and of the FP32 inner sweep.
+ * per SM; 0 blocks per SM = the persistent launch) of the FP64 sweep and of
+ * the FP32 inner sweep.
  */
 RBFFD_API int rbffd_plan_stats(const rbffd_plan* plan, double* h_loop_ms, int64_t* h_loop_steps,
                                int64_t* h_launches, int* h_shape);

@@ -41,6 +41,7 @@ RBFFD_ORDER_INPUT = 1
 RBFFD_ORDER_RANDOM = 2
 RBFFD_LAUNCH_GRAPH = 0
 RBFFD_LAUNCH_PERSISTENT = 16
+RBFFD_LAUNCH_AUTO = 64
 RBFFD_PACK_IDX32 = 32
 
 EXPORTED = [

@@ -75,6 +75,7 @@ struct rbffd_plan {
     int grid_steps = 0;             // blocks per SM of auxiliary sweeps (defect, power)
     // tuned launch shape per mode (0 FP64 sweep, 1 FP32 inner sweep)
     bool tuned[2] = {false, false};
+    bool persist[2] = {false, false};   // the step loop of each mode runs persistent
     int minb[2] = {2, 2};
     int per_sm[2] = {2, 2};
     float tune_ms[2] = {0.f, 0.f};

@@ -512,99 +512,132 @@ static int ctrl_reset(rbffd_plan* p, double dt, double tol, long long max_steps,
     return RBFFD_OK;
 }
 
+// launch modes the autotuner may choose from: persistent only when asked for
+// (or left to it) and the plan has no Neumann phase, which only graphs replay
+static bool may_persist(const rbffd_plan* p) {
+    return (p->flags & (RBFFD_LAUNCH_PERSISTENT | RBFFD_LAUNCH_AUTO)) != 0 && p->NN == 0;
+}
+static bool may_graph(const rbffd_plan* p) {
+    return !(p->flags & RBFFD_LAUNCH_PERSISTENT) || p->NN > 0;
+}
+
 // Autotuner: time every launch shape of `mode` for a few steps on this plan's
 // own stencils (u / e buffers zeroed; dt = 0 so nothing moves) and keep the
-// fastest.  Candidates: register budget minb in {1, 2, 3} x blocks per SM in
-// {1, 2, 3, 4} (graph mode), or minb alone (persistent mode, whose grid is
-// the resident maximum).  Runs once per plan and mode, on `s`.
+// fastest.  Candidates: register budget minb in {1, 2, 3} (and 4 for the FP32
+// sweep) x blocks per SM in {1, 2, 3, 4} (graph mode, timed as a captured
+// chunk of launches: what solves replay), and minb alone (persistent mode,
+// whose grid is the resident maximum); RBFFD_LAUNCH_AUTO times both modes and
+// keeps the faster.  The candidates are timed in interleaved rounds, one
+// untimed warm-up round first, each keeping its best round: timing them one
+// after another let drift (clocks, caches) favour whichever came last.  Runs
+// once per plan and mode, on `s`.
+struct TuneCand {
+    int minb, per_sm;
+    bool persistent;
+    StepFn fn;
+    int grid;
+    cudaGraphExec_t gx;
+    float ms;
+};
+
 static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
     const int mi = mode == MODE_SWEEP64 ? 0 : 1;
     if (p->tuned[mi]) return RBFFD_OK;
-    const bool persistent = (p->flags & RBFFD_LAUNCH_PERSISTENT) != 0;
     RBFFD_CHECK_CUDA(cudaMemsetAsync(p->u[0], 0, sizeof(double) * p->N, s));
     RBFFD_CHECK_CUDA(cudaMemsetAsync(p->u[1], 0, sizeof(double) * p->N, s));
     RBFFD_CHECK_CUDA(cudaMemsetAsync(p->e[0], 0, sizeof(float) * p->N, s));
     RBFFD_CHECK_CUDA(cudaMemsetAsync(p->e[1], 0, sizeof(float) * p->N, s));
     RBFFD_CHECK_CUDA(cudaMemsetAsync(p->d32, 0, sizeof(float) * p->NI, s));
-    cudaEvent_t e0, e1;
-    RBFFD_CHECK_CUDA(cudaEventCreate(&e0));
-    RBFFD_CHECK_CUDA(cudaEventCreate(&e1));
     StepArgs A = make_args(p);
-    // enough steps to time reliably on small plans, few on large ones
-    const long long reps = std::max<long long>(10, std::min<long long>(60, 40000000 / (p->NI * p->n + 1)));
-    float best = 1e30f;
-    int bm = 2, bg = 2;
-    int st = RBFFD_OK;
+    // enough steps to time reliably on small plans (a step there costs a few
+    // microseconds of mostly latency, so a short trial is noise), few on large ones
+    const long long reps =
+        std::max<long long>(10, std::min<long long>(600, 400000000 / (p->NI * p->n + 1)));
     const int n_minb = mode == MODE_INNER32 ? N_MINB + 1 : N_MINB;
-    for (int minb = 1; minb <= n_minb && st == RBFFD_OK; ++minb) {
-        StepFn fn = pick(mode, p->n, persistent, minb);
-        for (int per_sm = 1; per_sm <= (persistent ? 1 : 4); ++per_sm) {
-            int grid = persistent ? persistent_grid(fn, p->nslices) : grid_for(p, per_sm);
-            // pass 0 warms up; passes 1 and 2 are timed, the faster one counts.  Graph
-            // mode times a captured chunk of launches: exactly what solves replay.
-            float ms = 1e30f;
-            cudaGraphExec_t gx = nullptr;
-            if (!persistent) {
-                cudaStream_t cs;
-                cudaGraph_t gg;
-                cudaError_t ce = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    // candidate c: graph shapes per_sm = c (1..4), then the persistent launch (c = 5)
+    const int c_lo = may_graph(p) ? 1 : 5, c_hi = may_persist(p) ? 5 : 4;
+    std::vector<TuneCand> cands;
+    for (int minb = 1; minb <= n_minb; ++minb)
+        for (int c = c_lo; c <= c_hi; ++c) {
+            TuneCand t;
+            t.minb = minb;
+            t.persistent = c == 5;
+            t.per_sm = t.persistent ? 1 : c;
+            t.fn = pick(mode, p->n, t.persistent, minb);
+            t.grid = t.persistent ? persistent_grid(t.fn, p->nslices) : grid_for(p, t.per_sm);
+            t.gx = nullptr;
+            t.ms = 1e30f;
+            cands.push_back(t);
+        }
+    int st = RBFFD_OK;
+    // capture one chunk of `reps` launches per graph candidate
+    for (TuneCand& t : cands) {
+        if (t.persistent) continue;
+        cudaStream_t cs;
+        cudaGraph_t gg;
+        cudaError_t ce = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (ce == cudaSuccess) {
+            ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            if (ce == cudaSuccess) {
+                for (long long i = 0; i < reps; ++i)
+                    t.fn<<<t.grid, STEP_THREADS, 0, cs>>>(A, p->ctrl);
+                ce = cudaStreamEndCapture(cs, &gg);
                 if (ce == cudaSuccess) {
-                    ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-                    if (ce == cudaSuccess) {
-                        for (long long i = 0; i < reps; ++i)
-                            fn<<<grid, STEP_THREADS, 0, cs>>>(A, p->ctrl);
-                        ce = cudaStreamEndCapture(cs, &gg);
-                        if (ce == cudaSuccess) {
-                            ce = cudaGraphInstantiate(&gx, gg, 0);
-                            cudaGraphDestroy(gg);
-                        }
-                    }
-                    cudaStreamDestroy(cs);
-                }
-                if (ce != cudaSuccess) {
-                    set_error("autotune: capture: %s", cudaGetErrorString(ce));
-                    st = RBFFD_ERR_CUDA;
-                    break;
+                    ce = cudaGraphInstantiate(&t.gx, gg, 0);
+                    cudaGraphDestroy(gg);
                 }
             }
-            for (int pass = 0; pass < 3; ++pass) {
-                if ((st = ctrl_reset(p, 0.0, 0.0, reps, s))) break;
-                cudaEventRecord(e0, s);
-                if (persistent) {
-                    StepCtrl* c = p->ctrl;
-                    void* args[] = {(void*)&A, (void*)&c};
-                    cudaLaunchCooperativeKernel((const void*)fn, dim3(grid), dim3(STEP_THREADS), args,
-                                                0, s);
-                } else {
-                    cudaGraphLaunch(gx, s);
-                }
-                cudaEventRecord(e1, s);
-                cudaError_t e = cudaEventSynchronize(e1);
-                if (e == cudaSuccess) e = cudaGetLastError();
-                if (e != cudaSuccess) {
-                    set_error("autotune: %s", cudaGetErrorString(e));
-                    st = RBFFD_ERR_CUDA;
-                    break;
-                }
-                float t = 0.f;
-                cudaEventElapsedTime(&t, e0, e1);
-                if (pass) ms = std::min(ms, t);
-            }
-            if (gx) cudaGraphExecDestroy(gx);
-            if (st) break;
-            if (ms < best) {
-                best = ms;
-                bm = minb;
-                bg = per_sm;
-            }
+            cudaStreamDestroy(cs);
+        }
+        if (ce != cudaSuccess) {
+            set_error("autotune: capture: %s", cudaGetErrorString(ce));
+            st = RBFFD_ERR_CUDA;
+            break;
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (st == RBFFD_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) {
+        set_error("autotune: event creation failed");
+        st = RBFFD_ERR_CUDA;
+    }
+    // round 0 warms up; rounds 1..3 are timed
+    for (int round = 0; round < 4 && st == RBFFD_OK; ++round) {
+        for (TuneCand& t : cands) {
+            if ((st = ctrl_reset(p, 0.0, 0.0, reps, s))) break;
+            cudaEventRecord(e0, s);
+            if (t.persistent) {
+                StepCtrl* c = p->ctrl;
+                void* args[] = {(void*)&A, (void*)&c};
+                cudaLaunchCooperativeKernel((const void*)t.fn, dim3(t.grid), dim3(STEP_THREADS),
+                                            args, 0, s);
+            } else {
+                cudaGraphLaunch(t.gx, s);
+            }
+            cudaEventRecord(e1, s);
+            cudaError_t e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaGetLastError();
+            if (e != cudaSuccess) {
+                set_error("autotune: %s", cudaGetErrorString(e));
+                st = RBFFD_ERR_CUDA;
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (round) t.ms = std::min(t.ms, ms);
+        }
+    }
+    for (TuneCand& t : cands)
+        if (t.gx) cudaGraphExecDestroy(t.gx);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
     if (st) return st;
-    p->minb[mi] = bm;
-    p->per_sm[mi] = bg;
-    p->tune_ms[mi] = best / (float)reps;
+    const TuneCand* best = &cands[0];
+    for (const TuneCand& t : cands)
+        if (t.ms < best->ms) best = &t;
+    p->minb[mi] = best->minb;
+    p->per_sm[mi] = best->per_sm;
+    p->persist[mi] = best->persistent;
+    p->tune_ms[mi] = best->ms / (float)reps;
     p->tuned[mi] = true;
     return RBFFD_OK;
 }
@@ -648,6 +681,39 @@ static int ensure_graph(rbffd_plan* p, int mode, cudaStream_t s) {
     return RBFFD_OK;
 }
 
+// Tune the launch shape of `mode` and build its graph if the chosen mode
+// replays one; both clobber the iterate buffers, which are saved and restored.
+// Leaves the control block reset for the run.
+static int prepare_mode(rbffd_plan* p, int mode, double dt, double tol, long long max_steps,
+                        cudaStream_t s) {
+    const int mi = mode == MODE_SWEEP64 ? 0 : 1;
+    const bool graph_missing = mode == MODE_SWEEP64 ? !p->graph64 : !p->graph32;
+    if (p->tuned[mi] && (p->persist[mi] || !graph_missing)) return RBFFD_OK;
+    Scratch save;
+    RBFFD_CHECK_CUDA(save.alloc(sizeof(double) * 2 * p->N + sizeof(float) * 2 * p->N, s));
+    double* sv = save.as<double>();
+    float* se = reinterpret_cast<float*>(sv + 2 * p->N);
+    RBFFD_CHECK_CUDA(cudaMemcpyAsync(sv, p->u[0], sizeof(double) * p->N, cudaMemcpyDeviceToDevice, s));
+    RBFFD_CHECK_CUDA(cudaMemcpyAsync(sv + p->N, p->u[1], sizeof(double) * p->N, cudaMemcpyDeviceToDevice, s));
+    RBFFD_CHECK_CUDA(cudaMemcpyAsync(se, p->e[0], sizeof(float) * p->N, cudaMemcpyDeviceToDevice, s));
+    RBFFD_CHECK_CUDA(cudaMemcpyAsync(se + p->N, p->e[1], sizeof(float) * p->N, cudaMemcpyDeviceToDevice, s));
+    Scratch saved32;
+    RBFFD_CHECK_CUDA(saved32.alloc(sizeof(float) * p->NI, s));
+    RBFFD_CHECK_CUDA(cudaMemcpyAsync(saved32.p, p->d32, sizeof(float) * p->NI, cudaMemcpyDeviceToDevice, s));
+    int st = tune_shape(p, mode, s);
+    if (st) return st;
+    if (!p->persist[mi]) {
+        st = ensure_graph(p, mode, s);
+        if (st) return st;
+    }
+    RBFFD_CHECK_CUDA(cudaMemcpyAsync(p->u[0], sv, sizeof(double) * p->N, cudaMemcpyDeviceToDevice, s));
+    RBFFD_CHECK_CUDA(cudaMemcpyAsync(p->u[1], sv + p->N, sizeof(double) * p->N, cudaMemcpyDeviceToDevice, s));
+    RBFFD_CHECK_CUDA(cudaMemcpyAsync(p->e[0], se, sizeof(float) * p->N, cudaMemcpyDeviceToDevice, s));
+    RBFFD_CHECK_CUDA(cudaMemcpyAsync(p->e[1], se + p->N, sizeof(float) * p->N, cudaMemcpyDeviceToDevice, s));
+    RBFFD_CHECK_CUDA(cudaMemcpyAsync(p->d32, saved32.p, sizeof(float) * p->NI, cudaMemcpyDeviceToDevice, s));
+    return ctrl_reset(p, dt, tol, max_steps, s);
+}
+
 // run the step loop of `mode` until the control block says done.
 // Reads back done / k / res_last.
 static int run_steps(rbffd_plan* p, int mode, double dt, double tol, long long max_steps,
@@ -656,33 +722,10 @@ static int run_steps(rbffd_plan* p, int mode, double dt, double tol, long long m
     if (st) return st;
     StepCtrl h;
     if (max_steps > 0) {
-        // the persistent kernel has no Neumann phase: Neumann plans replay graphs
-        bool persistent = (p->flags & RBFFD_LAUNCH_PERSISTENT) != 0 && p->NN == 0;
-        if (persistent) {
-            const int mi = mode == MODE_SWEEP64 ? 0 : 1;
-            if (!p->tuned[mi]) {
-                // the tuner clobbers the iterate buffers: save and restore them
-                Scratch save;
-                RBFFD_CHECK_CUDA(save.alloc(sizeof(double) * 2 * p->N + sizeof(float) * 2 * p->N, s));
-                double* sv = save.as<double>();
-                float* se = reinterpret_cast<float*>(sv + 2 * p->N);
-                RBFFD_CHECK_CUDA(cudaMemcpyAsync(sv, p->u[0], sizeof(double) * p->N, cudaMemcpyDeviceToDevice, s));
-                RBFFD_CHECK_CUDA(cudaMemcpyAsync(sv + p->N, p->u[1], sizeof(double) * p->N, cudaMemcpyDeviceToDevice, s));
-                RBFFD_CHECK_CUDA(cudaMemcpyAsync(se, p->e[0], sizeof(float) * p->N, cudaMemcpyDeviceToDevice, s));
-                RBFFD_CHECK_CUDA(cudaMemcpyAsync(se + p->N, p->e[1], sizeof(float) * p->N, cudaMemcpyDeviceToDevice, s));
-                Scratch saved32;
-                RBFFD_CHECK_CUDA(saved32.alloc(sizeof(float) * p->NI, s));
-                RBFFD_CHECK_CUDA(cudaMemcpyAsync(saved32.p, p->d32, sizeof(float) * p->NI, cudaMemcpyDeviceToDevice, s));
-                st = tune_shape(p, mode, s);
-                if (st) return st;
-                RBFFD_CHECK_CUDA(cudaMemcpyAsync(p->u[0], sv, sizeof(double) * p->N, cudaMemcpyDeviceToDevice, s));
-                RBFFD_CHECK_CUDA(cudaMemcpyAsync(p->u[1], sv + p->N, sizeof(double) * p->N, cudaMemcpyDeviceToDevice, s));
-                RBFFD_CHECK_CUDA(cudaMemcpyAsync(p->e[0], se, sizeof(float) * p->N, cudaMemcpyDeviceToDevice, s));
-                RBFFD_CHECK_CUDA(cudaMemcpyAsync(p->e[1], se + p->N, sizeof(float) * p->N, cudaMemcpyDeviceToDevice, s));
-                RBFFD_CHECK_CUDA(cudaMemcpyAsync(p->d32, saved32.p, sizeof(float) * p->NI, cudaMemcpyDeviceToDevice, s));
-                st = ctrl_reset(p, dt, tol, max_steps, s);
-                if (st) return st;
-            }
+        const int mi = mode == MODE_SWEEP64 ? 0 : 1;
+        st = prepare_mode(p, mode, dt, tol, max_steps, s);
+        if (st) return st;
+        if (p->persist[mi]) {
             StepFn fn = pick(mode, p->n, true, p->minb[mi]);
             int grid = persistent_grid(fn, p->nslices);
             StepArgs A = make_args(p);
@@ -694,28 +737,6 @@ static int run_steps(rbffd_plan* p, int mode, double dt, double tol, long long m
             RBFFD_CHECK_CUDA(cudaEventRecord((cudaEvent_t)p->ev[1], s));
             p->last_launches += 1;
         } else {
-            if (!p->graph64 && mode == MODE_SWEEP64 || !p->graph32 && mode == MODE_INNER32) {
-                Scratch save;
-                RBFFD_CHECK_CUDA(save.alloc(sizeof(double) * 2 * p->N + sizeof(float) * 2 * p->N, s));
-                double* sv = save.as<double>();
-                float* se = reinterpret_cast<float*>(sv + 2 * p->N);
-                RBFFD_CHECK_CUDA(cudaMemcpyAsync(sv, p->u[0], sizeof(double) * p->N, cudaMemcpyDeviceToDevice, s));
-                RBFFD_CHECK_CUDA(cudaMemcpyAsync(sv + p->N, p->u[1], sizeof(double) * p->N, cudaMemcpyDeviceToDevice, s));
-                RBFFD_CHECK_CUDA(cudaMemcpyAsync(se, p->e[0], sizeof(float) * p->N, cudaMemcpyDeviceToDevice, s));
-                RBFFD_CHECK_CUDA(cudaMemcpyAsync(se + p->N, p->e[1], sizeof(float) * p->N, cudaMemcpyDeviceToDevice, s));
-                Scratch saved32;
-                RBFFD_CHECK_CUDA(saved32.alloc(sizeof(float) * p->NI, s));
-                RBFFD_CHECK_CUDA(cudaMemcpyAsync(saved32.p, p->d32, sizeof(float) * p->NI, cudaMemcpyDeviceToDevice, s));
-                st = ensure_graph(p, mode, s);
-                if (st) return st;
-                RBFFD_CHECK_CUDA(cudaMemcpyAsync(p->u[0], sv, sizeof(double) * p->N, cudaMemcpyDeviceToDevice, s));
-                RBFFD_CHECK_CUDA(cudaMemcpyAsync(p->u[1], sv + p->N, sizeof(double) * p->N, cudaMemcpyDeviceToDevice, s));
-                RBFFD_CHECK_CUDA(cudaMemcpyAsync(p->e[0], se, sizeof(float) * p->N, cudaMemcpyDeviceToDevice, s));
-                RBFFD_CHECK_CUDA(cudaMemcpyAsync(p->e[1], se + p->N, sizeof(float) * p->N, cudaMemcpyDeviceToDevice, s));
-                RBFFD_CHECK_CUDA(cudaMemcpyAsync(p->d32, saved32.p, sizeof(float) * p->NI, cudaMemcpyDeviceToDevice, s));
-                st = ctrl_reset(p, dt, tol, max_steps, s);
-                if (st) return st;
-            }
             cudaGraphExec_t ex = (cudaGraphExec_t)(mode == MODE_SWEEP64 ? p->graph64 : p->graph32);
             long long launched = 0;
             // replay chunks; check the device decision every `per_check` chunks
@@ -1176,9 +1197,9 @@ extern "C" int rbffd_plan_stats(const rbffd_plan* p, double* h_loop_ms, int64_t*
     if (h_launches) *h_launches = p->last_launches;
     if (h_shape) {
         h_shape[0] = p->minb[0];
-        h_shape[1] = p->per_sm[0];
+        h_shape[1] = p->persist[0] ? 0 : p->per_sm[0];
         h_shape[2] = p->minb[1];
-        h_shape[3] = p->per_sm[1];
+        h_shape[3] = p->persist[1] ? 0 : p->per_sm[1];
     }
     return RBFFD_OK;
 }
@@ -1241,10 +1262,20 @@ extern "C" int rbffd_plan_set_neumann(rbffd_plan* p, int64_t NN, const int32_t* 
     p->nw = p->ng = p->ng0 = p->uN = nullptr;
     p->NN = 0;
     p->nn = 0;
-    // captured graphs include (or not) the Neumann phase: capture again
+    // captured graphs include (or not) the Neumann phase: capture again; the
+    // launch modes may change with it (plans with Neumann nodes replay
+    // graphs), so the shapes are tuned again too
     if (p->graph64) {
         cudaGraphExecDestroy((cudaGraphExec_t)p->graph64);
         p->graph64 = nullptr;
+    }
+    if (p->graph32) {
+        cudaGraphExecDestroy((cudaGraphExec_t)p->graph32);
+        p->graph32 = nullptr;
+    }
+    for (int mi = 0; mi < 2; ++mi) {
+        p->tuned[mi] = false;
+        p->persist[mi] = false;
     }
     if (NN == 0) return RBFFD_OK;
     cudaError_t e = cudaSuccess;

@@ -77,3 +77,25 @@ def test_mixed_solve_matches_oracle(rb, orc):
     with pytest.raises(rb.RbffdError):
         plan.solve_dc(T(p.f), T(p.u0), dt, 0.0, 1, 10, 0.0)
     plan.destroy()
+
+
+def test_mixed_solve_auto_launch_after_retune(rb, orc):
+    """RBFFD_LAUNCH_AUTO: a solve before the Neumann nodes exist may tune the plan to the
+    persistent launch; setting Neumann nodes tunes again, and the FP64 sweep must then
+    replay graphs (only they run the Neumann update) and match the oracle."""
+    mp = build_mixed(orc, 2, 20, 4, seed=8)
+    p = mp.base
+    plan = rb.Plan(T(p.xyz), T(p.is_bnd), T(p.interior), T(p.idx), T(p.w),
+                   rb.RBFFD_LAUNCH_AUTO)
+    plan.solve_explicit(T(p.f), T(p.u0), 1e-7, 64, 0.0)
+    plan.set_neumann(T(mp.nnode), T(mp.nidx), T(mp.nw), T(mp.g))
+    dt = 0.9 * plan.stable_dt(T(gen.random_vector(p.NI, 3)), 400)[0]
+    K = 300
+    ou, os_, ores, ost = orc.solve_mixed(p.w, p.idx, p.interior, p.f, mp.nnode, mp.nidx, mp.nw,
+                                         mp.g, p.u0, dt, K, 0.0)
+    u = T(p.u0)
+    code, steps, res = plan.solve_explicit(T(p.f), u, dt, K, 0.0)
+    assert steps == os_ == K
+    assert np.max(np.abs(H(u) - ou)) <= 1e-12 * np.max(np.abs(ou))
+    assert plan.stats()[3][1] > 0      # the FP64 sweep replays graphs
+    plan.destroy()

@@ -220,6 +220,7 @@ SWEEP_CASES = [
     (2, 30, 6, 1, "input_graph"),
     (2, 29, 4, 2 | 16, "random_persistent"),
     (3, 9, 4, 0, "cube_m4"),
+    (2, 35, 4, 64, "morton_auto"),
 ]
 
 
@@ -288,6 +289,30 @@ def test_sweep_zero_steps_and_errors(rb, orc):
     with pytest.raises(rb.RbffdError):
         plan.solve_explicit(T(p.f), T(p.u0), -1.0, 10, 0.0)
     plan.destroy()
+
+
+def test_launch_modes_same_bits(rb, orc):
+    """Graph, persistent and autotuned launch modes: the same FP64 iterate and the same
+    defect-corrected iterate bit for bit; the reported shape says which mode ran
+    (0 blocks per SM = persistent)."""
+    p = build(orc, 2, 30, 4, seed=47)
+    dt = _dt(orc, p)
+    outs = []
+    for flags in (0, 16, 64):
+        plan = _plan(rb, p, flags)
+        u = T(p.u0)
+        plan.solve_explicit(T(p.f), u, dt, 500, 0.0)
+        u2 = T(p.u0)
+        plan.solve_dc(T(p.f), u2, dt, 0.0, 2, 200, 0.0)
+        shape = plan.stats()[3]
+        if flags == 0:
+            assert shape[1] > 0 and shape[3] > 0
+        if flags == 16:
+            assert shape[1] == 0 and shape[3] == 0
+        outs.append((H(u), H(u2)))
+        plan.destroy()
+    for a, b in outs[1:]:
+        assert np.array_equal(a, outs[0][0]) and np.array_equal(b, outs[0][1])
 
 
 def test_plan_rejects_bad_interior(rb, orc):

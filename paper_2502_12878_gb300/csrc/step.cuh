@@ -172,21 +172,29 @@ struct StepArgs {
     int n;
 };
 
-// FP32 inner sweep: bulk prefetch into L2 (one lane) of the weight and index
-// planes of slice sl, the warp's next one: the 16-bit code plane when the plan
-// has one (the few slices that keep int32 indices then read theirs from HBM;
-// choosing per slice would wait on the slice's window bases first, which
-// measured 3 % slower).  Both planes start on 16-byte boundaries and their
-// sizes (4n and 2n or 4n bytes per row, 32 rows) are multiples of 16.
-// Measured: +13 % for the FP32 sweep (the HBM-latency-bound one); two or
-// three slices ahead gain nothing; the FP64 sweep, which the FP64 pipe
-// binds, does not prefetch (whole slice or weights alone, it lost 12-15 %).
+// Bulk prefetch into L2 (one lane) of the weight and index planes of slice
+// sl, the warp's next one: the 16-bit code plane when the plan has one (the
+// few slices that keep int32 indices then read theirs from HBM; choosing per
+// slice would wait on the slice's window bases first, which measured 3 %
+// slower).  Both planes start on 16-byte boundaries and their sizes (8n or 4n
+// and 2n or 4n bytes per row, 32 rows) are multiples of 16.  Measured at 1M
+// rows: +13 % for the FP32 sweep (HBM-latency bound); two or three slices
+// ahead gain nothing.  The FP64 sweep prefetches only for n <= PF64_MAX_N:
+// +3.5 % at n = 12, +1.6 % at n = 13, nothing at 16, and 3-19 % lost from
+// n = 20 on, where the FP64 pipe binds.
+static constexpr int PF64_MAX_N = 13;
+
+template <int MODE>
 __device__ __forceinline__ void prefetch_planes(const StepArgs& A, int64_t sl) {
     if (sl >= A.nslices) return;
     const int64_t nb = sl * (int64_t)A.n * SLICE;
     const unsigned plane = (unsigned)(A.n * SLICE);
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(A.w32 + nb), "r"(plane * 4u)
-                 : "memory");
+    if (MODE == MODE_INNER32)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(A.w32 + nb),
+                     "r"(plane * 4u) : "memory");
+    else
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(A.w64 + nb),
+                     "r"(plane * 8u) : "memory");
     if (A.col16)
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(A.col16 + nb),
                      "r"(plane * 2u) : "memory");
@@ -207,7 +215,8 @@ __device__ __forceinline__ unsigned long long step_rows(const StepArgs& A, int p
         const int64_t row = sl * SLICE + lane;
         const int64_t base = sl * (int64_t)A.n * SLICE + lane;
         const int4 sb = A.col16 ? __ldg(A.sbase + sl) : make_int4(-1, -1, -1, -1);
-        if (MODE == MODE_INNER32 && lane == 0) prefetch_planes(A, sl + stride);
+        if ((MODE == MODE_INNER32 || (NN > 0 && NN <= PF64_MAX_N)) && lane == 0)
+            prefetch_planes<MODE>(A, sl + stride);
         if (row < A.NI) {
             if (MODE == MODE_SWEEP64) {
                 const double* uin = par ? A.u1 : A.u0;

@@ -389,8 +389,9 @@ RBFFD_API int rbffd_plan_set_dc(rbffd_plan* plan, int64_t K_in, double rho_in);
  *   steps taken, last residual max-norm, status (RBFFD_OK, RBFFD_NOT_CONVERGED
  *   or an error).  Returns the most severe per-domain status.
  * rbffd_batch_set_shape - launch shape of the persistent grid (re-captures the
- *   graph): threads per block (256, 512 or 1024), register budget minb (min
- *   resident blocks per SM: 1..3 at 256 threads, 1..2 at 512, 1 at 1024) and
+ *   graph): threads per block (256, 512, 768 or 1024), register budget minb
+ *   (min resident blocks per SM: 1..3 at 256 threads, 1..2 at 512, 1 at 768
+ *   and 1024) and
  *   blocks per SM; RBFFD_ERR_ARG for other combinations, RBFFD_ERR_CAPACITY
  *   when the grid cannot be co-resident.  The binding's autotuner times
  *   candidates through it.

@@ -555,7 +555,7 @@ class Batch:
             cands = candidates or (
                 [(m, b, 256) for m in (1, 2, 3) for b in (1, 2, 3, 4) if b >= m - 1]
                 + [(m, b, 512) for m in (1, 2) for b in (1, 2) if b >= m - 1]
-                + [(1, 1, 1024)])
+                + [(1, 1, 768), (1, 1, 1024)])
             best, best_ms = None, float("inf")
             for (m, b, th) in cands:
                 try:

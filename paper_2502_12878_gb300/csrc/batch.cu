@@ -31,7 +31,7 @@
 
 namespace rbffd {
 
-static constexpr int BATCH_MAX_WARPS = 32;   // blocks of 256, 512 or 1024 threads
+static constexpr int BATCH_MAX_WARPS = 32;   // blocks of 256, 512, 768 or 1024 threads
 static constexpr long long BATCH_SPIN_CYCLES = 4000000000LL;
 
 struct DomDesc {           // static part (from the plan)
@@ -218,7 +218,7 @@ __device__ bool team_sync_global(DomState* st, int size) {
 
 // one domain's solve by one team member (rank of size blocks); returns false
 // when a team wait gave up.  CH: neighbours per load phase (8 where the
-// register budget is 64 per thread).
+// register budget is below 80 per thread).
 template <int CH>
 __device__ bool run_domain(const TeamDesc T, const DomDesc* __restrict__ desc,
                            const DomCall* __restrict__ call, DomState* state,
@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(TH, MINB)
     batch_kernel(const DomDesc* __restrict__ desc, const DomCall* __restrict__ call,
                  DomState* state, const TeamDesc* __restrict__ assign,
                  const int* __restrict__ first) {
-    constexpr int CH = 65536 / (TH * MINB) >= 128 ? 16 : 8;
+    constexpr int CH = 65536 / (TH * MINB) >= 80 ? 16 : 8;
     __shared__ unsigned long long wmax[BATCH_MAX_WARPS];
     __shared__ int s_stop;
     for (int a = first[blockIdx.x]; a < first[blockIdx.x + 1]; ++a)
@@ -336,11 +336,12 @@ typedef void (*BatchFn)(const DomDesc*, const DomCall*, DomState*, const TeamDes
 // launch shapes: (register budget, block size) with TH x MINB <= 1024 threads
 static bool batch_shape_ok(int minb, int threads) {
     return (threads == 256 && minb >= 1 && minb <= 3) || (threads == 512 && minb >= 1 && minb <= 2) ||
-           (threads == 1024 && minb == 1);
+           ((threads == 768 || threads == 1024) && minb == 1);
 }
 
 static BatchFn batch_fn(int minb, int threads) {
     if (threads == 1024) return batch_kernel<1, 1024>;
+    if (threads == 768) return batch_kernel<1, 768>;
     if (threads == 512) return minb == 2 ? batch_kernel<2, 512> : batch_kernel<1, 512>;
     switch (minb) {
         case 1: return batch_kernel<1, 256>;

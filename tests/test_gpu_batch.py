@@ -80,7 +80,7 @@ def test_batch_autotune_and_errors(rb, orc):
     assert (shape[0], shape[1], shape[4]) == best and ms > 0
     # every block size gives the same iterates; bad shapes are refused
     ref = None
-    for th in (256, 512, 1024):
+    for th in (256, 512, 768, 1024):
         batch.set_shape(1, 1, th)
         uu = [T(p.u0) for p, _ in doms]
         batch.solve(fs, uu, [dt for _, dt in doms], [80] * 3, [0.0] * 3)
@@ -88,7 +88,7 @@ def test_batch_autotune_and_errors(rb, orc):
             ref = [H(u) for u in uu]
         else:
             assert all(np.array_equal(H(u), r) for u, r in zip(uu, ref))
-    for bad in ((2, 1, 1024), (3, 1, 512), (1, 1, 128)):
+    for bad in ((2, 1, 1024), (2, 1, 768), (3, 1, 512), (1, 1, 128)):
         with pytest.raises(rb.RbffdError):
             batch.set_shape(*bad)
     batch.set_shape(*best)

@@ -170,7 +170,17 @@ struct StepArgs {
     int64_t NI;
     int64_t nslices;
     int n;
+    int spread;   // 1: consecutive slices go to different blocks (small plans)
 };
+
+// The warp's first slice.  Large plans give each block runs of consecutive
+// slices (their gathers share the SM's L1); plans with fewer slices than the
+// blocks' warps would then leave SMs idle while others run several warps'
+// FP64 chains, so there consecutive slices go to different blocks.
+__device__ __forceinline__ int64_t step_warp(const StepArgs& A) {
+    return A.spread ? (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x
+                    : (int64_t)blockIdx.x * (STEP_THREADS / 32) + (threadIdx.x >> 5);
+}
 
 // Bulk prefetch into L2 (one lane) of the weight and index planes of slice
 // sl, the warp's next one: the 16-bit code plane when the plan has one (the
@@ -327,7 +337,7 @@ __global__ void __launch_bounds__(STEP_THREADS, MINB) step_kernel(StepArgs A, St
     if (s_skip) return;
     const long long k = s_k;
     const int par = (int)(k & 1);
-    const int64_t warp = (int64_t)blockIdx.x * (STEP_THREADS / 32) + (threadIdx.x >> 5);
+    const int64_t warp = step_warp(A);
     unsigned long long m = step_rows<NN, MODE, false>(A, par, s_dt, (float)s_dt, warp,
                                                       (int64_t)gridDim.x * (STEP_THREADS / 32));
     m = block_max_bits(m);
@@ -419,7 +429,7 @@ __global__ void __launch_bounds__(STEP_THREADS, MINB) persistent_kernel(StepArgs
     __syncthreads();
     const double dt = s_dt;
     const long long kmax = s_max, k0 = s_k;
-    const int64_t warp = (int64_t)blockIdx.x * (STEP_THREADS / 32) + (threadIdx.x >> 5);
+    const int64_t warp = step_warp(A);
     const int64_t nw = (int64_t)gridDim.x * (STEP_THREADS / 32);
     for (long long k = k0; k < kmax; ++k) {
         unsigned long long m = step_rows<NN, MODE, true>(A, (int)(k & 1), dt, (float)dt, warp, nw);

@@ -445,6 +445,11 @@ __global__ void apply_rowmajor(const double* w, const int32_t* idx, int64_t nc, 
 }
 
 // ------------------------------------------------------------ host side
+// fewer slices than one block of warps per SM: spread them over all SMs
+static bool spread_slices(const rbffd_plan* p) {
+    return (p->nslices + STEP_THREADS / 32 - 1) / (STEP_THREADS / 32) < device_sm_count();
+}
+
 static StepArgs make_args(const rbffd_plan* p) {
     StepArgs A;
     A.w64 = p->w64;
@@ -461,6 +466,7 @@ static StepArgs make_args(const rbffd_plan* p) {
     A.NI = p->NI;
     A.nslices = p->nslices;
     A.n = p->n;
+    A.spread = spread_slices(p) ? 1 : 0;
     return A;
 }
 
@@ -483,21 +489,26 @@ static void free_plan(rbffd_plan* p) {
 // longer-lived blocks avoid the tail of many short ones)
 static int grid_for(const rbffd_plan* p, int per_sm) {
     int64_t warps = p->nslices;
-    int64_t blocks = (warps + STEP_THREADS / 32 - 1) / (STEP_THREADS / 32);
+    // spread plans: one slice per block at most, so every SM takes a share
+    int64_t blocks = spread_slices(p) ? warps : (warps + STEP_THREADS / 32 - 1) / (STEP_THREADS / 32);
     int64_t cap = (int64_t)device_sm_count() * std::max(1, per_sm);
     return (int)std::max<int64_t>(1, std::min(blocks, cap));
 }
 static int step_grid(const rbffd_plan* p) { return grid_for(p, p->grid_steps); }
 
 // resident blocks of a persistent launch, no more than the slices need
-static int persistent_grid(StepFn fn, int64_t nslices) {
+// (spread plans: one block per SM at most)
+static int persistent_grid(StepFn fn, const rbffd_plan* p) {
+    const int64_t nslices = p->nslices;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)fn, STEP_THREADS, 0) !=
             cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
+    const int sms = device_sm_count();
     int64_t need = (nslices + STEP_THREADS / 32 - 1) / (STEP_THREADS / 32);
-    return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * device_sm_count(), need));
+    if (spread_slices(p)) need = std::min<int64_t>(nslices, sms);
+    return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sms, need));
 }
 
 // reset the control block for a run of at most max_steps steps
@@ -564,7 +575,7 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
             t.persistent = c == 5;
             t.per_sm = t.persistent ? 1 : c;
             t.fn = pick(mode, p->n, t.persistent, minb);
-            t.grid = t.persistent ? persistent_grid(t.fn, p->nslices) : grid_for(p, t.per_sm);
+            t.grid = t.persistent ? persistent_grid(t.fn, p) : grid_for(p, t.per_sm);
             t.gx = nullptr;
             t.ms = 1e30f;
             cands.push_back(t);
@@ -727,7 +738,7 @@ static int run_steps(rbffd_plan* p, int mode, double dt, double tol, long long m
         if (st) return st;
         if (p->persist[mi]) {
             StepFn fn = pick(mode, p->n, true, p->minb[mi]);
-            int grid = persistent_grid(fn, p->nslices);
+            int grid = persistent_grid(fn, p);
             StepArgs A = make_args(p);
             StepCtrl* c = p->ctrl;
             void* args[] = {(void*)&A, (void*)&c};

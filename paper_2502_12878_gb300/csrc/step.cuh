@@ -326,6 +326,13 @@ __global__ void __launch_bounds__(STEP_THREADS, MINB) step_kernel(StepArgs A, St
     __shared__ long long s_k;
     __shared__ int s_skip;
     __shared__ double s_dt;
+    // programmatic dependent launch: the next step's blocks may be scheduled
+    // now (they take SM slots as this step's blocks leave, so its launch
+    // overlaps this step's tail); every block then waits here until the
+    // previous step has completed and its writes are visible.  Both are no-ops
+    // for a launch without the programmatic-serialization attribute.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if (threadIdx.x == 0) {
         volatile StepCtrl* vc = c;
         long long k = vc->k;

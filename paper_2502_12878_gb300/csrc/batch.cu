@@ -421,7 +421,8 @@ static void make_assignment(const std::vector<double>& work, int grid, std::vect
     first[grid] = (int)asg.size();
 }
 
-static int batch_capture(rbffd_batch* B, cudaStream_t user) {
+// captures on a private stream (capture records, it runs nothing)
+static int batch_capture(rbffd_batch* B) {
     if (B->graph) {
         cudaGraphExecDestroy((cudaGraphExec_t)B->graph);
         B->graph = nullptr;
@@ -433,40 +434,40 @@ static int batch_capture(rbffd_batch* B, cudaStream_t user) {
     // first try a cooperative kernel node; if capture refuses it, a plain node
     // (the grid was checked to fit on the device at once; waits are bounded)
     for (int coop = 1; coop >= 0 && e != cudaSuccess; --coop) {
-    cudaGraph_t g;
-    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-        dim3 gg(64, (unsigned)std::min(B->ndom, 65535));
-        batch_gather<<<gg, 256, 0, cs>>>(B->d_desc, B->d_call, B->d_state, B->ndom);
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(B->grid);
-        cfg.blockDim = dim3(B->threads);
-        cfg.stream = cs;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeCooperative;
-        attr[0].val.cooperative = coop;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, fn, (const DomDesc*)B->d_desc, (const DomCall*)B->d_call,
-                               B->d_state, (const TeamDesc*)B->d_team, (const int*)B->d_first);
+        cudaGraph_t g;
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            batch_scatter<<<gg, 256, 0, cs>>>(B->d_desc, B->d_call, B->d_state, B->ndom);
-            e = cudaStreamEndCapture(cs, &g);
-        } else {
-            cudaGraph_t dummy;
-            cudaStreamEndCapture(cs, &dummy);
+            dim3 gg(64, (unsigned)std::min(B->ndom, 65535));
+            batch_gather<<<gg, 256, 0, cs>>>(B->d_desc, B->d_call, B->d_state, B->ndom);
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(B->grid);
+            cfg.blockDim = dim3(B->threads);
+            cfg.stream = cs;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeCooperative;
+            attr[0].val.cooperative = coop;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            e = cudaLaunchKernelEx(&cfg, fn, (const DomDesc*)B->d_desc, (const DomCall*)B->d_call,
+                                   B->d_state, (const TeamDesc*)B->d_team, (const int*)B->d_first);
+            if (e == cudaSuccess) {
+                batch_scatter<<<gg, 256, 0, cs>>>(B->d_desc, B->d_call, B->d_state, B->ndom);
+                e = cudaStreamEndCapture(cs, &g);
+            } else {
+                cudaGraph_t dummy;
+                cudaStreamEndCapture(cs, &dummy);
+            }
         }
-    }
-    if (e == cudaSuccess) {
-        cudaGraphExec_t ex;
-        e = cudaGraphInstantiate(&ex, g, 0);
-        cudaGraphDestroy(g);
         if (e == cudaSuccess) {
-            B->graph = (void*)ex;
-            B->coop = coop;
+            cudaGraphExec_t ex;
+            e = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            if (e == cudaSuccess) {
+                B->graph = (void*)ex;
+                B->coop = coop;
+            }
         }
-    }
-    if (e != cudaSuccess) cudaGetLastError();
+        if (e != cudaSuccess) cudaGetLastError();
     }
     cudaStreamDestroy(cs);
     RBFFD_CHECK_CUDA(e);
@@ -566,7 +567,7 @@ extern "C" int rbffd_batch_create(rbffd_plan* const* plans, int ndom, int blocks
         batch_free(B);
         return RBFFD_ERR_CAPACITY;
     }
-    int st = batch_capture(B, s);
+    int st = batch_capture(B);
     if (st) {
         batch_free(B);
         return st;
@@ -666,7 +667,8 @@ extern "C" int rbffd_batch_set_shape(rbffd_batch* B, int minb, int blocks_per_sm
     B->per_sm = blocks_per_sm;
     B->threads = threads;
     B->grid = grid;
-    return batch_capture(B, as_stream(stream));
+    (void)stream;
+    return batch_capture(B);
 }
 
 extern "C" int rbffd_batch_stats(const rbffd_batch* B, double* h_ms, int* h_shape) {

@@ -616,10 +616,14 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
         if (ce == cudaSuccess) {
             ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
             if (ce == cudaSuccess) {
-                for (long long i = 0; i < reps; ++i)
-                    launch_step(t.fn, t.grid, cs, A, p->ctrl, use_pdl(p));
+                cudaError_t le = cudaSuccess;
+                for (long long i = 0; i < reps && le == cudaSuccess; ++i)
+                    le = launch_step(t.fn, t.grid, cs, A, p->ctrl, use_pdl(p));
                 ce = cudaStreamEndCapture(cs, &gg);
-                if (ce == cudaSuccess) {
+                if (ce == cudaSuccess && le != cudaSuccess) {
+                    cudaGraphDestroy(gg);
+                    ce = le;
+                } else if (ce == cudaSuccess) {
                     ce = cudaGraphInstantiate(&t.gx, gg, 0);
                     cudaGraphDestroy(gg);
                 }
@@ -693,6 +697,7 @@ static int ensure_graph(rbffd_plan* p, int mode, cudaStream_t s) {
     StepArgs A = make_args(p);
     int grid = grid_for(p, p->per_sm[mi]);
     cudaGraph_t g;
+    cudaError_t le = cudaSuccess;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         const unsigned ng = (unsigned)std::max<int64_t>(1, std::min<int64_t>((p->NN + 255) / 256, 1024));
@@ -703,9 +708,14 @@ static int ensure_graph(rbffd_plan* p, int mode, cudaStream_t s) {
                 neumann_scatter<<<ng, 256, 0, cs>>>(p->nslot, p->uN, p->NN, p->u[0], p->u[1],
                                                     p->ctrl);
             }
-            launch_step(fn, grid, cs, A, p->ctrl, use_pdl(p));
+            if (le == cudaSuccess) le = launch_step(fn, grid, cs, A, p->ctrl, use_pdl(p));
         }
         e = cudaStreamEndCapture(cs, &g);
+        // a launch refused during capture would leave a graph short of steps
+        if (e == cudaSuccess && le != cudaSuccess) {
+            cudaGraphDestroy(g);
+            e = le;
+        }
     }
     if (e == cudaSuccess) {
         cudaGraphExec_t ex;

@@ -81,7 +81,7 @@ def _load():
         "oracle_apply": (None, [P, P, i64, i32, P, P]),
         "oracle_solve_explicit": (i32, [P, P, P, i64, i64, i32, P, P, f64, i64, f64, P, P]),
         "oracle_solve_dc": (i32, [P, P, P, i64, i64, i32, P, P, f64, f64, i64, i64, f64,
-                                  P, P, P]),
+                                  P, P, P, P]),
         "oracle_adjoint": (i32, [P, P, P, i64, i64, i32, P, i64, f64, P, P, P]),
         "oracle_adjoint_w": (i32, [P, P, P, i64, i64, i32, P, P, P, i64, f64, P, P, P, P]),
         "oracle_power_rho": (f64, [P, P, P, i64, i64, i32, P, i32]),
@@ -291,10 +291,11 @@ def solve_explicit(w, idx, interior, f, u0, dt, max_steps, tol):
     return u, int(steps.value), float(res.value), int(st)
 
 
-def solve_dc(w, idx, interior, f, u0, dt, tol, max_outer, K_in, rho_in):
+def solve_dc(w, idx, interior, f, u0, dt, tol, max_outer, K_in, rho_in, inner_res=False):
     """FP64 defect correction with an FP32 inner explicit iteration.
 
-    Returns (u, outer corrections, inner steps in total, final defect, status)."""
+    Returns (u, outer corrections, inner steps in total, final defect, status), and
+    with ``inner_res`` also max|rho| of the last inner step taken."""
     w = _c(w, np.float64)
     idx = _c(idx, np.int32)
     interior = _c(interior, np.int32)
@@ -304,10 +305,12 @@ def solve_dc(w, idx, interior, f, u0, dt, tol, max_outer, K_in, rho_in):
     outer = ctypes.c_int64(0)
     inner = ctypes.c_int64(0)
     res = ctypes.c_double(0.0)
+    res_in = ctypes.c_double(0.0)
     st = _load().oracle_solve_dc(_p(w), _p(idx), _p(interior), len(u), rows, n, _p(f), _p(u),
                                  dt, tol, max_outer, K_in, rho_in, ctypes.byref(outer),
-                                 ctypes.byref(inner), ctypes.byref(res))
-    return u, int(outer.value), int(inner.value), float(res.value), int(st)
+                                 ctypes.byref(inner), ctypes.byref(res), ctypes.byref(res_in))
+    out = (u, int(outer.value), int(inner.value), float(res.value), int(st))
+    return out + (float(res_in.value),) if inner_res else out
 
 
 def adjoint(w, idx, interior, N, lamK, K, dt):

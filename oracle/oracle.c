@@ -1100,12 +1100,13 @@ int oracle_solve_mixed(const double* w, const int32_t* idx, const int32_t* inter
 /* stopping after step k when max|rho| (of e^k) < rho_in * D, or at K_in.   */
 /* Then u_i += (double) e_i at interior nodes.                              */
 /* w32 = (float) w, d32 = (float) d, dt32 = (float) dt.                      */
+/* res_in_out (may be NULL): max|rho| of the last inner step taken.         */
 /* Returns 0 converged, 1 outer cap, 2 non-finite.                          */
 /* ------------------------------------------------------------------------- */
 int oracle_solve_dc(const double* w, const int32_t* idx, const int32_t* interior, int64_t N,
                     int64_t NI, int n, const double* f, double* u, double dt, double tol,
                     int64_t max_outer, int64_t K_in, double rho_in, int64_t* outer_out,
-                    int64_t* inner_total_out, double* res_out)
+                    int64_t* inner_total_out, double* res_out, double* res_in_out)
 {
     float* w32 = (float*)malloc(sizeof(float) * (size_t)(NI * n));
     float* e0 = (float*)calloc((size_t)N, sizeof(float));
@@ -1116,7 +1117,7 @@ int oracle_solve_dc(const double* w, const int32_t* idx, const int32_t* interior
     float dt32 = (float)dt;
     int status = 1;
     int64_t t = 0, inner_total = 0;
-    double D = 0.0;
+    double D = 0.0, R_in_last = 0.0;
     for (t = 0; t <= max_outer; ++t) {
         D = 0.0;
         int nonfinite = 0;
@@ -1155,6 +1156,7 @@ int oracle_solve_dc(const double* w, const int32_t* idx, const int32_t* interior
             }
             float* tmp = ec; ec = en; en = tmp;
             ++inner_total;
+            R_in_last = nf ? INFINITY : Rin;
             if (nf) { inner_bad = 1; break; }
             if (Rin < lim) break;
         }
@@ -1167,6 +1169,7 @@ int oracle_solve_dc(const double* w, const int32_t* idx, const int32_t* interior
     *outer_out = t;
     *inner_total_out = inner_total;
     *res_out = D;
+    if (res_in_out) *res_in_out = R_in_last;
     free(w32); free(e0); free(e1); free(d32);
     return status;
 }

@@ -10,6 +10,8 @@ Fixed by the mathematics rather than by the oracle's code:
 * the loss is quadratic in (f, g), so central differences are exact up to
   rounding and a dense reverse sweep in numpy gives the same gradient.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -221,3 +223,72 @@ def test_weight_gradient_matches_dense_reverse_sweep_and_fd(orc):
         fd = (loss(p.w + eps * v) - loss(p.w - eps * v)) / (2 * eps)
         an = np.sum(gw * v)
         assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-12)
+
+
+def test_defect_correction_inner_loop_stalls_at_the_fp32_floor(orc):
+    """The inner iteration runs in FP32: with no inner stop (rho_in = 0) it stalls
+    where each increment fmaf(dt32, rho_i, e_i) rounds back to e_i, i.e. at
+    |rho_i| <= ulp(e_i) / (2 dt32), a fraction of eps32 * max_i sum_j |w_ij e_j|.
+    An inner loop that silently ran in FP64 would keep falling ~1e8 times lower."""
+    p = build(orc, 2, 20, 4, seed=10)
+    dt = dt_stable(orc, p)
+    eps32 = float(np.finfo(np.float32).eps)
+    runs = [orc.solve_dc(p.w, p.idx, p.interior, p.f, p.u0, dt, 0.0, 1, K, 0.0, inner_res=True)
+            for K in (20000, 30000)]
+    (u1, o1, i1, D1, s1, rin1), (u2, o2, i2, D2, s2, rin2) = runs
+    assert (o1, i1, o2, i2) == (1, 20000, 1, 30000)
+    # stalled: 10,000 further FP32 steps change nothing
+    assert np.array_equal(u1, u2) and rin1 == rin2
+    e = (u1 - p.u0)[p.interior]                 # u0 = 0 inside: e exactly, as stored
+    assert np.array_equal(e.astype(np.float32).astype(np.float64), e)
+    ea = np.zeros(p.N)
+    ea[p.interior] = e
+    scale = np.max(np.sum(np.abs(p.w * ea[p.idx]), axis=1))
+    assert 0.01 * eps32 * scale <= rin1 <= 2.0 * eps32 * scale, rin1 / (eps32 * scale)
+    # the stall bound itself: no row's increment survives rounding
+    dt32 = float(np.float32(dt))
+    spacing = np.spacing(np.abs(e).astype(np.float32)).astype(np.float64)
+    assert rin1 <= np.max(spacing) / (2 * dt32) * 1.001
+    # the FP64 defect after this one correction sits at the same FP32 level
+    assert 0.01 * eps32 * scale <= D1 <= 4.0 * eps32 * scale
+
+
+@pytest.mark.parametrize("rho_in", [1e-2, 1e-3])
+def test_defect_correction_inner_step_count_follows_slowest_mode(orc, rho_in):
+    """From e = 0 the inner residual is rho^k = (I + dt W_II)^k d.  Here u0 = 0 and
+    g = 0, so d = -f = 2 pi^2 u^a, the slowest mode: max|rho^k| = (1 - dt lam_1)^k D
+    with lam_1 the smallest |eigenvalue| of W_II (numpy).  The rule 'stop after step
+    k once max|rho^k| < rho_in D' then takes ceil(ln rho_in / ln(1 - dt lam_1)) + 1
+    steps; an absolute rule (max|rho| < rho_in) would take ~ln(D)/ln(1/rho_in) more."""
+    p = build(orc, 2, 20, 4, seed=10)
+    dt = dt_stable(orc, p)
+    WII, _, _ = p.dense()
+    lam1 = np.min(np.abs(np.linalg.eigvals(WII).real))
+    assert abs(lam1 / (2 * np.pi ** 2) - 1) < 1e-3
+    u, outer, inner, D, st = orc.solve_dc(p.w, p.idx, p.interior, p.f, p.u0, dt, 0.0, 1,
+                                          10 ** 6, rho_in)
+    predicted = math.ceil(math.log(rho_in) / math.log(1 - dt * lam1)) + 1
+    assert outer == 1 and abs(inner / predicted - 1) < 0.01, (inner, predicted)
+
+
+def test_defect_correction_inner_arithmetic_is_binary32(orc):
+    """A hand-worked case of the inner step in IEEE binary32.  Interior nodes 0, 1,
+    boundary node 2 (g = 0), u0 = 0, f = (1, 1), dt = 2^-4, so d = -f = (-1, -1)
+    and D = 1.  Step 1 from e = 0: rho = d32, e^1 = fl(dt32 * -1) = (-2^-4, -2^-4).
+    Step 2, row 0 (w = -16, -2^-21 on nodes 0, 1): the products 1 and 2^-25 are
+    exact, but 1 + 2^-25 rounds to 1 in binary32 (half an ulp is 2^-24), so
+    rho_0 = 1 + d32_0 = 0 and e_0 stays -2^-4.  Accumulated in binary64, rho_0
+    would be 2^-25 and e_0 = -2^-4 + 2^-29 (a binary32 ulp of 2^-4 is 2^-27)."""
+    w = np.array([[-16.0, -2.0 ** -21, 0.0], [-16.0, 0.0, 0.0]])
+    idx = np.array([[0, 1, 2], [1, 0, 2]], dtype=np.int32)
+    interior = np.array([0, 1], dtype=np.int32)
+    f = np.array([1.0, 1.0])
+    u0 = np.zeros(3)
+    u, outer, inner, D, st, rin = orc.solve_dc(w, idx, interior, f, u0, 2.0 ** -4, 0.0, 1, 2,
+                                               0.0, inner_res=True)
+    assert (outer, inner) == (1, 2)
+    assert u[0] == -2.0 ** -4 and u[1] == -2.0 ** -4 and u[2] == 0.0
+    assert rin == 0.0
+    # the FP64 defect of the corrected iterate: row 0 is 1 + 2^-25 - 1 exactly
+    D_next = orc.solve_dc(w, idx, interior, f, u, 2.0 ** -4, 0.0, 0, 1, 0.0)[3]
+    assert D_next == 2.0 ** -25

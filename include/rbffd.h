@@ -176,12 +176,13 @@ RBFFD_API int rbffd_knn_masked(const double* xyz, int64_t N, int d, const uint8_
  *   Working memory: one fixed array of about 6 MB in the library's device
  *   image, held on every GPU that loads the library until the process exits.
  *   It never calls cudaMalloc, cudaMallocAsync, cudaFree or any allocating
- *   library routine; memsets, copies and kernels go on `stream`, and the call
+ *   library routine; memsets, copies and kernels go on `stream`.  Every call
  *   synchronises `stream` (host copies of the bounding box and of an error
- *   flag).
- *   The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress, once per device, with that device current); make
- *   that first call before any stream capture.
+ *   flag), so it must not be called while `stream` is being captured.
+ *   The first call on a device, with that device current, looks up the
+ *   array's device address (cudaGetSymbolAddress) and keeps it for the
+ *   process; a cudaDeviceReset of that device invalidates it, so do not call
+ *   this entry point on a device after resetting it.
  *   N <= RBFFD_KNN_NOALLOC_MAX_NODES, else RBFFD_ERR_CAPACITY (nothing
  *   enqueued).  All calls share the one array: calls that overlap on the GPU
  *   (other streams, other host threads) race and must be serialised by the
@@ -260,6 +261,19 @@ RBFFD_API int rbffd_error(const double* u, const double* ua, int64_t N, double* 
                           double* h_mean, void* stream);
 
 /*
+ * rbffd_fp64_fma_rate - measures the device's FP64 fused multiply-add rate
+ * (not part of the paper's method: the roofline of the kernels the FP64 pipe
+ * binds, the explicit sweep at larger stencils and the weight build).  For 4,
+ * 8 and 16 independent fma chains per thread, at the largest resident grid of
+ * 256-thread blocks: one untimed warm-up launch, then one launch of `iters`
+ * fmas per thread, timed with CUDA events on `stream`.  h_fma_per_s (host)
+ * receives the fastest shape's FMAs per second, h_ms (host, may be NULL) its
+ * timed launch's milliseconds.  Synchronises `stream`.
+ */
+RBFFD_API int rbffd_fp64_fma_rate(int64_t iters, double* h_fma_per_s, double* h_ms,
+                                  void* stream);
+
+/*
  * rbffd_plan_create - device-resident solver plan for Eq. 6.
  * Reorders the nodes (interior first, then by `flags` order), packs the
  * stencils into 32-row slices (weights and neighbour indices interleaved so a
@@ -305,6 +319,17 @@ RBFFD_API int rbffd_plan_destroy(rbffd_plan* plan);
 RBFFD_API int rbffd_plan_set_neumann(rbffd_plan* plan, int64_t NN, const int32_t* nodes,
                                      const int32_t* idx, const double* w, int nn,
                                      const double* g, void* stream);
+/*
+ * rbffd_plan_set_wait - the in-kernel waits of the persistent launch (the
+ * end-of-step grid barrier): each gives up after timeout_ms (<= 0: the
+ * default, about 2 s; at most 60,000), measured in SM clock cycles at the
+ * device's maximum clock, and the solve then returns RBFFD_ERR_TIMEOUT.
+ * held_arrivals (0..1024, normally 0) is a failure injection for testing that
+ * path: the barrier waits for that many arrivals beyond the grid's, which
+ * never come, so every block gives up after the timeout and returns.  Takes
+ * effect from the next solve; graph-mode steps have no waits.
+ */
+RBFFD_API int rbffd_plan_set_wait(rbffd_plan* plan, double timeout_ms, int held_arrivals);
 /* node permutation of the plan: perm [N] out, perm[p] = original index of slot p */
 RBFFD_API int rbffd_plan_perm(const rbffd_plan* plan, int32_t* perm, void* stream);
 
@@ -430,16 +455,32 @@ RBFFD_API int rbffd_stable_dt(rbffd_plan* plan, const double* v0, int iters, dou
                     double* h_dt_out, double* h_rho_out, void* stream);
 
 /*
+ * rbffd_transpose - build the plan's transposed interior operator now (the
+ * adjoint's W^T, derived from Eq. 6; otherwise the first rbffd_adjoint or
+ * rbffd_adjoint_w builds it).  Column c of W^T lists the rows r whose support
+ * holds c, in ascending interior-list order, with their weights w_rc; columns
+ * are stored in 32-column slices padded with zero weights.  Owned by the plan
+ * (freed by rbffd_plan_destroy); a second call does nothing.  Synchronises
+ * `stream`; scratch comes from cudaMallocAsync on `stream`.
+ */
+RBFFD_API int rbffd_transpose(rbffd_plan* plan, void* stream);
+
+/*
  * rbffd_adjoint - gradients of a loss of the K-th iterate of Eq. 6 (the
  * adjoint is not in the paper).  With u^{k+1}_I = u^k_I + dt (W_II u^k_I +
- * W_IB g - f) and lamK = dL/du^K_I [NI]:
+ * W_IB g - f) and u^k_B = g for every k, from dLdu = dL/du^K [N] (caller's
+ * node order, every node):
+ *   lambda^K = the interior entries of dLdu,
  *   lambda^k = lambda^{k+1} + dt W_II^T lambda^{k+1}, k = K-1..0,
  *   grad_f [NI] = -dt sum_{k=1..K} lambda^k,
- *   grad_g [N]  = dt W_IB^T sum_{k=1..K} lambda^k (boundary entries; 0 inside),
+ *   grad_g [N]  = dt W_IB^T sum_{k=1..K} lambda^k + dLdu (boundary entries:
+ *                 the loss's direct dependence on u^K_B = g; 0 inside),
  *   lam0 [NI]   = lambda^0 = dL/du^0_I (may be NULL).
- * (W^T v)_c is accumulated over rows in ascending interior-list order.
+ * (W^T v)_c is accumulated over rows in ascending interior-list order; the
+ * boundary entry is fl(fl(dt * sum) + dLdu_b).  Builds the transpose on the
+ * first call (see rbffd_transpose).
  */
-RBFFD_API int rbffd_adjoint(rbffd_plan* plan, const double* lamK, int64_t K, double dt, double* grad_f,
+RBFFD_API int rbffd_adjoint(rbffd_plan* plan, const double* dLdu, int64_t K, double dt, double* grad_f,
                   double* grad_g, double* lam0, void* stream);
 
 /*
@@ -452,12 +493,12 @@ RBFFD_API int rbffd_adjoint(rbffd_plan* plan, const double* lamK, int64_t K, dou
  * [ceil(K/every)][N], caller order); each segment is replayed forward from its
  * checkpoint (bit-identical to the forward sweep) into a segment buffer of
  * every x N doubles (stream-ordered scratch), then walked backward.
- *   f [NI] the source of the forward run; lamK [NI]; grad_w [NI][n] out
- *   (caller layout, the row order of the plan's interior list); grad_f,
- *   grad_g, lam0 as rbffd_adjoint.
+ *   f [NI] the source of the forward run; dLdu [N] as rbffd_adjoint;
+ *   grad_w [NI][n] out (caller layout, the row order of the plan's interior
+ *   list); grad_f, grad_g, lam0 as rbffd_adjoint.
  */
 RBFFD_API int rbffd_adjoint_w(rbffd_plan* plan, const double* f, const double* ckpt,
-                              int64_t every, const double* lamK, int64_t K, double dt,
+                              int64_t every, const double* dLdu, int64_t K, double dt,
                               double* grad_w, double* grad_f, double* grad_g, double* lam0,
                               void* stream);
 

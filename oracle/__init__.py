@@ -313,12 +313,15 @@ def solve_dc(w, idx, interior, f, u0, dt, tol, max_outer, K_in, rho_in, inner_re
     return out + (float(res_in.value),) if inner_res else out
 
 
-def adjoint(w, idx, interior, N, lamK, K, dt):
-    """Backward pass of K explicit steps.  Returns (grad_f [NI], grad_g [N], lam0 [NI])."""
+def adjoint(w, idx, interior, N, dLdu, K, dt):
+    """Backward pass of K explicit steps from dLdu = dL/du^K [N] (node order; the
+    boundary entries add directly to dL/dg).  Returns (grad_f [NI], grad_g [N], lam0 [NI])."""
     w = _c(w, np.float64)
     idx = _c(idx, np.int32)
     interior = _c(interior, np.int32)
-    lamK = _c(lamK, np.float64)
+    lamK = _c(dLdu, np.float64)
+    if lamK.shape != (N,):
+        raise ValueError("dLdu must have one entry per node")
     rows, n = idx.shape
     gf = np.zeros(rows, np.float64)
     gg = np.zeros(N, np.float64)
@@ -330,8 +333,8 @@ def adjoint(w, idx, interior, N, lamK, K, dt):
     return gf, gg, l0
 
 
-def adjoint_w(w, idx, interior, f, u0, lamK, K, dt):
-    """Backward pass including the weight gradient.
+def adjoint_w(w, idx, interior, f, u0, dLdu, K, dt):
+    """Backward pass including the weight gradient, from dLdu = dL/du^K [N].
 
     Returns (grad_w [NI, n], grad_f [NI], grad_g [N], lam0 [NI])."""
     w = _c(w, np.float64)
@@ -339,9 +342,11 @@ def adjoint_w(w, idx, interior, f, u0, lamK, K, dt):
     interior = _c(interior, np.int32)
     f = _c(f, np.float64)
     u0 = _c(u0, np.float64)
-    lamK = _c(lamK, np.float64)
+    lamK = _c(dLdu, np.float64)
     rows, n = idx.shape
     N = len(u0)
+    if lamK.shape != (N,):
+        raise ValueError("dLdu must have one entry per node")
     gw = np.zeros((rows, n), np.float64)
     gf = np.zeros(rows, np.float64)
     gg = np.zeros(N, np.float64)

@@ -1184,12 +1184,14 @@ int oracle_solve_dc(const double* w, const int32_t* idx, const int32_t* interior
 /* dL/du^0_I = lambda^0.                                                     */
 /* (W^T lambda)_j is accumulated over rows i in ascending order as an fma    */
 /* chain from 0; the update is fma(dt, acc_j, lambda_j).                     */
-/* Inputs: lamK [NI] (rows), col_of_node [N] -> interior row or -1.          */
+/* Input: dLdu [N] = dL/du^K over all nodes (node order).  Its interior     */
+/* entries are lambda^K; a boundary entry b is the loss's direct dependence  */
+/* on u^K_b = g_b, so dL/dg_b = dt (W_IB^T S)_b + dLdu_b (two roundings).    */
 /* Outputs: grad_f [NI], grad_g [N] (only boundary entries non-zero),        */
 /* lam0 [NI].  Sum of lambda is accumulated with plain additions in k order. */
 /* ------------------------------------------------------------------------- */
 int oracle_adjoint(const double* w, const int32_t* idx, const int32_t* interior, int64_t N,
-                   int64_t NI, int n, const double* lamK, int64_t K, double dt,
+                   int64_t NI, int n, const double* dLdu, int64_t K, double dt,
                    double* grad_f, double* grad_g, double* lam0)
 {
     double* lam = (double*)malloc(sizeof(double) * (size_t)NI);
@@ -1199,7 +1201,7 @@ int oracle_adjoint(const double* w, const int32_t* idx, const int32_t* interior,
     if (!lam || !acc || !S || !row_of) { free(lam); free(acc); free(S); free(row_of); return -2; }
     for (int64_t i = 0; i < N; ++i) row_of[i] = -1;
     for (int64_t r = 0; r < NI; ++r) row_of[interior[r]] = (int32_t)r;
-    memcpy(lam, lamK, sizeof(double) * (size_t)NI);
+    for (int64_t r = 0; r < NI; ++r) lam[r] = dLdu[interior[r]];
     for (int64_t k = K; k >= 1; --k) {
         /* S += lambda^k */
         for (int64_t r = 0; r < NI; ++r) S[r] = S[r] + lam[r];
@@ -1220,7 +1222,7 @@ int oracle_adjoint(const double* w, const int32_t* idx, const int32_t* interior,
             int64_t col = idx[r * n + j];
             acc[col] = fma(w[r * n + j], S[r], acc[col]);
         }
-    for (int64_t i = 0; i < N; ++i) grad_g[i] = (row_of[i] < 0) ? dt * acc[i] : 0.0;
+    for (int64_t i = 0; i < N; ++i) grad_g[i] = (row_of[i] < 0) ? dt * acc[i] + dLdu[i] : 0.0;
     free(lam); free(acc); free(S); free(row_of);
     return 0;
 }
@@ -1232,10 +1234,11 @@ int oracle_adjoint(const double* w, const int32_t* idx, const int32_t* interior,
 /* u^0..u^{K-1} are recomputed from u0 and stored (plain, memory K x N); the */
 /* sum runs k = K-1 down to 0 as G = fma(lambda^{k+1}_i, u^k_j, G), then     */
 /* grad_w = dt * G.  lambda follows oracle_adjoint (same order, same S).     */
-/* Also returns grad_f, grad_g, lam0 as oracle_adjoint does.                 */
+/* Also returns grad_f, grad_g, lam0 as oracle_adjoint does (dLdu [N] as    */
+/* there: interior entries lambda^K, boundary entries the direct term).     */
 /* ------------------------------------------------------------------------- */
 int oracle_adjoint_w(const double* w, const int32_t* idx, const int32_t* interior, int64_t N,
-                     int64_t NI, int n, const double* f, const double* u0, const double* lamK,
+                     int64_t NI, int n, const double* f, const double* u0, const double* dLdu,
                      int64_t K, double dt, double* grad_w, double* grad_f, double* grad_g,
                      double* lam0)
 {
@@ -1264,7 +1267,7 @@ int oracle_adjoint_w(const double* w, const int32_t* idx, const int32_t* interio
             nxt[interior[r]] = fma(dt, ri, cur[interior[r]]);
         }
     }
-    memcpy(lam, lamK, sizeof(double) * (size_t)NI);
+    for (int64_t r = 0; r < NI; ++r) lam[r] = dLdu[interior[r]];
     for (int64_t k = K - 1; k >= 0; --k) {
         const double* uk = U + (size_t)k * N;
         /* weight gradient with lambda^{k+1} and u^k */
@@ -1290,7 +1293,7 @@ int oracle_adjoint_w(const double* w, const int32_t* idx, const int32_t* interio
             int64_t col = idx[r * n + j];
             acc[col] = fma(w[r * n + j], S[r], acc[col]);
         }
-    for (int64_t i = 0; i < N; ++i) grad_g[i] = (row_of[i] < 0) ? dt * acc[i] : 0.0;
+    for (int64_t i = 0; i < N; ++i) grad_g[i] = (row_of[i] < 0) ? dt * acc[i] + dLdu[i] : 0.0;
     free(U); free(lam); free(acc); free(S); free(G); free(row_of);
     return 0;
 }

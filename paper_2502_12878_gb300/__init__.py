@@ -52,7 +52,8 @@ EXPORTED = [
     "rbffd_batch_destroy", "rbffd_solve_batch", "rbffd_batch_set_shape", "rbffd_batch_stats",
     "rbffd_error", "rbffd_batch_domain_times", "rbffd_batch_set_costs", "rbffd_adjoint_w",
     "rbffd_knn_masked", "rbffd_weights_dir", "rbffd_plan_set_neumann", "rbffd_plan_layout",
-    "rbffd_nodes_pds", "rbffd_nodes_pds_cap", "rbffd_weights_batch",
+    "rbffd_nodes_pds", "rbffd_nodes_pds_cap", "rbffd_weights_batch", "rbffd_transpose",
+    "rbffd_plan_set_wait", "rbffd_fp64_fma_rate",
 ]
 RBFFD_KNN_NOALLOC_MAX_NODES = 262144
 
@@ -114,6 +115,9 @@ def lib():
         "rbffd_nodes_pds": (I, [I, I, I, I, D, U64, P, P, I64, PI64, PI64, P]),
         "rbffd_nodes_pds_cap": (I, [I, I, D, PI64]),
         "rbffd_weights_batch": (I, [I, P, P, P, P, P, P, P, P, P, P, P]),
+        "rbffd_transpose": (I, [P, P]),
+        "rbffd_plan_set_wait": (I, [P, D, I]),
+        "rbffd_fp64_fma_rate": (I, [I64, PD, PD, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -246,11 +250,20 @@ def rbffd_knn_noalloc(xyz: torch.Tensor, centres: torch.Tensor, idx: torch.Tenso
 
     For callers that cannot allocate GPU memory while running: the library works in
     a fixed array of its own (N <= RBFFD_KNN_NOALLOC_MAX_NODES).  Calls that overlap
-    on the GPU share that array and race; serialise them."""
-    xyz = _dev(xyz, torch.float64, "xyz")
-    centres = _dev(centres, torch.int32, "centres")
-    if not (idx.is_cuda and idx.dtype == torch.int32 and idx.is_contiguous()):
-        raise ValueError("idx must be a contiguous int32 CUDA tensor [nc, n]")
+    on the GPU share that array and race; serialise them.  Nothing here copies or
+    allocates either: every tensor must already be contiguous, on one device, and
+    ``idx`` must have one row per centre."""
+    if xyz.dim() != 2 or centres.dim() != 1 or idx.dim() != 2:
+        raise ValueError("need xyz [d, N], centres [nc] and idx [nc, n]")
+    if idx.shape[0] != centres.numel() or not 1 <= idx.shape[1] <= 128:
+        raise ValueError(f"idx must be [{centres.numel()}, n] with 1 <= n <= 128, "
+                         f"got {list(idx.shape)}")
+    for t, dtype, name in ((xyz, torch.float64, "xyz"), (centres, torch.int32, "centres"),
+                           (idx, torch.int32, "idx")):
+        if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous {dtype} CUDA tensor")
+    if not (xyz.device == centres.device == idx.device):
+        raise ValueError("xyz, centres and idx must be on the same device")
     d, N = xyz.shape
     _check(lib().rbffd_knn_noalloc(_ptr(xyz), N, d, _ptr(centres), centres.numel(), idx.shape[1],
                                    _ptr(idx), _stream(xyz.device)))
@@ -315,6 +328,16 @@ def rbffd_error(u: torch.Tensor, ua: torch.Tensor):
     _check(lib().rbffd_error(_ptr(u), _ptr(ua), u.numel(), ctypes.byref(mx), ctypes.byref(mean),
                              _stream(u.device)))
     return mx.value, mean.value
+
+
+def rbffd_fp64_fma_rate(iters: int = 200_000, device="cuda"):
+    """Measured FP64 fused multiply-adds per second of the device (best of three
+    shapes, ``iters`` fmas per thread each), and the fastest shape's timed ms."""
+    rate = ctypes.c_double(0.0)
+    ms = ctypes.c_double(0.0)
+    _check(lib().rbffd_fp64_fma_rate(int(iters), ctypes.byref(rate), ctypes.byref(ms),
+                                     _stream(device)))
+    return rate.value, ms.value
 
 
 class Plan:
@@ -386,12 +409,15 @@ class Plan:
         _check(code, (RBFFD_OK, RBFFD_NOT_CONVERGED))
         return code, outer.value, inner.value, res.value
 
-    def adjoint_w(self, f, ckpt, every, lamK, K, dt):
+    def adjoint_w(self, f, ckpt, every, dLdu, K, dt):
         """Backward pass with the weight gradient from checkpoints ckpt [nseg, N] (caller
-        order, u^0, u^every, ...).  Returns (grad_w [NI, n], grad_f, grad_g, lam0)."""
+        order, u^0, u^every, ...) and dLdu = dL/du^K [N].
+        Returns (grad_w [NI, n], grad_f, grad_g, lam0)."""
         f = _dev(f, torch.float64, "f")
         ckpt = _dev(ckpt, torch.float64, "ckpt")
-        lamK = _dev(lamK, torch.float64, "lamK")
+        lamK = _dev(dLdu, torch.float64, "dLdu")
+        if lamK.numel() != self.N:
+            raise ValueError("dLdu must have one entry per node")
         gw = torch.empty((self.NI, self.n), dtype=torch.float64, device=self.device)
         gf = torch.empty(self.NI, dtype=torch.float64, device=self.device)
         gg = torch.empty(self.N, dtype=torch.float64, device=self.device)
@@ -431,6 +457,11 @@ class Plan:
         _check(lib().rbffd_plan_set_neumann(self.handle, nodes.numel(), _ptr(nodes), _ptr(idx),
                                             _ptr(w), idx.shape[1], _ptr(g), _stream(self.device)))
 
+    def set_wait(self, timeout_ms=0.0, held_arrivals=0):
+        """Timeout of the persistent launch's barrier waits (<= 0: default); held_arrivals
+        > 0 makes every barrier wait for arrivals that never come (tests the timeout)."""
+        _check(lib().rbffd_plan_set_wait(self.handle, float(timeout_ms), int(held_arrivals)))
+
     def set_dc(self, K_in, rho_in):
         _check(lib().rbffd_plan_set_dc(self.handle, int(K_in), float(rho_in)))
 
@@ -443,9 +474,16 @@ class Plan:
                                      ctypes.byref(dt), ctypes.byref(rho), _stream(self.device)))
         return dt.value, rho.value
 
-    def adjoint(self, lamK, K, dt, want_lam0=True):
-        """Reverse sweep of K steps.  Returns (grad_f [NI], grad_g [N], lam0 [NI] or None)."""
-        lamK = _dev(lamK, torch.float64, "lamK")
+    def transpose(self):
+        """Build the transposed interior operator now (else the first adjoint does)."""
+        _check(lib().rbffd_transpose(self.handle, _stream(self.device)))
+
+    def adjoint(self, dLdu, K, dt, want_lam0=True):
+        """Reverse sweep of K steps from dLdu = dL/du^K [N] (every node; boundary entries
+        add directly to grad_g).  Returns (grad_f [NI], grad_g [N], lam0 [NI] or None)."""
+        lamK = _dev(dLdu, torch.float64, "dLdu")
+        if lamK.numel() != self.N:
+            raise ValueError("dLdu must have one entry per node")
         gf = torch.empty(self.NI, dtype=torch.float64, device=self.device)
         gg = torch.empty(self.N, dtype=torch.float64, device=self.device)
         l0 = torch.empty(self.NI, dtype=torch.float64, device=self.device) if want_lam0 else None
@@ -638,15 +676,15 @@ class RBFFDExplicit(torch.autograd.Function):
         f, ckpt = ctx.saved_tensors
         plan = solver._plan
         grad_u = grad_u.contiguous()
-        lamK = grad_u[solver.interior.long()].contiguous()
         gw = None
         if ctx.needs_input_grad[2]:
-            gw, gf, gg, _ = plan.adjoint_w(f.contiguous(), ckpt, solver.every, lamK, solver.K,
+            gw, gf, gg, _ = plan.adjoint_w(f.contiguous(), ckpt, solver.every, grad_u, solver.K,
                                            solver.dt)
         else:
-            gf, gg, _ = plan.adjoint(lamK, solver.K, solver.dt, want_lam0=False)
-        grad_g = gg[solver.bnd] + grad_u[solver.bnd]
-        return gf, grad_g, gw, None
+            gf, gg, _ = plan.adjoint(grad_u, solver.K, solver.dt, want_lam0=False)
+        # grad_g holds dL/dg at the boundary nodes (direct term included); g is
+        # given in the order of the boundary nodes
+        return gf, gg[solver.bnd], gw, None
 
 
 def rbffd_plan_create(xyz, is_bnd, interior, idx, w, flags=0, seed=0) -> Plan:
@@ -665,8 +703,12 @@ def rbffd_stable_dt(plan: Plan, v0, iters=200, safety=1.05):
     return plan.stable_dt(v0, iters, safety)
 
 
-def rbffd_adjoint(plan: Plan, lamK, K, dt):
-    return plan.adjoint(lamK, K, dt)
+def rbffd_adjoint(plan: Plan, dLdu, K, dt):
+    return plan.adjoint(dLdu, K, dt)
+
+
+def rbffd_transpose(plan: Plan):
+    return plan.transpose()
 
 
 def monomial_count(d: int, m: int) -> int:

@@ -246,10 +246,12 @@ adjoint_step(const Transpose T, const int64_t NI, const double dt,
     }
 }
 
-// boundary columns: grad_g[node] = dt * sum_rows w_rc S_r
+// boundary columns: grad_g[node] = dt * sum_rows w_rc S_r + dLdu[node] (the
+// loss's direct dependence on u^K at a boundary node, where u^K = g)
 __global__ void adjoint_grad_g(const Transpose T, const int64_t NI, const int64_t N,
                                const double dt, const double* __restrict__ S,
-                               const int32_t* perm, double* grad_g) {
+                               const int32_t* perm, const double* __restrict__ dLdu,
+                               double* grad_g) {
     for (int64_t c = NI + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < N;
          c += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = c / SLICE, lane = c % SLICE;
@@ -258,7 +260,8 @@ __global__ void adjoint_grad_g(const Transpose T, const int64_t NI, const int64_
         double acc = 0.0;
         for (int j = 0; j < L; ++j)
             acc = __fma_rn(T.w[o + (int64_t)j * SLICE], S[T.row[o + (int64_t)j * SLICE]], acc);
-        grad_g[perm[c]] = __dmul_rn(dt, acc);
+        const int32_t node = perm[c];
+        grad_g[node] = __dadd_rn(__dmul_rn(dt, acc), dLdu[node]);
     }
 }
 
@@ -269,12 +272,13 @@ __global__ void adj_gather(const double* src, const int32_t* row_of_slot, int64_
         dst[p] = src[row_of_slot[p]];
 }
 
-// lambda^K (caller's interior-list order) into the placed order
-__global__ void adj_gather_placed(const double* src, const int32_t* row_of_slot,
-                                  const int32_t* colof, int64_t NI, double* dst) {
+// lambda^K = the interior entries of dL/du^K (caller's node order) into the
+// placed order
+__global__ void adj_gather_placed(const double* dLdu, const int32_t* perm, const int32_t* colof,
+                                  int64_t NI, double* dst) {
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < NI;
          q += (int64_t)gridDim.x * blockDim.x)
-        dst[q] = src[row_of_slot[colof[q]]];
+        dst[q] = dLdu[perm[colof[q]]];
 }
 
 // S and lambda^0 (placed order) out to the caller's order
@@ -443,10 +447,16 @@ static int build_transpose(rbffd_plan* p, cudaStream_t s) {
 
 using namespace rbffd;
 
-extern "C" int rbffd_adjoint(rbffd_plan* p, const double* lamK, int64_t K, double dt,
+extern "C" int rbffd_transpose(rbffd_plan* p, void* stream) {
+    clear_error();
+    RBFFD_ARG(p, "rbffd_transpose: NULL plan");
+    return build_transpose(p, as_stream(stream));
+}
+
+extern "C" int rbffd_adjoint(rbffd_plan* p, const double* dLdu, int64_t K, double dt,
                              double* grad_f, double* grad_g, double* lam0, void* stream) {
     clear_error();
-    RBFFD_ARG(p && lamK && grad_f && grad_g, "rbffd_adjoint: NULL argument");
+    RBFFD_ARG(p && dLdu && grad_f && grad_g, "rbffd_adjoint: NULL argument");
     RBFFD_ARG(K >= 0 && isfinite(dt), "rbffd_adjoint: bad K / dt");
     cudaStream_t s = as_stream(stream);
     int st = build_transpose(p, s);
@@ -454,14 +464,14 @@ extern "C" int rbffd_adjoint(rbffd_plan* p, const double* lamK, int64_t K, doubl
     Transpose& T = *p->tr;
     const int sms = device_sm_count();
     const unsigned G = (unsigned)sms * 8;
-    adj_gather_placed<<<G, 256, 0, s>>>(lamK, p->row_of_slot, T.colof, p->NI, T.lam[0]);
+    adj_gather_placed<<<G, 256, 0, s>>>(dLdu, p->perm, T.colof, p->NI, T.lam[0]);
     RBFFD_CHECK_CUDA(cudaMemsetAsync(T.S, 0, sizeof(double) * p->NI, s));
     const int64_t nsl_int = (p->NI + SLICE - 1) / SLICE;
     const unsigned grid = (unsigned)std::max<int64_t>(1, (nsl_int + 7) / 8);
     for (int64_t k = 0; k < K; ++k)
         adjoint_step<<<grid, 256, 0, s>>>(T, p->NI, dt, T.lam[k & 1], T.lam[(k + 1) & 1], T.S);
     RBFFD_CHECK_CUDA(cudaGetLastError());
-    adjoint_grad_g<<<G, 256, 0, s>>>(T, p->NI, p->N, dt, T.S, p->perm, grad_g);
+    adjoint_grad_g<<<G, 256, 0, s>>>(T, p->NI, p->N, dt, T.S, p->perm, dLdu, grad_g);
     adj_outputs<<<G, 256, 0, s>>>(T.S, T.lam[K & 1], p->row_of_slot, T.colof, p->perm, p->NI,
                                   dt, grad_f,
                                   grad_g, lam0);
@@ -470,10 +480,10 @@ extern "C" int rbffd_adjoint(rbffd_plan* p, const double* lamK, int64_t K, doubl
 }
 
 extern "C" int rbffd_adjoint_w(rbffd_plan* p, const double* f, const double* ckpt, int64_t every,
-                               const double* lamK, int64_t K, double dt, double* grad_w,
+                               const double* dLdu, int64_t K, double dt, double* grad_w,
                                double* grad_f, double* grad_g, double* lam0, void* stream) {
     clear_error();
-    RBFFD_ARG(p && f && ckpt && lamK && grad_w && grad_f && grad_g,
+    RBFFD_ARG(p && f && ckpt && dLdu && grad_w && grad_f && grad_g,
               "rbffd_adjoint_w: NULL argument");
     RBFFD_ARG(K >= 0 && every >= 1 && isfinite(dt), "rbffd_adjoint_w: bad K / every / dt");
     cudaStream_t s = as_stream(stream);
@@ -493,7 +503,7 @@ extern "C" int rbffd_adjoint_w(rbffd_plan* p, const double* f, const double* ckp
     RBFFD_CHECK_CUDA(cudaMemsetAsync(Gw, 0, sizeof(double) * (size_t)p->nslices * n * SLICE, s));
     // f in slot order for the replays; lambda^K in slot order
     adj_gather<<<G, 256, 0, s>>>(f, p->row_of_slot, NI, p->fs);
-    adj_gather_placed<<<G, 256, 0, s>>>(lamK, p->row_of_slot, T.colof, NI, T.lam[0]);
+    adj_gather_placed<<<G, 256, 0, s>>>(dLdu, p->perm, T.colof, NI, T.lam[0]);
     RBFFD_CHECK_CUDA(cudaMemsetAsync(T.S, 0, sizeof(double) * NI, s));
     const int64_t nseg = (K + every - 1) / every;
     const int64_t nsl_int = (NI + SLICE - 1) / SLICE;
@@ -514,7 +524,7 @@ extern "C" int rbffd_adjoint_w(rbffd_plan* p, const double* f, const double* ckp
         }
         RBFFD_CHECK_CUDA(cudaGetLastError());
     }
-    adjoint_grad_g<<<G, 256, 0, s>>>(T, NI, N, dt, T.S, p->perm, grad_g);
+    adjoint_grad_g<<<G, 256, 0, s>>>(T, NI, N, dt, T.S, p->perm, dLdu, grad_g);
     adj_outputs<<<G, 256, 0, s>>>(T.S, T.lam[cur], p->row_of_slot, T.colof, p->perm, NI, dt,
                                   grad_f,
                                   grad_g, lam0);

@@ -4,6 +4,8 @@
 // grid, then one block sums them in a fixed order.
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace rbffd {
@@ -85,5 +87,92 @@ extern "C" int rbffd_error(const double* u, const double* ua, int64_t N, double*
     RBFFD_CHECK_CUDA(cudaStreamSynchronize(s));
     if (h_max) *h_max = out[0];
     if (h_mean) *h_mean = out[1];
+    return RBFFD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// rbffd_fp64_fma_rate: the device's FP64 fused multiply-add rate, measured -
+// the roofline of the kernels the FP64 pipe binds (the explicit sweep at
+// larger stencils, the weight build).  Not part of the paper's method.
+// Every thread runs CH independent chains a <- fma(a, x, y), four fmas per
+// chain per loop iteration, so the pipe, not the chain latency or the loop,
+// sets the pace; the result is kept alive by a store that never happens (a
+// chain never reaches -1).  Shapes with 4, 8 and 16 chains per thread at the
+// largest resident grid are timed and the fastest kept.
+// ---------------------------------------------------------------------------
+namespace rbffd {
+
+static __device__ double g_fma_sink;
+
+template <int CH>
+__global__ void __launch_bounds__(256) fp64_fma_chains(long long iters) {
+    double a[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) a[c] = 1e-3 * (double)(threadIdx.x + c);
+    const double x = 0.9999999999, y = 1e-12;
+    for (long long i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int c = 0; c < CH; ++c) a[c] = __fma_rn(a[c], x, y);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) s = __dadd_rn(s, a[c]);
+    if (s == -1.0) g_fma_sink = s;
+}
+
+template <int CH>
+static cudaError_t time_fma_shape(long long fmas_per_thread, cudaStream_t s, double* rate,
+                                  float* ms_out) {
+    int per_sm = 0;
+    cudaError_t e =
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fp64_fma_chains<CH>, 256, 0);
+    if (e != cudaSuccess) return e;
+    const int grid = device_sm_count() * std::max(1, per_sm);
+    const long long iters = std::max<long long>(1, fmas_per_thread / (4 * CH));
+    cudaEvent_t e0, e1;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess) return e;
+    if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return e;
+    }
+    fp64_fma_chains<CH><<<grid, 256, 0, s>>>(std::max<long long>(1, iters / 16));   // warm-up
+    cudaEventRecord(e0, s);
+    fp64_fma_chains<CH><<<grid, 256, 0, s>>>(iters);
+    cudaEventRecord(e1, s);
+    e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e == cudaSuccess) {
+        *rate = (double)grid * 256.0 * 4.0 * CH * (double)iters / (ms * 1e-3);
+        *ms_out = ms;
+    }
+    return e;
+}
+
+}  // namespace rbffd
+
+extern "C" int rbffd_fp64_fma_rate(int64_t iters, double* h_fma_per_s, double* h_ms,
+                                   void* stream) {
+    using namespace rbffd;
+    clear_error();
+    RBFFD_ARG(iters >= 1 && iters <= (int64_t(1) << 32) && h_fma_per_s,
+              "rbffd_fp64_fma_rate: bad argument");
+    cudaStream_t s = as_stream(stream);
+    // `iters` fmas per thread in each timed launch
+    double best = 0.0, r = 0.0;
+    float best_ms = 0.f, ms = 0.f;
+    RBFFD_CHECK_CUDA(time_fma_shape<4>(iters, s, &r, &ms));
+    if (r > best) { best = r; best_ms = ms; }
+    RBFFD_CHECK_CUDA(time_fma_shape<8>(iters, s, &r, &ms));
+    if (r > best) { best = r; best_ms = ms; }
+    RBFFD_CHECK_CUDA(time_fma_shape<16>(iters, s, &r, &ms));
+    if (r > best) { best = r; best_ms = ms; }
+    *h_fma_per_s = best;
+    if (h_ms) *h_ms = best_ms;
     return RBFFD_OK;
 }

@@ -8,6 +8,7 @@
 namespace rbffd {
 
 static constexpr int SLICE = 32;   // rows per slice = one warp
+static constexpr int GRAPH_LOG2 = 5;   // the longest captured graph: 32 step launches
 
 // Device control block of a step loop.  Step kernels read their parameters
 // here (so a captured graph can be replayed with new ones) and the last block
@@ -23,7 +24,8 @@ struct StepCtrl {
     long long k;                 // steps taken so far
     long long max_steps;
     int done;                    // 0 running, 1 converged, 2 cap, 3 non-finite, 4 diverged, 5 timeout
-    int pad;
+    int held;                    // persistent barrier: arrivals it waits for beyond the grid's
+    long long spin_limit;        // persistent barrier: clock cycles a wait may last
     double dt;
     double tol;
     double res_first;            // R_0 of this run (divergence test)
@@ -68,10 +70,13 @@ struct rbffd_plan {
     rbffd::StepCtrl* ctrl = nullptr;
     int64_t dc_K_in = 20000;
     double dc_rho_in = 1e-3;
-    // CUDA graphs of a chunk of step launches (built on first use)
-    void* graph64 = nullptr;
-    void* graph32 = nullptr;
-    int graph_chunk = 0;
+    // CUDA graphs of step launches, per mode (0 FP64 sweep, 1 FP32 inner
+    // sweep) and length 2^b, b = 0..GRAPH_LOG2; built on first use
+    void* graphs[2][6] = {};
+    // persistent barrier: how long a wait may last, and (to test that path)
+    // arrivals withheld from every step's barrier
+    long long spin_limit = 0;
+    int held_arrivals = 0;
     int grid_steps = 0;             // blocks per SM of auxiliary sweeps (defect, power)
     // tuned launch shape per mode (0 FP64 sweep, 1 FP32 inner sweep)
     bool tuned[2] = {false, false};

@@ -15,7 +15,7 @@
 namespace rbffd {
 
 static constexpr int STEP_THREADS = 256;
-static constexpr long long SPIN_LIMIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
+static constexpr long long SPIN_LIMIT_CYCLES = 4000000000LL;   // default: ~2 s at 2 GHz
 
 // ------------------------------------------------------------- utilities
 __device__ __forceinline__ unsigned long long dbits(double x) {
@@ -371,14 +371,17 @@ __global__ void __launch_bounds__(STEP_THREADS, MINB) step_kernel(StepArgs A, St
 // arrive reads the step's max, applies the stop rule, clears the next-but-one
 // residual slot, and publishes ((k + 1) << 4) | decision in one word, which
 // the other blocks poll - so the decision needs no second round trip.  Waits
-// give up after SPIN_LIMIT_CYCLES (decision DONE_TIMEOUT).  Returns the
+// give up after `spin` clock cycles (decision DONE_TIMEOUT).  `held` arrivals
+// are added to each step's target: 0 in every solve, except a test of the
+// timeout path, where no step's barrier can then complete.  Returns the
 // decision in every thread.
 static __device__ int step_end(StepCtrl* c, long long k, long long k0, long long kmax,
-                               unsigned long long m) {
+                               unsigned long long m, long long spin, int held) {
     __shared__ int s_dec;
     if (threadIdx.x == 0) {
         atomicMax(&c->res[k % 3], m);
-        const unsigned long long target = (unsigned long long)(k - k0 + 1) * gridDim.x;
+        const unsigned long long target =
+            (unsigned long long)(k - k0 + 1) * gridDim.x + (unsigned long long)held;
         // the arrival releases this block's iterate writes and max, and (for
         // the last block) acquires every other block's
         const unsigned long long t = atom_add_acq_rel(&c->arrivals, 1ull) + 1ull;
@@ -409,7 +412,7 @@ static __device__ int step_end(StepCtrl* c, long long k, long long k0, long long
                     dn = (int)(v & 15ull);
                     break;
                 }
-                if (clock64() - t0 > SPIN_LIMIT_CYCLES) {
+                if (clock64() - t0 > spin) {
                     atomicExch(&c->done, DONE_TIMEOUT);
                     dn = DONE_TIMEOUT;
                     break;
@@ -425,23 +428,29 @@ static __device__ int step_end(StepCtrl* c, long long k, long long k0, long long
 // persistent mode: all steps in one cooperative launch
 template <int NN, int MODE, int MINB>
 __global__ void __launch_bounds__(STEP_THREADS, MINB) persistent_kernel(StepArgs A, StepCtrl* c) {
-    __shared__ long long s_k, s_max;
+    __shared__ long long s_k, s_max, s_spin;
+    __shared__ int s_held;
     __shared__ double s_dt;
     if (threadIdx.x == 0) {
         volatile StepCtrl* vc = c;
         s_k = vc->k;
         s_max = vc->max_steps;
         s_dt = vc->dt;
+        constexpr long long dflt = SPIN_LIMIT_CYCLES;
+        const long long lim = vc->spin_limit;
+        s_spin = lim > 0 ? lim : dflt;
+        s_held = vc->held;
     }
     __syncthreads();
     const double dt = s_dt;
-    const long long kmax = s_max, k0 = s_k;
+    const long long kmax = s_max, k0 = s_k, spin = s_spin;
+    const int held = s_held;
     const int64_t warp = step_warp(A);
     const int64_t nw = (int64_t)gridDim.x * (STEP_THREADS / 32);
     for (long long k = k0; k < kmax; ++k) {
         unsigned long long m = step_rows<NN, MODE, true>(A, (int)(k & 1), dt, (float)dt, warp, nw);
         m = block_max_bits(m);
-        if (step_end(c, k, k0, kmax, m) != DONE_RUNNING) return;
+        if (step_end(c, k, k0, kmax, m, spin, held) != DONE_RUNNING) return;
     }
 }
 

@@ -496,6 +496,15 @@ static StepArgs make_args(const rbffd_plan* p) {
     return A;
 }
 
+static void drop_graphs(rbffd_plan* p) {
+    for (auto& per_mode : p->graphs)
+        for (void*& g : per_mode)
+            if (g) {
+                cudaGraphExecDestroy((cudaGraphExec_t)g);
+                g = nullptr;
+            }
+}
+
 static void free_plan(rbffd_plan* p) {
     if (!p) return;
     void* bufs[] = {p->perm, p->inv, p->row_of_slot, p->w64, p->w32, p->col, p->u[0], p->u[1],
@@ -503,10 +512,9 @@ static void free_plan(rbffd_plan* p) {
                     p->nw, p->ng, p->ng0, p->uN, p->col16, p->sbase};
     for (void* b : bufs)
         if (b) cudaFree(b);
-    if (p->graph64) cudaGraphExecDestroy((cudaGraphExec_t)p->graph64);
+    drop_graphs(p);
     for (void* e : p->ev)
         if (e) cudaEventDestroy((cudaEvent_t)e);
-    if (p->graph32) cudaGraphExecDestroy((cudaGraphExec_t)p->graph32);
     free_transpose(p);
     delete p;
 }
@@ -537,14 +545,19 @@ static int persistent_grid(StepFn fn, const rbffd_plan* p) {
     return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sms, need));
 }
 
-// reset the control block for a run of at most max_steps steps
-static int ctrl_reset(rbffd_plan* p, double dt, double tol, long long max_steps, cudaStream_t s) {
+// reset the control block for a run of at most max_steps steps; `held`:
+// arrivals the persistent barrier waits for beyond the grid's (0 but in a
+// test of the timeout path, rbffd_plan_set_wait)
+static int ctrl_reset(rbffd_plan* p, double dt, double tol, long long max_steps, cudaStream_t s,
+                      int held = 0) {
     StepCtrl h;
     memset(&h, 0, sizeof(h));
     h.max_steps = max_steps;
     h.dt = dt;
     h.tol = tol;
     h.done = max_steps <= 0 ? DONE_CAP : DONE_RUNNING;
+    h.held = held;
+    h.spin_limit = p->spin_limit;
     RBFFD_CHECK_CUDA(cudaMemcpyAsync(p->ctrl, &h, sizeof(h), cudaMemcpyHostToDevice, s));
     return RBFFD_OK;
 }
@@ -683,11 +696,11 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
     return RBFFD_OK;
 }
 
-// build (once) a graph of `chunk` step launches of the given mode
-static int ensure_graph(rbffd_plan* p, int mode, cudaStream_t s) {
-    void** slot = mode == MODE_SWEEP64 ? &p->graph64 : &p->graph32;
-    if (*slot) return RBFFD_OK;
+// build (once) a graph of 2^b step launches of the given mode
+static int ensure_graph(rbffd_plan* p, int mode, int b, cudaStream_t s) {
     const int mi = mode == MODE_SWEEP64 ? 0 : 1;
+    void** slot = &p->graphs[mi][b];
+    if (*slot) return RBFFD_OK;
     int st = tune_shape(p, mode, s);
     if (st) return st;
     RBFFD_CHECK_CUDA(cudaStreamSynchronize(s));
@@ -701,7 +714,7 @@ static int ensure_graph(rbffd_plan* p, int mode, cudaStream_t s) {
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         const unsigned ng = (unsigned)std::max<int64_t>(1, std::min<int64_t>((p->NN + 255) / 256, 1024));
-        for (int i = 0; i < p->graph_chunk; ++i) {
+        for (int i = 0; i < (1 << b); ++i) {
             if (mode == MODE_SWEEP64 && p->NN > 0) {
                 neumann_update<<<ng, 256, 0, cs>>>(p->ncol, p->nw, p->ng, p->NN, p->nn, p->u[0],
                                                    p->u[1], p->uN, p->ctrl);
@@ -734,7 +747,7 @@ static int ensure_graph(rbffd_plan* p, int mode, cudaStream_t s) {
 static int prepare_mode(rbffd_plan* p, int mode, double dt, double tol, long long max_steps,
                         cudaStream_t s) {
     const int mi = mode == MODE_SWEEP64 ? 0 : 1;
-    const bool graph_missing = mode == MODE_SWEEP64 ? !p->graph64 : !p->graph32;
+    const bool graph_missing = !p->graphs[mi][GRAPH_LOG2];
     if (p->tuned[mi] && (p->persist[mi] || !graph_missing)) return RBFFD_OK;
     Scratch save;
     RBFFD_CHECK_CUDA(save.alloc(sizeof(double) * 2 * p->N + sizeof(float) * 2 * p->N, s));
@@ -750,7 +763,7 @@ static int prepare_mode(rbffd_plan* p, int mode, double dt, double tol, long lon
     int st = tune_shape(p, mode, s);
     if (st) return st;
     if (!p->persist[mi]) {
-        st = ensure_graph(p, mode, s);
+        st = ensure_graph(p, mode, GRAPH_LOG2, s);
         if (st) return st;
     }
     RBFFD_CHECK_CUDA(cudaMemcpyAsync(p->u[0], sv, sizeof(double) * p->N, cudaMemcpyDeviceToDevice, s));
@@ -758,14 +771,14 @@ static int prepare_mode(rbffd_plan* p, int mode, double dt, double tol, long lon
     RBFFD_CHECK_CUDA(cudaMemcpyAsync(p->e[0], se, sizeof(float) * p->N, cudaMemcpyDeviceToDevice, s));
     RBFFD_CHECK_CUDA(cudaMemcpyAsync(p->e[1], se + p->N, sizeof(float) * p->N, cudaMemcpyDeviceToDevice, s));
     RBFFD_CHECK_CUDA(cudaMemcpyAsync(p->d32, saved32.p, sizeof(float) * p->NI, cudaMemcpyDeviceToDevice, s));
-    return ctrl_reset(p, dt, tol, max_steps, s);
+    return ctrl_reset(p, dt, tol, max_steps, s, p->held_arrivals);
 }
 
 // run the step loop of `mode` until the control block says done.
 // Reads back done / k / res_last.
 static int run_steps(rbffd_plan* p, int mode, double dt, double tol, long long max_steps,
                      cudaStream_t s, long long* steps, double* res, int* done) {
-    int st = ctrl_reset(p, dt, tol, max_steps, s);
+    int st = ctrl_reset(p, dt, tol, max_steps, s, p->held_arrivals);
     if (st) return st;
     StepCtrl h;
     if (max_steps > 0) {
@@ -784,21 +797,34 @@ static int run_steps(rbffd_plan* p, int mode, double dt, double tol, long long m
             RBFFD_CHECK_CUDA(cudaEventRecord((cudaEvent_t)p->ev[1], s));
             p->last_launches += 1;
         } else {
-            cudaGraphExec_t ex = (cudaGraphExec_t)(mode == MODE_SWEEP64 ? p->graph64 : p->graph32);
-            long long launched = 0;
-            // replay chunks; check the device decision every `per_check` chunks
-            long long per_check = std::max<long long>(1, std::min<long long>(
-                                       64, (max_steps + p->graph_chunk - 1) / p->graph_chunk));
+            // max_steps launches exactly: chunks of 2^GRAPH_LOG2 launches, then one
+            // graph per set bit of the remainder, longest first
+            const long long chunk = 1LL << GRAPH_LOG2;
+            const long long full = max_steps >> GRAPH_LOG2;
+            const long long rem = max_steps & (chunk - 1);
+            for (int b = 0; b < GRAPH_LOG2; ++b)
+                if ((rem >> b) & 1) {
+                    st = ensure_graph(p, mode, b, s);
+                    if (st) return st;
+                }
+            std::vector<int> tail;
+            for (int b = GRAPH_LOG2 - 1; b >= 0; --b)
+                if ((rem >> b) & 1) tail.push_back(b);
+            const long long ngraphs = full + (long long)tail.size();
+            long long launched = 0, g = 0;
+            // check the device decision every `per_check` graphs
+            const long long per_check = std::max<long long>(1, std::min<long long>(64, full));
             RBFFD_CHECK_CUDA(cudaEventRecord((cudaEvent_t)p->ev[0], s));
             for (;;) {
-                for (long long i = 0; i < per_check && launched < max_steps; ++i) {
-                    RBFFD_CHECK_CUDA(cudaGraphLaunch(ex, s));
-                    launched += p->graph_chunk;
+                for (long long i = 0; i < per_check && g < ngraphs; ++i, ++g) {
+                    const int b = g < full ? GRAPH_LOG2 : tail[(size_t)(g - full)];
+                    RBFFD_CHECK_CUDA(cudaGraphLaunch((cudaGraphExec_t)p->graphs[mi][b], s));
+                    launched += 1LL << b;
                 }
                 RBFFD_CHECK_CUDA(cudaEventRecord((cudaEvent_t)p->ev[1], s));
                 RBFFD_CHECK_CUDA(cudaMemcpyAsync(&h, p->ctrl, sizeof(h), cudaMemcpyDeviceToHost, s));
                 RBFFD_CHECK_CUDA(cudaStreamSynchronize(s));
-                if (h.done != DONE_RUNNING || launched >= max_steps) break;
+                if (h.done != DONE_RUNNING || g >= ngraphs) break;
             }
             p->last_launches += launched;
         }
@@ -892,7 +918,6 @@ extern "C" int rbffd_plan_create(const double* xyz, const uint8_t* is_bnd, int64
     p->n = n;
     p->flags = flags;
     p->nslices = (NI + SLICE - 1) / SLICE;
-    p->graph_chunk = 32;
     p->grid_steps = 2;
     const size_t ell = (size_t)p->nslices * n * SLICE;
     cudaError_t e = cudaSuccess;
@@ -1052,6 +1077,23 @@ extern "C" int rbffd_plan_set_dc(rbffd_plan* p, int64_t K_in, double rho_in) {
     RBFFD_ARG(p && K_in >= 1 && rho_in >= 0.0, "rbffd_plan_set_dc: bad argument");
     p->dc_K_in = K_in;
     p->dc_rho_in = rho_in;
+    return RBFFD_OK;
+}
+
+extern "C" int rbffd_plan_set_wait(rbffd_plan* p, double timeout_ms, int held_arrivals) {
+    clear_error();
+    RBFFD_ARG(p && isfinite(timeout_ms) && timeout_ms <= 60000.0 && held_arrivals >= 0 &&
+                  held_arrivals <= 1024,
+              "rbffd_plan_set_wait: bad argument");
+    long long cycles = 0;
+    if (timeout_ms > 0.0) {
+        int dev = 0, khz = 0;
+        RBFFD_CHECK_CUDA(cudaGetDevice(&dev));
+        RBFFD_CHECK_CUDA(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
+        cycles = std::max<long long>(1, (long long)(timeout_ms * (double)khz));
+    }
+    p->spin_limit = cycles;
+    p->held_arrivals = held_arrivals;
     return RBFFD_OK;
 }
 
@@ -1312,14 +1354,7 @@ extern "C" int rbffd_plan_set_neumann(rbffd_plan* p, int64_t NN, const int32_t* 
     // captured graphs include (or not) the Neumann phase: capture again; the
     // launch modes may change with it (plans with Neumann nodes replay
     // graphs), so the shapes are tuned again too
-    if (p->graph64) {
-        cudaGraphExecDestroy((cudaGraphExec_t)p->graph64);
-        p->graph64 = nullptr;
-    }
-    if (p->graph32) {
-        cudaGraphExecDestroy((cudaGraphExec_t)p->graph32);
-        p->graph32 = nullptr;
-    }
+    drop_graphs(p);
     for (int mi = 0; mi < 2; ++mi) {
         p->tuned[mi] = false;
         p->persist[mi] = false;

@@ -64,3 +64,20 @@ def test_oracle_and_library_share_no_code():
         if os.path.isfile(f) and f.endswith((".cu", ".cuh", ".py")):
             txt = open(f).read()
             assert "import oracle" not in txt and "oracle/" not in txt, f
+
+
+def test_noalloc_binding_rejects_a_short_output_before_any_call():
+    """rbffd_knn_noalloc writes one row of idx per centre: a caller's buffer with
+    too few rows, or of the wrong rank, is refused in the binding (no launch)."""
+    torch = pytest.importorskip("torch")
+    import paper_2502_12878_gb300 as rb
+    xyz = torch.zeros((2, 100), dtype=torch.float64)
+    centres = torch.arange(10, dtype=torch.int32)
+    for bad in (torch.zeros((9, 12), dtype=torch.int32),        # one row short
+                torch.zeros((10, 129), dtype=torch.int32),      # n above 128
+                torch.zeros(120, dtype=torch.int32)):           # not [nc, n]
+        with pytest.raises(ValueError):
+            rb.rbffd_knn_noalloc(xyz, centres, bad)
+    # right shape, but host tensors: refused too (never copied to the device)
+    with pytest.raises(ValueError, match="CUDA"):
+        rb.rbffd_knn_noalloc(xyz, centres, torch.zeros((10, 12), dtype=torch.int32))

@@ -239,6 +239,39 @@ def test_sweep_parity_fixed_steps(rb, orc, d, Kg, m, flags, name):
     plan.destroy()
 
 
+# every stencil size with a kernel of its own (n fixed at compile time), in both
+# launch modes: 2D m = 1 for n = 6 (= 2M), m = 2 for n = 12..57, 3D m = 4 for 70, 71
+NN_CASES = [(2, 1, 6)] + [(2, 2, n) for n in (12, 13, 16, 20, 24, 30, 31, 40, 48, 56, 57)] + \
+           [(3, 4, 70), (3, 4, 71)]
+
+
+@pytest.mark.parametrize("d,m,n", NN_CASES)
+def test_sweep_parity_every_compiled_stencil_size(rb, orc, d, m, n):
+    """FP64 sweeps (graph and persistent launches) and a defect correction with FP32
+    inner sweeps, at each stencil size that has a specialised kernel; 529 interior
+    rows in 2D (16 full slices and a ragged one), 512 in 3D."""
+    p = build(orc, d, 24 if d == 2 else 9, m, seed=48, n=n)
+    dt = _dt(orc, p)
+    K = 100
+    ou, os_, ores, _ = orc.solve_explicit(p.w, p.idx, p.interior, p.f, p.u0, dt, K, 0.0)
+    for flags in (0, 16):
+        plan = _plan(rb, p, flags)
+        u = T(p.u0)
+        code, steps, res = plan.solve_explicit(T(p.f), u, dt, K, 0.0)
+        assert steps == os_ == K
+        assert np.max(np.abs(H(u) - ou)) <= 1e-12 * np.max(np.abs(ou)), (n, flags)
+        assert res == pytest.approx(ores, rel=1e-12)
+        plan.destroy()
+    args = (dt, 1e-7, 3, 400, 1e-3)
+    du, oo, oi, _, ost = orc.solve_dc(p.w, p.idx, p.interior, p.f, p.u0, *args)
+    plan = _plan(rb, p)
+    u = T(p.u0)
+    code, outer, inner, res = plan.solve_dc(T(p.f), u, *args)
+    assert (outer, inner) == (oo, oi)
+    assert np.max(np.abs(H(u) - du)) <= 1e-12 * np.max(np.abs(du))
+    plan.destroy()
+
+
 def test_sweep_stop_rule_matches(rb, orc):
     p = build(orc, 2, 24, 2, seed=42)
     dt = _dt(orc, p)
@@ -365,14 +398,70 @@ def test_adjoint_parity(rb, orc):
     p = build(orc, 2, 25, 4, seed=71)
     dt = _dt(orc, p)
     K = 200
-    lamK = np.zeros(p.NI)
+    dLdu = np.zeros(p.N)
     sens = gen.sensors(p.NI, 40, 2)
-    lamK[sens] = gen.random_vector(40, 3)
-    gf, gg, l0 = orc.adjoint(p.w, p.idx, p.interior, p.N, lamK, K, dt)
+    dLdu[p.interior[sens]] = gen.random_vector(40, 3)
+    gf, gg, l0 = orc.adjoint(p.w, p.idx, p.interior, p.N, dLdu, K, dt)
     plan = _plan(rb, p)
-    g_f, g_g, g_l0 = plan.adjoint(T(lamK), K, dt)
+    plan.transpose()
+    plan.transpose()                  # a second call keeps the built transpose
+    g_f, g_g, g_l0 = plan.adjoint(T(dLdu), K, dt)
     for a, b in ((H(g_f), gf), (H(g_g), gg), (H(g_l0), l0)):
         assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(b))
+    plan.destroy()
+
+
+def test_adjoint_with_boundary_sensors(rb, orc):
+    """A loss that also observes boundary nodes: dL/dg gets the direct term inside
+    the library (rbffd_adjoint through the C ABI), against the oracle and against
+    central differences of the GPU forward solve (the loss is quadratic in f, g)."""
+    import ctypes
+    p = build(orc, 2, 22, 4, seed=74)
+    dt = _dt(orc, p)
+    K = 80
+    bnd = np.nonzero(p.is_bnd)[0]
+    sens = gen.sensors(p.NI, 30, 7)
+    bsens = bnd[::4]
+    g = p.u0[bnd] + 0.1 * gen.random_vector(len(bnd), 8)
+    uobs = p.ua[p.interior][sens]
+    bobs = gen.random_vector(len(bsens), 9)
+    plan = _plan(rb, p)
+
+    def forward(f, gb):
+        u = p.u0.copy()
+        u[bnd] = gb
+        u = T(u)
+        plan.solve_explicit(T(f), u, dt, K, 0.0)
+        return H(u)
+
+    def loss(f, gb):
+        u = forward(f, gb)
+        return np.sum((u[p.interior][sens] - uobs) ** 2) + np.sum((u[bsens] - bobs) ** 2)
+
+    uK = forward(p.f, g)
+    dLdu = np.zeros(p.N)
+    dLdu[p.interior[sens]] = 2 * (uK[p.interior][sens] - uobs)
+    dLdu[bsens] = 2 * (uK[bsens] - bobs)
+    gf, gg, l0 = orc.adjoint(p.w, p.idx, p.interior, p.N, dLdu, K, dt)
+    L = rb.lib()
+    d_dLdu = T(dLdu)
+    g_f = torch.empty(p.NI, dtype=torch.float64, device=DEV)
+    g_g = torch.empty(p.N, dtype=torch.float64, device=DEV)
+    code = L.rbffd_adjoint(plan.handle, rb._ptr(d_dLdu), K, dt, rb._ptr(g_f), rb._ptr(g_g),
+                           None, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert code == rb.RBFFD_OK
+    torch.cuda.synchronize()
+    for a, b in ((H(g_f), gf), (H(g_g), gg)):
+        assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(b))
+    assert np.all(H(g_g)[p.interior] == 0)
+    rng = np.random.default_rng(3)
+    for _ in range(4):
+        vf = rng.standard_normal(p.NI)
+        vg = rng.standard_normal(len(bnd))
+        eps = 1e-3
+        fd = (loss(p.f + eps * vf, g + eps * vg) - loss(p.f - eps * vf, g - eps * vg)) / (2 * eps)
+        an = H(g_f) @ vf + H(g_g)[bnd] @ vg
+        assert abs(fd - an) <= 1e-7 * max(abs(an), 1e-12)
     plan.destroy()
 
 
@@ -411,8 +500,9 @@ def test_adjoint_w_parity_and_checkpoint_invariance(rb, orc):
     p = build(orc, 2, 18, 4, seed=72)
     dt = _dt(orc, p)
     K = 60
-    lamK = np.zeros(p.NI)
-    lamK[gen.sensors(p.NI, 20, 3)] = gen.random_vector(20, 4)
+    lamK = np.zeros(p.N)
+    lamK[p.interior[gen.sensors(p.NI, 20, 3)]] = gen.random_vector(20, 4)
+    lamK[np.nonzero(p.is_bnd)[0][::5]] = gen.random_vector(len(np.nonzero(p.is_bnd)[0][::5]), 5)
     gw, gf, gg, l0 = orc.adjoint_w(p.w, p.idx, p.interior, p.f, p.u0, lamK, K, dt)
     plan = _plan(rb, p)
     results = []
@@ -449,13 +539,71 @@ def test_autograd_function_matches_oracle(rb, orc):
     g = T(p.u0[bnd]).requires_grad_(True)
     w = T(p.w).requires_grad_(True)
     uK = solver(f, g, w)
-    loss = ((uK[T(p.interior).long()[T(sens).long()]] - T(uobs)) ** 2).sum()
+    bsens = bnd[::3]                 # boundary nodes observed too (u^K = g there)
+    bobs = gen.random_vector(len(bsens), 11)
+    loss = ((uK[T(p.interior).long()[T(sens).long()]] - T(uobs)) ** 2).sum() + \
+        ((uK[T(bsens).long()] - T(bobs)) ** 2).sum()
     loss.backward()
-    # oracle: forward, lambda^K, then the weight-aware adjoint
+    # oracle: forward, dL/du^K, then the weight-aware adjoint
     ou, *_ = orc.solve_explicit(p.w, p.idx, p.interior, p.f, p.u0, dt, K, 0.0)
     assert np.max(np.abs(H(uK.detach()) - ou)) <= 1e-12 * np.max(np.abs(ou))
-    lamK = np.zeros(p.NI)
-    lamK[sens] = 2 * (ou[p.interior][sens] - uobs)
+    lamK = np.zeros(p.N)
+    lamK[p.interior[sens]] = 2 * (ou[p.interior][sens] - uobs)
+    lamK[bsens] = 2 * (ou[bsens] - bobs)
     gw, gf, gg, _ = orc.adjoint_w(p.w, p.idx, p.interior, p.f, p.u0, lamK, K, dt)
     for a, b in ((f.grad, gf), (g.grad, gg[bnd]), (w.grad, gw)):
         assert np.max(np.abs(H(a) - b)) <= 1e-12 * np.max(np.abs(b))
+
+
+# ------------------------------------------------------------------ bounded waits
+def test_persistent_barrier_wait_runs_out(rb, orc):
+    """The persistent launch's grid barrier is a bounded wait.  With one arrival
+    withheld (a failure injected on the host: the barrier waits for a block that
+    does not exist) every block gives up after the 20 ms limit, the solve returns
+    RBFFD_ERR_TIMEOUT and the context stays usable: the same plan then solves
+    normally, bit-identical to the oracle."""
+    import time
+    p = build(orc, 2, 30, 4, seed=49)
+    dt = _dt(orc, p)
+    plan = _plan(rb, p, rb.RBFFD_LAUNCH_PERSISTENT)
+    plan.solve_explicit(T(p.f), T(p.u0), dt, 5, 0.0)          # tunes, no waits run out
+    plan.set_wait(20.0, 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with pytest.raises(rb.RbffdError) as ei:
+        plan.solve_explicit(T(p.f), T(p.u0), dt, 100, 0.0)
+    el = time.perf_counter() - t0
+    assert ei.value.code == rb.RBFFD_ERR_TIMEOUT
+    assert el < 5.0                                           # gave up, did not hang
+    # FP32 inner steps of defect correction: the same barrier, the same outcome
+    with pytest.raises(rb.RbffdError) as ei:
+        plan.solve_dc(T(p.f), T(p.u0), dt, 0.0, 1, 50, 0.0)
+    assert ei.value.code == rb.RBFFD_ERR_TIMEOUT
+    plan.set_wait(0.0, 0)
+    ou, *_ = orc.solve_explicit(p.w, p.idx, p.interior, p.f, p.u0, dt, 100, 0.0)
+    u = T(p.u0)
+    code, steps, res = plan.solve_explicit(T(p.f), u, dt, 100, 0.0)
+    assert steps == 100
+    assert np.max(np.abs(H(u) - ou)) <= 1e-12 * np.max(np.abs(ou))
+    plan.destroy()
+
+
+def test_graph_replays_launch_exactly_the_steps_asked(rb, orc):
+    """Graph mode replays 32-launch chunks and then one graph per set bit of the
+    remainder, so a run of K steps launches K step kernels (no early-exit tail)
+    besides the solve's fixed few (gathers of f and u, scatter of u)."""
+    p = build(orc, 2, 20, 2, seed=50)
+    dt = _dt(orc, p)
+    plan = _plan(rb, p)
+    extra = set()
+    for K in (1, 31, 32, 33, 200, 77):
+        ou, *_ = orc.solve_explicit(p.w, p.idx, p.interior, p.f, p.u0, dt, K, 0.0)
+        u = T(p.u0)
+        code, steps, res = plan.solve_explicit(T(p.f), u, dt, K, 0.0)
+        ms, loop_steps, launches, shape = plan.stats()
+        assert steps == loop_steps == K
+        assert shape[1] != 0                     # the default plan replays graphs
+        extra.add(launches - K)
+        assert np.max(np.abs(H(u) - ou)) <= 1e-12 * np.max(np.abs(ou))
+    assert len(extra) == 1 and 0 <= extra.pop() <= 4
+    plan.destroy()

@@ -150,7 +150,9 @@ def test_adjoint_matches_dense_reverse_sweep_and_fd(orc):
     uK = forward(p.f, g)
     lamK = np.zeros(p.NI)
     lamK[sens] = 2 * (uK[sens] - uobs)
-    gf, gg, l0 = orc.adjoint(p.w, p.idx, p.interior, p.N, lamK, K, dt)
+    dLdu = np.zeros(p.N)
+    dLdu[p.interior] = lamK
+    gf, gg, l0 = orc.adjoint(p.w, p.idx, p.interior, p.N, dLdu, K, dt)
     # dense reverse sweep
     lam, S = lamK.copy(), np.zeros(p.NI)
     for _ in range(K):
@@ -205,7 +207,9 @@ def test_weight_gradient_matches_dense_reverse_sweep_and_fd(orc):
     uK, U = forward(p.w)
     lamK = np.zeros(p.NI)
     lamK[sens] = 2 * (uK[p.interior][sens] - uobs)
-    gw, gf, gg, l0 = orc.adjoint_w(p.w, p.idx, p.interior, p.f, p.u0, lamK, K, dt)
+    dLdu = np.zeros(p.N)
+    dLdu[p.interior] = lamK
+    gw, gf, gg, l0 = orc.adjoint_w(p.w, p.idx, p.interior, p.f, p.u0, dLdu, K, dt)
     # dense reverse sweep
     lam = lamK.copy()
     ref = np.zeros_like(p.w)
@@ -214,7 +218,7 @@ def test_weight_gradient_matches_dense_reverse_sweep_and_fd(orc):
         lam = lam + dt * (WII.T @ lam)
     np.testing.assert_allclose(gw, ref, rtol=1e-11, atol=1e-13 * np.abs(ref).max())
     # the f/g gradients and lambda^0 equal the f/g-only adjoint's
-    gf2, gg2, l02 = orc.adjoint(p.w, p.idx, p.interior, p.N, lamK, K, dt)
+    gf2, gg2, l02 = orc.adjoint(p.w, p.idx, p.interior, p.N, dLdu, K, dt)
     assert np.array_equal(gf, gf2) and np.array_equal(gg, gg2) and np.array_equal(l0, l02)
     rng = np.random.default_rng(1)
     for _ in range(4):
@@ -292,3 +296,47 @@ def test_defect_correction_inner_arithmetic_is_binary32(orc):
     # the FP64 defect of the corrected iterate: row 0 is 1 + 2^-25 - 1 exactly
     D_next = orc.solve_dc(w, idx, interior, f, u, 2.0 ** -4, 0.0, 0, 1, 0.0)[3]
     assert D_next == 2.0 ** -25
+
+
+def test_adjoint_loss_on_boundary_nodes_too(orc):
+    """A misfit that also observes boundary nodes: u^K_b = g_b there, so dL/dg_b gets
+    the loss's direct derivative on top of the reverse sweep's dt (W_IB^T S)_b.  The
+    loss is quadratic in (f, g): central differences are exact up to rounding."""
+    p = build(orc, 2, 9, 2, seed=14)
+    WII, WIB, bnd = p.dense()
+    dt, K = dt_stable(orc, p), 30
+    sens = gen.sensors(p.NI, 8, 5)
+    bsens = bnd[::3]                      # every third boundary node observed
+    uobs = p.ua[p.interior][sens]
+    bobs = gen.random_vector(len(bsens), 9)
+
+    def forward(f, gb):
+        u = np.zeros(p.N)
+        u[bnd] = gb
+        uI = np.zeros(p.NI)
+        for _ in range(K):
+            uI = uI + dt * (WII @ uI + WIB @ gb - f)
+        u[p.interior] = uI
+        return u
+
+    def loss(f, gb):
+        u = forward(f, gb)
+        return np.sum((u[p.interior][sens] - uobs) ** 2) + np.sum((u[bsens] - bobs) ** 2)
+
+    g = p.u0[bnd] + 0.1 * gen.random_vector(len(bnd), 10)
+    uK = forward(p.f, g)
+    dLdu = np.zeros(p.N)
+    dLdu[p.interior[sens]] = 2 * (uK[p.interior][sens] - uobs)
+    dLdu[bsens] = 2 * (uK[bsens] - bobs)
+    gf, gg, l0 = orc.adjoint(p.w, p.idx, p.interior, p.N, dLdu, K, dt)
+    # without the direct term the boundary gradient would miss 2 (g_b - obs_b)
+    assert np.max(np.abs(dLdu[bsens])) > 1e-3
+    rng = np.random.default_rng(2)
+    for _ in range(5):
+        vf = rng.standard_normal(p.NI)
+        vg = rng.standard_normal(len(bnd))
+        eps = 1e-3
+        fd = (loss(p.f + eps * vf, g + eps * vg) - loss(p.f - eps * vf, g - eps * vg)) / (2 * eps)
+        an = gf @ vf + gg[bnd] @ vg
+        assert abs(fd - an) <= 1e-7 * max(abs(an), 1e-12)
+    assert np.all(gg[p.interior] == 0)

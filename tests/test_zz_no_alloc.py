@@ -71,6 +71,29 @@ def test_noalloc_knn_at_the_size_limit_and_beyond(rb):
     assert torch.all(got == -7)          # nothing was written
 
 
+def test_noalloc_knn_on_a_planar_3d_set_coarsens_its_grid(rb):
+    """Points of the plane z = 0 given as a 3D set: the flat extent makes a grid of
+    about one node per cell far larger than the fixed cell arrays, so the call
+    coarsens its grid until it fits.  The supports must not change."""
+    import oracle
+    N = 100_000
+    p2 = gen.random_points(N, 2, 31)
+    xyz_h = np.vstack([p2, np.zeros((1, N))])
+    xyz = torch.from_numpy(xyz_h).cuda()
+    centres = torch.arange(0, N, 7, dtype=torch.int32, device="cuda")
+    ref = rb.rbffd_knn(xyz, centres, 30)
+    for _ in range(2):
+        code, got = _call(rb, xyz, centres, 30)
+        torch.cuda.synchronize()
+        assert code == rb.RBFFD_OK, rb.lib().rbffd_last_error()
+        assert torch.equal(got, ref)
+    # and sampled rows against the oracle's brute force
+    rows = np.arange(0, centres.numel(), 97)
+    cen = centres.cpu().numpy()[rows]
+    exp = oracle.knn_brute(xyz_h, cen, 30)
+    assert np.array_equal(got.cpu().numpy()[rows], exp)
+
+
 def test_noalloc_knn_does_not_allocate(rb):
     xyz, bnd = rb.rbffd_nodes(2, 0, 200, 0.3, 21)
     centres = rb.rbffd_interior(bnd)

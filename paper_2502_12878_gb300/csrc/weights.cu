@@ -24,7 +24,7 @@
 #include <vector>
 
 #include "common.cuh"
-#include "fp64div.cuh"
+#include "intfp64.cuh"
 
 namespace rbffd {
 
@@ -86,22 +86,24 @@ __device__ __forceinline__ void team_sync() {
     }
 }
 
-// team-wide max of a double
+// team-wide max of a non-negative double, compared as IEEE bits (integer
+// instructions: the FP64 pipe stays free for the elimination)
 template <int TS>
-__device__ __forceinline__ double team_max(double v, double* red) {
+__device__ __forceinline__ double team_max_nonneg(double v, long long* red) {
+    long long b = __double_as_longlong(v);
     const unsigned mask = team_mask<TS>();
 #pragma unroll
-    for (int o = (TS < 32 ? TS : 32) / 2; o > 0; o >>= 1)
-        v = fmax(v, __shfl_xor_sync(mask, v, o));
-    if constexpr (TS <= 32) return v;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int w0 = (int)(threadIdx.x / TS) * (TS / 32);   // the team's first warp
-    if (lane == 0) red[wid] = v;
-    team_sync<TS>();
-    double m = red[w0];
-    for (int q = 1; q < TS / 32; ++q) m = fmax(m, red[w0 + q]);
-    team_sync<TS>();
-    return m;
+    for (int o = (TS < 32 ? TS : 32) / 2; o > 0; o >>= 1) b = max(b, __shfl_xor_sync(mask, b, o));
+    if constexpr (TS > 32) {
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        const int w0 = (int)(threadIdx.x / TS) * (TS / 32);
+        if (lane == 0) red[wid] = b;
+        team_sync<TS>();
+        b = red[w0];
+        for (int q = 1; q < TS / 32; ++q) b = max(b, red[w0 + q]);
+        team_sync<TS>();
+    }
+    return __longlong_as_double(b);
 }
 
 // argmax of |value| as IEEE bits (non-negative doubles order like integers;
@@ -142,19 +144,30 @@ __device__ __forceinline__ long long abs_key(double x) {
     return b > 0x7ff0000000000000ll ? -1ll : b;    // NaN: never the largest
 }
 
+// shared memory of one team, in doubles: the augmented matrix, the scaled
+// support coordinates, and per pivot its reciprocal and the fixed-point
+// reciprocal of its significand
+__host__ __device__ __forceinline__ size_t weight_team_doubles(const WeightArgs& A) {
+    return (size_t)A.s * A.pitch + 3 * (size_t)A.n + 2 * (size_t)A.s;
+}
+
 // the weights of stencil r of one call (all of the team's threads)
 template <int TS, bool PW>
 __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, double* G, double* xi,
                                             int tid, int team, double* redv, long long* redk,
                                             int* redi, double* bcast, int* spiv) {
     constexpr int T = TS;
-    double* rinv = xi + 3 * A.n;   // [s] reciprocal of each pivot, for the back substitution
+    double* rinv = xi + 3 * A.n;   // [s] reciprocal of each pivot
+    // [s] the pivots' fixed-point significand reciprocals, for the back
+    // substitution's quotients (if_div)
+    uint64_t* rinvY = reinterpret_cast<uint64_t*>(rinv + A.s);
     const int n = A.n, M = A.M, s = A.s, P = A.pitch, d = A.d;
     do {
         const int32_t* sup = A.idx + r * n;
         const int32_t c = sup[0];
-        // scale sigma = max_j |x_j - x_c|
-        double sig = 0.0;
+        // scale sigma = max_j |x_j - x_c| (distances are non-negative: their
+        // max is taken on the IEEE bits)
+        long long sigb = 0;
         for (int j = tid; j < n; j += T) {
             int32_t id = sup[j];
             double s2 = 0.0;
@@ -163,20 +176,22 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
                 double sq = __dmul_rn(t, t);
                 s2 = a == 0 ? sq : __dadd_rn(s2, sq);
             }
-            sig = fmax(sig, __dsqrt_rn(s2));
+            sigb = max(sigb, __double_as_longlong(if_sqrt(s2)));
         }
-        sig = team_max<TS>(sig, redv);
+        const double sig = team_max_nonneg<TS>(__longlong_as_double(sigb), redk);
         if (!(sig > 0.0)) {
             for (int j = tid; j < n; j += T) A.w[r * n + j] = 0.0;
             if (tid == 0) A.status[r] = 1;
             team_sync<TS>();
             break;
         }
+        uint64_t Ysig;
+        if_rcp(sig, &Ysig);
         for (int j = tid; j < n; j += T) {
             int32_t id = sup[j];
             for (int a = 0; a < d; ++a) {
                 double t = __dsub_rn(A.xyz[(int64_t)a * A.N + id], A.xyz[(int64_t)a * A.N + c]);
-                xi[3 * j + a] = __ddiv_rn(t, sig);
+                xi[3 * j + a] = if_div(t, sig, Ysig);
             }
         }
         team_sync<TS>();
@@ -199,7 +214,7 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
                     double sq = __dmul_rn(t, t);
                     r2 = a == 0 ? sq : __dadd_rn(r2, sq);
                 }
-                double rr = __dsqrt_rn(r2);
+                double rr = if_sqrt(r2);
                 double v = __dmul_rn(__dmul_rn(rr, rr), rr);
                 G[j * P + k] = v;
                 G[k * P + j] = v;
@@ -233,7 +248,7 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
                 rc2 = a == 0 ? sq : __dadd_rn(rc2, sq);
             }
             if (A.op == 0) {
-                G[j * P + s] = __dmul_rn(A.lap_phi, __dsqrt_rn(rc2));
+                G[j * P + s] = __dmul_rn(A.lap_phi, if_sqrt(rc2));
             } else {
                 // derivative of r^3 about x_j at x_c along dir: -3 |xi_j| (xi_j . dir)
                 double dot = 0.0;
@@ -241,7 +256,7 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
                     double t = __dmul_rn(xi[3 * j + a], dir[a]);
                     dot = a == 0 ? t : __dadd_rn(dot, t);
                 }
-                G[j * P + s] = -__dmul_rn(__dmul_rn(3.0, __dsqrt_rn(rc2)), dot);
+                G[j * P + s] = -__dmul_rn(__dmul_rn(3.0, if_sqrt(rc2)), dot);
             }
         }
         for (int al = tid; al < M; al += T) {
@@ -300,10 +315,12 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
                 }
                 // reciprocal pivot by one warp of the team, broadcast after the swap
                 if ((tid >> 5) == 0) {
-                    const double t = __drcp_rn(G[bi * P + k]);
+                    uint64_t Y;
+                    const double t = if_rcp(G[bi * P + k], &Y);
                     if (tid == 0) {
                         bcast[team] = t;
                         rinv[k] = t;
+                        rinvY[k] = Y;
                     }
                 }
                 if (bi != k)
@@ -376,11 +393,13 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
                 team_argmax<32>(bk, bi, redk, redi);
                 const int nogo =
                     diag_nan || bk <= key_tiny || bk <= key_min || bk == W_INF_BITS;
-                const double t = nogo ? 0.0 : __drcp_rn(G[bi * P + c]);
+                uint64_t Y = 0;
+                const double t = nogo ? 0.0 : if_rcp(G[bi * P + c], &Y);
                 if (lane == 0) {
                     spiv[team] = bi | (nogo << 16);
                     bcast[team] = t;
                     rinv[c] = t;
+                    rinvY[c] = Y;
                 }
             };
             if (pw) pivot(0);
@@ -458,7 +477,7 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
             // back substitution by columns; x_j overwrites the rhs entry of row j
             for (int j = s - 1; j >= 0; --j) {
                 if ((tid >> 5) == 0) {   // one warp divides, the team reads the result
-                    const double t = div_by_pivot(G[j * P + s], G[j * P + j], rinv[j]);
+                    const double t = if_div(G[j * P + s], G[j * P + j], rinvY[j]);
                     if (tid == 0) bcast[team] = t;
                 }
                 team_sync<TS>();
@@ -476,7 +495,9 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
         }
         // the Laplacian scales as 1/sigma^2, a first derivative as 1/sigma
         const double scl = A.op == 0 ? __dmul_rn(sig, sig) : sig;
-        for (int j = tid; j < n; j += T) A.w[r * n + j] = bad ? 0.0 : __ddiv_rn(G[j * P + s], scl);
+        uint64_t Yscl;
+        if_rcp(scl, &Yscl);
+        for (int j = tid; j < n; j += T) A.w[r * n + j] = bad ? 0.0 : if_div(G[j * P + s], scl, Yscl);
         if (tid == 0) A.status[r] = (int8_t)bad;
         team_sync<TS>();
     } while (0);
@@ -492,7 +513,7 @@ __global__ void __launch_bounds__(256) weights_kernel(WeightArgs A, int teams_pe
     __shared__ int spiv[16];       // per-team pivot row (pivot-warp teams)
     const int tid = threadIdx.x % TS;
     const int team = threadIdx.x / TS;
-    double* G = wsm + (size_t)team * ((size_t)A.s * A.pitch + 3 * A.n + A.s);
+    double* G = wsm + (size_t)team * weight_team_doubles(A);
     double* xi = G + (size_t)A.s * A.pitch;
     const int64_t teams = (int64_t)gridDim.x * teams_per_block;
     for (int64_t r = (int64_t)blockIdx.x * teams_per_block + team; r < A.nc; r += teams)
@@ -680,7 +701,7 @@ static int weights_impl(const double* xyz, int64_t N, int d, const int32_t* idx,
     A.lap_phi = (double)(3 * (d + 1));
     A.op = op;
     A.dirs = dirs;
-    const size_t per_team = sizeof(double) * ((size_t)A.s * A.pitch + 3 * (size_t)n + A.s);
+    const size_t per_team = sizeof(double) * weight_team_doubles(A);
     const int sms = device_sm_count();
     WeightShape ws;
     const int ts = weight_team_size(A.s);
@@ -774,8 +795,7 @@ extern "C" int rbffd_weights_batch(int ncalls, const double* const* xyz, const i
             if (c != cls || A.nc == 0) continue;
             sel.push_back(A);
             off.push_back(off.back() + A.nc);
-            team_doubles =
-                std::max(team_doubles, (size_t)A.s * A.pitch + 3 * (size_t)A.n + (size_t)A.s);
+            team_doubles = std::max(team_doubles, weight_team_doubles(A));
         }
         if (sel.empty()) continue;
         Scratch dcalls, doff;

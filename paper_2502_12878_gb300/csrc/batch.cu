@@ -13,7 +13,9 @@
 // and gather the iterate through L1 (their own writes are visible after the
 // barrier); larger teams use a per-domain barrier whose waits give up after
 // ~2 s (RBFFD_ERR_TIMEOUT) and gather through L2 (.cg), because other blocks
-// of the same launch rewrite the iterate.
+// of the same launch rewrite the iterate.  Slices read the plan's 16-bit
+// neighbour codes where it has them, and each warp prefetches its next
+// slice's planes into L2 (bulk prefetch) before it sweeps the current one.
 //
 // The per-call inputs (the caller's f / u pointers, dt, tol, step caps) are
 // copied into a device table at a fixed address, so one captured graph -
@@ -37,6 +39,8 @@ static constexpr long long BATCH_SPIN_CYCLES = 4000000000LL;
 struct DomDesc {           // static part (from the plan)
     const double* w64;
     const int32_t* col;
+    const uint16_t* col16;     // compact neighbour codes (NULL: int32 only)
+    const int4* sbase;         // per slice window bases; x < 0: the slice uses col
     double* fs;            // plan's f in slot order
     double* u0;            // plan's iterates in slot order
     double* u1;
@@ -120,9 +124,25 @@ __device__ __forceinline__ int32_t bld_cs(const int32_t* p) {
     return v;
 }
 
-template <int NN, bool COH, int CH>
-__device__ __forceinline__ double brow(const double* __restrict__ w, const int32_t* __restrict__ col,
-                                       const double* __restrict__ u, int n) {
+__device__ __forceinline__ uint32_t bld_cs(const uint16_t* p) {
+    unsigned short v;
+    asm volatile("ld.global.cs.u16 %0, [%1];" : "=h"(v) : "l"(p));
+    return (uint32_t)v;
+}
+
+// window k = code >> 14 of the slice's four bases, plus the 14-bit offset
+__device__ __forceinline__ int32_t bdecode16(uint32_t v, const int4& b) {
+    const uint32_t k = v >> 14;
+    const int32_t base = (k & 2u) ? ((k & 1u) ? b.w : b.z) : ((k & 1u) ? b.y : b.x);
+    return base + (int32_t)(v & 0x3fffu);
+}
+
+// sum_j w_j u[col_j], an fma chain from 0 in j order; loads in phases of CH
+// (indices, weights, then the gathers).  I16: 16-bit codes against the
+// slice's window bases `sb` (the same columns, fewer bytes).
+template <int NN, bool COH, int CH, bool I16>
+__device__ __forceinline__ double brow(const double* __restrict__ w, const void* __restrict__ colp,
+                                       const int4& sb, const double* __restrict__ u, int n) {
     double acc = 0.0;
     const int nn = NN > 0 ? NN : n;
 #pragma unroll
@@ -132,10 +152,20 @@ __device__ __forceinline__ double brow(const double* __restrict__ w, const int32
         double wv[CH], uv[CH];
 #pragma unroll
         for (int t = 0; t < CH; ++t)
-            if (j0 + t < nn) c[t] = bld_cs(col + (j0 + t) * SLICE);
+            if (j0 + t < nn) {
+                if constexpr (I16)
+                    c[t] = (int32_t)bld_cs((const uint16_t*)colp + (j0 + t) * SLICE);
+                else
+                    c[t] = bld_cs((const int32_t*)colp + (j0 + t) * SLICE);
+            }
 #pragma unroll
         for (int t = 0; t < CH; ++t)
             if (j0 + t < nn) wv[t] = bld_cs(w + (j0 + t) * SLICE);
+        if constexpr (I16) {
+#pragma unroll
+            for (int t = 0; t < CH; ++t)
+                if (j0 + t < nn) c[t] = bdecode16((uint32_t)c[t], sb);
+        }
 #pragma unroll
         for (int t = 0; t < CH; ++t)
             if (j0 + t < nn) uv[t] = COH ? bld_cg(u + c[t]) : bld_ca(u + c[t]);
@@ -151,6 +181,24 @@ __device__ __forceinline__ unsigned long long babs_bits(double x) {
     return b > 0x7ff0000000000000ull ? 0x7ff0000000000000ull : b;
 }
 
+// bulk prefetch into L2 (one lane) of the weight and index planes of slice
+// sl, the warp's next one: the 16-bit code plane when the plan has one.  Both
+// planes start on 16-byte boundaries and their sizes (8n and 2n or 4n bytes
+// per row, 32 rows) are multiples of 16.
+__device__ __forceinline__ void bprefetch(const DomDesc& D, int64_t sl) {
+    if (sl >= D.nslices) return;
+    const int64_t nb = sl * (int64_t)D.n * SLICE;
+    const unsigned plane = (unsigned)(D.n * SLICE);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(D.w64 + nb), "r"(plane * 8u)
+                 : "memory");
+    if (D.col16)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(D.col16 + nb),
+                     "r"(plane * 2u) : "memory");
+    else
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(D.col + nb),
+                     "r"(plane * 4u) : "memory");
+}
+
 // one step of domain D over the slices of this team member; returns max |r| bits
 template <int NN, bool COH, int CH>
 __device__ __noinline__ unsigned long long bstep(const DomDesc& D, int par, double dt, int64_t s0,
@@ -162,10 +210,14 @@ __device__ __noinline__ unsigned long long bstep(const DomDesc& D, int par, doub
     for (int64_t sl = s0; sl < D.nslices; sl += stride) {
         const int64_t row = sl * SLICE + lane;
         const int64_t base = sl * (int64_t)D.n * SLICE + lane;
+        const int4 sb = D.col16 ? __ldg(D.sbase + sl) : make_int4(-1, -1, -1, -1);
+        if (lane == 0) bprefetch(D, sl + stride);
         if (row < D.NI) {
             const double fi = bld_cs(D.fs + row);
             const double ui = COH ? bld_cg(uin + row) : bld_ca(uin + row);
-            double acc = brow<NN, COH, CH>(D.w64 + base, D.col + base, uin, D.n);
+            double acc = sb.x >= 0
+                             ? brow<NN, COH, CH, true>(D.w64 + base, D.col16 + base, sb, uin, D.n)
+                             : brow<NN, COH, CH, false>(D.w64 + base, D.col + base, sb, uin, D.n);
             double r = __dsub_rn(acc, fi);
             uout[row] = __fma_rn(dt, r, ui);
             m = max(m, babs_bits(r));
@@ -508,6 +560,8 @@ extern "C" int rbffd_batch_create(rbffd_plan* const* plans, int ndom, int blocks
         DomDesc d;
         d.w64 = p->w64;
         d.col = p->col;
+        d.col16 = p->col16;
+        d.sbase = p->sbase;
         d.fs = p->fs;
         d.u0 = p->u[0];
         d.u1 = p->u[1];

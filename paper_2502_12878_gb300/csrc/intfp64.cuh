@@ -176,106 +176,4 @@ __device__ __forceinline__ double if_sqrt(double x) {
     return if_double(E << 52 | (q - IF_HIDDEN));
 }
 
-// x >> s for a 128-bit x = (h, l) and 0 <= s, as 128 bits; *sticky: the bits
-// shifted out were not all zero
-__device__ __forceinline__ void if_shr128(uint64_t& h, uint64_t& l, int s, bool* sticky) {
-    if (s == 0) {
-        *sticky = false;
-    } else if (s < 64) {
-        *sticky = (l << (64 - s)) != 0;
-        l = (l >> s) | (h << (64 - s));
-        h >>= s;
-    } else if (s < 128) {
-        *sticky = l != 0 || (s > 64 && (h << (128 - s)) != 0);
-        l = s == 64 ? h : h >> (s - 64);
-        h = 0;
-    } else {
-        *sticky = (h | l) != 0;
-        h = l = 0;
-    }
-}
-
-// RN(a b + c), the fused multiply-add, on the integer pipes.  The product of
-// the 53-bit significands (106 bits) and c's significand are placed in a
-// 128-bit frame with the larger-scale operand at bits 20..125; the other is
-// shifted right into it, the bits shifted out OR-ed into bit 0 (a sticky bit:
-// with 20 spare low bits nothing is lost unless the operands are more than 20
-// bits apart, and then the sum's rounding cannot depend on more than whether
-// something was shifted out), added or subtracted exactly, normalised and
-// rounded to nearest even.  The library fma for zero, subnormal, infinite or
-// NaN a or b, subnormal / non-finite c, products near the ends of the range and
-// results outside the normal range; an exactly zero sum gives +0 as the
-// library's does in round-to-nearest.
-__device__ __forceinline__ double if_fma(double a, double b, double c) {
-    const uint64_t ab = if_bits(a), bb = if_bits(b), cb = if_bits(c);
-    const int ea = (int)((ab >> 52) & 0x7ff), eb = (int)((bb >> 52) & 0x7ff);
-    const int ec = (int)((cb >> 52) & 0x7ff);
-    const bool cz = (cb & ~IF_SIGN) == 0;
-    const int ep = ea + eb - 1023;
-    if (ea == 0 || ea == 2047 || eb == 0 || eb == 2047 || (!cz && (ec == 0 || ec == 2047)) ||
-        ep < 64 || ep > 1980)
-        return __fma_rn(a, b, c);
-    const uint64_t ma = (ab & IF_FRAC) | IF_HIDDEN, mb = (bb & IF_FRAC) | IF_HIDDEN;
-    const uint64_t pl = ma * mb, ph = __umul64hi(ma, mb);   // P < 2^106
-    // the product in the frame: P << 20, least significant bit 2^eF
-    uint64_t Rh = (ph << 20) | (pl >> 44), Rl = pl << 20;
-    int eF = ea + eb - 2170;
-    uint64_t sgn = (ab ^ bb) & IF_SIGN;
-    if (!cz) {
-        // c's significand << 73 (least significant bit 2^eC): the same frame position
-        uint64_t Ch = ((cb & IF_FRAC) | IF_HIDDEN) << 9, Cl = 0;
-        const int eC = ec - 1148;
-        const uint64_t sc = cb & IF_SIGN;
-        int d = eF - eC;
-        uint64_t Sh, Sl, ss;
-        if (d >= 0) {           // c at the finer scale: shift it
-            Sh = Ch; Sl = Cl; ss = sc;
-        } else {                // the product at the finer scale
-            Sh = Rh; Sl = Rl; ss = sgn;
-            Rh = Ch; Rl = Cl; sgn = sc; eF = eC; d = -d;
-        }
-        bool st;
-        if_shr128(Sh, Sl, d, &st);
-        Sl |= (uint64_t)st;
-        if (ss == sgn) {
-            const uint64_t lo = Rl + Sl;
-            Rh = Rh + Sh + (uint64_t)(lo < Rl);
-            Rl = lo;
-        } else {
-            const uint64_t lo = Rl - Sl;
-            Rh = Rh - Sh - (uint64_t)(Rl < Sl);
-            Rl = lo;
-            if ((int64_t)Rh < 0) {   // |S| > |R|: negate
-                Rl = 0ull - Rl;
-                Rh = ~Rh + (uint64_t)(Rl == 0);
-                sgn ^= IF_SIGN;
-            }
-            if ((Rh | Rl) == 0) return 0.0;   // exact cancellation: +0
-        }
-    }
-    // normalise to 53 bits and round to nearest even
-    const int t = Rh ? 127 - __clzll((long long)Rh) : 63 - __clzll((long long)Rl);
-    uint64_t m;
-    int e;
-    if (t <= 52) {   // fewer than 54 significant bits: exact
-        m = Rl << (52 - t);
-        e = eF - (52 - t) + 1075;
-    } else {
-        const int sh = t - 52;   // 1..75: keep bits sh..t, bit sh-1 decides
-        bool st;
-        uint64_t h = Rh, l = Rl;
-        if_shr128(h, l, sh - 1, &st);   // l now holds the 53 bits and the guard bit
-        const uint64_t guard = l & 1ull;
-        m = l >> 1;
-        m += guard & ((uint64_t)st | (m & 1ull));
-        e = eF + sh + 1075;
-        if (m == (IF_HIDDEN << 1)) {
-            m = IF_HIDDEN;
-            ++e;
-        }
-    }
-    if (e < 1 || e > 2046) return __fma_rn(a, b, c);
-    return if_double(sgn | (uint64_t)e << 52 | (m - IF_HIDDEN));
-}
-
 }  // namespace rbffd

@@ -1,13 +1,11 @@
 // Probe for the integer-pipe FP64 routines of the weight build
 // (csrc/intfp64.cuh): if_rcp, if_div and if_sqrt against the library's
-// correctly rounded reciprocal, quotient and square root, and if_fma against
-// the fused multiply-add, bit for bit, on
+// correctly rounded reciprocal, quotient and square root, bit for bit, on
 // seeded operands.  Operand families: 0 uniform significands, exponents in
 // [-60, 60]; 1 significands next to 1 and 2 (the hard cases for rounding);
 // 2 exponents in [-1020, 1020] (fallbacks at the ends of the range); 3 powers
 // of two, zeros, subnormals and exact squares.  Prints one line per routine
-// and family: "<routine> family F operands P mismatches K" (for fma the
-// families are described in probe()).
+// and family: "<routine> family F operands P mismatches K".
 #include <cstdint>
 #include <cstdio>
 #include <cuda_runtime.h>
@@ -63,31 +61,10 @@ __global__ void probe(int which, int fam, int iters, unsigned long long* bad) {
             rbffd::if_rcp(p, &Y);
             got = rbffd::if_div(b, p, Y);
             want = __ddiv_rn(b, p);
-        } else if (which == 2) {
+        } else {
             const double x = operand(a, a2, fam, true);
             got = rbffd::if_sqrt(x);
             want = __dsqrt_rn(x);
-        } else {
-            // fused multiply-add: family 0 independent operands; 1 c next to -a b
-            // (cancellation); 2 magnitudes of the sweep (weights to 1e7, values to
-            // 1, partial sums of either sign); 3 zeros, powers of two, subnormals
-            double x = operand(a, a2, fam == 2 ? 0 : fam, false);
-            double y = operand(c, c2, fam == 2 ? 0 : fam, false);
-            const uint64_t r3 = mix64(4 * id + 5);
-            double z = operand(r3, mix64(4 * id + 6), fam == 1 || fam == 2 ? 0 : fam, false);
-            if (fam == 1) {
-                // -a b rounded, moved by up to 2^20 ulps, sometimes exactly -a b
-                const double pr = __dmul_rn(x, y);
-                long long zb = __double_as_longlong(-pr) + ((long long)(r3 % (1u << 21)) - (1 << 20)) *
-                                                          (long long)((r3 >> 40) & 1);
-                z = __longlong_as_double(zb);
-            } else if (fam == 2) {
-                x = ldexp((double)(int64_t)(a >> 11) * 0x1p-53, (int)(a2 % 24));        // |w| < 2^24
-                y = (double)(int64_t)(c >> 11) * 0x1p-53;                              // |u| < 1
-                z = ldexp((double)(int64_t)(r3 >> 11) * 0x1p-53, (int)(r3 % 26) - 2);
-            }
-            got = rbffd::if_fma(x, y, z);
-            want = __fma_rn(x, y, z);
         }
         // NaN results compare as NaN (any payload)
         const bool both_nan = got != got && want != want;
@@ -100,8 +77,8 @@ int main() {
     unsigned long long* d = nullptr;
     if (cudaMalloc(&d, sizeof(unsigned long long)) != cudaSuccess) return 2;
     const int blocks = 152 * 8, threads = 256, iters = 128;
-    const char* names[4] = {"rcp", "div", "sqrt", "fma"};
-    for (int which = 0; which < 4; ++which)
+    const char* names[3] = {"rcp", "div", "sqrt"};
+    for (int which = 0; which < 3; ++which)
         for (int fam = 0; fam < 4; ++fam) {
             unsigned long long h = 0;
             cudaMemcpy(d, &h, sizeof(h), cudaMemcpyHostToDevice);

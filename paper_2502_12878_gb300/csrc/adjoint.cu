@@ -25,8 +25,13 @@ namespace rbffd {
 // placed order; boundary columns keep their slots.
 static constexpr int TR_WINDOW = 256;
 
+typedef void (*AdjStepFn)(const struct Transpose, const int64_t, const double, const double*,
+                          double*, double*);
+
 struct Transpose {
     int64_t nslices = 0;      // over all N columns (placed order)
+    AdjStepFn step = nullptr; // the reverse-step shape the tuner picked (on first use)
+    int step_shape = 0;       // its index in adj_shapes
     int64_t* off = nullptr;   // [nslices + 1] element offset of each slice
     int32_t* len = nullptr;   // [nslices] padded length of each slice
     int32_t* row = nullptr;   // placed position of each entry's row
@@ -208,12 +213,15 @@ __device__ __forceinline__ double adj_ld_nc(const double* p) {
 // one reverse step over interior columns c < NI:
 //   S_c += lam_c;  lam'_c = fma(dt, sum_rows w_rc lam_r, lam_c)
 // the column sum is an fma chain from 0 over the column's entries in order
-// (padding entries carry weight 0 and row 0, so they add exact zeros)
-__global__ void __launch_bounds__(256, 4)
+// (padding entries carry weight 0 and row 0, so they add exact zeros).
+// Shapes: CH entries per load phase (indices, weights, then gathers) and a
+// register budget for MINB resident blocks of 256 threads; every shape gives
+// the same bits.
+template <int CH, int MINB>
+__global__ void __launch_bounds__(256, MINB)
 adjoint_step(const Transpose T, const int64_t NI, const double dt,
              const double* __restrict__ lam, double* __restrict__ lam_out,
              double* __restrict__ S) {
-    constexpr int CH = 8;
     const int lane = threadIdx.x & 31;
     const int64_t nsl_int = (NI + SLICE - 1) / SLICE;
     for (int64_t s = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); s < nsl_int;
@@ -379,6 +387,57 @@ __global__ void ckpt_gather(const double* u, const int32_t* perm, int64_t N, dou
         out[p] = u[perm[p]];
 }
 
+// reverse-step shapes the tuner times: (phase width, resident blocks)
+static const AdjStepFn adj_shapes[] = {adjoint_step<8, 4>, adjoint_step<12, 3>,
+                                       adjoint_step<16, 2>, adjoint_step<8, 3>};
+static constexpr int N_ADJ_SHAPES = 4;
+
+static unsigned adj_grid(const rbffd_plan* p) {
+    const int64_t nsl_int = (p->NI + SLICE - 1) / SLICE;
+    return (unsigned)std::max<int64_t>(1, (nsl_int + 7) / 8);
+}
+
+// Time every reverse-step shape on this plan's transpose (a few steps each on
+// scratch vectors, dt = 0; an untimed round first, then the best of three
+// interleaved rounds) and keep the fastest.  Once per plan.
+static int tune_adjoint(rbffd_plan* p, cudaStream_t s) {
+    Transpose& T = *p->tr;
+    if (T.step) return RBFFD_OK;
+    const int64_t NI = p->NI;
+    RBFFD_CHECK_CUDA(cudaMemsetAsync(T.lam[0], 0, sizeof(double) * NI, s));
+    RBFFD_CHECK_CUDA(cudaMemsetAsync(T.lam[1], 0, sizeof(double) * NI, s));
+    RBFFD_CHECK_CUDA(cudaMemsetAsync(T.S, 0, sizeof(double) * NI, s));
+    const int reps = (int)std::max<int64_t>(4, std::min<int64_t>(64, 200000000 / (NI * p->n + 1)));
+    cudaEvent_t e0, e1;
+    RBFFD_CHECK_CUDA(cudaEventCreate(&e0));
+    RBFFD_CHECK_CUDA(cudaEventCreate(&e1));
+    float best[N_ADJ_SHAPES];
+    for (float& b : best) b = 1e30f;
+    cudaError_t e = cudaSuccess;
+    for (int round = 0; round < 4 && e == cudaSuccess; ++round)
+        for (int c = 0; c < N_ADJ_SHAPES && e == cudaSuccess; ++c) {
+            cudaEventRecord(e0, s);
+            for (int k = 0; k < reps; ++k)
+                adj_shapes[c]<<<adj_grid(p), 256, 0, s>>>(T, NI, 0.0, T.lam[k & 1],
+                                                          T.lam[(k + 1) & 1], T.S);
+            cudaEventRecord(e1, s);
+            e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaGetLastError();
+            float ms = 0.f;
+            if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+            if (round) best[c] = std::min(best[c], ms);
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    RBFFD_CHECK_CUDA(e);
+    int bi = 0;
+    for (int c = 1; c < N_ADJ_SHAPES; ++c)
+        if (best[c] < best[bi]) bi = c;
+    T.step = adj_shapes[bi];
+    T.step_shape = bi;
+    return RBFFD_OK;
+}
+
 static int build_transpose(rbffd_plan* p, cudaStream_t s) {
     if (p->tr) return RBFFD_OK;
     const int64_t N = p->N, NI = p->NI;
@@ -461,15 +520,15 @@ extern "C" int rbffd_adjoint(rbffd_plan* p, const double* dLdu, int64_t K, doubl
     cudaStream_t s = as_stream(stream);
     int st = build_transpose(p, s);
     if (st) return st;
+    if ((st = tune_adjoint(p, s))) return st;
     Transpose& T = *p->tr;
     const int sms = device_sm_count();
     const unsigned G = (unsigned)sms * 8;
     adj_gather_placed<<<G, 256, 0, s>>>(dLdu, p->perm, T.colof, p->NI, T.lam[0]);
     RBFFD_CHECK_CUDA(cudaMemsetAsync(T.S, 0, sizeof(double) * p->NI, s));
-    const int64_t nsl_int = (p->NI + SLICE - 1) / SLICE;
-    const unsigned grid = (unsigned)std::max<int64_t>(1, (nsl_int + 7) / 8);
+    const unsigned grid = adj_grid(p);
     for (int64_t k = 0; k < K; ++k)
-        adjoint_step<<<grid, 256, 0, s>>>(T, p->NI, dt, T.lam[k & 1], T.lam[(k + 1) & 1], T.S);
+        T.step<<<grid, 256, 0, s>>>(T, p->NI, dt, T.lam[k & 1], T.lam[(k + 1) & 1], T.S);
     RBFFD_CHECK_CUDA(cudaGetLastError());
     adjoint_grad_g<<<G, 256, 0, s>>>(T, p->NI, p->N, dt, T.S, p->perm, dLdu, grad_g);
     adj_outputs<<<G, 256, 0, s>>>(T.S, T.lam[K & 1], p->row_of_slot, T.colof, p->perm, p->NI,
@@ -489,6 +548,7 @@ extern "C" int rbffd_adjoint_w(rbffd_plan* p, const double* f, const double* ckp
     cudaStream_t s = as_stream(stream);
     int st = build_transpose(p, s);
     if (st) return st;
+    if ((st = tune_adjoint(p, s))) return st;
     Transpose& T = *p->tr;
     const int sms = device_sm_count();
     const unsigned G = (unsigned)sms * 8;
@@ -506,8 +566,7 @@ extern "C" int rbffd_adjoint_w(rbffd_plan* p, const double* f, const double* ckp
     adj_gather_placed<<<G, 256, 0, s>>>(dLdu, p->perm, T.colof, NI, T.lam[0]);
     RBFFD_CHECK_CUDA(cudaMemsetAsync(T.S, 0, sizeof(double) * NI, s));
     const int64_t nseg = (K + every - 1) / every;
-    const int64_t nsl_int = (NI + SLICE - 1) / SLICE;
-    const unsigned agrid = (unsigned)std::max<int64_t>(1, (nsl_int + 7) / 8);
+    const unsigned agrid = adj_grid(p);
     int cur = 0;   // lambda^{k+1} lives in T.lam[cur]
     for (int64_t sidx = nseg - 1; sidx >= 0; --sidx) {
         const int64_t k0 = sidx * every, k1 = std::min(K, k0 + every);
@@ -519,7 +578,7 @@ extern "C" int rbffd_adjoint_w(rbffd_plan* p, const double* f, const double* ckp
         for (int64_t k = k1 - 1; k >= k0; --k) {
             wgrad_accum<<<G, 256, 0, s>>>(p->col, T.lam[cur], T.posof, U + (k - k0) * N, Gw, NI,
                                           n);
-            adjoint_step<<<agrid, 256, 0, s>>>(T, NI, dt, T.lam[cur], T.lam[cur ^ 1], T.S);
+            T.step<<<agrid, 256, 0, s>>>(T, NI, dt, T.lam[cur], T.lam[cur ^ 1], T.S);
             cur ^= 1;
         }
         RBFFD_CHECK_CUDA(cudaGetLastError());

@@ -483,11 +483,12 @@ static StepFn pick_step_m(int n, bool persistent) {
 #undef RBFFD_CASE
 }
 
-// one per translation unit: FP64 sweep with register budgets 1..3 (minimum
-// resident blocks per SM), FP32 inner sweep with budgets 1..4
+// one per translation unit: FP64 sweep and FP32 inner sweep with register
+// budgets 1..4 (minimum resident blocks per SM)
 StepFn pick_step_f64_b1(int n, bool persistent);
 StepFn pick_step_f64_b2(int n, bool persistent);
 StepFn pick_step_f64_b3(int n, bool persistent);
+StepFn pick_step_f64_b4(int n, bool persistent);
 StepFn pick_step_f32_b1(int n, bool persistent);
 StepFn pick_step_f32_b2(int n, bool persistent);
 StepFn pick_step_f32_b3(int n, bool persistent);

@@ -37,16 +37,17 @@ namespace rbffd {
 // launch shape of a step kernel: the register budget (min resident blocks per
 // SM the compiler must allow: more blocks = fewer registers = fewer loads in
 // flight per thread) and the grid (blocks per SM of the grid-stride sweep).
-// A fourth budget (64 registers) exists only for the FP32 inner sweep, whose
-// rows need half the registers of the FP64 ones.
-static constexpr int N_MINB = 3;
+// Budgets 1..4 (255, 128, 80 and 64 registers per thread); the fourth suits
+// the FP32 inner sweep and the FP64 sweep at small stencils.
+static constexpr int N_MINB = 4;
 
 static StepFn pick(int mode, int n, bool persistent, int minb) {
     if (mode == MODE_SWEEP64) {
         switch (minb) {
             case 1: return pick_step_f64_b1(n, persistent);
             case 2: return pick_step_f64_b2(n, persistent);
-            default: return pick_step_f64_b3(n, persistent);
+            case 3: return pick_step_f64_b3(n, persistent);
+            default: return pick_step_f64_b4(n, persistent);
         }
     }
     switch (minb) {
@@ -603,7 +604,7 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
     // microseconds of mostly latency, so a short trial is noise), few on large ones
     const long long reps =
         std::max<long long>(10, std::min<long long>(600, 400000000 / (p->NI * p->n + 1)));
-    const int n_minb = mode == MODE_INNER32 ? N_MINB + 1 : N_MINB;
+    const int n_minb = N_MINB;
     // candidate c: graph shapes per_sm = c (1..4), then the persistent launch (c = 5)
     const int c_lo = may_graph(p) ? 1 : 5, c_hi = may_persist(p) ? 5 : 4;
     std::vector<TuneCand> cands;

@@ -327,8 +327,8 @@ def tta_case(rb, torch, Kg, dev, modes=("fp64", "fp32_dc", "fp64_persistent",
         finals[prec] = u
         if kind == "_auto":
             shape = plan.stats()[3]
-            row[prec]["launch"] = ("persistent" if shape[1 if prec.startswith("fp64") else 3] == 0
-                                   else "graph")
+            sh = shape[1 if prec.startswith("fp64") else 3]
+            row[prec]["launch"] = "resident" if sh < 0 else "persistent" if sh == 0 else "graph"
     for kind, plan in plans.items():
         plan.destroy()
     for k64, k32 in (("fp64", "fp32_dc"), ("fp64_auto", "fp32_dc_auto")):
@@ -362,7 +362,7 @@ def c1_case(rb, torch, dev):
             "residual": res, "wall_s": el, "us_per_step_wall": el / max(steps, 1) * 1e6,
             "us_per_step_gpu": ms * 1e3 / max(k, 1),
             "node_updates_per_s": Q["NI"] * steps / el, "max_err": err, "mean_abs_err": mean,
-            "launch": "persistent" if shape[1] == 0 else "graph"}
+            "launch": "resident" if shape[1] < 0 else "persistent" if shape[1] == 0 else "graph"}
 
 
 def support_sweep_case(rb, torch, dev, hbm, fma_peak, ns=(12, 13, 16, 20, 24, 30, 40, 48, 56)):

@@ -59,6 +59,7 @@ extern "C" {
 #define RBFFD_LAUNCH_PERSISTENT 16 /* one cooperative kernel runs many steps */
 #define RBFFD_PACK_IDX32 32        /* keep int32 neighbour indices only (no 16-bit codes) */
 #define RBFFD_LAUNCH_AUTO 64       /* the autotuner picks graph or persistent per arithmetic */
+#define RBFFD_LAUNCH_RESIDENT 128  /* persistent, stencil planes resident in shared memory */
 
 typedef struct rbffd_plan rbffd_plan;
 
@@ -292,10 +293,17 @@ RBFFD_API int rbffd_fp64_fma_rate(int64_t iters, double* h_fma_per_s, double* h_
  * (a slice whose supports need more windows keeps 32-bit indices); the codes
  * name the same neighbours, so the results are the same bit for bit.
  * Launch mode of the step loops: RBFFD_LAUNCH_GRAPH (default), _PERSISTENT,
- * or _AUTO, where the first solve of each arithmetic (FP64 sweep, FP32 inner
- * sweep) times the graph shapes and the persistent launch on the plan's own
- * stencils and keeps the faster.  A plan with Neumann nodes always replays
- * graphs.  Every mode gives the same results bit for bit.
+ * _RESIDENT, or _AUTO, where the first solve of each arithmetic (FP64 sweep,
+ * FP32 inner sweep) times the graph shapes, the persistent launch and (when
+ * it fits) the resident launch on the plan's own stencils and keeps the
+ * fastest.  The resident launch is a persistent launch of one block per SM
+ * whose slices' weight and index planes (and their rows' f) are copied into
+ * shared memory once per solve by TMA bulk copies, so each step reads only
+ * the iterate; it fits while the plan's share per SM does (about 107,000
+ * interior rows at n = 30 in FP64 with 16-bit codes, 185,000 for the FP32
+ * inner sweep); a _RESIDENT plan that does not fit returns
+ * RBFFD_ERR_CAPACITY from its first solve.  A plan with Neumann nodes always
+ * replays graphs.  Every mode gives the same results bit for bit.
  */
 RBFFD_API int rbffd_plan_create(const double* xyz, const uint8_t* is_bnd, int64_t N, int d,
                       const int32_t* interior, const int32_t* idx, const double* w, int64_t NI,
@@ -330,6 +338,17 @@ RBFFD_API int rbffd_plan_set_neumann(rbffd_plan* plan, int64_t NN, const int32_t
  * effect from the next solve; graph-mode steps have no waits.
  */
 RBFFD_API int rbffd_plan_set_wait(rbffd_plan* plan, double timeout_ms, int held_arrivals);
+/*
+ * rbffd_plan_set_resident_halo - the halo window of the resident launch: each
+ * block stages, every step, the iterate's slots from `halo` before its first
+ * row to `halo` after its last (clipped to the iterate and to the shared memory
+ * left beside the stencil planes) and reads its neighbours there, the others
+ * through L2.  halo = -1: no window; halo >= 0: that reach; -2: the autotuner
+ * times no window, the rows alone, 256, 1024, 4096 slots and the largest that
+ * fits, and keeps the fastest (the default).  Every reach gives the same
+ * results bit for bit.  The launch shapes are tuned again on the next solve.
+ */
+RBFFD_API int rbffd_plan_set_resident_halo(rbffd_plan* plan, int64_t halo);
 /* node permutation of the plan: perm [N] out, perm[p] = original index of slot p */
 RBFFD_API int rbffd_plan_perm(const rbffd_plan* plan, int32_t* perm, void* stream);
 
@@ -361,8 +380,8 @@ RBFFD_API int rbffd_solve_explicit(rbffd_plan* plan, const double* f, double* u,
  * events recorded on the caller's stream around the step launches;
  * h_loop_steps, the steps those loops took; h_launches, the kernels the solve
  * launched; h_shape[4], the autotuned launch shape (register budget, blocks
- * per SM; 0 blocks per SM = the persistent launch) of the FP64 sweep and of
- * the FP32 inner sweep.
+ * per SM; 0 blocks per SM = the persistent launch, -1 = the resident launch)
+ * of the FP64 sweep and of the FP32 inner sweep.
  */
 RBFFD_API int rbffd_plan_stats(const rbffd_plan* plan, double* h_loop_ms, int64_t* h_loop_steps,
                                int64_t* h_launches, int* h_shape);

@@ -42,6 +42,7 @@ RBFFD_ORDER_RANDOM = 2
 RBFFD_LAUNCH_GRAPH = 0
 RBFFD_LAUNCH_PERSISTENT = 16
 RBFFD_LAUNCH_AUTO = 64
+RBFFD_LAUNCH_RESIDENT = 128
 RBFFD_PACK_IDX32 = 32
 
 EXPORTED = [
@@ -53,7 +54,7 @@ EXPORTED = [
     "rbffd_error", "rbffd_batch_domain_times", "rbffd_batch_set_costs", "rbffd_adjoint_w",
     "rbffd_knn_masked", "rbffd_weights_dir", "rbffd_plan_set_neumann", "rbffd_plan_layout",
     "rbffd_nodes_pds", "rbffd_nodes_pds_cap", "rbffd_weights_batch", "rbffd_transpose",
-    "rbffd_plan_set_wait", "rbffd_fp64_fma_rate",
+    "rbffd_plan_set_wait", "rbffd_fp64_fma_rate", "rbffd_plan_set_resident_halo",
 ]
 RBFFD_KNN_NOALLOC_MAX_NODES = 262144
 
@@ -118,6 +119,7 @@ def lib():
         "rbffd_transpose": (I, [P, P]),
         "rbffd_plan_set_wait": (I, [P, D, I]),
         "rbffd_fp64_fma_rate": (I, [I64, PD, PD, P]),
+        "rbffd_plan_set_resident_halo": (I, [P, I64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -461,6 +463,10 @@ class Plan:
         """Timeout of the persistent launch's barrier waits (<= 0: default); held_arrivals
         > 0 makes every barrier wait for arrivals that never come (tests the timeout)."""
         _check(lib().rbffd_plan_set_wait(self.handle, float(timeout_ms), int(held_arrivals)))
+
+    def set_resident_halo(self, halo=-2):
+        """Halo reach of the resident launch (-1 none, >= 0 slots, -2 tuned)."""
+        _check(lib().rbffd_plan_set_resident_halo(self.handle, int(halo)))
 
     def set_dc(self, K_in, rho_in):
         _check(lib().rbffd_plan_set_dc(self.handle, int(K_in), float(rho_in)))

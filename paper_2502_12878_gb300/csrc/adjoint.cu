@@ -31,7 +31,7 @@ typedef void (*AdjStepFn)(const struct Transpose, const int64_t, const double, c
 struct Transpose {
     int64_t nslices = 0;      // over all N columns (placed order)
     AdjStepFn step = nullptr; // the reverse-step shape the tuner picked (on first use)
-    int step_shape = 0;       // its index in adj_shapes
+    unsigned step_grid = 0;   // and its grid
     int64_t* off = nullptr;   // [nslices + 1] element offset of each slice
     int32_t* len = nullptr;   // [nslices] padded length of each slice
     int32_t* row = nullptr;   // placed position of each entry's row
@@ -224,13 +224,32 @@ adjoint_step(const Transpose T, const int64_t NI, const double dt,
              double* __restrict__ S) {
     const int lane = threadIdx.x & 31;
     const int64_t nsl_int = (NI + SLICE - 1) / SLICE;
+    const int64_t stride = (int64_t)gridDim.x * (blockDim.x / 32);
     for (int64_t s = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); s < nsl_int;
-         s += (int64_t)gridDim.x * (blockDim.x / 32)) {
+         s += stride) {
+        // one lane prefetches the warp's next slice (row and weight planes)
+        // into L2: both start on 16-byte boundaries (slice offsets are
+        // multiples of 32 entries) and span a multiple of 16 bytes
+        if (lane == 0 && s + stride < nsl_int) {
+            const int64_t o = __ldg(T.off + s + stride);
+            const unsigned Ln = (unsigned)__ldg(T.len + s + stride) * SLICE;
+            if (Ln) {
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(T.w + o),
+                             "r"(Ln * 8u) : "memory");
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(T.row + o),
+                             "r"(Ln * 4u) : "memory");
+            }
+        }
         const int64_t c = s * SLICE + lane;
         if (c >= NI) continue;
-        const int L = T.len[s];
-        const double* wp = T.w + T.off[s] + lane;
-        const int32_t* rp = T.row + T.off[s] + lane;
+        const int L = __ldg(T.len + s);
+        const int64_t off = __ldg(T.off + s);
+        const double* wp = T.w + off + lane;
+        const int32_t* rp = T.row + off + lane;
+        // the column's own lambda and S are issued before the sum, so their
+        // latency overlaps the entry loads
+        const double lc = lam[c];
+        const double Sc = S[c];
         double acc = 0.0;
         for (int j0 = 0; j0 < L; j0 += CH) {
             int32_t r[CH];
@@ -248,8 +267,7 @@ adjoint_step(const Transpose T, const int64_t NI, const double dt,
             for (int t = 0; t < CH; ++t)
                 if (j0 + t < L) acc = __fma_rn(wv[t], lv[t], acc);
         }
-        const double lc = lam[c];
-        S[c] = __dadd_rn(S[c], lc);
+        S[c] = __dadd_rn(Sc, lc);
         lam_out[c] = __fma_rn(dt, acc, lc);
     }
 }
@@ -387,7 +405,9 @@ __global__ void ckpt_gather(const double* u, const int32_t* perm, int64_t N, dou
         out[p] = u[perm[p]];
 }
 
-// reverse-step shapes the tuner times: (phase width, resident blocks)
+// reverse-step shapes the tuner times: (phase width, register budget), each
+// with one warp per slice (the full grid) or a grid-stride loop over slices
+// on the resident blocks
 static const AdjStepFn adj_shapes[] = {adjoint_step<8, 4>, adjoint_step<12, 3>,
                                        adjoint_step<16, 2>, adjoint_step<8, 3>};
 static constexpr int N_ADJ_SHAPES = 4;
@@ -397,13 +417,29 @@ static unsigned adj_grid(const rbffd_plan* p) {
     return (unsigned)std::max<int64_t>(1, (nsl_int + 7) / 8);
 }
 
-// Time every reverse-step shape on this plan's transpose (a few steps each on
-// scratch vectors, dt = 0; an untimed round first, then the best of three
-// interleaved rounds) and keep the fastest.  Once per plan.
+// Time every reverse-step shape and grid on this plan's transpose (a few
+// steps each on scratch vectors, dt = 0; an untimed round first, then the
+// best of three interleaved rounds) and keep the fastest.  Once per plan.
 static int tune_adjoint(rbffd_plan* p, cudaStream_t s) {
     Transpose& T = *p->tr;
     if (T.step) return RBFFD_OK;
     const int64_t NI = p->NI;
+    const int sms = device_sm_count();
+    AdjStepFn cf[2 * N_ADJ_SHAPES];
+    unsigned cg[2 * N_ADJ_SHAPES];
+    int nc = 0;
+    for (int c = 0; c < N_ADJ_SHAPES; ++c) {
+        int per_sm = 0;
+        RBFFD_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, (const void*)adj_shapes[c], 256, 0));
+        cf[nc] = adj_shapes[c];
+        cg[nc++] = adj_grid(p);
+        const unsigned res = (unsigned)(sms * std::max(1, per_sm));
+        if (res < adj_grid(p)) {
+            cf[nc] = adj_shapes[c];
+            cg[nc++] = res;
+        }
+    }
     RBFFD_CHECK_CUDA(cudaMemsetAsync(T.lam[0], 0, sizeof(double) * NI, s));
     RBFFD_CHECK_CUDA(cudaMemsetAsync(T.lam[1], 0, sizeof(double) * NI, s));
     RBFFD_CHECK_CUDA(cudaMemsetAsync(T.S, 0, sizeof(double) * NI, s));
@@ -411,15 +447,14 @@ static int tune_adjoint(rbffd_plan* p, cudaStream_t s) {
     cudaEvent_t e0, e1;
     RBFFD_CHECK_CUDA(cudaEventCreate(&e0));
     RBFFD_CHECK_CUDA(cudaEventCreate(&e1));
-    float best[N_ADJ_SHAPES];
+    float best[2 * N_ADJ_SHAPES];
     for (float& b : best) b = 1e30f;
     cudaError_t e = cudaSuccess;
     for (int round = 0; round < 4 && e == cudaSuccess; ++round)
-        for (int c = 0; c < N_ADJ_SHAPES && e == cudaSuccess; ++c) {
+        for (int c = 0; c < nc && e == cudaSuccess; ++c) {
             cudaEventRecord(e0, s);
             for (int k = 0; k < reps; ++k)
-                adj_shapes[c]<<<adj_grid(p), 256, 0, s>>>(T, NI, 0.0, T.lam[k & 1],
-                                                          T.lam[(k + 1) & 1], T.S);
+                cf[c]<<<cg[c], 256, 0, s>>>(T, NI, 0.0, T.lam[k & 1], T.lam[(k + 1) & 1], T.S);
             cudaEventRecord(e1, s);
             e = cudaEventSynchronize(e1);
             if (e == cudaSuccess) e = cudaGetLastError();
@@ -431,10 +466,10 @@ static int tune_adjoint(rbffd_plan* p, cudaStream_t s) {
     cudaEventDestroy(e1);
     RBFFD_CHECK_CUDA(e);
     int bi = 0;
-    for (int c = 1; c < N_ADJ_SHAPES; ++c)
+    for (int c = 1; c < nc; ++c)
         if (best[c] < best[bi]) bi = c;
-    T.step = adj_shapes[bi];
-    T.step_shape = bi;
+    T.step = cf[bi];
+    T.step_grid = cg[bi];
     return RBFFD_OK;
 }
 
@@ -526,9 +561,8 @@ extern "C" int rbffd_adjoint(rbffd_plan* p, const double* dLdu, int64_t K, doubl
     const unsigned G = (unsigned)sms * 8;
     adj_gather_placed<<<G, 256, 0, s>>>(dLdu, p->perm, T.colof, p->NI, T.lam[0]);
     RBFFD_CHECK_CUDA(cudaMemsetAsync(T.S, 0, sizeof(double) * p->NI, s));
-    const unsigned grid = adj_grid(p);
     for (int64_t k = 0; k < K; ++k)
-        T.step<<<grid, 256, 0, s>>>(T, p->NI, dt, T.lam[k & 1], T.lam[(k + 1) & 1], T.S);
+        T.step<<<T.step_grid, 256, 0, s>>>(T, p->NI, dt, T.lam[k & 1], T.lam[(k + 1) & 1], T.S);
     RBFFD_CHECK_CUDA(cudaGetLastError());
     adjoint_grad_g<<<G, 256, 0, s>>>(T, p->NI, p->N, dt, T.S, p->perm, dLdu, grad_g);
     adj_outputs<<<G, 256, 0, s>>>(T.S, T.lam[K & 1], p->row_of_slot, T.colof, p->perm, p->NI,
@@ -566,7 +600,7 @@ extern "C" int rbffd_adjoint_w(rbffd_plan* p, const double* f, const double* ckp
     adj_gather_placed<<<G, 256, 0, s>>>(dLdu, p->perm, T.colof, NI, T.lam[0]);
     RBFFD_CHECK_CUDA(cudaMemsetAsync(T.S, 0, sizeof(double) * NI, s));
     const int64_t nseg = (K + every - 1) / every;
-    const unsigned agrid = adj_grid(p);
+    const unsigned agrid = T.step_grid;
     int cur = 0;   // lambda^{k+1} lives in T.lam[cur]
     for (int64_t sidx = nseg - 1; sidx >= 0; --sidx) {
         const int64_t k0 = sidx * every, k1 = std::min(K, k0 + every);

@@ -81,6 +81,10 @@ struct rbffd_plan {
     // tuned launch shape per mode (0 FP64 sweep, 1 FP32 inner sweep)
     bool tuned[2] = {false, false};
     bool persist[2] = {false, false};   // the step loop of each mode runs persistent
+    bool resident[2] = {false, false};  // ... as the resident launch (planes in shared memory)
+    unsigned res_smem[2] = {0, 0};      // its dynamic shared memory per block
+    int64_t res_halo[2] = {0, 0};       // and its halo reach (slots beyond a block's rows)
+    int64_t res_halo_set = -2;          // a reach fixed by rbffd_plan_set_resident_halo (-2: tuned)
     int minb[2] = {2, 2};
     int per_sm[2] = {2, 2};
     float tune_ms[2] = {0.f, 0.f};

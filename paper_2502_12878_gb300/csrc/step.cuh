@@ -171,6 +171,8 @@ struct StepArgs {
     int64_t nslices;
     int n;
     int spread;   // 1: consecutive slices go to different blocks (small plans)
+    int64_t N;    // slots (the iterate's length)
+    int64_t halo; // resident launch: slots staged beyond a block's rows on either side
 };
 
 // The warp's first slice.  Large plans give each block runs of consecutive
@@ -493,5 +495,14 @@ StepFn pick_step_f32_b1(int n, bool persistent);
 StepFn pick_step_f32_b2(int n, bool persistent);
 StepFn pick_step_f32_b3(int n, bool persistent);
 StepFn pick_step_f32_b4(int n, bool persistent);
+
+// the resident persistent launch (step_res.cu): one block of RES_THREADS_HOST
+// threads per SM keeps its slices' planes in shared memory; i16: the index
+// planes are 16-bit codes (every slice of the plan has them)
+static constexpr int RES_THREADS_HOST = 512;
+StepFn pick_resident(int mode, int n, bool i16);
+// dynamic shared memory of a resident launch of `grid` blocks whose halo
+// window reaches `halo` slots beyond each block's rows on either side
+unsigned resident_smem(int64_t nslices, int n, int mode, bool i16, int grid, int64_t halo);
 
 }  // namespace rbffd

@@ -494,6 +494,8 @@ static StepArgs make_args(const rbffd_plan* p) {
     A.nslices = p->nslices;
     A.n = p->n;
     A.spread = spread_slices(p) ? 1 : 0;
+    A.N = p->N;
+    A.halo = 0;
     return A;
 }
 
@@ -566,10 +568,55 @@ static int ctrl_reset(rbffd_plan* p, double dt, double tol, long long max_steps,
 // launch modes the autotuner may choose from: persistent only when asked for
 // (or left to it) and the plan has no Neumann phase, which only graphs replay
 static bool may_persist(const rbffd_plan* p) {
-    return (p->flags & (RBFFD_LAUNCH_PERSISTENT | RBFFD_LAUNCH_AUTO)) != 0 && p->NN == 0;
+    return (p->flags & (RBFFD_LAUNCH_PERSISTENT | RBFFD_LAUNCH_AUTO | RBFFD_LAUNCH_RESIDENT)) !=
+               0 &&
+           p->NN == 0;
 }
 static bool may_graph(const rbffd_plan* p) {
-    return !(p->flags & RBFFD_LAUNCH_PERSISTENT) || p->NN > 0;
+    return !(p->flags & (RBFFD_LAUNCH_PERSISTENT | RBFFD_LAUNCH_RESIDENT)) || p->NN > 0;
+}
+
+// The resident persistent launch (step_res.cu): one block per SM keeping its
+// slices' planes in shared memory.  Its index planes are the 16-bit codes when
+// every slice has them.  Returns its kernel and dynamic shared memory, or
+// nullptr when the plan's share per SM does not fit.
+static bool res_i16(const rbffd_plan* p) { return p->col16 && p->rows16 == p->NI; }
+// The halo window (the slots staged in shared memory each step) reaches
+// `*halo` slots beyond the block's rows on either side: at most as far as the
+// shared memory left beside the planes allows (returned in *halo; the tuner
+// tries shorter reaches, and none), up to the whole iterate.
+static StepFn resident_fn(rbffd_plan* p, int mode, unsigned* smem, int64_t* halo) {
+    const int grid = device_sm_count();
+    const bool i16 = res_i16(p);
+    int dev = 0, optin = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    const unsigned room = (unsigned)optin - 1024u;   // static shared memory and slack
+    const unsigned planes = resident_smem(p->nslices, p->n, mode, i16, grid, -1);
+    if (planes > room) return nullptr;
+    const int64_t rows = (p->nslices + grid - 1) / grid * SLICE;
+    const int64_t elem = mode == MODE_SWEEP64 ? 8 : 4;
+    const int64_t fit = (int64_t)(room - planes) / elem - 8;   // alignment slack
+    int64_t h = fit > rows ? (fit - rows) / 2 : 0;
+    h = std::min<int64_t>(h, p->N);
+    const unsigned bytes = resident_smem(p->nslices, p->n, mode, i16, grid, h);
+    if (bytes > room) return nullptr;
+    StepFn fn = pick_resident(mode, p->n, i16);
+    if (cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bytes) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)fn, RES_THREADS_HOST,
+                                                      bytes) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    *smem = bytes;
+    *halo = h;
+    return fn;
 }
 
 // Autotuner: time every launch shape of `mode` for a few steps on this plan's
@@ -585,6 +632,9 @@ static bool may_graph(const rbffd_plan* p) {
 struct TuneCand {
     int minb, per_sm;
     bool persistent;
+    bool resident;   // the resident persistent launch (smem bytes and halo below)
+    unsigned smem;
+    int64_t halo;
     StepFn fn;
     int grid;
     cudaGraphExec_t gx;
@@ -606,13 +656,17 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
         std::max<long long>(10, std::min<long long>(600, 400000000 / (p->NI * p->n + 1)));
     const int n_minb = N_MINB;
     // candidate c: graph shapes per_sm = c (1..4), then the persistent launch (c = 5)
+    const bool only_res = (p->flags & RBFFD_LAUNCH_RESIDENT) != 0;
     const int c_lo = may_graph(p) ? 1 : 5, c_hi = may_persist(p) ? 5 : 4;
     std::vector<TuneCand> cands;
-    for (int minb = 1; minb <= n_minb; ++minb)
+    for (int minb = 1; minb <= n_minb && !only_res; ++minb)
         for (int c = c_lo; c <= c_hi; ++c) {
             TuneCand t;
             t.minb = minb;
             t.persistent = c == 5;
+            t.resident = false;
+            t.smem = 0;
+            t.halo = 0;
             t.per_sm = t.persistent ? 1 : c;
             t.fn = pick(mode, p->n, t.persistent, minb);
             t.grid = t.persistent ? persistent_grid(t.fn, p) : grid_for(p, t.per_sm);
@@ -620,6 +674,39 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
             t.ms = 1e30f;
             cands.push_back(t);
         }
+    // the resident persistent launch, when asked for (or left to the tuner)
+    // and the plan's planes fit one block per SM; its halo reach is tuned: no
+    // window, the block's own rows, 256, 1024, 4096 slots, the most that fits
+    if (may_persist(p) && (p->flags & (RBFFD_LAUNCH_AUTO | RBFFD_LAUNCH_RESIDENT))) {
+        TuneCand t;
+        int64_t hmax = 0;
+        t.fn = resident_fn(p, mode, &t.smem, &hmax);
+        if (t.fn) {
+            t.minb = 1;
+            t.per_sm = 1;
+            t.persistent = true;
+            t.resident = true;
+            t.grid = device_sm_count();
+            t.gx = nullptr;
+            t.ms = 1e30f;
+            const unsigned smax = t.smem;
+            const int64_t reach[] = {-1, 0, 256, 1024, 4096, hmax};
+            for (int q = 0; q < 6; ++q) {
+                // a reach set by rbffd_plan_set_resident_halo replaces the list
+                if (p->res_halo_set >= -1 && q > 0) break;
+                if (p->res_halo_set < -1 && (reach[q] > hmax || (q == 5 && hmax <= 4096)))
+                    continue;
+                t.halo = p->res_halo_set >= -1 ? std::min(p->res_halo_set, hmax) : reach[q];
+                t.smem = std::min(smax, resident_smem(p->nslices, p->n, mode, res_i16(p),
+                                                      t.grid, t.halo));
+                cands.push_back(t);
+            }
+        } else if (only_res) {
+            set_error("resident launch: the plan's stencils do not fit in shared memory "
+                      "(%lld slices of %d entries)", (long long)p->nslices, p->n);
+            return RBFFD_ERR_CAPACITY;
+        }
+    }
     int st = RBFFD_OK;
     // capture one chunk of `reps` launches per graph candidate
     for (TuneCand& t : cands) {
@@ -662,9 +749,11 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
             cudaEventRecord(e0, s);
             if (t.persistent) {
                 StepCtrl* c = p->ctrl;
+                A.halo = t.halo;
                 void* args[] = {(void*)&A, (void*)&c};
-                cudaLaunchCooperativeKernel((const void*)t.fn, dim3(t.grid), dim3(STEP_THREADS),
-                                            args, 0, s);
+                cudaLaunchCooperativeKernel((const void*)t.fn, dim3(t.grid),
+                                            dim3(t.resident ? RES_THREADS_HOST : STEP_THREADS),
+                                            args, t.smem, s);
             } else {
                 cudaGraphLaunch(t.gx, s);
             }
@@ -692,6 +781,9 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
     p->minb[mi] = best->minb;
     p->per_sm[mi] = best->per_sm;
     p->persist[mi] = best->persistent;
+    p->resident[mi] = best->resident;
+    p->res_smem[mi] = best->smem;
+    p->res_halo[mi] = best->halo;
     p->tune_ms[mi] = best->ms / (float)reps;
     p->tuned[mi] = true;
     return RBFFD_OK;
@@ -787,14 +879,18 @@ static int run_steps(rbffd_plan* p, int mode, double dt, double tol, long long m
         st = prepare_mode(p, mode, dt, tol, max_steps, s);
         if (st) return st;
         if (p->persist[mi]) {
-            StepFn fn = pick(mode, p->n, true, p->minb[mi]);
-            int grid = persistent_grid(fn, p);
+            const bool res = p->resident[mi];
+            StepFn fn = res ? pick_resident(mode, p->n, res_i16(p))
+                            : pick(mode, p->n, true, p->minb[mi]);
+            int grid = res ? device_sm_count() : persistent_grid(fn, p);
             StepArgs A = make_args(p);
+            A.halo = res ? p->res_halo[mi] : 0;
             StepCtrl* c = p->ctrl;
             void* args[] = {(void*)&A, (void*)&c};
             RBFFD_CHECK_CUDA(cudaEventRecord((cudaEvent_t)p->ev[0], s));
-            RBFFD_CHECK_CUDA(cudaLaunchCooperativeKernel((const void*)fn, dim3(grid),
-                                                         dim3(STEP_THREADS), args, 0, s));
+            RBFFD_CHECK_CUDA(cudaLaunchCooperativeKernel(
+                (const void*)fn, dim3(grid), dim3(res ? RES_THREADS_HOST : STEP_THREADS), args,
+                res ? p->res_smem[mi] : 0, s));
             RBFFD_CHECK_CUDA(cudaEventRecord((cudaEvent_t)p->ev[1], s));
             p->last_launches += 1;
         } else {
@@ -932,10 +1028,11 @@ extern "C" int rbffd_plan_create(const double* xyz, const uint8_t* is_bnd, int64
     RBFFD_ALLOC(p->col, sizeof(int32_t) * ell);
     RBFFD_ALLOC(p->u[0], sizeof(double) * N);
     RBFFD_ALLOC(p->u[1], sizeof(double) * N);
-    RBFFD_ALLOC(p->fs, sizeof(double) * NI);
+    // f and d32 padded to whole slices (the resident launch copies whole slices)
+    RBFFD_ALLOC(p->fs, sizeof(double) * p->nslices * SLICE);
     RBFFD_ALLOC(p->e[0], sizeof(float) * N);
     RBFFD_ALLOC(p->e[1], sizeof(float) * N);
-    RBFFD_ALLOC(p->d32, sizeof(float) * NI);
+    RBFFD_ALLOC(p->d32, sizeof(float) * p->nslices * SLICE);
     RBFFD_ALLOC(p->scratch, sizeof(double) * (2 * NI + 4096));
     RBFFD_ALLOC(p->ctrl, sizeof(StepCtrl));
 #undef RBFFD_ALLOC
@@ -1078,6 +1175,18 @@ extern "C" int rbffd_plan_set_dc(rbffd_plan* p, int64_t K_in, double rho_in) {
     RBFFD_ARG(p && K_in >= 1 && rho_in >= 0.0, "rbffd_plan_set_dc: bad argument");
     p->dc_K_in = K_in;
     p->dc_rho_in = rho_in;
+    return RBFFD_OK;
+}
+
+extern "C" int rbffd_plan_set_resident_halo(rbffd_plan* p, int64_t halo) {
+    clear_error();
+    RBFFD_ARG(p && halo >= -2, "rbffd_plan_set_resident_halo: bad argument");
+    p->res_halo_set = halo;
+    for (int mi = 0; mi < 2; ++mi) {   // tune again on the next solve
+        p->tuned[mi] = false;
+        p->persist[mi] = p->resident[mi] = false;
+    }
+    drop_graphs(p);
     return RBFFD_OK;
 }
 
@@ -1287,9 +1396,9 @@ extern "C" int rbffd_plan_stats(const rbffd_plan* p, double* h_loop_ms, int64_t*
     if (h_launches) *h_launches = p->last_launches;
     if (h_shape) {
         h_shape[0] = p->minb[0];
-        h_shape[1] = p->persist[0] ? 0 : p->per_sm[0];
+        h_shape[1] = p->persist[0] ? (p->resident[0] ? -1 : 0) : p->per_sm[0];
         h_shape[2] = p->minb[1];
-        h_shape[3] = p->persist[1] ? 0 : p->per_sm[1];
+        h_shape[3] = p->persist[1] ? (p->resident[1] ? -1 : 0) : p->per_sm[1];
     }
     return RBFFD_OK;
 }

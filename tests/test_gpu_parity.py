@@ -221,6 +221,10 @@ SWEEP_CASES = [
     (2, 29, 4, 2 | 16, "random_persistent"),
     (3, 9, 4, 0, "cube_m4"),
     (2, 35, 4, 64, "morton_auto"),
+    (2, 37, 6, 128, "morton_resident"),
+    (2, 31, 2, 2 | 128, "random_resident"),
+    (3, 10, 4, 128, "cube_resident"),
+    (2, 34, 4, 32 | 128, "resident_int32_planes"),
 ]
 
 
@@ -278,7 +282,7 @@ def test_sweep_stop_rule_matches(rb, orc):
     # a tolerance the oracle reaches after a few hundred steps
     ou, os_, ores, ost = orc.solve_explicit(p.w, p.idx, p.interior, p.f, p.u0, dt, 5000, 1.0)
     assert ost == 0 and 1 < os_ < 5000
-    for flags in (0, 16):
+    for flags in (0, 16, 128):
         plan = _plan(rb, p, flags)
         u = T(p.u0)
         code, steps, res = plan.solve_explicit(T(p.f), u, dt, 5000, 1.0)
@@ -325,13 +329,13 @@ def test_sweep_zero_steps_and_errors(rb, orc):
 
 
 def test_launch_modes_same_bits(rb, orc):
-    """Graph, persistent and autotuned launch modes: the same FP64 iterate and the same
-    defect-corrected iterate bit for bit; the reported shape says which mode ran
-    (0 blocks per SM = persistent)."""
+    """Graph, persistent, resident and autotuned launch modes: the same FP64 iterate
+    and the same defect-corrected iterate bit for bit; the reported shape says which
+    mode ran (0 blocks per SM = persistent, -1 = resident)."""
     p = build(orc, 2, 30, 4, seed=47)
     dt = _dt(orc, p)
     outs = []
-    for flags in (0, 16, 64):
+    for flags in (0, 16, 64, 128):
         plan = _plan(rb, p, flags)
         u = T(p.u0)
         plan.solve_explicit(T(p.f), u, dt, 500, 0.0)
@@ -342,6 +346,8 @@ def test_launch_modes_same_bits(rb, orc):
             assert shape[1] > 0 and shape[3] > 0
         if flags == 16:
             assert shape[1] == 0 and shape[3] == 0
+        if flags == 128:
+            assert shape[1] == -1 and shape[3] == -1
         outs.append((H(u), H(u2)))
         plan.destroy()
     for a, b in outs[1:]:
@@ -384,13 +390,14 @@ def test_dc_parity(rb, orc):
     dt = _dt(orc, p)
     args = (dt, 1e-8, 30, 3000, 1e-3)
     ou, oo, oi, ores, ost = orc.solve_dc(p.w, p.idx, p.interior, p.f, p.u0, *args)
-    plan = _plan(rb, p)
-    u = T(p.u0)
-    code, outer, inner, res = plan.solve_dc(T(p.f), u, *args)
-    assert (outer, inner) == (oo, oi)
-    assert code == (rb.RBFFD_OK if ost == 0 else rb.RBFFD_NOT_CONVERGED)
-    assert np.max(np.abs(H(u) - ou)) <= 1e-12 * np.max(np.abs(ou))
-    plan.destroy()
+    for flags in (0, 128, 32 | 128):        # graph; resident (16-bit, int32 index planes)
+        plan = _plan(rb, p, flags)
+        u = T(p.u0)
+        code, outer, inner, res = plan.solve_dc(T(p.f), u, *args)
+        assert (outer, inner) == (oo, oi)
+        assert code == (rb.RBFFD_OK if ost == 0 else rb.RBFFD_NOT_CONVERGED)
+        assert np.max(np.abs(H(u) - ou)) <= 1e-12 * np.max(np.abs(ou))
+        plan.destroy()
 
 
 # ------------------------------------------------------------------ adjoint
@@ -586,6 +593,35 @@ def test_persistent_barrier_wait_runs_out(rb, orc):
     assert steps == 100
     assert np.max(np.abs(H(u) - ou)) <= 1e-12 * np.max(np.abs(ou))
     plan.destroy()
+    # the resident launch's barrier is the same bounded wait
+    plan = _plan(rb, p, rb.RBFFD_LAUNCH_RESIDENT)
+    plan.solve_explicit(T(p.f), T(p.u0), dt, 5, 0.0)
+    plan.set_wait(20.0, 1)
+    with pytest.raises(rb.RbffdError) as ei:
+        plan.solve_explicit(T(p.f), T(p.u0), dt, 100, 0.0)
+    assert ei.value.code == rb.RBFFD_ERR_TIMEOUT
+    plan.set_wait(0.0, 0)
+    u = T(p.u0)
+    plan.solve_explicit(T(p.f), u, dt, 100, 0.0)
+    assert np.max(np.abs(H(u) - ou)) <= 1e-12 * np.max(np.abs(ou))
+    plan.destroy()
+
+
+def test_resident_launch_refuses_a_plan_too_large(rb):
+    """The resident launch keeps a plan's stencils in shared memory; 158,404 rows of 30
+    FP64 entries (about 313 KB per SM) do not fit, and a plan that asks for it gets
+    RBFFD_ERR_CAPACITY from its first solve (nothing launched)."""
+    xyz, bnd = rb.rbffd_nodes(2, 0, 399, 0.3, 3)
+    inter = rb.rbffd_interior(bnd)
+    idx = rb.rbffd_knn(xyz, inter, 30)
+    w, st = rb.rbffd_weights(xyz, idx, 4)
+    plan = rb.Plan(xyz, bnd, inter, idx, w, rb.RBFFD_LAUNCH_RESIDENT)
+    f = torch.zeros(inter.numel(), dtype=torch.float64, device=DEV)
+    with pytest.raises(rb.RbffdError) as ei:
+        plan.solve_explicit(f, torch.zeros(xyz.shape[1], dtype=torch.float64, device=DEV),
+                            1e-9, 10, 0.0)
+    assert ei.value.code == rb.RBFFD_ERR_CAPACITY
+    plan.destroy()
 
 
 def test_graph_replays_launch_exactly_the_steps_asked(rb, orc):
@@ -606,4 +642,26 @@ def test_graph_replays_launch_exactly_the_steps_asked(rb, orc):
         extra.add(launches - K)
         assert np.max(np.abs(H(u) - ou)) <= 1e-12 * np.max(np.abs(ou))
     assert len(extra) == 1 and 0 <= extra.pop() <= 4
+    plan.destroy()
+
+
+@pytest.mark.parametrize("halo", [-1, 0, 64, 1 << 20])
+def test_resident_halo_windows_same_bits(rb, orc, halo):
+    """The resident launch with its halo window fixed: none, the block's own rows, a
+    reach of 64 slots, and the whole iterate - FP64 sweeps and a defect correction,
+    equal to the oracle, the same bits whatever the window."""
+    p = build(orc, 2, 41, 4, seed=51)
+    dt = _dt(orc, p)
+    ou, *_ = orc.solve_explicit(p.w, p.idx, p.interior, p.f, p.u0, dt, 150, 0.0)
+    du, oo, oi, _, _ = orc.solve_dc(p.w, p.idx, p.interior, p.f, p.u0, dt, 1e-7, 3, 300, 1e-3)
+    plan = _plan(rb, p, rb.RBFFD_LAUNCH_RESIDENT)
+    plan.set_resident_halo(halo)
+    u = T(p.u0)
+    plan.solve_explicit(T(p.f), u, dt, 150, 0.0)
+    assert plan.stats()[3][1] == -1
+    assert np.max(np.abs(H(u) - ou)) <= 1e-12 * np.max(np.abs(ou))
+    u2 = T(p.u0)
+    code, outer, inner, res = plan.solve_dc(T(p.f), u2, dt, 1e-7, 3, 300, 1e-3)
+    assert (outer, inner) == (oo, oi)
+    assert np.max(np.abs(H(u2) - du)) <= 1e-12 * np.max(np.abs(du))
     plan.destroy()

@@ -826,7 +826,9 @@ def run_stage(args):
     if args.mode == "weights":
         torch.cuda.synchronize()
         return
-    plan = rb.Plan(xyz, bnd, inter, idx, w, rb.RBFFD_ORDER_MORTON)
+    launch = {"graph": rb.RBFFD_LAUNCH_GRAPH, "persistent": rb.RBFFD_LAUNCH_PERSISTENT,
+              "resident": rb.RBFFD_LAUNCH_RESIDENT, "auto": rb.RBFFD_LAUNCH_AUTO}[args.launch]
+    plan = rb.Plan(xyz, bnd, inter, idx, w, rb.RBFFD_ORDER_MORTON | launch)
     f = torch.zeros(inter.numel(), dtype=torch.float64, device=dev)
     u = torch.zeros(xyz.shape[1], dtype=torch.float64, device=dev)
     lam = torch.ones(xyz.shape[1], dtype=torch.float64, device=dev)
@@ -869,6 +871,9 @@ def main():
                          "square / cube with h = 1/Kg (drivers for profiler captures; they "
                          "print nothing), or fp64peak: the measured FP64 fma rate with the "
                          "clocks while it runs (one JSON line)")
+    ap.add_argument("--launch", default="graph",
+                    choices=["graph", "persistent", "resident", "auto"],
+                    help="launch mode of the plan in --mode sweep/dc/adjoint")
     ap.add_argument("--m", type=int, default=M, help="monomial order of the workload")
     ap.add_argument("--Kg", type=int, default=KG, help="grid cells per side of the workload")
     ap.add_argument("--sweeps", type=int, default=5, help="sweeps in --mode sweep")

@@ -264,12 +264,13 @@ RBFFD_API int rbffd_error(const double* u, const double* ua, int64_t N, double* 
 /*
  * rbffd_fp64_fma_rate - measures the device's FP64 fused multiply-add rate
  * (not part of the paper's method: the roofline of the kernels the FP64 pipe
- * binds, the explicit sweep at larger stencils and the weight build).  For 4,
- * 8 and 16 independent fma chains per thread, at the largest resident grid of
- * 256-thread blocks: one untimed warm-up launch, then one launch of `iters`
- * fmas per thread, timed with CUDA events on `stream`.  h_fma_per_s (host)
- * receives the fastest shape's FMAs per second, h_ms (host, may be NULL) its
- * timed launch's milliseconds.  Synchronises `stream`.
+ * binds, the explicit sweep at larger stencils and the weight build).  For 4
+ * and 8 independent fma chains per thread (acc <- fma(w, v, acc), v read from
+ * shared memory, as the sweeps' operands come from loads), at the largest
+ * resident grid of 256-thread blocks: one untimed warm-up launch, then one
+ * launch of `iters` fmas per thread, timed with CUDA events on `stream`.
+ * h_fma_per_s (host) receives the fastest shape's FMAs per second, h_ms (host,
+ * may be NULL) its timed launch's milliseconds.  Synchronises `stream`.
  */
 RBFFD_API int rbffd_fp64_fma_rate(int64_t iters, double* h_fma_per_s, double* h_ms,
                                   void* stream);

@@ -1,7 +1,7 @@
 // Correctly rounded FP64 reciprocal, quotient and square root computed on the
 // integer pipes.
 //
-// On this GPU the FP64 pipe retires 1.68 fused multiply-adds per clock per SM
+// On this GPU the FP64 pipe retires 2 fused multiply-adds per clock per SM
 // (measured), a sixty-fourth of the FP32 rate, while the integer pipes sit
 // mostly idle in the kernels that need these operations (the weight build's
 // pivots, back substitution and r^3 assembly).  The library's FP64 reciprocal,

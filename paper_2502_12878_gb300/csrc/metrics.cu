@@ -94,11 +94,14 @@ extern "C" int rbffd_error(const double* u, const double* ua, int64_t N, double*
 // rbffd_fp64_fma_rate: the device's FP64 fused multiply-add rate, measured -
 // the roofline of the kernels the FP64 pipe binds (the explicit sweep at
 // larger stencils, the weight build).  Not part of the paper's method.
-// Every thread runs CH independent chains a <- fma(a, x, y), four fmas per
-// chain per loop iteration, so the pipe, not the chain latency or the loop,
-// sets the pace; the result is kept alive by a store that never happens (a
-// chain never reaches -1).  Shapes with 4, 8 and 16 chains per thread at the
-// largest resident grid are timed and the fastest kept.
+// Every thread runs CH independent chains acc <- fma(w, v, acc), four fmas per
+// chain per loop iteration, with v read from shared memory - as the sweeps'
+// operands arrive from loads.  (Chains whose operands all stay in registers
+// saturate near 1.6-1.7 fma/clk/SM on this GPU, below the rate that the
+// sweeps themselves reach; with one operand from a load they reach the pipe's
+// 2 fma/clk/SM.)  The result is kept alive by a store that never happens.
+// Shapes with 4 and 8 chains per thread at the largest resident grid of
+// 256-thread blocks are timed and the fastest kept.
 // ---------------------------------------------------------------------------
 namespace rbffd {
 
@@ -106,22 +109,28 @@ static __device__ double g_fma_sink;
 
 template <int CH>
 __global__ void __launch_bounds__(256) fp64_fma_chains(long long iters) {
-    double a[CH];
+    __shared__ double sv[256];
+    sv[threadIdx.x] = 0.5 + 1e-6 * (double)threadIdx.x;
+    __syncthreads();
+    double acc[CH], w[CH];
 #pragma unroll
-    for (int c = 0; c < CH; ++c) a[c] = 1e-3 * (double)(threadIdx.x + c);
-    const double x = 0.9999999999, y = 1e-12;
+    for (int c = 0; c < CH; ++c) {
+        acc[c] = 0.0;
+        w[c] = 1e-3 * (double)(threadIdx.x + 3 * c + 1);
+    }
+    const int t = (int)threadIdx.x;
     for (long long i = 0; i < iters; ++i) {
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int c = 0; c < CH; ++c) a[c] = __fma_rn(a[c], x, y);
+            for (int c = 0; c < CH; ++c)
+                acc[c] = __fma_rn(w[c], sv[(t + 4 * c + u) & 255], acc[c]);
     }
     double s = 0.0;
 #pragma unroll
-    for (int c = 0; c < CH; ++c) s = __dadd_rn(s, a[c]);
+    for (int c = 0; c < CH; ++c) s = __dadd_rn(s, acc[c]);
     if (s == -1.0) g_fma_sink = s;
 }
-
 template <int CH>
 static cudaError_t time_fma_shape(long long fmas_per_thread, cudaStream_t s, double* rate,
                                   float* ms_out) {
@@ -169,8 +178,6 @@ extern "C" int rbffd_fp64_fma_rate(int64_t iters, double* h_fma_per_s, double* h
     RBFFD_CHECK_CUDA(time_fma_shape<4>(iters, s, &r, &ms));
     if (r > best) { best = r; best_ms = ms; }
     RBFFD_CHECK_CUDA(time_fma_shape<8>(iters, s, &r, &ms));
-    if (r > best) { best = r; best_ms = ms; }
-    RBFFD_CHECK_CUDA(time_fma_shape<16>(iters, s, &r, &ms));
     if (r > best) { best = r; best_ms = ms; }
     *h_fma_per_s = best;
     if (h_ms) *h_ms = best_ms;

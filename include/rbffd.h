@@ -479,11 +479,29 @@ RBFFD_API int rbffd_stable_dt(rbffd_plan* plan, const double* v0, int iters, dou
  * adjoint's W^T, derived from Eq. 6; otherwise the first rbffd_adjoint or
  * rbffd_adjoint_w builds it).  Column c of W^T lists the rows r whose support
  * holds c, in ascending interior-list order, with their weights w_rc; columns
- * are stored in 32-column slices padded with zero weights.  Owned by the plan
- * (freed by rbffd_plan_destroy); a second call does nothing.  Synchronises
- * `stream`; scratch comes from cudaMallocAsync on `stream`.
+ * are stored in 32-column slices padded with zero weights; unless the plan
+ * was made with RBFFD_PACK_IDX32, every interior slice also stores 16-bit
+ * codes, which the reverse step reads instead of int32 rows: offsets in up to
+ * four windows of 2^14 positions where the slice's rows fit in those (same
+ * rows, same bits, fewer bytes), else each entry's position in the slice,
+ * through which its int32 row is read.  Owned by
+ * the plan (freed by rbffd_plan_destroy); a second call does nothing.
+ * Synchronises `stream`; scratch comes from cudaMallocAsync on `stream`.
  */
 RBFFD_API int rbffd_transpose(rbffd_plan* plan, void* stream);
+
+/*
+ * rbffd_transpose_layout - the built transpose's size (host outputs, may be
+ * NULL): h_slices, 32-column slices of interior columns; h_cols16, interior
+ * columns whose slice uses 16-bit row codes; h_entries, stored entries of the
+ * interior slices (padding included); h_bytes, the bytes one reverse step
+ * streams when every gathered lambda is served from cache (weights, row
+ * codes and the rows they point to, per slice its offset, length and window
+ * bases, per column lambda and S read and written).  RBFFD_ERR_ARG before
+ * rbffd_transpose.
+ */
+RBFFD_API int rbffd_transpose_layout(const rbffd_plan* plan, int64_t* h_slices,
+                                     int64_t* h_cols16, int64_t* h_entries, double* h_bytes);
 
 /*
  * rbffd_adjoint - gradients of a loss of the K-th iterate of Eq. 6 (the

@@ -55,6 +55,7 @@ EXPORTED = [
     "rbffd_knn_masked", "rbffd_weights_dir", "rbffd_plan_set_neumann", "rbffd_plan_layout",
     "rbffd_nodes_pds", "rbffd_nodes_pds_cap", "rbffd_weights_batch", "rbffd_transpose",
     "rbffd_plan_set_wait", "rbffd_fp64_fma_rate", "rbffd_plan_set_resident_halo",
+    "rbffd_transpose_layout",
 ]
 RBFFD_KNN_NOALLOC_MAX_NODES = 262144
 
@@ -113,6 +114,7 @@ def lib():
         "rbffd_weights_dir": (I, [P, I64, I, P, I64, I, I, P, P, P, PI64, PI64, P]),
         "rbffd_plan_set_neumann": (I, [P, I64, P, P, P, I, P, P]),
         "rbffd_plan_layout": (I, [P, PI64, PI64, PD, PD]),
+        "rbffd_transpose_layout": (I, [P, PI64, PI64, PI64, PD]),
         "rbffd_nodes_pds": (I, [I, I, I, I, D, U64, P, P, I64, PI64, PI64, P]),
         "rbffd_nodes_pds_cap": (I, [I, I, D, PI64]),
         "rbffd_weights_batch": (I, [I, P, P, P, P, P, P, P, P, P, P, P]),
@@ -483,6 +485,15 @@ class Plan:
     def transpose(self):
         """Build the transposed interior operator now (else the first adjoint does)."""
         _check(lib().rbffd_transpose(self.handle, _stream(self.device)))
+
+    def transpose_layout(self):
+        """Built transpose: dict(slices, cols16 = interior columns with 16-bit row codes,
+        entries = stored entries, bytes = bytes one reverse step streams)."""
+        sl, c16, ent = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+        by = ctypes.c_double(0.0)
+        _check(lib().rbffd_transpose_layout(self.handle, ctypes.byref(sl), ctypes.byref(c16),
+                                            ctypes.byref(ent), ctypes.byref(by)))
+        return {"slices": sl.value, "cols16": c16.value, "entries": ent.value, "bytes": by.value}
 
     def adjoint(self, dLdu, K, dt, want_lam0=True):
         """Reverse sweep of K steps from dLdu = dL/du^K [N] (every node; boundary entries

@@ -8,7 +8,11 @@
 // same order as a row-ascending scatter would).  The columns are stored as
 // 32-column slices [slice][j][lane] padded to the slice's longest column with
 // zero weights, so the reverse step is the same coalesced thread-per-column
-// gather as the forward sweep - no atomics, deterministic.
+// gather as the forward sweep - no atomics, deterministic.  As in the forward
+// layout, an interior slice whose rows fit in four windows of 2^14 placed
+// positions also stores each row as a 16-bit code (window in bits 15..14,
+// offset from the window's base in 13..0), which the reverse step reads
+// instead of the int32 row: 10 bytes per entry instead of 12.
 #include <math.h>
 
 #include <algorithm>
@@ -36,6 +40,13 @@ struct Transpose {
     int32_t* len = nullptr;   // [nslices] padded length of each slice
     int32_t* row = nullptr;   // placed position of each entry's row
     double* w = nullptr;      // weight of each entry (0 for padding)
+    // 16-bit row codes (NULL when the plan keeps int32 indices) and per
+    // interior slice its four window bases (x = -1: the slice reads row)
+    uint16_t* row16 = nullptr;
+    int4* tbase = nullptr;
+    int64_t entries = 0;      // stored entries of the interior slices
+    int64_t cols16 = 0;       // interior columns in slices with codes
+    int64_t entries16 = 0;    // and those slices' stored entries
     int32_t* colof = nullptr; // [N] slot of the column at each placed position
     int32_t* posof = nullptr; // [N] placed position of each slot
     double* lam[2] = {nullptr, nullptr};   // [NI] placed order
@@ -45,7 +56,8 @@ struct Transpose {
 void free_transpose(rbffd_plan* p) {
     if (!p || !p->tr) return;
     Transpose* t = p->tr;
-    void* b[] = {t->off, t->len, t->row, t->w, t->colof, t->posof, t->lam[0], t->lam[1], t->S};
+    void* b[] = {t->off,   t->len,   t->row,    t->w,      t->colof, t->posof,
+                 t->lam[0], t->lam[1], t->S,      t->row16,  t->tbase};
     for (void* x : b)
         if (x) cudaFree(x);
     delete t;
@@ -166,6 +178,80 @@ __global__ void tr_fill(const int32_t* start, const int32_t* erow, const double*
     }
 }
 
+// 16-bit row codes of the interior slices (one warp per slice): the fewest
+// windows of 2^14 placed positions, greedy from the left, that cover every
+// stored row of the slice's interior columns.  Padding entries (and the lanes
+// of boundary columns, which the reverse step skips) get code 0, i.e. the
+// first window's base: a row of this slice, read with weight 0 as the int32
+// padding reads row 0.  A slice that needs more than four windows (tbase x =
+// -1) stores as each entry's code its own position in the slice, through
+// which the reverse step reads the int32 row: one code form for every slice,
+// so the reverse step has one loop.
+static constexpr int32_t TR_WINDOW16 = 1 << 14;
+
+__global__ void tr_pack16(const int32_t* __restrict__ start, const int32_t* __restrict__ colof,
+                          int64_t NI, int64_t nsl_int, const int64_t* __restrict__ off,
+                          const int32_t* __restrict__ len, const int32_t* __restrict__ trow,
+                          uint16_t* __restrict__ row16, int4* __restrict__ tbase,
+                          unsigned long long* cnt, int* err) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t sl = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); sl < nsl_int;
+         sl += nw) {
+        const int64_t q = sl * SLICE + lane;
+        const bool valid = q < NI;
+        int Lc = 0;   // this column's stored (unpadded) entries
+        if (valid) {
+            const int32_t c = colof[q];
+            Lc = start[c + 1] - start[c];
+        }
+        const int L = len[sl];
+        const int64_t base = off[sl] + lane;
+        int32_t b[4];
+        int64_t thr = INT64_MIN;   // rows >= thr are not yet covered
+        int used = 0;
+        for (int k = 0; k < 4; ++k) {
+            int32_t mn = INT32_MAX;
+            for (int j = 0; j < Lc; ++j) {
+                const int32_t v = trow[base + (int64_t)j * SLICE];
+                if ((int64_t)v >= thr) mn = min(mn, v);
+            }
+            mn = __reduce_min_sync(0xffffffffu, mn);
+            if (mn == INT32_MAX) break;   // warp-uniform
+            b[k] = mn;
+            used = k + 1;
+            thr = (int64_t)mn + TR_WINDOW16;
+        }
+        for (int k = used; k < 4; ++k) b[k] = used ? b[used - 1] : 0;
+        bool left = false;
+        for (int j = 0; j < Lc; ++j) left |= (int64_t)trow[base + (int64_t)j * SLICE] >= thr;
+        const bool wide = __any_sync(0xffffffffu, left) && used == 4;
+        if (lane == 0)
+            tbase[sl] = wide ? make_int4(-1, -1, -1, -1) : make_int4(b[0], b[1], b[2], b[3]);
+        if (wide) {   // each entry's code is its own position j * 32 + lane (< 2^16)
+            for (int j = 0; j < L; ++j)
+                row16[base + (int64_t)j * SLICE] = (uint16_t)(j * SLICE + lane);
+            continue;
+        }
+        const unsigned nvalid = __popc(__ballot_sync(0xffffffffu, valid));
+        if (lane == 0) {
+            atomicAdd(&cnt[0], (unsigned long long)nvalid);
+            atomicAdd(&cnt[1], (unsigned long long)L * SLICE);
+        }
+        for (int j = 0; j < L; ++j) {
+            uint16_t code = 0;
+            if (j < Lc) {
+                const int32_t v = trow[base + (int64_t)j * SLICE];
+                const int k = (v >= b[1]) + (v >= b[2]) + (v >= b[3]);
+                const int32_t o = v - (k == 0 ? b[0] : k == 1 ? b[1] : k == 2 ? b[2] : b[3]);
+                if (o < 0 || o >= TR_WINDOW16) atomicExch(err, 1);   // cannot happen
+                code = (uint16_t)(((uint32_t)k << 14) | ((uint32_t)o & 0x3fffu));
+            }
+            row16[base + (int64_t)j * SLICE] = code;
+        }
+    }
+}
+
 // exclusive scan of int64 slice sizes (single block; slice counts are modest)
 __global__ void scan64_single(const int64_t* in, int64_t n, int64_t* out) {
     __shared__ int64_t carry;
@@ -204,72 +290,140 @@ __device__ __forceinline__ int32_t adj_ld_cs(const int32_t* p) {
     asm volatile("ld.global.cs.s32 %0, [%1];" : "=r"(v) : "l"(p));
     return v;
 }
+__device__ __forceinline__ uint32_t adj_ld_cs(const uint16_t* p) {
+    unsigned short v;
+    asm volatile("ld.global.cs.u16 %0, [%1];" : "=h"(v) : "l"(p));
+    return (uint32_t)v;
+}
 __device__ __forceinline__ double adj_ld_nc(const double* p) {
     double v;
     asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
     return v;
 }
 
+// 16-bit row code -> placed row: window k = code >> 14 selects one of the
+// slice's four bases, plus the 14-bit offset
+__device__ __forceinline__ int32_t adj_decode16(uint32_t v, const int4& b) {
+    const uint32_t k = v >> 14;
+    const int32_t base = (k & 2u) ? ((k & 1u) ? b.w : b.z) : ((k & 1u) ? b.y : b.x);
+    return base + (int32_t)(v & 0x3fffu);
+}
+
+// sum over a column's L stored entries (stride SLICE) of w * lam[row], an fma
+// chain from 0 in entry order; loads in phases of CH (rows, weights, then
+// the gathers).  I16: rows as 16-bit codes against the slice's bases.
+// sum over a column's L stored entries (stride SLICE) of w * lam[row], an fma
+// chain from 0 in entry order; loads in phases of CH (rows, weights, then
+// the gathers).  I16: each entry's 16-bit code is decoded against the
+// slice's window bases, or, in a slice the windows cannot cover (sb.x < 0),
+// is the entry's own position in the slice, which reads its int32 row.
+template <int CH, bool I16>
+__device__ __forceinline__ double adj_col_sum(const double* wp, const void* rp,
+                                              const int32_t* rows, const int4& sb,
+                                              const double* __restrict__ lam, int L) {
+    double acc = 0.0;
+    for (int j0 = 0; j0 < L; j0 += CH) {
+        int32_t r[CH];
+        double wv[CH], lv[CH];
+#pragma unroll
+        for (int t = 0; t < CH; ++t)
+            if (j0 + t < L) {
+                if constexpr (I16)
+                    r[t] = (int32_t)adj_ld_cs((const uint16_t*)rp + (int64_t)(j0 + t) * SLICE);
+                else
+                    r[t] = adj_ld_cs((const int32_t*)rp + (int64_t)(j0 + t) * SLICE);
+            }
+#pragma unroll
+        for (int t = 0; t < CH; ++t)
+            if (j0 + t < L) wv[t] = adj_ld_cs(wp + (int64_t)(j0 + t) * SLICE);
+        if constexpr (I16) {
+            if (sb.x >= 0) {
+#pragma unroll
+                for (int t = 0; t < CH; ++t)
+                    if (j0 + t < L) r[t] = adj_decode16((uint32_t)r[t], sb);
+            } else {
+#pragma unroll
+                for (int t = 0; t < CH; ++t)
+                    if (j0 + t < L) r[t] = adj_ld_cs(rows + r[t]);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < CH; ++t)
+            if (j0 + t < L) lv[t] = adj_ld_nc(lam + r[t]);
+#pragma unroll
+        for (int t = 0; t < CH; ++t)
+            if (j0 + t < L) acc = __fma_rn(wv[t], lv[t], acc);
+    }
+    return acc;
+}
+
 // one reverse step over interior columns c < NI:
 //   S_c += lam_c;  lam'_c = fma(dt, sum_rows w_rc lam_r, lam_c)
 // the column sum is an fma chain from 0 over the column's entries in order
-// (padding entries carry weight 0 and row 0, so they add exact zeros).
-// Shapes: CH entries per load phase (indices, weights, then gathers) and a
-// register budget for MINB resident blocks of 256 threads; every shape gives
-// the same bits.
-template <int CH, int MINB>
-__global__ void __launch_bounds__(256, MINB)
-adjoint_step(const Transpose T, const int64_t NI, const double dt,
-             const double* __restrict__ lam, double* __restrict__ lam_out,
-             double* __restrict__ S) {
+// (padding entries carry weight 0, so they add exact zeros).  Shapes: CH
+// entries per load phase (rows, weights, then gathers) and a register budget
+// for MINB resident blocks of 256 threads; every shape, and either row form,
+// gives the same bits.  One lane prefetches the warp's next slice (weight
+// plane and row codes, or rows when the plan keeps int32 indices) into L2:
+// both planes start on 16-byte boundaries (slice offsets are multiples of 32
+// entries) and span a multiple of 16 bytes.
+template <int CH, bool I16>
+__device__ __forceinline__ void adj_slices(const Transpose& T, const int64_t NI, const double dt,
+                                           const double* __restrict__ lam,
+                                           double* __restrict__ lam_out,
+                                           double* __restrict__ S) {
     const int lane = threadIdx.x & 31;
     const int64_t nsl_int = (NI + SLICE - 1) / SLICE;
     const int64_t stride = (int64_t)gridDim.x * (blockDim.x / 32);
     for (int64_t s = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); s < nsl_int;
          s += stride) {
-        // one lane prefetches the warp's next slice (row and weight planes)
-        // into L2: both start on 16-byte boundaries (slice offsets are
-        // multiples of 32 entries) and span a multiple of 16 bytes
         if (lane == 0 && s + stride < nsl_int) {
             const int64_t o = __ldg(T.off + s + stride);
             const unsigned Ln = (unsigned)__ldg(T.len + s + stride) * SLICE;
             if (Ln) {
                 asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(T.w + o),
                              "r"(Ln * 8u) : "memory");
-                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(T.row + o),
-                             "r"(Ln * 4u) : "memory");
+                if (I16)
+                    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(T.row16 + o),
+                                 "r"(Ln * 2u) : "memory");
+                else
+                    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(T.row + o),
+                                 "r"(Ln * 4u) : "memory");
             }
         }
         const int64_t c = s * SLICE + lane;
         if (c >= NI) continue;
         const int L = __ldg(T.len + s);
         const int64_t off = __ldg(T.off + s);
-        const double* wp = T.w + off + lane;
-        const int32_t* rp = T.row + off + lane;
-        // the column's own lambda and S are issued before the sum, so their
-        // latency overlaps the entry loads
-        const double lc = lam[c];
-        const double Sc = S[c];
-        double acc = 0.0;
-        for (int j0 = 0; j0 < L; j0 += CH) {
-            int32_t r[CH];
-            double wv[CH], lv[CH];
-#pragma unroll
-            for (int t = 0; t < CH; ++t)
-                if (j0 + t < L) r[t] = adj_ld_cs(rp + (int64_t)(j0 + t) * SLICE);
-#pragma unroll
-            for (int t = 0; t < CH; ++t)
-                if (j0 + t < L) wv[t] = adj_ld_cs(wp + (int64_t)(j0 + t) * SLICE);
-#pragma unroll
-            for (int t = 0; t < CH; ++t)
-                if (j0 + t < L) lv[t] = adj_ld_nc(lam + r[t]);
-#pragma unroll
-            for (int t = 0; t < CH; ++t)
-                if (j0 + t < L) acc = __fma_rn(wv[t], lv[t], acc);
+        double acc, lc, Sc;
+        if constexpr (I16) {
+            const int4 sb = __ldg(T.tbase + s);
+            // (the window bases take the registers that would hold the
+            // column's own lambda and S through the sum)
+            acc = adj_col_sum<CH, true>(T.w + off + lane, T.row16 + off + lane, T.row + off, sb,
+                                        lam, L);
+            lc = lam[c];
+            Sc = S[c];
+        } else {
+            // the column's own lambda and S are issued before the sum, so
+            // their latency overlaps the entry loads
+            lc = lam[c];
+            Sc = S[c];
+            acc = adj_col_sum<CH, false>(T.w + off + lane, T.row + off + lane, nullptr,
+                                         make_int4(-1, -1, -1, -1), lam, L);
         }
         S[c] = __dadd_rn(Sc, lc);
         lam_out[c] = __fma_rn(dt, acc, lc);
     }
+}
+
+template <int CH, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+adjoint_step(const Transpose T, const int64_t NI, const double dt,
+             const double* __restrict__ lam, double* __restrict__ lam_out,
+             double* __restrict__ S) {
+    if (T.row16) adj_slices<CH, true>(T, NI, dt, lam, lam_out, S);
+    else adj_slices<CH, false>(T, NI, dt, lam, lam_out, S);
 }
 
 // boundary columns: grad_g[node] = dt * sum_rows w_rc S_r + dLdu[node] (the
@@ -408,9 +562,12 @@ __global__ void ckpt_gather(const double* u, const int32_t* perm, int64_t N, dou
 // reverse-step shapes the tuner times: (phase width, register budget), each
 // with one warp per slice (the full grid) or a grid-stride loop over slices
 // on the resident blocks
-static const AdjStepFn adj_shapes[] = {adjoint_step<8, 4>, adjoint_step<12, 3>,
+// (with 16-bit row codes the window bases need registers: at four blocks
+// per SM phases of 8 spill and phases of 6 or 7 fit)
+static const AdjStepFn adj_shapes[] = {adjoint_step<8, 4>,  adjoint_step<7, 4>,
+                                       adjoint_step<6, 4>,  adjoint_step<12, 3>,
                                        adjoint_step<16, 2>, adjoint_step<8, 3>};
-static constexpr int N_ADJ_SHAPES = 4;
+static constexpr int N_ADJ_SHAPES = 6;
 
 static unsigned adj_grid(const rbffd_plan* p) {
     const int64_t nsl_int = (p->NI + SLICE - 1) / SLICE;
@@ -526,7 +683,39 @@ static int build_transpose(rbffd_plan* p, cudaStream_t s) {
         tr_fill<<<sms * 8, 256, 0, s>>>(start.as<int32_t>(), erow.as<int32_t>(), ew.as<double>(),
                                         t->colof, t->posof, N, t->nslices, t->off, t->len, t->row,
                                         t->w);
-        e = cudaGetLastError();
+        if ((e = cudaGetLastError())) break;
+        const int64_t nsl_int = (NI + SLICE - 1) / SLICE;
+        if ((e = cudaMemcpyAsync(&t->entries, t->off + nsl_int, sizeof(int64_t),
+                                 cudaMemcpyDeviceToHost, s)))
+            break;
+        if (p->col16 && nsl_int > 0) {   // the plan's index form: codes unless RBFFD_PACK_IDX32
+            Scratch cnt;
+            // columns and stored entries of the compact slices, then an error flag
+            if ((e = cnt.alloc(3 * sizeof(unsigned long long), s))) break;
+            if ((e = cudaMemsetAsync(cnt.p, 0, 3 * sizeof(unsigned long long), s))) break;
+            if ((e = cudaMalloc((void**)&t->row16, sizeof(uint16_t) * std::max<int64_t>(total, 1))))
+                break;
+            if ((e = cudaMalloc((void**)&t->tbase, sizeof(int4) * nsl_int))) break;
+            unsigned long long* dc = cnt.as<unsigned long long>();
+            tr_pack16<<<sms * 8, 256, 0, s>>>(start.as<int32_t>(), t->colof, NI, nsl_int, t->off,
+                                              t->len, t->row, t->row16, t->tbase, dc,
+                                              reinterpret_cast<int*>(dc + 2));
+            if ((e = cudaGetLastError())) break;
+            unsigned long long hc[2];
+            int herr = 0;
+            if ((e = cudaMemcpyAsync(hc, dc, sizeof(hc), cudaMemcpyDeviceToHost, s))) break;
+            if ((e = cudaMemcpyAsync(&herr, dc + 2, sizeof(int), cudaMemcpyDeviceToHost, s)))
+                break;
+            if ((e = cudaStreamSynchronize(s))) break;
+            if (herr) {
+                e = cudaErrorUnknown;
+                break;
+            }
+            t->cols16 = (int64_t)hc[0];
+            t->entries16 = (int64_t)hc[1];
+        } else {
+            e = cudaStreamSynchronize(s);
+        }
     } while (0);
     p->tr = t;
     if (e != cudaSuccess) {
@@ -545,6 +734,28 @@ extern "C" int rbffd_transpose(rbffd_plan* p, void* stream) {
     clear_error();
     RBFFD_ARG(p, "rbffd_transpose: NULL plan");
     return build_transpose(p, as_stream(stream));
+}
+
+extern "C" int rbffd_transpose_layout(const rbffd_plan* p, int64_t* h_slices, int64_t* h_cols16,
+                                      int64_t* h_entries, double* h_bytes) {
+    clear_error();
+    RBFFD_ARG(p, "rbffd_transpose_layout: NULL plan");
+    RBFFD_ARG(p->tr, "rbffd_transpose_layout: the transpose is not built (rbffd_transpose)");
+    const Transpose& T = *p->tr;
+    const int64_t nsl_int = (p->NI + SLICE - 1) / SLICE;
+    // with codes: entries of compact slices are 2 + 8 bytes, those of the
+    // other slices 2 + 4 + 8 (code, int32 row, weight); without: 4 + 8.  Per
+    // slice its offset and length (and window bases); per column lambda and
+    // S read, both written
+    const double e16 = (double)T.entries16, ew = (double)(T.entries - T.entries16);
+    const double bytes = (T.row16 ? 10.0 * e16 + 14.0 * ew + 28.0 * nsl_int
+                                  : 12.0 * (double)T.entries + 12.0 * nsl_int) +
+                         32.0 * (double)p->NI;
+    if (h_slices) *h_slices = nsl_int;
+    if (h_cols16) *h_cols16 = T.cols16;
+    if (h_entries) *h_entries = T.entries;
+    if (h_bytes) *h_bytes = bytes;
+    return RBFFD_OK;
 }
 
 extern "C" int rbffd_adjoint(rbffd_plan* p, const double* dLdu, int64_t K, double dt,

@@ -148,3 +148,67 @@ def test_codes_square_1M_mixed_slices(rb, orc):
     scale = np.abs(u0[ointer[rows]]) + dt * np.abs(ow * u0[oidx]).sum(axis=1)
     got = out[0][1][ointer[rows]]
     assert np.all(np.abs(got - ref) <= 1e-12 * scale)
+
+
+@pytest.mark.parametrize("Kg,m,order,name", CASES)
+def test_transpose_codes_match_int32_and_oracle(rb, orc, Kg, m, order, name):
+    """The reverse step reads the transpose's 16-bit row codes where a slice's rows
+    fit in four windows and int32 rows elsewhere: gradients bit-equal to the int32
+    transpose (RBFFD_PACK_IDX32) and within 1e-12 of the oracle's adjoint."""
+    p = build(orc, 2, Kg, m, seed=83)
+    dt = _dt(orc, p)
+    K = 60
+    dLdu = np.zeros(p.N)
+    sens = gen.sensors(p.NI, min(200, p.NI // 4), 3)
+    dLdu[p.interior[sens]] = gen.random_vector(len(sens), 4)
+    gf, gg, l0 = orc.adjoint(p.w, p.idx, p.interior, p.N, dLdu, K, dt)
+    out = {}
+    for pack in (0, rb.RBFFD_PACK_IDX32):
+        plan = _plan(rb, p, order | pack)
+        plan.transpose()
+        L = plan.transpose_layout()
+        assert L["slices"] == (p.NI + 31) // 32
+        assert L["entries"] >= p.NI * p.n       # every stored entry plus the padding
+        if pack:
+            assert L["cols16"] == 0
+        elif name == "random_int32_fallback":
+            assert L["cols16"] < 0.01 * p.NI
+        elif name == "one_window":
+            assert L["cols16"] == p.NI
+        else:
+            assert L["cols16"] > 0.5 * p.NI
+        e16 = L["entries"] if L["cols16"] == p.NI else None
+        if e16 is not None:
+            assert L["bytes"] == 10 * e16 + 28 * L["slices"] + 32 * p.NI
+        if pack:
+            assert L["bytes"] == 12 * L["entries"] + 12 * L["slices"] + 32 * p.NI
+        out[pack] = tuple(H(t) for t in plan.adjoint(T(dLdu), K, dt))
+        plan.destroy()
+    for a, b in zip(out[0], out[rb.RBFFD_PACK_IDX32]):
+        assert np.array_equal(a, b)
+    for a, b in zip(out[0], (gf, gg, l0)):
+        assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(b))
+
+
+def test_transpose_codes_square_1M(rb):
+    """The 1,002,001-node m=4 Morton plan's transpose: compact and int32 slices in
+    one reverse step; ten reverse steps bit-equal to the int32 transpose."""
+    d, Kg, m, seed = 2, 1000, 4, 2
+    n = gen.stencil_size(d, m)
+    xyz, bnd = rb.rbffd_nodes(d, 0, Kg, 0.3, seed)
+    inter = rb.rbffd_interior(bnd)
+    idx = rb.rbffd_knn(xyz, inter, n)
+    w, st = rb.rbffd_weights(xyz, idx, m)
+    NI, N = inter.numel(), xyz.shape[1]
+    dLdu = T(gen.random_vector(N, 6))
+    out = {}
+    for pack in (0, rb.RBFFD_PACK_IDX32):
+        plan = rb.Plan(xyz, bnd, inter, idx, w, rb.RBFFD_ORDER_MORTON | pack)
+        plan.transpose()
+        L = plan.transpose_layout()
+        if not pack:
+            assert 0.98 * NI < L["cols16"] <= NI
+        out[pack] = tuple(H(t) for t in plan.adjoint(dLdu, 10, 3.7e-8))
+        plan.destroy()
+    for a, b in zip(out[0], out[rb.RBFFD_PACK_IDX32]):
+        assert np.array_equal(a, b)

@@ -29,6 +29,12 @@
 namespace rbffd {
 
 static constexpr int W_SMAX = 128;
+// threads per block at most: one-warp teams up to sixteen per block (at
+// s = 45, thirteen fill the shared memory of an SM only as one block: a
+// second block would take its own reservation); the other team sizes keep
+// 256, which leaves their register budget as it was
+static constexpr int W_THREADS = 512;
+__host__ __device__ constexpr int weight_max_threads(int ts) { return ts == 32 ? 512 : 256; }
 
 struct WeightArgs {
     const double* xyz;
@@ -109,9 +115,24 @@ __device__ __forceinline__ double team_max_nonneg(double v, long long* red) {
 // argmax of |value| as IEEE bits (non-negative doubles order like integers;
 // NaN is mapped to -1 by the caller and never wins); ties -> lower index.
 // Integer compares keep the FP64 pipe for the elimination's multiply-adds.
+// A whole warp reduces with three warp-wide integer reductions instead of
+// five shuffle rounds: keys (>= -2, so key + 2 orders as unsigned) by their
+// high word, then the low word among the lanes holding the largest high word,
+// then the lowest index among the lanes holding the largest key.
 template <int TS>
 __device__ __forceinline__ void team_argmax(long long& bv, int& bi, long long* redv, int* redi) {
     const unsigned mask = team_mask<TS>();
+    if constexpr (TS == 32) {
+        const unsigned long long u = (unsigned long long)(bv + 2);
+        const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+        const unsigned mhi = __reduce_max_sync(0xffffffffu, hi);
+        const unsigned mlo = __reduce_max_sync(0xffffffffu, hi == mhi ? lo : 0u);
+        const unsigned mi =
+            __reduce_min_sync(0xffffffffu, (hi == mhi && lo == mlo) ? (unsigned)bi : 0xffffffffu);
+        bv = (long long)(((unsigned long long)mhi << 32) | mlo) - 2;
+        bi = (int)mi;
+        return;
+    }
 #pragma unroll
     for (int o = (TS < 32 ? TS : 32) / 2; o > 0; o >>= 1) {
         long long ov = __shfl_xor_sync(mask, bv, o);
@@ -145,10 +166,11 @@ __device__ __forceinline__ long long abs_key(double x) {
 }
 
 // shared memory of one team, in doubles: the augmented matrix, the scaled
-// support coordinates, and per pivot its reciprocal and the fixed-point
-// reciprocal of its significand
+// support coordinates (d per node), and per pivot the fixed-point reciprocal
+// of its significand.  At s = 45 (2D, m = 4) that is 17,760 bytes: thirteen
+// teams fill an SM's shared memory.
 __host__ __device__ __forceinline__ size_t weight_team_doubles(const WeightArgs& A) {
-    return (size_t)A.s * A.pitch + 3 * (size_t)A.n + 2 * (size_t)A.s;
+    return (size_t)A.s * A.pitch + (size_t)A.d * A.n + (size_t)A.s;
 }
 
 // the weights of stencil r of one call (all of the team's threads)
@@ -157,10 +179,9 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
                                             int tid, int team, double* redv, long long* redk,
                                             int* redi, double* bcast, int* spiv) {
     constexpr int T = TS;
-    double* rinv = xi + 3 * A.n;   // [s] reciprocal of each pivot
     // [s] the pivots' fixed-point significand reciprocals, for the back
     // substitution's quotients (if_div)
-    uint64_t* rinvY = reinterpret_cast<uint64_t*>(rinv + A.s);
+    uint64_t* rinvY = reinterpret_cast<uint64_t*>(xi + A.d * A.n);
     const int n = A.n, M = A.M, s = A.s, P = A.pitch, d = A.d;
     do {
         const int32_t* sup = A.idx + r * n;
@@ -191,12 +212,15 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
             int32_t id = sup[j];
             for (int a = 0; a < d; ++a) {
                 double t = __dsub_rn(A.xyz[(int64_t)a * A.N + id], A.xyz[(int64_t)a * A.N + c]);
-                xi[3 * j + a] = if_div(t, sig, Ysig);
+                xi[d * j + a] = if_div(t, sig, Ysig);
             }
         }
         team_sync<TS>();
         // assemble [[A P] [P^T 0]] | rhs; A from its strict upper triangle
-        // (pairs j < k enumerated row by row), diagonal 0
+        // (pairs j < k enumerated row by row), diagonal 0.  Each thread keeps
+        // the largest |entry| (IEEE bits; NaN ignored) it writes into the
+        // s x s block, for the relative pivot test.
+        long long gk = 0;
         {
             const int npairs = n * (n - 1) / 2;
             // pair number e -> (j, k): row j holds the n - 1 - j pairs (j, j+1..n-1)
@@ -210,7 +234,7 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
             for (; e < npairs; e += T) {
                 double r2 = 0.0;
                 for (int a = 0; a < d; ++a) {
-                    double t = __dsub_rn(xi[3 * j + a], xi[3 * k + a]);
+                    double t = __dsub_rn(xi[d * j + a], xi[d * k + a]);
                     double sq = __dmul_rn(t, t);
                     r2 = a == 0 ? sq : __dadd_rn(r2, sq);
                 }
@@ -218,6 +242,7 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
                 double v = __dmul_rn(__dmul_rn(rr, rr), rr);
                 G[j * P + k] = v;
                 G[k * P + j] = v;
+                gk = max(gk, abs_key(v));
                 // advance by T pairs (spilling into the following rows)
                 k += T;
                 while (j < n - 1 && k >= n) {
@@ -227,14 +252,20 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
             }
         }
         for (int j = tid; j < n; j += T) G[j * P + j] = 0.0;
-        for (int e = tid; e < n * M; e += T) {
-            int j = e / M, al = e - j * M;
-            // a factor x^0 = 1 multiplies exactly, so it is skipped
-            double p = powi(xi[3 * j + 0], A.ex[al][0]);
-            if (d >= 2 && A.ex[al][1]) p = __dmul_rn(p, powi(xi[3 * j + 1], A.ex[al][1]));
-            if (d >= 3 && A.ex[al][2]) p = __dmul_rn(p, powi(xi[3 * j + 2], A.ex[al][2]));
-            G[j * P + n + al] = p;
-            G[(n + al) * P + j] = p;
+        // monomials: one node per thread, the monomials in one loop for all
+        // threads (every lane takes the same powers at the same time)
+        for (int j = tid; j < n; j += T) {
+            const double x0 = xi[d * j];
+            const double x1 = d >= 2 ? xi[d * j + 1] : 0.0, x2 = d >= 3 ? xi[d * j + 2] : 0.0;
+            for (int al = 0; al < M; ++al) {
+                // a factor x^0 = 1 multiplies exactly, so it is skipped
+                double p = powi(x0, A.ex[al][0]);
+                if (d >= 2 && A.ex[al][1]) p = __dmul_rn(p, powi(x1, A.ex[al][1]));
+                if (d >= 3 && A.ex[al][2]) p = __dmul_rn(p, powi(x2, A.ex[al][2]));
+                G[j * P + n + al] = p;
+                G[(n + al) * P + j] = p;
+                gk = max(gk, abs_key(p));
+            }
         }
         for (int e = tid; e < M * M; e += T) {
             int a1 = e / M, a2 = e - a1 * M;
@@ -244,7 +275,7 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
         for (int j = tid; j < n; j += T) {
             double rc2 = 0.0;
             for (int a = 0; a < d; ++a) {
-                double sq = __dmul_rn(xi[3 * j + a], xi[3 * j + a]);
+                double sq = __dmul_rn(xi[d * j + a], xi[d * j + a]);
                 rc2 = a == 0 ? sq : __dadd_rn(rc2, sq);
             }
             if (A.op == 0) {
@@ -253,7 +284,7 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
                 // derivative of r^3 about x_j at x_c along dir: -3 |xi_j| (xi_j . dir)
                 double dot = 0.0;
                 for (int a = 0; a < d; ++a) {
-                    double t = __dmul_rn(xi[3 * j + a], dir[a]);
+                    double t = __dmul_rn(xi[d * j + a], dir[a]);
                     dot = a == 0 ? t : __dadd_rn(dot, t);
                 }
                 G[j * P + s] = -__dmul_rn(__dmul_rn(3.0, if_sqrt(rc2)), dot);
@@ -271,13 +302,8 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
             G[(n + al) * P + s] = v;
         }
         team_sync<TS>();
-        // scale of the assembled matrix for the relative pivot test (max |entry|
-        // over IEEE bits; NaN entries ignored)
-        long long gk = 0;
-        for (int e = tid; e < s * s; e += T) {
-            int i = e / s, j = e - i * s;
-            gk = max(gk, abs_key(G[i * P + j]));
-        }
+        // scale of the assembled matrix for the relative pivot test: the team's
+        // max of the threads' |entry| maxima (the zeros cannot exceed them)
         long long gkb = 0;
         {
             long long bk = gk;
@@ -313,13 +339,22 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
                     bad = 1;
                     break;
                 }
-                // reciprocal pivot by one warp of the team, broadcast after the swap
-                if ((tid >> 5) == 0) {
+                // reciprocal pivot: a team of at most one warp computes it in
+                // every lane, from the pivot read before the swap moves it; a
+                // larger team's first warp computes it and broadcasts it after
+                // the swap
+                double rp = 0.0;
+                if constexpr (T <= 32) {
+                    const double pv = G[bi * P + k];
+                    team_sync<TS>();
+                    uint64_t Y;
+                    rp = if_rcp(pv, &Y);
+                    if (tid == 0) rinvY[k] = Y;
+                } else if ((tid >> 5) == 0) {
                     uint64_t Y;
                     const double t = if_rcp(G[bi * P + k], &Y);
                     if (tid == 0) {
                         bcast[team] = t;
-                        rinv[k] = t;
                         rinvY[k] = Y;
                     }
                 }
@@ -330,7 +365,7 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
                         G[bi * P + j] = t;
                     }
                 team_sync<TS>();
-                const double rp = bcast[team];
+                if constexpr (T > 32) rp = bcast[team];
                 for (int i = k + 1 + tid; i < s; i += T) G[i * P + k] = __dmul_rn(G[i * P + k], rp);
                 team_sync<TS>();
                 // trailing update over (row, column) pairs: rows k+1..s-1,
@@ -398,7 +433,6 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
                 if (lane == 0) {
                     spiv[team] = bi | (nogo << 16);
                     bcast[team] = t;
-                    rinv[c] = t;
                     rinvY[c] = Y;
                 }
             };
@@ -476,12 +510,18 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
         if (!bad) {
             // back substitution by columns; x_j overwrites the rhs entry of row j
             for (int j = s - 1; j >= 0; --j) {
-                if ((tid >> 5) == 0) {   // one warp divides, the team reads the result
-                    const double t = if_div(G[j * P + s], G[j * P + j], rinvY[j]);
-                    if (tid == 0) bcast[team] = t;
+                double xj;
+                if constexpr (T <= 32) {   // every lane divides (row j is final: the
+                                           // previous column's update ended in a sync)
+                    xj = if_div(G[j * P + s], G[j * P + j], rinvY[j]);
+                } else {                   // one warp divides, the team reads the result
+                    if ((tid >> 5) == 0) {
+                        const double t = if_div(G[j * P + s], G[j * P + j], rinvY[j]);
+                        if (tid == 0) bcast[team] = t;
+                    }
+                    team_sync<TS>();
+                    xj = bcast[team];
                 }
-                team_sync<TS>();
-                const double xj = bcast[team];
                 if (bits_nonfinite(xj)) {
                     bad = 1;
                     break;
@@ -504,11 +544,12 @@ __device__ __forceinline__ void weights_one(const WeightArgs& A, int64_t r, doub
 }
 
 template <int TS, bool PW>
-__global__ void __launch_bounds__(256) weights_kernel(WeightArgs A, int teams_per_block) {
+__global__ void __launch_bounds__(weight_max_threads(TS))
+    weights_kernel(WeightArgs A, int teams_per_block) {
     extern __shared__ double wsm[];
-    __shared__ double redv[8];
-    __shared__ long long redk[8];
-    __shared__ int redi[8];
+    __shared__ double redv[W_THREADS / 32];
+    __shared__ long long redk[W_THREADS / 32];
+    __shared__ int redi[W_THREADS / 32];
     __shared__ double bcast[16];   // per-team scalar broadcast (reciprocal pivot, x_j)
     __shared__ int spiv[16];       // per-team pivot row (pivot-warp teams)
     const int tid = threadIdx.x % TS;
@@ -524,13 +565,13 @@ __global__ void __launch_bounds__(256) weights_kernel(WeightArgs A, int teams_pe
 // the call dI with off[dI] <= g < off[dI + 1]; a team's shared memory holds
 // the largest system of the launch (team_doubles)
 template <int TS, bool PW>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(weight_max_threads(TS))
     weights_multi_kernel(const WeightArgs* __restrict__ calls, const int64_t* __restrict__ off,
                          int ncalls, int teams_per_block, int64_t team_doubles) {
     extern __shared__ double wsm[];
-    __shared__ double redv[8];
-    __shared__ long long redk[8];
-    __shared__ int redi[8];
+    __shared__ double redv[W_THREADS / 32];
+    __shared__ long long redk[W_THREADS / 32];
+    __shared__ int redi[W_THREADS / 32];
     __shared__ double bcast[16];
     __shared__ int spiv[16];
     const int tid = threadIdx.x % TS;
@@ -616,7 +657,7 @@ template <class K>
 static cudaError_t pick_weight_shape(K kern, int ts, size_t per_team, WeightShape* out) {
     WeightShape b{};
     b.ts = ts;
-    const int max_tpb = std::min(256 / ts, 15);   // named barriers 1..15
+    const int max_tpb = std::min(weight_max_threads(ts) / ts, 15);   // named barriers 1..15
     const int step = ts == 16 ? 2 : 1;             // whole warps
     int best = -1;
     for (int tpb = step; tpb <= max_tpb; tpb += step) {

@@ -64,6 +64,15 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def _launch_label(per_sm: int) -> str:
+    """The launch mode a plan's stats report (blocks-per-SM entry of its shape)."""
+    if per_sm < 0:
+        return "resident"
+    if per_sm == 0:
+        return "persistent"
+    return "graph+pdl" if per_sm > 16 else "graph"
+
+
 def _traffic():
     """ncu DRAM bytes per launch of the FP64 sweep, if captured for the current kernel source."""
     import hashlib
@@ -328,7 +337,7 @@ def tta_case(rb, torch, Kg, dev, modes=("fp64", "fp32_dc", "fp64_persistent",
         if kind == "_auto":
             shape = plan.stats()[3]
             sh = shape[1 if prec.startswith("fp64") else 3]
-            row[prec]["launch"] = "resident" if sh < 0 else "persistent" if sh == 0 else "graph"
+            row[prec]["launch"] = _launch_label(sh)
     for kind, plan in plans.items():
         plan.destroy()
     for k64, k32 in (("fp64", "fp32_dc"), ("fp64_auto", "fp32_dc_auto")):
@@ -362,7 +371,7 @@ def c1_case(rb, torch, dev):
             "residual": res, "wall_s": el, "us_per_step_wall": el / max(steps, 1) * 1e6,
             "us_per_step_gpu": ms * 1e3 / max(k, 1),
             "node_updates_per_s": Q["NI"] * steps / el, "max_err": err, "mean_abs_err": mean,
-            "launch": "resident" if shape[1] < 0 else "persistent" if shape[1] == 0 else "graph"}
+            "launch": _launch_label(shape[1])}
 
 
 def support_sweep_case(rb, torch, dev, hbm, fma_peak, ns=(12, 13, 16, 20, 24, 30, 40, 48, 56)):

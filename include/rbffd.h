@@ -60,6 +60,11 @@ extern "C" {
 #define RBFFD_PACK_IDX32 32        /* keep int32 neighbour indices only (no 16-bit codes) */
 #define RBFFD_LAUNCH_AUTO 64       /* the autotuner picks graph or persistent per arithmetic */
 #define RBFFD_LAUNCH_RESIDENT 128  /* persistent, stencil planes resident in shared memory */
+/* graph-replayed steps: the autotuner times plain and programmatic dependent
+   launches (each step's blocks scheduled as the previous step drains) and
+   keeps the faster; these fix the choice */
+#define RBFFD_LAUNCH_PDL 256       /* graph steps as programmatic dependent launches */
+#define RBFFD_LAUNCH_NO_PDL 512    /* graph steps as plain launches */
 
 typedef struct rbffd_plan rbffd_plan;
 
@@ -381,8 +386,9 @@ RBFFD_API int rbffd_solve_explicit(rbffd_plan* plan, const double* f, double* u,
  * events recorded on the caller's stream around the step launches;
  * h_loop_steps, the steps those loops took; h_launches, the kernels the solve
  * launched; h_shape[4], the autotuned launch shape (register budget, blocks
- * per SM; 0 blocks per SM = the persistent launch, -1 = the resident launch)
- * of the FP64 sweep and of the FP32 inner sweep.
+ * per SM; 0 blocks per SM = the persistent launch, -1 = the resident launch;
+ * blocks per SM + 16 = graph-replayed steps launched as programmatic
+ * dependent launches) of the FP64 sweep and of the FP32 inner sweep.
  */
 RBFFD_API int rbffd_plan_stats(const rbffd_plan* plan, double* h_loop_ms, int64_t* h_loop_steps,
                                int64_t* h_launches, int* h_shape);

@@ -43,6 +43,8 @@ RBFFD_LAUNCH_GRAPH = 0
 RBFFD_LAUNCH_PERSISTENT = 16
 RBFFD_LAUNCH_AUTO = 64
 RBFFD_LAUNCH_RESIDENT = 128
+RBFFD_LAUNCH_PDL = 256
+RBFFD_LAUNCH_NO_PDL = 512
 RBFFD_PACK_IDX32 = 32
 
 EXPORTED = [

@@ -173,6 +173,7 @@ struct StepArgs {
     int spread;   // 1: consecutive slices go to different blocks (small plans)
     int64_t N;    // slots (the iterate's length)
     int64_t halo; // resident launch: slots staged beyond a block's rows on either side
+    int pdl;      // graph launch with programmatic serialization: prefetch before the wait
 };
 
 // The warp's first slice.  Large plans give each block runs of consecutive
@@ -332,8 +333,11 @@ __global__ void __launch_bounds__(STEP_THREADS, MINB) step_kernel(StepArgs A, St
     // now (they take SM slots as this step's blocks leave, so its launch
     // overlaps this step's tail); every block then waits here until the
     // previous step has completed and its writes are visible.  Both are no-ops
-    // for a launch without the programmatic-serialization attribute.
+    // for a launch without the programmatic-serialization attribute.  Before
+    // waiting, such a launch has one lane of each warp prefetch its first
+    // slice's planes into L2 (stencils only: nothing the previous step writes).
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    if (A.pdl && (threadIdx.x & 31) == 0) prefetch_planes<MODE>(A, step_warp(A));
     asm volatile("griddepcontrol.wait;" ::: "memory");
     if (threadIdx.x == 0) {
         volatile StepCtrl* vc = c;

@@ -447,10 +447,11 @@ __global__ void apply_rowmajor(const double* w, const int32_t* idx, int64_t nc, 
 
 // ------------------------------------------------------------ host side
 // One graph-mode step launch.  With programmatic stream serialization (pdl)
-// the next launch of a captured chunk can start while this one drains.
-// Measured: on plans of 10k-90k nodes the FP32 inner sweep gains 6-13 % per
-// step and the FP64 sweep up to 9 %; at 1M nodes the FP64 sweep loses 1 %, so
-// only plans below the use_pdl threshold use it.
+// the next launch of a captured chunk can start while this one drains.  The
+// autotuner times every graph shape with and without it (measured: on plans
+// of 10k-90k nodes the FP32 inner sweep gained 6-13 % per step and the FP64
+// sweep up to 9 %; at 1M nodes, without the prefetch before the wait, the
+// FP64 sweep lost 1 %).
 static cudaError_t launch_step(StepFn fn, int grid, cudaStream_t s, const StepArgs& A,
                                StepCtrl* ctrl, bool pdl) {
     cudaLaunchConfig_t cfg = {};
@@ -463,13 +464,9 @@ static cudaError_t launch_step(StepFn fn, int grid, cudaStream_t s, const StepAr
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, fn, A, ctrl);
-}
-
-// slices (of 32 rows) below which graph-mode steps use programmatic launches:
-// four slices per warp of one 256-thread block per SM
-static bool use_pdl(const rbffd_plan* p) {
-    return p->nslices < (int64_t)4 * (STEP_THREADS / 32) * device_sm_count();
+    StepArgs a = A;
+    a.pdl = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, fn, a, ctrl);
 }
 
 // fewer slices than one block of warps per SM: spread them over all SMs
@@ -496,6 +493,7 @@ static StepArgs make_args(const rbffd_plan* p) {
     A.spread = spread_slices(p) ? 1 : 0;
     A.N = p->N;
     A.halo = 0;
+    A.pdl = 0;
     return A;
 }
 
@@ -621,9 +619,10 @@ static StepFn resident_fn(rbffd_plan* p, int mode, unsigned* smem, int64_t* halo
 
 // Autotuner: time every launch shape of `mode` for a few steps on this plan's
 // own stencils (u / e buffers zeroed; dt = 0 so nothing moves) and keep the
-// fastest.  Candidates: register budget minb in {1, 2, 3} (and 4 for the FP32
-// sweep) x blocks per SM in {1, 2, 3, 4} (graph mode, timed as a captured
-// chunk of launches: what solves replay), and minb alone (persistent mode,
+// fastest.  Candidates: register budget minb in {1, 2, 3, 4} x blocks per SM
+// in {1, 2, 3, 4} x plain or programmatic dependent launches (graph mode,
+// timed as a captured chunk of launches: what solves replay), and minb alone
+// (persistent mode,
 // whose grid is the resident maximum); RBFFD_LAUNCH_AUTO times both modes and
 // keeps the faster.  The candidates are timed in interleaved rounds, one
 // untimed warm-up round first, each keeping its best round: timing them one
@@ -631,6 +630,7 @@ static StepFn resident_fn(rbffd_plan* p, int mode, unsigned* smem, int64_t* halo
 // once per plan and mode, on `s`.
 struct TuneCand {
     int minb, per_sm;
+    bool pdl;        // graph shapes: steps as programmatic dependent launches
     bool persistent;
     bool resident;   // the resident persistent launch (smem bytes and halo below)
     unsigned smem;
@@ -659,21 +659,25 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
     const bool only_res = (p->flags & RBFFD_LAUNCH_RESIDENT) != 0;
     const int c_lo = may_graph(p) ? 1 : 5, c_hi = may_persist(p) ? 5 : 4;
     std::vector<TuneCand> cands;
+    const int pdl_lo = (p->flags & RBFFD_LAUNCH_PDL) ? 1 : 0;
+    const int pdl_hi = (p->flags & RBFFD_LAUNCH_NO_PDL) ? 1 : 2;
     for (int minb = 1; minb <= n_minb && !only_res; ++minb)
-        for (int c = c_lo; c <= c_hi; ++c) {
-            TuneCand t;
-            t.minb = minb;
-            t.persistent = c == 5;
-            t.resident = false;
-            t.smem = 0;
-            t.halo = 0;
-            t.per_sm = t.persistent ? 1 : c;
-            t.fn = pick(mode, p->n, t.persistent, minb);
-            t.grid = t.persistent ? persistent_grid(t.fn, p) : grid_for(p, t.per_sm);
-            t.gx = nullptr;
-            t.ms = 1e30f;
-            cands.push_back(t);
-        }
+        for (int c = c_lo; c <= c_hi; ++c)
+            for (int pdl = c == 5 ? 0 : pdl_lo; pdl < (c == 5 ? 1 : pdl_hi); ++pdl) {
+                TuneCand t;
+                t.minb = minb;
+                t.pdl = pdl != 0;
+                t.persistent = c == 5;
+                t.resident = false;
+                t.smem = 0;
+                t.halo = 0;
+                t.per_sm = t.persistent ? 1 : c;
+                t.fn = pick(mode, p->n, t.persistent, minb);
+                t.grid = t.persistent ? persistent_grid(t.fn, p) : grid_for(p, t.per_sm);
+                t.gx = nullptr;
+                t.ms = 1e30f;
+                cands.push_back(t);
+            }
     // the resident persistent launch, when asked for (or left to the tuner)
     // and the plan's planes fit one block per SM; its halo reach is tuned: no
     // window, the block's own rows, 256, 1024, 4096 slots, the most that fits
@@ -683,6 +687,7 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
         t.fn = resident_fn(p, mode, &t.smem, &hmax);
         if (t.fn) {
             t.minb = 1;
+            t.pdl = false;
             t.per_sm = 1;
             t.persistent = true;
             t.resident = true;
@@ -719,7 +724,7 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
             if (ce == cudaSuccess) {
                 cudaError_t le = cudaSuccess;
                 for (long long i = 0; i < reps && le == cudaSuccess; ++i)
-                    le = launch_step(t.fn, t.grid, cs, A, p->ctrl, use_pdl(p));
+                    le = launch_step(t.fn, t.grid, cs, A, p->ctrl, t.pdl);
                 ce = cudaStreamEndCapture(cs, &gg);
                 if (ce == cudaSuccess && le != cudaSuccess) {
                     cudaGraphDestroy(gg);
@@ -780,6 +785,7 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
         if (t.ms < best->ms) best = &t;
     p->minb[mi] = best->minb;
     p->per_sm[mi] = best->per_sm;
+    p->pdl[mi] = best->pdl;
     p->persist[mi] = best->persistent;
     p->resident[mi] = best->resident;
     p->res_smem[mi] = best->smem;
@@ -814,7 +820,7 @@ static int ensure_graph(rbffd_plan* p, int mode, int b, cudaStream_t s) {
                 neumann_scatter<<<ng, 256, 0, cs>>>(p->nslot, p->uN, p->NN, p->u[0], p->u[1],
                                                     p->ctrl);
             }
-            if (le == cudaSuccess) le = launch_step(fn, grid, cs, A, p->ctrl, use_pdl(p));
+            if (le == cudaSuccess) le = launch_step(fn, grid, cs, A, p->ctrl, p->pdl[mi]);
         }
         e = cudaStreamEndCapture(cs, &g);
         // a launch refused during capture would leave a graph short of steps
@@ -1006,6 +1012,9 @@ extern "C" int rbffd_plan_create(const double* xyz, const uint8_t* is_bnd, int64
     RBFFD_ARG(n >= 1 && n <= 128, "rbffd_plan_create: n must be in [1, 128]");
     int order = flags & 15;
     RBFFD_ARG(order <= RBFFD_ORDER_RANDOM, "rbffd_plan_create: unknown order flag");
+    RBFFD_ARG((flags & (RBFFD_LAUNCH_PDL | RBFFD_LAUNCH_NO_PDL)) !=
+                  (RBFFD_LAUNCH_PDL | RBFFD_LAUNCH_NO_PDL),
+              "rbffd_plan_create: RBFFD_LAUNCH_PDL and RBFFD_LAUNCH_NO_PDL together");
     *out = nullptr;
     cudaStream_t s = as_stream(stream);
     rbffd_plan* p = new rbffd_plan();
@@ -1396,9 +1405,9 @@ extern "C" int rbffd_plan_stats(const rbffd_plan* p, double* h_loop_ms, int64_t*
     if (h_launches) *h_launches = p->last_launches;
     if (h_shape) {
         h_shape[0] = p->minb[0];
-        h_shape[1] = p->persist[0] ? (p->resident[0] ? -1 : 0) : p->per_sm[0];
+        h_shape[1] = p->persist[0] ? (p->resident[0] ? -1 : 0) : p->per_sm[0] + (p->pdl[0] ? 16 : 0);
         h_shape[2] = p->minb[1];
-        h_shape[3] = p->persist[1] ? (p->resident[1] ? -1 : 0) : p->per_sm[1];
+        h_shape[3] = p->persist[1] ? (p->resident[1] ? -1 : 0) : p->per_sm[1] + (p->pdl[1] ? 16 : 0);
     }
     return RBFFD_OK;
 }

@@ -137,6 +137,16 @@ def test_codes_square_1M_mixed_slices(rb, orc):
         out[pack] = (H(u), H(u1))
         plan.destroy()
     assert np.array_equal(out[0][0], out[rb.RBFFD_PACK_IDX32][0])
+    # graph steps as programmatic dependent launches (each warp prefetching its
+    # first slice before the wait), and as plain launches: the same bits
+    for launch in (rb.RBFFD_LAUNCH_PDL, rb.RBFFD_LAUNCH_NO_PDL):
+        plan = rb.Plan(xyz, bnd, inter, idx, w, rb.RBFFD_ORDER_MORTON | launch)
+        u = T(u0)
+        plan.solve_explicit(T(f), u, dt, 5, 0.0)
+        shape = plan.stats()[3]
+        assert (shape[1] > 16) == (launch == rb.RBFFD_LAUNCH_PDL)
+        assert np.array_equal(H(u), out[0][0])
+        plan.destroy()
     # one step on sampled rows against the oracle's own stencil sums
     oxyz, obnd = orc.nodes(d, 0, Kg, 0.3, seed)
     ointer = gen.interior_ids(obnd)

@@ -329,13 +329,14 @@ def test_sweep_zero_steps_and_errors(rb, orc):
 
 
 def test_launch_modes_same_bits(rb, orc):
-    """Graph, persistent, resident and autotuned launch modes: the same FP64 iterate
-    and the same defect-corrected iterate bit for bit; the reported shape says which
-    mode ran (0 blocks per SM = persistent, -1 = resident)."""
+    """Graph (tuned, with and without programmatic dependent launches), persistent,
+    resident and autotuned launch modes: the same FP64 iterate and the same
+    defect-corrected iterate bit for bit; the reported shape says which mode ran
+    (0 blocks per SM = persistent, -1 = resident, + 16 = programmatic launches)."""
     p = build(orc, 2, 30, 4, seed=47)
     dt = _dt(orc, p)
     outs = []
-    for flags in (0, 16, 64, 128):
+    for flags in (0, 16, 64, 128, 256, 512):
         plan = _plan(rb, p, flags)
         u = T(p.u0)
         plan.solve_explicit(T(p.f), u, dt, 500, 0.0)
@@ -348,6 +349,10 @@ def test_launch_modes_same_bits(rb, orc):
             assert shape[1] == 0 and shape[3] == 0
         if flags == 128:
             assert shape[1] == -1 and shape[3] == -1
+        if flags == 256:
+            assert shape[1] > 16 and shape[3] > 16
+        if flags == 512:
+            assert 0 < shape[1] <= 4 and 0 < shape[3] <= 4
         outs.append((H(u), H(u2)))
         plan.destroy()
     for a, b in outs[1:]:

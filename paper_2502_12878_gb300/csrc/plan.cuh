@@ -17,10 +17,9 @@ struct StepCtrl {
     unsigned long long res[3];   // per-step max |r| as IEEE bits (r >= 0 orders as uint64)
     unsigned int arrive[3];      // blocks finished with step k (ring by k % 3)
     unsigned int pad0[2];
-    // persistent mode: blocks arrived since the run started, and the word the
-    // last arrival of step k publishes: (k + 1) << 4 | decision
+    // persistent launches: block arrivals at step ends since the run started
     unsigned long long arrivals;
-    unsigned long long sync_word;
+    unsigned long long pad1;
     long long k;                 // steps taken so far
     long long max_steps;
     int done;                    // 0 running, 1 converged, 2 cap, 3 non-finite, 4 diverged, 5 timeout

@@ -303,12 +303,6 @@ __device__ __forceinline__ int decide(StepCtrl* c, long long k, double R) {
 // acquire every access that follows it.  The step ends use them instead of
 // full fences around relaxed atomics: measured 4-11 % less time per step on
 // 10k-90k-node plans (graph and persistent launches), 0.9 % at 1M nodes.
-__device__ __forceinline__ unsigned long long atom_add_acq_rel(unsigned long long* p,
-                                                               unsigned long long v) {
-    unsigned long long old;
-    asm volatile("atom.add.acq_rel.gpu.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
-    return old;
-}
 __device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
     unsigned old;
     asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
@@ -318,9 +312,6 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
     unsigned long long v;
     asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
-}
-__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
-    asm volatile("st.release.gpu.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 // graph mode: one step per launch, one slice per warp
@@ -371,64 +362,96 @@ __global__ void __launch_bounds__(STEP_THREADS, MINB) step_kernel(StepArgs A, St
     }
 }
 
-// End of step k in the persistent launch: a grid barrier fused with the
-// stop decision.  Each block adds its max |r| and arrives (arrivals are
-// counted from the start of the run, so nothing is reset); the last block to
-// arrive reads the step's max, applies the stop rule, clears the next-but-one
-// residual slot, and publishes ((k + 1) << 4) | decision in one word, which
-// the other blocks poll - so the decision needs no second round trip.  Waits
-// give up after `spin` clock cycles (decision DONE_TIMEOUT).  `held` arrivals
-// are added to each step's target: 0 in every solve, except a test of the
-// timeout path, where no step's barrier can then complete.  Returns the
-// decision in every thread.
-static __device__ int step_end(StepCtrl* c, long long k, long long k0, long long kmax,
-                               unsigned long long m, long long spin, int held) {
-    __shared__ int s_dec;
+// Step ends of the persistent launches: a counter barrier, with the stop
+// decision one step behind.  At the end of step k each block adds its max |r|
+// to the step's residual slot and its arrival to a counter (both fire-and-
+// forget reductions; the arrival releases the block's iterate writes and its
+// max), and waits until the counter shows every block's arrival (bounded by
+// `spin` clock cycles; `held` arrivals are added to every target - 0 in every
+// solve, except a test of the timeout path, where no barrier can complete).
+// Right after the barrier thread 0 starts loading the step's full residual and
+// the block computes step k + 1 meanwhile; at its end every block applies the
+// stop rule to step k - the same rule to the same value in every block, so all
+// stop together.  A stop wastes step k + 1, which writes the other buffer: the
+// result, u^{k+1}, is untouched.  The barrier's critical path is one
+// reduction and one poll, against the four round trips of a barrier whose last
+// arrival decides and publishes.  Block 0 clears the slot that step k + 2 will
+// use (every block read its previous contents before arriving here) and, when
+// the run stops, writes the outcome to the control block.
+__device__ __forceinline__ void red_max_relaxed(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.relaxed.gpu.global.max.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void red_add_release(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+struct LagState {
+    unsigned long long pend;   // thread 0: the last barrier's step residual (bits)
+    double R0;                 // thread 0: residual of step 0
+    double tol;
+    long long kmax;
+};
+
+// barrier at the end of step k (m: the block's max, valid in thread 0);
+// false in every thread when the wait gave up (done = DONE_TIMEOUT)
+__device__ __forceinline__ bool lag_barrier(StepCtrl* c, LagState& S, long long k, long long k0,
+                                            unsigned long long m, long long spin, int held) {
+    __shared__ int s_ok;
     if (threadIdx.x == 0) {
-        atomicMax(&c->res[k % 3], m);
+        red_max_relaxed(&c->res[k % 3], m);
+        red_add_release(&c->arrivals, 1ull);
         const unsigned long long target =
             (unsigned long long)(k - k0 + 1) * gridDim.x + (unsigned long long)held;
-        // the arrival releases this block's iterate writes and max, and (for
-        // the last block) acquires every other block's
-        const unsigned long long t = atom_add_acq_rel(&c->arrivals, 1ull) + 1ull;
-        int dn;
-        if (t == target) {
-            const double R = bitsd(atomicAdd(&c->res[k % 3], 0ull));
-            volatile StepCtrl* vc = c;
-            if (k == 0) vc->res_first = R;
-            const double R0 = k == 0 ? R : vc->res_first;
-            if (!isfinite(R)) dn = DONE_NONFINITE;
-            else if (R < vc->tol) dn = DONE_CONVERGED;
-            else if (k > 0 && R0 > 0.0 && R > 1e6 * R0) dn = DONE_DIVERGED;
-            else if (k + 1 >= kmax) dn = DONE_CAP;
-            else dn = DONE_RUNNING;
-            vc->res_last = R;
-            vc->k = k + 1;
-            vc->res[(k + 1) % 3] = 0ull;
-            if (dn != DONE_RUNNING) vc->done = dn;
-            const unsigned long long word =
-                ((unsigned long long)(k + 1) << 4) | (unsigned long long)dn;
-            // releases the decision and, transitively, every block's writes
-            st_release(&c->sync_word, word);
-        } else {
-            const long long t0 = clock64();
-            for (;;) {
-                const unsigned long long v = ld_acquire(&c->sync_word);
-                if ((v >> 4) == (unsigned long long)(k + 1)) {
-                    dn = (int)(v & 15ull);
-                    break;
-                }
-                if (clock64() - t0 > spin) {
-                    atomicExch(&c->done, DONE_TIMEOUT);
-                    dn = DONE_TIMEOUT;
-                    break;
-                }
+        const long long t0 = clock64();
+        int ok = 1;
+        while (ld_acquire(&c->arrivals) < target)
+            if (clock64() - t0 > spin) {
+                atomicExch(&c->done, DONE_TIMEOUT);
+                ok = 0;
+                break;
             }
+        if (ok) {
+            if (blockIdx.x == 0) st_relaxed(&c->res[(k + 2) % 3], 0ull);
+            S.pend = ld_relaxed(&c->res[k % 3]);
         }
-        s_dec = dn;
+        s_ok = ok;
     }
     __syncthreads();
-    return s_dec;
+    return s_ok != 0;
+}
+
+// the stop rule for step kk from its residual (loaded at its barrier), in
+// every thread; block 0 records the outcome of a run that stops
+__device__ __forceinline__ int lag_decide(StepCtrl* c, LagState& S, long long kk) {
+    __shared__ int s_dn;
+    if (threadIdx.x == 0) {
+        const double R = bitsd(S.pend);
+        if (kk == 0) S.R0 = R;
+        int dn;
+        if (!isfinite(R)) dn = DONE_NONFINITE;
+        else if (R < S.tol) dn = DONE_CONVERGED;
+        else if (kk > 0 && S.R0 > 0.0 && R > 1e6 * S.R0) dn = DONE_DIVERGED;
+        else if (kk + 1 >= S.kmax) dn = DONE_CAP;
+        else dn = DONE_RUNNING;
+        if (dn != DONE_RUNNING && blockIdx.x == 0) {
+            volatile StepCtrl* vc = c;
+            vc->res_first = S.R0;
+            vc->res_last = R;
+            vc->k = kk + 1;
+            vc->done = dn;
+        }
+        s_dn = dn;
+    }
+    __syncthreads();
+    return s_dn;
 }
 
 // persistent mode: all steps in one cooperative launch
@@ -437,6 +460,7 @@ __global__ void __launch_bounds__(STEP_THREADS, MINB) persistent_kernel(StepArgs
     __shared__ long long s_k, s_max, s_spin;
     __shared__ int s_held;
     __shared__ double s_dt;
+    LagState S;
     if (threadIdx.x == 0) {
         volatile StepCtrl* vc = c;
         s_k = vc->k;
@@ -446,6 +470,10 @@ __global__ void __launch_bounds__(STEP_THREADS, MINB) persistent_kernel(StepArgs
         const long long lim = vc->spin_limit;
         s_spin = lim > 0 ? lim : dflt;
         s_held = vc->held;
+        S.R0 = vc->res_first;
+        S.tol = vc->tol;
+        S.kmax = vc->max_steps;
+        S.pend = 0ull;
     }
     __syncthreads();
     const double dt = s_dt;
@@ -455,9 +483,12 @@ __global__ void __launch_bounds__(STEP_THREADS, MINB) persistent_kernel(StepArgs
     const int64_t nw = (int64_t)gridDim.x * (STEP_THREADS / 32);
     for (long long k = k0; k < kmax; ++k) {
         unsigned long long m = step_rows<NN, MODE, true>(A, (int)(k & 1), dt, (float)dt, warp, nw);
+        // the decision of step k - 1 (its residual loaded at its barrier)
+        if (k > k0 && lag_decide(c, S, k - 1) != DONE_RUNNING) return;
         m = block_max_bits(m);
-        if (step_end(c, k, k0, kmax, m, spin, held) != DONE_RUNNING) return;
+        if (!lag_barrier(c, S, k, k0, m, spin, held)) return;
     }
+    if (kmax > k0) lag_decide(c, S, kmax - 1);   // the last step's: it stops the run
 }
 
 // ------------------------------------------------------ dispatch by n

@@ -125,6 +125,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1) resident_kernel(StepArgs A, St
     __shared__ long long s_k, s_max, s_spin;
     __shared__ int s_held, s_fail;
     __shared__ double s_dt;
+    LagState S;
     int64_t s0, s1;
     res_range(A.nslices, &s0, &s1);
     const int64_t nsl = s1 - s0;
@@ -154,6 +155,10 @@ __global__ void __launch_bounds__(RES_THREADS, 1) resident_kernel(StepArgs A, St
         s_spin = lim > 0 ? lim : dflt;
         s_held = vc->held;
         s_fail = 0;
+        S.R0 = vc->res_first;
+        S.tol = vc->tol;
+        S.kmax = vc->max_steps;
+        S.pend = 0ull;
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -275,9 +280,12 @@ __global__ void __launch_bounds__(RES_THREADS, 1) resident_kernel(StepArgs A, St
                 m = max(m, abs_bits(rho));
             }
         }
+        // the decision of step k - 1 (its residual loaded at its barrier)
+        if (k > k0 && lag_decide(c, S, k - 1) != DONE_RUNNING) return;
         m = block_max_bits(m);
-        if (step_end(c, k, k0, kmax, m, spin, held) != DONE_RUNNING) return;
+        if (!lag_barrier(c, S, k, k0, m, spin, held)) return;
     }
+    if (kmax > k0) lag_decide(c, S, kmax - 1);   // the last step's: it stops the run
 }
 
 // the resident kernel for stencil size n (a specialisation for the sizes of

@@ -11,12 +11,13 @@ static constexpr int SLICE = 32;   // rows per slice = one warp
 static constexpr int GRAPH_LOG2 = 5;   // the longest captured graph: 32 step launches
 
 // Device control block of a step loop.  Step kernels read their parameters
-// here (so a captured graph can be replayed with new ones) and the last block
-// of a step publishes the decision.
+// here (so a captured graph can be replayed with new ones); the stop decision
+// of each step is taken one step later (graph launches: at the start of the
+// next step's kernels; persistent launches: after the next step's rows) and
+// a run that stops records its outcome here.
 struct StepCtrl {
     unsigned long long res[3];   // per-step max |r| as IEEE bits (r >= 0 orders as uint64)
-    unsigned int arrive[3];      // blocks finished with step k (ring by k % 3)
-    unsigned int pad0[2];
+    unsigned long long steps;    // graph launches: steps completed (block 0 of each adds 1)
     // persistent launches: block arrivals at step ends since the run started
     unsigned long long arrivals;
     unsigned long long pad1;

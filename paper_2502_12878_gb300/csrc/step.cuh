@@ -283,18 +283,49 @@ __device__ __forceinline__ unsigned long long block_max_bits(unsigned long long 
     return m;
 }
 
-// decision after step k with residual R (same rule in both launch modes);
-// returns the new `done` code
-__device__ __forceinline__ int decide(StepCtrl* c, long long k, double R) {
-    if (k == 0) c->res_first = R;
-    c->res_last = R;
-    c->k = k + 1;
+// the stop rule after step kk with residual R (R0: step 0's), the same in
+// every launch mode: non-finite, below tol, grown 1e6-fold, or the cap
+__device__ __forceinline__ int stop_rule(double R, double R0, long long kk, long long kmax,
+                                         double tol) {
     if (!isfinite(R)) return DONE_NONFINITE;
-    if (R < c->tol) return DONE_CONVERGED;
-    double R0 = (k == 0) ? R : c->res_first;
-    if (R > 1e6 * R0 && R0 > 0.0) return DONE_DIVERGED;
-    if (k + 1 >= c->max_steps) return DONE_CAP;
+    if (R < tol) return DONE_CONVERGED;
+    if (kk > 0 && R0 > 0.0 && R > 1e6 * R0) return DONE_DIVERGED;
+    if (kk + 1 >= kmax) return DONE_CAP;
     return DONE_RUNNING;
+}
+
+// Graph launches: the state at the start of a step's kernels, read by one
+// thread after the previous kernel completed.  k = steps completed; the stop
+// rule is applied here to step k - 1 (whose residual slot is complete at the
+// kernel boundary), so a step's kernel ends without a last-block ticket.
+// `record` (one block of the step kernel, and the finish kernel): on a stop
+// write the outcome, at step 0 its residual, and clear the slot step k + 1
+// will use (its last reader, step k's start, has completed).  Returns true
+// when the kernel should run step k.
+__device__ __forceinline__ bool graph_state(StepCtrl* c, bool record, long long* k_out) {
+    volatile StepCtrl* vc = c;
+    const long long k = (long long)vc->steps;
+    *k_out = k;
+    if (vc->done != DONE_RUNNING) return false;
+    const long long kmax = vc->max_steps;
+    if (k > 0) {
+        const long long kk = k - 1;
+        const double R = bitsd(vc->res[kk % 3]);
+        const double R0 = kk == 0 ? R : vc->res_first;
+        const int dn = stop_rule(R, R0, kk, kmax, vc->tol);
+        if (record && kk == 0) vc->res_first = R;
+        if (dn != DONE_RUNNING) {
+            if (record) {
+                vc->res_last = R;
+                vc->k = k;
+                vc->done = dn;
+            }
+            return false;
+        }
+    }
+    if (k >= kmax) return false;
+    if (record) vc->res[(k + 1) % 3] = 0ull;
+    return true;
 }
 
 // release / acquire accesses at GPU scope (PTX memory model): a release
@@ -314,6 +345,13 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
     return v;
 }
 
+__device__ __forceinline__ void red_max_relaxed(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.relaxed.gpu.global.max.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void red_add_relaxed(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 // graph mode: one step per launch, one slice per warp
 template <int NN, int MODE, int MINB>
 __global__ void __launch_bounds__(STEP_THREADS, MINB) step_kernel(StepArgs A, StepCtrl* c) {
@@ -331,11 +369,10 @@ __global__ void __launch_bounds__(STEP_THREADS, MINB) step_kernel(StepArgs A, St
     if (A.pdl && (threadIdx.x & 31) == 0) prefetch_planes<MODE>(A, step_warp(A));
     asm volatile("griddepcontrol.wait;" ::: "memory");
     if (threadIdx.x == 0) {
-        volatile StepCtrl* vc = c;
-        long long k = vc->k;
+        long long k;
+        s_skip = !graph_state(c, blockIdx.x == 0, &k);
         s_k = k;
-        s_skip = (vc->done != DONE_RUNNING) || (k >= vc->max_steps);
-        s_dt = vc->dt;
+        s_dt = ((volatile StepCtrl*)c)->dt;
     }
     __syncthreads();
     if (s_skip) return;
@@ -345,20 +382,11 @@ __global__ void __launch_bounds__(STEP_THREADS, MINB) step_kernel(StepArgs A, St
     unsigned long long m = step_rows<NN, MODE, false>(A, par, s_dt, (float)s_dt, warp,
                                                       (int64_t)gridDim.x * (STEP_THREADS / 32));
     m = block_max_bits(m);
+    // the block's max and (block 0) the step count: fire-and-forget; the
+    // next step's kernels see both through the kernel boundary
     if (threadIdx.x == 0) {
-        const int slot = (int)(k % 3);
-        atomicMax(&c->res[slot], m);
-        // the arrival releases this block's max and (for the last block)
-        // acquires every other block's; the decision's writes reach the next
-        // launch through the kernel boundary
-        unsigned t = atom_add_acq_rel(&c->arrive[slot], 1u);
-        if (t == gridDim.x - 1) {
-            double R = bitsd(atomicAdd(&c->res[slot], 0ull));
-            int dn = decide(c, k, R);
-            c->res[slot] = 0ull;
-            c->arrive[slot] = 0u;
-            c->done = dn;
-        }
+        red_max_relaxed(&c->res[k % 3], m);
+        if (blockIdx.x == 0) red_add_relaxed(&c->steps, 1ull);
     }
 }
 
@@ -378,9 +406,6 @@ __global__ void __launch_bounds__(STEP_THREADS, MINB) step_kernel(StepArgs A, St
 // arrival decides and publishes.  Block 0 clears the slot that step k + 2 will
 // use (every block read its previous contents before arriving here) and, when
 // the run stops, writes the outcome to the control block.
-__device__ __forceinline__ void red_max_relaxed(unsigned long long* p, unsigned long long v) {
-    asm volatile("red.relaxed.gpu.global.max.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
 __device__ __forceinline__ void red_add_release(unsigned long long* p, unsigned long long v) {
     asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
@@ -435,12 +460,7 @@ __device__ __forceinline__ int lag_decide(StepCtrl* c, LagState& S, long long kk
     if (threadIdx.x == 0) {
         const double R = bitsd(S.pend);
         if (kk == 0) S.R0 = R;
-        int dn;
-        if (!isfinite(R)) dn = DONE_NONFINITE;
-        else if (R < S.tol) dn = DONE_CONVERGED;
-        else if (kk > 0 && S.R0 > 0.0 && R > 1e6 * S.R0) dn = DONE_DIVERGED;
-        else if (kk + 1 >= S.kmax) dn = DONE_CAP;
-        else dn = DONE_RUNNING;
+        const int dn = stop_rule(R, S.R0, kk, S.kmax, S.tol);
         if (dn != DONE_RUNNING && blockIdx.x == 0) {
             volatile StepCtrl* vc = c;
             vc->res_first = S.R0;

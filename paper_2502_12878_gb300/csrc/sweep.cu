@@ -283,9 +283,9 @@ __global__ void neumann_update(const int32_t* __restrict__ ncol, const double* _
                                const double* u0, const double* u1, double* uN, StepCtrl* c) {
     __shared__ int s_skip, s_par;
     if (threadIdx.x == 0) {
-        volatile StepCtrl* vc = c;
-        s_skip = c ? ((vc->done != DONE_RUNNING) || (vc->k >= vc->max_steps)) : 0;
-        s_par = c ? (int)(vc->k & 1) : 0;
+        long long k = 0;
+        s_skip = c ? !graph_state(c, false, &k) : 0;
+        s_par = (int)(k & 1);
     }
     __syncthreads();
     if (s_skip) return;
@@ -299,11 +299,11 @@ __global__ void neumann_update(const int32_t* __restrict__ ncol, const double* _
 }
 
 __global__ void neumann_scatter(const int32_t* __restrict__ nslot, const double* __restrict__ uN,
-                                int64_t NN, double* u0, double* u1, const StepCtrl* c) {
+                                int64_t NN, double* u0, double* u1, StepCtrl* c) {
     __shared__ int s_skip;
     if (threadIdx.x == 0) {
-        const volatile StepCtrl* vc = c;
-        s_skip = c ? ((vc->done != DONE_RUNNING) || (vc->k >= vc->max_steps)) : 0;
+        long long k = 0;
+        s_skip = c ? !graph_state(c, false, &k) : 0;
     }
     __syncthreads();
     if (s_skip) return;
@@ -319,6 +319,13 @@ __global__ void neumann_out(const int32_t* nslot, const double* us, const int32_
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < NN;
          b += (int64_t)gridDim.x * blockDim.x)
         u[perm[nslot[b]]] = us[nslot[b]];
+}
+
+// graph launches: after the last replayed step, the stop rule for it (the
+// next step's kernels would apply it at their start); records the outcome
+__global__ void graph_finish(StepCtrl* c) {
+    long long k;
+    graph_state(c, true, &k);
 }
 
 // --------------------------------------------------------- DC kernels
@@ -929,7 +936,11 @@ static int run_steps(rbffd_plan* p, int mode, double dt, double tol, long long m
                 RBFFD_CHECK_CUDA(cudaStreamSynchronize(s));
                 if (h.done != DONE_RUNNING || g >= ngraphs) break;
             }
-            p->last_launches += launched;
+            // the last step's stop rule (a stop found earlier by a step's
+            // kernels only makes the rest of the replayed kernels skip)
+            graph_finish<<<1, 1, 0, s>>>(p->ctrl);
+            RBFFD_CHECK_CUDA(cudaGetLastError());
+            p->last_launches += launched + 1;
         }
     }
     RBFFD_CHECK_CUDA(cudaMemcpyAsync(&h, p->ctrl, sizeof(h), cudaMemcpyDeviceToHost, s));

@@ -84,6 +84,7 @@ struct rbffd_plan {
     bool resident[2] = {false, false};  // ... as the resident launch (planes in shared memory)
     bool pdl[2] = {false, false};       // graph-mode steps as programmatic dependent launches
     unsigned res_smem[2] = {0, 0};      // its dynamic shared memory per block
+    int res_threads[2] = {512, 512};    // and its block size
     int64_t res_halo[2] = {0, 0};       // and its halo reach (slots beyond a block's rows)
     int64_t res_halo_set = -2;          // a reach fixed by rbffd_plan_set_resident_halo (-2: tuned)
     int minb[2] = {2, 2};

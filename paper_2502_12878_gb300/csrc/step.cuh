@@ -551,11 +551,15 @@ StepFn pick_step_f32_b2(int n, bool persistent);
 StepFn pick_step_f32_b3(int n, bool persistent);
 StepFn pick_step_f32_b4(int n, bool persistent);
 
-// the resident persistent launch (step_res.cu): one block of RES_THREADS_HOST
+// the resident persistent launch (step_res.cuh): one block of RES_THREADS_HOST
 // threads per SM keeps its slices' planes in shared memory; i16: the index
-// planes are 16-bit codes (every slice of the plan has them)
+// planes are 16-bit codes (every slice of the plan has them).  The wide
+// variant has RES_THREADS_WIDE threads a block (nullptr for stencil sizes
+// without one, step_res_w.cu)
 static constexpr int RES_THREADS_HOST = 512;
+static constexpr int RES_THREADS_WIDE = 1024;
 StepFn pick_resident(int mode, int n, bool i16);
+StepFn pick_resident_wide(int mode, int n, bool i16);
 // dynamic shared memory of a resident launch of `grid` blocks whose halo
 // window reaches `halo` slots beyond each block's rows on either side
 unsigned resident_smem(int64_t nslices, int n, int mode, bool i16, int grid, int64_t halo);

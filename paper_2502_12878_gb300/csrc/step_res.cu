@@ -1,299 +1,16 @@
-// Resident persistent launch of the explicit sweep (Eq. 6): for plans whose
-// packed stencils fit in the shared memory of one block per SM, every block
-// keeps its slices' weight and index planes (and their rows' f or d32) in
-// shared memory for the whole run, and at the start of every step stages the
-// halo of its rows - a window of the iterate around its own slots, which in
-// Morton order holds nearly all of its rows' neighbours - into shared memory
-// too, so the gathers read shared memory and only the neighbours outside the
-// window go to L2.  Both are TMA bulk copies (cp.async.bulk, global ->
-// shared, completion on an mbarrier: the planes once per launch on its first
-// phase, the halo every step on the next); every wait is bounded.  The arithmetic is that of the other step kernels - the same fused
-// multiply-add chain per row in support order - so the results are the same
-// bit for bit.
-#include <type_traits>
-
-#include "step.cuh"
+// Resident persistent launch, 512-thread blocks: the kernel instantiations
+// for every compiled stencil size (the kernel itself is in step_res.cuh), and
+// the shared-memory size of a launch.
+#include "step_res.cuh"
 
 namespace rbffd {
-
-static constexpr int RES_THREADS = RES_THREADS_HOST;
-static constexpr unsigned RES_COPY_CHUNK = 32768;   // bytes per bulk copy
-
-// shared-memory layout of one block (byte offsets; every region 128-aligned):
-// the mbarrier, the weight and index planes, the rows' f (or d32), and the
-// halo window of the iterate
-struct ResLayout {
-    unsigned w, idx, f, h, total;
-};
-
-__host__ __device__ __forceinline__ unsigned res_align(unsigned x) { return (x + 127u) & ~127u; }
-
-// the layout for at most `nsl` slices of n entries: weights of `wbytes`,
-// indices of `ibytes` (2: 16-bit codes, 4: int32 slots); the halo window
-// holds the block's rows and `halo` slots on either side (halo < 0: no window)
-__host__ __device__ __forceinline__ unsigned res_window(int64_t nsl, int64_t halo) {
-    return halo < 0 ? 0u : (unsigned)(nsl * SLICE + 2 * halo + 8);
-}
-__host__ __device__ __forceinline__ ResLayout res_layout(int64_t nsl, int n, int wbytes,
-                                                         int ibytes, int64_t halo) {
-    ResLayout L;
-    const unsigned ent = (unsigned)(nsl * n * SLICE);
-    L.w = 128;   // the mbarrier lives at offset 0
-    L.idx = L.w + res_align(ent * (unsigned)wbytes);
-    L.f = L.idx + res_align(ent * (unsigned)ibytes);
-    L.h = L.f + res_align((unsigned)(nsl * SLICE) * (unsigned)wbytes);
-    L.total = L.h + res_align(res_window(nsl, halo) * (unsigned)wbytes);
-    return L;
-}
-
-// slices of block b of G: a contiguous range, sizes differing by at most one
-__device__ __forceinline__ void res_range(int64_t nslices, int64_t* s0, int64_t* s1) {
-    *s0 = nslices * blockIdx.x / gridDim.x;
-    *s1 = nslices * (blockIdx.x + 1) / gridDim.x;
-}
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// bounded wait on phase `parity` of the mbarrier; false if it gave up
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long long spin) {
-    const long long t0 = clock64();
-    for (;;) {
-        uint32_t done;
-        asm volatile(
-            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; "
-            "selp.u32 %0, 1, 0, p; }"
-            : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
-        if (done) return true;
-        if (clock64() - t0 > spin) return false;
-    }
-}
-
-// the iterate at slot c: from the block's halo window [lo, lo + W) in shared
-// memory, else through L2 (.cg: other blocks rewrite the iterate between steps)
-template <class T>
-__device__ __forceinline__ T res_u(const T* hs, int32_t lo, uint32_t W, const T* __restrict__ u,
-                                   int32_t c) {
-    const uint32_t o = (uint32_t)(c - lo);
-    return o < W ? hs[o] : ld_iter<true>(u + c);
-}
-
-// sum_j w_j u[col_j] with the planes in shared memory (entries at stride 32),
-// an fma chain from 0 in j order; the iterate from the halo window where it
-// covers the neighbour, CH gathers in flight at a time
-template <int NN, bool I16, class T>
-__device__ __forceinline__ T row_dot_res(const T* w, const void* colp, const int4& sb,
-                                         const T* hs, int32_t lo, uint32_t W,
-                                         const T* __restrict__ u, int n) {
-    constexpr int CH = 16;
-    T acc = T(0);
-    const int nn = NN > 0 ? NN : n;
-#pragma unroll
-    for (int j0 = 0; j0 < (NN > 0 ? NN : 1 << 30); j0 += CH) {
-        if (NN == 0 && j0 >= nn) break;
-        int32_t c[CH];
-        T uv[CH];
-#pragma unroll
-        for (int t = 0; t < CH; ++t)
-            if (j0 + t < nn) {
-                if constexpr (I16)
-                    c[t] = decode16((uint32_t)((const uint16_t*)colp)[(j0 + t) * SLICE], sb);
-                else
-                    c[t] = ((const int32_t*)colp)[(j0 + t) * SLICE];
-            }
-#pragma unroll
-        for (int t = 0; t < CH; ++t)
-            if (j0 + t < nn) uv[t] = res_u<T>(hs, lo, W, u, c[t]);
-#pragma unroll
-        for (int t = 0; t < CH; ++t)
-            if (j0 + t < nn) {
-                if constexpr (sizeof(T) == 8) acc = __fma_rn(w[(j0 + t) * SLICE], uv[t], acc);
-                else acc = __fmaf_rn(w[(j0 + t) * SLICE], uv[t], acc);
-            }
-    }
-    return acc;
-}
-
-// All steps of a run in one cooperative launch of one block per SM.  The
-// index planes are the 16-bit codes when every slice of the plan has them
-// (I16), else the int32 slots.
-template <int NN, int MODE, bool I16>
-__global__ void __launch_bounds__(RES_THREADS, 1) resident_kernel(StepArgs A, StepCtrl* c) {
-    typedef typename std::conditional<MODE == MODE_SWEEP64, double, float>::type T;
-    extern __shared__ __align__(128) unsigned char rsm[];
-    __shared__ long long s_k, s_max, s_spin;
-    __shared__ int s_held, s_fail;
-    __shared__ double s_dt;
-    LagState S;
-    int64_t s0, s1;
-    res_range(A.nslices, &s0, &s1);
-    const int64_t nsl = s1 - s0;
-    const int n = NN > 0 ? NN : A.n;
-    const ResLayout L = res_layout(nsl, n, (int)sizeof(T), I16 ? 2 : 4, A.halo);
-    T* w_s = reinterpret_cast<T*>(rsm + L.w);
-    unsigned char* idx_s = rsm + L.idx;
-    T* f_s = reinterpret_cast<T*>(rsm + L.f);
-    T* h_s = reinterpret_cast<T*>(rsm + L.h);
-    // the halo window: the block's rows and A.halo slots on either side, its
-    // start rounded down and its length down to 16-byte multiples (a TMA bulk
-    // copy's rule), within [0, N)
-    // (A.halo < 0: no window, every gather through L2)
-    const int64_t lo64 = max((int64_t)0, s0 * SLICE - A.halo) & ~(int64_t)3;
-    const int64_t hi64 = min(A.N, s1 * SLICE + A.halo);
-    const uint32_t W =
-        A.halo >= 0 && hi64 > lo64 ? (uint32_t)((hi64 - lo64) & ~(int64_t)3) : 0u;
-    const int32_t lo = (int32_t)lo64;
-    const uint32_t mbar = smem_addr(rsm);
-    if (threadIdx.x == 0) {
-        volatile StepCtrl* vc = c;
-        s_k = vc->k;
-        s_max = vc->max_steps;
-        s_dt = vc->dt;
-        constexpr long long dflt = SPIN_LIMIT_CYCLES;
-        const long long lim = vc->spin_limit;
-        s_spin = lim > 0 ? lim : dflt;
-        s_held = vc->held;
-        s_fail = 0;
-        S.R0 = vc->res_first;
-        S.tol = vc->tol;
-        S.kmax = vc->max_steps;
-        S.pend = 0ull;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    __syncthreads();
-    // stage the block's planes: one thread announces the bytes and issues the
-    // bulk copies in chunks; sources and destinations are 16-byte aligned and
-    // every size a multiple of 16 (planes of 32 rows of 2-, 4- or 8-byte entries)
-    const unsigned ent = (unsigned)(nsl * n * SLICE);
-    const unsigned wb = ent * (unsigned)sizeof(T), ib = ent * (I16 ? 2u : 4u);
-    const unsigned fb = (unsigned)(nsl * SLICE) * (unsigned)sizeof(T);
-    if (threadIdx.x == 0 && nsl > 0) {
-        const T* wg = (MODE == MODE_SWEEP64 ? (const T*)(const void*)A.w64
-                                            : (const T*)(const void*)A.w32) +
-                      s0 * (int64_t)n * SLICE;
-        const unsigned char* ig =
-            I16 ? (const unsigned char*)(A.col16 + s0 * (int64_t)n * SLICE)
-                : (const unsigned char*)(A.col + s0 * (int64_t)n * SLICE);
-        const T* fg = (MODE == MODE_SWEEP64 ? (const T*)(const void*)A.f
-                                            : (const T*)(const void*)A.d32) +
-                      s0 * SLICE;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar),
-                     "r"(wb + ib + fb) : "memory");
-        const void* src[3] = {wg, ig, fg};
-        const uint32_t dst[3] = {smem_addr(w_s), smem_addr(idx_s), smem_addr(f_s)};
-        const unsigned bytes[3] = {wb, ib, fb};
-        for (int q = 0; q < 3; ++q)
-            for (unsigned o = 0; o < bytes[q]; o += RES_COPY_CHUNK) {
-                const unsigned sz = min(RES_COPY_CHUNK, bytes[q] - o);
-                asm volatile(
-                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
-                    "[%0], [%1], %2, [%3];" ::"r"(dst[q] + o),
-                    "l"((const unsigned char*)src[q] + o), "r"(sz), "r"(mbar)
-                    : "memory");
-            }
-    } else if (threadIdx.x == 0) {
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
-    }
-    // the rows' f (or the inner sweep's d32) beyond NI in the last slice are
-    // padding of the plan's arrays; the planes stay valid for every row < NI
-    if (!mbar_wait(mbar, 0, s_spin)) s_fail = 1;
-    __syncthreads();
-    if (s_fail) {
-        // give the copies a second bounded wait before the block leaves
-        if (threadIdx.x == 0) {
-            atomicExch(&c->done, DONE_TIMEOUT);
-            mbar_wait(mbar, 0, s_spin);
-        }
-        __syncthreads();
-        return;
-    }
-    const double dt = s_dt;
-    const float dt32 = (float)dt;
-    const long long kmax = s_max, k0 = s_k, spin = s_spin;
-    const int held = s_held;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int NW = RES_THREADS / 32;
-    for (long long k = k0; k < kmax; ++k) {
-        const int par = (int)(k & 1);
-        // stage this step's halo window of the iterate (one bulk copy on the
-        // mbarrier's next phase).  The other blocks' writes of the previous
-        // step were acquired at the step's barrier; the proxy fence orders
-        // them before the copy, which reads through the async proxy.
-        const T* ucur = MODE == MODE_SWEEP64 ? (const T*)(const void*)(par ? A.u1 : A.u0)
-                                             : (const T*)(const void*)(par ? A.e1 : A.e0);
-        if (A.halo >= 0 && threadIdx.x == 0) {
-            asm volatile("fence.proxy.async.global;" ::: "memory");
-            if (W > 0) {
-                const unsigned hb = W * (unsigned)sizeof(T);
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar),
-                             "r"(hb) : "memory");
-                for (unsigned o = 0; o < hb; o += RES_COPY_CHUNK)
-                    asm volatile(
-                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
-                        "[%0], [%1], %2, [%3];" ::"r"(smem_addr(h_s) + o),
-                        "l"((const unsigned char*)(ucur + lo) + o),
-                        "r"(min(RES_COPY_CHUNK, hb - o)), "r"(mbar)
-                        : "memory");
-            } else {
-                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
-            }
-        }
-        const uint32_t phase = (uint32_t)((k - k0 + 1) & 1);
-        if (A.halo >= 0 && !mbar_wait(mbar, phase, spin)) s_fail = 1;
-        __syncthreads();
-        if (s_fail) {
-            if (threadIdx.x == 0) {
-                atomicExch(&c->done, DONE_TIMEOUT);
-                mbar_wait(mbar, phase, spin);
-            }
-            __syncthreads();
-            return;
-        }
-        unsigned long long m = 0;
-        for (int64_t ls = warp; ls < nsl; ls += NW) {
-            const int64_t sl = s0 + ls;
-            const int64_t row = sl * SLICE + lane;
-            if (row >= A.NI) continue;
-            const int64_t eo = ls * (int64_t)n * SLICE + lane;
-            const int4 sb = I16 ? __ldg(A.sbase + sl) : make_int4(0, 0, 0, 0);
-            const void* cp = I16 ? (const void*)((const uint16_t*)idx_s + eo)
-                                 : (const void*)((const int32_t*)idx_s + eo);
-            if constexpr (MODE == MODE_SWEEP64) {
-                const double* uin = par ? A.u1 : A.u0;
-                double* uout = par ? A.u0 : A.u1;
-                const double ui = res_u<double>((const double*)h_s, lo, W, uin, (int32_t)row);
-                const double acc = row_dot_res<NN, I16, double>(w_s + eo, cp, sb,
-                                                                (const double*)h_s, lo, W, uin, n);
-                const double r = __dsub_rn(acc, f_s[ls * SLICE + lane]);
-                uout[row] = __fma_rn(dt, r, ui);
-                m = max(m, abs_bits(r));
-            } else {
-                const float* ein = par ? A.e1 : A.e0;
-                float* eout = par ? A.e0 : A.e1;
-                const float ei = res_u<float>((const float*)h_s, lo, W, ein, (int32_t)row);
-                const float acc = row_dot_res<NN, I16, float>(w_s + eo, cp, sb,
-                                                              (const float*)h_s, lo, W, ein, n);
-                const float rho = __fadd_rn(acc, f_s[ls * SLICE + lane]);
-                eout[row] = __fmaf_rn(dt32, rho, ei);
-                m = max(m, abs_bits(rho));
-            }
-        }
-        // the decision of step k - 1 (its residual loaded at its barrier)
-        if (k > k0 && lag_decide(c, S, k - 1) != DONE_RUNNING) return;
-        m = block_max_bits(m);
-        if (!lag_barrier(c, S, k, k0, m, spin, held)) return;
-    }
-    if (kmax > k0) lag_decide(c, S, kmax - 1);   // the last step's: it stops the run
-}
 
 // the resident kernel for stencil size n (a specialisation for the sizes of
 // the monomial orders in 2D and 3D, else the generic one)
 template <int MODE, bool I16>
 static StepFn pick_res_m(int n) {
 #define RBFFD_RCASE(NN) \
-    case NN: return resident_kernel<NN, MODE, I16>;
+    case NN: return resident_kernel<NN, MODE, I16, RES_THREADS_HOST>;
     switch (n) {
         RBFFD_RCASE(6)
         RBFFD_RCASE(12)
@@ -309,7 +26,7 @@ static StepFn pick_res_m(int n) {
         RBFFD_RCASE(57)
         RBFFD_RCASE(70)
         RBFFD_RCASE(71)
-        default: return resident_kernel<0, MODE, I16>;
+        default: return resident_kernel<0, MODE, I16, RES_THREADS_HOST>;
     }
 #undef RBFFD_RCASE
 }

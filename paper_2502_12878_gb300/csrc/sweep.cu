@@ -590,7 +590,7 @@ static bool res_i16(const rbffd_plan* p) { return p->col16 && p->rows16 == p->NI
 // `*halo` slots beyond the block's rows on either side: at most as far as the
 // shared memory left beside the planes allows (returned in *halo; the tuner
 // tries shorter reaches, and none), up to the whole iterate.
-static StepFn resident_fn(rbffd_plan* p, int mode, unsigned* smem, int64_t* halo) {
+static StepFn resident_fn(rbffd_plan* p, int mode, int threads, unsigned* smem, int64_t* halo) {
     const int grid = device_sm_count();
     const bool i16 = res_i16(p);
     int dev = 0, optin = 0, per_sm = 0;
@@ -610,10 +610,12 @@ static StepFn resident_fn(rbffd_plan* p, int mode, unsigned* smem, int64_t* halo
     h = std::min<int64_t>(h, p->N);
     const unsigned bytes = resident_smem(p->nslices, p->n, mode, i16, grid, h);
     if (bytes > room) return nullptr;
-    StepFn fn = pick_resident(mode, p->n, i16);
+    StepFn fn = threads == RES_THREADS_WIDE ? pick_resident_wide(mode, p->n, i16)
+                                            : pick_resident(mode, p->n, i16);
+    if (!fn) return nullptr;
     if (cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)bytes) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)fn, RES_THREADS_HOST,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)fn, threads,
                                                       bytes) != cudaSuccess ||
         per_sm < 1) {
         cudaGetLastError();
@@ -639,7 +641,8 @@ struct TuneCand {
     int minb, per_sm;
     bool pdl;        // graph shapes: steps as programmatic dependent launches
     bool persistent;
-    bool resident;   // the resident persistent launch (smem bytes and halo below)
+    bool resident;   // the resident persistent launch (smem bytes, halo, threads below)
+    int threads;
     unsigned smem;
     int64_t halo;
     StepFn fn;
@@ -676,6 +679,7 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
                 t.pdl = pdl != 0;
                 t.persistent = c == 5;
                 t.resident = false;
+                t.threads = STEP_THREADS;
                 t.smem = 0;
                 t.halo = 0;
                 t.per_sm = t.persistent ? 1 : c;
@@ -687,12 +691,18 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
             }
     // the resident persistent launch, when asked for (or left to the tuner)
     // and the plan's planes fit one block per SM; its halo reach is tuned: no
-    // window, the block's own rows, 256, 1024, 4096 slots, the most that fits
-    if (may_persist(p) && (p->flags & (RBFFD_LAUNCH_AUTO | RBFFD_LAUNCH_RESIDENT))) {
+    // window, the block's own rows, 256, 1024, 4096 slots, the most that fits;
+    // and its block size: 512 threads, and 1024 where the stencil size has it
+    bool res_any = false;
+    for (int wide = 0; wide < 2 && may_persist(p) &&
+                       (p->flags & (RBFFD_LAUNCH_AUTO | RBFFD_LAUNCH_RESIDENT));
+         ++wide) {
         TuneCand t;
         int64_t hmax = 0;
-        t.fn = resident_fn(p, mode, &t.smem, &hmax);
+        t.threads = wide ? RES_THREADS_WIDE : RES_THREADS_HOST;
+        t.fn = resident_fn(p, mode, t.threads, &t.smem, &hmax);
         if (t.fn) {
+            res_any = true;
             t.minb = 1;
             t.pdl = false;
             t.per_sm = 1;
@@ -713,11 +723,12 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
                                                       t.grid, t.halo));
                 cands.push_back(t);
             }
-        } else if (only_res) {
-            set_error("resident launch: the plan's stencils do not fit in shared memory "
-                      "(%lld slices of %d entries)", (long long)p->nslices, p->n);
-            return RBFFD_ERR_CAPACITY;
         }
+    }
+    if (only_res && !res_any) {
+        set_error("resident launch: the plan's stencils do not fit in shared memory "
+                  "(%lld slices of %d entries)", (long long)p->nslices, p->n);
+        return RBFFD_ERR_CAPACITY;
     }
     int st = RBFFD_OK;
     // capture one chunk of `reps` launches per graph candidate
@@ -764,7 +775,7 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
                 A.halo = t.halo;
                 void* args[] = {(void*)&A, (void*)&c};
                 cudaLaunchCooperativeKernel((const void*)t.fn, dim3(t.grid),
-                                            dim3(t.resident ? RES_THREADS_HOST : STEP_THREADS),
+                                            dim3(t.resident ? t.threads : STEP_THREADS),
                                             args, t.smem, s);
             } else {
                 cudaGraphLaunch(t.gx, s);
@@ -796,6 +807,7 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
     p->persist[mi] = best->persistent;
     p->resident[mi] = best->resident;
     p->res_smem[mi] = best->smem;
+    p->res_threads[mi] = best->resident ? best->threads : RES_THREADS_HOST;
     p->res_halo[mi] = best->halo;
     p->tune_ms[mi] = best->ms / (float)reps;
     p->tuned[mi] = true;
@@ -893,7 +905,9 @@ static int run_steps(rbffd_plan* p, int mode, double dt, double tol, long long m
         if (st) return st;
         if (p->persist[mi]) {
             const bool res = p->resident[mi];
-            StepFn fn = res ? pick_resident(mode, p->n, res_i16(p))
+            StepFn fn = res ? (p->res_threads[mi] == RES_THREADS_WIDE
+                                   ? pick_resident_wide(mode, p->n, res_i16(p))
+                                   : pick_resident(mode, p->n, res_i16(p)))
                             : pick(mode, p->n, true, p->minb[mi]);
             int grid = res ? device_sm_count() : persistent_grid(fn, p);
             StepArgs A = make_args(p);
@@ -902,7 +916,7 @@ static int run_steps(rbffd_plan* p, int mode, double dt, double tol, long long m
             void* args[] = {(void*)&A, (void*)&c};
             RBFFD_CHECK_CUDA(cudaEventRecord((cudaEvent_t)p->ev[0], s));
             RBFFD_CHECK_CUDA(cudaLaunchCooperativeKernel(
-                (const void*)fn, dim3(grid), dim3(res ? RES_THREADS_HOST : STEP_THREADS), args,
+                (const void*)fn, dim3(grid), dim3(res ? p->res_threads[mi] : STEP_THREADS), args,
                 res ? p->res_smem[mi] : 0, s));
             RBFFD_CHECK_CUDA(cudaEventRecord((cudaEvent_t)p->ev[1], s));
             p->last_launches += 1;
@@ -1415,9 +1429,9 @@ extern "C" int rbffd_plan_stats(const rbffd_plan* p, double* h_loop_ms, int64_t*
     if (h_loop_steps) *h_loop_steps = p->last_loop_steps;
     if (h_launches) *h_launches = p->last_launches;
     if (h_shape) {
-        h_shape[0] = p->minb[0];
+        h_shape[0] = p->resident[0] ? p->res_threads[0] / 512 : p->minb[0];
         h_shape[1] = p->persist[0] ? (p->resident[0] ? -1 : 0) : p->per_sm[0] + (p->pdl[0] ? 16 : 0);
-        h_shape[2] = p->minb[1];
+        h_shape[2] = p->resident[1] ? p->res_threads[1] / 512 : p->minb[1];
         h_shape[3] = p->persist[1] ? (p->resident[1] ? -1 : 0) : p->per_sm[1] + (p->pdl[1] ? 16 : 0);
     }
     return RBFFD_OK;

@@ -15,15 +15,19 @@
 // support order as the definition.  Weights and indices are streamed with
 // evict-first loads; the iterate (8 bytes per node) stays in L2.
 //
-// Step loop.  One step = one pass over all rows.  Two launch modes:
+// Step loop.  One step = one pass over all rows.  Launch modes:
 //  graph       one launch per step, a chunk of launches captured once into a
-//              CUDA graph and replayed; the last block of a step (atomic
-//              ticket) reads the step's residual max and publishes the stop
-//              decision to a device control block that later launches read.
-//  persistent  one cooperative launch runs the steps, separated by a grid
-//              barrier whose waits are bounded in time (RBFFD_ERR_TIMEOUT).
-// The residual max-norm is reduced warp -> block -> atomicMax on its IEEE
-// bits (non-negative doubles order like unsigned integers).
+//              CUDA graph and replayed; the next step's kernels apply the
+//              stop rule to the completed step (its residual slot in a device
+//              control block) at their start, one small kernel after the
+//              replays to the last step.
+//  persistent  one cooperative launch runs the steps, separated by a counter
+//              barrier whose waits are bounded in time (RBFFD_ERR_TIMEOUT);
+//              the stop rule for a step is applied after the next one.
+//  resident    the persistent launch with each block's stencil planes held
+//              in shared memory (step_res.cuh).
+// The residual max-norm is reduced warp -> block -> a max reduction on its
+// IEEE bits (non-negative doubles order like unsigned integers).
 #include <math.h>
 
 #include <algorithm>

@@ -65,6 +65,9 @@ extern "C" {
    keeps the faster; these fix the choice */
 #define RBFFD_LAUNCH_PDL 256       /* graph steps as programmatic dependent launches */
 #define RBFFD_LAUNCH_NO_PDL 512    /* graph steps as plain launches */
+#define RBFFD_LAUNCH_FAR 2048      /* resident, with far lists: each block also stages the
+                                      values outside its window that its rows read, so
+                                      every gather reads shared memory */
 
 typedef struct rbffd_plan rbffd_plan;
 
@@ -387,7 +390,8 @@ RBFFD_API int rbffd_solve_explicit(rbffd_plan* plan, const double* f, double* u,
  * h_loop_steps, the steps those loops took; h_launches, the kernels the solve
  * launched; h_shape[4], the autotuned launch shape (register budget, blocks
  * per SM; 0 blocks per SM = the persistent launch, -1 = the resident launch,
- * whose first entry is then its block size in units of 512 threads;
+ * whose first entry is then its block size in units of 512 threads, + 4
+ * when it stages far lists (every gather from shared memory);
  * blocks per SM + 16 = graph-replayed steps launched as programmatic
  * dependent launches) of the FP64 sweep and of the FP32 inner sweep.
  */

@@ -85,6 +85,17 @@ struct rbffd_plan {
     bool pdl[2] = {false, false};       // graph-mode steps as programmatic dependent launches
     unsigned res_smem[2] = {0, 0};      // its dynamic shared memory per block
     int res_threads[2] = {512, 512};    // and its block size
+    bool res_far[2] = {false, false};   // ... with far lists (every gather in shared memory)
+    // far-list data per mode (built when the tuner first considers it): the
+    // window reach it was built for, the most far slots of a block, the
+    // entries' local indices, each block's far slots
+    bool fl_built[2] = {false, false};
+    bool fl_ok[2] = {false, false};
+    int64_t fl_halo[2] = {0, 0};
+    int64_t fl_max[2] = {0, 0};
+    uint16_t* fl_idx[2] = {nullptr, nullptr};
+    int32_t* fl_off[2] = {nullptr, nullptr};
+    int32_t* fl_slot[2] = {nullptr, nullptr};
     int64_t res_halo[2] = {0, 0};       // and its halo reach (slots beyond a block's rows)
     int64_t res_halo_set = -2;          // a reach fixed by rbffd_plan_set_resident_halo (-2: tuned)
     int minb[2] = {2, 2};

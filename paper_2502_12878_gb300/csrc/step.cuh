@@ -174,6 +174,13 @@ struct StepArgs {
     int64_t N;    // slots (the iterate's length)
     int64_t halo; // resident launch: slots staged beyond a block's rows on either side
     int pdl;      // graph launch with programmatic serialization: prefetch before the wait
+    // resident launch with far lists: per block the sorted slots its rows
+    // read outside its window (staged every step behind the window), and for
+    // every stencil entry its position in the window + far values
+    const uint16_t* fl_idx;   // [nslices][n][32]
+    const int32_t* fl_off;    // [blocks + 1]
+    const int32_t* fl_slot;
+    int64_t fl_max;           // most far slots of a block
 };
 
 // The warp's first slice.  Large plans give each block runs of consecutive
@@ -560,8 +567,13 @@ static constexpr int RES_THREADS_HOST = 512;
 static constexpr int RES_THREADS_WIDE = 1024;
 StepFn pick_resident(int mode, int n, bool i16);
 StepFn pick_resident_wide(int mode, int n, bool i16);
+// the resident launch with far lists (step_res_far.cu), `threads` a block
+// (nullptr where that block size is not compiled for n)
+StepFn pick_resident_far(int mode, int n, int threads);
 // dynamic shared memory of a resident launch of `grid` blocks whose halo
-// window reaches `halo` slots beyond each block's rows on either side
-unsigned resident_smem(int64_t nslices, int n, int mode, bool i16, int grid, int64_t halo);
+// window reaches `halo` slots beyond each block's rows on either side, with
+// room for `extra` more values behind it (the far values)
+unsigned resident_smem(int64_t nslices, int n, int mode, bool i16, int grid, int64_t halo,
+                       int64_t extra = 0);
 
 }  // namespace rbffd

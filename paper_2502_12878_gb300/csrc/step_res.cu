@@ -40,9 +40,10 @@ StepFn pick_resident(int mode, int n, bool i16) {
 // dynamic shared memory of a resident launch of `grid` blocks (the largest
 // block's share of the slices, its halo window reaching `halo` slots beyond
 // its rows; halo < 0: the planes alone)
-unsigned resident_smem(int64_t nslices, int n, int mode, bool i16, int grid, int64_t halo) {
+unsigned resident_smem(int64_t nslices, int n, int mode, bool i16, int grid, int64_t halo,
+                       int64_t extra) {
     const int64_t nsl = (nslices + grid - 1) / grid;
-    return res_layout(nsl, n, mode == MODE_SWEEP64 ? 8 : 4, i16 ? 2 : 4, halo).total;
+    return res_layout(nsl, n, mode == MODE_SWEEP64 ? 8 : 4, i16 ? 2 : 4, halo, extra).total;
 }
 
 }  // namespace rbffd

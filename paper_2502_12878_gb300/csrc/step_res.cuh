@@ -35,14 +35,15 @@ __host__ __device__ __forceinline__ unsigned res_window(int64_t nsl, int64_t hal
     return halo < 0 ? 0u : (unsigned)(nsl * SLICE + 2 * halo + 8);
 }
 __host__ __device__ __forceinline__ ResLayout res_layout(int64_t nsl, int n, int wbytes,
-                                                         int ibytes, int64_t halo) {
+                                                         int ibytes, int64_t halo,
+                                                         int64_t extra = 0) {
     ResLayout L;
     const unsigned ent = (unsigned)(nsl * n * SLICE);
     L.w = 128;   // the mbarrier lives at offset 0
     L.idx = L.w + res_align(ent * (unsigned)wbytes);
     L.f = L.idx + res_align(ent * (unsigned)ibytes);
     L.h = L.f + res_align((unsigned)(nsl * SLICE) * (unsigned)wbytes);
-    L.total = L.h + res_align(res_window(nsl, halo) * (unsigned)wbytes);
+    L.total = L.h + res_align((res_window(nsl, halo) + (unsigned)extra) * (unsigned)wbytes);
     return L;
 }
 
@@ -115,12 +116,40 @@ __device__ __forceinline__ T row_dot_res(const T* w, const void* colp, const int
     return acc;
 }
 
+// FAR: sum_j w_j v_j with every v_j in shared memory at the entry's local
+// index (window position, or the window's length plus its far position)
+template <int NN, class T>
+__device__ __forceinline__ T row_dot_far(const T* w, const uint16_t* li, const T* hs, int n) {
+    constexpr int CH = 16;
+    T acc = T(0);
+    const int nn = NN > 0 ? NN : n;
+#pragma unroll
+    for (int j0 = 0; j0 < (NN > 0 ? NN : 1 << 30); j0 += CH) {
+        if (NN == 0 && j0 >= nn) break;
+        T uv[CH];
+#pragma unroll
+        for (int t = 0; t < CH; ++t)
+            if (j0 + t < nn) uv[t] = hs[li[(j0 + t) * SLICE]];
+#pragma unroll
+        for (int t = 0; t < CH; ++t)
+            if (j0 + t < nn) {
+                if constexpr (sizeof(T) == 8) acc = __fma_rn(w[(j0 + t) * SLICE], uv[t], acc);
+                else acc = __fmaf_rn(w[(j0 + t) * SLICE], uv[t], acc);
+            }
+    }
+    return acc;
+}
+
 // All steps of a run in one cooperative launch of one block per SM.  The
 // index planes are the 16-bit codes when every slice of the plan has them
 // (I16), else the int32 slots.
 // TH: threads per block (one block per SM): 512, or 1024 where the kernel
-// fits 64 registers - one round of slices per step for more blocks' shares
-template <int NN, int MODE, bool I16, int TH>
+// fits 64 registers - one round of slices per step for more blocks' shares.
+// FAR: the index planes are the entries' local indices (A.fl_idx) and every
+// step the block's far values (the slots outside its window that its rows
+// read: A.fl_slot) are loaded behind the window while its bulk copy runs, so
+// every gather reads shared memory (no L2 round trip in the rows' chains).
+template <int NN, int MODE, bool I16, int TH, bool FAR = false>
 __global__ void __launch_bounds__(TH, 1) resident_kernel(StepArgs A, StepCtrl* c) {
     typedef typename std::conditional<MODE == MODE_SWEEP64, double, float>::type T;
     extern __shared__ __align__(128) unsigned char rsm[];
@@ -132,7 +161,11 @@ __global__ void __launch_bounds__(TH, 1) resident_kernel(StepArgs A, StepCtrl* c
     res_range(A.nslices, &s0, &s1);
     const int64_t nsl = s1 - s0;
     const int n = NN > 0 ? NN : A.n;
-    const ResLayout L = res_layout(nsl, n, (int)sizeof(T), I16 ? 2 : 4, A.halo);
+    constexpr bool IDX2 = I16 || FAR;   // 2-byte index planes
+    const ResLayout L = res_layout(nsl, n, (int)sizeof(T), IDX2 ? 2 : 4, A.halo,
+                                   FAR ? A.fl_max : 0);
+    const int32_t f0 = FAR ? A.fl_off[blockIdx.x] : 0;
+    const int32_t nfar = FAR ? A.fl_off[blockIdx.x + 1] - f0 : 0;
     T* w_s = reinterpret_cast<T*>(rsm + L.w);
     unsigned char* idx_s = rsm + L.idx;
     T* f_s = reinterpret_cast<T*>(rsm + L.f);
@@ -169,15 +202,16 @@ __global__ void __launch_bounds__(TH, 1) resident_kernel(StepArgs A, StepCtrl* c
     // bulk copies in chunks; sources and destinations are 16-byte aligned and
     // every size a multiple of 16 (planes of 32 rows of 2-, 4- or 8-byte entries)
     const unsigned ent = (unsigned)(nsl * n * SLICE);
-    const unsigned wb = ent * (unsigned)sizeof(T), ib = ent * (I16 ? 2u : 4u);
+    const unsigned wb = ent * (unsigned)sizeof(T), ib = ent * (IDX2 ? 2u : 4u);
     const unsigned fb = (unsigned)(nsl * SLICE) * (unsigned)sizeof(T);
     if (threadIdx.x == 0 && nsl > 0) {
         const T* wg = (MODE == MODE_SWEEP64 ? (const T*)(const void*)A.w64
                                             : (const T*)(const void*)A.w32) +
                       s0 * (int64_t)n * SLICE;
         const unsigned char* ig =
-            I16 ? (const unsigned char*)(A.col16 + s0 * (int64_t)n * SLICE)
-                : (const unsigned char*)(A.col + s0 * (int64_t)n * SLICE);
+            FAR   ? (const unsigned char*)(A.fl_idx + s0 * (int64_t)n * SLICE)
+            : I16 ? (const unsigned char*)(A.col16 + s0 * (int64_t)n * SLICE)
+                  : (const unsigned char*)(A.col + s0 * (int64_t)n * SLICE);
         const T* fg = (MODE == MODE_SWEEP64 ? (const T*)(const void*)A.f
                                             : (const T*)(const void*)A.d32) +
                       s0 * SLICE;
@@ -242,6 +276,12 @@ __global__ void __launch_bounds__(TH, 1) resident_kernel(StepArgs A, StepCtrl* c
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
             }
         }
+        // far values: plain loads through L2 (acquired at the barrier like the
+        // window's source), stored behind the window - other addresses than
+        // the bulk copy's, ordered for the readers by the barrier below
+        if constexpr (FAR)
+            for (int32_t i = threadIdx.x; i < nfar; i += TH)
+                h_s[W + i] = ld_iter<true>(ucur + __ldg(A.fl_slot + f0 + i));
         const uint32_t phase = (uint32_t)((k - k0 + 1) & 1);
         if (A.halo >= 0 && !mbar_wait(mbar, phase, spin)) s_fail = 1;
         __syncthreads();
@@ -259,24 +299,33 @@ __global__ void __launch_bounds__(TH, 1) resident_kernel(StepArgs A, StepCtrl* c
             const int64_t row = sl * SLICE + lane;
             if (row >= A.NI) continue;
             const int64_t eo = ls * (int64_t)n * SLICE + lane;
-            const int4 sb = I16 ? __ldg(A.sbase + sl) : make_int4(0, 0, 0, 0);
-            const void* cp = I16 ? (const void*)((const uint16_t*)idx_s + eo)
-                                 : (const void*)((const int32_t*)idx_s + eo);
+            const int4 sb = (I16 && !FAR) ? __ldg(A.sbase + sl) : make_int4(0, 0, 0, 0);
+            const void* cp = IDX2 ? (const void*)((const uint16_t*)idx_s + eo)
+                                  : (const void*)((const int32_t*)idx_s + eo);
             if constexpr (MODE == MODE_SWEEP64) {
                 const double* uin = par ? A.u1 : A.u0;
                 double* uout = par ? A.u0 : A.u1;
-                const double ui = res_u<double>((const double*)h_s, lo, W, uin, (int32_t)row);
-                const double acc = row_dot_res<NN, I16, double>(w_s + eo, cp, sb,
-                                                                (const double*)h_s, lo, W, uin, n);
+                const double ui = FAR ? ((const double*)h_s)[row - lo]
+                                      : res_u<double>((const double*)h_s, lo, W, uin,
+                                                      (int32_t)row);
+                const double acc =
+                    FAR ? row_dot_far<NN, double>(w_s + eo, (const uint16_t*)cp,
+                                                  (const double*)h_s, n)
+                        : row_dot_res<NN, I16, double>(w_s + eo, cp, sb, (const double*)h_s, lo,
+                                                       W, uin, n);
                 const double r = __dsub_rn(acc, f_s[ls * SLICE + lane]);
                 uout[row] = __fma_rn(dt, r, ui);
                 m = max(m, abs_bits(r));
             } else {
                 const float* ein = par ? A.e1 : A.e0;
                 float* eout = par ? A.e0 : A.e1;
-                const float ei = res_u<float>((const float*)h_s, lo, W, ein, (int32_t)row);
-                const float acc = row_dot_res<NN, I16, float>(w_s + eo, cp, sb,
-                                                              (const float*)h_s, lo, W, ein, n);
+                const float ei = FAR ? ((const float*)h_s)[row - lo]
+                                     : res_u<float>((const float*)h_s, lo, W, ein, (int32_t)row);
+                const float acc =
+                    FAR ? row_dot_far<NN, float>(w_s + eo, (const uint16_t*)cp,
+                                                 (const float*)h_s, n)
+                        : row_dot_res<NN, I16, float>(w_s + eo, cp, sb, (const float*)h_s, lo, W,
+                                                      ein, n);
                 const float rho = __fadd_rn(acc, f_s[ls * SLICE + lane]);
                 eout[row] = __fmaf_rn(dt32, rho, ei);
                 m = max(m, abs_bits(rho));

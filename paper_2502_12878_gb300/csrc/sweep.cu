@@ -505,7 +505,19 @@ static StepArgs make_args(const rbffd_plan* p) {
     A.N = p->N;
     A.halo = 0;
     A.pdl = 0;
+    A.fl_idx = nullptr;
+    A.fl_off = nullptr;
+    A.fl_slot = nullptr;
+    A.fl_max = 0;
     return A;
+}
+
+// the far-list fields of the resident launch of mode mi
+static void far_args(const rbffd_plan* p, int mi, StepArgs* A) {
+    A->fl_idx = p->fl_idx[mi];
+    A->fl_off = p->fl_off[mi];
+    A->fl_slot = p->fl_slot[mi];
+    A->fl_max = p->fl_max[mi];
 }
 
 static void drop_graphs(rbffd_plan* p) {
@@ -521,7 +533,9 @@ static void free_plan(rbffd_plan* p) {
     if (!p) return;
     void* bufs[] = {p->perm, p->inv, p->row_of_slot, p->w64, p->w32, p->col, p->u[0], p->u[1],
                     p->fs, p->e[0], p->e[1], p->d32, p->scratch, p->ctrl, p->nslot, p->ncol,
-                    p->nw, p->ng, p->ng0, p->uN, p->col16, p->sbase};
+                    p->nw, p->ng, p->ng0, p->uN, p->col16, p->sbase,
+                    p->fl_idx[0], p->fl_idx[1], p->fl_off[0], p->fl_off[1],
+                    p->fl_slot[0], p->fl_slot[1]};
     for (void* b : bufs)
         if (b) cudaFree(b);
     drop_graphs(p);
@@ -577,12 +591,13 @@ static int ctrl_reset(rbffd_plan* p, double dt, double tol, long long max_steps,
 // launch modes the autotuner may choose from: persistent only when asked for
 // (or left to it) and the plan has no Neumann phase, which only graphs replay
 static bool may_persist(const rbffd_plan* p) {
-    return (p->flags & (RBFFD_LAUNCH_PERSISTENT | RBFFD_LAUNCH_AUTO | RBFFD_LAUNCH_RESIDENT)) !=
-               0 &&
+    return (p->flags & (RBFFD_LAUNCH_PERSISTENT | RBFFD_LAUNCH_AUTO | RBFFD_LAUNCH_RESIDENT |
+                        RBFFD_LAUNCH_FAR)) != 0 &&
            p->NN == 0;
 }
 static bool may_graph(const rbffd_plan* p) {
-    return !(p->flags & (RBFFD_LAUNCH_PERSISTENT | RBFFD_LAUNCH_RESIDENT)) || p->NN > 0;
+    return !(p->flags & (RBFFD_LAUNCH_PERSISTENT | RBFFD_LAUNCH_RESIDENT | RBFFD_LAUNCH_FAR)) ||
+           p->NN > 0;
 }
 
 // The resident persistent launch (step_res.cu): one block per SM keeping its
@@ -630,6 +645,116 @@ static StepFn resident_fn(rbffd_plan* p, int mode, int threads, unsigned* smem, 
     return fn;
 }
 
+// Far lists of the resident launch (mode mi, grid = SMs; block b owns slices
+// [nslices b / G, nslices (b+1) / G)): with the window reach h, block b stages
+// slots [lo, lo + W) (lo = (b's first slot - h) rounded down to 4, W its span
+// to b's last slot + h, rounded down to 4, both within [0, N)) - the kernel's
+// own formula - and every other slot its rows read is a far slot, kept in a
+// sorted per-block list and staged behind the window each step.  Each stencil
+// entry gets its local index: c - lo in the window, W + its position in the
+// list otherwise.  h starts at the largest window that fits beside the planes
+// and shrinks until the window and the largest far list fit; the build fails
+// (fl_ok false) when own rows fall outside the window or indices exceed 16 bits.
+static int build_far(rbffd_plan* p, int mode, cudaStream_t s) {
+    const int mi = mode == MODE_SWEEP64 ? 0 : 1;
+    if (p->fl_built[mi]) return RBFFD_OK;
+    p->fl_built[mi] = true;
+    p->fl_ok[mi] = false;
+    const int G = device_sm_count();
+    const int64_t NI = p->NI, N = p->N, nsl = p->nslices;
+    const int n = p->n;
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return RBFFD_OK;
+    }
+    const int64_t room = (int64_t)optin - 1024;
+    const int64_t elem = mode == MODE_SWEEP64 ? 8 : 4;
+    const int64_t planes = resident_smem(nsl, n, mode, true, G, -1);
+    const int64_t rows = (nsl + G - 1) / G * SLICE;
+    if (planes + (rows + 8) * elem > room || NI > 4000000) return RBFFD_OK;
+    const int64_t ent = nsl * n * SLICE;
+    std::vector<int32_t> col(ent);
+    RBFFD_CHECK_CUDA(cudaMemcpyAsync(col.data(), p->col, sizeof(int32_t) * ent,
+                                     cudaMemcpyDeviceToHost, s));
+    RBFFD_CHECK_CUDA(cudaStreamSynchronize(s));
+    std::vector<uint16_t> lidx(ent, 0);
+    std::vector<int32_t> off(G + 1, 0);
+    std::vector<int32_t> slots;
+    int64_t h = std::max<int64_t>(0, (room - planes) / elem - 8 - rows) / 2;
+    for (int attempt = 0; attempt < 12; ++attempt) {
+        slots.clear();
+        int64_t fmax = 0;
+        bool bad = false;
+        for (int b = 0; b < G && !bad; ++b) {
+            const int64_t s0 = nsl * b / G, s1 = nsl * (b + 1) / G;
+            const int64_t lo = std::max<int64_t>(0, s0 * SLICE - h) & ~(int64_t)3;
+            const int64_t hi = std::min<int64_t>(N, s1 * SLICE + h);
+            const int64_t W = hi > lo ? (hi - lo) & ~(int64_t)3 : 0;
+            const int64_t r1 = std::min<int64_t>(s1 * SLICE, NI);
+            if (r1 > s0 * SLICE && r1 - lo > W) {
+                bad = true;
+                break;
+            }
+            std::vector<int32_t> far;
+            for (int64_t sl = s0; sl < s1; ++sl)
+                for (int j = 0; j < n; ++j)
+                    for (int l = 0; l < SLICE; ++l) {
+                        if (sl * SLICE + l >= NI) continue;
+                        const int32_t c = col[(sl * n + j) * SLICE + l];
+                        if (c < lo || c >= lo + W) far.push_back(c);
+                    }
+            std::sort(far.begin(), far.end());
+            far.erase(std::unique(far.begin(), far.end()), far.end());
+            if (W + (int64_t)far.size() > 65535) {
+                bad = true;
+                break;
+            }
+            fmax = std::max<int64_t>(fmax, (int64_t)far.size());
+            for (int64_t sl = s0; sl < s1; ++sl)
+                for (int j = 0; j < n; ++j)
+                    for (int l = 0; l < SLICE; ++l) {
+                        const int64_t e = (sl * n + j) * SLICE + l;
+                        if (sl * SLICE + l >= NI) continue;
+                        const int32_t c = col[e];
+                        lidx[e] = (uint16_t)(c >= lo && c < lo + W
+                                                 ? c - lo
+                                                 : W + (std::lower_bound(far.begin(), far.end(),
+                                                                         c) -
+                                                        far.begin()));
+                    }
+            off[b] = (int32_t)slots.size();
+            slots.insert(slots.end(), far.begin(), far.end());
+        }
+        off[G] = (int32_t)slots.size();
+        if (bad) return RBFFD_OK;
+        const int64_t need = resident_smem(nsl, n, mode, true, G, h, fmax);
+        if (need <= room) {
+            cudaError_t e = cudaSuccess;
+            auto up = [&](void** dst, const void* src, size_t bytes) {
+                if (e == cudaSuccess) e = cudaMalloc(dst, bytes);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, s);
+            };
+            if (slots.empty()) slots.push_back(0);
+            up((void**)&p->fl_idx[mi], lidx.data(), sizeof(uint16_t) * lidx.size());
+            up((void**)&p->fl_off[mi], off.data(), sizeof(int32_t) * off.size());
+            up((void**)&p->fl_slot[mi], slots.data(), sizeof(int32_t) * slots.size());
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            RBFFD_CHECK_CUDA(e);
+            p->fl_halo[mi] = h;
+            p->fl_max[mi] = fmax;
+            p->fl_ok[mi] = true;
+            return RBFFD_OK;
+        }
+        if (h == 0) return RBFFD_OK;
+        h = std::max<int64_t>(0, h - ((need - room) / elem + 127) / 2 - 64);
+    }
+    return RBFFD_OK;
+}
+
 // Autotuner: time every launch shape of `mode` for a few steps on this plan's
 // own stencils (u / e buffers zeroed; dt = 0 so nothing moves) and keep the
 // fastest.  Candidates: register budget minb in {1, 2, 3, 4} x blocks per SM
@@ -646,6 +771,7 @@ struct TuneCand {
     bool pdl;        // graph shapes: steps as programmatic dependent launches
     bool persistent;
     bool resident;   // the resident persistent launch (smem bytes, halo, threads below)
+    bool far;        // ... with far lists
     int threads;
     unsigned smem;
     int64_t halo;
@@ -670,7 +796,8 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
         std::max<long long>(10, std::min<long long>(600, 400000000 / (p->NI * p->n + 1)));
     const int n_minb = N_MINB;
     // candidate c: graph shapes per_sm = c (1..4), then the persistent launch (c = 5)
-    const bool only_res = (p->flags & RBFFD_LAUNCH_RESIDENT) != 0;
+    const bool only_far = (p->flags & RBFFD_LAUNCH_FAR) != 0;
+    const bool only_res = (p->flags & RBFFD_LAUNCH_RESIDENT) != 0 || only_far;
     const int c_lo = may_graph(p) ? 1 : 5, c_hi = may_persist(p) ? 5 : 4;
     std::vector<TuneCand> cands;
     const int pdl_lo = (p->flags & RBFFD_LAUNCH_PDL) ? 1 : 0;
@@ -683,6 +810,7 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
                 t.pdl = pdl != 0;
                 t.persistent = c == 5;
                 t.resident = false;
+                t.far = false;
                 t.threads = STEP_THREADS;
                 t.smem = 0;
                 t.halo = 0;
@@ -698,12 +826,13 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
     // window, the block's own rows, 256, 1024, 4096 slots, the most that fits;
     // and its block size: 512 threads, and 1024 where the stencil size has it
     bool res_any = false;
-    for (int wide = 0; wide < 2 && may_persist(p) &&
+    for (int wide = 0; wide < 2 && may_persist(p) && !only_far &&
                        (p->flags & (RBFFD_LAUNCH_AUTO | RBFFD_LAUNCH_RESIDENT));
          ++wide) {
         TuneCand t;
         int64_t hmax = 0;
         t.threads = wide ? RES_THREADS_WIDE : RES_THREADS_HOST;
+        t.far = false;
         t.fn = resident_fn(p, mode, t.threads, &t.smem, &hmax);
         if (t.fn) {
             res_any = true;
@@ -727,6 +856,45 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
                                                       t.grid, t.halo));
                 cands.push_back(t);
             }
+        }
+    }
+    // the resident launch with far lists (its reach fixed by the build; not
+    // when rbffd_plan_set_resident_halo fixed one)
+    if (may_persist(p) &&
+        (p->flags & (RBFFD_LAUNCH_AUTO | RBFFD_LAUNCH_RESIDENT | RBFFD_LAUNCH_FAR)) &&
+        p->res_halo_set < -1) {
+        int st0 = build_far(p, mode, s);
+        if (st0) return st0;
+        for (int wide = 0; wide < 2 && p->fl_ok[mi]; ++wide) {
+            TuneCand t;
+            t.threads = wide ? RES_THREADS_WIDE : RES_THREADS_HOST;
+            t.fn = pick_resident_far(mode, p->n, t.threads);
+            if (!t.fn) continue;
+            t.smem = resident_smem(p->nslices, p->n, mode, true, device_sm_count(),
+                                   p->fl_halo[mi], p->fl_max[mi]);
+            int per_sm = 0;
+            if (cudaFuncSetAttribute((const void*)t.fn,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)t.smem) != cudaSuccess ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)t.fn,
+                                                              t.threads, t.smem) !=
+                    cudaSuccess ||
+                per_sm < 1) {
+                cudaGetLastError();
+                continue;
+            }
+            t.minb = 1;
+            t.pdl = false;
+            t.per_sm = 1;
+            t.persistent = true;
+            t.resident = true;
+            t.far = true;
+            t.halo = p->fl_halo[mi];
+            t.grid = device_sm_count();
+            t.gx = nullptr;
+            t.ms = 1e30f;
+            res_any = true;
+            cands.push_back(t);
         }
     }
     if (only_res && !res_any) {
@@ -777,6 +945,7 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
             if (t.persistent) {
                 StepCtrl* c = p->ctrl;
                 A.halo = t.halo;
+                far_args(p, mi, &A);
                 void* args[] = {(void*)&A, (void*)&c};
                 cudaLaunchCooperativeKernel((const void*)t.fn, dim3(t.grid),
                                             dim3(t.resident ? t.threads : STEP_THREADS),
@@ -812,6 +981,7 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
     p->resident[mi] = best->resident;
     p->res_smem[mi] = best->smem;
     p->res_threads[mi] = best->resident ? best->threads : RES_THREADS_HOST;
+    p->res_far[mi] = best->resident && best->far;
     p->res_halo[mi] = best->halo;
     p->tune_ms[mi] = best->ms / (float)reps;
     p->tuned[mi] = true;
@@ -909,13 +1079,15 @@ static int run_steps(rbffd_plan* p, int mode, double dt, double tol, long long m
         if (st) return st;
         if (p->persist[mi]) {
             const bool res = p->resident[mi];
-            StepFn fn = res ? (p->res_threads[mi] == RES_THREADS_WIDE
+            StepFn fn = res ? (p->res_far[mi] ? pick_resident_far(mode, p->n, p->res_threads[mi])
+                               : p->res_threads[mi] == RES_THREADS_WIDE
                                    ? pick_resident_wide(mode, p->n, res_i16(p))
                                    : pick_resident(mode, p->n, res_i16(p)))
                             : pick(mode, p->n, true, p->minb[mi]);
             int grid = res ? device_sm_count() : persistent_grid(fn, p);
             StepArgs A = make_args(p);
             A.halo = res ? p->res_halo[mi] : 0;
+            far_args(p, mi, &A);
             StepCtrl* c = p->ctrl;
             void* args[] = {(void*)&A, (void*)&c};
             RBFFD_CHECK_CUDA(cudaEventRecord((cudaEvent_t)p->ev[0], s));
@@ -1433,9 +1605,11 @@ extern "C" int rbffd_plan_stats(const rbffd_plan* p, double* h_loop_ms, int64_t*
     if (h_loop_steps) *h_loop_steps = p->last_loop_steps;
     if (h_launches) *h_launches = p->last_launches;
     if (h_shape) {
-        h_shape[0] = p->resident[0] ? p->res_threads[0] / 512 : p->minb[0];
+        h_shape[0] = p->resident[0] ? p->res_threads[0] / 512 + (p->res_far[0] ? 4 : 0)
+                                    : p->minb[0];
         h_shape[1] = p->persist[0] ? (p->resident[0] ? -1 : 0) : p->per_sm[0] + (p->pdl[0] ? 16 : 0);
-        h_shape[2] = p->resident[1] ? p->res_threads[1] / 512 : p->minb[1];
+        h_shape[2] = p->resident[1] ? p->res_threads[1] / 512 + (p->res_far[1] ? 4 : 0)
+                                    : p->minb[1];
         h_shape[3] = p->persist[1] ? (p->resident[1] ? -1 : 0) : p->per_sm[1] + (p->pdl[1] ? 16 : 0);
     }
     return RBFFD_OK;

@@ -225,6 +225,10 @@ SWEEP_CASES = [
     (2, 31, 2, 2 | 128, "random_resident"),
     (3, 10, 4, 128, "cube_resident"),
     (2, 34, 4, 32 | 128, "resident_int32_planes"),
+    (2, 37, 4, 2048, "morton_resident_far"),
+    (2, 31, 2, 2 | 2048, "random_resident_far"),
+    (3, 10, 4, 2048, "cube_resident_far"),
+    (2, 90, 4, 2048, "morton_resident_far_every_sm"),
 ]
 
 
@@ -251,14 +255,15 @@ NN_CASES = [(2, 1, 6)] + [(2, 2, n) for n in (12, 13, 16, 20, 24, 30, 31, 40, 48
 
 @pytest.mark.parametrize("d,m,n", NN_CASES)
 def test_sweep_parity_every_compiled_stencil_size(rb, orc, d, m, n):
-    """FP64 sweeps (graph and persistent launches) and a defect correction with FP32
-    inner sweeps, at each stencil size that has a specialised kernel; 529 interior
-    rows in 2D (16 full slices and a ragged one), 512 in 3D."""
+    """FP64 sweeps (graph, persistent and resident-with-far-lists launches) and a
+    defect correction with FP32 inner sweeps, at each stencil size that has a
+    specialised kernel; 529 interior rows in 2D (16 full slices and a ragged one),
+    512 in 3D."""
     p = build(orc, d, 24 if d == 2 else 9, m, seed=48, n=n)
     dt = _dt(orc, p)
     K = 100
     ou, os_, ores, _ = orc.solve_explicit(p.w, p.idx, p.interior, p.f, p.u0, dt, K, 0.0)
-    for flags in (0, 16):
+    for flags in (0, 16, 2048):
         plan = _plan(rb, p, flags)
         u = T(p.u0)
         code, steps, res = plan.solve_explicit(T(p.f), u, dt, K, 0.0)
@@ -282,7 +287,7 @@ def test_sweep_stop_rule_matches(rb, orc):
     # a tolerance the oracle reaches after a few hundred steps
     ou, os_, ores, ost = orc.solve_explicit(p.w, p.idx, p.interior, p.f, p.u0, dt, 5000, 1.0)
     assert ost == 0 and 1 < os_ < 5000
-    for flags in (0, 16, 128):
+    for flags in (0, 16, 128, 2048):
         plan = _plan(rb, p, flags)
         u = T(p.u0)
         code, steps, res = plan.solve_explicit(T(p.f), u, dt, 5000, 1.0)
@@ -336,7 +341,7 @@ def test_launch_modes_same_bits(rb, orc):
     p = build(orc, 2, 30, 4, seed=47)
     dt = _dt(orc, p)
     outs = []
-    for flags in (0, 16, 64, 128, 256, 512):
+    for flags in (0, 16, 64, 128, 256, 512, 2048):
         plan = _plan(rb, p, flags)
         u = T(p.u0)
         plan.solve_explicit(T(p.f), u, dt, 500, 0.0)
@@ -353,6 +358,8 @@ def test_launch_modes_same_bits(rb, orc):
             assert shape[1] > 16 and shape[3] > 16
         if flags == 512:
             assert 0 < shape[1] <= 4 and 0 < shape[3] <= 4
+        if flags == 2048:
+            assert shape[1] == -1 and shape[3] == -1 and shape[0] >= 4 and shape[2] >= 4
         outs.append((H(u), H(u2)))
         plan.destroy()
     for a, b in outs[1:]:
@@ -395,7 +402,7 @@ def test_dc_parity(rb, orc):
     dt = _dt(orc, p)
     args = (dt, 1e-8, 30, 3000, 1e-3)
     ou, oo, oi, ores, ost = orc.solve_dc(p.w, p.idx, p.interior, p.f, p.u0, *args)
-    for flags in (0, 128, 32 | 128):        # graph; resident (16-bit, int32 index planes)
+    for flags in (0, 128, 32 | 128, 2048):  # graph; resident (16-bit, int32 planes; far lists)
         plan = _plan(rb, p, flags)
         u = T(p.u0)
         code, outer, inner, res = plan.solve_dc(T(p.f), u, *args)
@@ -598,18 +605,19 @@ def test_persistent_barrier_wait_runs_out(rb, orc):
     assert steps == 100
     assert np.max(np.abs(H(u) - ou)) <= 1e-12 * np.max(np.abs(ou))
     plan.destroy()
-    # the resident launch's barrier is the same bounded wait
-    plan = _plan(rb, p, rb.RBFFD_LAUNCH_RESIDENT)
-    plan.solve_explicit(T(p.f), T(p.u0), dt, 5, 0.0)
-    plan.set_wait(20.0, 1)
-    with pytest.raises(rb.RbffdError) as ei:
-        plan.solve_explicit(T(p.f), T(p.u0), dt, 100, 0.0)
-    assert ei.value.code == rb.RBFFD_ERR_TIMEOUT
-    plan.set_wait(0.0, 0)
-    u = T(p.u0)
-    plan.solve_explicit(T(p.f), u, dt, 100, 0.0)
-    assert np.max(np.abs(H(u) - ou)) <= 1e-12 * np.max(np.abs(ou))
-    plan.destroy()
+    # the resident launch's barrier (with or without far lists) is the same bounded wait
+    for flags in (rb.RBFFD_LAUNCH_RESIDENT, rb.RBFFD_LAUNCH_FAR):
+        plan = _plan(rb, p, flags)
+        plan.solve_explicit(T(p.f), T(p.u0), dt, 5, 0.0)
+        plan.set_wait(20.0, 1)
+        with pytest.raises(rb.RbffdError) as ei:
+            plan.solve_explicit(T(p.f), T(p.u0), dt, 100, 0.0)
+        assert ei.value.code == rb.RBFFD_ERR_TIMEOUT
+        plan.set_wait(0.0, 0)
+        u = T(p.u0)
+        plan.solve_explicit(T(p.f), u, dt, 100, 0.0)
+        assert np.max(np.abs(H(u) - ou)) <= 1e-12 * np.max(np.abs(ou))
+        plan.destroy()
 
 
 def test_resident_launch_refuses_a_plan_too_large(rb):

@@ -1201,6 +1201,59 @@ extern "C" int rbffd_apply(const double* w, const int32_t* idx, int64_t nc, int 
     return RBFFD_OK;
 }
 
+// Shares of the resident launch: block b of its grid (one block per SM) owns
+// slices [nslices b / G, nslices (b+1) / G).  For a Morton plan that asks for
+// the resident launch (or leaves the choice to the autotuner) and whose
+// planes could fit, the rows of each share are reordered once at creation:
+// the rows whose stencils read only rows of the same share ("inner" rows)
+// first, then the others, each group in its Morton order.  The share's rows
+// stay the same set, so the same rows are inner; now the leading slices of a
+// share are whole slices of inner rows, which the resident kernel computes
+// while it waits for the other blocks at the step barrier.
+static bool inner_first_applies(const rbffd_plan* p, int flags) {
+    if ((flags & 15) != RBFFD_ORDER_MORTON ||
+        !(flags & (RBFFD_LAUNCH_AUTO | RBFFD_LAUNCH_RESIDENT | RBFFD_LAUNCH_FAR)))
+        return false;
+    const int G = device_sm_count();
+    if (p->nslices < 2 * (int64_t)G) return false;   // a share of less than two slices
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    // the smaller (FP32) planes with 16-bit indices: the resident launch of at
+    // least one arithmetic may fit
+    return resident_smem(p->nslices, p->n, MODE_INNER32, true, G, -1) + 1024u <= (unsigned)optin;
+}
+
+// the reordered perm (slot -> node) from the packed neighbour slots `col`
+static void inner_first_perm(const rbffd_plan* p, const std::vector<int32_t>& col,
+                             std::vector<int32_t>& perm) {
+    const int G = device_sm_count();
+    const int64_t nsl = p->nslices, NI = p->NI;
+    const int n = p->n;
+    std::vector<int32_t> inner, other;
+    for (int b = 0; b < G; ++b) {
+        const int64_t r0 = nsl * b / G * SLICE;
+        const int64_t r1 = std::min<int64_t>(nsl * (b + 1) / G * SLICE, NI);
+        inner.clear();
+        other.clear();
+        for (int64_t r = r0; r < r1; ++r) {
+            const int64_t base = (r / SLICE) * n * SLICE + r % SLICE;
+            bool in = true;
+            for (int j = 0; j < n && in; ++j) {
+                const int32_t c = col[base + (int64_t)j * SLICE];
+                in = c >= r0 && c < r1;
+            }
+            (in ? inner : other).push_back(perm[r]);
+        }
+        std::copy(inner.begin(), inner.end(), perm.begin() + r0);
+        std::copy(other.begin(), other.end(), perm.begin() + r0 + (int64_t)inner.size());
+    }
+}
+
 extern "C" int rbffd_plan_create(const double* xyz, const uint8_t* is_bnd, int64_t N, int d,
                                  const int32_t* interior, const int32_t* idx, const double* w,
                                  int64_t NI, int n, int flags, uint64_t seed, rbffd_plan** out,
@@ -1329,6 +1382,37 @@ extern "C" int rbffd_plan_create(const double* xyz, const uint8_t* is_bnd, int64
                                   "exactly once (NI = number of interior nodes)");
             st = RBFFD_ERR_ARG;
             break;
+        }
+        if (inner_first_applies(p, flags)) {
+            std::vector<int32_t> col(ell), perm(N);
+            if ((e = cudaMemcpyAsync(col.data(), p->col, sizeof(int32_t) * ell,
+                                     cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(perm.data(), p->perm, sizeof(int32_t) * N,
+                                     cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+                (e = cudaStreamSynchronize(s)) != cudaSuccess)
+                break;
+            inner_first_perm(p, col, perm);
+            if ((e = cudaMemcpyAsync(p->perm, perm.data(), sizeof(int32_t) * N,
+                                     cudaMemcpyHostToDevice, s)) != cudaSuccess)
+                break;
+            invert_perm<<<G, 256, 0, s>>>(p->perm, N, p->inv);
+            if ((e = cudaMemsetAsync(p->row_of_slot, 0xff, sizeof(int32_t) * NI, s)) !=
+                cudaSuccess)
+                break;
+            check_interior<<<G, 256, 0, s>>>(is_bnd, interior, p->inv, N, NI, p->row_of_slot,
+                                             err.as<int>());
+            pack_stencils<<<G, 256, 0, s>>>(p->row_of_slot, p->inv, idx, w, NI, p->nslices, n, N,
+                                            p->w64, p->w32, p->col, err.as<int>());
+            if ((e = cudaGetLastError()) != cudaSuccess) break;
+            if ((e = cudaMemcpyAsync(hv, err.p, sizeof(hv), cudaMemcpyDeviceToHost, s)) !=
+                    cudaSuccess ||
+                (e = cudaStreamSynchronize(s)) != cudaSuccess)
+                break;
+            if (hv[0] & 0xffffffffull) {
+                set_error("rbffd_plan_create: repacking the resident shares failed");
+                st = RBFFD_ERR_CUDA;
+                break;
+            }
         }
         if (!(flags & RBFFD_PACK_IDX32)) {
             if ((e = cudaMalloc((void**)&p->col16, sizeof(uint16_t) * ell)) != cudaSuccess) break;

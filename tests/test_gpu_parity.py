@@ -678,3 +678,64 @@ def test_resident_halo_windows_same_bits(rb, orc, halo):
     assert (outer, inner) == (oo, oi)
     assert np.max(np.abs(H(u2) - du)) <= 1e-12 * np.max(np.abs(du))
     plan.destroy()
+
+
+def _share_inner_flags(p, perm, G):
+    """Per resident share (block b of G owns slices [nsl b / G, nsl (b+1) / G)):
+    for each of its rows, whether every neighbour is a row of the same share."""
+    NI = p.NI
+    slot = np.empty(p.N, np.int64)
+    slot[perm] = np.arange(p.N)
+    row_of_node = np.full(p.N, -1, np.int64)
+    row_of_node[p.interior] = np.arange(NI)
+    cols = slot[p.idx[row_of_node[perm[:NI]]]]        # [slot][j] neighbour slots
+    nsl = (NI + 31) // 32
+    out = []
+    for b in range(G):
+        r0, r1 = nsl * b // G * 32, min(nsl * (b + 1) // G * 32, NI)
+        c = cols[r0:r1]
+        out.append(np.all((c >= r0) & (c < r1), axis=1))
+    return out
+
+
+@pytest.mark.parametrize("Kg", [200, 300])
+def test_resident_shares_inner_rows_first(rb, orc, Kg):
+    """Morton plans that may take the resident launch put, in each SM's share of
+    the rows, the rows whose stencils stay inside the share first (each group in
+    Morton order); the resident launch computes those slices while it waits at
+    the step barrier.  40k- and 90k-node squares: the order's invariant (the same
+    set of inner rows as plain Morton order, now leading each share), then 300
+    FP64 sweeps and a defect correction in the resident launches (window and
+    L2, far lists, and the autotuner's pick) against the oracle."""
+    p = build(orc, 2, Kg, 4, seed=67)
+    G = torch.cuda.get_device_properties(0).multi_processor_count
+    dt = _dt(orc, p)
+    K = 300
+    ou, os_, ores, ost = orc.solve_explicit(p.w, p.idx, p.interior, p.f, p.u0, dt, K, 0.0)
+    args = (dt, 1e-7, 3, 400, 1e-3)
+    du, oo, oi, _, _ = orc.solve_dc(p.w, p.idx, p.interior, p.f, p.u0, *args)
+    plain = _plan(rb, p, rb.RBFFD_LAUNCH_GRAPH)
+    ref = _share_inner_flags(p, H(plain.perm()), G)
+    plain.destroy()
+    for flags in (rb.RBFFD_LAUNCH_RESIDENT, rb.RBFFD_LAUNCH_FAR, rb.RBFFD_LAUNCH_AUTO):
+        plan = _plan(rb, p, flags)
+        perm = H(plan.perm())
+        assert np.array_equal(np.sort(perm), np.arange(p.N))
+        flags_b = _share_inner_flags(p, perm, G)
+        for a, b in zip(ref, flags_b):
+            assert a.sum() == b.sum()                       # the same inner rows
+            assert np.all(np.diff(b.astype(np.int8)) <= 0)  # inner rows lead the share
+        assert sum(b.sum() for b in flags_b) > 32 * G       # whole inner slices exist
+        u = T(p.u0)
+        code, steps, res = plan.solve_explicit(T(p.f), u, dt, K, 0.0)
+        assert code == rb.RBFFD_NOT_CONVERGED and steps == os_ == K
+        assert np.max(np.abs(H(u) - ou)) <= 1e-12 * np.max(np.abs(ou))
+        assert res == pytest.approx(ores, rel=1e-12)
+        u2 = T(p.u0)
+        code, outer, inner, res = plan.solve_dc(T(p.f), u2, *args)
+        assert (outer, inner) == (oo, oi)
+        assert np.max(np.abs(H(u2) - du)) <= 1e-12 * np.max(np.abs(du))
+        if flags != rb.RBFFD_LAUNCH_AUTO:
+            shape = plan.stats()[3]
+            assert shape[1] == -1 and shape[3] == -1   # resident launch, both sweeps
+        plan.destroy()

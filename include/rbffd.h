@@ -308,11 +308,16 @@ RBFFD_API int rbffd_fp64_fma_rate(int64_t iters, double* h_fma_per_s, double* h_
  * fastest.  The resident launch is a persistent launch of one block per SM
  * whose slices' weight and index planes (and their rows' f) are copied into
  * shared memory once per solve by TMA bulk copies, so each step reads only
- * the iterate; it fits while the plan's share per SM does (about 107,000
- * interior rows at n = 30 in FP64 with 16-bit codes, 185,000 for the FP32
+ * the iterate; it fits while the plan's share per SM does (about 102,000
+ * interior rows at n = 30 in FP64 with 16-bit codes, 175,000 for the FP32
  * inner sweep); a _RESIDENT plan that does not fit returns
- * RBFFD_ERR_CAPACITY from its first solve.  A plan with Neumann nodes always
- * replays graphs.  Every mode gives the same results bit for bit.
+ * RBFFD_ERR_CAPACITY from its first solve.  A Morton plan created with
+ * _RESIDENT, _FAR or _AUTO whose planes could fit (and whose share per SM
+ * is at least two slices) orders each share's rows with the rows whose
+ * supports lie inside the share first, each group in Morton order; the
+ * resident launch computes those while it waits for the other SMs at the
+ * step barrier.  A plan with Neumann nodes always replays graphs.  Every
+ * mode gives the same results bit for bit.
  */
 RBFFD_API int rbffd_plan_create(const double* xyz, const uint8_t* is_bnd, int64_t N, int d,
                       const int32_t* interior, const int32_t* idx, const double* w, int64_t NI,

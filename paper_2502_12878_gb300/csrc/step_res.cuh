@@ -184,9 +184,11 @@ __device__ __forceinline__ T row_dot_own(const T* w, const unsigned char* idx_s,
 // fire-and-forget; the arrival releases the block's iterate writes), and at
 // the start of step k + 1 one thread waits for every block's arrival (bounded
 // by `spin` clock cycles; `held`: arrivals added to every target, 0 but in a
-// test of the timeout path), then loads step k's full residual for the stop
-// decision (applied at the end of step k + 1, one step behind), and block 0
-// clears the slot step k + 2 will use.  Thread 0 only.
+// test of the timeout path), then loads step k's full residual, to which the
+// stop rule is applied once the block has staged step k + 1's window (every
+// block the same rule to the same value, so all stop together, before step
+// k + 1 writes more than the other buffer), and block 0 clears the slot step
+// k + 2 will use.  Thread 0 only.
 __device__ __forceinline__ void res_arrive(StepCtrl* c, long long k, unsigned long long m) {
     red_max_relaxed(&c->res[k % 3], m);
     red_add_release(&c->arrivals, 1ull);
@@ -206,6 +208,40 @@ __device__ __forceinline__ bool res_wait(StepCtrl* c, LagState& S, long long k, 
     return true;
 }
 
+// the stop rule for step kk from its residual (loaded at its barrier); block 0
+// records the outcome of a run that stops.  Thread 0 only.
+__device__ __forceinline__ int res_decide(StepCtrl* c, LagState& S, long long kk) {
+    const double R = bitsd(S.pend);
+    if (kk == 0) S.R0 = R;
+    const int dn = stop_rule(R, S.R0, kk, S.kmax, S.tol);
+    if (dn != DONE_RUNNING && blockIdx.x == 0) {
+        volatile StepCtrl* vc = c;
+        vc->res_first = S.R0;
+        vc->res_last = R;
+        vc->k = kk + 1;
+        vc->done = dn;
+    }
+    return dn;
+}
+
+// block max of IEEE bits over TH threads, valid in thread 0: one shared-memory
+// round and a warp-wide reduction in warp 0
+template <int TH>
+__device__ __forceinline__ unsigned long long res_block_max(unsigned long long v) {
+    __shared__ unsigned long long wm[TH / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) wm[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        v = lane < TH / 32 ? wm[lane] : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    }
+    return v;
+}
+
 // All steps of a run in one cooperative launch of one block per SM.  The
 // index planes are the 16-bit codes when every slice of the plan has them
 // (I16), else the int32 slots.
@@ -221,16 +257,18 @@ __device__ __forceinline__ bool res_wait(StepCtrl* c, LagState& S, long long k, 
 // of an inner slice needs nothing but the block's own u^{k+1}, which it keeps
 // in shared memory, so while warp 0 waits for the other blocks' arrivals of
 // step k and then stages the halo window, the other warps compute the inner
-// slices (holding their results in registers: the global buffer they go to
-// is still being read by slower blocks until the barrier completes).  Then
-// all warps compute the remaining slices from the window.  Each row's
-// arithmetic is the same whichever phase computes it.
+// slices into the second own-row buffer; their results go to the iterate
+// only after the barrier (slower blocks may still read the buffer they
+// overwrite).  Then all warps compute the remaining slices from the window.
+// Each row's arithmetic is the same whichever phase computes it.  Shares are
+// ordered with their inner rows first at plan creation, so whole slices of
+// them lead.
 template <int NN, int MODE, bool I16, int TH, bool FAR = false>
 __global__ void __launch_bounds__(TH, 1) resident_kernel(StepArgs A, StepCtrl* c) {
     typedef typename std::conditional<MODE == MODE_SWEEP64, double, float>::type T;
     extern __shared__ __align__(128) unsigned char rsm[];
     __shared__ long long s_k, s_max, s_spin;
-    __shared__ int s_held, s_fail, s_nin;
+    __shared__ int s_held, s_fail, s_nin, s_dn;
     __shared__ double s_dt;
     LagState S;
     int64_t s0, s1;
@@ -389,13 +427,13 @@ __global__ void __launch_bounds__(TH, 1) resident_kernel(StepArgs A, StepCtrl* c
         unsigned long long m = 0;
         if (warp == 0) {
             if (lane == 0) {
-                // the barrier of step k - 1, then this step's halo window of the
-                // iterate (one bulk copy on the mbarrier's next phase).  The
-                // other blocks' writes of the previous step were acquired at the
-                // barrier; the proxy fence orders them before the copy, which
-                // reads through the async proxy.
-                bool ok = k == k0 || res_wait(c, S, k - 1, k0, spin, held);
-                if (!ok) s_fail = 1;
+                // the barrier of step k - 1 and its stop decision, then this
+                // step's halo window of the iterate (one bulk copy on the
+                // mbarrier's next phase).  The other blocks' writes of the
+                // previous step were acquired at the barrier; the proxy fence
+                // orders them before the copy, which reads through the async proxy.
+                const bool ok = k == k0 || res_wait(c, S, k - 1, k0, spin, held);
+                s_fail = ok ? 0 : 1;
                 if (ok && A.halo >= 0) {
                     asm volatile("fence.proxy.async.global;" ::: "memory");
                     if (W > 0) {
@@ -416,7 +454,6 @@ __global__ void __launch_bounds__(TH, 1) resident_kernel(StepArgs A, StepCtrl* c
                     }
                 }
             }
-            __syncwarp();
         } else {
             for (int i = warp - 1; i < npre; i += NW - 1) {
                 const int ls = ord[i];
@@ -453,9 +490,15 @@ __global__ void __launch_bounds__(TH, 1) resident_kernel(StepArgs A, StepCtrl* c
         if constexpr (FAR)
             for (int32_t i = threadIdx.x; i < nfar; i += TH)
                 h_s[W + i] = ld_iter<true>(ucur + __ldg(A.fl_slot + f0 + i));
+        // the stop decision for step k - 1 (its residual was loaded at the
+        // barrier, off the path of this step's copy)
+        if (threadIdx.x == 0) s_dn = k > k0 ? res_decide(c, S, k - 1) : DONE_RUNNING;
         const uint32_t phase = (uint32_t)((k - k0 + 1) & 1);
         if (A.halo >= 0 && !mbar_wait(mbar, phase, spin)) s_fail = 1;
         __syncthreads();
+        // the run stopped after step k - 1: its result u^k is complete (phase
+        // 1 wrote only the other buffer) and this step's copy has landed
+        if (s_dn != DONE_RUNNING && !s_fail) return;
         if (s_fail) {
             if (threadIdx.x == 0) {
                 atomicExch(&c->done, DONE_TIMEOUT);
@@ -505,18 +548,12 @@ __global__ void __launch_bounds__(TH, 1) resident_kernel(StepArgs A, StepCtrl* c
                 m = max(m, abs_bits(rho));
             }
         }
-        // the decision of step k - 1 (its residual loaded at its barrier)
-        if (k > k0 && lag_decide(c, S, k - 1) != DONE_RUNNING) return;
-        m = block_max_bits(m);
+        m = res_block_max<TH>(m);
         if (threadIdx.x == 0) res_arrive(c, k, m);
     }
-    if (kmax > k0) {
-        // the last step's barrier and decision: it stops the run
-        if (threadIdx.x == 0 && !res_wait(c, S, kmax - 1, k0, spin, held)) s_fail = 1;
-        __syncthreads();
-        if (s_fail) return;
-        lag_decide(c, S, kmax - 1);
-    }
+    // the last step's barrier and decision: it stops the run
+    if (kmax > k0 && threadIdx.x == 0 && res_wait(c, S, kmax - 1, k0, spin, held))
+        res_decide(c, S, kmax - 1);
 }
 
 }  // namespace rbffd

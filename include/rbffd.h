@@ -68,6 +68,10 @@ extern "C" {
 #define RBFFD_LAUNCH_FAR 2048      /* resident, with far lists: each block also stages the
                                       values outside its window that its rows read, so
                                       every gather reads shared memory */
+#define RBFFD_LAUNCH_SPLIT 4096    /* persistent, one block per SM over a share of the
+                                      rows: stencils streamed, the share's iterate in shared
+                                      memory, the rows inside the share computed while
+                                      the block waits at the step barrier */
 
 typedef struct rbffd_plan rbffd_plan;
 

@@ -46,6 +46,7 @@ RBFFD_LAUNCH_RESIDENT = 128
 RBFFD_LAUNCH_PDL = 256
 RBFFD_LAUNCH_NO_PDL = 512
 RBFFD_LAUNCH_FAR = 2048
+RBFFD_LAUNCH_SPLIT = 4096
 RBFFD_PACK_IDX32 = 32
 
 EXPORTED = [

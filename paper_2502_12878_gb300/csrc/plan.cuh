@@ -86,6 +86,10 @@ struct rbffd_plan {
     unsigned res_smem[2] = {0, 0};      // its dynamic shared memory per block
     int res_threads[2] = {512, 512};    // and its block size
     bool res_far[2] = {false, false};   // ... with far lists (every gather in shared memory)
+    bool split[2] = {false, false};     // ... as the split launch (stencils streamed, own rows
+                                        // in shared memory; res_smem / res_threads its shape)
+    bool inner_first = false;           // each SM's share ordered with its inner rows first
+    int32_t* inner_sl = nullptr;        // [SMs] its leading slices of inner rows only
     // far-list data per mode (built when the tuner first considers it): the
     // window reach it was built for, the most far slots of a block, the
     // entries' local indices, each block's far slots

@@ -181,6 +181,9 @@ struct StepArgs {
     const int32_t* fl_off;    // [blocks + 1]
     const int32_t* fl_slot;
     int64_t fl_max;           // most far slots of a block
+    // split launch: per block (SM) the number of leading slices of its share
+    // that are inner rows only (plans ordered inner rows first)
+    const int32_t* inner;
 };
 
 // The warp's first slice.  Large plans give each block runs of consecutive

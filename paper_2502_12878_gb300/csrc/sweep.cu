@@ -34,6 +34,7 @@
 #include <vector>
 
 #include "step.cuh"
+#include "step_split.cuh"
 
 namespace rbffd {
 
@@ -509,6 +510,7 @@ static StepArgs make_args(const rbffd_plan* p) {
     A.fl_off = nullptr;
     A.fl_slot = nullptr;
     A.fl_max = 0;
+    A.inner = p->inner_sl;
     return A;
 }
 
@@ -535,7 +537,7 @@ static void free_plan(rbffd_plan* p) {
                     p->fs, p->e[0], p->e[1], p->d32, p->scratch, p->ctrl, p->nslot, p->ncol,
                     p->nw, p->ng, p->ng0, p->uN, p->col16, p->sbase,
                     p->fl_idx[0], p->fl_idx[1], p->fl_off[0], p->fl_off[1],
-                    p->fl_slot[0], p->fl_slot[1]};
+                    p->fl_slot[0], p->fl_slot[1], p->inner_sl};
     for (void* b : bufs)
         if (b) cudaFree(b);
     drop_graphs(p);
@@ -592,11 +594,12 @@ static int ctrl_reset(rbffd_plan* p, double dt, double tol, long long max_steps,
 // (or left to it) and the plan has no Neumann phase, which only graphs replay
 static bool may_persist(const rbffd_plan* p) {
     return (p->flags & (RBFFD_LAUNCH_PERSISTENT | RBFFD_LAUNCH_AUTO | RBFFD_LAUNCH_RESIDENT |
-                        RBFFD_LAUNCH_FAR)) != 0 &&
+                        RBFFD_LAUNCH_FAR | RBFFD_LAUNCH_SPLIT)) != 0 &&
            p->NN == 0;
 }
 static bool may_graph(const rbffd_plan* p) {
-    return !(p->flags & (RBFFD_LAUNCH_PERSISTENT | RBFFD_LAUNCH_RESIDENT | RBFFD_LAUNCH_FAR)) ||
+    return !(p->flags & (RBFFD_LAUNCH_PERSISTENT | RBFFD_LAUNCH_RESIDENT | RBFFD_LAUNCH_FAR |
+                         RBFFD_LAUNCH_SPLIT)) ||
            p->NN > 0;
 }
 
@@ -772,6 +775,7 @@ struct TuneCand {
     bool persistent;
     bool resident;   // the resident persistent launch (smem bytes, halo, threads below)
     bool far;        // ... with far lists
+    bool split;      // the split persistent launch (smem bytes, threads below)
     int threads;
     unsigned smem;
     int64_t halo;
@@ -797,7 +801,8 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
     const int n_minb = N_MINB;
     // candidate c: graph shapes per_sm = c (1..4), then the persistent launch (c = 5)
     const bool only_far = (p->flags & RBFFD_LAUNCH_FAR) != 0;
-    const bool only_res = (p->flags & RBFFD_LAUNCH_RESIDENT) != 0 || only_far;
+    const bool only_split = (p->flags & RBFFD_LAUNCH_SPLIT) != 0;
+    const bool only_res = (p->flags & RBFFD_LAUNCH_RESIDENT) != 0 || only_far || only_split;
     const int c_lo = may_graph(p) ? 1 : 5, c_hi = may_persist(p) ? 5 : 4;
     std::vector<TuneCand> cands;
     const int pdl_lo = (p->flags & RBFFD_LAUNCH_PDL) ? 1 : 0;
@@ -811,6 +816,7 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
                 t.persistent = c == 5;
                 t.resident = false;
                 t.far = false;
+                t.split = false;
                 t.threads = STEP_THREADS;
                 t.smem = 0;
                 t.halo = 0;
@@ -826,13 +832,14 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
     // window, the block's own rows, 256, 1024, 4096 slots, the most that fits;
     // and its block size: 512 threads, and 1024 where the stencil size has it
     bool res_any = false;
-    for (int wide = 0; wide < 2 && may_persist(p) && !only_far &&
+    for (int wide = 0; wide < 2 && may_persist(p) && !only_far && !only_split &&
                        (p->flags & (RBFFD_LAUNCH_AUTO | RBFFD_LAUNCH_RESIDENT));
          ++wide) {
         TuneCand t;
         int64_t hmax = 0;
         t.threads = wide ? RES_THREADS_WIDE : RES_THREADS_HOST;
         t.far = false;
+        t.split = false;
         t.fn = resident_fn(p, mode, t.threads, &t.smem, &hmax);
         if (t.fn) {
             res_any = true;
@@ -860,7 +867,7 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
     }
     // the resident launch with far lists (its reach fixed by the build; not
     // when rbffd_plan_set_resident_halo fixed one)
-    if (may_persist(p) &&
+    if (may_persist(p) && !only_split &&
         (p->flags & (RBFFD_LAUNCH_AUTO | RBFFD_LAUNCH_RESIDENT | RBFFD_LAUNCH_FAR)) &&
         p->res_halo_set < -1) {
         int st0 = build_far(p, mode, s);
@@ -889,6 +896,7 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
             t.persistent = true;
             t.resident = true;
             t.far = true;
+            t.split = false;
             t.halo = p->fl_halo[mi];
             t.grid = device_sm_count();
             t.gx = nullptr;
@@ -897,7 +905,50 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
             cands.push_back(t);
         }
     }
-    if (only_res && !res_any) {
+    // the split launch: Morton plans ordered with each share's inner rows first
+    // (plan creation), when its own-row buffers fit one block per SM
+    bool split_any = false;
+    for (int wide = 0; wide < 2 && may_persist(p) && p->inner_first &&
+                       (p->flags & (RBFFD_LAUNCH_AUTO | RBFFD_LAUNCH_PERSISTENT | RBFFD_LAUNCH_SPLIT));
+         ++wide) {
+        TuneCand t;
+        t.threads = wide ? RES_THREADS_WIDE : RES_THREADS_HOST;
+        t.fn = pick_split(mode, p->n, t.threads);
+        if (!t.fn) continue;
+        t.grid = device_sm_count();
+        t.smem = split_smem(p->nslices, mode, t.grid);
+        int dev = 0, optin = 0, per_sm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+                cudaSuccess ||
+            t.smem + 1024u > (unsigned)optin ||
+            cudaFuncSetAttribute((const void*)t.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)t.smem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)t.fn, t.threads,
+                                                          t.smem) != cudaSuccess ||
+            per_sm < 1) {
+            cudaGetLastError();
+            continue;
+        }
+        t.minb = 1;
+        t.pdl = false;
+        t.per_sm = 1;
+        t.persistent = true;
+        t.resident = false;
+        t.far = false;
+        t.split = true;
+        t.halo = 0;
+        t.gx = nullptr;
+        t.ms = 1e30f;
+        split_any = true;
+        cands.push_back(t);
+    }
+    if (only_split && !split_any) {
+        set_error("split launch: not available for this plan (a Morton plan created with "
+                  "RBFFD_LAUNCH_SPLIT whose share of rows per SM fits shared memory)");
+        return RBFFD_ERR_CAPACITY;
+    }
+    if (only_res && !only_split && !res_any) {
         set_error("resident launch: the plan's stencils do not fit in shared memory "
                   "(%lld slices of %d entries)", (long long)p->nslices, p->n);
         return RBFFD_ERR_CAPACITY;
@@ -948,7 +999,7 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
                 far_args(p, mi, &A);
                 void* args[] = {(void*)&A, (void*)&c};
                 cudaLaunchCooperativeKernel((const void*)t.fn, dim3(t.grid),
-                                            dim3(t.resident ? t.threads : STEP_THREADS),
+                                            dim3(t.resident || t.split ? t.threads : STEP_THREADS),
                                             args, t.smem, s);
             } else {
                 cudaGraphLaunch(t.gx, s);
@@ -980,8 +1031,9 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
     p->persist[mi] = best->persistent;
     p->resident[mi] = best->resident;
     p->res_smem[mi] = best->smem;
-    p->res_threads[mi] = best->resident ? best->threads : RES_THREADS_HOST;
+    p->res_threads[mi] = best->resident || best->split ? best->threads : RES_THREADS_HOST;
     p->res_far[mi] = best->resident && best->far;
+    p->split[mi] = best->split;
     p->res_halo[mi] = best->halo;
     p->tune_ms[mi] = best->ms / (float)reps;
     p->tuned[mi] = true;
@@ -1078,15 +1130,18 @@ static int run_steps(rbffd_plan* p, int mode, double dt, double tol, long long m
         st = prepare_mode(p, mode, dt, tol, max_steps, s);
         if (st) return st;
         if (p->persist[mi]) {
-            const bool res = p->resident[mi];
-            StepFn fn = res ? (p->res_far[mi] ? pick_resident_far(mode, p->n, p->res_threads[mi])
+            // resident and split launches: one block of res_threads per SM
+            const bool res = p->resident[mi] || p->split[mi];
+            StepFn fn = p->split[mi] ? pick_split(mode, p->n, p->res_threads[mi])
+                        : p->resident[mi]
+                            ? (p->res_far[mi] ? pick_resident_far(mode, p->n, p->res_threads[mi])
                                : p->res_threads[mi] == RES_THREADS_WIDE
                                    ? pick_resident_wide(mode, p->n, res_i16(p))
                                    : pick_resident(mode, p->n, res_i16(p)))
                             : pick(mode, p->n, true, p->minb[mi]);
             int grid = res ? device_sm_count() : persistent_grid(fn, p);
             StepArgs A = make_args(p);
-            A.halo = res ? p->res_halo[mi] : 0;
+            A.halo = p->resident[mi] ? p->res_halo[mi] : 0;
             far_args(p, mi, &A);
             StepCtrl* c = p->ctrl;
             void* args[] = {(void*)&A, (void*)&c};
@@ -1201,18 +1256,19 @@ extern "C" int rbffd_apply(const double* w, const int32_t* idx, int64_t nc, int 
     return RBFFD_OK;
 }
 
-// Shares of the resident launch: block b of its grid (one block per SM) owns
-// slices [nslices b / G, nslices (b+1) / G).  For a Morton plan that asks for
-// the resident launch (or leaves the choice to the autotuner) and whose
-// planes could fit, the rows of each share are reordered once at creation:
+// Shares of the resident and split launches: block b of their grid (one
+// block per SM) owns slices [nslices b / G, nslices (b+1) / G).  For a Morton
+// plan that asks for one of them (or leaves the choice to the autotuner) and
+// that one could fit, the rows of each share are reordered once at creation:
 // the rows whose stencils read only rows of the same share ("inner" rows)
 // first, then the others, each group in its Morton order.  The share's rows
 // stay the same set, so the same rows are inner; now the leading slices of a
-// share are whole slices of inner rows, which the resident kernel computes
-// while it waits for the other blocks at the step barrier.
+// share are whole slices of inner rows, which those kernels compute while
+// they wait for the other blocks at the step barrier.
 static bool inner_first_applies(const rbffd_plan* p, int flags) {
     if ((flags & 15) != RBFFD_ORDER_MORTON ||
-        !(flags & (RBFFD_LAUNCH_AUTO | RBFFD_LAUNCH_RESIDENT | RBFFD_LAUNCH_FAR)))
+        !(flags & (RBFFD_LAUNCH_AUTO | RBFFD_LAUNCH_RESIDENT | RBFFD_LAUNCH_FAR |
+                   RBFFD_LAUNCH_PERSISTENT | RBFFD_LAUNCH_SPLIT)))
         return false;
     const int G = device_sm_count();
     if (p->nslices < 2 * (int64_t)G) return false;   // a share of less than two slices
@@ -1224,17 +1280,23 @@ static bool inner_first_applies(const rbffd_plan* p, int flags) {
         return false;
     }
     // the smaller (FP32) planes with 16-bit indices: the resident launch of at
-    // least one arithmetic may fit
-    return resident_smem(p->nslices, p->n, MODE_INNER32, true, G, -1) + 1024u <= (unsigned)optin;
+    // least one arithmetic may fit; else the split launch's own-row buffers
+    if (flags & (RBFFD_LAUNCH_AUTO | RBFFD_LAUNCH_RESIDENT | RBFFD_LAUNCH_FAR))
+        if (resident_smem(p->nslices, p->n, MODE_INNER32, true, G, -1) + 1024u <= (unsigned)optin)
+            return true;
+    return (flags & (RBFFD_LAUNCH_AUTO | RBFFD_LAUNCH_PERSISTENT | RBFFD_LAUNCH_SPLIT)) &&
+           split_smem(p->nslices, MODE_INNER32, G) + 1024u <= (unsigned)optin;
 }
 
-// the reordered perm (slot -> node) from the packed neighbour slots `col`
+// the reordered perm (slot -> node) from the packed neighbour slots `col`,
+// and per share the number of its leading slices that hold inner rows only
 static void inner_first_perm(const rbffd_plan* p, const std::vector<int32_t>& col,
-                             std::vector<int32_t>& perm) {
+                             std::vector<int32_t>& perm, std::vector<int32_t>& inner_sl) {
     const int G = device_sm_count();
     const int64_t nsl = p->nslices, NI = p->NI;
     const int n = p->n;
     std::vector<int32_t> inner, other;
+    inner_sl.assign(G, 0);
     for (int b = 0; b < G; ++b) {
         const int64_t r0 = nsl * b / G * SLICE;
         const int64_t r1 = std::min<int64_t>(nsl * (b + 1) / G * SLICE, NI);
@@ -1251,6 +1313,7 @@ static void inner_first_perm(const rbffd_plan* p, const std::vector<int32_t>& co
         }
         std::copy(inner.begin(), inner.end(), perm.begin() + r0);
         std::copy(other.begin(), other.end(), perm.begin() + r0 + (int64_t)inner.size());
+        inner_sl[b] = (int32_t)(inner.size() / SLICE);
     }
 }
 
@@ -1391,9 +1454,16 @@ extern "C" int rbffd_plan_create(const double* xyz, const uint8_t* is_bnd, int64
                                      cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
                 (e = cudaStreamSynchronize(s)) != cudaSuccess)
                 break;
-            inner_first_perm(p, col, perm);
+            std::vector<int32_t> inner_sl;
+            inner_first_perm(p, col, perm, inner_sl);
+            p->inner_first = true;
             if ((e = cudaMemcpyAsync(p->perm, perm.data(), sizeof(int32_t) * N,
-                                     cudaMemcpyHostToDevice, s)) != cudaSuccess)
+                                     cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+                (e = cudaMalloc((void**)&p->inner_sl, sizeof(int32_t) * inner_sl.size())) !=
+                    cudaSuccess ||
+                (e = cudaMemcpyAsync(p->inner_sl, inner_sl.data(),
+                                     sizeof(int32_t) * inner_sl.size(), cudaMemcpyHostToDevice,
+                                     s)) != cudaSuccess)
                 break;
             invert_perm<<<G, 256, 0, s>>>(p->perm, N, p->inv);
             if ((e = cudaMemsetAsync(p->row_of_slot, 0xff, sizeof(int32_t) * NI, s)) !=
@@ -1689,12 +1759,14 @@ extern "C" int rbffd_plan_stats(const rbffd_plan* p, double* h_loop_ms, int64_t*
     if (h_loop_steps) *h_loop_steps = p->last_loop_steps;
     if (h_launches) *h_launches = p->last_launches;
     if (h_shape) {
-        h_shape[0] = p->resident[0] ? p->res_threads[0] / 512 + (p->res_far[0] ? 4 : 0)
-                                    : p->minb[0];
-        h_shape[1] = p->persist[0] ? (p->resident[0] ? -1 : 0) : p->per_sm[0] + (p->pdl[0] ? 16 : 0);
-        h_shape[2] = p->resident[1] ? p->res_threads[1] / 512 + (p->res_far[1] ? 4 : 0)
-                                    : p->minb[1];
-        h_shape[3] = p->persist[1] ? (p->resident[1] ? -1 : 0) : p->per_sm[1] + (p->pdl[1] ? 16 : 0);
+        for (int mi = 0; mi < 2; ++mi) {
+            h_shape[2 * mi] = p->resident[mi] ? p->res_threads[mi] / 512 + (p->res_far[mi] ? 4 : 0)
+                              : p->split[mi] ? p->res_threads[mi] / 512
+                                             : p->minb[mi];
+            h_shape[2 * mi + 1] = p->persist[mi]
+                                      ? (p->resident[mi] ? -1 : p->split[mi] ? -2 : 0)
+                                      : p->per_sm[mi] + (p->pdl[mi] ? 16 : 0);
+        }
     }
     return RBFFD_OK;
 }

@@ -121,23 +121,29 @@ def test_square_1M_m4_all_rows(rb, orc):
     dt = 3.7e-8
     K = 50
     ou, osteps, ores, _ = orc.solve_explicit(ow, oidx, ointer, f, u0, dt, K, 0.0)
-    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
-    plan = rb.Plan(T(oxyz), T(obnd), T(ointer), T(oidx), T(ow), rb.RBFFD_ORDER_MORTON)
-    lay = plan.layout()
-    assert 0 < lay["rows16"] < len(ointer)          # both kinds of slice run
-    u = T(u0)
-    code, steps, res = plan.solve_explicit(T(f), u, dt, K, 0.0)
-    assert steps == osteps == K
-    assert np.max(np.abs(H(u) - ou)) <= 1e-12 * np.max(np.abs(ou))
-    assert res == pytest.approx(ores, rel=1e-12)
     # defect correction: one outer pass of 50 FP32 inner steps
     du, oo, oi, ores_dc, _ = orc.solve_dc(ow, oidx, ointer, f, u0, dt, 0.0, 1, K, 0.0)
-    u = T(u0)
-    code, outer, inner, res_dc = plan.solve_dc(T(f), u, dt, 0.0, 1, K, 0.0)
-    assert (outer, inner) == (oo, oi) == (1, K)
-    assert np.max(np.abs(H(u) - du)) <= 1e-12 * np.max(np.abs(du))
-    assert res_dc == pytest.approx(ores_dc, rel=1e-12)
-    plan.destroy()
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    # graph-replayed steps, and the split persistent launch (each SM's share of
+    # rows ordered inner rows first, its iterate in shared memory)
+    for flags in (rb.RBFFD_LAUNCH_GRAPH, rb.RBFFD_LAUNCH_SPLIT):
+        plan = rb.Plan(T(oxyz), T(obnd), T(ointer), T(oidx), T(ow), rb.RBFFD_ORDER_MORTON | flags)
+        lay = plan.layout()
+        assert 0 < lay["rows16"] < len(ointer)          # both kinds of slice run
+        u = T(u0)
+        code, steps, res = plan.solve_explicit(T(f), u, dt, K, 0.0)
+        assert steps == osteps == K
+        assert np.max(np.abs(H(u) - ou)) <= 1e-12 * np.max(np.abs(ou))
+        assert res == pytest.approx(ores, rel=1e-12)
+        u = T(u0)
+        code, outer, inner, res_dc = plan.solve_dc(T(f), u, dt, 0.0, 1, K, 0.0)
+        assert (outer, inner) == (oo, oi) == (1, K)
+        assert np.max(np.abs(H(u) - du)) <= 1e-12 * np.max(np.abs(du))
+        assert res_dc == pytest.approx(ores_dc, rel=1e-12)
+        if flags == rb.RBFFD_LAUNCH_SPLIT:
+            shape = plan.stats()[3]
+            assert shape[1] == -2 and shape[3] == -2
+        plan.destroy()
 
 
 def test_cube_8M_m4_one_step_sampled(rb, orc):

@@ -618,6 +618,25 @@ def test_persistent_barrier_wait_runs_out(rb, orc):
         plan.solve_explicit(T(p.f), u, dt, 100, 0.0)
         assert np.max(np.abs(H(u) - ou)) <= 1e-12 * np.max(np.abs(ou))
         plan.destroy()
+    # the split launch (a plan of at least two slices per SM): the same bounded
+    # wait, while its other warps compute the inner slices
+    q = build(orc, 2, 110, 4, seed=53)
+    dtq = _dt(orc, q)
+    qu, *_ = orc.solve_explicit(q.w, q.idx, q.interior, q.f, q.u0, dtq, 100, 0.0)
+    plan = _plan(rb, q, rb.RBFFD_LAUNCH_SPLIT)
+    plan.solve_explicit(T(q.f), T(q.u0), dtq, 5, 0.0)
+    plan.set_wait(20.0, 1)
+    for solve in (lambda: plan.solve_explicit(T(q.f), T(q.u0), dtq, 100, 0.0),
+                  lambda: plan.solve_dc(T(q.f), T(q.u0), dtq, 0.0, 1, 50, 0.0)):
+        with pytest.raises(rb.RbffdError) as ei:
+            solve()
+        assert ei.value.code == rb.RBFFD_ERR_TIMEOUT
+    plan.set_wait(0.0, 0)
+    u = T(q.u0)
+    plan.solve_explicit(T(q.f), u, dtq, 100, 0.0)
+    assert np.max(np.abs(H(u) - qu)) <= 1e-12 * np.max(np.abs(qu))
+    assert plan.stats()[3][1] == -2
+    plan.destroy()
 
 
 def test_resident_launch_refuses_a_plan_too_large(rb):
@@ -700,13 +719,14 @@ def _share_inner_flags(p, perm, G):
 
 @pytest.mark.parametrize("Kg", [200, 300])
 def test_resident_shares_inner_rows_first(rb, orc, Kg):
-    """Morton plans that may take the resident launch put, in each SM's share of
-    the rows, the rows whose stencils stay inside the share first (each group in
-    Morton order); the resident launch computes those slices while it waits at
-    the step barrier.  40k- and 90k-node squares: the order's invariant (the same
-    set of inner rows as plain Morton order, now leading each share), then 300
-    FP64 sweeps and a defect correction in the resident launches (window and
-    L2, far lists, and the autotuner's pick) against the oracle."""
+    """Morton plans that may take the resident or split launch put, in each SM's
+    share of the rows, the rows whose stencils stay inside the share first (each
+    group in Morton order); those launches compute these slices while they wait
+    at the step barrier.  40k- and 90k-node squares: the order's invariant (the
+    same set of inner rows as plain Morton order, now leading each share), then
+    300 FP64 sweeps and a defect correction in the resident launches (window and
+    L2, far lists), the split launch and the autotuner's pick, against the
+    oracle."""
     p = build(orc, 2, Kg, 4, seed=67)
     G = torch.cuda.get_device_properties(0).multi_processor_count
     dt = _dt(orc, p)
@@ -717,7 +737,8 @@ def test_resident_shares_inner_rows_first(rb, orc, Kg):
     plain = _plan(rb, p, rb.RBFFD_LAUNCH_GRAPH)
     ref = _share_inner_flags(p, H(plain.perm()), G)
     plain.destroy()
-    for flags in (rb.RBFFD_LAUNCH_RESIDENT, rb.RBFFD_LAUNCH_FAR, rb.RBFFD_LAUNCH_AUTO):
+    for flags, kind in ((rb.RBFFD_LAUNCH_RESIDENT, -1), (rb.RBFFD_LAUNCH_FAR, -1),
+                        (rb.RBFFD_LAUNCH_SPLIT, -2), (rb.RBFFD_LAUNCH_AUTO, None)):
         plan = _plan(rb, p, flags)
         perm = H(plan.perm())
         assert np.array_equal(np.sort(perm), np.arange(p.N))
@@ -735,7 +756,7 @@ def test_resident_shares_inner_rows_first(rb, orc, Kg):
         code, outer, inner, res = plan.solve_dc(T(p.f), u2, *args)
         assert (outer, inner) == (oo, oi)
         assert np.max(np.abs(H(u2) - du)) <= 1e-12 * np.max(np.abs(du))
-        if flags != rb.RBFFD_LAUNCH_AUTO:
+        if kind is not None:
             shape = plan.stats()[3]
-            assert shape[1] == -1 and shape[3] == -1   # resident launch, both sweeps
+            assert shape[1] == kind and shape[3] == kind   # resident / split, both sweeps
         plan.destroy()

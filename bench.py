@@ -66,6 +66,8 @@ def _peaks():
 
 def _launch_label(per_sm: int) -> str:
     """The launch mode a plan's stats report (blocks-per-SM entry of its shape)."""
+    if per_sm == -2:
+        return "split"
     if per_sm < 0:
         return "resident"
     if per_sm == 0:
@@ -73,18 +75,22 @@ def _launch_label(per_sm: int) -> str:
     return "graph+pdl" if per_sm > 16 else "graph"
 
 
-def _traffic():
-    """ncu DRAM bytes per launch of the FP64 sweep, if captured for the current kernel source."""
+def _traffic(record: str):
+    """ncu DRAM bytes per sweep of the FP64 sweep kernel, from the record under
+    profiles/ (`record`), if it was captured for the current kernel sources (the
+    sha1 of the concatenated files it names)."""
     import hashlib
     try:
         rec = {}
-        for line in open(os.path.join(ROOT, "profiles", "sweep64_traffic.txt")):
+        for line in open(os.path.join(ROOT, "profiles", record)):
             if "=" in line and not line.startswith("#"):
                 k, v = line.split("=", 1)
                 rec[k.strip()] = v.strip()
-        src = os.path.join(ROOT, "paper_2502_12878_gb300", "csrc", "step.cuh")
-        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
-        if rec.get("kernel_source_sha1") == sha:
+        h = hashlib.sha1()
+        for name in rec.get("kernel_sources", "step.cuh").split(","):
+            with open(os.path.join(ROOT, "paper_2502_12878_gb300", "csrc", name.strip()), "rb") as fh:
+                h.update(fh.read())
+        if rec.get("kernel_source_sha1") == h.hexdigest():
             return int(rec["traffic_bytes_per_launch"])
     except Exception:
         pass
@@ -183,7 +189,9 @@ def build_gpu_problem(rb, torch, d, Kg, m, seed, dev):
     torch.cuda.synchronize()
     t["weights_ms"] = (time.perf_counter() - t0) * 1e3
     t0 = time.perf_counter()
-    plan = rb.Plan(xyz, bnd, inter, idx, w, rb.RBFFD_ORDER_MORTON)
+    # launch mode left to the autotuner (first solve): graph-replayed steps or
+    # a persistent launch (plain, resident or split)
+    plan = rb.Plan(xyz, bnd, inter, idx, w, rb.RBFFD_ORDER_MORTON | rb.RBFFD_LAUNCH_AUTO)
     torch.cuda.synchronize()
     t["plan_ms"] = (time.perf_counter() - t0) * 1e3
     # inputs of the test problem (Eq. 4-5) from the node coordinates
@@ -376,8 +384,8 @@ def c1_case(rb, torch, dev):
 
 def support_sweep_case(rb, torch, dev, hbm, fma_peak, ns=(12, 13, 16, 20, 24, 30, 40, 48, 56)):
     """m = 2 on the 1,002,001-node square with n = 12..56 (the support-size study):
-    FP64 node-updates/s and the fractions of HBM (streamed bytes) and of the FP64
-    pipe (n + 2 FP64 instructions per row) per n."""
+    FP64 node-updates/s in the autotuned launch mode and the fractions of HBM
+    (streamed bytes) and of the FP64 pipe (n + 2 FP64 instructions per row) per n."""
     xyz, bnd = rb.rbffd_nodes(2, 0, 1000, 0.3, 2, device=dev)
     inter = rb.rbffd_interior(bnd)
     NI = inter.numel()
@@ -388,10 +396,10 @@ def support_sweep_case(rb, torch, dev, hbm, fma_peak, ns=(12, 13, 16, 20, 24, 30
     for n in ns:
         idx = rb.rbffd_knn(xyz, inter, n)
         w, st = rb.rbffd_weights(xyz, idx, 2)
-        plan = rb.Plan(xyz, bnd, inter, idx, w)
+        plan = rb.Plan(xyz, bnd, inter, idx, w, rb.RBFFD_ORDER_MORTON | rb.RBFFD_LAUNCH_AUTO)
         del idx, w
         u = u0.clone()
-        plan.solve_explicit(f, u, 1e-9, 64, 0.0)
+        plan.solve_explicit(f, u, 1e-9, 64, 0.0)   # tunes the launch mode
         plan.solve_explicit(f, u, 1e-9, 200, 0.0)
         ms, k, nl, shape = plan.stats()
         per = ms * 1e-3 / k
@@ -399,7 +407,8 @@ def support_sweep_case(rb, torch, dev, hbm, fma_peak, ns=(12, 13, 16, 20, 24, 30
         rows[str(n)] = {"node_updates_per_s": NI / per, "alg_GBps": lay["bytes64"] / per / 1e9,
                         "frac_hbm": lay["bytes64"] / per / 1e9 / hbm,
                         "frac_fp64_pipe": NI * (n + 2) / per / fma_peak,
-                        "rows16_frac": lay["rows16"] / NI, "launch_shape": shape}
+                        "rows16_frac": lay["rows16"] / NI, "launch_shape": shape,
+                        "launch": _launch_label(shape[1])}
         plan.destroy()
     return rows
 
@@ -836,7 +845,8 @@ def run_stage(args):
         torch.cuda.synchronize()
         return
     launch = {"graph": rb.RBFFD_LAUNCH_GRAPH, "persistent": rb.RBFFD_LAUNCH_PERSISTENT,
-              "resident": rb.RBFFD_LAUNCH_RESIDENT, "auto": rb.RBFFD_LAUNCH_AUTO}[args.launch]
+              "resident": rb.RBFFD_LAUNCH_RESIDENT, "auto": rb.RBFFD_LAUNCH_AUTO,
+              "split": rb.RBFFD_LAUNCH_SPLIT, "far": rb.RBFFD_LAUNCH_FAR}[args.launch]
     plan = rb.Plan(xyz, bnd, inter, idx, w, rb.RBFFD_ORDER_MORTON | launch)
     f = torch.zeros(inter.numel(), dtype=torch.float64, device=dev)
     u = torch.zeros(xyz.shape[1], dtype=torch.float64, device=dev)
@@ -881,7 +891,7 @@ def main():
                          "print nothing), or fp64peak: the measured FP64 fma rate with the "
                          "clocks while it runs (one JSON line)")
     ap.add_argument("--launch", default="graph",
-                    choices=["graph", "persistent", "resident", "auto"],
+                    choices=["graph", "persistent", "resident", "auto", "split", "far"],
                     help="launch mode of the plan in --mode sweep/dc/adjoint")
     ap.add_argument("--m", type=int, default=M, help="monomial order of the workload")
     ap.add_argument("--Kg", type=int, default=KG, help="grid cells per side of the workload")
@@ -983,12 +993,29 @@ def main():
                                      f"{max_mhz} MHz (nominal FP64 1.25 TFLOP/s)",
                 "frac_of_derived": round(NI * (n + 2) / per_launch_s / fma_derived, 4)}
     # the binding resource is the one closer to its peak
-    if alu_frac > achieved / hbm:
-        roof = {"bound": "alu", **alu_part, "traffic": _traffic(), "hbm": hbm_part}
+    # the kernel the autotuner picked for the FP64 sweep (a persistent launch
+    # runs every sweep of a solve: its figures are per sweep)
+    shape = plan.stats()[3]
+    launch = _launch_label(shape[1])
+    if launch == "split":
+        kname = f"split_kernel<{n},0,{512 * shape[0]}>"
+        record = "split64_traffic.txt"
+    elif launch == "resident":
+        kname = f"resident_kernel<{n},0,...>"
+        record = None
+    elif launch == "persistent":
+        kname = f"persistent_kernel<{n},0,{shape[0]}>"
+        record = None
     else:
-        roof = {"bound": "hbm", **hbm_part, "traffic": _traffic(), "fp64_pipe": alu_part}
-    roof.update({"kernel": f"step_kernel<{n},0> (FP64 sweep)",
-                 "launch_us": round(per_launch_s * 1e6, 2)})
+        kname = f"step_kernel<{n},0,{shape[0]}>"
+        record = "sweep64_traffic.txt"
+    traffic = _traffic(record) if record else None
+    if alu_frac > achieved / hbm:
+        roof = {"bound": "alu", **alu_part, "traffic": traffic, "hbm": hbm_part}
+    else:
+        roof = {"bound": "hbm", **hbm_part, "traffic": traffic, "fp64_pipe": alu_part}
+    roof.update({"kernel": f"{kname} (FP64 sweep, {launch} launch)",
+                 "launch_us": round(per_launch_s * 1e6, 2), "per": "sweep"})
 
     # end to end through the same C-ABI call with host buffers
     f_h = f.cpu().pin_memory()
@@ -1052,7 +1079,9 @@ def main():
            "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": "2D unit square, 1,002,001 jittered nodes (998,001 interior), "
-                                  "m=4 (n=30), FP64 explicit sweeps, Morton-packed plan",
+                                  "m=4 (n=30), FP64 explicit sweeps, Morton-packed plan, "
+                                  "autotuned launch mode",
+                      "launch": launch,
                       "sweeps_per_step": SWEEPS, "dt": P["dt"],
                       "l2": f"inputs larger than L2 (packed stencils {alg_bytes / 1e6:.0f} MB "
                             f"streamed per sweep, L2 126 MB); no flush needed",

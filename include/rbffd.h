@@ -367,6 +367,15 @@ RBFFD_API int rbffd_plan_set_wait(rbffd_plan* plan, double timeout_ms, int held_
  * results bit for bit.  The launch shapes are tuned again on the next solve.
  */
 RBFFD_API int rbffd_plan_set_resident_halo(rbffd_plan* plan, int64_t halo);
+/*
+ * rbffd_plan_set_block - block size of the resident and split launches (one
+ * block per SM): 512 or 1024 threads (1024 only for the stencil sizes
+ * compiled with it; a size without it leaves that launch out), or 0: the
+ * autotuner times both (the default).  Every block size gives the same results
+ * bit for bit.  The launch shapes are tuned again on the next solve;
+ * RBFFD_ERR_ARG for any other value.
+ */
+RBFFD_API int rbffd_plan_set_block(rbffd_plan* plan, int threads);
 /* node permutation of the plan: perm [N] out, perm[p] = original index of slot p */
 RBFFD_API int rbffd_plan_perm(const rbffd_plan* plan, int32_t* perm, void* stream);
 

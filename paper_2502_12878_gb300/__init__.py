@@ -59,6 +59,7 @@ EXPORTED = [
     "rbffd_knn_masked", "rbffd_weights_dir", "rbffd_plan_set_neumann", "rbffd_plan_layout",
     "rbffd_nodes_pds", "rbffd_nodes_pds_cap", "rbffd_weights_batch", "rbffd_transpose",
     "rbffd_plan_set_wait", "rbffd_fp64_fma_rate", "rbffd_plan_set_resident_halo",
+    "rbffd_plan_set_block",
     "rbffd_transpose_layout",
 ]
 RBFFD_KNN_NOALLOC_MAX_NODES = 262144
@@ -126,6 +127,7 @@ def lib():
         "rbffd_plan_set_wait": (I, [P, D, I]),
         "rbffd_fp64_fma_rate": (I, [I64, PD, PD, P]),
         "rbffd_plan_set_resident_halo": (I, [P, I64]),
+        "rbffd_plan_set_block": (I, [P, I]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -473,6 +475,10 @@ class Plan:
     def set_resident_halo(self, halo=-2):
         """Halo reach of the resident launch (-1 none, >= 0 slots, -2 tuned)."""
         _check(lib().rbffd_plan_set_resident_halo(self.handle, int(halo)))
+
+    def set_block(self, threads=0):
+        """Block size of the resident and split launches (512, 1024; 0 tuned)."""
+        _check(lib().rbffd_plan_set_block(self.handle, int(threads)))
 
     def set_dc(self, K_in, rho_in):
         _check(lib().rbffd_plan_set_dc(self.handle, int(K_in), float(rho_in)))

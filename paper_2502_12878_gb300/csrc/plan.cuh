@@ -102,6 +102,7 @@ struct rbffd_plan {
     int32_t* fl_slot[2] = {nullptr, nullptr};
     int64_t res_halo[2] = {0, 0};       // and its halo reach (slots beyond a block's rows)
     int64_t res_halo_set = -2;          // a reach fixed by rbffd_plan_set_resident_halo (-2: tuned)
+    int res_threads_set = 0;            // block size fixed by rbffd_plan_set_block (0: tuned)
     int minb[2] = {2, 2};
     int per_sm[2] = {2, 2};
     float tune_ms[2] = {0.f, 0.f};

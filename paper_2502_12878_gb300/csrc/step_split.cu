@@ -1,7 +1,7 @@
 // Split persistent launch: the kernel instantiations for every compiled
-// stencil size (the kernel itself is in step_split.cuh), 512-thread blocks for
-// every size and 1024-thread blocks for n <= 31, and the shared-memory size
-// of a launch.
+// stencil size (the kernel itself is in step_split.cuh), 512- and 1024-thread
+// blocks (the generic size and n = 6: 512 only), and the shared-memory size of
+// a launch.
 #include "step_split.cuh"
 
 namespace rbffd {
@@ -19,6 +19,12 @@ static StepFn pick_split_m(int n) {
             RBFFD_SCASE(24)
             RBFFD_SCASE(30)
             RBFFD_SCASE(31)
+            RBFFD_SCASE(40)
+            RBFFD_SCASE(48)
+            RBFFD_SCASE(56)
+            RBFFD_SCASE(57)
+            RBFFD_SCASE(70)
+            RBFFD_SCASE(71)
             default: return nullptr;
         }
     } else {

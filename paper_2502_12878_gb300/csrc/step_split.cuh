@@ -80,8 +80,8 @@ __device__ __forceinline__ T split_row(const StepArgs& A, int64_t sl, int32_t ro
     const int64_t base = sl * (int64_t)A.n * SLICE + lane;
     const int4 sb = A.col16 ? __ldg(A.sbase + sl) : make_int4(-1, -1, -1, -1);
     // loads in flight per thread: fewer for the generic size and in the FP64
-    // 1024-thread blocks (64 registers), so nothing spills (12 fit for n = 30
-    // and 31, 8 for the smaller sizes: by the compiler's register report)
+    // 1024-thread blocks (64 registers), so nothing spills (12 fit from n = 30
+    // on, 8 for the smaller sizes: by the compiler's register report)
     constexpr int CH = NN == 0                                    ? 8
                        : !(MODE == MODE_SWEEP64 && TH >= 1024)    ? 16
                        : NN >= 30                                 ? 12
@@ -274,8 +274,8 @@ __global__ void __launch_bounds__(TH, 1) split_kernel(StepArgs A, StepCtrl* c) {
 }
 
 // kernel of the split launch for stencil size n, mode and block size (512, or
-// 1024 for n <= 31; nullptr otherwise), and its dynamic shared memory with
-// `grid` blocks
+// 1024 for the compiled sizes from 12 on; nullptr otherwise), and its dynamic
+// shared memory with `grid` blocks
 StepFn pick_split(int mode, int n, int threads);
 unsigned split_smem(int64_t nslices, int mode, int grid);
 

@@ -838,6 +838,7 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
         TuneCand t;
         int64_t hmax = 0;
         t.threads = wide ? RES_THREADS_WIDE : RES_THREADS_HOST;
+        if (p->res_threads_set && t.threads != p->res_threads_set) continue;
         t.far = false;
         t.split = false;
         t.fn = resident_fn(p, mode, t.threads, &t.smem, &hmax);
@@ -875,6 +876,7 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
         for (int wide = 0; wide < 2 && p->fl_ok[mi]; ++wide) {
             TuneCand t;
             t.threads = wide ? RES_THREADS_WIDE : RES_THREADS_HOST;
+            if (p->res_threads_set && t.threads != p->res_threads_set) continue;
             t.fn = pick_resident_far(mode, p->n, t.threads);
             if (!t.fn) continue;
             t.smem = resident_smem(p->nslices, p->n, mode, true, device_sm_count(),
@@ -913,6 +915,7 @@ static int tune_shape(rbffd_plan* p, int mode, cudaStream_t s) {
          ++wide) {
         TuneCand t;
         t.threads = wide ? RES_THREADS_WIDE : RES_THREADS_HOST;
+        if (p->res_threads_set && t.threads != p->res_threads_set) continue;
         t.fn = pick_split(mode, p->n, t.threads);
         if (!t.fn) continue;
         t.grid = device_sm_count();
@@ -1542,15 +1545,29 @@ extern "C" int rbffd_plan_set_dc(rbffd_plan* p, int64_t K_in, double rho_in) {
     return RBFFD_OK;
 }
 
+// the launch shapes are tuned again on the next solve
+static void retune(rbffd_plan* p) {
+    for (int mi = 0; mi < 2; ++mi) {
+        p->tuned[mi] = false;
+        p->persist[mi] = p->resident[mi] = p->split[mi] = false;
+    }
+    drop_graphs(p);
+}
+
 extern "C" int rbffd_plan_set_resident_halo(rbffd_plan* p, int64_t halo) {
     clear_error();
     RBFFD_ARG(p && halo >= -2, "rbffd_plan_set_resident_halo: bad argument");
     p->res_halo_set = halo;
-    for (int mi = 0; mi < 2; ++mi) {   // tune again on the next solve
-        p->tuned[mi] = false;
-        p->persist[mi] = p->resident[mi] = false;
-    }
-    drop_graphs(p);
+    retune(p);
+    return RBFFD_OK;
+}
+
+extern "C" int rbffd_plan_set_block(rbffd_plan* p, int threads) {
+    clear_error();
+    RBFFD_ARG(p && (threads == 0 || threads == RES_THREADS_HOST || threads == RES_THREADS_WIDE),
+              "rbffd_plan_set_block: threads must be 0, 512 or 1024");
+    p->res_threads_set = threads;
+    retune(p);
     return RBFFD_OK;
 }
 

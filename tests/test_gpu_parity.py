@@ -281,6 +281,48 @@ def test_sweep_parity_every_compiled_stencil_size(rb, orc, d, m, n):
     plan.destroy()
 
 
+@pytest.mark.parametrize("d,m,n", NN_CASES)
+def test_split_launch_every_compiled_stencil_size(rb, orc, d, m, n):
+    """The split persistent launch at each stencil size that has a kernel of its
+    own, in each block size it is compiled with (512; 1024 from n = 12 on): 50 FP64
+    sweeps and a defect correction (FP32 inner sweeps) against the oracle, on plans
+    of at least two slices per SM (11,881 interior rows in 2D, 12,167 in 3D)."""
+    p = build(orc, d, 110 if d == 2 else 24, m, seed=57, n=n)
+    G = torch.cuda.get_device_properties(0).multi_processor_count
+    assert (p.NI + 31) // 32 >= 2 * G
+    dt = _dt(orc, p)
+    K = 50
+    ou, os_, ores, _ = orc.solve_explicit(p.w, p.idx, p.interior, p.f, p.u0, dt, K, 0.0)
+    args = (dt, 1e-7, 2, 60, 1e-3)
+    du, oo, oi, _, _ = orc.solve_dc(p.w, p.idx, p.interior, p.f, p.u0, *args)
+    for threads in ((512,) if n < 12 else (512, 1024)):
+        plan = _plan(rb, p, rb.RBFFD_LAUNCH_SPLIT)
+        plan.set_block(threads)
+        u = T(p.u0)
+        code, steps, res = plan.solve_explicit(T(p.f), u, dt, K, 0.0)
+        assert steps == os_ == K
+        assert np.max(np.abs(H(u) - ou)) <= 1e-12 * np.max(np.abs(ou)), (n, threads)
+        assert res == pytest.approx(ores, rel=1e-12)
+        u2 = T(p.u0)
+        code, outer, inner, res = plan.solve_dc(T(p.f), u2, *args)
+        assert (outer, inner) == (oo, oi)
+        assert np.max(np.abs(H(u2) - du)) <= 1e-12 * np.max(np.abs(du)), (n, threads)
+        shape = plan.stats()[3]
+        assert shape[1] == shape[3] == -2 and shape[0] == shape[2] == threads // 512
+        plan.destroy()
+
+
+def test_plan_set_block_rejects_other_sizes(rb, orc):
+    p = build(orc, 2, 20, 2, seed=58)
+    plan = _plan(rb, p, rb.RBFFD_LAUNCH_AUTO)
+    for bad in (-1, 256, 768, 2048):
+        with pytest.raises(rb.RbffdError) as ei:
+            plan.set_block(bad)
+        assert ei.value.code == rb.RBFFD_ERR_ARG
+    plan.set_block(0)
+    plan.destroy()
+
+
 def test_sweep_stop_rule_matches(rb, orc):
     p = build(orc, 2, 24, 2, seed=42)
     dt = _dt(orc, p)

@@ -283,7 +283,7 @@ def run_reference(args):
 
 
 def _gpu_problem_from_nodes(rb, torch, xyz, bnd, m, dev, power_iters=200, inter=None, idx=None,
-                            w=None):
+                            w=None, flags=0):
     d = xyz.shape[0]
     n = gen.stencil_size(d, m)
     if inter is None:
@@ -292,7 +292,7 @@ def _gpu_problem_from_nodes(rb, torch, xyz, bnd, m, dev, power_iters=200, inter=
         idx = rb.rbffd_knn(xyz, inter, n)
     if w is None:
         w, st = rb.rbffd_weights(xyz, idx, m)
-    plan = rb.Plan(xyz, bnd, inter, idx, w, rb.RBFFD_ORDER_MORTON)
+    plan = rb.Plan(xyz, bnd, inter, idx, w, rb.RBFFD_ORDER_MORTON | flags)
     xyz_h, bnd_h, inter_h = xyz.cpu().numpy(), bnd.cpu().numpy(), inter.cpu().numpy()
     f = torch.from_numpy(gen.source(xyz_h, inter_h)).to(dev)
     u0 = torch.from_numpy(gen.start_iterate(xyz_h, bnd_h)).to(dev)
@@ -575,7 +575,8 @@ def run_workload(args):
 
     if args.workload == "adjoint1M_m4":
         xyz, bnd = rb.rbffd_nodes(2, 0, 1000, 0.3, 5, device=dev)
-        Q = _gpu_problem_from_nodes(rb, torch, xyz, bnd, 4, dev)
+        # launch modes of the forward sweeps and of the reverse sweep autotuned
+        Q = _gpu_problem_from_nodes(rb, torch, xyz, bnd, 4, dev, flags=rb.RBFFD_LAUNCH_AUTO)
         plan, NI, N, dt = Q["plan"], Q["NI"], Q["N"], Q["dt"]
         K = 5000
         sens = torch.from_numpy(gen.sensors(NI, 10000, 5).astype(np.int64)).to(dev)

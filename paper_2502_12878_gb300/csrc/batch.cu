@@ -59,7 +59,7 @@ struct DomCall {           // per-call part
 
 struct DomState {          // per-domain control, written by the kernel
     unsigned long long res[3];
-    unsigned int bar_count, bar_gen;
+    unsigned long long arrivals;   // team barrier: block arrivals since the solve started
     long long k;
     int done, pad;
     double res_first, res_last;
@@ -237,40 +237,56 @@ __device__ unsigned long long bstep_any(const DomDesc& D, int par, double dt, in
     }
 }
 
-// per-domain barrier over the team's blocks; false when a wait gave up
-__device__ bool team_sync_global(DomState* st, int size) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned* genp = &st->bar_gen;
-        unsigned g = *genp;
-        int ok = 1;
-        __threadfence();
-        unsigned t = atomicAdd(&st->bar_count, 1u);
-        if (t == (unsigned)size - 1) {
-            atomicExch(&st->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&st->bar_gen, 1u);
-        } else {
-            long long t0 = clock64();
-            while (*genp == g) {
-                if (clock64() - t0 > BATCH_SPIN_CYCLES) {
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-        s_ok = ok;
+// release / acquire accesses at GPU scope for the team barrier
+__device__ __forceinline__ void bred_max(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.relaxed.gpu.global.max.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void bred_add_release(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long bld_acquire(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long bld_relaxed(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// the stop rule for step kk with residual R (R0: step 0's), in thread 0;
+// rank 0 of the team records a stop in the domain's state
+__device__ __forceinline__ int bdecide(DomState* st, const DomCall& C, int rank, long long kk,
+                                       double R, double* R0) {
+    if (kk == 0) *R0 = R;
+    int dn;
+    if (!isfinite(R)) dn = DONE_NONFINITE;
+    else if (R < C.tol) dn = DONE_CONVERGED;
+    else if (kk > 0 && *R0 > 0.0 && R > 1e6 * *R0) dn = DONE_DIVERGED;
+    else if (kk + 1 >= C.max_steps) dn = DONE_CAP;
+    else dn = DONE_RUNNING;
+    if (rank == 0 && dn != DONE_RUNNING) {
+        st->k = kk + 1;
+        st->res_first = *R0;
+        st->res_last = R;
+        st->done = dn;
+        st->t_end = gtimer();
     }
-    __syncthreads();
-    return s_ok != 0;
+    return dn;
 }
 
 // one domain's solve by one team member (rank of size blocks); returns false
 // when a team wait gave up.  CH: neighbours per load phase (8 where the
-// register budget is below 80 per thread).
+// register budget is below 80 per thread).  A one-block team decides right
+// after each step (its residual is the block's).  Larger teams end a step
+// with a counter barrier (each block adds its max |r| to the step's residual
+// slot and its arrival to the domain's counter - both fire-and-forget, the
+// arrival a release - and polls the counter, bounded), load the step's full
+// residual right after it and apply the stop rule to it after their next
+// step: the same rule to the same value in every member, so the team stops
+// together.  A stop wastes that next step, which writes the other buffer; the
+// result u^{k+1} is untouched.  Rank 0 clears the slot step k + 2 will use.
 template <int CH>
 __device__ bool run_domain(const TeamDesc T, const DomDesc* __restrict__ desc,
                            const DomCall* __restrict__ call, DomState* state,
@@ -283,6 +299,8 @@ __device__ bool run_domain(const TeamDesc T, const DomDesc* __restrict__ desc,
     const int64_t s0 = (int64_t)T.rank * nw + wid;
     const int64_t stride = (int64_t)T.size * nw;
     double R0 = 0.0;
+    unsigned long long pend = 0ull;   // thread 0: the last barrier's step residual
+    bool decided = false;
     if (threadIdx.x == 0 && T.rank == 0) st->t_start = gtimer();
     for (long long k = 0; k < C.max_steps; ++k) {
         unsigned long long m = T.size == 1
@@ -292,44 +310,49 @@ __device__ bool run_domain(const TeamDesc T, const DomDesc* __restrict__ desc,
         for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
         if (lane == 0) wmax[wid] = m;
         __syncthreads();
-        unsigned long long bm = 0;
-        if (threadIdx.x == 0)
-            for (int w = 0; w < nw; ++w) bm = max(bm, wmax[w]);
-        double R;
-        if (T.size == 1) {
-            R = __longlong_as_double((long long)bm);
-        } else {
-            if (threadIdx.x == 0) {
-                atomicMax(&st->res[k % 3], bm);
-                if (T.rank == 0) atomicExch(&st->res[(k + 1) % 3], 0ull);
-            }
-            if (!team_sync_global(st, T.size)) {
-                if (threadIdx.x == 0) atomicExch(&st->done, DONE_TIMEOUT);
-                return false;
-            }
-            volatile unsigned long long* rp = &st->res[k % 3];
-            R = __longlong_as_double((long long)*rp);
+        if (wid == 0) {
+            m = lane < nw ? wmax[lane] : 0ull;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
         }
         if (threadIdx.x == 0) {
-            if (k == 0) R0 = R;
-            int dn;
-            if (!isfinite(R)) dn = DONE_NONFINITE;
-            else if (R < C.tol) dn = DONE_CONVERGED;
-            else if (k > 0 && R0 > 0.0 && R > 1e6 * R0) dn = DONE_DIVERGED;
-            else if (k + 1 >= C.max_steps) dn = DONE_CAP;
-            else dn = DONE_RUNNING;
-            *s_stop = dn;
-            if (T.rank == 0 && dn != DONE_RUNNING) {
-                st->k = k + 1;
-                st->res_first = R0;
-                st->res_last = R;
-                st->done = dn;
-                st->t_end = gtimer();
+            int dn = DONE_RUNNING;
+            if (T.size == 1) {
+                dn = bdecide(st, C, T.rank, k, __longlong_as_double((long long)m), &R0);
+            } else {
+                if (k > 0) dn = bdecide(st, C, T.rank, k - 1, __longlong_as_double((long long)pend),
+                                        &R0);
+                if (dn == DONE_RUNNING) {
+                    bred_max(&st->res[k % 3], m);
+                    bred_add_release(&st->arrivals, 1ull);
+                    const unsigned long long target = (unsigned long long)(k + 1) * T.size;
+                    const long long t0 = clock64();
+                    while (bld_acquire(&st->arrivals) < target)
+                        if (clock64() - t0 > BATCH_SPIN_CYCLES) {
+                            atomicExch(&st->done, DONE_TIMEOUT);
+                            dn = -1;
+                            break;
+                        }
+                    if (dn == DONE_RUNNING) {
+                        if (T.rank == 0) atomicExch(&st->res[(k + 2) % 3], 0ull);
+                        pend = bld_relaxed(&st->res[k % 3]);
+                    }
+                }
             }
+            *s_stop = dn;
         }
         __syncthreads();
-        if (*s_stop != DONE_RUNNING) break;
+        const int dn = *s_stop;
+        __syncthreads();   // every thread has read it before thread 0 writes the next
+        if (dn == -1) return false;
+        if (dn != DONE_RUNNING) {
+            decided = true;
+            break;
+        }
     }
+    // a larger team's last step (the cap): its rule, from the residual of its barrier
+    if (!decided && T.size > 1 && C.max_steps > 0 && threadIdx.x == 0)
+        bdecide(st, C, T.rank, C.max_steps - 1, __longlong_as_double((long long)pend), &R0);
     __syncthreads();
     return true;
 }
@@ -362,7 +385,7 @@ __global__ void batch_gather(const DomDesc* desc, const DomCall* call, DomState*
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             DomState& s = state[dI];
             s.res[0] = s.res[1] = s.res[2] = 0ull;
-            s.bar_count = s.bar_gen = 0u;
+            s.arrivals = 0ull;
             s.k = 0;
             s.done = C.max_steps <= 0 ? DONE_CAP : DONE_RUNNING;
             s.res_first = s.res_last = 0.0;

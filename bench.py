@@ -673,23 +673,23 @@ def run_workload(args):
             cpu = {"value": cpu_ms, "unit": "ms (node placement)", "cores": 1, "kind": "oracle",
                    "sample": f"the whole sequential walk, {oxyz.shape[1]} nodes",
                    "bit_equal_to_gpu": bool(np.array_equal(oxyz, xyz.cpu().numpy()))}
-        Q = _gpu_problem_from_nodes(rb, torch, xyz, bnd, 4, dev)
+        Q = _gpu_problem_from_nodes(rb, torch, xyz, bnd, 4, dev, flags=rb.RBFFD_LAUNCH_AUTO)
         plan, f, u0, NI = Q["plan"], Q["f"], Q["u0"], Q["NI"]
         u = u0.clone()
-        plan.solve_explicit(f, u, Q["dt"], 64, 0.0)
+        plan.solve_explicit(f, u, Q["dt"], 64, 0.0)   # tunes the launch mode
         S = 200
         plan.solve_explicit(f, u, Q["dt"], S, 0.0)
         ms, k, nl, shape = plan.stats()
         per = ms * 1e-3 / k
         lay = plan.layout()
         _line(f"Poisson-disc nodes (Sec. II-C): 2D unit square, h = 1/{Kg}, {Q['N']:,} nodes "
-              f"({NI:,} interior), m=4 (n=30), FP64 sweeps, Morton-packed plan",
+              f"({NI:,} interior), m=4 (n=30), FP64 sweeps, Morton-packed plan, autotuned launch",
               NI / per, UNIT, per * 1e3 * S, S, 64,
               {"node_placement_gpu_ms": gen_ms, "generations": rounds,
                "alg_GBps": lay["bytes64"] / per / 1e9,
                "frac_hbm": lay["bytes64"] / per / 1e9 / hbm,
                "rows16_frac": lay["rows16"] / NI, "rho_h2": Q["rho"] / Kg ** 2,
-               "launch_shape": shape, "cpu_baseline": cpu})
+               "launch_shape": shape, "launch": _launch_label(shape[1]), "cpu_baseline": cpu})
         plan.destroy()
         return
 

@@ -306,22 +306,31 @@ RBFFD_API int rbffd_fp64_fma_rate(int64_t iters, double* h_fma_per_s, double* h_
  * (a slice whose supports need more windows keeps 32-bit indices); the codes
  * name the same neighbours, so the results are the same bit for bit.
  * Launch mode of the step loops: RBFFD_LAUNCH_GRAPH (default), _PERSISTENT,
- * _RESIDENT, or _AUTO, where the first solve of each arithmetic (FP64 sweep,
- * FP32 inner sweep) times the graph shapes, the persistent launch and (when
- * it fits) the resident launch on the plan's own stencils and keeps the
- * fastest.  The resident launch is a persistent launch of one block per SM
+ * _RESIDENT, _FAR, _SPLIT, or _AUTO, where the first solve of each
+ * arithmetic (FP64 sweep, FP32 inner sweep) times the graph shapes, the
+ * persistent launches and (when they fit) the resident and split launches
+ * on the plan's own stencils and keeps the fastest (_PERSISTENT times the
+ * grid-stride and split launches).  The split launch is a persistent launch
+ * of one block per SM over a contiguous share of the slices: the stencils
+ * stream from HBM every step, the share's rows' iterate stays in shared
+ * memory (two buffers: 16 bytes a row in FP64, so up to about 2.2M interior
+ * rows), and the share's leading slices of rows whose supports lie inside
+ * it are computed while the block waits for the other SMs at the step
+ * barrier; a _SPLIT plan that cannot take it returns RBFFD_ERR_CAPACITY from
+ * its first solve.  The resident launch is a persistent launch of one block per SM
  * whose slices' weight and index planes (and their rows' f) are copied into
  * shared memory once per solve by TMA bulk copies, so each step reads only
  * the iterate; it fits while the plan's share per SM does (about 102,000
  * interior rows at n = 30 in FP64 with 16-bit codes, 175,000 for the FP32
  * inner sweep); a _RESIDENT plan that does not fit returns
- * RBFFD_ERR_CAPACITY from its first solve.  A Morton plan created with
- * _RESIDENT, _FAR or _AUTO whose planes could fit (and whose share per SM
- * is at least two slices) orders each share's rows with the rows whose
- * supports lie inside the share first, each group in Morton order; the
- * resident launch computes those while it waits for the other SMs at the
- * step barrier.  A plan with Neumann nodes always replays graphs.  Every
- * mode gives the same results bit for bit.
+ * RBFFD_ERR_CAPACITY from its first solve.  A Morton plan created with a
+ * flag that allows the resident or split launch, whose share per SM is at
+ * least two slices and fits one of them, orders each share's rows with the
+ * rows whose supports lie inside the share first, each group in Morton
+ * order (the plan's slot order; rbffd_plan_perm reports it); those launches
+ * compute these rows while they wait for the other SMs at the step barrier.
+ * A plan with Neumann nodes always replays graphs.  Every mode gives the same
+ * results bit for bit.
  */
 RBFFD_API int rbffd_plan_create(const double* xyz, const uint8_t* is_bnd, int64_t N, int d,
                       const int32_t* interior, const int32_t* idx, const double* w, int64_t NI,

@@ -1291,33 +1291,93 @@ static bool inner_first_applies(const rbffd_plan* p, int flags) {
            split_smem(p->nslices, MODE_INNER32, G) + 1024u <= (unsigned)optin;
 }
 
-// the reordered perm (slot -> node) from the packed neighbour slots `col`,
-// and per share the number of its leading slices that hold inner rows only
-static void inner_first_perm(const rbffd_plan* p, const std::vector<int32_t>& col,
-                             std::vector<int32_t>& perm, std::vector<int32_t>& inner_sl) {
-    const int G = device_sm_count();
-    const int64_t nsl = p->nslices, NI = p->NI;
-    const int n = p->n;
-    std::vector<int32_t> inner, other;
-    inner_sl.assign(G, 0);
-    for (int b = 0; b < G; ++b) {
-        const int64_t r0 = nsl * b / G * SLICE;
-        const int64_t r1 = std::min<int64_t>(nsl * (b + 1) / G * SLICE, NI);
-        inner.clear();
-        other.clear();
-        for (int64_t r = r0; r < r1; ++r) {
-            const int64_t base = (r / SLICE) * n * SLICE + r % SLICE;
-            bool in = true;
-            for (int j = 0; j < n && in; ++j) {
-                const int32_t c = col[base + (int64_t)j * SLICE];
-                in = c >= r0 && c < r1;
-            }
-            (in ? inner : other).push_back(perm[r]);
+// the share (block of G) that owns slice sl: nsl b / G <= sl < nsl (b+1) / G
+__device__ __forceinline__ int share_of(int64_t sl, int64_t nsl, int G) {
+    int64_t b = sl * G / nsl;
+    while (b > 0 && nsl * b / G > sl) --b;
+    while (b + 1 < G && nsl * (b + 1) / G <= sl) ++b;
+    return (int)b;
+}
+
+// per interior slot: 1 when every neighbour slot of its row lies in its share
+__global__ void share_inner_flags(const int32_t* __restrict__ col, int64_t NI, int64_t nsl, int n,
+                                  int G, uint8_t* __restrict__ flag) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < NI;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t sl = r / SLICE;
+        const int b = share_of(sl, nsl, G);
+        const int64_t c0 = nsl * b / G * SLICE;
+        const int64_t c1e = nsl * (b + 1) / G * SLICE;
+        const int64_t c1 = c1e < NI ? c1e : NI;
+        const int64_t base = sl * n * SLICE + r % SLICE;
+        bool in = true;
+        for (int j = 0; j < n && in; ++j) {
+            const int32_t c = col[base + (int64_t)j * SLICE];
+            in = c >= c0 && c < c1;
         }
-        std::copy(inner.begin(), inner.end(), perm.begin() + r0);
-        std::copy(other.begin(), other.end(), perm.begin() + r0 + (int64_t)inner.size());
-        inner_sl[b] = (int32_t)(inner.size() / SLICE);
+        flag[r] = in ? 1 : 0;
     }
+}
+
+// One block per share: the share's slots of perm_in in a stable partition,
+// inner rows first, written to perm_out; inner_sl[b] = its leading slices of
+// inner rows only.  Block size 1024 (32 warps).
+__global__ void __launch_bounds__(1024) share_partition(const uint8_t* __restrict__ flag,
+                                                         const int32_t* __restrict__ perm_in,
+                                                         int32_t* __restrict__ perm_out,
+                                                         int64_t NI, int64_t nsl, int G,
+                                                         int32_t* __restrict__ inner_sl) {
+    __shared__ int s_wi[32], s_wo[32];
+    __shared__ int s_total;
+    const int b = blockIdx.x;
+    const int64_t r0 = nsl * b / G * SLICE;
+    const int64_t r1e = nsl * (b + 1) / G * SLICE;
+    const int64_t r1 = r1e < NI ? r1e : NI;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // the share's inner rows
+    int cnt = 0;
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) cnt += flag[r];
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    if (lane == 0) s_wi[wid] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_wi[w];
+        s_total = t;
+    }
+    __syncthreads();
+    const int64_t ninner = s_total;
+    // each chunk of blockDim slots in order: ranks among the chunk's inner and
+    // other rows by warp ballots, then the warps' offsets
+    int64_t run_i = 0, run_o = 0;
+    const unsigned below = (1u << lane) - 1u;
+    for (int64_t c = r0; c < r1; c += blockDim.x) {
+        const int64_t r = c + threadIdx.x;
+        const bool valid = r < r1;
+        const bool f = valid && flag[r];
+        const unsigned bi = __ballot_sync(0xffffffffu, f);
+        const unsigned bo = __ballot_sync(0xffffffffu, valid && !f);
+        __syncthreads();   // the previous chunk's offsets are read
+        if (lane == 0) {
+            s_wi[wid] = __popc(bi);
+            s_wo[wid] = __popc(bo);
+        }
+        __syncthreads();
+        int oi = 0, oo = 0, ti = 0, to = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            if (w < wid) {
+                oi += s_wi[w];
+                oo += s_wo[w];
+            }
+            ti += s_wi[w];
+            to += s_wo[w];
+        }
+        if (f) perm_out[r0 + run_i + oi + __popc(bi & below)] = perm_in[r];
+        else if (valid) perm_out[r0 + ninner + run_o + oo + __popc(bo & below)] = perm_in[r];
+        run_i += ti;
+        run_o += to;
+    }
+    if (threadIdx.x == 0) inner_sl[b] = (int32_t)(ninner / SLICE);
 }
 
 extern "C" int rbffd_plan_create(const double* xyz, const uint8_t* is_bnd, int64_t N, int d,
@@ -1450,24 +1510,18 @@ extern "C" int rbffd_plan_create(const double* xyz, const uint8_t* is_bnd, int64
             break;
         }
         if (inner_first_applies(p, flags)) {
-            std::vector<int32_t> col(ell), perm(N);
-            if ((e = cudaMemcpyAsync(col.data(), p->col, sizeof(int32_t) * ell,
-                                     cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-                (e = cudaMemcpyAsync(perm.data(), p->perm, sizeof(int32_t) * N,
-                                     cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-                (e = cudaStreamSynchronize(s)) != cudaSuccess)
-                break;
-            std::vector<int32_t> inner_sl;
-            inner_first_perm(p, col, perm, inner_sl);
-            p->inner_first = true;
-            if ((e = cudaMemcpyAsync(p->perm, perm.data(), sizeof(int32_t) * N,
-                                     cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-                (e = cudaMalloc((void**)&p->inner_sl, sizeof(int32_t) * inner_sl.size())) !=
-                    cudaSuccess ||
-                (e = cudaMemcpyAsync(p->inner_sl, inner_sl.data(),
-                                     sizeof(int32_t) * inner_sl.size(), cudaMemcpyHostToDevice,
+            // on the device: each row's flag, then per share a stable partition
+            // of its slots (perm copied to `key` first)
+            Scratch fl;
+            if ((e = fl.alloc(NI, s)) != cudaSuccess) break;
+            if ((e = cudaMalloc((void**)&p->inner_sl, sizeof(int32_t) * sms)) != cudaSuccess) break;
+            share_inner_flags<<<G, 256, 0, s>>>(p->col, NI, p->nslices, n, sms, fl.as<uint8_t>());
+            if ((e = cudaMemcpyAsync(key.p, p->perm, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice,
                                      s)) != cudaSuccess)
                 break;
+            share_partition<<<sms, 1024, 0, s>>>(fl.as<uint8_t>(), key.as<int32_t>(), p->perm, NI,
+                                                 p->nslices, sms, p->inner_sl);
+            p->inner_first = true;
             invert_perm<<<G, 256, 0, s>>>(p->perm, N, p->inv);
             if ((e = cudaMemsetAsync(p->row_of_slot, 0xff, sizeof(int32_t) * NI, s)) !=
                 cudaSuccess)

@@ -777,13 +777,21 @@ def test_resident_shares_inner_rows_first(rb, orc, Kg):
     args = (dt, 1e-7, 3, 400, 1e-3)
     du, oo, oi, _, _ = orc.solve_dc(p.w, p.idx, p.interior, p.f, p.u0, *args)
     plain = _plan(rb, p, rb.RBFFD_LAUNCH_GRAPH)
-    ref = _share_inner_flags(p, H(plain.perm()), G)
+    pperm = H(plain.perm())
+    ref = _share_inner_flags(p, pperm, G)
     plain.destroy()
+    # the expected order: per share, plain Morton order's inner rows, then the others
+    nsl = (p.NI + 31) // 32
+    expect = pperm.copy()
+    for b, fl in enumerate(ref):
+        r0, r1 = nsl * b // G * 32, min(nsl * (b + 1) // G * 32, p.NI)
+        seg = pperm[r0:r1]
+        expect[r0:r1] = np.concatenate([seg[fl], seg[~fl]])
     for flags, kind in ((rb.RBFFD_LAUNCH_RESIDENT, -1), (rb.RBFFD_LAUNCH_FAR, -1),
                         (rb.RBFFD_LAUNCH_SPLIT, -2), (rb.RBFFD_LAUNCH_AUTO, None)):
         plan = _plan(rb, p, flags)
         perm = H(plan.perm())
-        assert np.array_equal(np.sort(perm), np.arange(p.N))
+        assert np.array_equal(perm, expect)              # stable: each group in Morton order
         flags_b = _share_inner_flags(p, perm, G)
         for a, b in zip(ref, flags_b):
             assert a.sum() == b.sum()                       # the same inner rows

@@ -36,6 +36,7 @@ struct Transpose {
     int64_t nslices = 0;      // over all N columns (placed order)
     AdjStepFn step = nullptr; // the reverse-step shape the tuner picked (on first use)
     unsigned step_grid = 0;   // and its grid
+    bool step_pdl = false;    // and whether consecutive steps are programmatic dependent launches
     int64_t* off = nullptr;   // [nslices + 1] element offset of each slice
     int32_t* len = nullptr;   // [nslices] padded length of each slice
     int32_t* row = nullptr;   // placed position of each entry's row
@@ -417,13 +418,19 @@ __device__ __forceinline__ void adj_slices(const Transpose& T, const int64_t NI,
     }
 }
 
+// As a programmatic dependent launch (the tuner's choice in rbffd_adjoint's
+// step loop) a step waits for the previous step before its first read of
+// lambda, and lets the next step's blocks be scheduled as its own blocks
+// finish their slices; both are no-ops in a plain launch.
 template <int CH, int MINB>
 __global__ void __launch_bounds__(256, MINB)
 adjoint_step(const Transpose T, const int64_t NI, const double dt,
              const double* __restrict__ lam, double* __restrict__ lam_out,
              double* __restrict__ S) {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if (T.row16) adj_slices<CH, true>(T, NI, dt, lam, lam_out, S);
     else adj_slices<CH, false>(T, NI, dt, lam, lam_out, S);
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // boundary columns: grad_g[node] = dt * sum_rows w_rc S_r + dLdu[node] (the
@@ -569,6 +576,26 @@ static const AdjStepFn adj_shapes[] = {adjoint_step<8, 4>,  adjoint_step<7, 4>,
                                        adjoint_step<16, 2>, adjoint_step<8, 3>};
 static constexpr int N_ADJ_SHAPES = 6;
 
+// one reverse step; `pdl`: as a programmatic dependent launch
+static cudaError_t adj_launch(AdjStepFn fn, unsigned grid, bool pdl, cudaStream_t s,
+                              const Transpose& T, int64_t NI, double dt, const double* lam,
+                              double* lam_out, double* S) {
+    if (!pdl) {
+        fn<<<grid, 256, 0, s>>>(T, NI, dt, lam, lam_out, S);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(256);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fn, T, NI, dt, lam, lam_out, S);
+}
+
 static unsigned adj_grid(const rbffd_plan* p) {
     const int64_t nsl_int = (p->NI + SLICE - 1) / SLICE;
     return (unsigned)std::max<int64_t>(1, (nsl_int + 7) / 8);
@@ -582,19 +609,28 @@ static int tune_adjoint(rbffd_plan* p, cudaStream_t s) {
     if (T.step) return RBFFD_OK;
     const int64_t NI = p->NI;
     const int sms = device_sm_count();
-    AdjStepFn cf[2 * N_ADJ_SHAPES];
-    unsigned cg[2 * N_ADJ_SHAPES];
+    // shapes x (the full grid, the resident grid) x (plain, programmatic
+    // dependent launches; RBFFD_LAUNCH_PDL / _NO_PDL fix that choice)
+    AdjStepFn cf[4 * N_ADJ_SHAPES];
+    unsigned cg[4 * N_ADJ_SHAPES];
+    bool cp[4 * N_ADJ_SHAPES];
     int nc = 0;
+    const int pdl_lo = (p->flags & RBFFD_LAUNCH_PDL) ? 1 : 0;
+    const int pdl_hi = (p->flags & RBFFD_LAUNCH_NO_PDL) ? 1 : 2;
     for (int c = 0; c < N_ADJ_SHAPES; ++c) {
         int per_sm = 0;
         RBFFD_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
             &per_sm, (const void*)adj_shapes[c], 256, 0));
-        cf[nc] = adj_shapes[c];
-        cg[nc++] = adj_grid(p);
         const unsigned res = (unsigned)(sms * std::max(1, per_sm));
-        if (res < adj_grid(p)) {
+        for (int pdl = pdl_lo; pdl < pdl_hi; ++pdl) {
             cf[nc] = adj_shapes[c];
-            cg[nc++] = res;
+            cg[nc] = adj_grid(p);
+            cp[nc++] = pdl != 0;
+            if (res < adj_grid(p)) {
+                cf[nc] = adj_shapes[c];
+                cg[nc] = res;
+                cp[nc++] = pdl != 0;
+            }
         }
     }
     RBFFD_CHECK_CUDA(cudaMemsetAsync(T.lam[0], 0, sizeof(double) * NI, s));
@@ -604,16 +640,17 @@ static int tune_adjoint(rbffd_plan* p, cudaStream_t s) {
     cudaEvent_t e0, e1;
     RBFFD_CHECK_CUDA(cudaEventCreate(&e0));
     RBFFD_CHECK_CUDA(cudaEventCreate(&e1));
-    float best[2 * N_ADJ_SHAPES];
+    float best[4 * N_ADJ_SHAPES];
     for (float& b : best) b = 1e30f;
     cudaError_t e = cudaSuccess;
     for (int round = 0; round < 4 && e == cudaSuccess; ++round)
         for (int c = 0; c < nc && e == cudaSuccess; ++c) {
             cudaEventRecord(e0, s);
-            for (int k = 0; k < reps; ++k)
-                cf[c]<<<cg[c], 256, 0, s>>>(T, NI, 0.0, T.lam[k & 1], T.lam[(k + 1) & 1], T.S);
+            for (int k = 0; k < reps && e == cudaSuccess; ++k)
+                e = adj_launch(cf[c], cg[c], cp[c], s, T, NI, 0.0, T.lam[k & 1],
+                               T.lam[(k + 1) & 1], T.S);
             cudaEventRecord(e1, s);
-            e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             if (e == cudaSuccess) e = cudaGetLastError();
             float ms = 0.f;
             if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
@@ -627,6 +664,7 @@ static int tune_adjoint(rbffd_plan* p, cudaStream_t s) {
         if (best[c] < best[bi]) bi = c;
     T.step = cf[bi];
     T.step_grid = cg[bi];
+    T.step_pdl = cp[bi];
     return RBFFD_OK;
 }
 
@@ -773,8 +811,8 @@ extern "C" int rbffd_adjoint(rbffd_plan* p, const double* dLdu, int64_t K, doubl
     adj_gather_placed<<<G, 256, 0, s>>>(dLdu, p->perm, T.colof, p->NI, T.lam[0]);
     RBFFD_CHECK_CUDA(cudaMemsetAsync(T.S, 0, sizeof(double) * p->NI, s));
     for (int64_t k = 0; k < K; ++k)
-        T.step<<<T.step_grid, 256, 0, s>>>(T, p->NI, dt, T.lam[k & 1], T.lam[(k + 1) & 1], T.S);
-    RBFFD_CHECK_CUDA(cudaGetLastError());
+        RBFFD_CHECK_CUDA(adj_launch(T.step, T.step_grid, T.step_pdl && k > 0, s, T, p->NI, dt,
+                                    T.lam[k & 1], T.lam[(k + 1) & 1], T.S));
     adjoint_grad_g<<<G, 256, 0, s>>>(T, p->NI, p->N, dt, T.S, p->perm, dLdu, grad_g);
     adj_outputs<<<G, 256, 0, s>>>(T.S, T.lam[K & 1], p->row_of_slot, T.colof, p->perm, p->NI,
                                   dt, grad_f,

@@ -284,9 +284,10 @@ def test_sweep_parity_every_compiled_stencil_size(rb, orc, d, m, n):
 @pytest.mark.parametrize("d,m,n", NN_CASES)
 def test_split_launch_every_compiled_stencil_size(rb, orc, d, m, n):
     """The split persistent launch at each stencil size that has a kernel of its
-    own, in each block size it is compiled with (512; 1024 from n = 12 on): 50 FP64
-    sweeps and a defect correction (FP32 inner sweeps) against the oracle, on plans
-    of at least two slices per SM (11,881 interior rows in 2D, 12,167 in 3D)."""
+    own, in each block size it is compiled with (512; 1024 from n = 12 on), and at
+    n = 30 also with int32 neighbour indices only: 50 FP64 sweeps and a defect
+    correction (FP32 inner sweeps) against the oracle, on plans of at least two
+    slices per SM (11,881 interior rows in 2D, 12,167 in 3D)."""
     p = build(orc, d, 110 if d == 2 else 24, m, seed=57, n=n)
     G = torch.cuda.get_device_properties(0).multi_processor_count
     assert (p.NI + 31) // 32 >= 2 * G
@@ -295,8 +296,11 @@ def test_split_launch_every_compiled_stencil_size(rb, orc, d, m, n):
     ou, os_, ores, _ = orc.solve_explicit(p.w, p.idx, p.interior, p.f, p.u0, dt, K, 0.0)
     args = (dt, 1e-7, 2, 60, 1e-3)
     du, oo, oi, _, _ = orc.solve_dc(p.w, p.idx, p.interior, p.f, p.u0, *args)
-    for threads in ((512,) if n < 12 else (512, 1024)):
-        plan = _plan(rb, p, rb.RBFFD_LAUNCH_SPLIT)
+    shapes = [(th, 0) for th in ((512,) if n < 12 else (512, 1024))]
+    if n == 30:   # and with int32 neighbour indices only
+        shapes += [(512, rb.RBFFD_PACK_IDX32), (1024, rb.RBFFD_PACK_IDX32)]
+    for threads, pack in shapes:
+        plan = _plan(rb, p, rb.RBFFD_LAUNCH_SPLIT | pack)
         plan.set_block(threads)
         u = T(p.u0)
         code, steps, res = plan.solve_explicit(T(p.f), u, dt, K, 0.0)
@@ -463,13 +467,15 @@ def test_adjoint_parity(rb, orc):
     sens = gen.sensors(p.NI, 40, 2)
     dLdu[p.interior[sens]] = gen.random_vector(40, 3)
     gf, gg, l0 = orc.adjoint(p.w, p.idx, p.interior, p.N, dLdu, K, dt)
-    plan = _plan(rb, p)
-    plan.transpose()
-    plan.transpose()                  # a second call keeps the built transpose
-    g_f, g_g, g_l0 = plan.adjoint(T(dLdu), K, dt)
-    for a, b in ((H(g_f), gf), (H(g_g), gg), (H(g_l0), l0)):
-        assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(b))
-    plan.destroy()
+    # reverse steps as plain and as programmatic dependent launches
+    for flags in (rb.RBFFD_LAUNCH_NO_PDL, rb.RBFFD_LAUNCH_PDL):
+        plan = _plan(rb, p, flags)
+        plan.transpose()
+        plan.transpose()                  # a second call keeps the built transpose
+        g_f, g_g, g_l0 = plan.adjoint(T(dLdu), K, dt)
+        for a, b in ((H(g_f), gf), (H(g_g), gg), (H(g_l0), l0)):
+            assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(b))
+        plan.destroy()
 
 
 def test_adjoint_with_boundary_sensors(rb, orc):

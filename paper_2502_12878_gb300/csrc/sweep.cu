@@ -334,10 +334,11 @@ __global__ void graph_finish(StepCtrl* c) {
 }
 
 // --------------------------------------------------------- DC kernels
-// d = W u - f (FP64 chain), d32 = (float) d; max |d| into *dmax (bits)
+// d = W u - f (FP64 chain), d32 = (float) d; max |d| into *dmax (bits); the
+// register budget and index codes as power_apply below
 template <int NN>
-__global__ void __launch_bounds__(STEP_THREADS) defect_kernel(StepArgs A, const double* u,
-                                                              unsigned long long* dmax) {
+__global__ void __launch_bounds__(STEP_THREADS, NN > 0 ? 4 : 1) defect_kernel(StepArgs A, const double* u,
+                                                                 unsigned long long* dmax) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * (STEP_THREADS / 32) + (threadIdx.x >> 5);
     const int64_t nw = (int64_t)gridDim.x * (STEP_THREADS / 32);
@@ -346,7 +347,11 @@ __global__ void __launch_bounds__(STEP_THREADS) defect_kernel(StepArgs A, const 
         const int64_t row = sl * SLICE + lane;
         const int64_t base = sl * (int64_t)A.n * SLICE + lane;
         if (row < A.NI) {
-            double acc = row_dot64<NN>(A.w64 + base, A.col + base, u, A.n);
+            const int4 sb = A.col16 ? __ldg(A.sbase + sl) : make_int4(-1, -1, -1, -1);
+            const double acc =
+                sb.x >= 0 ? row_dot<NN, false, true, double>(A.w64 + base, A.col16 + base, sb, u,
+                                                             A.n)
+                          : row_dot64<NN>(A.w64 + base, A.col + base, u, A.n);
             double dr = __dsub_rn(acc, A.f[row]);
             A.d32[row] = (float)dr;
             double a = fabs(dr);
@@ -364,10 +369,14 @@ __global__ void dc_update(double* u, const float* e, int64_t NI) {
 }
 
 // ----------------------------------------------- power iteration kernels
-// y = W_II v (v in slot order, boundary slots 0); partial sums of y^2 per block
+// y = W_II v (v in slot order, boundary slots 0); partial sums of y^2 per
+// block.  Four blocks of 256 per SM (the register budget of 64; no budget for
+// the generic stencil size, which needs more) and the plan's 16-bit neighbour
+// codes where a slice has them, as the step kernels: the same columns, so the
+// same sums.
 template <int NN>
-__global__ void __launch_bounds__(STEP_THREADS) power_apply(StepArgs A, const double* v, double* y,
-                                                            double* part) {
+__global__ void __launch_bounds__(STEP_THREADS, NN > 0 ? 4 : 1) power_apply(StepArgs A, const double* v,
+                                                               double* y, double* part) {
     __shared__ double ws[STEP_THREADS / 32];
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * (STEP_THREADS / 32) + (threadIdx.x >> 5);
@@ -377,7 +386,11 @@ __global__ void __launch_bounds__(STEP_THREADS) power_apply(StepArgs A, const do
         const int64_t row = sl * SLICE + lane;
         const int64_t base = sl * (int64_t)A.n * SLICE + lane;
         if (row < A.NI) {
-            double acc = row_dot64<NN>(A.w64 + base, A.col + base, v, A.n);
+            const int4 sb = A.col16 ? __ldg(A.sbase + sl) : make_int4(-1, -1, -1, -1);
+            const double acc =
+                sb.x >= 0 ? row_dot<NN, false, true, double>(A.w64 + base, A.col16 + base, sb, v,
+                                                             A.n)
+                          : row_dot64<NN>(A.w64 + base, A.col + base, v, A.n);
             y[row] = acc;
             s = __fma_rn(acc, acc, s);
         }
@@ -1666,7 +1679,7 @@ extern "C" int rbffd_solve_dc(rbffd_plan* p, const double* f, double* u, double 
     if (st) return st;
     StepArgs A = make_args(p);
     const int sms = device_sm_count();
-    const int grid = step_grid(p);
+    const int grid = grid_for(p, 4);
     unsigned long long* dmax = reinterpret_cast<unsigned long long*>(p->scratch);
     typedef void (*DefFn)(StepArgs, const double*, unsigned long long*);
     DefFn def;
@@ -1797,7 +1810,7 @@ extern "C" int rbffd_stable_dt(rbffd_plan* p, const double* v0, int iters, doubl
         case 70: pf = power_apply<70>; break;
         default: pf = power_apply<0>; break;
     }
-    const int grid = std::min(step_grid(p), nparts);
+    const int grid = std::min(grid_for(p, 4), nparts);
     for (int it = 0; it < iters; ++it) {
         if (p->NN > 0) {   // Neumann values of v from its interior values (data 0)
             const unsigned ngr = (unsigned)std::max<int64_t>(1, std::min<int64_t>((p->NN + 255) / 256, 1024));

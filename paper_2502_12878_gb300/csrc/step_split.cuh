@@ -70,13 +70,22 @@ __device__ __forceinline__ T row_dot_split(const T* __restrict__ w, const void* 
     return acc;
 }
 
+// |x| of a float as IEEE bits, NaN mapped to +Inf: orders like |x| (widened to
+// double once per step, it gives the residual slot's bits without an FP64
+// conversion per row)
+__device__ __forceinline__ unsigned abs_bits32(float x) {
+    const unsigned b = __float_as_uint(x) & 0x7fffffffu;
+    return b > 0x7f800000u ? 0x7f800000u : b;
+}
+
 // one row of the split launch: its stencil from the packed planes (16-bit
 // codes where the slice has them), u_i from the own-row buffer; returns the
-// new value and folds |r| into m
+// new value and folds |r| into m (FP64: as double bits; FP32 inner sweep: as
+// float bits, widened at the step's end)
 template <int NN, int MODE, bool OWN, int TH, class T>
 __device__ __forceinline__ T split_row(const StepArgs& A, int64_t sl, int32_t row, int lane,
                                        const T* o, int32_t r0, uint32_t nown, const T* u,
-                                       double dt, unsigned long long& m) {
+                                       double dt, float dt32, unsigned long long& m) {
     const int64_t base = sl * (int64_t)A.n * SLICE + lane;
     const int4 sb = A.col16 ? __ldg(A.sbase + sl) : make_int4(-1, -1, -1, -1);
     // loads in flight per thread: fewer for the generic size and in the FP64
@@ -106,8 +115,8 @@ __device__ __forceinline__ T split_row(const StepArgs& A, int64_t sl, int32_t ro
                       : row_dot_split<NN, OWN, false, CH, float>(A.w32 + base, A.col + base, sb, o,
                                                              r0, nown, u, A.n);
         const float rho = __fadd_rn(acc, di);
-        m = max(m, abs_bits(rho));
-        return __fmaf_rn((float)dt, rho, ei);
+        m = max(m, (unsigned long long)abs_bits32(rho));
+        return __fmaf_rn(dt32, rho, ei);
     }
 }
 
@@ -140,6 +149,7 @@ __global__ void __launch_bounds__(TH, 1) split_kernel(StepArgs A, StepCtrl* c) {
     __shared__ int s_held, s_fail, s_dn, s_next;
     __shared__ unsigned s_go;   // steps whose barrier warp 0 has passed (k - k0 + 1)
     __shared__ double s_dt;
+    __shared__ float s_dt32;
     // the stop decision's state lives in shared memory: only thread 0 uses it,
     // and registers are the 1024-thread blocks' tight budget
     __shared__ LagState S;
@@ -158,6 +168,7 @@ __global__ void __launch_bounds__(TH, 1) split_kernel(StepArgs A, StepCtrl* c) {
         s_k = vc->k;
         s_max = vc->max_steps;
         s_dt = vc->dt;
+        s_dt32 = (float)vc->dt;
         constexpr long long dflt = SPIN_LIMIT_CYCLES;
         const long long lim = vc->spin_limit;
         s_spin = lim > 0 ? lim : dflt;
@@ -224,7 +235,7 @@ __global__ void __launch_bounds__(TH, 1) split_kernel(StepArgs A, StepCtrl* c) {
                 if (row < NI32)
                     o_next[row - r0] =
                         split_row<NN, MODE, true, TH, T>(A, s0 + i, row, lane, o_cur, r0,
-                                                         (uint32_t)nown, ucur, s_dt, m);
+                                                         (uint32_t)nown, ucur, s_dt, s_dt32, m);
             }
             // warp 0's flag (its own wait is bounded by `spin`)
             if (lane == 0) {
@@ -257,11 +268,12 @@ __global__ void __launch_bounds__(TH, 1) split_kernel(StepArgs A, StepCtrl* c) {
             const int32_t row = r0 + i * SLICE + lane;
             if (row < NI32) {
                 const T v = split_row<NN, MODE, false, TH, T>(A, s0 + i, row, lane, o_cur, r0,
-                                                              (uint32_t)nown, ucur, s_dt, m);
+                                                              (uint32_t)nown, ucur, s_dt, s_dt32, m);
                 unext[row] = v;
                 o_next[row - r0] = v;
             }
         }
+        if constexpr (MODE == MODE_INNER32) m = abs_bits((double)__uint_as_float((unsigned)m));
         m = res_block_max<TH>(m);
         if (threadIdx.x == 0) {
             res_arrive(c, k, m);

@@ -418,7 +418,8 @@ RBFFD_API int rbffd_solve_explicit(rbffd_plan* plan, const double* f, double* u,
  * launched; h_shape[4], the autotuned launch shape (register budget, blocks
  * per SM; 0 blocks per SM = the persistent launch, -1 = the resident launch,
  * whose first entry is then its block size in units of 512 threads, + 4
- * when it stages far lists (every gather from shared memory);
+ * when it stages far lists (every gather from shared memory), -2 = the split
+ * launch, whose first entry is its block size in units of 512 threads;
  * blocks per SM + 16 = graph-replayed steps launched as programmatic
  * dependent launches) of the FP64 sweep and of the FP32 inner sweep.
  */

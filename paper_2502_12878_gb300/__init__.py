@@ -438,7 +438,11 @@ class Plan:
         return gw, gf, gg, l0
 
     def stats(self):
-        """(GPU ms of the last solve's step loops, their steps, kernels launched, launch shape)."""
+        """(GPU ms of the last solve's step loops, their steps, kernels launched, launch shape).
+        The shape is [a, b] for the FP64 sweep then for the FP32 inner sweep: b = -2 split
+        launch (a = threads / 512), -1 resident launch (a = threads / 512, + 4 with far
+        lists), 0 grid-stride persistent launch (a = register budget), else graph-replayed
+        steps with b blocks per SM (+ 16 as programmatic dependent launches, a = budget)."""
         ms = ctypes.c_double(0.0)
         steps = ctypes.c_int64(0)
         launches = ctypes.c_int64(0)
